@@ -1,0 +1,206 @@
+/*
+ * vsz.h -- C ABI of the GB300 dual-quantization library (libvsz.so).
+ *
+ * The library implements the prediction-and-quantization step of SZ as the
+ * paper "SIMD Lossy Compression for Scientific Data" (arXiv 2201.04614)
+ * restates it (dual-quantization, Sec. III-A, Alg. 2), with the paper's
+ * error-bound modes (Sec. II-B) and padding values (Sec. IV), and its inverse.
+ * Every step runs in the library's own CUDA kernels for sm_103a.
+ *
+ * Conventions for every call:
+ *  - Fields are fp32, C-order: dims[0] is the slowest axis, dims[ndim-1] the
+ *    fastest (x).  Blocks are b^ndim boxes; blocks at the + edges are
+ *    truncated.  Blocks are numbered in row-major order over the block grid.
+ *  - "d_" pointers are device pointers; "h_" pointers are host pointers.
+ *  - The caller owns every buffer.  The library allocates nothing on the
+ *    compression and reconstruction paths (the batch API caches one small
+ *    descriptor table per handle, freed by vsz_batch_destroy).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  All calls are asynchronous on it unless stated otherwise, and
+ *    none synchronizes the device, so sequences of calls can be captured
+ *    into a CUDA graph.
+ *  - Errors are returned as a vsz_status; nothing aborts, traps or throws.
+ *    Errors that only the device can see (capacity overflow, inconsistent
+ *    outlier data) are recorded in the vsz_header in device memory and are
+ *    read with vsz_read_header().
+ */
+#ifndef VSZ_H
+#define VSZ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VSZ_ABI_VERSION 1
+
+#if defined(__GNUC__)
+#define VSZ_API __attribute__((visibility("default")))
+#else
+#define VSZ_API
+#endif
+
+typedef enum {
+    VSZ_OK = 0,
+    VSZ_ERR_INVALID_ARG = 1,  /* a NULL pointer, a bad size or parameter */
+    VSZ_ERR_UNSUPPORTED = 2,  /* valid for the method, not built (e.g. ndim 4) */
+    VSZ_ERR_CAPACITY = 3,     /* outlier or fixup lists longer than the caller's capacity */
+    VSZ_ERR_CUDA = 4,         /* a CUDA launch or runtime call failed */
+    VSZ_ERR_CORRUPT = 5       /* reconstruction met a code 0 with no matching outlier */
+} vsz_status;
+
+/* Sec. II-B: absolute, or value-range relative (eb * (max - min)). */
+typedef enum { VSZ_EB_ABS = 0, VSZ_EB_REL = 1 } vsz_eb_mode;
+
+/* Sec. IV: padding value standing in for every Lorenzo neighbour outside a
+ * block: zero (cuSZ), or the min / max / average of the prequantized data,
+ * over the whole field (global, Sec. IV-B-1) or per block (Sec. IV-B-2). */
+typedef enum {
+    VSZ_PAD_ZERO = 0,
+    VSZ_PAD_GLOBAL_MIN = 1,
+    VSZ_PAD_GLOBAL_MAX = 2,
+    VSZ_PAD_GLOBAL_AVG = 3,
+    VSZ_PAD_BLOCK_MIN = 4,
+    VSZ_PAD_BLOCK_MAX = 5,
+    VSZ_PAD_BLOCK_AVG = 6
+} vsz_pad_mode;
+
+/* The paper's statement of the problem: field dims, block size, error bound
+ * and its mode, quantization radius, padding mode. */
+typedef struct {
+    int32_t  ndim;       /* 1, 2 or 3 (4D is VSZ_ERR_UNSUPPORTED) */
+    uint64_t dims[3];    /* C-order extents, dims[0] slowest; product < 2^32 */
+    uint32_t block;      /* block edge b, a power of two: 1D 4..256, 2D 4..128, 3D 4..32 */
+    double   eb;         /* error bound, finite and > 0 */
+    int32_t  eb_mode;    /* vsz_eb_mode */
+    uint32_t radius;     /* R, 1..32768: codes are delta+R in [1, 2R-1], 0 = outlier */
+    int32_t  pad;        /* vsz_pad_mode */
+} vsz_params;
+
+/* Per-field header in device memory (caller-allocated, sizeof(vsz_header)
+ * bytes, 8-byte aligned).  Compression writes it; reconstruction reads the
+ * scalars it needs from it, so no host round trip is needed between them. */
+typedef struct {
+    double   eb_abs;       /* absolute error bound used (Sec. II-B) */
+    float    inv2eb;       /* (float)(1 / (2 eb_abs)), rounded once */
+    float    ebx2;         /* (float)(2 eb_abs) */
+    float    eb_f32;       /* largest float <= eb_abs: the guard's bound */
+    float    xmin, xmax;   /* finite range of the input (valid if has_range) */
+    int32_t  pad_global;   /* P for ZERO and GLOBAL_* modes (q domain) */
+    uint32_t has_range;
+    uint32_t status;       /* 0, or a vsz_status raised by compression */
+    uint32_t recon_status; /* 0, or a vsz_status raised by reconstruction */
+    uint32_t reserved;
+    uint64_t n_out;        /* outliers: exact count, even on overflow */
+    uint64_t n_fix;        /* fixups: exact count, even on overflow */
+} vsz_header;
+
+/* A compressed field: caller-owned device buffers. */
+typedef struct {
+    uint16_t*   codes;     /* [n] quantization codes, field layout */
+    int32_t*    pad;       /* [nb] per-block padding values (BLOCK_* modes only; else may be NULL) */
+    uint32_t*   blk_off;   /* [nb+1] outlier offsets per block, canonical order */
+    uint32_t*   out_idx;   /* [out_cap] global linear index of each outlier */
+    int32_t*    out_delta; /* [out_cap] its residual delta */
+    uint64_t    out_cap;
+    uint32_t*   fix_idx;   /* [fix_cap] index of each fixup (value kept verbatim) */
+    uint32_t*   fix_bits;  /* [fix_cap] raw fp32 bits of x */
+    uint64_t    fix_cap;
+    vsz_header* hdr;       /* device header */
+} vsz_compressed;
+
+/* Human-readable name of a status.  Never NULL. */
+VSZ_API const char* vsz_status_string(vsz_status s);
+
+/* Text of the last CUDA error that made a call on this host thread return
+ * VSZ_ERR_CUDA ("" if none).  Never NULL; valid until the next failing call. */
+VSZ_API const char* vsz_last_cuda_error(void);
+
+/* VSZ_ABI_VERSION of the loaded library. */
+VSZ_API int vsz_abi_version(void);
+
+/* Host-side check of a parameter set: VSZ_OK, VSZ_ERR_INVALID_ARG or
+ * VSZ_ERR_UNSUPPORTED.  No GPU work. */
+VSZ_API vsz_status vsz_validate(const vsz_params* p);
+
+/* Number of elements and of blocks of the field (0 if p is invalid). */
+VSZ_API uint64_t vsz_num_elems(const vsz_params* p);
+VSZ_API uint64_t vsz_num_blocks(const vsz_params* p);
+
+/* Bytes of device workspace that vsz_prequant_lorenzo / vsz_outlier_compact
+ * need for this field when the caller's lists hold out_cap outliers and
+ * fix_cap fixups (0 if p is invalid).  The workspace is caller-owned, must
+ * be 256-byte aligned, and must not be shared by calls in flight at once. */
+VSZ_API size_t vsz_workspace_size(const vsz_params* p, uint64_t out_cap, uint64_t fix_cap);
+
+/*
+ * Compression, step 1 (Sec. III-A, Alg. 2; Sec. IV; Sec. II-B): error-bound
+ * resolution, prequantization q = rint(x * inv2eb), padding value, blockwise
+ * first-order Lorenzo prediction, post-quantization into uint16 codes, and
+ * the fp32 error-bound guard.  Writes c->codes, c->pad (block modes),
+ * c->hdr (scalars), and leaves per-tile outlier and fixup lists staged in
+ * the workspace.  For VSZ_EB_REL the value range is reduced on the device;
+ * no host synchronization happens.
+ *   p         field and method parameters (host)
+ *   d_x       [n] fp32 input (device), 16-byte aligned for the vector path
+ *   c         output buffers (host struct of device pointers)
+ *   d_ws      workspace of at least vsz_workspace_size(p, c->out_cap, c->fix_cap) bytes
+ * Returns VSZ_ERR_INVALID_ARG / VSZ_ERR_UNSUPPORTED before any GPU work on
+ * bad input, VSZ_ERR_CUDA if a launch fails.
+ */
+VSZ_API vsz_status vsz_prequant_lorenzo(const vsz_params* p, const float* d_x, vsz_compressed* c,
+                                void* d_ws, size_t ws_bytes, void* stream);
+
+/*
+ * Compression, step 2: outlier compaction.  Places the staged outliers and
+ * fixups in canonical order (blocks in row-major block order, elements
+ * row-major inside each block) in c->out_idx/out_delta and c->fix_idx/
+ * fix_bits, writes c->blk_off[0..nb] and c->hdr->n_out / n_fix.  If a list
+ * is longer than its capacity, the counts and blk_off are still exact, the
+ * lists are truncated and c->hdr->status = VSZ_ERR_CAPACITY; retry with
+ * larger buffers.  Must follow vsz_prequant_lorenzo on the same workspace.
+ */
+VSZ_API vsz_status vsz_outlier_compact(const vsz_params* p, vsz_compressed* c,
+                               void* d_ws, size_t ws_bytes, void* stream);
+
+/* Both compression steps in order. */
+VSZ_API vsz_status vsz_compress(const vsz_params* p, const float* d_x, vsz_compressed* c,
+                        void* d_ws, size_t ws_bytes, void* stream);
+
+/*
+ * Decompression (Sec. III-A: the inverse of the dual-quant): residuals from
+ * the codes and the outlier lists, per-block inclusive prefix sums along x,
+ * y and z, q = e + P, x_hat = (float)q * ebx2, then fixups restore their
+ * values verbatim.  Reads the scalars from c->hdr.  |x - x_hat| <= eb(1+2^-20)
+ * for every finite x; NaN/Inf come back bit for bit.  A code 0 without a
+ * matching outlier sets c->hdr->recon_status = VSZ_ERR_CORRUPT.
+ *   d_xhat    [n] fp32 output (device)
+ */
+VSZ_API vsz_status vsz_reconstruct(const vsz_params* p, const vsz_compressed* c, float* d_xhat,
+                           void* stream);
+
+/* Same inverse, writing the reconstructed prequantized integers q (int32[n])
+ * instead of values (no fixups applied).  Used to verify that the inverse
+ * reproduces the prequantization exactly. */
+VSZ_API vsz_status vsz_reconstruct_q(const vsz_params* p, const vsz_compressed* c, int32_t* d_q,
+                             void* stream);
+
+/*
+ * Code statistics (the learned tuner's labels): d_hist[0..2R-1] receives the
+ * number of elements with each code (code 0 = outliers).  d_hist must hold
+ * 2R uint32 and is overwritten.  Shannon entropy of the codes follows from
+ * it on the host.
+ */
+VSZ_API vsz_status vsz_code_histogram(const vsz_params* p, const uint16_t* d_codes, uint32_t* d_hist,
+                              void* stream);
+
+/* Copy the device header to the host and wait for it (synchronizes the
+ * stream). */
+VSZ_API vsz_status vsz_read_header(const vsz_compressed* c, vsz_header* h_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VSZ_H */

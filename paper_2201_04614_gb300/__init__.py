@@ -1,0 +1,278 @@
+"""GB300 dual-quantization (the vecSZ hot path, arXiv 2201.04614).
+
+Thin Python binding of the C ABI in include/vsz.h (libvsz.so).  It only
+marshals arguments: every step of compression and reconstruction runs in the
+library's CUDA kernels.  PyTorch supplies device memory and streams.  There
+is no CPU fallback: without a CUDA device or the built library every call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+from . import buildlib as _build
+
+__all__ = [
+    "VszError", "Params", "Field", "lib", "build", "EB_ABS", "EB_REL", "PAD_MODES",
+    "num_blocks", "workspace_size",
+]
+
+EB_ABS, EB_REL = 0, 1
+PAD_MODES = {
+    "zero": 0, "global_min": 1, "global_max": 2, "global_avg": 3,
+    "block_min": 4, "block_max": 5, "block_avg": 6,
+}
+_STATUS = {0: "VSZ_OK", 1: "VSZ_ERR_INVALID_ARG", 2: "VSZ_ERR_UNSUPPORTED",
+           3: "VSZ_ERR_CAPACITY", 4: "VSZ_ERR_CUDA", 5: "VSZ_ERR_CORRUPT"}
+
+
+class VszError(RuntimeError):
+    def __init__(self, status: int, what: str, detail: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {_STATUS.get(status, status)}{(' (' + detail + ')') if detail else ''}")
+
+
+class _CParams(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int32), ("dims", ctypes.c_uint64 * 3), ("block", ctypes.c_uint32),
+                ("eb", ctypes.c_double), ("eb_mode", ctypes.c_int32), ("radius", ctypes.c_uint32),
+                ("pad", ctypes.c_int32)]
+
+
+class _CHeader(ctypes.Structure):
+    _fields_ = [("eb_abs", ctypes.c_double), ("inv2eb", ctypes.c_float), ("ebx2", ctypes.c_float),
+                ("eb_f32", ctypes.c_float), ("xmin", ctypes.c_float), ("xmax", ctypes.c_float),
+                ("pad_global", ctypes.c_int32), ("has_range", ctypes.c_uint32),
+                ("status", ctypes.c_uint32), ("recon_status", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32), ("n_out", ctypes.c_uint64), ("n_fix", ctypes.c_uint64)]
+
+
+class _CCompressed(ctypes.Structure):
+    _fields_ = [("codes", ctypes.c_void_p), ("pad", ctypes.c_void_p), ("blk_off", ctypes.c_void_p),
+                ("out_idx", ctypes.c_void_p), ("out_delta", ctypes.c_void_p), ("out_cap", ctypes.c_uint64),
+                ("fix_idx", ctypes.c_void_p), ("fix_bits", ctypes.c_void_p), ("fix_cap", ctypes.c_uint64),
+                ("hdr", ctypes.c_void_p)]
+
+
+HEADER_BYTES = ctypes.sizeof(_CHeader)
+EXPORTED = ["vsz_status_string", "vsz_last_cuda_error", "vsz_abi_version", "vsz_validate",
+            "vsz_num_elems", "vsz_num_blocks", "vsz_workspace_size", "vsz_prequant_lorenzo",
+            "vsz_outlier_compact", "vsz_compress", "vsz_reconstruct", "vsz_reconstruct_q",
+            "vsz_code_histogram", "vsz_read_header"]
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    return _build.build(force=force)
+
+
+def lib():
+    """Load libvsz.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB_PATH
+    if not os.path.exists(path) or _build.is_stale():
+        _build.build()
+    L = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    vp, u64, sz = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_size_t
+    L.vsz_status_string.restype = ctypes.c_char_p
+    L.vsz_status_string.argtypes = [ctypes.c_int]
+    L.vsz_last_cuda_error.restype = ctypes.c_char_p
+    L.vsz_last_cuda_error.argtypes = []
+    L.vsz_abi_version.restype = ctypes.c_int
+    L.vsz_validate.argtypes = [P(_CParams)]
+    L.vsz_num_elems.restype = u64
+    L.vsz_num_elems.argtypes = [P(_CParams)]
+    L.vsz_num_blocks.restype = u64
+    L.vsz_num_blocks.argtypes = [P(_CParams)]
+    L.vsz_workspace_size.restype = sz
+    L.vsz_workspace_size.argtypes = [P(_CParams), u64, u64]
+    for name in ("vsz_prequant_lorenzo", "vsz_compress"):
+        getattr(L, name).argtypes = [P(_CParams), vp, P(_CCompressed), vp, sz, vp]
+    L.vsz_outlier_compact.argtypes = [P(_CParams), P(_CCompressed), vp, sz, vp]
+    L.vsz_reconstruct.argtypes = [P(_CParams), P(_CCompressed), vp, vp]
+    L.vsz_reconstruct_q.argtypes = [P(_CParams), P(_CCompressed), vp, vp]
+    L.vsz_code_histogram.argtypes = [P(_CParams), vp, vp, vp]
+    L.vsz_read_header.argtypes = [P(_CCompressed), P(_CHeader), vp]
+    for name in EXPORTED:
+        if name not in ("vsz_status_string", "vsz_last_cuda_error", "vsz_abi_version",
+                        "vsz_num_elems", "vsz_num_blocks", "vsz_workspace_size"):
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        detail = lib().vsz_last_cuda_error().decode() if rc == 4 else ""
+        raise VszError(rc, what, detail)
+
+
+@dataclass(frozen=True)
+class Params:
+    """Field dims (C-order, dims[0] slowest), block edge, error bound and its
+    mode, radius R, padding mode -- the paper's statement of the problem."""
+    dims: tuple
+    block: int
+    eb: float
+    eb_mode: int = EB_REL
+    radius: int = 512
+    pad: int = 0
+
+    @classmethod
+    def make(cls, dims, block, eb, eb_mode="rel", radius=512, pad="zero") -> "Params":
+        em = {"abs": EB_ABS, "rel": EB_REL}[eb_mode] if isinstance(eb_mode, str) else int(eb_mode)
+        pm = PAD_MODES[pad] if isinstance(pad, str) else int(pad)
+        return cls(tuple(int(d) for d in dims), int(block), float(eb), em, int(radius), pm)
+
+    def c(self) -> _CParams:
+        d = list(self.dims) + [0] * (3 - len(self.dims))
+        return _CParams(len(self.dims), (ctypes.c_uint64 * 3)(*d), self.block, self.eb,
+                        self.eb_mode, self.radius, self.pad)
+
+    @property
+    def n(self) -> int:
+        return int(lib().vsz_num_elems(ctypes.byref(self.c())))
+
+    @property
+    def nblocks(self) -> int:
+        return int(lib().vsz_num_blocks(ctypes.byref(self.c())))
+
+    @property
+    def is_block_pad(self) -> bool:
+        return self.pad in (4, 5, 6)
+
+    def validate(self) -> int:
+        return int(lib().vsz_validate(ctypes.byref(self.c())))
+
+
+def num_blocks(p: Params) -> int:
+    return p.nblocks
+
+
+def workspace_size(p: Params, out_cap: int, fix_cap: int) -> int:
+    return int(lib().vsz_workspace_size(ctypes.byref(p.c()), out_cap, fix_cap))
+
+
+def _stream_handle(stream) -> ctypes.c_void_p:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr() if t is not None and t.numel() > 0 else 0)
+
+
+class Field:
+    """Device buffers of one compressed field, and the calls on them.
+
+    codes int16[n] (uint16 codes), pad int32[nb] (block padding modes),
+    blk_off int32[nb+1] (uint32 offsets), out_idx/out_delta int32[out_cap],
+    fix_idx/fix_bits int32[fix_cap], hdr (device vsz_header), ws (workspace).
+    """
+
+    def __init__(self, params: Params, out_cap: int | None = None, fix_cap: int | None = None,
+                 device=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("paper_2201_04614_gb300 needs a CUDA device (no CPU fallback)")
+        rc = params.validate()
+        _check(rc, "vsz_validate")
+        self.p = params
+        dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        n, nb = params.n, params.nblocks
+        self.n, self.nb = n, nb
+        self.out_cap = int(out_cap if out_cap is not None else max(1024, n))
+        self.fix_cap = int(fix_cap if fix_cap is not None else max(1024, n // 64))
+        i32 = torch.int32
+        self.codes = torch.empty(max(n, 1), dtype=torch.int16, device=dev)
+        self.pad = torch.empty(max(nb, 1), dtype=i32, device=dev) if params.is_block_pad else None
+        self.blk_off = torch.empty(nb + 1, dtype=i32, device=dev)
+        self.out_idx = torch.empty(max(self.out_cap, 1), dtype=i32, device=dev)
+        self.out_delta = torch.empty(max(self.out_cap, 1), dtype=i32, device=dev)
+        self.fix_idx = torch.empty(max(self.fix_cap, 1), dtype=i32, device=dev)
+        self.fix_bits = torch.empty(max(self.fix_cap, 1), dtype=i32, device=dev)
+        self.hdr = torch.zeros((HEADER_BYTES + 7) // 8, dtype=torch.int64, device=dev)
+        self.ws_bytes = workspace_size(params, self.out_cap, self.fix_cap)
+        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=dev)
+        self._cp = params.c()
+        self._cc = _CCompressed(self.codes.data_ptr(), self.pad.data_ptr() if self.pad is not None else 0,
+                                self.blk_off.data_ptr(), self.out_idx.data_ptr(), self.out_delta.data_ptr(),
+                                self.out_cap, self.fix_idx.data_ptr(), self.fix_bits.data_ptr(),
+                                self.fix_cap, self.hdr.data_ptr())
+
+    # ---- calls through the C ABI -------------------------------------------
+    def _x(self, x):
+        import torch
+        if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float32 and x.is_contiguous()):
+            raise TypeError("x must be a contiguous float32 CUDA tensor")
+        if x.numel() != self.n:
+            raise ValueError(f"x has {x.numel()} elements, params describe {self.n}")
+        return ctypes.c_void_p(x.data_ptr() if self.n else 0)
+
+    def prequant_lorenzo(self, x, stream=None):
+        _check(lib().vsz_prequant_lorenzo(ctypes.byref(self._cp), self._x(x), ctypes.byref(self._cc),
+                                          _ptr(self.ws), self.ws_bytes, _stream_handle(stream)),
+               "vsz_prequant_lorenzo")
+
+    def outlier_compact(self, stream=None):
+        _check(lib().vsz_outlier_compact(ctypes.byref(self._cp), ctypes.byref(self._cc), _ptr(self.ws),
+                                         self.ws_bytes, _stream_handle(stream)), "vsz_outlier_compact")
+
+    def compress(self, x, stream=None):
+        _check(lib().vsz_compress(ctypes.byref(self._cp), self._x(x), ctypes.byref(self._cc), _ptr(self.ws),
+                                  self.ws_bytes, _stream_handle(stream)), "vsz_compress")
+
+    def reconstruct(self, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(max(self.n, 1), dtype=torch.float32, device=self.codes.device)
+        _check(lib().vsz_reconstruct(ctypes.byref(self._cp), ctypes.byref(self._cc), _ptr(out),
+                                     _stream_handle(stream)), "vsz_reconstruct")
+        return out[: self.n]
+
+    def reconstruct_q(self, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(max(self.n, 1), dtype=torch.int32, device=self.codes.device)
+        _check(lib().vsz_reconstruct_q(ctypes.byref(self._cp), ctypes.byref(self._cc), _ptr(out),
+                                       _stream_handle(stream)), "vsz_reconstruct_q")
+        return out[: self.n]
+
+    def code_histogram(self, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(2 * self.p.radius, dtype=torch.int32, device=self.codes.device)
+        _check(lib().vsz_code_histogram(ctypes.byref(self._cp), _ptr(self.codes), _ptr(out),
+                                        _stream_handle(stream)), "vsz_code_histogram")
+        return out
+
+    def header(self, stream=None) -> dict:
+        h = _CHeader()
+        _check(lib().vsz_read_header(ctypes.byref(self._cc), ctypes.byref(h), _stream_handle(stream)),
+               "vsz_read_header")
+        return {k: getattr(h, k) for k, _ in _CHeader._fields_}
+
+    # ---- host copies of the results (synchronizing) ------------------------
+    def to_host(self) -> dict:
+        """Codes, pads, offsets, outliers and fixups as numpy arrays."""
+        import numpy as np
+        h = self.header()
+        no, nf = int(h["n_out"]), int(h["n_fix"])
+        if h["status"] != 0:
+            raise VszError(int(h["status"]), "compression")
+        return {
+            "header": h,
+            "codes": self.codes[: self.n].cpu().numpy().view(np.uint16),
+            "pad": self.pad[: self.nb].cpu().numpy() if self.pad is not None else None,
+            "blk_off": self.blk_off.cpu().numpy().view(np.uint32),
+            "out_idx": self.out_idx[:no].cpu().numpy().view(np.uint32),
+            "out_delta": self.out_delta[:no].cpu().numpy(),
+            "fix_idx": self.fix_idx[:nf].cpu().numpy().view(np.uint32),
+            "fix_bits": self.fix_bits[:nf].cpu().numpy().view(np.uint32),
+        }

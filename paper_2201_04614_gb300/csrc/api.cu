@@ -1,0 +1,300 @@
+// api.cu -- host implementation of the vsz.h C ABI.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <unordered_map>
+
+#include "common.cuh"
+#include "misc.cuh"
+
+namespace vsz {
+
+int num_sms() {
+    static int cached[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+    if (!cached[dev]) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 148;
+        cached[dev] = v;
+    }
+    return cached[dev];
+}
+
+// CTAs for a grid-stride kernel: enough to cover `work` at `per_cta` items
+// each, capped at the number of CTAs that are resident at once.
+int grid_for(const void* kernel, int threads, size_t smem, uint64_t per_cta, uint64_t work) {
+    static std::mutex mu;
+    static std::unordered_map<const void*, int> occ_cache;
+    int occ = 0;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = occ_cache.find(kernel);
+        if (it != occ_cache.end()) {
+            occ = it->second;
+        } else {
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, smem) != cudaSuccess || occ < 1)
+                occ = 1;
+            occ_cache[kernel] = occ;
+        }
+    }
+    const uint64_t want = (work + per_cta - 1) / (per_cta ? per_cta : 1);
+    const uint64_t cap = (uint64_t)num_sms() * (uint64_t)occ;
+    uint64_t g = want < cap ? want : cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+static thread_local char g_last_err[256] = "";
+
+static vsz_status cuda_fail(cudaError_t e) {
+    std::snprintf(g_last_err, sizeof g_last_err, "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+    return VSZ_ERR_CUDA;
+}
+
+static bool pow2(uint32_t v) { return v && !(v & (v - 1)); }
+
+// Validate parameters and derive the geometry and tiling of a field.
+static vsz_status make_geom(const vsz_params* p, Geom* g) {
+    if (!p) return VSZ_ERR_INVALID_ARG;
+    if (p->ndim == 4) return VSZ_ERR_UNSUPPORTED;
+    if (p->ndim < 1 || p->ndim > 3) return VSZ_ERR_INVALID_ARG;
+    if (!(p->eb > 0.0) || !std::isfinite(p->eb)) return VSZ_ERR_INVALID_ARG;
+    if (p->eb_mode != VSZ_EB_ABS && p->eb_mode != VSZ_EB_REL) return VSZ_ERR_INVALID_ARG;
+    if (p->radius < 1 || p->radius > 32768) return VSZ_ERR_INVALID_ARG;
+    if (p->pad < VSZ_PAD_ZERO || p->pad > VSZ_PAD_BLOCK_AVG) return VSZ_ERR_INVALID_ARG;
+    if (p->block < 1) return VSZ_ERR_INVALID_ARG;
+    const uint32_t bmax = p->ndim == 1 ? 256u : p->ndim == 2 ? 128u : 32u;
+    if (!pow2(p->block) || p->block < 4 || p->block > bmax) return VSZ_ERR_UNSUPPORTED;
+    uint64_t n = 1;
+    for (int k = 0; k < p->ndim; ++k) {
+        const uint64_t d = p->dims[k];
+        if (d >= (1ull << 32)) return VSZ_ERR_INVALID_ARG;
+        n *= d;
+        if (n >= (1ull << 32)) return VSZ_ERR_INVALID_ARG;
+    }
+    std::memset(g, 0, sizeof *g);
+    g->nd = p->ndim;
+    g->b = p->block;
+    g->n = n;
+    const uint64_t b = p->block;
+    g->nz = p->ndim == 3 ? p->dims[0] : 1;
+    g->ny = p->ndim == 3 ? p->dims[1] : p->ndim == 2 ? p->dims[0] : 1;
+    g->nx = p->dims[p->ndim - 1];
+    g->nbx = (g->nx + b - 1) / b;
+    g->nby = p->ndim >= 2 ? (g->ny + b - 1) / b : 1;
+    g->nbz = p->ndim == 3 ? (g->nz + b - 1) / b : 1;
+    g->nb = n ? g->nbx * g->nby * g->nbz : 0;
+    if (n == 0) {
+        g->nseg = 0;
+        g->ntiles = 0;
+        g->bpt = p->ndim == 1 ? (uint32_t)(kChunk1D / b) : (uint32_t)(kSegCols / b);
+    } else if (p->ndim == 1) {
+        g->ntiles = (n + kChunk1D - 1) / kChunk1D;
+        g->nseg = g->ntiles;
+        g->bpt = (uint32_t)(kChunk1D / b);
+    } else {
+        g->nseg = (g->nx + kSegCols - 1) / kSegCols;
+        g->ntiles = g->nseg * g->nby * g->nbz;
+        g->bpt = (uint32_t)(kSegCols / b);
+    }
+    g->nchunks = (g->ntiles + kTilesPerChunk - 1) / kTilesPerChunk;
+    return VSZ_OK;
+}
+
+static bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+}  // namespace vsz
+
+using namespace vsz;
+
+extern "C" {
+
+const char* vsz_status_string(vsz_status s) {
+    switch (s) {
+    case VSZ_OK: return "VSZ_OK";
+    case VSZ_ERR_INVALID_ARG: return "VSZ_ERR_INVALID_ARG";
+    case VSZ_ERR_UNSUPPORTED: return "VSZ_ERR_UNSUPPORTED";
+    case VSZ_ERR_CAPACITY: return "VSZ_ERR_CAPACITY";
+    case VSZ_ERR_CUDA: return "VSZ_ERR_CUDA";
+    case VSZ_ERR_CORRUPT: return "VSZ_ERR_CORRUPT";
+    default: return "VSZ_ERR_UNKNOWN";
+    }
+}
+
+const char* vsz_last_cuda_error(void) { return g_last_err; }
+
+int vsz_abi_version(void) { return VSZ_ABI_VERSION; }
+
+vsz_status vsz_validate(const vsz_params* p) {
+    Geom g;
+    return make_geom(p, &g);
+}
+
+uint64_t vsz_num_elems(const vsz_params* p) {
+    Geom g;
+    return make_geom(p, &g) == VSZ_OK ? g.n : 0;
+}
+
+uint64_t vsz_num_blocks(const vsz_params* p) {
+    Geom g;
+    return make_geom(p, &g) == VSZ_OK ? g.nb : 0;
+}
+
+size_t vsz_workspace_size(const vsz_params* p, uint64_t out_cap, uint64_t fix_cap) {
+    Geom g;
+    if (make_geom(p, &g) != VSZ_OK) return 0;
+    return ws_layout(g, out_cap, fix_cap).total;
+}
+
+static vsz_status check_compressed(const Geom& g, const vsz_params* p, const vsz_compressed* c) {
+    if (!c || !c->hdr || !c->blk_off) return VSZ_ERR_INVALID_ARG;
+    if (!aligned(c->hdr, 8)) return VSZ_ERR_INVALID_ARG;
+    if (g.n > 0 && !c->codes) return VSZ_ERR_INVALID_ARG;
+    if (is_block_pad(p->pad) && g.nb > 0 && !c->pad) return VSZ_ERR_INVALID_ARG;
+    if (c->out_cap > 0 && (!c->out_idx || !c->out_delta)) return VSZ_ERR_INVALID_ARG;
+    if (c->fix_cap > 0 && (!c->fix_idx || !c->fix_bits)) return VSZ_ERR_INVALID_ARG;
+    if (c->out_cap >= (1ull << 32) || c->fix_cap >= (1ull << 32)) return VSZ_ERR_INVALID_ARG;
+    return VSZ_OK;
+}
+
+vsz_status vsz_prequant_lorenzo(const vsz_params* p, const float* d_x, vsz_compressed* c, void* d_ws,
+                                size_t ws_bytes, void* stream) {
+    Geom g;
+    vsz_status st = make_geom(p, &g);
+    if (st != VSZ_OK) return st;
+    if ((st = check_compressed(g, p, c)) != VSZ_OK) return st;
+    if (g.n > 0 && !d_x) return VSZ_ERR_INVALID_ARG;
+    const WsLayout L = ws_layout(g, c->out_cap, c->fix_cap);
+    if (!d_ws || ws_bytes < L.total || !aligned(d_ws, 256)) return VSZ_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    char* ws = (char*)d_ws;
+    WsHeader* wsh = (WsHeader*)ws;
+    uint4* tiles = (uint4*)(ws + L.tiles);
+    uint4* chunks = (uint4*)(ws + L.chunks);
+    const bool rel = p->eb_mode == VSZ_EB_REL;
+    const bool xvec = aligned(d_x, 16);
+
+    cudaError_t e = launch_begin(wsh, chunks, g.nchunks, c->hdr, p->eb, rel, s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (rel) {
+        e = launch_range(d_x, g.n, wsh, c->hdr, p->eb, xvec, s);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    if (p->pad == VSZ_PAD_GLOBAL_MIN || p->pad == VSZ_PAD_GLOBAL_MAX || p->pad == VSZ_PAD_GLOBAL_AVG) {
+        e = launch_qstats(d_x, g.n, wsh, c->hdr, p->pad, xvec, s);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    if (g.ntiles == 0) return VSZ_OK;
+
+    CompressArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.x = d_x;
+    a.codes = c->codes;
+    a.pad = c->pad;
+    a.blk_off = c->blk_off;
+    a.hdr = c->hdr;
+    a.wsh = wsh;
+    a.tiles = tiles;
+    a.chunks = chunks;
+    a.stage_out = (uint2*)(ws + L.stage_out);
+    a.stage_fix = (uint2*)(ws + L.stage_fix);
+    a.out_cap = c->out_cap;
+    a.fix_cap = c->fix_cap;
+    a.g = g;
+    a.R = (int32_t)p->radius;
+    a.pad_mode = p->pad;
+    a.vec = (xvec && aligned(c->codes, 16) && (g.nd == 1 || g.nx % 4 == 0)) ? 1 : 0;
+    e = g.nd == 1 ? launch_lorenzo_1d(a, s) : g.nd == 2 ? launch_lorenzo_2d(a, s) : launch_lorenzo_3d(a, s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return VSZ_OK;
+}
+
+vsz_status vsz_outlier_compact(const vsz_params* p, vsz_compressed* c, void* d_ws, size_t ws_bytes,
+                               void* stream) {
+    Geom g;
+    vsz_status st = make_geom(p, &g);
+    if (st != VSZ_OK) return st;
+    if ((st = check_compressed(g, p, c)) != VSZ_OK) return st;
+    const WsLayout L = ws_layout(g, c->out_cap, c->fix_cap);
+    if (!d_ws || ws_bytes < L.total || !aligned(d_ws, 256)) return VSZ_ERR_INVALID_ARG;
+    char* ws = (char*)d_ws;
+    cudaError_t e = launch_compact(g, (uint4*)(ws + L.tiles), (uint4*)(ws + L.chunks), c->hdr, c->blk_off,
+                                   (const uint2*)(ws + L.stage_out), (const uint2*)(ws + L.stage_fix), c->out_idx,
+                                   c->out_delta, c->out_cap, c->fix_idx, c->fix_bits, c->fix_cap,
+                                   (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return VSZ_OK;
+}
+
+vsz_status vsz_compress(const vsz_params* p, const float* d_x, vsz_compressed* c, void* d_ws, size_t ws_bytes,
+                        void* stream) {
+    vsz_status st = vsz_prequant_lorenzo(p, d_x, c, d_ws, ws_bytes, stream);
+    if (st != VSZ_OK) return st;
+    return vsz_outlier_compact(p, c, d_ws, ws_bytes, stream);
+}
+
+static vsz_status reconstruct_impl(const vsz_params* p, const vsz_compressed* c, void* out, bool q_out,
+                                   void* stream) {
+    Geom g;
+    vsz_status st = make_geom(p, &g);
+    if (st != VSZ_OK) return st;
+    if ((st = check_compressed(g, p, c)) != VSZ_OK) return st;
+    if (g.n > 0 && !out) return VSZ_ERR_INVALID_ARG;
+    if (g.n == 0) return VSZ_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    ReconArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.codes = c->codes;
+    a.pad = c->pad;
+    a.blk_off = c->blk_off;
+    a.out_idx = c->out_idx;
+    a.out_delta = c->out_delta;
+    a.out_cap = c->out_cap;
+    a.hdr = c->hdr;
+    a.out = out;
+    a.g = g;
+    a.R = (int32_t)p->radius;
+    a.pad_mode = p->pad;
+    a.vec = (aligned(c->codes, 16) && aligned(out, 16) && (g.nd == 1 || g.nx % 4 == 0)) ? 1 : 0;
+    cudaError_t e = g.nd == 1 ? launch_recon_1d(a, q_out, s)
+                  : g.nd == 2 ? launch_recon_2d(a, q_out, s)
+                              : launch_recon_3d(a, q_out, s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (!q_out && c->fix_cap > 0) {
+        e = launch_fixups(c->hdr, c->fix_idx, c->fix_bits, c->fix_cap, (float*)out, g.n, s);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    return VSZ_OK;
+}
+
+vsz_status vsz_reconstruct(const vsz_params* p, const vsz_compressed* c, float* d_xhat, void* stream) {
+    return reconstruct_impl(p, c, d_xhat, false, stream);
+}
+
+vsz_status vsz_reconstruct_q(const vsz_params* p, const vsz_compressed* c, int32_t* d_q, void* stream) {
+    return reconstruct_impl(p, c, d_q, true, stream);
+}
+
+vsz_status vsz_code_histogram(const vsz_params* p, const uint16_t* d_codes, uint32_t* d_hist, void* stream) {
+    Geom g;
+    vsz_status st = make_geom(p, &g);
+    if (st != VSZ_OK) return st;
+    if (!d_hist || (g.n > 0 && !d_codes)) return VSZ_ERR_INVALID_ARG;
+    cudaError_t e = launch_histogram(d_codes, g.n, d_hist, 2u * p->radius, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return VSZ_OK;
+}
+
+vsz_status vsz_read_header(const vsz_compressed* c, vsz_header* h_out, void* stream) {
+    if (!c || !c->hdr || !h_out) return VSZ_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(h_out, c->hdr, sizeof(vsz_header), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return VSZ_OK;
+}
+
+}  // extern "C"

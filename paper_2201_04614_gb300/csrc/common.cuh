@@ -1,0 +1,189 @@
+// common.cuh -- internal definitions shared by the libvsz kernels and host code.
+//
+// Geometry, workspace layout and the device arithmetic of the dual-quant
+// (prequantization, int->float, guard).  Nothing here is visible through the
+// C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "vsz.h"
+
+#define VSZ_FULL 0xffffffffu
+
+namespace vsz {
+
+// Tiling.  2D/3D: a warp-tile is one 128-column segment along x of one row
+// of blocks (all b rows of the block row in 2D, all b*b rows of the block
+// slab in 3D); every lane owns 4 consecutive columns.  1D: a warp-tile is a
+// chunk of 4096 consecutive elements.  A tile always holds whole blocks along
+// x, so its blocks are consecutive in the canonical block order.
+constexpr int kSegCols = 128;
+constexpr int kChunk1D = 4096;
+constexpr int kTilesPerChunk = 256;  // tiles per compaction chunk
+
+struct Geom {
+    int32_t nd;
+    uint32_t b;
+    uint64_t n;
+    uint64_t nx, ny, nz;     // nz = ny = 1 for lower ranks
+    uint64_t nbx, nby, nbz;  // blocks per axis
+    uint64_t nb;
+    uint64_t nseg;           // tiles per row of blocks (1D: all tiles)
+    uint64_t ntiles;
+    uint32_t bpt;            // blocks per tile (interior)
+    uint64_t nchunks;
+};
+
+// Workspace header (first 256 bytes of the workspace).
+struct WsHeader {
+    unsigned long long stage_out;  // staging cursors
+    unsigned long long stage_fix;
+    unsigned long long qsum;       // sum of q, two's complement
+    unsigned int xmin_ord, xmax_ord;  // order-preserving encodings of finite min/max
+    int qmin, qmax;
+    unsigned int done0, done1;     // last-block counters
+    unsigned int has_finite;
+    unsigned int pad_[3];
+};
+static_assert(sizeof(WsHeader) <= 256, "ws header");
+
+struct WsLayout {
+    size_t tiles;      // uint4 per tile {stage_base_out, tot_out, stage_base_fix, tot_fix}
+    size_t chunks;     // uint4 per chunk {sum_out, sum_fix, off_out, off_fix}
+    size_t stage_out;  // uint2 per outlier {idx, delta}
+    size_t stage_fix;  // uint2 per fixup {idx, bits}
+    size_t total;
+};
+
+inline size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+inline WsLayout ws_layout(const Geom& g, uint64_t out_cap, uint64_t fix_cap) {
+    WsLayout L;
+    size_t off = 256;
+    L.tiles = off;
+    off = align256(off + g.ntiles * 16);
+    L.chunks = off;
+    off = align256(off + g.nchunks * 16);
+    L.stage_out = off;
+    off = align256(off + out_cap * 8);
+    L.stage_fix = off;
+    off = align256(off + fix_cap * 8);
+    L.total = off;
+    return L;
+}
+
+// ---- device arithmetic ------------------------------------------------------
+
+__host__ __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
+
+// Prequantization q = rint(x * inv2eb) (Sec. III-A): one fp32 product, round
+// to nearest with ties to even, saturate to int32, NaN -> 0.  For |p| < 2^22
+// adding 1.5*2^23 rounds p to an integer in the default IEEE mode and the
+// integer appears in the low mantissa bits (the classic magic-number
+// rounding); larger magnitudes take the saturating conversion instruction.
+__device__ __forceinline__ int32_t prequant(float x, float inv2eb) {
+    const float p = __fmul_rn(x, inv2eb);
+    if (fabsf(p) < 4194304.0f) return __float_as_int(__fadd_rn(p, 12582912.0f)) - 0x4B400000;
+    if (p != p) return 0;
+    int32_t q;
+    asm("cvt.rni.sat.s32.f32 %0, %1;" : "=r"(q) : "f"(p));
+    return q;
+}
+
+// (float)q, round to nearest even.  Exact for |q| < 2^22 via the same
+// mantissa construction; otherwise the conversion instruction.
+__device__ __forceinline__ float q2f(int32_t q) {
+    if ((uint32_t)(q + 4194304) < 8388608u)
+        return __fsub_rn(__int_as_float(q + 0x4B400000), 12582912.0f);
+    return __int2float_rn(q);
+}
+
+// Error-bound guard (fixup test): true when x_hat = fl(fl(q) * ebx2) misses
+// |x - x_hat| <= eb_f32, and for every NaN or Inf x.
+__device__ __forceinline__ bool needs_fixup(float x, int32_t q, float ebx2, float eb_f32) {
+    const float xh = __fmul_rn(q2f(q), ebx2);
+    return !(fabsf(__fsub_rn(x, xh)) <= eb_f32);
+}
+
+// Code of a residual: delta + R when -R < delta < R, else 0 (outlier).
+__device__ __forceinline__ uint32_t code_of(int32_t d, int32_t R) {
+    return (d > -R && d < R) ? (uint32_t)(d + R) : 0u;
+}
+
+// Rounded mean of the q values of a block: floor((2S + m) / (2m)), computed
+// without overflow as floor(S/m) plus one when the remainder is >= m/2.
+__device__ __forceinline__ int32_t rounded_mean(long long S, long long m) {
+    long long qt = S / m;
+    long long r = S - qt * m;
+    if (r < 0) { qt -= 1; r += m; }
+    return (int32_t)(qt + ((2 * r >= m) ? 1 : 0));
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Order-preserving uint encoding of a float (for atomic min/max).
+__device__ __forceinline__ unsigned int float_to_ord(float f) {
+    unsigned int u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float ord_to_float(unsigned int u) {
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+// ---- kernel argument blocks --------------------------------------------------
+
+struct CompressArgs {
+    const float* x;
+    uint16_t* codes;
+    int32_t* pad;          // [nb] block modes
+    uint32_t* blk_off;     // [nb+1]; receives in-tile exclusive prefixes here
+    const vsz_header* hdr;
+    WsHeader* wsh;
+    uint4* tiles;
+    uint4* chunks;
+    uint2* stage_out;
+    uint2* stage_fix;
+    uint64_t out_cap, fix_cap;
+    Geom g;
+    int32_t R;
+    int32_t pad_mode;
+    int32_t vec;           // 16-byte vector path allowed
+};
+
+struct ReconArgs {
+    const uint16_t* codes;
+    const int32_t* pad;
+    const uint32_t* blk_off;
+    const uint32_t* out_idx;
+    const int32_t* out_delta;
+    uint64_t out_cap;      // entries readable in out_idx / out_delta
+    vsz_header* hdr;
+    void* out;             // float* (values) or int32_t* (q)
+    Geom g;
+    int32_t R;
+    int32_t pad_mode;
+    int32_t vec;
+};
+
+__host__ __device__ inline bool is_block_pad(int m) {
+    return m == VSZ_PAD_BLOCK_MIN || m == VSZ_PAD_BLOCK_MAX || m == VSZ_PAD_BLOCK_AVG;
+}
+
+// Host launchers implemented in the per-rank translation units.
+cudaError_t launch_lorenzo_1d(const CompressArgs& a, cudaStream_t s);
+cudaError_t launch_lorenzo_2d(const CompressArgs& a, cudaStream_t s);
+cudaError_t launch_lorenzo_3d(const CompressArgs& a, cudaStream_t s);
+cudaError_t launch_recon_1d(const ReconArgs& a, bool q_out, cudaStream_t s);
+cudaError_t launch_recon_2d(const ReconArgs& a, bool q_out, cudaStream_t s);
+cudaError_t launch_recon_3d(const ReconArgs& a, bool q_out, cudaStream_t s);
+
+int num_sms();
+int grid_for(const void* kernel, int threads, size_t smem, uint64_t work_items_per_cta, uint64_t work);
+
+}  // namespace vsz

@@ -1,0 +1,377 @@
+// k_rank1.cu -- 1D dual-quant: fused compression and the inverse.
+//
+// A warp-tile is a chunk of 4096 consecutive elements processed in steps of
+// 32*EPL elements (each lane owns EPL consecutive values: 4, or 8 for b=256).
+// The step width is a multiple of the block length b, so every block lies
+// inside one step and a step needs nothing from its neighbours: the 1D
+// Lorenzo residual is q[i] - q[i-1] inside a block and q - P at its first
+// element (Sec. III-A), and the inverse is a segmented inclusive prefix sum
+// over the b/EPL lanes of each block.
+#include <climits>
+
+#include "common.cuh"
+#include "memops.cuh"
+
+namespace vsz {
+
+template <int B>
+struct Cfg1 {
+    static_assert(B >= 4 && B <= 256 && (B & (B - 1)) == 0, "block length");
+    static constexpr int EPL = B >= 256 ? 8 : 4;
+    static constexpr int SPAN = 32 * EPL;
+    static constexpr int STEPS = kChunk1D / SPAN;
+    static constexpr int G = B / EPL;  // lanes per block
+    static constexpr int WARPS = 8;
+};
+
+__device__ __forceinline__ int32_t wsub1(int32_t a, int32_t b) { return (int32_t)((uint32_t)a - (uint32_t)b); }
+
+template <int EPL>
+__device__ __forceinline__ void load_epl(const float* __restrict__ p, int valid, bool vec, float (&v)[EPL]) {
+    if (vec) {
+#pragma unroll
+        for (int h = 0; h < EPL / 4; ++h) {
+            const float4 f = ld_stream_f4(p + 4 * h);
+            v[4 * h + 0] = f.x; v[4 * h + 1] = f.y; v[4 * h + 2] = f.z; v[4 * h + 3] = f.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < EPL; ++k) v[k] = (k < valid) ? p[k] : 0.0f;
+    }
+}
+
+// One step of 32*EPL elements: prequant, padding value, residual, codes.
+template <int B, bool BP>
+struct Step1 {
+    static constexpr int EPL = Cfg1<B>::EPL;
+    static constexpr int G = Cfg1<B>::G;
+    float x[EPL];
+    int32_t d[EPL];
+    int32_t q[EPL];
+    int32_t P;
+    int valid;
+
+    __device__ __forceinline__ void run(const CompressArgs& a, uint64_t base, int lane, float inv2eb, int32_t Pg) {
+        const uint64_t n = a.g.n;
+        valid = base < n ? (int)umin64(EPL, n - base) : 0;
+        load_epl<EPL>(a.x + base, valid, a.vec && valid == EPL, x);
+#pragma unroll
+        for (int k = 0; k < EPL; ++k) q[k] = prequant(x[k], inv2eb);
+        const int glane = lane & (G - 1);
+        P = Pg;
+        if (BP) {
+            int32_t smin = INT_MAX, smax = INT_MIN;
+            long long ssum = 0;
+#pragma unroll
+            for (int k = 0; k < EPL; ++k)
+                if (k < valid) { smin = min(smin, q[k]); smax = max(smax, q[k]); ssum += q[k]; }
+#pragma unroll
+            for (int off = 1; off < G; off <<= 1) {
+                smin = min(smin, __shfl_xor_sync(VSZ_FULL, smin, off));
+                smax = max(smax, __shfl_xor_sync(VSZ_FULL, smax, off));
+                ssum += __shfl_xor_sync(VSZ_FULL, ssum, off);
+            }
+            const uint64_t bstart = base - (uint64_t)glane * EPL;
+            const long long m = bstart < n ? (long long)umin64(B, n - bstart) : 1;
+            P = a.pad_mode == VSZ_PAD_BLOCK_MIN ? smin
+              : a.pad_mode == VSZ_PAD_BLOCK_MAX ? smax
+              : rounded_mean(ssum, m);
+        }
+        const int32_t left = __shfl_up_sync(VSZ_FULL, q[EPL - 1], 1);
+        d[0] = wsub1(q[0], glane == 0 ? P : left);
+#pragma unroll
+        for (int k = 1; k < EPL; ++k) d[k] = wsub1(q[k], q[k - 1]);
+    }
+};
+
+template <int B, bool BP>
+__global__ void __launch_bounds__(256) k_lorenzo_1d(const CompressArgs a) {
+    using C = Cfg1<B>;
+    constexpr int EPL = C::EPL, G = C::G, SPAN = C::SPAN;
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const float inv2eb = a.hdr->inv2eb;
+    const float ebx2 = a.hdr->ebx2;
+    const float ebf = a.hdr->eb_f32;
+    const int32_t Pg = a.hdr->pad_global;
+    const int32_t R = a.R;
+    const uint64_t n = a.g.n;
+    const int glane = lane & (G - 1);
+    const uint32_t lt = lanemask_lt();
+
+    for (uint64_t t = (uint64_t)blockIdx.x * C::WARPS + wib; t < a.g.ntiles;
+         t += (uint64_t)gridDim.x * C::WARPS) {
+        const uint64_t start = t * kChunk1D;
+        uint32_t run_out = 0, run_fix = 0, stepmask = 0;
+#pragma unroll 2
+        for (int st = 0; st < C::STEPS; ++st) {
+            const uint64_t s0 = start + (uint64_t)st * SPAN;
+            if (s0 >= n) break;
+            const uint64_t base = s0 + (uint64_t)lane * EPL;
+            Step1<B, BP> S;
+            S.run(a, base, lane, inv2eb, Pg);
+            uint32_t co = 0, cf = 0;
+            uint32_t c[EPL];
+#pragma unroll
+            for (int k = 0; k < EPL; ++k) {
+                c[k] = code_of(S.d[k], R);
+                if (k < S.valid) {
+                    co += (c[k] == 0u);
+                    cf += needs_fixup(S.x[k], S.q[k], ebx2, ebf) ? 1u : 0u;
+                }
+            }
+            // in-step exclusive prefix of outliers -> per-block offsets
+            uint32_t io = co, iff = cf;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const uint32_t yo = __shfl_up_sync(VSZ_FULL, io, off);
+                const uint32_t yf = __shfl_up_sync(VSZ_FULL, iff, off);
+                if (lane >= off) { io += yo; iff += yf; }
+            }
+            const uint32_t so = __shfl_sync(VSZ_FULL, io, 31);
+            const uint32_t sf = __shfl_sync(VSZ_FULL, iff, 31);
+            if (glane == 0 && base < n) {
+                const uint64_t blk = base / B;
+                a.blk_off[blk] = run_out + (io - co);
+                if (BP) a.pad[blk] = S.P;
+            }
+            run_out += so;
+            run_fix += sf;
+            if (so | sf) stepmask |= 1u << st;
+            // codes
+            uint16_t* cp = a.codes + base;
+            if (a.vec && S.valid == EPL) {
+                if (EPL == 4) {
+                    *reinterpret_cast<uint2*>(cp) = make_uint2(c[0] | (c[1] << 16), c[2] | (c[3] << 16));
+                } else {
+                    *reinterpret_cast<uint4*>(cp) = make_uint4(c[0] | (c[1] << 16), c[2] | (c[3] << 16),
+                                                               c[4 % EPL] | (c[5 % EPL] << 16),
+                                                               c[6 % EPL] | (c[7 % EPL] << 16));
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < EPL; ++k)
+                    if (k < S.valid) cp[k] = (uint16_t)c[k];
+            }
+        }
+
+        unsigned long long base_out = 0, base_fix = 0;
+        if (run_out | run_fix) {
+            if (lane == 0) {
+                if (run_out) base_out = atomicAdd(&a.wsh->stage_out, (unsigned long long)run_out);
+                if (run_fix) base_fix = atomicAdd(&a.wsh->stage_fix, (unsigned long long)run_fix);
+                uint4* ch = a.chunks + t / kTilesPerChunk;
+                if (run_out) atomicAdd(&ch->x, run_out);
+                if (run_fix) atomicAdd(&ch->y, run_fix);
+            }
+            base_out = __shfl_sync(VSZ_FULL, base_out, 0);
+            base_fix = __shfl_sync(VSZ_FULL, base_fix, 0);
+        }
+        if (lane == 0) a.tiles[t] = make_uint4((uint32_t)base_out, run_out, (uint32_t)base_fix, run_fix);
+
+        // Emission in linear (= canonical) order, only for steps with entries.
+        uint64_t ko = base_out, kf = base_fix;
+        while (stepmask) {
+            const int st = __ffs(stepmask) - 1;
+            stepmask &= stepmask - 1;
+            const uint64_t base = start + (uint64_t)st * SPAN + (uint64_t)lane * EPL;
+            Step1<B, BP> S;
+            S.run(a, base, lane, inv2eb, Pg);
+            uint32_t mo = 0, mf = 0;  // per-element flags of this lane
+#pragma unroll
+            for (int k = 0; k < EPL; ++k) {
+                if (k < S.valid) {
+                    if (code_of(S.d[k], R) == 0u) mo |= 1u << k;
+                    if (needs_fixup(S.x[k], S.q[k], ebx2, ebf)) mf |= 1u << k;
+                }
+            }
+            uint32_t io = __popc(mo), iff = __popc(mf);
+            const uint32_t co = io, cf = iff;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const uint32_t yo = __shfl_up_sync(VSZ_FULL, io, off);
+                const uint32_t yf = __shfl_up_sync(VSZ_FULL, iff, off);
+                if (lane >= off) { io += yo; iff += yf; }
+            }
+            uint64_t po = ko + (io - co), pf = kf + (iff - cf);
+#pragma unroll
+            for (int k = 0; k < EPL; ++k) {
+                if (mo & (1u << k)) {
+                    if (po < a.out_cap) a.stage_out[po] = make_uint2((uint32_t)(base + k), (uint32_t)S.d[k]);
+                    ++po;
+                }
+                if (mf & (1u << k)) {
+                    if (pf < a.fix_cap) a.stage_fix[pf] = make_uint2((uint32_t)(base + k), __float_as_uint(S.x[k]));
+                    ++pf;
+                }
+            }
+            ko += __shfl_sync(VSZ_FULL, io, 31);
+            kf += __shfl_sync(VSZ_FULL, iff, 31);
+        }
+        (void)lt;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Inverse: codes -> residuals (outliers patched by their rank inside the
+// block), block origin += P, segmented inclusive scan, x_hat = q * ebx2.
+template <int B, bool QOUT>
+__global__ void __launch_bounds__(256) k_recon_1d(const ReconArgs a) {
+    using C = Cfg1<B>;
+    constexpr int EPL = C::EPL, G = C::G, SPAN = C::SPAN;
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const float ebx2 = a.hdr->ebx2;
+    const int32_t Pg = a.hdr->pad_global;
+    const int32_t R = a.R;
+    const uint64_t n = a.g.n;
+    const int glane = lane & (G - 1);
+    const bool bp = is_block_pad(a.pad_mode);
+    const uint64_t nsteps = (n + SPAN - 1) / SPAN;
+
+    for (uint64_t st = (uint64_t)blockIdx.x * C::WARPS + wib; st < nsteps; st += (uint64_t)gridDim.x * C::WARPS) {
+        const uint64_t base = st * SPAN + (uint64_t)lane * EPL;
+        const int valid = base < n ? (int)umin64(EPL, n - base) : 0;
+        const bool vec = a.vec && valid == EPL;
+        uint32_t c[EPL];
+        if (vec) {
+            if (EPL == 4) {
+                const uint2 u = ld_stream_u2(a.codes + base);
+                c[0] = u.x & 0xffffu; c[1] = u.x >> 16; c[2 % EPL] = u.y & 0xffffu; c[3 % EPL] = u.y >> 16;
+            } else {
+                const uint4 u = ld_stream_u4(a.codes + base);
+                c[0] = u.x & 0xffffu; c[1] = u.x >> 16; c[2] = u.y & 0xffffu; c[3] = u.y >> 16;
+                c[4 % EPL] = u.z & 0xffffu; c[5 % EPL] = u.z >> 16; c[6 % EPL] = u.w & 0xffffu; c[7 % EPL] = u.w >> 16;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < EPL; ++k) c[k] = (k < valid) ? (uint32_t)a.codes[base + k] : (uint32_t)R;
+        }
+        int32_t d[EPL];
+        uint32_t zm = 0;
+#pragma unroll
+        for (int k = 0; k < EPL; ++k) {
+            d[k] = (int32_t)c[k] - R;
+            if (k < valid && c[k] == 0u) zm |= 1u << k;
+        }
+        const uint64_t blk = base / B;
+        if (__any_sync(VSZ_FULL, zm != 0)) {
+            // rank of each outlier inside its block = zeros before it
+            uint32_t iz = __popc(zm);
+            const uint32_t cz = iz;
+#pragma unroll
+            for (int off = 1; off < G; off <<= 1) {
+                const uint32_t y = __shfl_up_sync(VSZ_FULL, iz, off);
+                if (glane >= off) iz += y;
+            }
+            if (zm) {
+                const uint32_t lo = a.blk_off[blk], hi = a.blk_off[blk + 1];
+                uint32_t r = lo + (iz - cz);
+#pragma unroll
+                for (int k = 0; k < EPL; ++k) {
+                    if (zm & (1u << k)) {
+                        if (r < hi && r < a.out_cap && a.out_idx[r] == (uint32_t)(base + k)) {
+                            d[k] = a.out_delta[r];
+                        } else {
+                            atomicMax(&a.hdr->recon_status, (unsigned)VSZ_ERR_CORRUPT);
+                            d[k] = 0;
+                        }
+                        ++r;
+                    }
+                }
+            }
+        }
+        if (glane == 0 && valid > 0) {
+            const int32_t P = bp ? a.pad[blk] : Pg;
+            d[0] = (int32_t)((uint32_t)d[0] + (uint32_t)P);
+        }
+        // inclusive scan: in lane, then segmented across the block's lanes
+#pragma unroll
+        for (int k = 1; k < EPL; ++k) d[k] = (int32_t)((uint32_t)d[k] + (uint32_t)d[k - 1]);
+        uint32_t tot = (uint32_t)d[EPL - 1], inc = tot;
+#pragma unroll
+        for (int off = 1; off < G; off <<= 1) {
+            const uint32_t y = __shfl_up_sync(VSZ_FULL, inc, off);
+            if (glane >= off) inc += y;
+        }
+        const uint32_t ex = inc - tot;
+#pragma unroll
+        for (int k = 0; k < EPL; ++k) d[k] = (int32_t)((uint32_t)d[k] + ex);
+
+        if (QOUT) {
+            int32_t* o = reinterpret_cast<int32_t*>(a.out) + base;
+            if (vec) {
+#pragma unroll
+                for (int h = 0; h < EPL / 4; ++h)
+                    *reinterpret_cast<int4*>(o + 4 * h) = make_int4(d[4 * h], d[4 * h + 1], d[4 * h + 2], d[4 * h + 3]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < EPL; ++k)
+                    if (k < valid) o[k] = d[k];
+            }
+        } else {
+            float* o = reinterpret_cast<float*>(a.out) + base;
+            float v[EPL];
+#pragma unroll
+            for (int k = 0; k < EPL; ++k) v[k] = __fmul_rn(q2f(d[k]), ebx2);
+            if (vec) {
+#pragma unroll
+                for (int h = 0; h < EPL / 4; ++h)
+                    *reinterpret_cast<float4*>(o + 4 * h) = make_float4(v[4 * h], v[4 * h + 1], v[4 * h + 2], v[4 * h + 3]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < EPL; ++k)
+                    if (k < valid) o[k] = v[k];
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+template <int B>
+static cudaError_t launch_c1(const CompressArgs& a, cudaStream_t s) {
+    const bool bp = is_block_pad(a.pad_mode);
+    const void* k = bp ? (const void*)k_lorenzo_1d<B, true> : (const void*)k_lorenzo_1d<B, false>;
+    const int grid = grid_for(k, 256, 0, Cfg1<B>::WARPS, a.g.ntiles);
+    if (bp) k_lorenzo_1d<B, true><<<grid, 256, 0, s>>>(a);
+    else k_lorenzo_1d<B, false><<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int B>
+static cudaError_t launch_r1(const ReconArgs& a, bool q_out, cudaStream_t s) {
+    const uint64_t nsteps = (a.g.n + Cfg1<B>::SPAN - 1) / Cfg1<B>::SPAN;
+    const void* k = q_out ? (const void*)k_recon_1d<B, true> : (const void*)k_recon_1d<B, false>;
+    const int grid = grid_for(k, 256, 0, 8, nsteps);
+    if (q_out) k_recon_1d<B, true><<<grid, 256, 0, s>>>(a);
+    else k_recon_1d<B, false><<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lorenzo_1d(const CompressArgs& a, cudaStream_t s) {
+    switch (a.g.b) {
+    case 4: return launch_c1<4>(a, s);
+    case 8: return launch_c1<8>(a, s);
+    case 16: return launch_c1<16>(a, s);
+    case 32: return launch_c1<32>(a, s);
+    case 64: return launch_c1<64>(a, s);
+    case 128: return launch_c1<128>(a, s);
+    case 256: return launch_c1<256>(a, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_recon_1d(const ReconArgs& a, bool q_out, cudaStream_t s) {
+    switch (a.g.b) {
+    case 4: return launch_r1<4>(a, q_out, s);
+    case 8: return launch_r1<8>(a, q_out, s);
+    case 16: return launch_r1<16>(a, q_out, s);
+    case 32: return launch_r1<32>(a, q_out, s);
+    case 64: return launch_r1<64>(a, q_out, s);
+    case 128: return launch_r1<128>(a, q_out, s);
+    case 256: return launch_r1<256>(a, q_out, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace vsz

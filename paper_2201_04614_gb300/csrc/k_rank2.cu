@@ -1,0 +1,30 @@
+// k_rank2.cu -- 2D instantiations of the fused compression and the inverse.
+#include "recon_nd.cuh"
+
+namespace vsz {
+
+cudaError_t launch_lorenzo_2d(const CompressArgs& a, cudaStream_t s) {
+    switch (a.g.b) {
+    case 4: return launch_nd_compress<2, 4>(a, s);
+    case 8: return launch_nd_compress<2, 8>(a, s);
+    case 16: return launch_nd_compress<2, 16>(a, s);
+    case 32: return launch_nd_compress<2, 32>(a, s);
+    case 64: return launch_nd_compress<2, 64>(a, s);
+    case 128: return launch_nd_compress<2, 128>(a, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_recon_2d(const ReconArgs& a, bool q_out, cudaStream_t s) {
+    switch (a.g.b) {
+    case 4: return launch_nd_recon<2, 4>(a, q_out, s);
+    case 8: return launch_nd_recon<2, 8>(a, q_out, s);
+    case 16: return launch_nd_recon<2, 16>(a, q_out, s);
+    case 32: return launch_nd_recon<2, 32>(a, q_out, s);
+    case 64: return launch_nd_recon<2, 64>(a, q_out, s);
+    case 128: return launch_nd_recon<2, 128>(a, q_out, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace vsz

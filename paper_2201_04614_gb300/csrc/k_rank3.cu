@@ -1,0 +1,26 @@
+// k_rank3.cu -- 3D instantiations of the fused compression and the inverse.
+#include "recon_nd.cuh"
+
+namespace vsz {
+
+cudaError_t launch_lorenzo_3d(const CompressArgs& a, cudaStream_t s) {
+    switch (a.g.b) {
+    case 4: return launch_nd_compress<3, 4>(a, s);
+    case 8: return launch_nd_compress<3, 8>(a, s);
+    case 16: return launch_nd_compress<3, 16>(a, s);
+    case 32: return launch_nd_compress<3, 32>(a, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_recon_3d(const ReconArgs& a, bool q_out, cudaStream_t s) {
+    switch (a.g.b) {
+    case 4: return launch_nd_recon<3, 4>(a, q_out, s);
+    case 8: return launch_nd_recon<3, 8>(a, q_out, s);
+    case 16: return launch_nd_recon<3, 16>(a, q_out, s);
+    case 32: return launch_nd_recon<3, 32>(a, q_out, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace vsz

@@ -1,0 +1,204 @@
+"""GPU parity: the CUDA path (called through the C ABI) against the CPU oracle,
+element by element on the same seeded inputs.
+
+Integer work is compared bit-exactly: codes, per-block padding values, block
+offsets, outlier indices and residuals, fixup indices and bits, the
+reconstructed prequantized integers.  Reconstructed values are compared bit
+for bit too (both sides evaluate the same IEEE fp32 product), and the error
+bound |x - x_hat| <= eb (1 + 2^-20) is checked on every finite element.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import oracle  # noqa: E402
+import paper_2201_04614_gb300 as vsz  # noqa: E402
+
+PADS = ["zero", "global_min", "global_max", "global_avg", "block_min", "block_max", "block_avg"]
+
+
+def run_both(x, dims, block, eb, eb_mode="rel", radius=512, pad="zero", out_cap=None, fix_cap=None):
+    x = np.ascontiguousarray(x, np.float32).reshape(-1)
+    p = vsz.Params.make(dims, block, eb, eb_mode, radius, pad)
+    n = max(1, x.size)
+    f = vsz.Field(p, out_cap=out_cap or n, fix_cap=fix_cap or n)
+    xd = torch.from_numpy(x).cuda()
+    f.compress(xd)
+    qg = f.reconstruct_q().cpu().numpy()
+    xg = f.reconstruct().cpu().numpy()
+    po = oracle.Params(tuple(dims), block, eb, oracle.EB_REL if eb_mode == "rel" else oracle.EB_ABS,
+                       radius, oracle.PAD_NAMES[pad])
+    c = oracle.compress(po, x)
+    xo, qo = oracle.decompress(po, c, return_q=True)
+    return f, c, (qg, xg), (qo, xo), x
+
+
+def assert_parity(f, c, g, o, x, pad):
+    got = f.to_host()
+    h = got["header"]
+    assert h["recon_status"] == 0
+    # error-bound resolution (Sec. II-B) and padding value (Sec. IV)
+    assert h["eb_abs"] == c.eb.eb_abs
+    assert np.float32(h["inv2eb"]) == c.eb.inv2eb
+    assert np.float32(h["ebx2"]) == c.eb.ebx2
+    assert np.float32(h["eb_f32"]) == c.eb.eb_f32
+    if pad.startswith("global") or pad == "zero":
+        assert h["pad_global"] == int(c.pad[0])
+    else:
+        assert np.array_equal(got["pad"], c.pad)
+    assert np.array_equal(got["codes"], c.codes)
+    assert np.array_equal(got["blk_off"], c.blk_off)
+    assert np.array_equal(got["out_idx"], c.out_idx)
+    assert np.array_equal(got["out_delta"], c.out_delta)
+    assert np.array_equal(got["fix_idx"], c.fix_idx)
+    assert np.array_equal(got["fix_bits"], c.fix_bits)
+    qg, xg = g
+    qo, xo = o
+    assert np.array_equal(qg, c.q)          # prequantized values, via the inverse
+    assert np.array_equal(qo, c.q)
+    assert np.array_equal(xg.view(np.uint32), xo.view(np.uint32))
+    fin = np.isfinite(x)
+    err = np.abs(x[fin].astype(np.float64) - xg[fin].astype(np.float64))
+    assert (err <= c.eb.eb_abs * (1 + 2.0 ** -20)).all()
+    assert np.array_equal(x[~fin].view(np.uint32), xg[~fin].view(np.uint32))
+
+
+CASES_1D = [((10007,), b) for b in (4, 32, 256)] + [((4096 * 3,), 128), ((77,), 8)]
+CASES_2D = [((300, 519), 16), ((160, 384), 16), ((130, 260), 4), ((70, 300), 64), ((129, 257), 128),
+            ((33, 1000), 8), ((1, 700), 32), ((700, 3), 16)]
+CASES_3D = [((19, 37, 260), 8), ((17, 23, 29), 8), ((9, 10, 140), 4), ((20, 18, 132), 16),
+            ((33, 35, 70), 32), ((8, 8, 128), 8), ((3, 1, 5), 4)]
+
+
+def field_for(dims, seed):
+    if len(dims) == 1:
+        return synth.random_walk1d(dims[0], seed)
+    if len(dims) == 2:
+        return synth.fourier2d(dims[0], dims[1], seed=seed, value_range=20.0, offset=5.0)
+    return np.exp(synth.grf3d(dims, seed))
+
+
+@pytest.mark.parametrize("dims,block", CASES_1D + CASES_2D + CASES_3D)
+@pytest.mark.parametrize("pad", PADS)
+def test_parity_shapes_pads(dims, block, pad):
+    x = field_for(dims, seed=len(dims) * 100 + block)
+    for eb in (1e-2, 1e-5):
+        f, c, g, o, xx = run_both(x, dims, block, eb, "rel", 512, pad)
+        assert_parity(f, c, g, o, xx, pad)
+
+
+@pytest.mark.parametrize("radius", [1, 2, 32768])
+@pytest.mark.parametrize("dims,block", [((5000,), 64), ((90, 130), 16), ((12, 20, 68), 8)])
+def test_parity_radius_extremes(dims, block, radius):
+    x = field_for(dims, seed=7)
+    for pad in ("zero", "block_avg", "global_max"):
+        f, c, g, o, xx = run_both(x, dims, block, 1e-4, "rel", radius, pad)
+        assert_parity(f, c, g, o, xx, pad)
+
+
+@pytest.mark.parametrize("dims,block", [((6000,), 16), ((60, 100), 8), ((10, 15, 40), 4)])
+@pytest.mark.parametrize("eb_abs", [0.5, 1e-3, 3e-7])
+def test_parity_adversarial(dims, block, eb_abs):
+    n = int(np.prod(dims))
+    x = synth.adversarial_values(n, seed=3, inv2eb=1.0 / (2 * eb_abs))
+    for pad in PADS:
+        f, c, g, o, xx = run_both(x, dims, block, eb_abs, "abs", 512, pad, out_cap=n, fix_cap=n)
+        assert len(c.fix_idx) > 0
+        assert_parity(f, c, g, o, xx, pad)
+
+
+def test_parity_all_nan_and_constant():
+    for x in (np.full(3000, np.nan, np.float32), np.full(3000, 2.5, np.float32)):
+        for pad in ("zero", "block_avg", "global_avg"):
+            f, c, g, o, xx = run_both(x, (50, 60), 16, 1e-3, "rel", 512, pad, out_cap=3000, fix_cap=3000)
+            assert_parity(f, c, g, o, xx, pad)
+
+
+def test_empty_field():
+    p = vsz.Params.make((0,), 16, 1e-3)
+    f = vsz.Field(p)
+    f.compress(torch.empty(0, dtype=torch.float32, device="cuda"))
+    h = f.header()
+    assert h["n_out"] == 0 and h["n_fix"] == 0 and h["status"] == 0
+    assert f.reconstruct().numel() == 0
+    p2 = vsz.Params.make((0, 17), 16, 1e-3, pad="block_avg")
+    f2 = vsz.Field(p2)
+    f2.compress(torch.empty(0, dtype=torch.float32, device="cuda"))
+    assert f2.header()["n_out"] == 0
+
+
+def test_capacity_overflow_reports_exact_counts():
+    dims = (100, 200)
+    x = field_for(dims, seed=11)
+    p = vsz.Params.make(dims, 8, 1e-6, "rel", 4, "zero")
+    po = oracle.Params(dims, 8, 1e-6, oracle.EB_REL, 4, oracle.PAD_ZERO)
+    c = oracle.compress(po, x)
+    assert len(c.out_idx) > 50
+    f = vsz.Field(p, out_cap=10, fix_cap=10)
+    f.compress(torch.from_numpy(x.reshape(-1)).cuda())
+    h = f.header()
+    assert h["status"] == 3  # VSZ_ERR_CAPACITY
+    assert h["n_out"] == len(c.out_idx)
+    assert np.array_equal(f.blk_off.cpu().numpy().view(np.uint32), c.blk_off)
+    # retry with room: exact parity
+    f2 = vsz.Field(p, out_cap=int(h["n_out"]), fix_cap=max(1, int(h["n_fix"])))
+    f2.compress(torch.from_numpy(x.reshape(-1)).cuda())
+    got = f2.to_host()
+    assert np.array_equal(got["out_idx"], c.out_idx) and np.array_equal(got["codes"], c.codes)
+
+
+def test_corrupt_outlier_list_is_reported():
+    dims = (64, 64)
+    x = field_for(dims, seed=12)
+    p = vsz.Params.make(dims, 16, 1e-6, "rel", 8, "zero")
+    f = vsz.Field(p)
+    f.compress(torch.from_numpy(x.reshape(-1)).cuda())
+    h = f.header()
+    assert h["n_out"] > 0
+    f.out_idx[0] += 1  # the first outlier no longer matches its code 0
+    f.reconstruct()
+    assert f.header()["recon_status"] == 5
+
+
+def test_code_histogram_matches_codes():
+    dims = (200, 300)
+    x = field_for(dims, seed=13)
+    p = vsz.Params.make(dims, 16, 1e-4, "rel", 64, "zero")
+    f = vsz.Field(p)
+    f.compress(torch.from_numpy(x.reshape(-1)).cuda())
+    hist = f.code_histogram().cpu().numpy()
+    codes = f.to_host()["codes"]
+    assert np.array_equal(hist, np.bincount(codes, minlength=128)[:128])
+
+
+def test_split_calls_equal_fused_call():
+    dims = (50, 70, 36)
+    x = field_for(dims, seed=14)
+    p = vsz.Params.make(dims, 8, 1e-5, "rel", 512, "block_avg")
+    xd = torch.from_numpy(x.reshape(-1)).cuda()
+    f1, f2 = vsz.Field(p), vsz.Field(p)
+    f1.compress(xd)
+    f2.prequant_lorenzo(xd)
+    f2.outlier_compact()
+    a, b = f1.to_host(), f2.to_host()
+    for k in ("codes", "pad", "blk_off", "out_idx", "out_delta"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_repeated_calls_reuse_workspace():
+    dims = (40, 300)
+    p = vsz.Params.make(dims, 16, 1e-5, "rel", 32, "global_avg")
+    f = vsz.Field(p)
+    for seed in (21, 22, 23):
+        x = field_for(dims, seed)
+        f.compress(torch.from_numpy(x.reshape(-1)).cuda())
+        c = oracle.compress(oracle.Params(dims, 16, 1e-5, oracle.EB_REL, 32, oracle.PAD_GLOBAL_AVG), x)
+        got = f.to_host()
+        assert np.array_equal(got["out_idx"], c.out_idx) and np.array_equal(got["codes"], c.codes)
