@@ -1,0 +1,462 @@
+#!/usr/bin/env python
+"""Benchmark of the dual-quantization hot path on GB300.
+
+Workload: one NYX-like fp32 field of 512^3 values (exp of a seeded Gaussian
+random field with a k^-3 spectrum), blocks of 8^3, radius R = 512, value-range
+relative eb = 1e-4, zero padding.  One step is the whole path over the field:
+compression (on-device eb resolution from the value range, fused
+prequantization + Lorenzo + post-quantization + guard, outlier compaction)
+followed by reconstruction.  The metric is GB/s of fp32 input per step.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Under torchrun every rank compresses its own 512^3 field (blocks are
+independent, so the path shards with no collective on the data path: weak
+scaling); rank 0 prints one JSON line.  `--impl reference` times the CPU
+oracle (the plain single-threaded C implementation) on bounded samples of
+the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "dual-quant GB/s fp32 in & %HBM roofline, batched+tuned vs plain at fixed eb"
+UNIT = "GB/s"
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--size", type=int, default=512, help="edge of the cubic field")
+    ap.add_argument("--eb", type=float, default=1e-4)
+    ap.add_argument("--pad", default="zero")
+    ap.add_argument("--block", type=int, default=8)
+    ap.add_argument("--radius", type=int, default=512)
+    ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def workload_config(a) -> dict:
+    return {
+        "workload": f"NYX-like log-normal fp32 {a.size}^3 (exp of k^-3 GRF, seed 2), block {a.block}^3, "
+                    f"R={a.radius}, rel eb {a.eb:g}, {a.pad} padding: compress (range + fused "
+                    f"prequant/Lorenzo/post-quant + compaction) then reconstruct",
+        "field_elems": a.size ** 3, "block": a.block, "radius": a.radius, "eb_rel": a.eb, "pad": a.pad,
+        "l2": "inputs larger than L2 (512 MiB field vs 129 MB L2); no flush needed",
+    }
+
+
+def measured_peaks() -> tuple[float, str]:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.samples = []
+        self.proc = None
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100"]
+        if uuid:
+            cmd += ["-i", uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append((time.time(), parts))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self, t0: float, t1: float) -> dict | None:
+        if not self.samples:
+            return None
+        win = [p for (t, p) in self.samples if t0 <= t <= t1] or [p for (_, p) in self.samples]
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = sorted(v for v in (num(p[1]) for p in win) if v is not None)
+        mx = [num(p[2]) for p in win if num(p[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for p in win for i in range(4) if p[5 + i].lower().startswith("active")})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(win)}
+
+
+# ---------------------------------------------------------------- roofline
+def algorithmic_bytes(name: str, n: int, nb: int, n_out: int, n_fix: int, block_pad: bool) -> int:
+    """Bytes a launch must move at minimum (each input read once, each output
+    written once), per the data layout of the path."""
+    if name == "range" or name == "qstats":
+        return 4 * n
+    if name == "lorenzo":   # x in; codes, staged outliers/fixups, block offsets (+ pads) out
+        return 4 * n + 2 * n + 8 * (n_out + n_fix) + 4 * nb + (4 * nb if block_pad else 0)
+    if name == "compact_move":  # staged entries in and out, block offsets read-modify-write
+        return 16 * (n_out + n_fix) + 8 * nb
+    if name == "recon":     # codes, outliers, block offsets (+ pads) in; values out
+        return 2 * n + 8 * n_out + 4 * (nb + 1) + (4 * nb if block_pad else 0) + 4 * n
+    if name == "fixups":
+        return 12 * n_fix
+    return 0
+
+
+def kernel_sources_digest() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2201_04614_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str, workload: str) -> int | None:
+    """dram bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            tab = json.load(f)
+    except Exception:
+        return None
+    ent = tab.get(f"{kernel}|{workload}")
+    if not ent or ent.get("src_digest") != kernel_sources_digest():
+        return None
+    return int(ent["dram_bytes_per_launch"])
+
+
+# ---------------------------------------------------------------- CPU oracle
+def oracle_rate(x3, a, seconds: float, unit_planes: int = 8, rows: int | None = None):
+    """Time the oracle (compress + decompress) on consecutive block-aligned
+    slabs of the field until `seconds` of CPU time are spent (at least one).
+    Returns (GB/s of fp32 input, elements, slabs, sample description)."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    nz, ny, nx = x3.shape
+    rows = rows or ny
+    pad = oracle.PAD_NAMES[a.pad]
+    done, elems, t_used, k = 0, 0, 0.0, 0
+    while True:
+        z0 = (k * unit_planes) % nz
+        y0 = ((k * unit_planes) // nz * rows) % ny
+        sl = np.ascontiguousarray(x3[z0:z0 + unit_planes, y0:y0 + rows, :])
+        p = oracle.Params(sl.shape, a.block, a.eb, oracle.EB_REL, a.radius, pad)
+        t = time.perf_counter()
+        c = oracle.compress(p, sl)
+        oracle.decompress(p, c)
+        t_used += time.perf_counter() - t
+        elems += sl.size
+        k += 1
+        if t_used >= seconds:
+            break
+    desc = (f"{k} block-aligned slabs of {unit_planes}x{rows}x{nx} of the same field, each compressed "
+            f"(own rel-eb range pass) and decompressed by the single-threaded oracle")
+    return elems * 4 / t_used / 1e9, elems, k, desc
+
+
+def run_reference(a):
+    """The oracle, as it stands, on the host cores: each step one bounded
+    sample of the workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+    import synth
+    x3 = synth.cfg2_field(a.size)
+    # size one step so that warmup + steps take about a minute
+    probe, _, _, _ = oracle_rate(x3, a, 0.0, 8, 64)
+    unit_s = (8 * 64 * x3.shape[2] * 4 / 1e9) / probe
+    per_step_units = max(1, min(64, int(60.0 / max(1, a.steps + a.warmup) / unit_s)))
+    rows = min(x3.shape[1], 64 * per_step_units)
+    for _ in range(a.warmup):
+        oracle_rate(x3, a, 0.0, 8, rows)
+    t = time.perf_counter()
+    elems = 0
+    for _ in range(a.steps):
+        _, e, _, desc = oracle_rate(x3, a, 0.0, 8, rows)
+        elems += e
+    dt = time.perf_counter() - t
+    value = elems * 4 / dt / 1e9
+    sample = (f"each step: one block-aligned slab of 8x{rows}x{x3.shape[2]} of the {a.size}^3 field, "
+              f"compressed and decompressed by the single-threaded oracle")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": dt / a.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/i32",
+        "data": "synthetic", "config": workload_config(a),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_gpu(a):
+    import numpy as np
+    import torch
+    import paper_2201_04614_gb300 as vsz
+    import synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (no CPU fallback)")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    vsz.lib()
+    t = time.time()
+    x3 = synth.lognormal3d(a.size, seed=2 + rank)
+    log(f"[bench] rank {rank}: generated {a.size}^3 field in {time.time() - t:.1f}s")
+    n = x3.size
+    p = vsz.Params.make(x3.shape, a.block, a.eb, "rel", a.radius, a.pad)
+    f = vsz.Field(p, out_cap=max(1 << 20, n // 8), fix_cap=max(1 << 16, n // 64))
+    xd = torch.from_numpy(x3.reshape(-1)).cuda()
+    xh = torch.empty(n, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        f.compress(xd)
+        f.reconstruct(out=xh)
+
+    for _ in range(max(3, a.warmup)):
+        step()
+    torch.cuda.synchronize()
+    h = f.header()
+    if h["status"] != 0:
+        raise SystemExit(f"compression status {h['status']} (capacity too small?)")
+    n_out, n_fix = int(h["n_out"]), int(h["n_fix"])
+
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+        if not uuid.startswith("GPU-"):
+            uuid = "GPU-" + uuid
+    except Exception:
+        uuid = None
+    sampler = ClockSampler(uuid) if rank == 0 else None
+    time.sleep(0.3 if sampler else 0)
+
+    vsz.trace_enable(True)
+    vsz.trace_read()
+    barrier()
+    t0 = time.time()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(a.steps):
+        step()
+    ev1.record(stream)
+    barrier()
+    t1 = time.time()
+    vsz.trace_enable(False)
+    recs = vsz.trace_read(1 << 20)
+    ms = ev0.elapsed_time(ev1)
+    if dist:
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    ms_step = ms / a.steps
+    value = world * n * 4 / (ms_step * 1e-3) / 1e9
+
+    # per-kernel device times, and the roofline of the dominant kernel
+    per = {}
+    for r in recs:
+        d = per.setdefault(r["name"], {"launches": 0, "ms": 0.0})
+        d["launches"] += 1
+        d["ms"] += max(0.0, r["ms"])
+    nb = p.nblocks
+    bp = p.is_block_pad
+    peak, peak_kind = measured_peaks()
+    kernels = {}
+    step_bytes = 0
+    for name, d in per.items():
+        avg = d["ms"] / d["launches"]
+        by = algorithmic_bytes(name, n, nb, n_out, n_fix, bp)
+        step_bytes += by
+        kernels[name] = {"launches": d["launches"], "avg_us": avg * 1e3,
+                         "share": d["ms"] / max(1e-9, sum(v["ms"] for v in per.values())),
+                         "GBps": (by / (avg * 1e-3) / 1e9) if (by and avg > 0) else None}
+    dom = max(("lorenzo", "recon"), key=lambda k: per.get(k, {"ms": 0})["ms"])
+    dom_avg_s = per[dom]["ms"] / per[dom]["launches"] * 1e-3
+    dom_bytes = algorithmic_bytes(dom, n, nb, n_out, n_fix, bp)
+    achieved = dom_bytes / dom_avg_s / 1e9
+    kname = {"lorenzo": f"k_lorenzo_nd<3,{a.block},{str(bp).lower()}>",
+             "recon": f"k_recon_nd<3,{a.block},false>"}[dom]
+    wl = f"{a.size}^3 b{a.block} eb{a.eb:g} {a.pad}"
+    roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, copy bandwidth)" if peak_kind == "measured"
+                else "fallback 6.8 TB/s", "unit": "GB/s", "frac": achieved / peak,
+                "bytes_per_launch": dom_bytes, "traffic": profiled_traffic(kname, wl)}
+    step_frac = step_bytes / (ms_step * 1e-3) / 1e9 / peak
+    clocks = sampler.summary(t0, t1) if sampler else None
+
+    # e2e through the public API with host buffers
+    e2e = None
+    if not a.no_e2e:
+        hx = torch.from_numpy(x3.reshape(-1)).pin_memory()
+        hcodes = torch.empty(n, dtype=torch.int16).pin_memory()
+        hblk = torch.empty(nb + 1, dtype=torch.int32).pin_memory()
+        hout = torch.empty(f.out_cap, dtype=torch.int32).pin_memory()
+        hxh = torch.empty(n, dtype=torch.float32).pin_memory()
+        ke = max(3, min(a.steps, 20))
+        bi = bo = 0
+
+        def e2e_step():
+            nonlocal bi, bo
+            xd.copy_(hx, non_blocking=True)
+            f.compress(xd)
+            hd = f.header()  # synchronizes: the host needs the list lengths
+            no, nf = int(hd["n_out"]), int(hd["n_fix"])
+            f.reconstruct(out=xh)
+            hcodes.copy_(f.codes[:n], non_blocking=True)
+            hblk.copy_(f.blk_off, non_blocking=True)
+            hout[:no].copy_(f.out_idx[:no], non_blocking=True)
+            hxh.copy_(xh, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+            bi = 4 * n
+            bo = 64 + 2 * n + 4 * (nb + 1) + 4 * no + 4 * n
+        for _ in range(2):
+            e2e_step()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(ke):
+            e2e_step()
+        e1.record()
+        barrier()
+        ems = e0.elapsed_time(e1) / ke
+        if dist:
+            tt = torch.tensor([ems], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ems = float(tt.item())
+        e2e = {"value": world * n * 4 / (ems * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": bi,
+               "d2h_bytes_per_step": bo, "ms_per_step": ems,
+               "what": "pinned host x -> device, compress, read header, reconstruct, codes + blk_off + "
+                       "outlier indices + x_hat -> pinned host"}
+        del hx, hcodes, hblk, hout, hxh
+
+    # eb x padding sweep (separate short runs, outside the timed region)
+    sweep = None
+    if not a.no_sweep and rank == 0:
+        sweep = []
+        for eb in (1e-2, 1e-3, 1e-4, 1e-5):
+            for pad in ("zero", "block_avg", "global_avg"):
+                ps = vsz.Params.make(x3.shape, a.block, eb, "rel", a.radius, pad)
+                fs = vsz.Field(ps, out_cap=n // 4, fix_cap=max(1 << 16, n // 64))
+                for _ in range(3):
+                    fs.compress(xd)
+                    fs.reconstruct(out=xh)
+                torch.cuda.synchronize()
+                k = 20
+                c0, c1, r1 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+                tc = tr = 0.0
+                for _ in range(k):
+                    c0.record()
+                    fs.compress(xd)
+                    c1.record()
+                    fs.reconstruct(out=xh)
+                    r1.record()
+                    r1.synchronize()
+                    tc += c0.elapsed_time(c1)
+                    tr += c1.elapsed_time(r1)
+                hs = fs.header()
+                sweep.append({"eb": eb, "pad": pad, "compress_GBps": n * 4 / (tc / k * 1e-3) / 1e9,
+                              "reconstruct_GBps": n * 4 / (tr / k * 1e-3) / 1e9,
+                              "n_out": int(hs["n_out"]), "n_fix": int(hs["n_fix"]), "status": int(hs["status"])})
+                del fs
+                torch.cuda.empty_cache()
+
+    # CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and a.cpu_seconds > 0:
+        v, elems, k, desc = oracle_rate(x3, a, a.cpu_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+
+    if sampler:
+        sampler.stop()
+    launches = sum(d["launches"] for d in per.values())
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32/i32", "data": "synthetic", "config": workload_config(a),
+            "roofline": roofline, "step_hbm_frac": step_frac, "cpu_baseline": cpu, "e2e": e2e,
+            "clocks": clocks, "gpu_launches": launches, "kernels": kernels,
+            "outliers": {"n_out": n_out, "n_fix": n_fix, "frac_out": n_out / n},
+            "compress_GBps": n * 4 / (sum(per[k]["ms"] for k in ("begin", "range", "lorenzo", "compact_scan",
+                                                                  "compact_move") if k in per)
+                                      / a.steps * 1e-3) / 1e9,
+            "reconstruct_GBps": n * 4 / (sum(per[k]["ms"] for k in ("recon", "fixups") if k in per)
+                                         / a.steps * 1e-3) / 1e9,
+            "sweep": sweep,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    a = parse_args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_gpu(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -196,6 +196,26 @@ VSZ_API vsz_status vsz_reconstruct_q(const vsz_params* p, const vsz_compressed* 
 VSZ_API vsz_status vsz_code_histogram(const vsz_params* p, const uint16_t* d_codes, uint32_t* d_hist,
                               void* stream);
 
+/* One traced kernel launch. */
+typedef struct {
+    char     name[24];  /* kernel: begin, range, qstats, lorenzo, compact_scan, compact_move, recon, fixups, histogram */
+    int32_t  ndim;      /* field rank (0 if not field-specific) */
+    uint32_t block;     /* block edge (0 if not field-specific) */
+    uint64_t n;         /* elements of the field */
+    float    ms;        /* device time between the events around the launch (-1 if unknown) */
+    uint32_t reserved;
+} vsz_trace_record;
+
+/* Launch tracing (profiling aid, no counterpart in the paper's method): when
+ * on, every kernel the library launches is bracketed by two CUDA events on
+ * its stream.  Off by default.  Not meant for streams under graph capture. */
+VSZ_API vsz_status vsz_trace_enable(int on);
+
+/* Waits for every traced launch since the last read, writes up to
+ * max_records of them (oldest first) to h_out (host, may be NULL), clears
+ * the list and returns how many launches were traced. */
+VSZ_API int vsz_trace_read(vsz_trace_record* h_out, int max_records);
+
 /* Copy the device header to the host and wait for it (synchronizes the
  * stream). */
 VSZ_API vsz_status vsz_read_header(const vsz_compressed* c, vsz_header* h_out, void* stream);

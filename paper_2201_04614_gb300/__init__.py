@@ -16,7 +16,7 @@ from . import buildlib as _build
 
 __all__ = [
     "VszError", "Params", "Field", "lib", "build", "EB_ABS", "EB_REL", "PAD_MODES",
-    "num_blocks", "workspace_size",
+    "num_blocks", "workspace_size", "trace_enable", "trace_read",
 ]
 
 EB_ABS, EB_REL = 0, 1
@@ -55,11 +55,16 @@ class _CCompressed(ctypes.Structure):
                 ("hdr", ctypes.c_void_p)]
 
 
+class _CTrace(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("ndim", ctypes.c_int32), ("block", ctypes.c_uint32),
+                ("n", ctypes.c_uint64), ("ms", ctypes.c_float), ("reserved", ctypes.c_uint32)]
+
+
 HEADER_BYTES = ctypes.sizeof(_CHeader)
 EXPORTED = ["vsz_status_string", "vsz_last_cuda_error", "vsz_abi_version", "vsz_validate",
             "vsz_num_elems", "vsz_num_blocks", "vsz_workspace_size", "vsz_prequant_lorenzo",
             "vsz_outlier_compact", "vsz_compress", "vsz_reconstruct", "vsz_reconstruct_q",
-            "vsz_code_histogram", "vsz_read_header"]
+            "vsz_code_histogram", "vsz_read_header", "vsz_trace_enable", "vsz_trace_read"]
 
 _lib = None
 
@@ -98,12 +103,27 @@ def lib():
     L.vsz_reconstruct_q.argtypes = [P(_CParams), P(_CCompressed), vp, vp]
     L.vsz_code_histogram.argtypes = [P(_CParams), vp, vp, vp]
     L.vsz_read_header.argtypes = [P(_CCompressed), P(_CHeader), vp]
+    L.vsz_trace_enable.argtypes = [ctypes.c_int]
+    L.vsz_trace_read.argtypes = [P(_CTrace), ctypes.c_int]
     for name in EXPORTED:
         if name not in ("vsz_status_string", "vsz_last_cuda_error", "vsz_abi_version",
                         "vsz_num_elems", "vsz_num_blocks", "vsz_workspace_size"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
+
+
+def trace_enable(on: bool = True) -> None:
+    """Bracket every library kernel launch with CUDA events (profiling aid)."""
+    _check(lib().vsz_trace_enable(1 if on else 0), "vsz_trace_enable")
+
+
+def trace_read(max_records: int = 1 << 16) -> list:
+    """Wait for the traced launches and return [{name, ndim, block, n, ms}], oldest first."""
+    buf = (_CTrace * max_records)()
+    k = lib().vsz_trace_read(buf, max_records)
+    return [{"name": r.name.decode(), "ndim": r.ndim, "block": r.block, "n": r.n, "ms": r.ms}
+            for r in buf[: min(k, max_records)]]
 
 
 def _check(rc: int, what: str):

@@ -7,6 +7,7 @@
 
 #include "common.cuh"
 #include "misc.cuh"
+#include "trace.cuh"
 
 namespace vsz {
 
@@ -176,13 +177,19 @@ vsz_status vsz_prequant_lorenzo(const vsz_params* p, const float* d_x, vsz_compr
     const bool rel = p->eb_mode == VSZ_EB_REL;
     const bool xvec = aligned(d_x, 16);
 
-    cudaError_t e = launch_begin(wsh, chunks, g.nchunks, c->hdr, p->eb, rel, s);
+    cudaError_t e;
+    {
+        TraceScope ts("begin", s, g.nd, g.b, g.n);
+        e = launch_begin(wsh, chunks, g.nchunks, c->hdr, p->eb, rel, s);
+    }
     if (e != cudaSuccess) return cuda_fail(e);
     if (rel) {
+        TraceScope ts("range", s, g.nd, g.b, g.n);
         e = launch_range(d_x, g.n, wsh, c->hdr, p->eb, xvec, s);
         if (e != cudaSuccess) return cuda_fail(e);
     }
     if (p->pad == VSZ_PAD_GLOBAL_MIN || p->pad == VSZ_PAD_GLOBAL_MAX || p->pad == VSZ_PAD_GLOBAL_AVG) {
+        TraceScope ts("qstats", s, g.nd, g.b, g.n);
         e = launch_qstats(d_x, g.n, wsh, c->hdr, p->pad, xvec, s);
         if (e != cudaSuccess) return cuda_fail(e);
     }
@@ -206,7 +213,10 @@ vsz_status vsz_prequant_lorenzo(const vsz_params* p, const float* d_x, vsz_compr
     a.R = (int32_t)p->radius;
     a.pad_mode = p->pad;
     a.vec = (xvec && aligned(c->codes, 16) && (g.nd == 1 || g.nx % 4 == 0)) ? 1 : 0;
-    e = g.nd == 1 ? launch_lorenzo_1d(a, s) : g.nd == 2 ? launch_lorenzo_2d(a, s) : launch_lorenzo_3d(a, s);
+    {
+        TraceScope ts("lorenzo", s, g.nd, g.b, g.n);
+        e = g.nd == 1 ? launch_lorenzo_1d(a, s) : g.nd == 2 ? launch_lorenzo_2d(a, s) : launch_lorenzo_3d(a, s);
+    }
     if (e != cudaSuccess) return cuda_fail(e);
     return VSZ_OK;
 }
@@ -220,10 +230,19 @@ vsz_status vsz_outlier_compact(const vsz_params* p, vsz_compressed* c, void* d_w
     const WsLayout L = ws_layout(g, c->out_cap, c->fix_cap);
     if (!d_ws || ws_bytes < L.total || !aligned(d_ws, 256)) return VSZ_ERR_INVALID_ARG;
     char* ws = (char*)d_ws;
-    cudaError_t e = launch_compact(g, (uint4*)(ws + L.tiles), (uint4*)(ws + L.chunks), c->hdr, c->blk_off,
-                                   (const uint2*)(ws + L.stage_out), (const uint2*)(ws + L.stage_fix), c->out_idx,
-                                   c->out_delta, c->out_cap, c->fix_idx, c->fix_bits, c->fix_cap,
-                                   (cudaStream_t)stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e;
+    {
+        TraceScope ts("compact_scan", s, g.nd, g.b, g.n);
+        e = launch_compact_scan(g, (uint4*)(ws + L.chunks), c->hdr, c->blk_off, c->out_cap, c->fix_cap, s);
+    }
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (g.nchunks > 0) {
+        TraceScope ts("compact_move", s, g.nd, g.b, g.n);
+        e = launch_compact_move(g, (const uint4*)(ws + L.tiles), (const uint4*)(ws + L.chunks), c->blk_off,
+                                (const uint2*)(ws + L.stage_out), (const uint2*)(ws + L.stage_fix), c->out_idx,
+                                c->out_delta, c->out_cap, c->fix_idx, c->fix_bits, c->fix_cap, s);
+    }
     if (e != cudaSuccess) return cuda_fail(e);
     return VSZ_OK;
 }
@@ -258,11 +277,16 @@ static vsz_status reconstruct_impl(const vsz_params* p, const vsz_compressed* c,
     a.R = (int32_t)p->radius;
     a.pad_mode = p->pad;
     a.vec = (aligned(c->codes, 16) && aligned(out, 16) && (g.nd == 1 || g.nx % 4 == 0)) ? 1 : 0;
-    cudaError_t e = g.nd == 1 ? launch_recon_1d(a, q_out, s)
-                  : g.nd == 2 ? launch_recon_2d(a, q_out, s)
-                              : launch_recon_3d(a, q_out, s);
+    cudaError_t e;
+    {
+        TraceScope ts(q_out ? "recon_q" : "recon", s, g.nd, g.b, g.n);
+        e = g.nd == 1 ? launch_recon_1d(a, q_out, s)
+          : g.nd == 2 ? launch_recon_2d(a, q_out, s)
+                      : launch_recon_3d(a, q_out, s);
+    }
     if (e != cudaSuccess) return cuda_fail(e);
     if (!q_out && c->fix_cap > 0) {
+        TraceScope ts("fixups", s, g.nd, g.b, g.n);
         e = launch_fixups(c->hdr, c->fix_idx, c->fix_bits, c->fix_cap, (float*)out, g.n, s);
         if (e != cudaSuccess) return cuda_fail(e);
     }
@@ -282,9 +306,22 @@ vsz_status vsz_code_histogram(const vsz_params* p, const uint16_t* d_codes, uint
     vsz_status st = make_geom(p, &g);
     if (st != VSZ_OK) return st;
     if (!d_hist || (g.n > 0 && !d_codes)) return VSZ_ERR_INVALID_ARG;
-    cudaError_t e = launch_histogram(d_codes, g.n, d_hist, 2u * p->radius, (cudaStream_t)stream);
+    cudaError_t e;
+    {
+        TraceScope ts("histogram", (cudaStream_t)stream, g.nd, g.b, g.n);
+        e = launch_histogram(d_codes, g.n, d_hist, 2u * p->radius, (cudaStream_t)stream);
+    }
     if (e != cudaSuccess) return cuda_fail(e);
     return VSZ_OK;
+}
+
+vsz_status vsz_trace_enable(int on) {
+    Tracer::get().enable(on != 0);
+    return VSZ_OK;
+}
+
+int vsz_trace_read(vsz_trace_record* h_out, int max_records) {
+    return Tracer::get().read(h_out, h_out ? max_records : 0);
 }
 
 vsz_status vsz_read_header(const vsz_compressed* c, vsz_header* h_out, void* stream) {

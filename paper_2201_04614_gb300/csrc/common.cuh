@@ -78,26 +78,21 @@ inline WsLayout ws_layout(const Geom& g, uint64_t out_cap, uint64_t fix_cap) {
 
 __host__ __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
 
-// Prequantization q = rint(x * inv2eb) (Sec. III-A): one fp32 product, round
-// to nearest with ties to even, saturate to int32, NaN -> 0.  For |p| < 2^22
-// adding 1.5*2^23 rounds p to an integer in the default IEEE mode and the
-// integer appears in the low mantissa bits (the classic magic-number
-// rounding); larger magnitudes take the saturating conversion instruction.
+// Prequantization q = rint(x * inv2eb) (Sec. III-A): one fp32 product, then
+// the conversion instruction with round-to-nearest-even, which saturates to
+// the int32 range and maps NaN to 0.  Branch-free.
 __device__ __forceinline__ int32_t prequant(float x, float inv2eb) {
     const float p = __fmul_rn(x, inv2eb);
-    if (fabsf(p) < 4194304.0f) return __float_as_int(__fadd_rn(p, 12582912.0f)) - 0x4B400000;
-    if (p != p) return 0;
     int32_t q;
     asm("cvt.rni.sat.s32.f32 %0, %1;" : "=r"(q) : "f"(p));
     return q;
 }
 
-// (float)q, round to nearest even.  Exact for |q| < 2^22 via the same
-// mantissa construction; otherwise the conversion instruction.
+// (float)q, round to nearest even.
 __device__ __forceinline__ float q2f(int32_t q) {
-    if ((uint32_t)(q + 4194304) < 8388608u)
-        return __fsub_rn(__int_as_float(q + 0x4B400000), 12582912.0f);
-    return __int2float_rn(q);
+    float f;
+    asm("cvt.rn.f32.s32 %0, %1;" : "=f"(f) : "r"(q));
+    return f;
 }
 
 // Error-bound guard (fixup test): true when x_hat = fl(fl(q) * ebx2) misses

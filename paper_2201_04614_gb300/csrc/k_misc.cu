@@ -341,13 +341,17 @@ cudaError_t launch_qstats(const float* x, uint64_t n, WsHeader* wsh, vsz_header*
     return cudaGetLastError();
 }
 
-cudaError_t launch_compact(const Geom& g, uint4* tiles, uint4* chunks, vsz_header* hdr, uint32_t* blk_off,
-                           const uint2* stage_out, const uint2* stage_fix, uint32_t* out_idx, int32_t* out_delta,
-                           uint64_t out_cap, uint32_t* fix_idx, uint32_t* fix_bits, uint64_t fix_cap,
-                           cudaStream_t s) {
+cudaError_t launch_compact_scan(const Geom& g, uint4* chunks, vsz_header* hdr, uint32_t* blk_off,
+                                uint64_t out_cap, uint64_t fix_cap, cudaStream_t s) {
     k_compact_scan<<<1, 1024, 0, s>>>(chunks, g.nchunks, hdr, blk_off, g.nb, out_cap, fix_cap);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess || g.nchunks == 0) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compact_move(const Geom& g, const uint4* tiles, const uint4* chunks, uint32_t* blk_off,
+                                const uint2* stage_out, const uint2* stage_fix, uint32_t* out_idx,
+                                int32_t* out_delta, uint64_t out_cap, uint32_t* fix_idx, uint32_t* fix_bits,
+                                uint64_t fix_cap, cudaStream_t s) {
+    if (g.nchunks == 0) return cudaSuccess;
     k_compact<<<(unsigned)g.nchunks, 256, 0, s>>>(tiles, chunks, g.ntiles, g.nseg, g.nbx, g.bpt, blk_off,
                                                   stage_out, stage_fix, out_idx, out_delta, out_cap, fix_idx,
                                                   fix_bits, fix_cap);

@@ -202,3 +202,50 @@ def test_repeated_calls_reuse_workspace():
         c = oracle.compress(oracle.Params(dims, 16, 1e-5, oracle.EB_REL, 32, oracle.PAD_GLOBAL_AVG), x)
         got = f.to_host()
         assert np.array_equal(got["out_idx"], c.out_idx) and np.array_equal(got["codes"], c.codes)
+
+
+GUARD = 4096
+
+
+def _guarded(n, dtype, fill):
+    t = torch.full((n + GUARD,), fill, dtype=dtype, device="cuda")
+    return t, t[:n]
+
+
+@pytest.mark.parametrize("dims,block", [((260,), 4), ((1000,), 256), ((130, 260), 4), ((33, 130), 16),
+                                        ((17, 259), 8), ((9, 11, 132), 8), ((5, 7, 133), 4),
+                                        ((12, 40, 200), 32)])
+@pytest.mark.parametrize("pad", ["zero", "block_avg", "global_max"])
+def test_no_writes_past_outputs(dims, block, pad):
+    """Every output buffer is followed by a guard region filled with a
+    sentinel; compression and reconstruction must leave it untouched."""
+    x = field_for(dims, seed=31)
+    x = np.ascontiguousarray(x, np.float32).reshape(-1)
+    n = x.size
+    p = vsz.Params.make(dims, block, 1e-5, "rel", 8, pad)
+    f = vsz.Field(p, out_cap=n, fix_cap=n)
+    nb = p.nblocks
+    codes_g, f.codes = _guarded(n, torch.int16, 0x5A5A)
+    blk_g, f.blk_off = _guarded(nb + 1, torch.int32, 0x5A5A5A5A)
+    f._cc.codes = f.codes.data_ptr()
+    f._cc.blk_off = f.blk_off.data_ptr()
+    if f.pad is not None:
+        pad_g, f.pad = _guarded(nb, torch.int32, 0x5A5A5A5A)
+        f._cc.pad = f.pad.data_ptr()
+    f.compress(torch.from_numpy(x).cuda())
+    xh_g, xh = _guarded(n, torch.float32, 1234.5)
+    q_g, qv = _guarded(n, torch.int32, 0x5A5A5A5A)
+    f.reconstruct(out=xh)
+    f.reconstruct_q(out=qv)
+    torch.cuda.synchronize()
+    assert (codes_g[n:] == 0x5A5A).all()
+    assert (blk_g[nb + 1:] == 0x5A5A5A5A).all()
+    if f.pad is not None:
+        assert (pad_g[nb:] == 0x5A5A5A5A).all()
+    assert (xh_g[n:] == 1234.5).all()
+    assert (q_g[n:] == 0x5A5A5A5A).all()
+    po = oracle.Params(dims, block, 1e-5, oracle.EB_REL, 8, oracle.PAD_NAMES[pad])
+    c = oracle.compress(po, x)
+    got = f.to_host()
+    assert np.array_equal(got["codes"], c.codes)
+    assert np.array_equal(got["out_idx"], c.out_idx)
