@@ -45,7 +45,8 @@ struct WsHeader {
     int qmin, qmax;
     unsigned int done0, done1;     // last-block counters
     unsigned int has_finite;
-    unsigned int pad_[3];
+    unsigned int pad_;
+    unsigned long long ticket;     // dynamic tile scheduling of the compression kernel
 };
 static_assert(sizeof(WsHeader) <= 256, "ws header");
 

@@ -43,6 +43,7 @@ __global__ void k_begin(WsHeader* wsh, uint4* chunks, uint64_t nchunks, vsz_head
         wsh->done0 = 0;
         wsh->done1 = 0;
         wsh->has_finite = 0;
+        wsh->ticket = 0;
         hdr->pad_global = 0;
         hdr->status = 0;
         hdr->recon_status = 0;

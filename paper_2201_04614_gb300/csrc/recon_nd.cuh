@@ -1,7 +1,8 @@
 // recon_nd.cuh -- inverse dual-quant for 2D and 3D fields (Sec. III-A).
 //
-// Same tiles and lane layout as the compression walk; the codes stream
-// through a lane-private cp.async ring (8 bytes per lane and row).  Per row:
+// Same tiles, lane layout and batches of rows as the compression walk; the
+// codes stream through a lane-private, double-buffered cp.async ring (8
+// bytes per lane and row).  Per row:
 // residuals from the codes (code - R), outliers patched from the block's
 // slice of the outlier list, P added at the block origin, then the inverse of
 // each first-order difference:
@@ -12,26 +13,29 @@
 //       memory (zeroed per tile).
 // The walk visits a block's elements in canonical order (planes, rows, then
 // x), so the k-th code 0 met in a block is the block's k-th outlier: no
-// search over the outlier list is needed.
+// search over the outlier list is needed.  A batch is first checked for
+// code 0 as a whole; only batches that contain one take the patching path.
 #pragma once
+
+#include <type_traits>
 
 #include "compress_nd.cuh"
 
 namespace vsz {
 
 template <int ND, int B, bool QOUT>
-__global__ void __launch_bounds__(NdCfg<ND, B>::THREADS)
+__global__ void __launch_bounds__(NdCfg<ND, B>::THREADS, NdCfg<ND, B>::MINB_R)
 k_recon_nd(const ReconArgs a) {
     using C = NdCfg<ND, B>;
     constexpr int G = C::G;
-    constexpr int S = C::S;
+    constexpr int U = C::U;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     unsigned char* wsm = smem_raw + (size_t)wib * C::WARP_R;
-    unsigned char* ring = wsm;
     int4* zs = reinterpret_cast<int4*>(wsm + C::RING_R);
-    const uint32_t ring_lane = smem_addr(ring) + lane * 8;
+    const uint2* ring_rd = reinterpret_cast<const uint2*>(wsm) + lane;  // slot (h*U + u)*32
+    const uint32_t ring_wr = smem_addr(wsm) + lane * 8;
 
     const Geom& g = a.g;
     const float ebx2 = a.hdr->ebx2;
@@ -56,9 +60,11 @@ k_recon_nd(const ReconArgs a) {
         const bool bexists = bx < g.nbx;
         const int valid = x0 < nx ? (int)umin64(4, nx - x0) : 0;
         const uint32_t vmask = (1u << valid) - 1u;
+        const bool full = vec && valid == 4;
         const int ylen = (int)umin64(B, g.ny - by * B);
         const int zlen = ND == 3 ? (int)umin64(B, g.nz - bz * B) : 1;
-        const int nrows = zlen * ylen;
+        const int nbpp = (ylen + U - 1) / U;
+        const int nbatch = zlen * nbpp;
         const uint64_t blk = (bz * g.nby + by) * g.nbx + bx;
         const uint64_t tile_base = (ND == 3 ? bz * B * plane : 0) + by * B * nx + x0;
 
@@ -75,159 +81,170 @@ k_recon_nd(const ReconArgs a) {
         const bool anyout = __any_sync(VSZ_FULL, hi > lo);
         uint32_t rank = lo;
 
-        auto issue = [&](const RowCursor& ic, int row) {
-            if (!vec) return;
-            const uint32_t dst = ring_lane + (uint32_t)((row & (S - 1)) * 32 * 8);
-            const uint16_t* p = valid ? a.codes + ic.off : a.codes;
-            cp_async8(dst, p, valid ? 8u : 0u);
+        // copy the codes of batch (lz, j) into ring half h (vector path only)
+        auto issue_batch = [&](int lz, int j, int h) {
+            if (vec) {
+                const uint64_t off0 = tile_base + (uint64_t)lz * plane + (uint64_t)(j * U) * nx;
+                const uint32_t dst0 = ring_wr + (uint32_t)(h * U * 32 * 8);
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    if (j * U + u < ylen) {
+                        const uint64_t off = off0 + (uint64_t)u * nx;
+                        cp_async8(dst0 + u * 32 * 8, valid ? a.codes + off : a.codes, valid ? 8u : 0u);
+                    }
+                }
+            }
+            cp_async_commit();
         };
 
         int32_t ys[4] = {0, 0, 0, 0};
-        int32_t zr[C::ZREG ? B : 1][4];
-        if (C::ZREG) {
-#pragma unroll
-            for (int i = 0; i < (C::ZREG ? B : 1); ++i)
-#pragma unroll
-                for (int k = 0; k < 4; ++k) zr[i][k] = 0;
-        }
         if (C::ZSMEM)
             for (int ly = 0; ly < ylen; ++ly) zs[ly * 32 + lane] = make_int4(0, 0, 0, 0);
 
-        RowCursor ic{tile_base, 0, 0};
+        issue_batch(0, 0, 0);
+        int lz = 0, j = 0, h = 0;
+        for (int kb = 0; kb < nbatch; ++kb) {
+            int nj = j + 1, nlz = lz;
+            if (nj == nbpp) { nj = 0; ++nlz; }
+            if (kb + 1 < nbatch) issue_batch(nlz, nj, h ^ 1);
+            else cp_async_commit();
+            cp_async_wait<1>();
+            if (j == 0) {
 #pragma unroll
-        for (int i = 0; i < S - 1; ++i) {
-            if (i < nrows) {
-                issue(ic, i);
-                ic.next(ylen, nx, plane);
+                for (int k = 0; k < 4; ++k) ys[k] = 0;
             }
-            cp_async_commit();
-        }
-        RowCursor rc{tile_base, 0, 0};
-        int row = 0;
+            const uint64_t boff = tile_base + (uint64_t)lz * plane + (uint64_t)(j * U) * nx;
+            const bool b0 = kb == 0;
+            // Codes of the batch; rows past the edge read as "no outlier".
+            uint2 cw[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (j * U + u < ylen) {
+                    if (vec) {
+                        cw[u] = ring_rd[(h * U + u) * 32];
+                    } else {
+                        uint32_t c4[4];
+                        load4c(a.codes + boff + (uint64_t)u * nx, valid, false, c4);
+                        const uint32_t rr = (uint32_t)R;
+                        cw[u] = make_uint2((valid > 0 ? c4[0] : rr) | ((valid > 1 ? c4[1] : rr) << 16),
+                                           (valid > 2 ? c4[2] : rr) | ((valid > 3 ? c4[3] : rr) << 16));
+                    }
+                } else {
+                    cw[u] = make_uint2(0x00010001u, 0x00010001u);
+                }
+            }
+            // Does any code 0 (an outlier) occur in this batch?
+            uint32_t hz = 0;
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                hz |= ((cw[u].x - 0x00010001u) & ~cw[u].x & 0x80008000u) |
+                      ((cw[u].y - 0x00010001u) & ~cw[u].y & 0x80008000u);
+            const bool patch = anyout && __any_sync(VSZ_FULL, valid > 0 && hz != 0u);
 
-        auto do_row = [&](int ly, int zi) {
-            if (row + S - 1 < nrows) {
-                issue(ic, row + S - 1);
-                ic.next(ylen, nx, plane);
-            }
-            cp_async_commit();
-            uint32_t c[4];
-            if (vec) {
-                cp_async_wait<S - 1>();
-                const uint2 u = *reinterpret_cast<const uint2*>(ring + ((row & (S - 1)) * 32 + lane) * 8);
-                c[0] = u.x & 0xffffu; c[1] = u.x >> 16; c[2] = u.y & 0xffffu; c[3] = u.y >> 16;
-            } else {
-                load4c(a.codes + rc.off, valid, false, c);
-            }
-            int32_t d[4];
+            auto row = [&](auto patch_tag, int u) {
+                constexpr bool PATCH = decltype(patch_tag)::value;
+                const int ly = j * U + u;
+                const uint64_t roff = boff + (uint64_t)u * nx;
+                const uint32_t c[4] = {cw[u].x & 0xffffu, cw[u].x >> 16, cw[u].y & 0xffffu, cw[u].y >> 16};
+                int32_t d[4];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) d[k] = (int32_t)c[k] - R;
-            if (anyout) {
-                uint32_t zm = 0;
+                for (int k = 0; k < 4; ++k) d[k] = (int32_t)c[k] - R;
+                if (PATCH) {
+                    uint32_t zm = 0;
 #pragma unroll
-                for (int k = 0; k < 4; ++k) zm |= (c[k] == 0u ? 1u : 0u) << k;
-                zm &= vmask;
-                if (__any_sync(VSZ_FULL, zm != 0u)) {
-                    const uint32_t cz = __popc(zm);
-                    uint32_t iz = cz;
+                    for (int k = 0; k < 4; ++k) zm |= (c[k] == 0u ? 1u : 0u) << k;
+                    zm &= vmask;
+                    if (__any_sync(VSZ_FULL, zm != 0u)) {
+                        const uint32_t cz = __popc(zm);
+                        uint32_t iz = cz;
+#pragma unroll
+                        for (int off = 1; off < G; off <<= 1) {
+                            const uint32_t y = __shfl_up_sync(VSZ_FULL, iz, off);
+                            if (glane >= off) iz += y;
+                        }
+                        const uint32_t gtot = __shfl_sync(VSZ_FULL, iz, src + G - 1);
+                        uint32_t r = rank + (iz - cz);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            if (zm & (1u << k)) {
+                                if (r < hi && r < a.out_cap && a.out_idx[r] == (uint32_t)(roff + k)) {
+                                    d[k] = a.out_delta[r];
+                                } else {
+                                    atomicMax(&a.hdr->recon_status, (unsigned)VSZ_ERR_CORRUPT);
+                                    d[k] = 0;
+                                }
+                                ++r;
+                            }
+                        }
+                        rank += gtot;
+                    }
+                }
+                if (b0 && u == 0 && first) d[0] = wadd(d[0], P);
+                // Sx
+                d[1] = wadd(d[1], d[0]);
+                d[2] = wadd(d[2], d[1]);
+                d[3] = wadd(d[3], d[2]);
+                {
+                    const uint32_t tot = (uint32_t)d[3];
+                    uint32_t inc = tot;
 #pragma unroll
                     for (int off = 1; off < G; off <<= 1) {
-                        const uint32_t y = __shfl_up_sync(VSZ_FULL, iz, off);
-                        if (glane >= off) iz += y;
+                        const uint32_t y = __shfl_up_sync(VSZ_FULL, inc, off);
+                        if (glane >= off) inc += y;
                     }
-                    const uint32_t gtot = __shfl_sync(VSZ_FULL, iz, src + G - 1);
-                    uint32_t r = rank + (iz - cz);
+                    const int32_t ex = (int32_t)(inc - tot);
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        if (zm & (1u << k)) {
-                            if (r < hi && r < a.out_cap && a.out_idx[r] == (uint32_t)(rc.off + k)) {
-                                d[k] = a.out_delta[r];
-                            } else {
-                                atomicMax(&a.hdr->recon_status, (unsigned)VSZ_ERR_CORRUPT);
-                                d[k] = 0;
-                            }
-                            ++r;
-                        }
-                    }
-                    rank += gtot;
+                    for (int k = 0; k < 4; ++k) d[k] = wadd(d[k], ex);
                 }
-            }
-            if (row == 0 && first) d[0] = wadd(d[0], P);
-            // Sx
-            d[1] = wadd(d[1], d[0]);
-            d[2] = wadd(d[2], d[1]);
-            d[3] = wadd(d[3], d[2]);
-            {
-                const uint32_t tot = (uint32_t)d[3];
-                uint32_t inc = tot;
+                // Sy
 #pragma unroll
-                for (int off = 1; off < G; off <<= 1) {
-                    const uint32_t y = __shfl_up_sync(VSZ_FULL, inc, off);
-                    if (glane >= off) inc += y;
+                for (int k = 0; k < 4; ++k) {
+                    d[k] = wadd(d[k], ys[k]);
+                    ys[k] = d[k];
                 }
-                const int32_t ex = (int32_t)(inc - tot);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) d[k] = wadd(d[k], ex);
-            }
-            // Sy
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                d[k] = wadd(d[k], ys[k]);
-                ys[k] = d[k];
-            }
-            // Sz
-            if (ND == 3) {
+                // Sz
                 if (C::ZSMEM) {
                     int4& stz = zs[ly * 32 + lane];
                     const int4 pv = stz;
                     d[0] = wadd(d[0], pv.x); d[1] = wadd(d[1], pv.y);
                     d[2] = wadd(d[2], pv.z); d[3] = wadd(d[3], pv.w);
                     stz = make_int4(d[0], d[1], d[2], d[3]);
-                } else {
+                }
+                if (QOUT) {
+                    int32_t* o = reinterpret_cast<int32_t*>(a.out) + roff;
+                    if (full) {
+                        *reinterpret_cast<int4*>(o) = make_int4(d[0], d[1], d[2], d[3]);
+                    } else {
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        d[k] = wadd(d[k], zr[zi][k]);
-                        zr[zi][k] = d[k];
+                        for (int k = 0; k < 4; ++k)
+                            if (k < valid) o[k] = d[k];
+                    }
+                } else {
+                    float vv[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) vv[k] = __fmul_rn(q2f(d[k]), ebx2);
+                    float* o = reinterpret_cast<float*>(a.out) + roff;
+                    if (full) {
+                        *reinterpret_cast<float4*>(o) = make_float4(vv[0], vv[1], vv[2], vv[3]);
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            if (k < valid) o[k] = vv[k];
                     }
                 }
-            }
-            const bool full = vec && valid == 4;
-            if (QOUT) {
-                int32_t* o = reinterpret_cast<int32_t*>(a.out) + rc.off;
-                if (full) {
-                    *reinterpret_cast<int4*>(o) = make_int4(d[0], d[1], d[2], d[3]);
-                } else {
+            };
+            if (patch) {
 #pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        if (k < valid) o[k] = d[k];
-                }
+                for (int u = 0; u < U; ++u)
+                    if (j * U + u < ylen) row(std::true_type{}, u);
             } else {
-                float v[4];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) v[k] = __fmul_rn(q2f(d[k]), ebx2);
-                float* o = reinterpret_cast<float*>(a.out) + rc.off;
-                if (full) {
-                    *reinterpret_cast<float4*>(o) = make_float4(v[0], v[1], v[2], v[3]);
-                } else {
-#pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        if (k < valid) o[k] = v[k];
-                }
+                for (int u = 0; u < U; ++u)
+                    if (j * U + u < ylen) row(std::false_type{}, u);
             }
-            rc.next(ylen, nx, plane);
-            ++row;
-        };
-
-        for (int lz = 0; lz < zlen; ++lz) {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) ys[k] = 0;
-            if (C::ZREG) {
-#pragma unroll
-                for (int ly = 0; ly < (C::ZREG ? B : 1); ++ly)
-                    if (ly < ylen) do_row(ly, ly);
-            } else {
-                for (int ly = 0; ly < ylen; ++ly) do_row(ly, 0);
-            }
+            h ^= 1;
+            lz = nlz;
+            j = nj;
         }
         cp_async_wait<0>();
     }

@@ -2,8 +2,8 @@
 //
 // Each lane streams its own slice of consecutive rows into its own slots;
 // only that lane reads them back, so completion is tracked by the lane's
-// own cp.async groups (one group per row) and no cross-lane barrier is
-// needed.  The bytes in flight live in shared memory instead of registers.
+// own cp.async groups and no cross-lane barrier is needed.  The bytes in
+// flight live in shared memory instead of registers.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -27,21 +27,5 @@ __device__ __forceinline__ void cp_async4(uint32_t dst, const void* src, uint32_
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
-// Row cursor over a warp-tile: rows are (lz, ly) with ly fastest; advancing
-// moves the element offset of the row start.
-struct RowCursor {
-    uint64_t off;    // element offset of the current row (at the lane's column x0)
-    int ly, lz;
-    __device__ __forceinline__ void next(int ylen, uint64_t nx, uint64_t plane) {
-        if (++ly == ylen) {
-            ly = 0;
-            ++lz;
-            off += plane - (uint64_t)(ylen - 1) * nx;
-        } else {
-            off += nx;
-        }
-    }
-};
 
 }  // namespace vsz

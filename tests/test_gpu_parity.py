@@ -249,3 +249,23 @@ def test_no_writes_past_outputs(dims, block, pad):
     got = f.to_host()
     assert np.array_equal(got["codes"], c.codes)
     assert np.array_equal(got["out_idx"], c.out_idx)
+
+
+@pytest.mark.parametrize("dims,block", [((40, 300), 16), ((40, 260), 8), ((20, 24, 132), 8),
+                                        ((20, 40, 68), 16), ((300000,), 64)])
+@pytest.mark.parametrize("pad", ["zero", "block_avg", "block_min", "global_avg"])
+def test_parity_exact_mode_switch(dims, block, pad):
+    """Rows (2D), planes (3D) or a stretch (1D) whose prequantized values
+    cross 2^20 in the middle of a tile, and values right at 2^20, so a tile
+    starts in one arithmetic mode and has to continue in the other."""
+    rng = np.random.default_rng(17)
+    n = int(np.prod(dims))
+    x = rng.integers(-300, 301, n).astype(np.float64)
+    lead = np.arange(n) // (n // dims[0]) if len(dims) > 1 else np.arange(n)
+    big = lead >= (dims[0] * 3) // 5
+    x = np.where(big, x + 1.5e6, x + 1000.0)
+    x[::97] = 1048576.0          # exactly 2^20
+    x[1::89] = -1048575.0
+    x = x.astype(np.float32)
+    f, c, g, o, xx = run_both(x, dims, block, 0.5, "abs", 512, pad)
+    assert_parity(f, c, g, o, xx, pad)
