@@ -48,7 +48,8 @@ typedef enum {
     VSZ_ERR_UNSUPPORTED = 2,  /* valid for the method, not built (e.g. ndim 4) */
     VSZ_ERR_CAPACITY = 3,     /* outlier or fixup lists longer than the caller's capacity */
     VSZ_ERR_CUDA = 4,         /* a CUDA launch or runtime call failed */
-    VSZ_ERR_CORRUPT = 5       /* reconstruction met a code 0 with no matching outlier */
+    VSZ_ERR_CORRUPT = 5,      /* reconstruction met a code 0 with no matching outlier */
+    VSZ_ERR_TOO_LARGE = 6     /* the call needs more scratch than vsz_compress_noalloc's fixed workspace */
 } vsz_status;
 
 /* Sec. II-B: absolute, or value-range relative (eb * (max - min)). */
@@ -168,6 +169,35 @@ VSZ_API vsz_status vsz_outlier_compact(const vsz_params* p, vsz_compressed* c,
 /* Both compression steps in order. */
 VSZ_API vsz_status vsz_compress(const vsz_params* p, const float* d_x, vsz_compressed* c,
                         void* d_ws, size_t ws_bytes, void* stream);
+
+/* Bytes of the fixed workspace that vsz_compress_noalloc uses (16 MiB). */
+#define VSZ_NOALLOC_WS_BYTES (16u << 20)
+
+/*
+ * vsz_compress without a caller-supplied workspace and without allocating
+ * (the paper has no counterpart: this is a deployment aid).  Some callers
+ * cannot allocate device memory: code running inside a framework whose
+ * caching allocator already owns the GPU's memory, where a cudaMalloc of its
+ * own fails or makes the framework release its caches, and latency-critical
+ * paths that cannot accept the device-wide synchronization a cudaMalloc or
+ * cudaFree may cause.  They pass inputs and outputs exactly as for
+ * vsz_compress; the scratch is a fixed VSZ_NOALLOC_WS_BYTES array in the
+ * library's own device memory, which every GPU that loads the library holds
+ * until the process exits.  The call allocates nothing (no cudaMalloc, no
+ * cudaFree, no allocating library routine).
+ *  - Size limit: if vsz_workspace_size(p, c->out_cap, c->fix_cap) exceeds
+ *    VSZ_NOALLOC_WS_BYTES the call returns VSZ_ERR_TOO_LARGE before any GPU
+ *    work (use vsz_compress with your own workspace, or smaller capacities).
+ *  - The first call on a device looks up the array's device address (once
+ *    per device, with that device current); make that first call before any
+ *    stream capture.
+ *  - All calls share the one array, and it keeps the last call's contents;
+ *    each call clears the parts that must start at zero itself.  Calls whose
+ *    GPU work overlaps (on different streams, or from several host threads
+ *    without ordering) race on it: order them on one stream.
+ */
+VSZ_API vsz_status vsz_compress_noalloc(const vsz_params* p, const float* d_x, vsz_compressed* c,
+                                        void* stream);
 
 /*
  * Decompression (Sec. III-A: the inverse of the dual-quant): residuals from

@@ -25,7 +25,8 @@ PAD_MODES = {
     "block_min": 4, "block_max": 5, "block_avg": 6,
 }
 _STATUS = {0: "VSZ_OK", 1: "VSZ_ERR_INVALID_ARG", 2: "VSZ_ERR_UNSUPPORTED",
-           3: "VSZ_ERR_CAPACITY", 4: "VSZ_ERR_CUDA", 5: "VSZ_ERR_CORRUPT"}
+           3: "VSZ_ERR_CAPACITY", 4: "VSZ_ERR_CUDA", 5: "VSZ_ERR_CORRUPT", 6: "VSZ_ERR_TOO_LARGE"}
+NOALLOC_WS_BYTES = 16 << 20  # VSZ_NOALLOC_WS_BYTES
 
 
 class VszError(RuntimeError):
@@ -64,7 +65,8 @@ HEADER_BYTES = ctypes.sizeof(_CHeader)
 EXPORTED = ["vsz_status_string", "vsz_last_cuda_error", "vsz_abi_version", "vsz_validate",
             "vsz_num_elems", "vsz_num_blocks", "vsz_workspace_size", "vsz_prequant_lorenzo",
             "vsz_outlier_compact", "vsz_compress", "vsz_reconstruct", "vsz_reconstruct_q",
-            "vsz_code_histogram", "vsz_read_header", "vsz_trace_enable", "vsz_trace_read"]
+            "vsz_code_histogram", "vsz_read_header", "vsz_trace_enable", "vsz_trace_read",
+            "vsz_compress_noalloc"]
 
 _lib = None
 
@@ -99,6 +101,7 @@ def lib():
     for name in ("vsz_prequant_lorenzo", "vsz_compress"):
         getattr(L, name).argtypes = [P(_CParams), vp, P(_CCompressed), vp, sz, vp]
     L.vsz_outlier_compact.argtypes = [P(_CParams), P(_CCompressed), vp, sz, vp]
+    L.vsz_compress_noalloc.argtypes = [P(_CParams), vp, P(_CCompressed), vp]
     L.vsz_reconstruct.argtypes = [P(_CParams), P(_CCompressed), vp, vp]
     L.vsz_reconstruct_q.argtypes = [P(_CParams), P(_CCompressed), vp, vp]
     L.vsz_code_histogram.argtypes = [P(_CParams), vp, vp, vp]
@@ -247,6 +250,12 @@ class Field:
     def compress(self, x, stream=None):
         _check(lib().vsz_compress(ctypes.byref(self._cp), self._x(x), ctypes.byref(self._cc), _ptr(self.ws),
                                   self.ws_bytes, _stream_handle(stream)), "vsz_compress")
+
+    def compress_noalloc(self, x, stream=None):
+        """Compression through vsz_compress_noalloc: the library's fixed
+        workspace instead of self.ws (for callers that cannot allocate)."""
+        _check(lib().vsz_compress_noalloc(ctypes.byref(self._cp), self._x(x), ctypes.byref(self._cc),
+                                          _stream_handle(stream)), "vsz_compress_noalloc")
 
     def reconstruct(self, out=None, stream=None):
         import torch

@@ -106,6 +106,31 @@ static vsz_status make_geom(const vsz_params* p, Geom* g) {
 
 static bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
+// Fixed workspace of vsz_compress_noalloc: part of the library's device
+// image, so it exists on every GPU that loads the library, until exit.
+static __device__ __align__(256) unsigned char g_noalloc_ws[VSZ_NOALLOC_WS_BYTES];
+
+// Device address of g_noalloc_ws on the current device, looked up once per
+// device.  In host code the array's name is only a host-side stand-in, so
+// kernels must get this address, never the name.
+static vsz_status noalloc_workspace(void** out) {
+    static std::mutex mu;
+    static void* addr[64] = {nullptr};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (dev < 0 || dev >= 64) return VSZ_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_ws);
+        if (e != cudaSuccess) return cuda_fail(e);
+        addr[dev] = p;
+    }
+    *out = addr[dev];
+    return VSZ_OK;
+}
+
 }  // namespace vsz
 
 using namespace vsz;
@@ -120,6 +145,7 @@ const char* vsz_status_string(vsz_status s) {
     case VSZ_ERR_CAPACITY: return "VSZ_ERR_CAPACITY";
     case VSZ_ERR_CUDA: return "VSZ_ERR_CUDA";
     case VSZ_ERR_CORRUPT: return "VSZ_ERR_CORRUPT";
+    case VSZ_ERR_TOO_LARGE: return "VSZ_ERR_TOO_LARGE";
     default: return "VSZ_ERR_UNKNOWN";
     }
 }
@@ -252,6 +278,20 @@ vsz_status vsz_compress(const vsz_params* p, const float* d_x, vsz_compressed* c
     vsz_status st = vsz_prequant_lorenzo(p, d_x, c, d_ws, ws_bytes, stream);
     if (st != VSZ_OK) return st;
     return vsz_outlier_compact(p, c, d_ws, ws_bytes, stream);
+}
+
+vsz_status vsz_compress_noalloc(const vsz_params* p, const float* d_x, vsz_compressed* c, void* stream) {
+    Geom g;
+    vsz_status st = make_geom(p, &g);
+    if (st != VSZ_OK) return st;
+    if ((st = check_compressed(g, p, c)) != VSZ_OK) return st;
+    const size_t need = ws_layout(g, c->out_cap, c->fix_cap).total;
+    if (need > (size_t)VSZ_NOALLOC_WS_BYTES) return VSZ_ERR_TOO_LARGE;
+    void* ws = nullptr;
+    if ((st = noalloc_workspace(&ws)) != VSZ_OK) return st;
+    // k_begin, the first kernel of the call, re-zeroes the cursors, counters
+    // and chunk sums this call relies on; the rest is written before it is read.
+    return vsz_compress(p, d_x, c, ws, VSZ_NOALLOC_WS_BYTES, stream);
 }
 
 static vsz_status reconstruct_impl(const vsz_params* p, const vsz_compressed* c, void* out, bool q_out,
