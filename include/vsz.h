@@ -199,6 +199,9 @@ VSZ_API vsz_status vsz_compress(const vsz_params* p, const float* d_x, vsz_compr
 VSZ_API vsz_status vsz_compress_noalloc(const vsz_params* p, const float* d_x, vsz_compressed* c,
                                         void* stream);
 
+/* Bytes of the optional reconstruction workspace. */
+#define VSZ_RECON_WS_BYTES 256
+
 /*
  * Decompression (Sec. III-A: the inverse of the dual-quant): residuals from
  * the codes and the outlier lists, per-block inclusive prefix sums along x,
@@ -207,15 +210,20 @@ VSZ_API vsz_status vsz_compress_noalloc(const vsz_params* p, const float* d_x, v
  * for every finite x; NaN/Inf come back bit for bit.  A code 0 without a
  * matching outlier sets c->hdr->recon_status = VSZ_ERR_CORRUPT.
  *   d_xhat    [n] fp32 output (device)
+ *   d_ws      optional workspace of VSZ_RECON_WS_BYTES (device, 16-byte
+ *             aligned) or NULL.  With it, tiles are handed to warps by an
+ *             atomic ticket, which evens out tiles that hold many outliers;
+ *             without it, tiles are assigned statically.  Calls in flight at
+ *             the same time need distinct workspaces.
  */
 VSZ_API vsz_status vsz_reconstruct(const vsz_params* p, const vsz_compressed* c, float* d_xhat,
-                           void* stream);
+                                   void* d_ws, size_t ws_bytes, void* stream);
 
 /* Same inverse, writing the reconstructed prequantized integers q (int32[n])
  * instead of values (no fixups applied).  Used to verify that the inverse
  * reproduces the prequantization exactly. */
 VSZ_API vsz_status vsz_reconstruct_q(const vsz_params* p, const vsz_compressed* c, int32_t* d_q,
-                             void* stream);
+                                     void* d_ws, size_t ws_bytes, void* stream);
 
 /*
  * Code statistics (the learned tuner's labels): d_hist[0..2R-1] receives the

@@ -27,6 +27,7 @@ PAD_MODES = {
 _STATUS = {0: "VSZ_OK", 1: "VSZ_ERR_INVALID_ARG", 2: "VSZ_ERR_UNSUPPORTED",
            3: "VSZ_ERR_CAPACITY", 4: "VSZ_ERR_CUDA", 5: "VSZ_ERR_CORRUPT", 6: "VSZ_ERR_TOO_LARGE"}
 NOALLOC_WS_BYTES = 16 << 20  # VSZ_NOALLOC_WS_BYTES
+RECON_WS_BYTES = 256         # VSZ_RECON_WS_BYTES
 
 
 class VszError(RuntimeError):
@@ -102,8 +103,8 @@ def lib():
         getattr(L, name).argtypes = [P(_CParams), vp, P(_CCompressed), vp, sz, vp]
     L.vsz_outlier_compact.argtypes = [P(_CParams), P(_CCompressed), vp, sz, vp]
     L.vsz_compress_noalloc.argtypes = [P(_CParams), vp, P(_CCompressed), vp]
-    L.vsz_reconstruct.argtypes = [P(_CParams), P(_CCompressed), vp, vp]
-    L.vsz_reconstruct_q.argtypes = [P(_CParams), P(_CCompressed), vp, vp]
+    L.vsz_reconstruct.argtypes = [P(_CParams), P(_CCompressed), vp, vp, sz, vp]
+    L.vsz_reconstruct_q.argtypes = [P(_CParams), P(_CCompressed), vp, vp, sz, vp]
     L.vsz_code_histogram.argtypes = [P(_CParams), vp, vp, vp]
     L.vsz_read_header.argtypes = [P(_CCompressed), P(_CHeader), vp]
     L.vsz_trace_enable.argtypes = [ctypes.c_int]
@@ -223,6 +224,7 @@ class Field:
         self.hdr = torch.zeros((HEADER_BYTES + 7) // 8, dtype=torch.int64, device=dev)
         self.ws_bytes = workspace_size(params, self.out_cap, self.fix_cap)
         self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=dev)
+        self.rws = torch.zeros(RECON_WS_BYTES // 4, dtype=torch.int32, device=dev)
         self._cp = params.c()
         self._cc = _CCompressed(self.codes.data_ptr(), self.pad.data_ptr() if self.pad is not None else 0,
                                 self.blk_off.data_ptr(), self.out_idx.data_ptr(), self.out_delta.data_ptr(),
@@ -261,16 +263,16 @@ class Field:
         import torch
         if out is None:
             out = torch.empty(max(self.n, 1), dtype=torch.float32, device=self.codes.device)
-        _check(lib().vsz_reconstruct(ctypes.byref(self._cp), ctypes.byref(self._cc), _ptr(out),
-                                     _stream_handle(stream)), "vsz_reconstruct")
+        _check(lib().vsz_reconstruct(ctypes.byref(self._cp), ctypes.byref(self._cc), _ptr(out), _ptr(self.rws),
+                                     RECON_WS_BYTES, _stream_handle(stream)), "vsz_reconstruct")
         return out[: self.n]
 
     def reconstruct_q(self, out=None, stream=None):
         import torch
         if out is None:
             out = torch.empty(max(self.n, 1), dtype=torch.int32, device=self.codes.device)
-        _check(lib().vsz_reconstruct_q(ctypes.byref(self._cp), ctypes.byref(self._cc), _ptr(out),
-                                       _stream_handle(stream)), "vsz_reconstruct_q")
+        _check(lib().vsz_reconstruct_q(ctypes.byref(self._cp), ctypes.byref(self._cc), _ptr(out), _ptr(self.rws),
+                                       RECON_WS_BYTES, _stream_handle(stream)), "vsz_reconstruct_q")
         return out[: self.n]
 
     def code_histogram(self, out=None, stream=None):

@@ -295,12 +295,13 @@ vsz_status vsz_compress_noalloc(const vsz_params* p, const float* d_x, vsz_compr
 }
 
 static vsz_status reconstruct_impl(const vsz_params* p, const vsz_compressed* c, void* out, bool q_out,
-                                   void* stream) {
+                                   void* d_ws, size_t ws_bytes, void* stream) {
     Geom g;
     vsz_status st = make_geom(p, &g);
     if (st != VSZ_OK) return st;
     if ((st = check_compressed(g, p, c)) != VSZ_OK) return st;
     if (g.n > 0 && !out) return VSZ_ERR_INVALID_ARG;
+    if (d_ws && (ws_bytes < VSZ_RECON_WS_BYTES || !aligned(d_ws, 16))) return VSZ_ERR_INVALID_ARG;
     if (g.n == 0) return VSZ_OK;
     cudaStream_t s = (cudaStream_t)stream;
     ReconArgs a;
@@ -311,6 +312,7 @@ static vsz_status reconstruct_impl(const vsz_params* p, const vsz_compressed* c,
     a.out_idx = c->out_idx;
     a.out_delta = c->out_delta;
     a.out_cap = c->out_cap;
+    a.ticket = (d_ws && g.nd > 1) ? (unsigned int*)d_ws : nullptr;
     a.hdr = c->hdr;
     a.out = out;
     a.g = g;
@@ -318,6 +320,10 @@ static vsz_status reconstruct_impl(const vsz_params* p, const vsz_compressed* c,
     a.pad_mode = p->pad;
     a.vec = (aligned(c->codes, 16) && aligned(out, 16) && (g.nd == 1 || g.nx % 4 == 0)) ? 1 : 0;
     cudaError_t e;
+    if (a.ticket) {
+        e = cudaMemsetAsync(a.ticket, 0, sizeof(unsigned int), s);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
     {
         TraceScope ts(q_out ? "recon_q" : "recon", s, g.nd, g.b, g.n);
         e = g.nd == 1 ? launch_recon_1d(a, q_out, s)
@@ -333,12 +339,14 @@ static vsz_status reconstruct_impl(const vsz_params* p, const vsz_compressed* c,
     return VSZ_OK;
 }
 
-vsz_status vsz_reconstruct(const vsz_params* p, const vsz_compressed* c, float* d_xhat, void* stream) {
-    return reconstruct_impl(p, c, d_xhat, false, stream);
+vsz_status vsz_reconstruct(const vsz_params* p, const vsz_compressed* c, float* d_xhat, void* d_ws,
+                           size_t ws_bytes, void* stream) {
+    return reconstruct_impl(p, c, d_xhat, false, d_ws, ws_bytes, stream);
 }
 
-vsz_status vsz_reconstruct_q(const vsz_params* p, const vsz_compressed* c, int32_t* d_q, void* stream) {
-    return reconstruct_impl(p, c, d_q, true, stream);
+vsz_status vsz_reconstruct_q(const vsz_params* p, const vsz_compressed* c, int32_t* d_q, void* d_ws,
+                             size_t ws_bytes, void* stream) {
+    return reconstruct_impl(p, c, d_q, true, d_ws, ws_bytes, stream);
 }
 
 vsz_status vsz_code_histogram(const vsz_params* p, const uint16_t* d_codes, uint32_t* d_hist, void* stream) {

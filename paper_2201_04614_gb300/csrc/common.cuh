@@ -21,7 +21,7 @@ namespace vsz {
 // x, so its blocks are consecutive in the canonical block order.
 constexpr int kSegCols = 128;
 constexpr int kChunk1D = 4096;
-constexpr int kTilesPerChunk = 256;  // tiles per compaction chunk
+constexpr int kTilesPerChunk = 32;   // tiles per compaction chunk (one CTA each)
 
 struct Geom {
     int32_t nd;
@@ -159,6 +159,7 @@ struct ReconArgs {
     const uint32_t* out_idx;
     const int32_t* out_delta;
     uint64_t out_cap;      // entries readable in out_idx / out_delta
+    unsigned int* ticket;  // zeroed tile counter (dynamic scheduling) or nullptr (static)
     vsz_header* hdr;
     void* out;             // float* (values) or int32_t* (q)
     Geom g;

@@ -57,7 +57,7 @@
 #define VSZ_ND_MINB_C 5
 #endif
 #ifndef VSZ_ND_MINB_R
-#define VSZ_ND_MINB_R 8
+#define VSZ_ND_MINB_R 7
 #endif
 #ifndef VSZ_ND_STASH
 #define VSZ_ND_STASH 256
@@ -84,9 +84,11 @@ struct NdCfg {
     static constexpr size_t HIST_B = (size_t)U * 32 * 16;  // residuals of the current batch
     static constexpr size_t WARP_C = RING_C + STASH_B + TAB_B + ZS_B + HIST_B;
     static constexpr size_t SMEM_C = WARP_C * WARPS;
-    // per-warp shared memory, reconstruction: ring of codes | z state
+    // per-warp shared memory, reconstruction: ring of codes | z state | outliers of the tile
+    static constexpr int OCAP = 256;
     static constexpr size_t RING_R = (size_t)2 * U * 32 * 8;
-    static constexpr size_t WARP_R = RING_R + ZS_B;
+    static constexpr size_t OC_B = (size_t)OCAP * 8;
+    static constexpr size_t WARP_R = RING_R + ZS_B + OC_B;
     static constexpr size_t SMEM_R = WARP_R * WARPS;
 };
 

@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(1024) k_compact_scan(uint4* chunks, uint64_t n
     }
 }
 
-// Compaction, part 2: per chunk of tiles, the tiles' offsets, the blocks'
+// Compaction, part 2: per chunk of tiles (one CTA), the tiles' offsets, the blocks'
 // final offsets (in-tile prefix + tile offset) and the move of each tile's
 // staged entries to their canonical place.
 __global__ void __launch_bounds__(256) k_compact(const uint4* __restrict__ tiles, const uint4* __restrict__ chunks,
@@ -236,25 +236,27 @@ __global__ void __launch_bounds__(256) k_compact(const uint4* __restrict__ tiles
                                                  uint32_t* fix_bits, uint64_t fix_cap) {
     __shared__ uint4 rec[kTilesPerChunk];
     __shared__ uint32_t toff_o[kTilesPerChunk], toff_f[kTilesPerChunk];
-    __shared__ uint32_t wso[8], wsf[8];
     const uint64_t t0 = (uint64_t)blockIdx.x * kTilesPerChunk;
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    const uint64_t t = t0 + threadIdx.x;
-    const uint4 r = t < ntiles ? tiles[t] : make_uint4(0, 0, 0, 0);
-    uint32_t io = r.y, iff = r.w;
+    if (w == 0) {  // the chunk's tile offsets: chunk offset + exclusive scan of the tile totals
+        uint32_t bo = chunks[blockIdx.x].z, bf = chunks[blockIdx.x].w;
+        for (int i0 = 0; i0 < kTilesPerChunk; i0 += 32) {
+            const uint64_t t = t0 + i0 + l;
+            const uint4 r = t < ntiles ? tiles[t] : make_uint4(0, 0, 0, 0);
+            uint32_t io = r.y, iff = r.w;
 #pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const uint32_t yo = __shfl_up_sync(VSZ_FULL, io, off);
-        const uint32_t yf = __shfl_up_sync(VSZ_FULL, iff, off);
-        if (l >= off) { io += yo; iff += yf; }
+            for (int off = 1; off < 32; off <<= 1) {
+                const uint32_t yo = __shfl_up_sync(VSZ_FULL, io, off);
+                const uint32_t yf = __shfl_up_sync(VSZ_FULL, iff, off);
+                if (l >= off) { io += yo; iff += yf; }
+            }
+            rec[i0 + l] = r;
+            toff_o[i0 + l] = bo + io - r.y;
+            toff_f[i0 + l] = bf + iff - r.w;
+            bo += __shfl_sync(VSZ_FULL, io, 31);
+            bf += __shfl_sync(VSZ_FULL, iff, 31);
+        }
     }
-    if (l == 31) { wso[w] = io; wsf[w] = iff; }
-    __syncthreads();
-    uint32_t bo = chunks[blockIdx.x].z, bf = chunks[blockIdx.x].w;
-    for (int k = 0; k < w; ++k) { bo += wso[k]; bf += wsf[k]; }
-    rec[threadIdx.x] = r;
-    toff_o[threadIdx.x] = bo + io - r.y;
-    toff_f[threadIdx.x] = bf + iff - r.w;
     __syncthreads();
 
     const int nt = (int)umin64(kTilesPerChunk, ntiles - t0);

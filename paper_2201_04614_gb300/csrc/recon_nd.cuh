@@ -34,6 +34,8 @@ k_recon_nd(const ReconArgs a) {
     const int wib = threadIdx.x >> 5;
     unsigned char* wsm = smem_raw + (size_t)wib * C::WARP_R;
     int4* zs = reinterpret_cast<int4*>(wsm + C::RING_R);
+    uint32_t* oc_idx = reinterpret_cast<uint32_t*>(wsm + C::RING_R + C::ZS_B);
+    int32_t* oc_del = reinterpret_cast<int32_t*>(oc_idx + C::OCAP);
     const uint2* ring_rd = reinterpret_cast<const uint2*>(wsm) + lane;  // slot (h*U + u)*32
     const uint32_t ring_wr = smem_addr(wsm) + lane * 8;
 
@@ -49,8 +51,18 @@ k_recon_nd(const ReconArgs a) {
     const int src = lane & ~(G - 1);
     const bool vec = a.vec != 0;
 
-    for (uint64_t t = (uint64_t)blockIdx.x * C::WARPS + wib; t < g.ntiles;
-         t += (uint64_t)gridDim.x * C::WARPS) {
+    uint64_t tnext = (uint64_t)blockIdx.x * C::WARPS + wib;
+    for (;;) {
+        // next tile: from the ticket when there is one (evens out tiles with
+        // many outliers), else a static grid stride
+        uint64_t t = tnext;
+        if (a.ticket) {
+            unsigned int tk = 0;
+            if (lane == 0) tk = atomicAdd(a.ticket, 1u);
+            t = __shfl_sync(VSZ_FULL, tk, 0);
+        }
+        tnext += (uint64_t)gridDim.x * C::WARPS;
+        if (t >= g.ntiles) break;
         const uint64_t s = t % g.nseg;
         const uint64_t rb = t / g.nseg;
         const uint64_t by = rb % g.nby;
@@ -81,6 +93,31 @@ k_recon_nd(const ReconArgs a) {
         const bool anyout = __any_sync(VSZ_FULL, hi > lo);
         uint32_t rank = lo;
 
+        // The tile's blocks are consecutive in canonical order, so its outliers
+        // are one slice of the list: bring it into shared memory with the first
+        // batch when it is short enough.
+        uint32_t lo_t = 0;
+        bool cached = false;
+        if (anyout) {
+            const uint64_t fb = (bz * g.nby + by) * g.nbx + (s * kSegCols) / B;
+            const uint64_t nblk = umin64(kSegCols / B, g.nbx - (s * kSegCols) / B);
+            uint32_t hi_t = 0;
+            if (lane == 0) {
+                lo_t = a.blk_off[fb];
+                hi_t = a.blk_off[fb + nblk];
+            }
+            lo_t = __shfl_sync(VSZ_FULL, lo_t, 0);
+            hi_t = __shfl_sync(VSZ_FULL, hi_t, 0);
+            cached = hi_t >= lo_t && hi_t - lo_t <= (uint32_t)C::OCAP && (uint64_t)hi_t <= a.out_cap;
+            if (cached) {
+                const uint32_t sidx = smem_addr(oc_idx), sdel = smem_addr(oc_del);
+                for (uint32_t i = lane; i < hi_t - lo_t; i += 32) {
+                    cp_async4(sidx + 4 * i, a.out_idx + lo_t + i, 4u);
+                    cp_async4(sdel + 4 * i, a.out_delta + lo_t + i, 4u);
+                }
+            }
+        }
+
         // copy the codes of batch (lz, j) into ring half h (vector path only)
         auto issue_batch = [&](int lz, int j, int h) {
             if (vec) {
@@ -109,6 +146,7 @@ k_recon_nd(const ReconArgs a) {
             if (kb + 1 < nbatch) issue_batch(nlz, nj, h ^ 1);
             else cp_async_commit();
             cp_async_wait<1>();
+            if (cached && kb == 0) __syncwarp();  // every lane's share of the outlier slice has landed
             if (j == 0) {
 #pragma unroll
                 for (int k = 0; k < 4; ++k) ys[k] = 0;
@@ -167,8 +205,10 @@ k_recon_nd(const ReconArgs a) {
 #pragma unroll
                         for (int k = 0; k < 4; ++k) {
                             if (zm & (1u << k)) {
-                                if (r < hi && r < a.out_cap && a.out_idx[r] == (uint32_t)(roff + k)) {
-                                    d[k] = a.out_delta[r];
+                                const bool in = r < hi && r < a.out_cap;
+                                const uint32_t oi = !in ? ~0u : cached ? oc_idx[r - lo_t] : a.out_idx[r];
+                                if (in && oi == (uint32_t)(roff + k)) {
+                                    d[k] = cached ? oc_del[r - lo_t] : a.out_delta[r];
                                 } else {
                                     atomicMax(&a.hdr->recon_status, (unsigned)VSZ_ERR_CORRUPT);
                                     d[k] = 0;

@@ -100,5 +100,5 @@ def test_calls_without_gpu_fail_cleanly(vsz):
     cc = vsz._CCompressed()
     rc = L.vsz_prequant_lorenzo(ctypes.byref(p), None, ctypes.byref(cc), None, 0, None)
     assert rc == 1
-    rc = L.vsz_reconstruct(ctypes.byref(p), ctypes.byref(cc), None, None)
+    rc = L.vsz_reconstruct(ctypes.byref(p), ctypes.byref(cc), None, None, 0, None)
     assert rc == 1

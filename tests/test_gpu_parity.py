@@ -269,3 +269,28 @@ def test_parity_exact_mode_switch(dims, block, pad):
     x = x.astype(np.float32)
     f, c, g, o, xx = run_both(x, dims, block, 0.5, "abs", 512, pad)
     assert_parity(f, c, g, o, xx, pad)
+
+
+def test_reconstruct_with_and_without_workspace_agree():
+    """vsz_reconstruct with the optional workspace (ticket-scheduled tiles)
+    and without it (static tiles) give identical values and integers."""
+    import ctypes
+    dims = (24, 40, 200)
+    x = field_for(dims, seed=41).reshape(-1)
+    p = vsz.Params.make(dims, 8, 1e-5, "rel", 16, "block_avg")
+    f = vsz.Field(p)
+    f.compress(torch.from_numpy(np.ascontiguousarray(x, np.float32)).cuda())
+    a = f.reconstruct().clone()
+    qa = f.reconstruct_q().clone()
+    L = vsz.lib()
+    b = torch.empty_like(a)
+    qb = torch.empty_like(qa)
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert L.vsz_reconstruct(ctypes.byref(f._cp), ctypes.byref(f._cc), ctypes.c_void_p(b.data_ptr()),
+                             None, 0, s) == 0
+    assert L.vsz_reconstruct_q(ctypes.byref(f._cp), ctypes.byref(f._cc), ctypes.c_void_p(qb.data_ptr()),
+                               None, 0, s) == 0
+    torch.cuda.synchronize()
+    assert torch.equal(a.view(torch.int32), b.view(torch.int32))
+    assert torch.equal(qa, qb)
+    assert f.header()["n_out"] > 0
