@@ -199,6 +199,49 @@ VSZ_API vsz_status vsz_compress(const vsz_params* p, const float* d_x, vsz_compr
 VSZ_API vsz_status vsz_compress_noalloc(const vsz_params* p, const float* d_x, vsz_compressed* c,
                                         void* stream);
 
+/* ------------------------------------------------------------------------ */
+/* Batches: many fields of uneven rank and size compressed together.        */
+/* ------------------------------------------------------------------------ */
+
+/* One field of a batch: its parameters, its fp32 input and its output
+ * buffers, exactly as for vsz_compress. */
+typedef struct {
+    vsz_params     params;
+    const float*   d_x;
+    vsz_compressed out;
+} vsz_field_job;
+
+/* Opaque batch plan. */
+typedef struct vsz_batch_st* vsz_batch;
+
+/* Workspace bytes for a batch (0 if a job is invalid). */
+VSZ_API size_t vsz_batch_workspace_size(const vsz_field_job* jobs, int njobs);
+
+/*
+ * Plan a batch (the batching pattern of this build; the paper processes one
+ * field at a time with OpenMP over its blocks, Sec. III-F).  Fields are
+ * grouped by class (rank, block edge, per-block padding or not); compressing
+ * the batch then takes a fixed number of launches whatever the number of
+ * fields: one initialisation, one value-range pass over every relative-eb
+ * field, one global-statistics pass over every global-padding field, one
+ * persistent compression kernel per class whose warps draw tiles of all the
+ * class's fields from one queue, and two compaction kernels.  Results are
+ * identical to vsz_compress on each field.  The plan keeps the jobs' pointers;
+ * their buffers must outlive it.  The plan allocates its descriptor tables on
+ * the device (freed by vsz_batch_destroy); d_ws (caller-owned, 256-byte
+ * aligned) holds every field's compression workspace.  use_graph != 0
+ * captures the launch sequence into a CUDA graph on the first submit and
+ * replays it afterwards (not on the legacy default stream).
+ */
+VSZ_API vsz_status vsz_batch_create(const vsz_field_job* jobs, int njobs, void* d_ws, size_t ws_bytes,
+                                    int use_graph, vsz_batch* out);
+
+/* Compress every field of the batch, asynchronously on `stream`. */
+VSZ_API vsz_status vsz_batch_submit(vsz_batch b, void* stream);
+
+/* Free the plan (waits for nothing; do not destroy a plan with work in flight). */
+VSZ_API vsz_status vsz_batch_destroy(vsz_batch b);
+
 /* Bytes of the optional reconstruction workspace. */
 #define VSZ_RECON_WS_BYTES 256
 

@@ -15,7 +15,7 @@ from dataclasses import dataclass
 from . import buildlib as _build
 
 __all__ = [
-    "VszError", "Params", "Field", "lib", "build", "EB_ABS", "EB_REL", "PAD_MODES",
+    "VszError", "Params", "Field", "Batch", "lib", "build", "EB_ABS", "EB_REL", "PAD_MODES",
     "num_blocks", "workspace_size", "trace_enable", "trace_read",
 ]
 
@@ -57,6 +57,10 @@ class _CCompressed(ctypes.Structure):
                 ("hdr", ctypes.c_void_p)]
 
 
+class _CFieldJob(ctypes.Structure):
+    _fields_ = [("params", _CParams), ("d_x", ctypes.c_void_p), ("out", _CCompressed)]
+
+
 class _CTrace(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 24), ("ndim", ctypes.c_int32), ("block", ctypes.c_uint32),
                 ("n", ctypes.c_uint64), ("ms", ctypes.c_float), ("reserved", ctypes.c_uint32)]
@@ -67,7 +71,8 @@ EXPORTED = ["vsz_status_string", "vsz_last_cuda_error", "vsz_abi_version", "vsz_
             "vsz_num_elems", "vsz_num_blocks", "vsz_workspace_size", "vsz_prequant_lorenzo",
             "vsz_outlier_compact", "vsz_compress", "vsz_reconstruct", "vsz_reconstruct_q",
             "vsz_code_histogram", "vsz_read_header", "vsz_trace_enable", "vsz_trace_read",
-            "vsz_compress_noalloc"]
+            "vsz_compress_noalloc", "vsz_batch_workspace_size", "vsz_batch_create", "vsz_batch_submit",
+            "vsz_batch_destroy"]
 
 _lib = None
 
@@ -107,6 +112,11 @@ def lib():
     L.vsz_reconstruct_q.argtypes = [P(_CParams), P(_CCompressed), vp, vp, sz, vp]
     L.vsz_code_histogram.argtypes = [P(_CParams), vp, vp, vp]
     L.vsz_read_header.argtypes = [P(_CCompressed), P(_CHeader), vp]
+    L.vsz_batch_workspace_size.restype = sz
+    L.vsz_batch_workspace_size.argtypes = [P(_CFieldJob), ctypes.c_int]
+    L.vsz_batch_create.argtypes = [P(_CFieldJob), ctypes.c_int, vp, sz, ctypes.c_int, P(ctypes.c_void_p)]
+    L.vsz_batch_submit.argtypes = [vp, vp]
+    L.vsz_batch_destroy.argtypes = [vp]
     L.vsz_trace_enable.argtypes = [ctypes.c_int]
     L.vsz_trace_read.argtypes = [P(_CTrace), ctypes.c_int]
     for name in EXPORTED:
@@ -307,3 +317,46 @@ class Field:
             "fix_idx": self.fix_idx[:nf].cpu().numpy().view(np.uint32),
             "fix_bits": self.fix_bits[:nf].cpu().numpy().view(np.uint32),
         }
+
+
+class Batch:
+    """Many fields compressed together (vsz_batch_*): a fixed number of
+    launches whatever the number of fields, optionally replayed as a CUDA
+    graph.  `fields` are Field objects (their output buffers are used) and
+    `xs` the matching contiguous float32 CUDA inputs; both must stay alive
+    and in place while the batch exists (the plan holds their pointers)."""
+
+    def __init__(self, fields, xs, use_graph: bool = True):
+        import torch
+        if len(fields) != len(xs) or not fields:
+            raise ValueError("one input per field, at least one field")
+        self.fields, self.xs = list(fields), list(xs)
+        jobs = (_CFieldJob * len(fields))()
+        for i, (f, x) in enumerate(zip(fields, xs)):
+            jobs[i].params = f._cp
+            jobs[i].d_x = f._x(x)
+            jobs[i].out = f._cc
+        self._jobs = jobs
+        L = lib()
+        self.ws_bytes = int(L.vsz_batch_workspace_size(jobs, len(fields)))
+        if self.ws_bytes == 0:
+            raise VszError(1, "vsz_batch_workspace_size")
+        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=fields[0].codes.device)
+        h = ctypes.c_void_p()
+        _check(L.vsz_batch_create(jobs, len(fields), _ptr(self.ws), self.ws_bytes, 1 if use_graph else 0,
+                                  ctypes.byref(h)), "vsz_batch_create")
+        self._h = h
+
+    def submit(self, stream=None):
+        _check(lib().vsz_batch_submit(self._h, _stream_handle(stream)), "vsz_batch_submit")
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().vsz_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -49,7 +49,7 @@ int grid_for(const void* kernel, int threads, size_t smem, uint64_t per_cta, uin
 
 static thread_local char g_last_err[256] = "";
 
-static vsz_status cuda_fail(cudaError_t e) {
+vsz_status cuda_fail(cudaError_t e) {
     std::snprintf(g_last_err, sizeof g_last_err, "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
     return VSZ_ERR_CUDA;
 }
@@ -57,7 +57,7 @@ static vsz_status cuda_fail(cudaError_t e) {
 static bool pow2(uint32_t v) { return v && !(v & (v - 1)); }
 
 // Validate parameters and derive the geometry and tiling of a field.
-static vsz_status make_geom(const vsz_params* p, Geom* g) {
+vsz_status make_geom(const vsz_params* p, Geom* g) {
     if (!p) return VSZ_ERR_INVALID_ARG;
     if (p->ndim == 4) return VSZ_ERR_UNSUPPORTED;
     if (p->ndim < 1 || p->ndim > 3) return VSZ_ERR_INVALID_ARG;
@@ -104,7 +104,18 @@ static vsz_status make_geom(const vsz_params* p, Geom* g) {
     return VSZ_OK;
 }
 
-static bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+vsz_status check_compressed(const Geom& g, const vsz_params* p, const vsz_compressed* c) {
+    if (!c || !c->hdr || !c->blk_off) return VSZ_ERR_INVALID_ARG;
+    if (!aligned(c->hdr, 8)) return VSZ_ERR_INVALID_ARG;
+    if (g.n > 0 && !c->codes) return VSZ_ERR_INVALID_ARG;
+    if (is_block_pad(p->pad) && g.nb > 0 && !c->pad) return VSZ_ERR_INVALID_ARG;
+    if (c->out_cap > 0 && (!c->out_idx || !c->out_delta)) return VSZ_ERR_INVALID_ARG;
+    if (c->fix_cap > 0 && (!c->fix_idx || !c->fix_bits)) return VSZ_ERR_INVALID_ARG;
+    if (c->out_cap >= (1ull << 32) || c->fix_cap >= (1ull << 32)) return VSZ_ERR_INVALID_ARG;
+    return VSZ_OK;
+}
 
 // Fixed workspace of vsz_compress_noalloc: part of the library's device
 // image, so it exists on every GPU that loads the library, until exit.
@@ -175,16 +186,6 @@ size_t vsz_workspace_size(const vsz_params* p, uint64_t out_cap, uint64_t fix_ca
     return ws_layout(g, out_cap, fix_cap).total;
 }
 
-static vsz_status check_compressed(const Geom& g, const vsz_params* p, const vsz_compressed* c) {
-    if (!c || !c->hdr || !c->blk_off) return VSZ_ERR_INVALID_ARG;
-    if (!aligned(c->hdr, 8)) return VSZ_ERR_INVALID_ARG;
-    if (g.n > 0 && !c->codes) return VSZ_ERR_INVALID_ARG;
-    if (is_block_pad(p->pad) && g.nb > 0 && !c->pad) return VSZ_ERR_INVALID_ARG;
-    if (c->out_cap > 0 && (!c->out_idx || !c->out_delta)) return VSZ_ERR_INVALID_ARG;
-    if (c->fix_cap > 0 && (!c->fix_idx || !c->fix_bits)) return VSZ_ERR_INVALID_ARG;
-    if (c->out_cap >= (1ull << 32) || c->fix_cap >= (1ull << 32)) return VSZ_ERR_INVALID_ARG;
-    return VSZ_OK;
-}
 
 vsz_status vsz_prequant_lorenzo(const vsz_params* p, const float* d_x, vsz_compressed* c, void* d_ws,
                                 size_t ws_bytes, void* stream) {
@@ -233,6 +234,10 @@ vsz_status vsz_prequant_lorenzo(const vsz_params* p, const float* d_x, vsz_compr
     a.chunks = chunks;
     a.stage_out = (uint2*)(ws + L.stage_out);
     a.stage_fix = (uint2*)(ws + L.stage_fix);
+    a.out_idx = c->out_idx;
+    a.out_delta = c->out_delta;
+    a.fix_idx = c->fix_idx;
+    a.fix_bits = c->fix_bits;
     a.out_cap = c->out_cap;
     a.fix_cap = c->fix_cap;
     a.g = g;

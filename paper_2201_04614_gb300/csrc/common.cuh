@@ -145,6 +145,10 @@ struct CompressArgs {
     uint4* chunks;
     uint2* stage_out;
     uint2* stage_fix;
+    uint32_t* out_idx;     // final lists (used by the batch compaction)
+    int32_t* out_delta;
+    uint32_t* fix_idx;
+    uint32_t* fix_bits;
     uint64_t out_cap, fix_cap;
     Geom g;
     int32_t R;
@@ -180,7 +184,20 @@ cudaError_t launch_recon_1d(const ReconArgs& a, bool q_out, cudaStream_t s);
 cudaError_t launch_recon_2d(const ReconArgs& a, bool q_out, cudaStream_t s);
 cudaError_t launch_recon_3d(const ReconArgs& a, bool q_out, cudaStream_t s);
 
+cudaError_t launch_lorenzo_batch_1d(uint32_t b, bool bp, const CompressArgs* fields, const uint64_t* tile_prefix,
+                                    int nfields, uint64_t total_tiles, unsigned long long* ticket, cudaStream_t s);
+cudaError_t launch_lorenzo_batch_2d(uint32_t b, bool bp, const CompressArgs* fields, const uint64_t* tile_prefix,
+                                    int nfields, uint64_t total_tiles, unsigned long long* ticket, cudaStream_t s);
+cudaError_t launch_lorenzo_batch_3d(uint32_t b, bool bp, const CompressArgs* fields, const uint64_t* tile_prefix,
+                                    int nfields, uint64_t total_tiles, unsigned long long* ticket, cudaStream_t s);
+
 int num_sms();
 int grid_for(const void* kernel, int threads, size_t smem, uint64_t work_items_per_cta, uint64_t work);
+
+// Host helpers of the C ABI (api.cu).
+vsz_status make_geom(const vsz_params* p, Geom* g);
+vsz_status check_compressed(const Geom& g, const vsz_params* p, const vsz_compressed* c);
+vsz_status cuda_fail(cudaError_t e);
+bool aligned(const void* p, size_t a);
 
 }  // namespace vsz

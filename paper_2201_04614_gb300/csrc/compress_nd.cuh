@@ -100,18 +100,15 @@ __device__ __forceinline__ uint32_t stash_key(uint32_t fix, uint32_t g, uint32_t
     return (fix << 31) | (g << 26) | (row << 7) | col;
 }
 
+// All the work of one tile t of one field: the walk(s), the per-block
+// padding and counts, and the tile's staged outliers and fixups.
 template <int ND, int B, bool BP>
-__global__ void __launch_bounds__(NdCfg<ND, B>::THREADS, NdCfg<ND, B>::MINB_C)
-k_lorenzo_nd(const CompressArgs a) {
+__device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t t, unsigned char* wsm, int lane) {
     using C = NdCfg<ND, B>;
     constexpr int G = C::G;
     constexpr int U = C::U;
     constexpr float kSafe = 1048576.0f;     // 2^20
     constexpr float kMagic = 12582912.0f;   // 1.5 * 2^23: adding it rounds |p| < 2^22 to an integer
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    unsigned char* wsm = smem_raw + (size_t)wib * C::WARP_C;
     uint2* stash = reinterpret_cast<uint2*>(wsm + C::RING_C);
     uint32_t* pre_out = reinterpret_cast<uint32_t*>(wsm + C::RING_C + C::STASH_B);
     uint32_t* pre_fix = pre_out + 32;
@@ -141,167 +138,217 @@ k_lorenzo_nd(const CompressArgs a) {
     const bool pg_small = BP || (Pg >= -(1 << 20) && Pg <= (1 << 20));
     const float Pgf = (float)(BP ? 0 : Pg);
 
-    for (;;) {
-        unsigned long long tk = 0;
-        if (lane == 0) tk = atomicAdd(&a.wsh->ticket, 1ull);
-        const uint64_t t = __shfl_sync(VSZ_FULL, tk, 0);
-        if (t >= g.ntiles) break;
-        const uint64_t s = t % g.nseg;
-        const uint64_t rb = t / g.nseg;
-        const uint64_t by = rb % g.nby;
-        const uint64_t bz = rb / g.nby;
-        const uint64_t x0 = s * kSegCols + (uint64_t)lane * 4;
-        const uint64_t bx = (s * kSegCols) / B + grp;
-        const bool bexists = bx < g.nbx;
-        const int valid = x0 < nx ? (int)umin64(4, nx - x0) : 0;
-        const uint32_t vmask = (1u << valid) - 1u;
-        const bool vst = vec && valid == 4;  // this lane's 4 codes are stored as one 8-byte word
-        const int ylen = (int)umin64(B, g.ny - by * B);
-        const int zlen = ND == 3 ? (int)umin64(B, g.nz - bz * B) : 1;
-        const int nbpp = (ylen + U - 1) / U;  // batches per plane
-        const int nbatch = zlen * nbpp;
-        const uint64_t blk = (bz * g.nby + by) * g.nbx + bx;
-        const uint64_t tile_base = (ND == 3 ? bz * B * plane : 0) + by * B * nx + x0;
-        const float* xsrc = a.x;
+    const uint64_t s = t % g.nseg;
+    const uint64_t rb = t / g.nseg;
+    const uint64_t by = rb % g.nby;
+    const uint64_t bz = rb / g.nby;
+    const uint64_t x0 = s * kSegCols + (uint64_t)lane * 4;
+    const uint64_t bx = (s * kSegCols) / B + grp;
+    const bool bexists = bx < g.nbx;
+    const int valid = x0 < nx ? (int)umin64(4, nx - x0) : 0;
+    const uint32_t vmask = (1u << valid) - 1u;
+    const bool vst = vec && valid == 4;  // this lane's 4 codes are stored as one 8-byte word
+    const int ylen = (int)umin64(B, g.ny - by * B);
+    const int zlen = ND == 3 ? (int)umin64(B, g.nz - bz * B) : 1;
+    const int nbpp = (ylen + U - 1) / U;  // batches per plane
+    const int nbatch = zlen * nbpp;
+    const uint64_t blk = (bz * g.nby + by) * g.nbx + bx;
+    const uint64_t tile_base = (ND == 3 ? bz * B * plane : 0) + by * B * nx + x0;
+    const float* xsrc = a.x;
 
-        // copy the rows of batch (lz, j) into ring half h
-        auto issue_batch = [&](int lz, int j, int h) {
-            const uint64_t off0 = tile_base + (uint64_t)lz * plane + (uint64_t)(j * U) * nx;
-            const uint32_t dst0 = ring_wr + (uint32_t)(h * U * 32 * 16);
+    // copy the rows of batch (lz, j) into ring half h
+    auto issue_batch = [&](int lz, int j, int h) {
+        const uint64_t off0 = tile_base + (uint64_t)lz * plane + (uint64_t)(j * U) * nx;
+        const uint32_t dst0 = ring_wr + (uint32_t)(h * U * 32 * 16);
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                if (j * U + u < ylen) {
-                    const uint64_t off = off0 + (uint64_t)u * nx;
-                    const uint32_t dst = dst0 + u * 32 * 16;
-                    if (vec) {
-                        cp_async16(dst, valid ? xsrc + off : xsrc, valid ? 16u : 0u);
-                    } else {
+        for (int u = 0; u < U; ++u) {
+            if (j * U + u < ylen) {
+                const uint64_t off = off0 + (uint64_t)u * nx;
+                const uint32_t dst = dst0 + u * 32 * 16;
+                if (vec) {
+                    cp_async16(dst, valid ? xsrc + off : xsrc, valid ? 16u : 0u);
+                } else {
 #pragma unroll
-                        for (int k = 0; k < 4; ++k)
-                            cp_async4(dst + 4 * k, (k < valid) ? xsrc + off + k : xsrc, (k < valid) ? 4u : 0u);
-                    }
+                    for (int k = 0; k < 4; ++k)
+                        cp_async4(dst + 4 * k, (k < valid) ? xsrc + off + k : xsrc, (k < valid) ? 4u : 0u);
                 }
             }
-            cp_async_commit();
-        };
+        }
+        cp_async_commit();
+    };
 
-        // results of the first pass that the second pass needs
-        uint32_t cnt_out = 0, cnt_fix = 0, nst = 0;
-        int32_t Pb = BP ? 0 : Pg;
-        uint32_t eo_g = 0, ef_g = 0;
-        unsigned long long base_out = 0, base_fix = 0;
-        int32_t qcorner = 0;
-        uint32_t r0c01 = 0, r0c23 = 0;
-        int32_t smin = INT_MAX, smax = INT_MIN;
-        float sminf = __int_as_float(0x7f800000), smaxf = -__int_as_float(0x7f800000);
-        long long ssum = 0;
+    // results of the first pass that the second pass needs
+    uint32_t cnt_out = 0, cnt_fix = 0, nst = 0;
+    int32_t Pb = BP ? 0 : Pg;
+    uint32_t eo_g = 0, ef_g = 0;
+    unsigned long long base_out = 0, base_fix = 0;
+    int32_t qcorner = 0;
+    uint32_t r0c01 = 0, r0c23 = 0;
+    int32_t smin = INT_MAX, smax = INT_MIN;
+    float sminf = __int_as_float(0x7f800000), smaxf = -__int_as_float(0x7f800000);
+    long long ssum = 0;
 
-        for (int pass = 0; pass < 2; ++pass) {
-            const bool emit = pass == 1;  // second walk: write entries, no codes
-            // carried state: fp32 mode uses pf / float bits in zs, int mode p1 / ints in zs
-            float pf[4] = {0.f, 0.f, 0.f, 0.f};
-            int32_t p1[4] = {0, 0, 0, 0};
-            if (C::ZSMEM)
-                for (int ly = 0; ly < ylen; ++ly) zs[ly * 32 + lane] = make_int4(0, 0, 0, 0);
-            bool imode = emit || !pg_small;
-            uint32_t run_o = 0, run_f = 0;  // running ranks inside this lane's block (second walk)
+    for (int pass = 0; pass < 2; ++pass) {
+        const bool emit = pass == 1;  // second walk: write entries, no codes
+        // carried state: fp32 mode uses pf / float bits in zs, int mode p1 / ints in zs
+        float pf[4] = {0.f, 0.f, 0.f, 0.f};
+        int32_t p1[4] = {0, 0, 0, 0};
+        if (C::ZSMEM)
+            for (int ly = 0; ly < ylen; ++ly) zs[ly * 32 + lane] = make_int4(0, 0, 0, 0);
+        bool imode = emit || !pg_small;
+        uint32_t run_o = 0, run_f = 0;  // running ranks inside this lane's block (second walk)
 
-            issue_batch(0, 0, 0);
-            int lz = 0, j = 0, h = 0;
-            for (int kb = 0; kb < nbatch; ++kb) {
-                int nj = j + 1, nlz = lz;
-                if (nj == nbpp) { nj = 0; ++nlz; }
-                if (kb + 1 < nbatch) issue_batch(nlz, nj, h ^ 1);
-                else cp_async_commit();
-                cp_async_wait<1>();
-                if (j == 0) {
+        issue_batch(0, 0, 0);
+        int lz = 0, j = 0, h = 0;
+        for (int kb = 0; kb < nbatch; ++kb) {
+            int nj = j + 1, nlz = lz;
+            if (nj == nbpp) { nj = 0; ++nlz; }
+            if (kb + 1 < nbatch) issue_batch(nlz, nj, h ^ 1);
+            else cp_async_commit();
+            cp_async_wait<1>();
+            if (j == 0) {
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) { pf[k] = 0.f; p1[k] = 0; }
+                for (int k = 0; k < 4; ++k) { pf[k] = 0.f; p1[k] = 0; }
+            }
+            const uint64_t boff = tile_base + (uint64_t)lz * plane + (uint64_t)(j * U) * nx;
+            const bool b0 = kb == 0;
+            float xr[U][4], pr[U][4];
+            bool unsafe = false;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const float4 v = (j * U + u < ylen) ? ring_rd[(h * U + u) * 32] : make_float4(0.f, 0.f, 0.f, 0.f);
+                xr[u][0] = v.x; xr[u][1] = v.y; xr[u][2] = v.z; xr[u][3] = v.w;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    pr[u][k] = __fmul_rn(xr[u][k], inv2eb);
+                    unsafe |= !(fabsf(pr[u][k]) < kSafe);
                 }
-                const uint64_t boff = tile_base + (uint64_t)lz * plane + (uint64_t)(j * U) * nx;
-                const bool b0 = kb == 0;
-                float xr[U][4], pr[U][4];
-                bool unsafe = false;
+            }
+            if (!imode && __any_sync(VSZ_FULL, unsafe)) {
+                // switch this tile to int32 arithmetic; the carried state is exact
+                imode = true;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) p1[k] = __float2int_rn(pf[k]);
+                if (C::ZSMEM)
+                    for (int ly = 0; ly < ylen; ++ly) {
+                        const int4 w = zs[ly * 32 + lane];
+                        zs[ly * 32 + lane] = make_int4(__float2int_rn(__int_as_float(w.x)), __float2int_rn(__int_as_float(w.y)),
+                                                       __float2int_rn(__int_as_float(w.z)), __float2int_rn(__int_as_float(w.w)));
+                    }
+            }
+            // Branch-free pass over the batch: codes out, residuals to the
+            // history, one flag bit per row that may hold an outlier or fixup.
+            uint32_t fmask = 0;
+            if (!imode) {
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
-                    const float4 v = (j * U + u < ylen) ? ring_rd[(h * U + u) * 32] : make_float4(0.f, 0.f, 0.f, 0.f);
-                    xr[u][0] = v.x; xr[u][1] = v.y; xr[u][2] = v.z; xr[u][3] = v.w;
+                    const int ly = j * U + u;
+                    if (ly >= ylen) break;
+                    float rp[4], d[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) rp[k] = __fsub_rn(__fadd_rn(pr[u][k], kMagic), kMagic);
+                    float left = __shfl_up_sync(VSZ_FULL, rp[3], 1);
+                    if (first) left = 0.f;
+                    d[0] = __fsub_rn(rp[0], left);
+                    d[1] = __fsub_rn(rp[1], rp[0]);
+                    d[2] = __fsub_rn(rp[2], rp[1]);
+                    d[3] = __fsub_rn(rp[3], rp[2]);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {  // Dy
+                        const float r1 = d[k];
+                        d[k] = __fsub_rn(r1, pf[k]);
+                        pf[k] = r1;
+                    }
+                    if (C::ZSMEM) {  // Dz
+                        int4& st = zs[ly * 32 + lane];
+                        const int4 pv = st;
+                        st = make_int4(__float_as_int(d[0]), __float_as_int(d[1]), __float_as_int(d[2]), __float_as_int(d[3]));
+                        d[0] = __fsub_rn(d[0], __int_as_float(pv.x)); d[1] = __fsub_rn(d[1], __int_as_float(pv.y));
+                        d[2] = __fsub_rn(d[2], __int_as_float(pv.z)); d[3] = __fsub_rn(d[3], __int_as_float(pv.w));
+                    }
+                    if (u == 0 && b0 && first) {
+                        if (BP) qcorner = __float2int_rn(rp[0]);
+                        else d[0] = __fsub_rn(d[0], Pgf);
+                    }
+                    dh[u * 32] = make_int4(__float_as_int(d[0]), __float_as_int(d[1]), __float_as_int(d[2]), __float_as_int(d[3]));
+                    uint32_t cb[4];
+                    bool flag = false;
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
-                        pr[u][k] = __fmul_rn(xr[u][k], inv2eb);
-                        unsafe |= !(fabsf(pr[u][k]) < kSafe);
+                        const bool ok = fabsf(d[k]) < Rf;
+                        cb[k] = ok ? __float_as_uint(__fadd_rn(d[k], RB)) : 0u;
+                        const float xh = __fmul_rn(rp[k], ebx2);
+                        flag |= !ok | !(fabsf(__fsub_rn(xr[u][k], xh)) <= ebf);
                     }
-                }
-                if (!imode && __any_sync(VSZ_FULL, unsafe)) {
-                    // switch this tile to int32 arithmetic; the carried state is exact
-                    imode = true;
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) p1[k] = __float2int_rn(pf[k]);
-                    if (C::ZSMEM)
-                        for (int ly = 0; ly < ylen; ++ly) {
-                            const int4 w = zs[ly * 32 + lane];
-                            zs[ly * 32 + lane] = make_int4(__float2int_rn(__int_as_float(w.x)), __float2int_rn(__int_as_float(w.y)),
-                                                           __float2int_rn(__int_as_float(w.z)), __float2int_rn(__int_as_float(w.w)));
-                        }
-                }
-                // Branch-free pass over the batch: codes out, residuals to the
-                // history, one flag bit per row that may hold an outlier or fixup.
-                uint32_t fmask = 0;
-                if (!imode) {
-#pragma unroll
-                    for (int u = 0; u < U; ++u) {
-                        const int ly = j * U + u;
-                        if (ly >= ylen) break;
-                        float rp[4], d[4];
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) rp[k] = __fsub_rn(__fadd_rn(pr[u][k], kMagic), kMagic);
-                        float left = __shfl_up_sync(VSZ_FULL, rp[3], 1);
-                        if (first) left = 0.f;
-                        d[0] = __fsub_rn(rp[0], left);
-                        d[1] = __fsub_rn(rp[1], rp[0]);
-                        d[2] = __fsub_rn(rp[2], rp[1]);
-                        d[3] = __fsub_rn(rp[3], rp[2]);
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) {  // Dy
-                            const float r1 = d[k];
-                            d[k] = __fsub_rn(r1, pf[k]);
-                            pf[k] = r1;
-                        }
-                        if (C::ZSMEM) {  // Dz
-                            int4& st = zs[ly * 32 + lane];
-                            const int4 pv = st;
-                            st = make_int4(__float_as_int(d[0]), __float_as_int(d[1]), __float_as_int(d[2]), __float_as_int(d[3]));
-                            d[0] = __fsub_rn(d[0], __int_as_float(pv.x)); d[1] = __fsub_rn(d[1], __int_as_float(pv.y));
-                            d[2] = __fsub_rn(d[2], __int_as_float(pv.z)); d[3] = __fsub_rn(d[3], __int_as_float(pv.w));
-                        }
-                        if (u == 0 && b0 && first) {
-                            if (BP) qcorner = __float2int_rn(rp[0]);
-                            else d[0] = __fsub_rn(d[0], Pgf);
-                        }
-                        dh[u * 32] = make_int4(__float_as_int(d[0]), __float_as_int(d[1]), __float_as_int(d[2]), __float_as_int(d[3]));
-                        uint32_t cb[4];
-                        bool flag = false;
+                    if (BP) {
+                        float rs = 0.f;
 #pragma unroll
                         for (int k = 0; k < 4; ++k) {
-                            const bool ok = fabsf(d[k]) < Rf;
-                            cb[k] = ok ? __float_as_uint(__fadd_rn(d[k], RB)) : 0u;
-                            const float xh = __fmul_rn(rp[k], ebx2);
-                            flag |= !ok | !(fabsf(__fsub_rn(xr[u][k], xh)) <= ebf);
-                        }
-                        if (BP) {
-                            float rs = 0.f;
-#pragma unroll
-                            for (int k = 0; k < 4; ++k) {
-                                if (k < valid) {
-                                    sminf = fminf(sminf, rp[k]);
-                                    smaxf = fmaxf(smaxf, rp[k]);
-                                }
-                                rs = __fadd_rn(rs, rp[k]);  // zero-filled past the edge; exact below 2^22
+                            if (k < valid) {
+                                sminf = fminf(sminf, rp[k]);
+                                smaxf = fmaxf(smaxf, rp[k]);
                             }
-                            ssum += __float2int_rn(rs);
+                            rs = __fadd_rn(rs, rp[k]);  // zero-filled past the edge; exact below 2^22
                         }
-                        fmask |= flag ? (1u << u) : 0u;
-                        const uint32_t c01 = __byte_perm(cb[0], cb[1], 0x5410), c23 = __byte_perm(cb[2], cb[3], 0x5410);
+                        ssum += __float2int_rn(rs);
+                    }
+                    fmask |= flag ? (1u << u) : 0u;
+                    const uint32_t c01 = __byte_perm(cb[0], cb[1], 0x5410), c23 = __byte_perm(cb[2], cb[3], 0x5410);
+                    if (BP && b0 && u == 0) {
+                        r0c01 = c01;
+                        r0c23 = c23;
+                    } else {
+                        store4c(a.codes + boff + (uint64_t)u * nx, valid, vst, c01, c23);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int ly = j * U + u;
+                    if (ly >= ylen) break;
+                    int32_t q[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) q[k] = prequant(xr[u][k], inv2eb);
+                    int32_t left = __shfl_up_sync(VSZ_FULL, q[3], 1);
+                    if (first) left = 0;
+                    int32_t d[4];
+                    d[0] = wsub(q[0], left);
+                    d[1] = wsub(q[1], q[0]);
+                    d[2] = wsub(q[2], q[1]);
+                    d[3] = wsub(q[3], q[2]);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {  // Dy
+                        const int32_t r1 = d[k];
+                        d[k] = wsub(r1, p1[k]);
+                        p1[k] = r1;
+                    }
+                    if (C::ZSMEM) {  // Dz
+                        int4& st = zs[ly * 32 + lane];
+                        const int4 pv = st;
+                        st = make_int4(d[0], d[1], d[2], d[3]);
+                        d[0] = wsub(d[0], pv.x); d[1] = wsub(d[1], pv.y);
+                        d[2] = wsub(d[2], pv.z); d[3] = wsub(d[3], pv.w);
+                    }
+                    if (u == 0 && b0 && first) {
+                        if (BP && !emit) qcorner = q[0];
+                        else d[0] = wsub(d[0], Pb);
+                    }
+                    dh[u * 32] = make_int4(d[0], d[1], d[2], d[3]);
+                    uint32_t c[4];
+                    bool flag = false;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        c[k] = code_of(d[k], R);
+                        flag |= (c[k] == 0u) | needs_fixup(xr[u][k], q[k], ebx2, ebf);
+                        if (BP && !emit && k < valid) {
+                            smin = min(smin, q[k]);
+                            smax = max(smax, q[k]);
+                            ssum += q[k];
+                        }
+                    }
+                    fmask |= flag ? (1u << u) : 0u;
+                    if (!emit) {
+                        const uint32_t c01 = c[0] | (c[1] << 16), c23 = c[2] | (c[3] << 16);
                         if (BP && b0 && u == 0) {
                             r0c01 = c01;
                             r0c23 = c23;
@@ -309,258 +356,243 @@ k_lorenzo_nd(const CompressArgs a) {
                             store4c(a.codes + boff + (uint64_t)u * nx, valid, vst, c01, c23);
                         }
                     }
+                }
+            }
+            // Rare path: exact masks of flagged rows; counts and stash entries
+            // (first walk) or direct canonical writes (second walk).
+            uint32_t rows = __reduce_or_sync(VSZ_FULL, valid ? fmask : 0u);
+            while (rows) {
+                const int u = __ffs(rows) - 1;
+                rows &= rows - 1;
+                const int ly = j * U + u;
+                const int4 dv = dh[u * 32];
+                int32_t d[4];
+                if (imode) {
+                    d[0] = dv.x; d[1] = dv.y; d[2] = dv.z; d[3] = dv.w;
                 } else {
+                    d[0] = __float2int_rn(__int_as_float(dv.x)); d[1] = __float2int_rn(__int_as_float(dv.y));
+                    d[2] = __float2int_rn(__int_as_float(dv.z)); d[3] = __float2int_rn(__int_as_float(dv.w));
+                }
+                const float4 v = ring_rd[(h * U + u) * 32];
+                const float xv[4] = {v.x, v.y, v.z, v.w};
+                uint32_t om = 0, fm = 0;
 #pragma unroll
-                    for (int u = 0; u < U; ++u) {
-                        const int ly = j * U + u;
-                        if (ly >= ylen) break;
-                        int32_t q[4];
+                for (int k = 0; k < 4; ++k) {
+                    om |= (code_of(d[k], R) == 0u ? 1u : 0u) << k;
+                    fm |= (needs_fixup(xv[k], prequant(xv[k], inv2eb), ebx2, ebf) ? 1u : 0u) << k;
+                }
+                om &= vmask;
+                fm &= vmask;
+                if (BP && !emit && b0 && u == 0 && first) om &= ~1u;  // the origin waits for P
+                const uint32_t co = __popc(om), cf = __popc(fm);
+                if (!emit) {
+                    cnt_out += co;
+                    cnt_fix += cf;
+                    const uint32_t cl = co + cf;
+                    uint32_t incl = cl;
 #pragma unroll
-                        for (int k = 0; k < 4; ++k) q[k] = prequant(xr[u][k], inv2eb);
-                        int32_t left = __shfl_up_sync(VSZ_FULL, q[3], 1);
-                        if (first) left = 0;
-                        int32_t d[4];
-                        d[0] = wsub(q[0], left);
-                        d[1] = wsub(q[1], q[0]);
-                        d[2] = wsub(q[2], q[1]);
-                        d[3] = wsub(q[3], q[2]);
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) {  // Dy
-                            const int32_t r1 = d[k];
-                            d[k] = wsub(r1, p1[k]);
-                            p1[k] = r1;
-                        }
-                        if (C::ZSMEM) {  // Dz
-                            int4& st = zs[ly * 32 + lane];
-                            const int4 pv = st;
-                            st = make_int4(d[0], d[1], d[2], d[3]);
-                            d[0] = wsub(d[0], pv.x); d[1] = wsub(d[1], pv.y);
-                            d[2] = wsub(d[2], pv.z); d[3] = wsub(d[3], pv.w);
-                        }
-                        if (u == 0 && b0 && first) {
-                            if (BP && !emit) qcorner = q[0];
-                            else d[0] = wsub(d[0], Pb);
-                        }
-                        dh[u * 32] = make_int4(d[0], d[1], d[2], d[3]);
-                        uint32_t c[4];
-                        bool flag = false;
+                    for (int off = 1; off < 32; off <<= 1) {
+                        const uint32_t y = __shfl_up_sync(VSZ_FULL, incl, off);
+                        if (lane >= off) incl += y;
+                    }
+                    uint32_t pos = nst + incl - cl;
+                    const uint32_t total = __shfl_sync(VSZ_FULL, incl, 31);
+                    if (nst + total <= (uint32_t)C::STASH) {
+                        const uint32_t row = (uint32_t)(lz * ylen + ly);
 #pragma unroll
                         for (int k = 0; k < 4; ++k) {
-                            c[k] = code_of(d[k], R);
-                            flag |= (c[k] == 0u) | needs_fixup(xr[u][k], q[k], ebx2, ebf);
-                            if (BP && !emit && k < valid) {
-                                smin = min(smin, q[k]);
-                                smax = max(smax, q[k]);
-                                ssum += q[k];
-                            }
-                        }
-                        fmask |= flag ? (1u << u) : 0u;
-                        if (!emit) {
-                            const uint32_t c01 = c[0] | (c[1] << 16), c23 = c[2] | (c[3] << 16);
-                            if (BP && b0 && u == 0) {
-                                r0c01 = c01;
-                                r0c23 = c23;
-                            } else {
-                                store4c(a.codes + boff + (uint64_t)u * nx, valid, vst, c01, c23);
-                            }
+                            if (om & (1u << k))
+                                stash[pos++] = make_uint2(stash_key(0, grp, row, lane * 4 + k), (uint32_t)d[k]);
+                            if (fm & (1u << k))
+                                stash[pos++] = make_uint2(stash_key(1, grp, row, lane * 4 + k), __float_as_uint(xv[k]));
                         }
                     }
-                }
-                // Rare path: exact masks of flagged rows; counts and stash entries
-                // (first walk) or direct canonical writes (second walk).
-                uint32_t rows = __reduce_or_sync(VSZ_FULL, valid ? fmask : 0u);
-                while (rows) {
-                    const int u = __ffs(rows) - 1;
-                    rows &= rows - 1;
-                    const int ly = j * U + u;
-                    const int4 dv = dh[u * 32];
-                    int32_t d[4];
-                    if (imode) {
-                        d[0] = dv.x; d[1] = dv.y; d[2] = dv.z; d[3] = dv.w;
-                    } else {
-                        d[0] = __float2int_rn(__int_as_float(dv.x)); d[1] = __float2int_rn(__int_as_float(dv.y));
-                        d[2] = __float2int_rn(__int_as_float(dv.z)); d[3] = __float2int_rn(__int_as_float(dv.w));
+                    nst += total;
+                } else {
+                    // ranks inside the block: earlier rows, then earlier lanes of this row
+                    uint32_t io = co, iff = cf;
+#pragma unroll
+                    for (int off = 1; off < G; off <<= 1) {
+                        const uint32_t yo = __shfl_up_sync(VSZ_FULL, io, off);
+                        const uint32_t yf = __shfl_up_sync(VSZ_FULL, iff, off);
+                        if (glane >= off) { io += yo; iff += yf; }
                     }
-                    const float4 v = ring_rd[(h * U + u) * 32];
-                    const float xv[4] = {v.x, v.y, v.z, v.w};
-                    uint32_t om = 0, fm = 0;
+                    uint64_t po = base_out + eo_g + run_o + (io - co);
+                    uint64_t pq = base_fix + ef_g + run_f + (iff - cf);
+                    const uint32_t idx0 = (uint32_t)(boff + (uint64_t)u * nx);
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
-                        om |= (code_of(d[k], R) == 0u ? 1u : 0u) << k;
-                        fm |= (needs_fixup(xv[k], prequant(xv[k], inv2eb), ebx2, ebf) ? 1u : 0u) << k;
+                        if (om & (1u << k)) {
+                            if (po < a.out_cap) a.stage_out[po] = make_uint2(idx0 + k, (uint32_t)d[k]);
+                            ++po;
+                        }
+                        if (fm & (1u << k)) {
+                            if (pq < a.fix_cap) a.stage_fix[pq] = make_uint2(idx0 + k, __float_as_uint(xv[k]));
+                            ++pq;
+                        }
                     }
-                    om &= vmask;
-                    fm &= vmask;
-                    if (BP && !emit && b0 && u == 0 && first) om &= ~1u;  // the origin waits for P
-                    const uint32_t co = __popc(om), cf = __popc(fm);
-                    if (!emit) {
-                        cnt_out += co;
-                        cnt_fix += cf;
-                        const uint32_t cl = co + cf;
-                        uint32_t incl = cl;
-#pragma unroll
-                        for (int off = 1; off < 32; off <<= 1) {
-                            const uint32_t y = __shfl_up_sync(VSZ_FULL, incl, off);
-                            if (lane >= off) incl += y;
-                        }
-                        uint32_t pos = nst + incl - cl;
-                        const uint32_t total = __shfl_sync(VSZ_FULL, incl, 31);
-                        if (nst + total <= (uint32_t)C::STASH) {
-                            const uint32_t row = (uint32_t)(lz * ylen + ly);
-#pragma unroll
-                            for (int k = 0; k < 4; ++k) {
-                                if (om & (1u << k))
-                                    stash[pos++] = make_uint2(stash_key(0, grp, row, lane * 4 + k), (uint32_t)d[k]);
-                                if (fm & (1u << k))
-                                    stash[pos++] = make_uint2(stash_key(1, grp, row, lane * 4 + k), __float_as_uint(xv[k]));
-                            }
-                        }
-                        nst += total;
-                    } else {
-                        // ranks inside the block: earlier rows, then earlier lanes of this row
-                        uint32_t io = co, iff = cf;
-#pragma unroll
-                        for (int off = 1; off < G; off <<= 1) {
-                            const uint32_t yo = __shfl_up_sync(VSZ_FULL, io, off);
-                            const uint32_t yf = __shfl_up_sync(VSZ_FULL, iff, off);
-                            if (glane >= off) { io += yo; iff += yf; }
-                        }
-                        uint64_t po = base_out + eo_g + run_o + (io - co);
-                        uint64_t pq = base_fix + ef_g + run_f + (iff - cf);
-                        const uint32_t idx0 = (uint32_t)(boff + (uint64_t)u * nx);
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            if (om & (1u << k)) {
-                                if (po < a.out_cap) a.stage_out[po] = make_uint2(idx0 + k, (uint32_t)d[k]);
-                                ++po;
-                            }
-                            if (fm & (1u << k)) {
-                                if (pq < a.fix_cap) a.stage_fix[pq] = make_uint2(idx0 + k, __float_as_uint(xv[k]));
-                                ++pq;
-                            }
-                        }
-                        run_o += __shfl_sync(VSZ_FULL, io, src + G - 1);
-                        run_f += __shfl_sync(VSZ_FULL, iff, src + G - 1);
-                    }
+                    run_o += __shfl_sync(VSZ_FULL, io, src + G - 1);
+                    run_f += __shfl_sync(VSZ_FULL, iff, src + G - 1);
                 }
-                h ^= 1;
-                lz = nlz;
-                j = nj;
             }
-            cp_async_wait<0>();
-            if (emit) break;
+            h ^= 1;
+            lz = nlz;
+            j = nj;
+        }
+        cp_async_wait<0>();
+        if (emit) break;
 
-            // Per-block padding value (Sec. IV-B-2) and the deferred block origin.
-            uint32_t corner_out = 0;
-            int32_t dcorner = 0;
-            if (BP) {
-                // fp32-mode extremes are exact integers; +-inf saturate to the identities
-                smin = min(smin, __float2int_rn(sminf));
-                smax = max(smax, __float2int_rn(smaxf));
-#pragma unroll
-                for (int off = 1; off < G; off <<= 1) {
-                    smin = min(smin, __shfl_xor_sync(VSZ_FULL, smin, off));
-                    smax = max(smax, __shfl_xor_sync(VSZ_FULL, smax, off));
-                    ssum += __shfl_xor_sync(VSZ_FULL, ssum, off);
-                }
-                const long long xlen = bexists ? (long long)umin64(B, nx - bx * B) : 1;
-                const long long m = (long long)zlen * ylen * xlen;
-                Pb = a.pad_mode == VSZ_PAD_BLOCK_MIN ? smin
-                   : a.pad_mode == VSZ_PAD_BLOCK_MAX ? smax
-                   : rounded_mean(ssum, m);
-                if (first && bexists) {
-                    a.pad[blk] = Pb;
-                    dcorner = wsub(qcorner, Pb);
-                    const uint32_t cc = code_of(dcorner, R);
-                    corner_out = (cc == 0u) ? 1u : 0u;
-                    cnt_out += corner_out;
-                    r0c01 = (r0c01 & 0xffff0000u) | cc;
-                }
-                store4c(a.codes + tile_base, valid, vst, r0c01, r0c23);
-            }
-
-            // Per-block counts, in-tile exclusive offsets (blk_off), tile totals.
-            uint32_t bo = cnt_out, bf = cnt_fix;
+        // Per-block padding value (Sec. IV-B-2) and the deferred block origin.
+        uint32_t corner_out = 0;
+        int32_t dcorner = 0;
+        if (BP) {
+            // fp32-mode extremes are exact integers; +-inf saturate to the identities
+            smin = min(smin, __float2int_rn(sminf));
+            smax = max(smax, __float2int_rn(smaxf));
 #pragma unroll
             for (int off = 1; off < G; off <<= 1) {
-                bo += __shfl_xor_sync(VSZ_FULL, bo, off);
-                bf += __shfl_xor_sync(VSZ_FULL, bf, off);
+                smin = min(smin, __shfl_xor_sync(VSZ_FULL, smin, off));
+                smax = max(smax, __shfl_xor_sync(VSZ_FULL, smax, off));
+                ssum += __shfl_xor_sync(VSZ_FULL, ssum, off);
             }
-            const uint32_t vo = (first && bexists) ? bo : 0u;
-            const uint32_t vf = (first && bexists) ? bf : 0u;
-            uint32_t io = vo, iff = vf;
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const uint32_t yo = __shfl_up_sync(VSZ_FULL, io, off);
-                const uint32_t yf = __shfl_up_sync(VSZ_FULL, iff, off);
-                if (lane >= off) { io += yo; iff += yf; }
+            const long long xlen = bexists ? (long long)umin64(B, nx - bx * B) : 1;
+            const long long m = (long long)zlen * ylen * xlen;
+            Pb = a.pad_mode == VSZ_PAD_BLOCK_MIN ? smin
+               : a.pad_mode == VSZ_PAD_BLOCK_MAX ? smax
+               : rounded_mean(ssum, m);
+            if (first && bexists) {
+                a.pad[blk] = Pb;
+                dcorner = wsub(qcorner, Pb);
+                const uint32_t cc = code_of(dcorner, R);
+                corner_out = (cc == 0u) ? 1u : 0u;
+                cnt_out += corner_out;
+                r0c01 = (r0c01 & 0xffff0000u) | cc;
             }
-            const uint32_t eo = io - vo, ef = iff - vf;
-            eo_g = __shfl_sync(VSZ_FULL, eo, src);
-            ef_g = __shfl_sync(VSZ_FULL, ef, src);
-            const uint32_t tot_out = __shfl_sync(VSZ_FULL, io, 31);
-            const uint32_t tot_fix = __shfl_sync(VSZ_FULL, iff, 31);
-            if (first && bexists) a.blk_off[blk] = eo;
-
-            if (tot_out | tot_fix) {
-                if (lane == 0) {
-                    if (tot_out) base_out = atomicAdd(&a.wsh->stage_out, (unsigned long long)tot_out);
-                    if (tot_fix) base_fix = atomicAdd(&a.wsh->stage_fix, (unsigned long long)tot_fix);
-                    uint4* ch = a.chunks + t / kTilesPerChunk;
-                    if (tot_out) atomicAdd(&ch->x, tot_out);
-                    if (tot_fix) atomicAdd(&ch->y, tot_fix);
-                }
-                base_out = __shfl_sync(VSZ_FULL, base_out, 0);
-                base_fix = __shfl_sync(VSZ_FULL, base_fix, 0);
-            }
-            if (lane == 0)
-                a.tiles[t] = make_uint4((uint32_t)base_out, tot_out, (uint32_t)base_fix, tot_fix);
-            if (!(tot_out | tot_fix)) break;
-            if (nst > (uint32_t)C::STASH) continue;  // stash overflow: second walk
-
-            // Counting sort of the stash into canonical order.
-            if (first) {
-                pre_out[grp] = (uint32_t)base_out + eo + corner_out;
-                pre_fix[grp] = (uint32_t)base_fix + ef;
-                if (BP && corner_out) {
-                    const uint64_t pos = base_out + eo;
-                    if (pos < a.out_cap) a.stage_out[pos] = make_uint2((uint32_t)tile_base, (uint32_t)dcorner);
-                }
-            }
-            run[lane] = 0;
-            run[lane + 32] = 0;
-            __syncwarp();
-            const uint64_t row_base = (ND == 3 ? bz * B * plane : 0) + by * B * nx + s * kSegCols;
-            for (uint32_t j0 = 0; j0 < nst; j0 += 32) {
-                const uint32_t jj = j0 + lane;
-                const bool act = jj < nst;
-                const uint2 e = act ? stash[jj] : make_uint2(0, 0);
-                const uint32_t bucket = act ? (e.x >> 26) : (64u + lane);
-                const uint32_t peers = __match_any_sync(VSZ_FULL, bucket);
-                const uint32_t rank = __popc(peers & lt);
-                uint32_t cnt0 = 0;
-                if (act) {
-                    const uint32_t isfix = e.x >> 31;
-                    const uint32_t gb = (e.x >> 26) & 31u;
-                    const uint32_t rowi = (e.x >> 7) & 0x7ffffu;
-                    const uint32_t col = e.x & 127u;
-                    cnt0 = run[bucket];
-                    const uint32_t lzr = rowi / (uint32_t)ylen, lyr = rowi % (uint32_t)ylen;
-                    const uint32_t idx = (uint32_t)(row_base + (uint64_t)lzr * plane + (uint64_t)lyr * nx + col);
-                    const uint64_t pos = (uint64_t)(isfix ? pre_fix[gb] : pre_out[gb]) + cnt0 + rank;
-                    if (isfix) {
-                        if (pos < a.fix_cap) a.stage_fix[pos] = make_uint2(idx, e.y);
-                    } else {
-                        if (pos < a.out_cap) a.stage_out[pos] = make_uint2(idx, e.y);
-                    }
-                }
-                __syncwarp();
-                if (act && (peers >> lane) == 1u) run[bucket] = cnt0 + rank + 1;  // last peer updates
-                __syncwarp();
-            }
-            break;
+            store4c(a.codes + tile_base, valid, vst, r0c01, r0c23);
         }
+
+        // Per-block counts, in-tile exclusive offsets (blk_off), tile totals.
+        uint32_t bo = cnt_out, bf = cnt_fix;
+#pragma unroll
+        for (int off = 1; off < G; off <<= 1) {
+            bo += __shfl_xor_sync(VSZ_FULL, bo, off);
+            bf += __shfl_xor_sync(VSZ_FULL, bf, off);
+        }
+        const uint32_t vo = (first && bexists) ? bo : 0u;
+        const uint32_t vf = (first && bexists) ? bf : 0u;
+        uint32_t io = vo, iff = vf;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t yo = __shfl_up_sync(VSZ_FULL, io, off);
+            const uint32_t yf = __shfl_up_sync(VSZ_FULL, iff, off);
+            if (lane >= off) { io += yo; iff += yf; }
+        }
+        const uint32_t eo = io - vo, ef = iff - vf;
+        eo_g = __shfl_sync(VSZ_FULL, eo, src);
+        ef_g = __shfl_sync(VSZ_FULL, ef, src);
+        const uint32_t tot_out = __shfl_sync(VSZ_FULL, io, 31);
+        const uint32_t tot_fix = __shfl_sync(VSZ_FULL, iff, 31);
+        if (first && bexists) a.blk_off[blk] = eo;
+
+        if (tot_out | tot_fix) {
+            if (lane == 0) {
+                if (tot_out) base_out = atomicAdd(&a.wsh->stage_out, (unsigned long long)tot_out);
+                if (tot_fix) base_fix = atomicAdd(&a.wsh->stage_fix, (unsigned long long)tot_fix);
+                uint4* ch = a.chunks + t / kTilesPerChunk;
+                if (tot_out) atomicAdd(&ch->x, tot_out);
+                if (tot_fix) atomicAdd(&ch->y, tot_fix);
+            }
+            base_out = __shfl_sync(VSZ_FULL, base_out, 0);
+            base_fix = __shfl_sync(VSZ_FULL, base_fix, 0);
+        }
+        if (lane == 0)
+            a.tiles[t] = make_uint4((uint32_t)base_out, tot_out, (uint32_t)base_fix, tot_fix);
+        if (!(tot_out | tot_fix)) break;
+        if (nst > (uint32_t)C::STASH) continue;  // stash overflow: second walk
+
+        // Counting sort of the stash into canonical order.
+        if (first) {
+            pre_out[grp] = (uint32_t)base_out + eo + corner_out;
+            pre_fix[grp] = (uint32_t)base_fix + ef;
+            if (BP && corner_out) {
+                const uint64_t pos = base_out + eo;
+                if (pos < a.out_cap) a.stage_out[pos] = make_uint2((uint32_t)tile_base, (uint32_t)dcorner);
+            }
+        }
+        run[lane] = 0;
+        run[lane + 32] = 0;
         __syncwarp();
+        const uint64_t row_base = (ND == 3 ? bz * B * plane : 0) + by * B * nx + s * kSegCols;
+        for (uint32_t j0 = 0; j0 < nst; j0 += 32) {
+            const uint32_t jj = j0 + lane;
+            const bool act = jj < nst;
+            const uint2 e = act ? stash[jj] : make_uint2(0, 0);
+            const uint32_t bucket = act ? (e.x >> 26) : (64u + lane);
+            const uint32_t peers = __match_any_sync(VSZ_FULL, bucket);
+            const uint32_t rank = __popc(peers & lt);
+            uint32_t cnt0 = 0;
+            if (act) {
+                const uint32_t isfix = e.x >> 31;
+                const uint32_t gb = (e.x >> 26) & 31u;
+                const uint32_t rowi = (e.x >> 7) & 0x7ffffu;
+                const uint32_t col = e.x & 127u;
+                cnt0 = run[bucket];
+                const uint32_t lzr = rowi / (uint32_t)ylen, lyr = rowi % (uint32_t)ylen;
+                const uint32_t idx = (uint32_t)(row_base + (uint64_t)lzr * plane + (uint64_t)lyr * nx + col);
+                const uint64_t pos = (uint64_t)(isfix ? pre_fix[gb] : pre_out[gb]) + cnt0 + rank;
+                if (isfix) {
+                    if (pos < a.fix_cap) a.stage_fix[pos] = make_uint2(idx, e.y);
+                } else {
+                    if (pos < a.out_cap) a.stage_out[pos] = make_uint2(idx, e.y);
+                }
+            }
+            __syncwarp();
+            if (act && (peers >> lane) == 1u) run[bucket] = cnt0 + rank + 1;  // last peer updates
+            __syncwarp();
+        }
+        break;
+    }
+    __syncwarp();
+}
+
+// One field: tiles handed out by the field's own ticket.
+template <int ND, int B, bool BP>
+__global__ void __launch_bounds__(NdCfg<ND, B>::THREADS, NdCfg<ND, B>::MINB_C)
+k_lorenzo_nd(const CompressArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    unsigned char* wsm = smem_raw + (size_t)(threadIdx.x >> 5) * NdCfg<ND, B>::WARP_C;
+    for (;;) {
+        unsigned long long tk = 0;
+        if (lane == 0) tk = atomicAdd(&a.wsh->ticket, 1ull);
+        const uint64_t t = __shfl_sync(VSZ_FULL, tk, 0);
+        if (t >= a.g.ntiles) break;
+        nd_compress_tile<ND, B, BP>(a, t, wsm, lane);
+    }
+}
+
+// Many fields of one class (rank, block edge, padding kind): one queue over
+// the tiles of all of them.  tile_prefix[f] is the first global tile of field
+// f, tile_prefix[nfields] the total.
+template <int ND, int B, bool BP>
+__global__ void __launch_bounds__(NdCfg<ND, B>::THREADS, NdCfg<ND, B>::MINB_C)
+k_lorenzo_nd_batch(const CompressArgs* __restrict__ fields, const uint64_t* __restrict__ tile_prefix, int nfields,
+                   unsigned long long* ticket) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    unsigned char* wsm = smem_raw + (size_t)(threadIdx.x >> 5) * NdCfg<ND, B>::WARP_C;
+    const uint64_t total = tile_prefix[nfields];
+    for (;;) {
+        unsigned long long tk = 0;
+        if (lane == 0) tk = atomicAdd(ticket, 1ull);
+        const uint64_t gt = __shfl_sync(VSZ_FULL, tk, 0);
+        if (gt >= total) break;
+        int lo = 0, hi = nfields - 1;  // last field whose first tile is <= gt
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (tile_prefix[mid] <= gt) lo = mid; else hi = mid - 1;
+        }
+        nd_compress_tile<ND, B, BP>(fields[lo], gt - tile_prefix[lo], wsm, lane);
     }
 }
 

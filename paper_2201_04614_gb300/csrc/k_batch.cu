@@ -1,0 +1,446 @@
+// k_batch.cu -- many fields compressed together (vsz_batch_*).
+//
+// A batch is planned once: every field's geometry and workspace region, its
+// class (rank, block edge, per-block padding or not), and device tables of
+// per-field descriptors and prefix sums of work items.  Submitting it runs a
+// fixed sequence of launches, whatever the number of fields:
+//   k_batch_begin         one CTA per field: workspace and header set-up;
+//   k_batch_range         value range of every relative-eb field, items of
+//                         1M elements; the last item of a field resolves eb;
+//   k_batch_qstats        min / max / sum of q of every global-padding field;
+//   k_lorenzo_*_batch     per class, one persistent kernel drawing tiles of
+//                         all the class's fields from one ticket;
+//   k_batch_compact_scan  one CTA per field: chunk offsets and totals;
+//   k_batch_compact_move  one CTA per chunk of any field: final placement.
+// The sequence can be captured into a CUDA graph once and replayed.
+#include <climits>
+#include <cstring>
+#include <map>
+#include <tuple>
+#include <vector>
+
+#include "common.cuh"
+#include "compact.cuh"
+#include "memops.cuh"
+#include "stats.cuh"
+#include "trace.cuh"
+
+namespace vsz {
+
+constexpr uint64_t kItemElems = 1ull << 20;  // elements per statistics work item
+constexpr int kMaxClasses = 28;               // tickets in the batch header
+
+struct BatchField {
+    CompressArgs a;     // the field's pointers, geometry and workspace
+    double eb;          // user error bound
+    int32_t rel;        // value-range relative bound
+    int32_t gpad;       // a global padding mode (needs the q statistics)
+};
+
+// Index of the last entry of prefix[0..n) that is <= v (prefix[0] == 0).
+__device__ __forceinline__ int find_field(const uint64_t* __restrict__ prefix, int n, uint64_t v) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= v) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256) k_batch_begin(const BatchField* __restrict__ F,
+                                                     unsigned long long* tickets) {
+    const BatchField& b = F[blockIdx.x];
+    const CompressArgs& a = b.a;
+    for (uint64_t i = threadIdx.x; i < a.g.nchunks; i += blockDim.x) a.chunks[i] = make_uint4(0, 0, 0, 0);
+    if (threadIdx.x == 0) {
+        WsHeader* w = a.wsh;
+        w->stage_out = 0;
+        w->stage_fix = 0;
+        w->qsum = 0;
+        w->xmin_ord = 0xffffffffu;
+        w->xmax_ord = 0u;
+        w->qmin = INT_MAX;
+        w->qmax = INT_MIN;
+        w->done0 = 0;
+        w->done1 = 0;
+        w->has_finite = 0;
+        w->ticket = 0;
+        vsz_header* h = const_cast<vsz_header*>(a.hdr);
+        h->pad_global = 0;
+        h->status = 0;
+        h->recon_status = 0;
+        h->reserved = 0;
+        h->n_out = 0;
+        h->n_fix = 0;
+        if (!b.rel) resolve_eb(h, b.eb, false, false, 0.0f, 0.0f);
+    }
+    if (blockIdx.x == 0 && threadIdx.x < kMaxClasses) tickets[threadIdx.x] = 0;
+}
+
+// Finite min/max of every relative-eb field; items of kItemElems elements.
+__global__ void __launch_bounds__(256) k_batch_range(const BatchField* __restrict__ F, int nf,
+                                                     const uint64_t* __restrict__ prefix, uint64_t nitems) {
+    __shared__ unsigned int smu[32];
+    __shared__ bool last;
+    for (uint64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
+        const int f = find_field(prefix, nf, item);
+        const BatchField& b = F[f];
+        const uint64_t n = b.a.g.n;
+        const uint64_t i0 = (item - prefix[f]) * kItemElems, i1 = umin64(n, i0 + kItemElems);
+        const float* x = b.a.x;
+        unsigned int lo = 0xffffffffu, hi = 0u;
+        if (b.a.vec) {
+            for (uint64_t i = i0 + 4 * threadIdx.x; i + 3 < i1; i += 4 * blockDim.x) {
+                const float4 v = ld_stream_f4(x + i);
+                const float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (isfinite(e[k])) { const unsigned u = float_to_ord(e[k]); lo = min(lo, u); hi = max(hi, u); }
+            }
+            for (uint64_t i = i0 + ((i1 - i0) & ~3ull) + threadIdx.x; i < i1; i += blockDim.x)
+                if (isfinite(x[i])) { const unsigned u = float_to_ord(x[i]); lo = min(lo, u); hi = max(hi, u); }
+        } else {
+            for (uint64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x)
+                if (isfinite(x[i])) { const unsigned u = float_to_ord(x[i]); lo = min(lo, u); hi = max(hi, u); }
+        }
+        lo = block_reduce(lo, OpMin(), smu, 0xffffffffu);
+        hi = block_reduce(hi, OpMax(), smu, 0u);
+        if (threadIdx.x == 0) {
+            WsHeader* w = b.a.wsh;
+            if (lo != 0xffffffffu) {
+                atomicMin(&w->xmin_ord, lo);
+                atomicMax(&w->xmax_ord, hi);
+            }
+            __threadfence();
+            last = atomicAdd(&w->done0, 1u) == (unsigned)(prefix[f + 1] - prefix[f] - 1);
+            if (last) {
+                __threadfence();
+                const unsigned l = atomicAdd(&w->xmin_ord, 0u);
+                const unsigned h = atomicAdd(&w->xmax_ord, 0u);
+                const bool has = l != 0xffffffffu;
+                resolve_eb(const_cast<vsz_header*>(b.a.hdr), b.eb, true, has, has ? ord_to_float(l) : 0.0f,
+                           has ? ord_to_float(h) : 0.0f);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Min / max / sum of q of every global-padding field; the last item of a
+// field sets its padding value.
+__global__ void __launch_bounds__(256) k_batch_qstats(const BatchField* __restrict__ F, int nf,
+                                                      const uint64_t* __restrict__ prefix, uint64_t nitems) {
+    __shared__ int smi[32];
+    __shared__ long long sml[32];
+    for (uint64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
+        const int f = find_field(prefix, nf, item);
+        const BatchField& b = F[f];
+        const uint64_t n = b.a.g.n;
+        const uint64_t i0 = (item - prefix[f]) * kItemElems, i1 = umin64(n, i0 + kItemElems);
+        const float* x = b.a.x;
+        const float inv2eb = b.a.hdr->inv2eb;
+        int qlo = INT_MAX, qhi = INT_MIN;
+        long long qs = 0;
+        for (uint64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+            const int q = prequant(x[i], inv2eb);
+            qlo = min(qlo, q); qhi = max(qhi, q); qs += q;
+        }
+        qlo = block_reduce(qlo, OpMin(), smi, INT_MAX);
+        qhi = block_reduce(qhi, OpMax(), smi, INT_MIN);
+        qs = block_reduce(qs, OpAdd(), sml, 0ll);
+        if (threadIdx.x == 0) {
+            WsHeader* w = b.a.wsh;
+            atomicMin(&w->qmin, qlo);
+            atomicMax(&w->qmax, qhi);
+            atomicAdd(&w->qsum, (unsigned long long)qs);
+            __threadfence();
+            if (atomicAdd(&w->done1, 1u) == (unsigned)(prefix[f + 1] - prefix[f] - 1)) {
+                __threadfence();
+                const int l = atomicAdd(&w->qmin, 0);
+                const int h = atomicAdd(&w->qmax, 0);
+                const long long S = (long long)atomicAdd(&w->qsum, 0ull);
+                int32_t P = 0;
+                if (n > 0) {
+                    const int m = b.a.pad_mode;
+                    P = m == VSZ_PAD_GLOBAL_MIN ? l : m == VSZ_PAD_GLOBAL_MAX ? h : rounded_mean(S, (long long)n);
+                }
+                const_cast<vsz_header*>(b.a.hdr)->pad_global = P;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_batch_compact_scan(const BatchField* __restrict__ F) {
+    const CompressArgs& a = F[blockIdx.x].a;
+    compact_scan_body(a.chunks, a.g.nchunks, const_cast<vsz_header*>(a.hdr), a.blk_off, a.g.nb, a.out_cap,
+                      a.fix_cap);
+}
+
+__global__ void __launch_bounds__(256) k_batch_compact_move(const BatchField* __restrict__ F, int nf,
+                                                            const uint64_t* __restrict__ prefix,
+                                                            uint64_t nchunks) {
+    for (uint64_t item = blockIdx.x; item < nchunks; item += gridDim.x) {
+        const int f = find_field(prefix, nf, item);
+        const CompressArgs& a = F[f].a;
+        compact_chunk_body(item - prefix[f], a.tiles, a.chunks, a.g.ntiles, a.g.nseg, a.g.nbx, a.g.bpt, a.blk_off,
+                           a.stage_out, a.stage_fix, a.out_idx, a.out_delta, a.out_cap, a.fix_idx, a.fix_bits,
+                           a.fix_cap);
+        __syncthreads();
+    }
+}
+
+}  // namespace vsz
+
+// ---------------------------------------------------------------------------
+// Host side.
+
+using namespace vsz;
+
+struct BatchClass {
+    int nd;
+    uint32_t b;
+    bool bp;
+    std::vector<int> fields;       // indices into the batch
+    CompressArgs* d_args = nullptr;
+    uint64_t* d_prefix = nullptr;
+    uint64_t total_tiles = 0;
+};
+
+struct vsz_batch_st {
+    int n = 0;
+    std::vector<vsz_field_job> jobs;
+    std::vector<BatchField> fields;
+    std::vector<BatchClass> classes;
+    BatchField* d_fields = nullptr;
+    uint64_t* d_range_prefix = nullptr;
+    uint64_t* d_q_prefix = nullptr;
+    uint64_t* d_chunk_prefix = nullptr;
+    uint64_t range_items = 0, q_items = 0, chunks = 0;
+    unsigned long long* tickets = nullptr;  // in the caller's workspace
+    bool use_graph = false;
+    cudaGraphExec_t exec = nullptr;
+};
+
+static size_t batch_layout(const vsz_field_job* jobs, int n, std::vector<size_t>* offs, std::vector<Geom>* geoms) {
+    size_t off = 256;  // batch header: class tickets
+    for (int i = 0; i < n; ++i) {
+        Geom g;
+        if (make_geom(&jobs[i].params, &g) != VSZ_OK) return 0;
+        const WsLayout L = ws_layout(g, jobs[i].out.out_cap, jobs[i].out.fix_cap);
+        if (offs) offs->push_back(off);
+        if (geoms) geoms->push_back(g);
+        off = align256(off + L.total);
+    }
+    return off;
+}
+
+static void free_batch(vsz_batch_st* b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    for (BatchClass& c : b->classes) {
+        if (c.d_args) cudaFree(c.d_args);
+        if (c.d_prefix) cudaFree(c.d_prefix);
+    }
+    if (b->d_fields) cudaFree(b->d_fields);
+    if (b->d_range_prefix) cudaFree(b->d_range_prefix);
+    if (b->d_q_prefix) cudaFree(b->d_q_prefix);
+    if (b->d_chunk_prefix) cudaFree(b->d_chunk_prefix);
+    delete b;
+}
+
+template <typename T>
+static cudaError_t upload(T** dst, const std::vector<T>& v) {
+    cudaError_t e = cudaMalloc((void**)dst, sizeof(T) * (v.empty() ? 1 : v.size()));
+    if (e != cudaSuccess) return e;
+    if (!v.empty()) e = cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
+    return e;
+}
+
+static vsz_status launch_sequence(vsz_batch_st* b, cudaStream_t s) {
+    cudaError_t e;
+    {
+        TraceScope ts("batch_begin", s);
+        k_batch_begin<<<b->n, 256, 0, s>>>(b->d_fields, b->tickets);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (b->range_items) {
+        TraceScope ts("batch_range", s);
+        const int grid = grid_for((const void*)k_batch_range, 256, 0, 1, b->range_items);
+        k_batch_range<<<grid, 256, 0, s>>>(b->d_fields, b->n, b->d_range_prefix, b->range_items);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
+    }
+    if (b->q_items) {
+        TraceScope ts("batch_qstats", s);
+        const int grid = grid_for((const void*)k_batch_qstats, 256, 0, 1, b->q_items);
+        k_batch_qstats<<<grid, 256, 0, s>>>(b->d_fields, b->n, b->d_q_prefix, b->q_items);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
+    }
+    for (size_t c = 0; c < b->classes.size(); ++c) {
+        BatchClass& k = b->classes[c];
+        if (!k.total_tiles) continue;
+        TraceScope ts("batch_lorenzo", s, k.nd, k.b);
+        e = k.nd == 1 ? launch_lorenzo_batch_1d(k.b, k.bp, k.d_args, k.d_prefix, (int)k.fields.size(), k.total_tiles,
+                                                b->tickets + c, s)
+          : k.nd == 2 ? launch_lorenzo_batch_2d(k.b, k.bp, k.d_args, k.d_prefix, (int)k.fields.size(), k.total_tiles,
+                                                b->tickets + c, s)
+                      : launch_lorenzo_batch_3d(k.b, k.bp, k.d_args, k.d_prefix, (int)k.fields.size(), k.total_tiles,
+                                                b->tickets + c, s);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    {
+        TraceScope ts("batch_compact_scan", s);
+        k_batch_compact_scan<<<b->n, 1024, 0, s>>>(b->d_fields);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
+    }
+    if (b->chunks) {
+        TraceScope ts("batch_compact_move", s);
+        const int grid = grid_for((const void*)k_batch_compact_move, 256, 0, 1, b->chunks);
+        k_batch_compact_move<<<grid, 256, 0, s>>>(b->d_fields, b->n, b->d_chunk_prefix, b->chunks);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
+    }
+    return VSZ_OK;
+}
+
+extern "C" {
+
+size_t vsz_batch_workspace_size(const vsz_field_job* jobs, int njobs) {
+    if (!jobs || njobs <= 0) return 0;
+    return batch_layout(jobs, njobs, nullptr, nullptr);
+}
+
+vsz_status vsz_batch_create(const vsz_field_job* jobs, int njobs, void* d_ws, size_t ws_bytes, int use_graph,
+                            vsz_batch* out) {
+    if (!jobs || njobs <= 0 || !out || !d_ws || !aligned(d_ws, 256)) return VSZ_ERR_INVALID_ARG;
+    *out = nullptr;
+    std::vector<size_t> offs;
+    std::vector<Geom> geoms;
+    for (int i = 0; i < njobs; ++i) {
+        Geom g;
+        vsz_status st = make_geom(&jobs[i].params, &g);
+        if (st != VSZ_OK) return st;
+        if ((st = check_compressed(g, &jobs[i].params, &jobs[i].out)) != VSZ_OK) return st;
+        if (g.n > 0 && !jobs[i].d_x) return VSZ_ERR_INVALID_ARG;
+    }
+    const size_t need = batch_layout(jobs, njobs, &offs, &geoms);
+    if (!need || ws_bytes < need) return VSZ_ERR_INVALID_ARG;
+
+    vsz_batch_st* b = new vsz_batch_st();
+    b->n = njobs;
+    b->jobs.assign(jobs, jobs + njobs);
+    b->use_graph = use_graph != 0;
+    char* ws = (char*)d_ws;
+    b->tickets = (unsigned long long*)ws;
+    std::vector<uint64_t> rp(1, 0), qp(1, 0), cp(1, 0);
+    std::map<std::tuple<int, uint32_t, bool>, int> cls;
+    for (int i = 0; i < njobs; ++i) {
+        const vsz_field_job& j = jobs[i];
+        const Geom& g = geoms[i];
+        const WsLayout L = ws_layout(g, j.out.out_cap, j.out.fix_cap);
+        char* fw = ws + offs[i];
+        BatchField bf;
+        std::memset(&bf, 0, sizeof bf);
+        CompressArgs& a = bf.a;
+        a.x = j.d_x;
+        a.codes = j.out.codes;
+        a.pad = j.out.pad;
+        a.blk_off = j.out.blk_off;
+        a.hdr = j.out.hdr;
+        a.wsh = (WsHeader*)fw;
+        a.tiles = (uint4*)(fw + L.tiles);
+        a.chunks = (uint4*)(fw + L.chunks);
+        a.stage_out = (uint2*)(fw + L.stage_out);
+        a.stage_fix = (uint2*)(fw + L.stage_fix);
+        a.out_idx = j.out.out_idx;
+        a.out_delta = j.out.out_delta;
+        a.fix_idx = j.out.fix_idx;
+        a.fix_bits = j.out.fix_bits;
+        a.out_cap = j.out.out_cap;
+        a.fix_cap = j.out.fix_cap;
+        a.g = g;
+        a.R = (int32_t)j.params.radius;
+        a.pad_mode = j.params.pad;
+        a.vec = (aligned(j.d_x, 16) && aligned(j.out.codes, 16) && (g.nd == 1 || g.nx % 4 == 0)) ? 1 : 0;
+        bf.eb = j.params.eb;
+        bf.rel = j.params.eb_mode == VSZ_EB_REL;
+        bf.gpad = j.params.pad == VSZ_PAD_GLOBAL_MIN || j.params.pad == VSZ_PAD_GLOBAL_MAX ||
+                  j.params.pad == VSZ_PAD_GLOBAL_AVG;
+        b->fields.push_back(bf);
+        const uint64_t items = (g.n + kItemElems - 1) / kItemElems;
+        rp.push_back(rp.back() + (bf.rel ? (items ? items : 1) : 0));
+        qp.push_back(qp.back() + (bf.gpad ? (items ? items : 1) : 0));
+        cp.push_back(cp.back() + g.nchunks);
+        const auto key = std::make_tuple(g.nd, g.b, is_block_pad(j.params.pad));
+        auto it = cls.find(key);
+        if (it == cls.end()) {
+            BatchClass c;
+            c.nd = g.nd;
+            c.b = g.b;
+            c.bp = is_block_pad(j.params.pad);
+            b->classes.push_back(c);
+            it = cls.emplace(key, (int)b->classes.size() - 1).first;
+        }
+        b->classes[it->second].fields.push_back(i);
+    }
+    if ((int)b->classes.size() > kMaxClasses) { free_batch(b); return VSZ_ERR_UNSUPPORTED; }
+    b->range_items = rp.back();
+    b->q_items = qp.back();
+    b->chunks = cp.back();
+    cudaError_t e = upload(&b->d_fields, b->fields);
+    if (e == cudaSuccess) e = upload(&b->d_range_prefix, rp);
+    if (e == cudaSuccess) e = upload(&b->d_q_prefix, qp);
+    if (e == cudaSuccess) e = upload(&b->d_chunk_prefix, cp);
+    for (BatchClass& c : b->classes) {
+        if (e != cudaSuccess) break;
+        std::vector<CompressArgs> args;
+        std::vector<uint64_t> pre(1, 0);
+        for (int i : c.fields) {
+            args.push_back(b->fields[i].a);
+            pre.push_back(pre.back() + b->fields[i].a.g.ntiles);
+        }
+        c.total_tiles = pre.back();
+        e = upload(&c.d_args, args);
+        if (e == cudaSuccess) e = upload(&c.d_prefix, pre);
+    }
+    if (e != cudaSuccess) {
+        free_batch(b);
+        return cuda_fail(e);
+    }
+    *out = b;
+    return VSZ_OK;
+}
+
+vsz_status vsz_batch_submit(vsz_batch b, void* stream) {
+    if (!b) return VSZ_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!b->use_graph || s == nullptr || s == cudaStreamLegacy || Tracer::get().on()) return launch_sequence(b, s);
+    if (!b->exec) {
+        cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(e);
+        const vsz_status st = launch_sequence(b, s);
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(s, &graph);
+        if (st != VSZ_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (e != cudaSuccess) return cuda_fail(e);
+        e = cudaGraphInstantiate(&b->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            b->exec = nullptr;
+            return cuda_fail(e);
+        }
+    }
+    const cudaError_t e = cudaGraphLaunch(b->exec, s);
+    return e == cudaSuccess ? VSZ_OK : cuda_fail(e);
+}
+
+vsz_status vsz_batch_destroy(vsz_batch b) {
+    if (!b) return VSZ_ERR_INVALID_ARG;
+    free_batch(b);
+    return VSZ_OK;
+}
+
+}  // extern "C"

@@ -4,30 +4,11 @@
 
 #include "common.cuh"
 #include "memops.cuh"
+#include "compact.cuh"
+#include "stats.cuh"
 #include "misc.cuh"
 
 namespace vsz {
-
-// ---------------------------------------------------------------------------
-// Error-bound resolution (Sec. II-B), on the device so that relative mode
-// needs no host round trip: eb_abs = eb, or eb * (max - min) over the finite
-// values (eb itself when that range is zero or empty); 1/(2 eb_abs) and
-// 2 eb_abs are formed in double and rounded once to float; the guard's bound
-// is eb_abs rounded toward zero.
-__device__ void resolve_eb(vsz_header* h, double eb, bool rel, bool has, float xmin, float xmax) {
-    double eb_abs = eb;
-    if (rel && has) {
-        const double range = __dsub_rn((double)xmax, (double)xmin);
-        if (range > 0.0) eb_abs = __dmul_rn(eb, range);
-    }
-    h->eb_abs = eb_abs;
-    h->inv2eb = __double2float_rn(__ddiv_rn(1.0, __dmul_rn(2.0, eb_abs)));
-    h->ebx2 = __double2float_rn(__dmul_rn(2.0, eb_abs));
-    h->eb_f32 = __double2float_rz(eb_abs);
-    h->has_range = has ? 1u : 0u;
-    h->xmin = has ? xmin : 0.0f;
-    h->xmax = has ? xmax : 0.0f;
-}
 
 __global__ void k_begin(WsHeader* wsh, uint4* chunks, uint64_t nchunks, vsz_header* hdr, double eb, int rel) {
     const uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -53,27 +34,6 @@ __global__ void k_begin(WsHeader* wsh, uint4* chunks, uint64_t nchunks, vsz_head
         if (!rel) resolve_eb(hdr, eb, false, false, 0.0f, 0.0f);
     }
 }
-
-// Block-wide reductions through shared memory (blockDim.x == 256).
-template <typename T, typename Op>
-__device__ __forceinline__ T block_reduce(T v, Op op, T* sm, T identity) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v = op(v, __shfl_xor_sync(VSZ_FULL, v, off));
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    __syncthreads();
-    if (l == 0) sm[w] = v;
-    __syncthreads();
-    if (w == 0) {
-        v = (l < (int)(blockDim.x >> 5)) ? sm[l] : identity;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) v = op(v, __shfl_xor_sync(VSZ_FULL, v, off));
-    }
-    return v;  // valid in warp 0
-}
-
-struct OpMin { template <class T> __device__ T operator()(T a, T b) const { return a < b ? a : b; } };
-struct OpMax { template <class T> __device__ T operator()(T a, T b) const { return a > b ? a : b; } };
-struct OpAdd { template <class T> __device__ T operator()(T a, T b) const { return a + b; } };
 
 // Finite min/max of x; the last block resolves the relative error bound.
 __global__ void __launch_bounds__(256) k_range(const float* __restrict__ x, uint64_t n, WsHeader* wsh,
@@ -176,113 +136,21 @@ __global__ void __launch_bounds__(256) k_qstats(const float* __restrict__ x, uin
     }
 }
 
-// ---------------------------------------------------------------------------
-// Compaction, part 1: exclusive scan of the per-chunk totals (one CTA).
+// Compaction of one field (bodies in compact.cuh).
 __global__ void __launch_bounds__(1024) k_compact_scan(uint4* chunks, uint64_t nchunks, vsz_header* hdr,
                                                        uint32_t* blk_off, uint64_t nb, uint64_t out_cap,
                                                        uint64_t fix_cap) {
-    __shared__ unsigned long long so[32], sf[32];
-    unsigned long long carry_o = 0, carry_f = 0;
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    for (uint64_t b0 = 0; b0 < nchunks; b0 += blockDim.x) {
-        const uint64_t i = b0 + threadIdx.x;
-        const uint4 c = i < nchunks ? chunks[i] : make_uint4(0, 0, 0, 0);
-        unsigned long long io = c.x, iff = c.y;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const unsigned long long yo = __shfl_up_sync(VSZ_FULL, io, off);
-            const unsigned long long yf = __shfl_up_sync(VSZ_FULL, iff, off);
-            if (l >= off) { io += yo; iff += yf; }
-        }
-        if (l == 31) { so[w] = io; sf[w] = iff; }
-        __syncthreads();
-        if (w == 0) {
-            unsigned long long vo = so[l], vf = sf[l];
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const unsigned long long yo = __shfl_up_sync(VSZ_FULL, vo, off);
-                const unsigned long long yf = __shfl_up_sync(VSZ_FULL, vf, off);
-                if (l >= off) { vo += yo; vf += yf; }
-            }
-            so[l] = vo;  // inclusive over warps
-            sf[l] = vf;
-        }
-        __syncthreads();
-        const unsigned long long wo = w ? so[w - 1] : 0ull, wf = w ? sf[w - 1] : 0ull;
-        if (i < nchunks) {
-            chunks[i].z = (uint32_t)(carry_o + wo + io - c.x);
-            chunks[i].w = (uint32_t)(carry_f + wf + iff - c.y);
-        }
-        carry_o += so[31];
-        carry_f += sf[31];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        hdr->n_out = carry_o;
-        hdr->n_fix = carry_f;
-        blk_off[nb] = (uint32_t)carry_o;
-        if (carry_o > out_cap || carry_f > fix_cap) hdr->status = VSZ_ERR_CAPACITY;
-    }
+    compact_scan_body(chunks, nchunks, hdr, blk_off, nb, out_cap, fix_cap);
 }
 
-// Compaction, part 2: per chunk of tiles (one CTA), the tiles' offsets, the blocks'
-// final offsets (in-tile prefix + tile offset) and the move of each tile's
-// staged entries to their canonical place.
 __global__ void __launch_bounds__(256) k_compact(const uint4* __restrict__ tiles, const uint4* __restrict__ chunks,
                                                  uint64_t ntiles, uint64_t nseg, uint64_t nbx, uint32_t bpt,
                                                  uint32_t* blk_off, const uint2* __restrict__ stage_out,
                                                  const uint2* __restrict__ stage_fix, uint32_t* out_idx,
                                                  int32_t* out_delta, uint64_t out_cap, uint32_t* fix_idx,
                                                  uint32_t* fix_bits, uint64_t fix_cap) {
-    __shared__ uint4 rec[kTilesPerChunk];
-    __shared__ uint32_t toff_o[kTilesPerChunk], toff_f[kTilesPerChunk];
-    const uint64_t t0 = (uint64_t)blockIdx.x * kTilesPerChunk;
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (w == 0) {  // the chunk's tile offsets: chunk offset + exclusive scan of the tile totals
-        uint32_t bo = chunks[blockIdx.x].z, bf = chunks[blockIdx.x].w;
-        for (int i0 = 0; i0 < kTilesPerChunk; i0 += 32) {
-            const uint64_t t = t0 + i0 + l;
-            const uint4 r = t < ntiles ? tiles[t] : make_uint4(0, 0, 0, 0);
-            uint32_t io = r.y, iff = r.w;
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const uint32_t yo = __shfl_up_sync(VSZ_FULL, io, off);
-                const uint32_t yf = __shfl_up_sync(VSZ_FULL, iff, off);
-                if (l >= off) { io += yo; iff += yf; }
-            }
-            rec[i0 + l] = r;
-            toff_o[i0 + l] = bo + io - r.y;
-            toff_f[i0 + l] = bf + iff - r.w;
-            bo += __shfl_sync(VSZ_FULL, io, 31);
-            bf += __shfl_sync(VSZ_FULL, iff, 31);
-        }
-    }
-    __syncthreads();
-
-    const int nt = (int)umin64(kTilesPerChunk, ntiles - t0);
-    for (int j = w; j < nt; j += 8) {
-        const uint64_t tt = t0 + j;
-        const uint4 rr = rec[j];
-        const uint32_t to = toff_o[j], tf = toff_f[j];
-        const uint64_t s = tt % nseg;
-        const uint64_t fb = (tt / nseg) * nbx + s * bpt;
-        const uint64_t nblk = umin64(bpt, nbx - s * bpt);
-        for (uint64_t k = l; k < nblk; k += 32) blk_off[fb + k] += to;
-        if (rr.y && (uint64_t)rr.x + rr.y <= out_cap && (uint64_t)to + rr.y <= out_cap) {
-            for (uint32_t k = l; k < rr.y; k += 32) {
-                const uint2 e = stage_out[rr.x + k];
-                out_idx[to + k] = e.x;
-                out_delta[to + k] = (int32_t)e.y;
-            }
-        }
-        if (rr.w && (uint64_t)rr.z + rr.w <= fix_cap && (uint64_t)tf + rr.w <= fix_cap) {
-            for (uint32_t k = l; k < rr.w; k += 32) {
-                const uint2 e = stage_fix[rr.z + k];
-                fix_idx[tf + k] = e.x;
-                fix_bits[tf + k] = e.y;
-            }
-        }
-    }
+    compact_chunk_body(blockIdx.x, tiles, chunks, ntiles, nseg, nbx, bpt, blk_off, stage_out, stage_fix, out_idx,
+                       out_delta, out_cap, fix_idx, fix_bits, fix_cap);
 }
 
 // Fixups restore their values verbatim after the inverse.

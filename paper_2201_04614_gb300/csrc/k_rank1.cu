@@ -84,12 +84,11 @@ struct Step1 {
     }
 };
 
+// All the work of one 4096-element tile t of a 1D field.
 template <int B, bool BP>
-__global__ void __launch_bounds__(256) k_lorenzo_1d(const CompressArgs a) {
+__device__ __forceinline__ void compress_1d_tile(const CompressArgs& a, uint64_t t, int lane) {
     using C = Cfg1<B>;
     constexpr int EPL = C::EPL, G = C::G, SPAN = C::SPAN;
-    const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
     const float inv2eb = a.hdr->inv2eb;
     const float ebx2 = a.hdr->ebx2;
     const float ebf = a.hdr->eb_f32;
@@ -97,118 +96,147 @@ __global__ void __launch_bounds__(256) k_lorenzo_1d(const CompressArgs a) {
     const int32_t R = a.R;
     const uint64_t n = a.g.n;
     const int glane = lane & (G - 1);
-    const uint32_t lt = lanemask_lt();
-
-    for (uint64_t t = (uint64_t)blockIdx.x * C::WARPS + wib; t < a.g.ntiles;
-         t += (uint64_t)gridDim.x * C::WARPS) {
-        const uint64_t start = t * kChunk1D;
-        uint32_t run_out = 0, run_fix = 0, stepmask = 0;
+    const uint64_t start = t * kChunk1D;
+    uint32_t run_out = 0, run_fix = 0, stepmask = 0;
 #pragma unroll 2
-        for (int st = 0; st < C::STEPS; ++st) {
-            const uint64_t s0 = start + (uint64_t)st * SPAN;
-            if (s0 >= n) break;
-            const uint64_t base = s0 + (uint64_t)lane * EPL;
-            Step1<B, BP> S;
-            S.run(a, base, lane, inv2eb, Pg);
-            uint32_t co = 0, cf = 0;
-            uint32_t c[EPL];
+    for (int st = 0; st < C::STEPS; ++st) {
+        const uint64_t s0 = start + (uint64_t)st * SPAN;
+        if (s0 >= n) break;
+        const uint64_t base = s0 + (uint64_t)lane * EPL;
+        Step1<B, BP> S;
+        S.run(a, base, lane, inv2eb, Pg);
+        uint32_t co = 0, cf = 0;
+        uint32_t c[EPL];
 #pragma unroll
-            for (int k = 0; k < EPL; ++k) {
-                c[k] = code_of(S.d[k], R);
-                if (k < S.valid) {
-                    co += (c[k] == 0u);
-                    cf += needs_fixup(S.x[k], S.q[k], ebx2, ebf) ? 1u : 0u;
-                }
+        for (int k = 0; k < EPL; ++k) {
+            c[k] = code_of(S.d[k], R);
+            if (k < S.valid) {
+                co += (c[k] == 0u);
+                cf += needs_fixup(S.x[k], S.q[k], ebx2, ebf) ? 1u : 0u;
             }
-            // in-step exclusive prefix of outliers -> per-block offsets
-            uint32_t io = co, iff = cf;
+        }
+        // in-step exclusive prefix of outliers -> per-block offsets
+        uint32_t io = co, iff = cf;
 #pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const uint32_t yo = __shfl_up_sync(VSZ_FULL, io, off);
-                const uint32_t yf = __shfl_up_sync(VSZ_FULL, iff, off);
-                if (lane >= off) { io += yo; iff += yf; }
-            }
-            const uint32_t so = __shfl_sync(VSZ_FULL, io, 31);
-            const uint32_t sf = __shfl_sync(VSZ_FULL, iff, 31);
-            if (glane == 0 && base < n) {
-                const uint64_t blk = base / B;
-                a.blk_off[blk] = run_out + (io - co);
-                if (BP) a.pad[blk] = S.P;
-            }
-            run_out += so;
-            run_fix += sf;
-            if (so | sf) stepmask |= 1u << st;
-            // codes
-            uint16_t* cp = a.codes + base;
-            if (a.vec && S.valid == EPL) {
-                if (EPL == 4) {
-                    *reinterpret_cast<uint2*>(cp) = make_uint2(c[0] | (c[1] << 16), c[2] | (c[3] << 16));
-                } else {
-                    *reinterpret_cast<uint4*>(cp) = make_uint4(c[0] | (c[1] << 16), c[2] | (c[3] << 16),
-                                                               c[4 % EPL] | (c[5 % EPL] << 16),
-                                                               c[6 % EPL] | (c[7 % EPL] << 16));
-                }
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t yo = __shfl_up_sync(VSZ_FULL, io, off);
+            const uint32_t yf = __shfl_up_sync(VSZ_FULL, iff, off);
+            if (lane >= off) { io += yo; iff += yf; }
+        }
+        const uint32_t so = __shfl_sync(VSZ_FULL, io, 31);
+        const uint32_t sf = __shfl_sync(VSZ_FULL, iff, 31);
+        if (glane == 0 && base < n) {
+            const uint64_t blk = base / B;
+            a.blk_off[blk] = run_out + (io - co);
+            if (BP) a.pad[blk] = S.P;
+        }
+        run_out += so;
+        run_fix += sf;
+        if (so | sf) stepmask |= 1u << st;
+        // codes
+        uint16_t* cp = a.codes + base;
+        if (a.vec && S.valid == EPL) {
+            if (EPL == 4) {
+                *reinterpret_cast<uint2*>(cp) = make_uint2(c[0] | (c[1] << 16), c[2] | (c[3] << 16));
             } else {
-#pragma unroll
-                for (int k = 0; k < EPL; ++k)
-                    if (k < S.valid) cp[k] = (uint16_t)c[k];
+                *reinterpret_cast<uint4*>(cp) = make_uint4(c[0] | (c[1] << 16), c[2] | (c[3] << 16),
+                                                           c[4 % EPL] | (c[5 % EPL] << 16),
+                                                           c[6 % EPL] | (c[7 % EPL] << 16));
             }
+        } else {
+#pragma unroll
+            for (int k = 0; k < EPL; ++k)
+                if (k < S.valid) cp[k] = (uint16_t)c[k];
         }
+    }
 
-        unsigned long long base_out = 0, base_fix = 0;
-        if (run_out | run_fix) {
-            if (lane == 0) {
-                if (run_out) base_out = atomicAdd(&a.wsh->stage_out, (unsigned long long)run_out);
-                if (run_fix) base_fix = atomicAdd(&a.wsh->stage_fix, (unsigned long long)run_fix);
-                uint4* ch = a.chunks + t / kTilesPerChunk;
-                if (run_out) atomicAdd(&ch->x, run_out);
-                if (run_fix) atomicAdd(&ch->y, run_fix);
-            }
-            base_out = __shfl_sync(VSZ_FULL, base_out, 0);
-            base_fix = __shfl_sync(VSZ_FULL, base_fix, 0);
+    unsigned long long base_out = 0, base_fix = 0;
+    if (run_out | run_fix) {
+        if (lane == 0) {
+            if (run_out) base_out = atomicAdd(&a.wsh->stage_out, (unsigned long long)run_out);
+            if (run_fix) base_fix = atomicAdd(&a.wsh->stage_fix, (unsigned long long)run_fix);
+            uint4* ch = a.chunks + t / kTilesPerChunk;
+            if (run_out) atomicAdd(&ch->x, run_out);
+            if (run_fix) atomicAdd(&ch->y, run_fix);
         }
-        if (lane == 0) a.tiles[t] = make_uint4((uint32_t)base_out, run_out, (uint32_t)base_fix, run_fix);
+        base_out = __shfl_sync(VSZ_FULL, base_out, 0);
+        base_fix = __shfl_sync(VSZ_FULL, base_fix, 0);
+    }
+    if (lane == 0) a.tiles[t] = make_uint4((uint32_t)base_out, run_out, (uint32_t)base_fix, run_fix);
 
-        // Emission in linear (= canonical) order, only for steps with entries.
-        uint64_t ko = base_out, kf = base_fix;
-        while (stepmask) {
-            const int st = __ffs(stepmask) - 1;
-            stepmask &= stepmask - 1;
-            const uint64_t base = start + (uint64_t)st * SPAN + (uint64_t)lane * EPL;
-            Step1<B, BP> S;
-            S.run(a, base, lane, inv2eb, Pg);
-            uint32_t mo = 0, mf = 0;  // per-element flags of this lane
+    // Emission in linear (= canonical) order, only for steps with entries.
+    uint64_t ko = base_out, kf = base_fix;
+    while (stepmask) {
+        const int st = __ffs(stepmask) - 1;
+        stepmask &= stepmask - 1;
+        const uint64_t base = start + (uint64_t)st * SPAN + (uint64_t)lane * EPL;
+        Step1<B, BP> S;
+        S.run(a, base, lane, inv2eb, Pg);
+        uint32_t mo = 0, mf = 0;  // per-element flags of this lane
 #pragma unroll
-            for (int k = 0; k < EPL; ++k) {
-                if (k < S.valid) {
-                    if (code_of(S.d[k], R) == 0u) mo |= 1u << k;
-                    if (needs_fixup(S.x[k], S.q[k], ebx2, ebf)) mf |= 1u << k;
-                }
+        for (int k = 0; k < EPL; ++k) {
+            if (k < S.valid) {
+                if (code_of(S.d[k], R) == 0u) mo |= 1u << k;
+                if (needs_fixup(S.x[k], S.q[k], ebx2, ebf)) mf |= 1u << k;
             }
-            uint32_t io = __popc(mo), iff = __popc(mf);
-            const uint32_t co = io, cf = iff;
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const uint32_t yo = __shfl_up_sync(VSZ_FULL, io, off);
-                const uint32_t yf = __shfl_up_sync(VSZ_FULL, iff, off);
-                if (lane >= off) { io += yo; iff += yf; }
-            }
-            uint64_t po = ko + (io - co), pf = kf + (iff - cf);
-#pragma unroll
-            for (int k = 0; k < EPL; ++k) {
-                if (mo & (1u << k)) {
-                    if (po < a.out_cap) a.stage_out[po] = make_uint2((uint32_t)(base + k), (uint32_t)S.d[k]);
-                    ++po;
-                }
-                if (mf & (1u << k)) {
-                    if (pf < a.fix_cap) a.stage_fix[pf] = make_uint2((uint32_t)(base + k), __float_as_uint(S.x[k]));
-                    ++pf;
-                }
-            }
-            ko += __shfl_sync(VSZ_FULL, io, 31);
-            kf += __shfl_sync(VSZ_FULL, iff, 31);
         }
-        (void)lt;
+        uint32_t io = __popc(mo), iff = __popc(mf);
+        const uint32_t co = io, cf = iff;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t yo = __shfl_up_sync(VSZ_FULL, io, off);
+            const uint32_t yf = __shfl_up_sync(VSZ_FULL, iff, off);
+            if (lane >= off) { io += yo; iff += yf; }
+        }
+        uint64_t po = ko + (io - co), pf = kf + (iff - cf);
+#pragma unroll
+        for (int k = 0; k < EPL; ++k) {
+            if (mo & (1u << k)) {
+                if (po < a.out_cap) a.stage_out[po] = make_uint2((uint32_t)(base + k), (uint32_t)S.d[k]);
+                ++po;
+            }
+            if (mf & (1u << k)) {
+                if (pf < a.fix_cap) a.stage_fix[pf] = make_uint2((uint32_t)(base + k), __float_as_uint(S.x[k]));
+                ++pf;
+            }
+        }
+        ko += __shfl_sync(VSZ_FULL, io, 31);
+        kf += __shfl_sync(VSZ_FULL, iff, 31);
+    }
+}
+
+// One field: tiles handed out by the field's own ticket.
+template <int B, bool BP>
+__global__ void __launch_bounds__(256) k_lorenzo_1d(const CompressArgs a) {
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned long long tk = 0;
+        if (lane == 0) tk = atomicAdd(&a.wsh->ticket, 1ull);
+        const uint64_t t = __shfl_sync(VSZ_FULL, tk, 0);
+        if (t >= a.g.ntiles) break;
+        compress_1d_tile<B, BP>(a, t, lane);
+    }
+}
+
+// Many 1D fields with the same block length and padding kind: one queue
+// over all their tiles (tile_prefix as for the 2D/3D batch kernel).
+template <int B, bool BP>
+__global__ void __launch_bounds__(256) k_lorenzo_1d_batch(const CompressArgs* __restrict__ fields,
+                                                          const uint64_t* __restrict__ tile_prefix, int nfields,
+                                                          unsigned long long* ticket) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t total = tile_prefix[nfields];
+    for (;;) {
+        unsigned long long tk = 0;
+        if (lane == 0) tk = atomicAdd(ticket, 1ull);
+        const uint64_t gt = __shfl_sync(VSZ_FULL, tk, 0);
+        if (gt >= total) break;
+        int lo = 0, hi = nfields - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (tile_prefix[mid] <= gt) lo = mid; else hi = mid - 1;
+        }
+        compress_1d_tile<B, BP>(fields[lo], gt - tile_prefix[lo], lane);
     }
 }
 
@@ -339,6 +367,16 @@ static cudaError_t launch_c1(const CompressArgs& a, cudaStream_t s) {
 }
 
 template <int B>
+static cudaError_t launch_c1_batch(bool bp, const CompressArgs* fields, const uint64_t* tile_prefix, int nfields,
+                                   uint64_t total_tiles, unsigned long long* ticket, cudaStream_t s) {
+    const void* k = bp ? (const void*)k_lorenzo_1d_batch<B, true> : (const void*)k_lorenzo_1d_batch<B, false>;
+    const int grid = grid_for(k, 256, 0, Cfg1<B>::WARPS, total_tiles);
+    if (bp) k_lorenzo_1d_batch<B, true><<<grid, 256, 0, s>>>(fields, tile_prefix, nfields, ticket);
+    else k_lorenzo_1d_batch<B, false><<<grid, 256, 0, s>>>(fields, tile_prefix, nfields, ticket);
+    return cudaGetLastError();
+}
+
+template <int B>
 static cudaError_t launch_r1(const ReconArgs& a, bool q_out, cudaStream_t s) {
     const uint64_t nsteps = (a.g.n + Cfg1<B>::SPAN - 1) / Cfg1<B>::SPAN;
     const void* k = q_out ? (const void*)k_recon_1d<B, true> : (const void*)k_recon_1d<B, false>;
@@ -357,6 +395,20 @@ cudaError_t launch_lorenzo_1d(const CompressArgs& a, cudaStream_t s) {
     case 64: return launch_c1<64>(a, s);
     case 128: return launch_c1<128>(a, s);
     case 256: return launch_c1<256>(a, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_lorenzo_batch_1d(uint32_t b, bool bp, const CompressArgs* fields, const uint64_t* tile_prefix,
+                                    int nfields, uint64_t total_tiles, unsigned long long* ticket, cudaStream_t s) {
+    switch (b) {
+    case 4: return launch_c1_batch<4>(bp, fields, tile_prefix, nfields, total_tiles, ticket, s);
+    case 8: return launch_c1_batch<8>(bp, fields, tile_prefix, nfields, total_tiles, ticket, s);
+    case 16: return launch_c1_batch<16>(bp, fields, tile_prefix, nfields, total_tiles, ticket, s);
+    case 32: return launch_c1_batch<32>(bp, fields, tile_prefix, nfields, total_tiles, ticket, s);
+    case 64: return launch_c1_batch<64>(bp, fields, tile_prefix, nfields, total_tiles, ticket, s);
+    case 128: return launch_c1_batch<128>(bp, fields, tile_prefix, nfields, total_tiles, ticket, s);
+    case 256: return launch_c1_batch<256>(bp, fields, tile_prefix, nfields, total_tiles, ticket, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -305,6 +305,19 @@ cudaError_t launch_nd_compress(const CompressArgs& a, cudaStream_t s) {
 }
 
 template <int ND, int B>
+cudaError_t launch_nd_compress_batch(bool bp, const CompressArgs* fields, const uint64_t* tile_prefix, int nfields,
+                                     uint64_t total_tiles, unsigned long long* ticket, cudaStream_t s) {
+    using C = NdCfg<ND, B>;
+    const void* k = bp ? (const void*)k_lorenzo_nd_batch<ND, B, true> : (const void*)k_lorenzo_nd_batch<ND, B, false>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM_C);
+    if (e != cudaSuccess) return e;
+    const int grid = grid_for(k, C::THREADS, C::SMEM_C, C::WARPS, total_tiles);
+    if (bp) k_lorenzo_nd_batch<ND, B, true><<<grid, C::THREADS, C::SMEM_C, s>>>(fields, tile_prefix, nfields, ticket);
+    else k_lorenzo_nd_batch<ND, B, false><<<grid, C::THREADS, C::SMEM_C, s>>>(fields, tile_prefix, nfields, ticket);
+    return cudaGetLastError();
+}
+
+template <int ND, int B>
 cudaError_t launch_nd_recon(const ReconArgs& a, bool q_out, cudaStream_t s) {
     using C = NdCfg<ND, B>;
     const void* k = q_out ? (const void*)k_recon_nd<ND, B, true> : (const void*)k_recon_nd<ND, B, false>;
