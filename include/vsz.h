@@ -277,6 +277,114 @@ VSZ_API vsz_status vsz_reconstruct_q(const vsz_params* p, const vsz_compressed* 
 VSZ_API vsz_status vsz_code_histogram(const vsz_params* p, const uint16_t* d_codes, uint32_t* d_hist,
                               void* stream);
 
+/* ------------------------------------------------------------------------ */
+/* Learned tuner of block size and padding mode.                            */
+/* ------------------------------------------------------------------------ */
+/*
+ * The paper picks the block size with a sampling autotuner (Sec. III-D,
+ * Sec. V-E) and compares padding values by hand (Sec. IV, Sec. V-H).  This
+ * library instead maps cheap sampled statistics of a field to a class
+ * (block size x padding mode) with a small MLP, trained on the GPU with the
+ * kernels below on labels from an exhaustive GPU sweep.  No call here
+ * changes any integer result of compression: a class is only a vsz_params.
+ *
+ * Classes: c = 3 * slot + padslot; padslot 0 zero, 1 global average,
+ * 2 block average (Sec. IV-B); block slots 1D {32, 64, 128, 256},
+ * 2D {8, 16, 32, 64}, 3D {8, 16, 32} (slot 3 not allowed in 3D).
+ */
+#define VSZ_TUNER_NFEAT 12
+#define VSZ_TUNER_NCLASS 12
+#define VSZ_TUNER_HIDDEN 64
+/* flat fp32 parameters: W1[64x12] b1[64] W2[64x64] b2[64] W3[12x64] b3[12], row-major */
+#define VSZ_TUNER_NPARAM 5772
+
+/* Bytes of workspace vsz_tuner_features needs (device, 16-byte aligned). */
+VSZ_API size_t vsz_tuner_features_workspace_size(void);
+
+/*
+ * The 12 tuner features of a field, from S = min(n, 32768) samples at
+ * linear indices (k * 2654435761) mod n: ndim one-hot (3); log10 n;
+ * log10(range / eb_abs); log1p(mean |forward difference| / eb_abs) along x,
+ * y, z (0 for absent axes); |mean| / range; std / range; the fraction of
+ * samples with |q| >= R (under zero padding a block origin's residual is
+ * q itself, Sec. IV-A); log2 R.  Statistics cover the finite samples; range
+ * is theirs; eb_abs = eb, or eb * range in relative mode (Sec. II-B).
+ * p->block and p->pad are ignored.
+ *   d_feat    [12] double (device) or NULL;  d_feat32  [12] float or NULL
+ */
+VSZ_API vsz_status vsz_tuner_features(const vsz_params* p, const float* d_x, double* d_feat, float* d_feat32,
+                                      void* d_ws, size_t ws_bytes, void* stream);
+
+/* Bytes of workspace vsz_tuner_sweep needs (0 if p is invalid). */
+VSZ_API size_t vsz_tuner_sweep_workspace_size(const vsz_params* p);
+
+/*
+ * Exhaustive sweep (the tuner's labels): compresses the field with every
+ * allowed class (counting outliers and fixups exactly, keeping no lists),
+ * takes the 2R-bin code histogram and writes the estimated size in bytes of
+ * each class, n * H / 8 + 8 n_out + 8 n_fix + 4 * (padding scalars), with H
+ * the Shannon entropy of the codes in bits per element (the Huffman stage
+ * that follows the quantization, Sec. II-B), to d_cost[c]; +inf for classes
+ * the rank does not allow.  p->block and p->pad are ignored.
+ *   d_cost    [12] double (device)
+ *   d_nout    [12] uint64 (device) or NULL: each class's outlier count
+ *             (UINT64_MAX for classes not allowed)
+ *   d_ws      workspace of vsz_tuner_sweep_workspace_size(p) bytes, 256-byte aligned
+ */
+VSZ_API vsz_status vsz_tuner_sweep(const vsz_params* p, const float* d_x, double* d_cost, uint64_t* d_nout,
+                                   void* d_ws, size_t ws_bytes, void* stream);
+
+/*
+ * Guard of a tuned class: the exact outlier counts of classes a and b on a
+ * fixed sample of the field (d_nout[0], d_nout[1], device uint64).  The
+ * sample is the whole field when n <= 2^20 or dims[0] < 4 E0; otherwise K =
+ * max(1, min(m0, floor(n / (50 r)))) regions (about 2% of the field) stacked
+ * along dims[0] into one field and compressed with the same eb, eb mode and
+ * R.  With L = 256 (1D), 64 (2D), 32 (3D): E0 = 65536 (1D) or L; region i
+ * starts along dims[0] at floor(i * m0 / K) * E0, m0 = floor(dims[0] / E0);
+ * a region is E0 values (1D), E0 rows (2D), or E0 planes of Ey = min(ny, L)
+ * rows starting at row floor(i * my / K) * Ey, my = max(1, floor(ny / L))
+ * (3D); r is a region's element count.  Regions are aligned to every
+ * class's blocks, so each sampled block is a block of the field.  In
+ * relative mode the error bound is relative to the sample's own range.
+ */
+VSZ_API size_t vsz_tuner_guard_workspace_size(const vsz_params* p, int class_a, int class_b);
+VSZ_API vsz_status vsz_tuner_guard(const vsz_params* p, const float* d_x, int class_a, int class_b,
+                                   uint64_t* d_nout, void* d_ws, size_t ws_bytes, void* stream);
+
+/* Dims of the guard's stacked sample (host, no GPU work): sub_dims[0..2]. */
+VSZ_API vsz_status vsz_tuner_guard_sample_dims(const vsz_params* p, uint64_t* sub_dims);
+
+/*
+ * MLP inference: for n samples X[n][12] (fp32, device) with allowed-class
+ * bit masks d_mask[n], the logits z = W3 relu(W2 relu(W1 xt + b1) + b2) + b3
+ * with xt = (x - mu) / sigma (d_norm = mu[12] then sigma[12]); masked
+ * classes get -inf.  d_logits [n][12] and/or d_class [n] (the most probable
+ * allowed class, ties to the lowest index) may be NULL.
+ */
+VSZ_API vsz_status vsz_mlp_forward(const float* d_theta, const float* d_norm, const float* d_X,
+                                   const uint32_t* d_mask, int n, float* d_logits, int32_t* d_class,
+                                   void* stream);
+
+/* Bytes of workspace vsz_mlp_grad needs for a minibatch of `batch` samples. */
+VSZ_API size_t vsz_mlp_grad_workspace_size(int batch);
+
+/*
+ * Mean masked-softmax cross-entropy over a minibatch and its gradient with
+ * respect to the flat parameters (backpropagation).  The minibatch is the
+ * samples d_idx[0..batch-1] (or 0..batch-1 when d_idx is NULL) of X / d_y /
+ * d_mask.  Writes d_grad[VSZ_TUNER_NPARAM] and, if non-NULL, *d_loss.
+ * Deterministic: every sum runs in a fixed order.
+ */
+VSZ_API vsz_status vsz_mlp_grad(const float* d_theta, const float* d_norm, const float* d_X, const int32_t* d_y,
+                                const uint32_t* d_mask, const int32_t* d_idx, int batch, float* d_grad,
+                                float* d_loss, void* d_ws, size_t ws_bytes, void* stream);
+
+/* One Adam step (Kingma & Ba, 2015) at step >= 1 on nparam parameters, with
+ * first and second moment buffers d_m, d_v (zero before step 1). */
+VSZ_API vsz_status vsz_mlp_adam(float* d_theta, const float* d_grad, float* d_m, float* d_v, int nparam,
+                                float lr, float beta1, float beta2, float eps, int step, void* stream);
+
 /* One traced kernel launch. */
 typedef struct {
     char     name[24];  /* kernel: begin, range, qstats, lorenzo, compact_scan, compact_move, recon, fixups, histogram */

@@ -72,7 +72,10 @@ EXPORTED = ["vsz_status_string", "vsz_last_cuda_error", "vsz_abi_version", "vsz_
             "vsz_outlier_compact", "vsz_compress", "vsz_reconstruct", "vsz_reconstruct_q",
             "vsz_code_histogram", "vsz_read_header", "vsz_trace_enable", "vsz_trace_read",
             "vsz_compress_noalloc", "vsz_batch_workspace_size", "vsz_batch_create", "vsz_batch_submit",
-            "vsz_batch_destroy"]
+            "vsz_batch_destroy", "vsz_tuner_features_workspace_size", "vsz_tuner_features",
+            "vsz_tuner_sweep_workspace_size", "vsz_tuner_sweep", "vsz_tuner_guard_workspace_size",
+            "vsz_tuner_guard", "vsz_tuner_guard_sample_dims", "vsz_mlp_forward", "vsz_mlp_grad_workspace_size",
+            "vsz_mlp_grad", "vsz_mlp_adam"]
 
 _lib = None
 
@@ -120,6 +123,8 @@ def lib():
     L.vsz_trace_enable.argtypes = [ctypes.c_int]
     L.vsz_trace_read.argtypes = [P(_CTrace), ctypes.c_int]
     for name in EXPORTED:
+        if name.startswith(("vsz_tuner", "vsz_mlp")):
+            continue  # bound by tuner.py
         if name not in ("vsz_status_string", "vsz_last_cuda_error", "vsz_abi_version",
                         "vsz_num_elems", "vsz_num_blocks", "vsz_workspace_size"):
             getattr(L, name).restype = ctypes.c_int
