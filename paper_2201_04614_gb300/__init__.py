@@ -89,8 +89,8 @@ def lib():
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.LIB_PATH
-    if not os.path.exists(path) or _build.is_stale():
+    path = os.environ.get("VSZ_LIBRARY") or _build.LIB_PATH  # a variant build (tile-shape experiments)
+    if path == _build.LIB_PATH and (not os.path.exists(path) or _build.is_stale()):
         _build.build()
     L = ctypes.CDLL(path)
     P = ctypes.POINTER

@@ -44,8 +44,8 @@ struct WsHeader {
     unsigned int xmin_ord, xmax_ord;  // order-preserving encodings of finite min/max
     int qmin, qmax;
     unsigned int done0, done1;     // last-block counters
-    unsigned int has_finite;
-    unsigned int pad_;
+    unsigned int nonfinite;        // a range pass met a NaN or Inf
+    unsigned int fp32_ok;          // every |x * inv2eb| < 2^20 and no NaN/Inf (relative mode only)
     unsigned long long ticket;     // dynamic tile scheduling of the compression kernel
 };
 static_assert(sizeof(WsHeader) <= 256, "ws header");

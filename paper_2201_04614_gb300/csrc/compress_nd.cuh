@@ -4,10 +4,10 @@
 // One warp owns one tile: a 128-column segment along x of one row of blocks
 // (2D: b rows; 3D: b*b rows, z outer, y inner).  Lane l owns columns
 // 4l..4l+3, so b/4 consecutive lanes cover one block along x.  Rows arrive in
-// batches of U = min(b, 8) rows of one plane, double-buffered in a
-// lane-private cp.async ring in shared memory (each lane copies and reads
-// only its own 16 bytes per row, so one cp.async group per batch is all the
-// synchronization needed).  Walking the rows in order, the first-order
+// batches of U = min(b, 4) rows of one plane through an NS-stage lane-private
+// cp.async ring in shared memory (each lane copies and reads only its own 16
+// bytes per row, so one cp.async group per batch is all the synchronization
+// needed; NS - 1 batches are in flight while one is processed).  Walking the rows in order, the first-order
 // Lorenzo residual is the mixed difference delta = Dz Dy Dx q, where a
 // difference at a block's low face is the identity: the neighbour outside
 // the block is the padding value P, which cancels everywhere except at the
@@ -17,11 +17,15 @@
 //   Dz: against the previous plane's Dy result at the same row, kept in
 //       lane-private shared memory (zeroed per tile).
 // Two exact arithmetic modes compute the same integers.  While every
-// |x * inv2eb| of a batch is below 2^20 (checked per batch; NaN fails the
-// check), rounding, differences, the code and the guard run on the fp32
+// |x * inv2eb| of a batch is below 2^20 (proved for the whole field by the
+// range pass of relative mode, else checked per batch; NaN fails both
+// checks), rounding, differences, the code and the guard run on the fp32
 // pipe: the rounded values are integers below 2^20 and every difference an
 // integer below 2^24, so each fp32 operation is exact.  Otherwise the tile
 // continues in int32 (wrapping) arithmetic, its carried state converted.
+// The fp32 mode stores every code raw (the low half of fl(d + R + 2^23),
+// which is d + R when |d| < R) and rewrites the codes of flagged rows that
+// hold an outlier.
 // Every input byte is read once from HBM and every code written once.
 //
 // The pass over a batch is branch-free: each row's residuals go to a
@@ -54,13 +58,19 @@
 #define VSZ_ND_WARPS 4
 #endif
 #ifndef VSZ_ND_MINB_C
-#define VSZ_ND_MINB_C 5
+#define VSZ_ND_MINB_C 4
 #endif
 #ifndef VSZ_ND_MINB_R
 #define VSZ_ND_MINB_R 7
 #endif
 #ifndef VSZ_ND_STASH
 #define VSZ_ND_STASH 256
+#endif
+#ifndef VSZ_ND_STAGES
+#define VSZ_ND_STAGES 2
+#endif
+#ifndef VSZ_ND_STAGES_R
+#define VSZ_ND_STAGES_R 4
 #endif
 
 namespace vsz {
@@ -76,17 +86,20 @@ struct NdCfg {
     static constexpr int MINB_C = ZSMEM && B >= 32 ? 2 : VSZ_ND_MINB_C;  // caps registers
     static constexpr int MINB_R = VSZ_ND_MINB_R;
     static constexpr int STASH = VSZ_ND_STASH;             // stash entries per warp
+    static constexpr size_t ZS_B = ZSMEM ? (size_t)B * 32 * 16 : 0;
+    // ring stages: the z state of 3D blocks of 32 leaves room for two
+    static constexpr int NS = ZS_B > 8192 ? 2 : VSZ_ND_STAGES;
+    static constexpr int NSR = ZS_B > 8192 ? 2 : VSZ_ND_STAGES_R;
     // per-warp shared memory, compression: ring | stash | tables | z state
-    static constexpr size_t RING_C = (size_t)2 * U * 32 * 16;
+    static constexpr size_t RING_C = (size_t)NS * U * 32 * 16;
     static constexpr size_t STASH_B = (size_t)STASH * 8;
     static constexpr size_t TAB_B = 128 * 4;
-    static constexpr size_t ZS_B = ZSMEM ? (size_t)B * 32 * 16 : 0;
     static constexpr size_t HIST_B = (size_t)U * 32 * 16;  // residuals of the current batch
     static constexpr size_t WARP_C = RING_C + STASH_B + TAB_B + ZS_B + HIST_B;
     static constexpr size_t SMEM_C = WARP_C * WARPS;
     // per-warp shared memory, reconstruction: ring of codes | z state | outliers of the tile
     static constexpr int OCAP = 256;
-    static constexpr size_t RING_R = (size_t)2 * U * 32 * 8;
+    static constexpr size_t RING_R = (size_t)NSR * U * 32 * 8;
     static constexpr size_t OC_B = (size_t)OCAP * 8;
     static constexpr size_t WARP_R = RING_R + ZS_B + OC_B;
     static constexpr size_t SMEM_R = WARP_R * WARPS;
@@ -137,6 +150,9 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
     // the fp32 mode needs the global padding value itself to be small
     const bool pg_small = BP || (Pg >= -(1 << 20) && Pg <= (1 << 20));
     const float Pgf = (float)(BP ? 0 : Pg);
+    // a range pass that proved every |x * inv2eb| < 2^20 (and no NaN/Inf)
+    // lets the fp32 mode skip its per-batch check
+    const bool fast = pg_small && a.wsh->fp32_ok != 0u;
 
     const uint64_t s = t % g.nseg;
     const uint64_t rb = t / g.nseg;
@@ -155,6 +171,8 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
     const uint64_t blk = (bz * g.nby + by) * g.nbx + bx;
     const uint64_t tile_base = (ND == 3 ? bz * B * plane : 0) + by * B * nx + x0;
     const float* xsrc = a.x;
+    // interior tile: every lane holds 4 columns, b rows and (3D) b planes
+    const bool interior = vec && s * kSegCols + kSegCols <= nx && ylen == B && (ND == 2 || zlen == B);
 
     // copy the rows of batch (lz, j) into ring half h
     auto issue_batch = [&](int lz, int j, int h) {
@@ -188,6 +206,101 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
     float sminf = __int_as_float(0x7f800000), smaxf = -__int_as_float(0x7f800000);
     long long ssum = 0;
 
+    // Rare path of one batch: exact masks of the flagged rows; counts and
+    // stash entries (first walk) or direct canonical writes (second walk).
+    // Rows of a batch stored raw by the fp32 mode get their outliers' codes
+    // zeroed here.
+    uint32_t run_o = 0, run_f = 0;  // running ranks inside this lane's block (second walk)
+    auto rare_rows = [&](uint32_t rows, int h, uint64_t boff, int j, int lz, bool b0, bool imode, bool raw,
+                         bool emit) {
+        while (rows) {
+            const int u = __ffs(rows) - 1;
+            rows &= rows - 1;
+            const int ly = j * U + u;
+            const int4 dv = dh[u * 32];
+            int32_t d[4];
+            if (imode) {
+                d[0] = dv.x; d[1] = dv.y; d[2] = dv.z; d[3] = dv.w;
+            } else {
+                d[0] = __float2int_rn(__int_as_float(dv.x)); d[1] = __float2int_rn(__int_as_float(dv.y));
+                d[2] = __float2int_rn(__int_as_float(dv.z)); d[3] = __float2int_rn(__int_as_float(dv.w));
+            }
+            const float4 v = ring_rd[(h * U + u) * 32];
+            const float xv[4] = {v.x, v.y, v.z, v.w};
+            uint32_t om = 0, fm = 0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                om |= (code_of(d[k], R) == 0u ? 1u : 0u) << k;
+                fm |= (needs_fixup(xv[k], prequant(xv[k], inv2eb), ebx2, ebf) ? 1u : 0u) << k;
+            }
+            om &= vmask;
+            fm &= vmask;
+            if (raw && om) {  // fp32 mode stored raw codes: zero the outliers' codes
+                uint32_t c[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) c[k] = ((om >> k) & 1u) ? 0u : ((uint32_t)(d[k] + R) & 0xffffu);
+                const uint32_t c01 = c[0] | (c[1] << 16), c23 = c[2] | (c[3] << 16);
+                if (BP && b0 && u == 0) {
+                    r0c01 = c01;
+                    r0c23 = c23;
+                } else {
+                    store4c(a.codes + boff + (uint64_t)u * nx, valid, vst, c01, c23);
+                }
+            }
+            if (BP && !emit && b0 && u == 0 && first) om &= ~1u;  // the origin waits for P
+            const uint32_t co = __popc(om), cf = __popc(fm);
+            if (!emit) {
+                cnt_out += co;
+                cnt_fix += cf;
+                const uint32_t cl = co + cf;
+                uint32_t incl = cl;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const uint32_t y = __shfl_up_sync(VSZ_FULL, incl, off);
+                    if (lane >= off) incl += y;
+                }
+                uint32_t pos = nst + incl - cl;
+                const uint32_t total = __shfl_sync(VSZ_FULL, incl, 31);
+                if (nst + total <= (uint32_t)C::STASH) {
+                    const uint32_t row = (uint32_t)(lz * ylen + ly);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        if (om & (1u << k))
+                            stash[pos++] = make_uint2(stash_key(0, grp, row, lane * 4 + k), (uint32_t)d[k]);
+                        if (fm & (1u << k))
+                            stash[pos++] = make_uint2(stash_key(1, grp, row, lane * 4 + k), __float_as_uint(xv[k]));
+                    }
+                }
+                nst += total;
+            } else {
+                // ranks inside the block: earlier rows, then earlier lanes of this row
+                uint32_t io = co, iff = cf;
+#pragma unroll
+                for (int off = 1; off < G; off <<= 1) {
+                    const uint32_t yo = __shfl_up_sync(VSZ_FULL, io, off);
+                    const uint32_t yf = __shfl_up_sync(VSZ_FULL, iff, off);
+                    if (glane >= off) { io += yo; iff += yf; }
+                }
+                uint64_t po = base_out + eo_g + run_o + (io - co);
+                uint64_t pq = base_fix + ef_g + run_f + (iff - cf);
+                const uint32_t idx0 = (uint32_t)(boff + (uint64_t)u * nx);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    if (om & (1u << k)) {
+                        if (po < a.out_cap) a.stage_out[po] = make_uint2(idx0 + k, (uint32_t)d[k]);
+                        ++po;
+                    }
+                    if (fm & (1u << k)) {
+                        if (pq < a.fix_cap) a.stage_fix[pq] = make_uint2(idx0 + k, __float_as_uint(xv[k]));
+                        ++pq;
+                    }
+                }
+                run_o += __shfl_sync(VSZ_FULL, io, src + G - 1);
+                run_f += __shfl_sync(VSZ_FULL, iff, src + G - 1);
+            }
+        }
+    };
+
     for (int pass = 0; pass < 2; ++pass) {
         const bool emit = pass == 1;  // second walk: write entries, no codes
         // carried state: fp32 mode uses pf / float bits in zs, int mode p1 / ints in zs
@@ -196,16 +309,130 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
         if (C::ZSMEM)
             for (int ly = 0; ly < ylen; ++ly) zs[ly * 32 + lane] = make_int4(0, 0, 0, 0);
         bool imode = emit || !pg_small;
-        uint32_t run_o = 0, run_f = 0;  // running ranks inside this lane's block (second walk)
+        run_o = 0;
+        run_f = 0;
 
-        issue_batch(0, 0, 0);
-        int lz = 0, j = 0, h = 0;
+        if (!emit && fast && interior) {
+            // Lean first walk of an interior tile in fp32 mode: compile-time
+            // trip counts, 32-bit offsets, no per-row bounds or mode checks.
+            constexpr int BPP = B / U;                       // batches per plane
+            constexpr int NB = (ND == 3 ? B : 1) * BPP;      // batches per tile
+            const uint32_t nx32 = (uint32_t)nx, pl32 = (uint32_t)plane;
+            const float* xl = a.x + tile_base;
+            uint16_t* cl = a.codes + tile_base;
+            auto off32 = [&](int kb) -> uint32_t {
+                return (uint32_t)(kb / BPP) * pl32 + (uint32_t)((kb % BPP) * U) * nx32;
+            };
+            auto issue_fast = [&](int kb, int st) {
+                const float* src0 = xl + off32(kb);
+                const uint32_t dst0 = ring_wr + (uint32_t)(st * U * 32 * 16);
+#pragma unroll
+                for (int u = 0; u < U; ++u) cp_async16(dst0 + u * 32 * 16, src0 + (uint32_t)u * nx32, 16u);
+                cp_async_commit();
+            };
+#pragma unroll
+            for (int st = 0; st < C::NS - 1; ++st) {
+                if (st < NB) issue_fast(st, st);
+                else cp_async_commit();
+            }
+            // the padding value only enters at the tile's origin: preload it
+            // into the carried difference state (3D: plane state of row 0;
+            // 2D: row state)
+            if (!BP && first) {
+                if (ND == 3) zs[lane] = make_int4(__float_as_int(Pgf), 0, 0, 0);
+                else pf[0] = Pgf;
+            }
+            int h = 0;
+            for (int kb = 0; kb < NB; ++kb) {
+                const int jb = kb % BPP;
+                if (kb + C::NS - 1 < NB) issue_fast(kb + C::NS - 1, (kb + C::NS - 1) % C::NS);
+                else cp_async_commit();
+                cp_async_wait<C::NS - 1>();
+                if (ND == 3 && jb == 0) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) pf[k] = 0.f;
+                }
+                const float4* rr = ring_rd + h * U * 32;
+                uint16_t* crow = cl + off32(kb);
+                int4* zrow = zs + jb * U * 32 + lane;
+                uint32_t fmask = 0;
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const float4 v = rr[u * 32];
+                    const float xv[4] = {v.x, v.y, v.z, v.w};
+                    float rp[4], d[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) rp[k] = __fsub_rn(__fadd_rn(__fmul_rn(xv[k], inv2eb), kMagic), kMagic);
+                    float left = __shfl_up_sync(VSZ_FULL, rp[3], 1);
+                    if (first) left = 0.f;
+                    d[0] = __fsub_rn(rp[0], left);
+                    d[1] = __fsub_rn(rp[1], rp[0]);
+                    d[2] = __fsub_rn(rp[2], rp[1]);
+                    d[3] = __fsub_rn(rp[3], rp[2]);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {  // Dy
+                        const float r1 = d[k];
+                        d[k] = __fsub_rn(r1, pf[k]);
+                        pf[k] = r1;
+                    }
+                    if (ND == 3) {  // Dz
+                        const int4 pv = zrow[u * 32];
+                        zrow[u * 32] = make_int4(__float_as_int(d[0]), __float_as_int(d[1]), __float_as_int(d[2]),
+                                                 __float_as_int(d[3]));
+                        d[0] = __fsub_rn(d[0], __int_as_float(pv.x)); d[1] = __fsub_rn(d[1], __int_as_float(pv.y));
+                        d[2] = __fsub_rn(d[2], __int_as_float(pv.z)); d[3] = __fsub_rn(d[3], __int_as_float(pv.w));
+                    }
+                    dh[u * 32] = make_int4(__float_as_int(d[0]), __float_as_int(d[1]), __float_as_int(d[2]),
+                                           __float_as_int(d[3]));
+                    uint32_t cb[4];
+                    bool flag = false;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        cb[k] = __float_as_uint(__fadd_rn(d[k], RB));
+                        const float xh = __fmul_rn(rp[k], ebx2);
+                        flag |= !(fabsf(d[k]) < Rf) | !(fabsf(__fsub_rn(xv[k], xh)) <= ebf);
+                    }
+                    if (BP) {
+                        sminf = fminf(sminf, fminf(fminf(rp[0], rp[1]), fminf(rp[2], rp[3])));
+                        smaxf = fmaxf(smaxf, fmaxf(fmaxf(rp[0], rp[1]), fmaxf(rp[2], rp[3])));
+                        ssum += __float2int_rn(__fadd_rn(__fadd_rn(__fadd_rn(rp[0], rp[1]), rp[2]), rp[3]));
+                    }
+                    fmask |= flag ? (1u << u) : 0u;
+                    const uint32_t c01 = __byte_perm(cb[0], cb[1], 0x5410), c23 = __byte_perm(cb[2], cb[3], 0x5410);
+                    if (BP && u == 0 && kb == 0) {
+                        r0c01 = c01;
+                        r0c23 = c23;
+                    }
+                    *reinterpret_cast<uint2*>(crow + (uint32_t)u * nx32) = make_uint2(c01, c23);
+                }
+                if (BP && kb == 0) qcorner = __float2int_rn(__int_as_float(dh[0].x));
+                const uint32_t rows = __reduce_or_sync(VSZ_FULL, fmask);
+                if (rows) rare_rows(rows, h, tile_base + off32(kb), jb, kb / BPP, kb == 0, false, true, false);
+                h = h + 1 == C::NS ? 0 : h + 1;
+            }
+        } else {
+        // NS-stage ring: batches kb+1 .. kb+NS-1 are in flight while batch kb is processed
+        int ilz = 0, ij = 0;  // next batch to issue
+#pragma unroll
+        for (int st = 0; st < C::NS - 1; ++st) {
+            if (st < nbatch) {
+                issue_batch(ilz, ij, st);
+                if (++ij == nbpp) { ij = 0; ++ilz; }
+            } else {
+                cp_async_commit();
+            }
+        }
+        int lz = 0, j = 0, h = 0, hi = C::NS - 1;
         for (int kb = 0; kb < nbatch; ++kb) {
             int nj = j + 1, nlz = lz;
             if (nj == nbpp) { nj = 0; ++nlz; }
-            if (kb + 1 < nbatch) issue_batch(nlz, nj, h ^ 1);
-            else cp_async_commit();
-            cp_async_wait<1>();
+            if (kb + C::NS - 1 < nbatch) {
+                issue_batch(ilz, ij, hi);
+                if (++ij == nbpp) { ij = 0; ++ilz; }
+            } else {
+                cp_async_commit();
+            }
+            cp_async_wait<C::NS - 1>();
             if (j == 0) {
 #pragma unroll
                 for (int k = 0; k < 4; ++k) { pf[k] = 0.f; p1[k] = 0; }
@@ -213,18 +440,26 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
             const uint64_t boff = tile_base + (uint64_t)lz * plane + (uint64_t)(j * U) * nx;
             const bool b0 = kb == 0;
             float xr[U][4], pr[U][4];
-            bool unsafe = false;
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const float4 v = (j * U + u < ylen) ? ring_rd[(h * U + u) * 32] : make_float4(0.f, 0.f, 0.f, 0.f);
                 xr[u][0] = v.x; xr[u][1] = v.y; xr[u][2] = v.z; xr[u][3] = v.w;
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    pr[u][k] = __fmul_rn(xr[u][k], inv2eb);
-                    unsafe |= !(fabsf(pr[u][k]) < kSafe);
-                }
+                for (int k = 0; k < 4; ++k) pr[u][k] = __fmul_rn(xr[u][k], inv2eb);
             }
-            if (!imode && __any_sync(VSZ_FULL, unsafe)) {
+            bool unsafe = false;
+            if (!imode && !fast) {
+                // |p0|+|p1|+|p2|+|p3| < 2^20 bounds every |p| (NaN fails it)
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const float sa = __fadd_rn(__fadd_rn(fabsf(pr[u][0]), fabsf(pr[u][1])),
+                                               __fadd_rn(fabsf(pr[u][2]), fabsf(pr[u][3])));
+                    unsafe |= !(sa < kSafe);
+                }
+                unsafe = __any_sync(VSZ_FULL, unsafe);
+            }
+            const bool raw = !imode && !unsafe;  // codes of this batch stored raw, outliers fixed below
+            if (unsafe) {
                 // switch this tile to int32 arithmetic; the carried state is exact
                 imode = true;
 #pragma unroll
@@ -271,14 +506,15 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
                         else d[0] = __fsub_rn(d[0], Pgf);
                     }
                     dh[u * 32] = make_int4(__float_as_int(d[0]), __float_as_int(d[1]), __float_as_int(d[2]), __float_as_int(d[3]));
+                    // raw codes: the low 16 bits of fl(d + R + 2^23) are d + R
+                    // whenever |d| < R; outlier rows are rewritten below
                     uint32_t cb[4];
                     bool flag = false;
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
-                        const bool ok = fabsf(d[k]) < Rf;
-                        cb[k] = ok ? __float_as_uint(__fadd_rn(d[k], RB)) : 0u;
+                        cb[k] = __float_as_uint(__fadd_rn(d[k], RB));
                         const float xh = __fmul_rn(rp[k], ebx2);
-                        flag |= !ok | !(fabsf(__fsub_rn(xr[u][k], xh)) <= ebf);
+                        flag |= !(fabsf(d[k]) < Rf) | !(fabsf(__fsub_rn(xr[u][k], xh)) <= ebf);
                     }
                     if (BP) {
                         float rs = 0.f;
@@ -358,86 +594,14 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
                     }
                 }
             }
-            // Rare path: exact masks of flagged rows; counts and stash entries
-            // (first walk) or direct canonical writes (second walk).
-            uint32_t rows = __reduce_or_sync(VSZ_FULL, valid ? fmask : 0u);
-            while (rows) {
-                const int u = __ffs(rows) - 1;
-                rows &= rows - 1;
-                const int ly = j * U + u;
-                const int4 dv = dh[u * 32];
-                int32_t d[4];
-                if (imode) {
-                    d[0] = dv.x; d[1] = dv.y; d[2] = dv.z; d[3] = dv.w;
-                } else {
-                    d[0] = __float2int_rn(__int_as_float(dv.x)); d[1] = __float2int_rn(__int_as_float(dv.y));
-                    d[2] = __float2int_rn(__int_as_float(dv.z)); d[3] = __float2int_rn(__int_as_float(dv.w));
-                }
-                const float4 v = ring_rd[(h * U + u) * 32];
-                const float xv[4] = {v.x, v.y, v.z, v.w};
-                uint32_t om = 0, fm = 0;
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    om |= (code_of(d[k], R) == 0u ? 1u : 0u) << k;
-                    fm |= (needs_fixup(xv[k], prequant(xv[k], inv2eb), ebx2, ebf) ? 1u : 0u) << k;
-                }
-                om &= vmask;
-                fm &= vmask;
-                if (BP && !emit && b0 && u == 0 && first) om &= ~1u;  // the origin waits for P
-                const uint32_t co = __popc(om), cf = __popc(fm);
-                if (!emit) {
-                    cnt_out += co;
-                    cnt_fix += cf;
-                    const uint32_t cl = co + cf;
-                    uint32_t incl = cl;
-#pragma unroll
-                    for (int off = 1; off < 32; off <<= 1) {
-                        const uint32_t y = __shfl_up_sync(VSZ_FULL, incl, off);
-                        if (lane >= off) incl += y;
-                    }
-                    uint32_t pos = nst + incl - cl;
-                    const uint32_t total = __shfl_sync(VSZ_FULL, incl, 31);
-                    if (nst + total <= (uint32_t)C::STASH) {
-                        const uint32_t row = (uint32_t)(lz * ylen + ly);
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            if (om & (1u << k))
-                                stash[pos++] = make_uint2(stash_key(0, grp, row, lane * 4 + k), (uint32_t)d[k]);
-                            if (fm & (1u << k))
-                                stash[pos++] = make_uint2(stash_key(1, grp, row, lane * 4 + k), __float_as_uint(xv[k]));
-                        }
-                    }
-                    nst += total;
-                } else {
-                    // ranks inside the block: earlier rows, then earlier lanes of this row
-                    uint32_t io = co, iff = cf;
-#pragma unroll
-                    for (int off = 1; off < G; off <<= 1) {
-                        const uint32_t yo = __shfl_up_sync(VSZ_FULL, io, off);
-                        const uint32_t yf = __shfl_up_sync(VSZ_FULL, iff, off);
-                        if (glane >= off) { io += yo; iff += yf; }
-                    }
-                    uint64_t po = base_out + eo_g + run_o + (io - co);
-                    uint64_t pq = base_fix + ef_g + run_f + (iff - cf);
-                    const uint32_t idx0 = (uint32_t)(boff + (uint64_t)u * nx);
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        if (om & (1u << k)) {
-                            if (po < a.out_cap) a.stage_out[po] = make_uint2(idx0 + k, (uint32_t)d[k]);
-                            ++po;
-                        }
-                        if (fm & (1u << k)) {
-                            if (pq < a.fix_cap) a.stage_fix[pq] = make_uint2(idx0 + k, __float_as_uint(xv[k]));
-                            ++pq;
-                        }
-                    }
-                    run_o += __shfl_sync(VSZ_FULL, io, src + G - 1);
-                    run_f += __shfl_sync(VSZ_FULL, iff, src + G - 1);
-                }
-            }
-            h ^= 1;
+            // Rare path: rows that may hold an outlier or a fixup.
+            const uint32_t rows = __reduce_or_sync(VSZ_FULL, valid ? fmask : 0u);
+            if (rows) rare_rows(rows, h, boff, j, lz, b0, imode, raw, emit);
+            h = h + 1 == C::NS ? 0 : h + 1;
+            hi = hi + 1 == C::NS ? 0 : hi + 1;
             lz = nlz;
             j = nj;
+        }
         }
         cp_async_wait<0>();
         if (emit) break;

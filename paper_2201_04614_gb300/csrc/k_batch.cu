@@ -63,7 +63,8 @@ __global__ void __launch_bounds__(256) k_batch_begin(const BatchField* __restric
         w->qmax = INT_MIN;
         w->done0 = 0;
         w->done1 = 0;
-        w->has_finite = 0;
+        w->nonfinite = 0;
+        w->fp32_ok = 0;
         w->ticket = 0;
         vsz_header* h = const_cast<vsz_header*>(a.hdr);
         h->pad_global = 0;
@@ -89,24 +90,31 @@ __global__ void __launch_bounds__(256) k_batch_range(const BatchField* __restric
         const uint64_t i0 = (item - prefix[f]) * kItemElems, i1 = umin64(n, i0 + kItemElems);
         const float* x = b.a.x;
         unsigned int lo = 0xffffffffu, hi = 0u;
+        bool nf = false;
+        auto take = [&](float v) {
+            if (isfinite(v)) {
+                const unsigned u = float_to_ord(v);
+                lo = min(lo, u);
+                hi = max(hi, u);
+            } else {
+                nf = true;
+            }
+        };
         if (b.a.vec) {
             for (uint64_t i = i0 + 4 * threadIdx.x; i + 3 < i1; i += 4 * blockDim.x) {
                 const float4 v = ld_stream_f4(x + i);
-                const float e[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    if (isfinite(e[k])) { const unsigned u = float_to_ord(e[k]); lo = min(lo, u); hi = max(hi, u); }
+                take(v.x); take(v.y); take(v.z); take(v.w);
             }
-            for (uint64_t i = i0 + ((i1 - i0) & ~3ull) + threadIdx.x; i < i1; i += blockDim.x)
-                if (isfinite(x[i])) { const unsigned u = float_to_ord(x[i]); lo = min(lo, u); hi = max(hi, u); }
+            for (uint64_t i = i0 + ((i1 - i0) & ~3ull) + threadIdx.x; i < i1; i += blockDim.x) take(x[i]);
         } else {
-            for (uint64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x)
-                if (isfinite(x[i])) { const unsigned u = float_to_ord(x[i]); lo = min(lo, u); hi = max(hi, u); }
+            for (uint64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) take(x[i]);
         }
+        nf = __syncthreads_or(nf) != 0;
         lo = block_reduce(lo, OpMin(), smu, 0xffffffffu);
         hi = block_reduce(hi, OpMax(), smu, 0u);
         if (threadIdx.x == 0) {
             WsHeader* w = b.a.wsh;
+            if (nf) atomicOr(&w->nonfinite, 1u);
             if (lo != 0xffffffffu) {
                 atomicMin(&w->xmin_ord, lo);
                 atomicMax(&w->xmax_ord, hi);
@@ -115,11 +123,7 @@ __global__ void __launch_bounds__(256) k_batch_range(const BatchField* __restric
             last = atomicAdd(&w->done0, 1u) == (unsigned)(prefix[f + 1] - prefix[f] - 1);
             if (last) {
                 __threadfence();
-                const unsigned l = atomicAdd(&w->xmin_ord, 0u);
-                const unsigned h = atomicAdd(&w->xmax_ord, 0u);
-                const bool has = l != 0xffffffffu;
-                resolve_eb(const_cast<vsz_header*>(b.a.hdr), b.eb, true, has, has ? ord_to_float(l) : 0.0f,
-                           has ? ord_to_float(h) : 0.0f);
+                finish_range(w, const_cast<vsz_header*>(b.a.hdr), b.eb);
             }
         }
         __syncthreads();

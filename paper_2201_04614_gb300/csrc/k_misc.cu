@@ -23,7 +23,8 @@ __global__ void k_begin(WsHeader* wsh, uint4* chunks, uint64_t nchunks, vsz_head
         wsh->qmax = INT_MIN;
         wsh->done0 = 0;
         wsh->done1 = 0;
-        wsh->has_finite = 0;
+        wsh->nonfinite = 0;
+        wsh->fp32_ok = 0;
         wsh->ticket = 0;
         hdr->pad_global = 0;
         hdr->status = 0;
@@ -41,26 +42,33 @@ __global__ void __launch_bounds__(256) k_range(const float* __restrict__ x, uint
     __shared__ unsigned int smu[32];
     __shared__ bool last;
     unsigned int lo = 0xffffffffu, hi = 0u;
+    bool nf = false;
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t nth = (uint64_t)gridDim.x * blockDim.x;
+    auto take = [&](float v) {
+        if (isfinite(v)) {
+            const unsigned u = float_to_ord(v);
+            lo = min(lo, u);
+            hi = max(hi, u);
+        } else {
+            nf = true;
+        }
+    };
     if (vec) {
         const uint64_t n4 = n / 4;
         for (uint64_t i = tid; i < n4; i += nth) {
             const float4 v = ld_stream_f4(x + 4 * i);
-            const float a[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                if (isfinite(a[k])) { const unsigned u = float_to_ord(a[k]); lo = min(lo, u); hi = max(hi, u); }
+            take(v.x); take(v.y); take(v.z); take(v.w);
         }
-        for (uint64_t i = 4 * n4 + tid; i < n; i += nth)
-            if (isfinite(x[i])) { const unsigned u = float_to_ord(x[i]); lo = min(lo, u); hi = max(hi, u); }
+        for (uint64_t i = 4 * n4 + tid; i < n; i += nth) take(x[i]);
     } else {
-        for (uint64_t i = tid; i < n; i += nth)
-            if (isfinite(x[i])) { const unsigned u = float_to_ord(x[i]); lo = min(lo, u); hi = max(hi, u); }
+        for (uint64_t i = tid; i < n; i += nth) take(x[i]);
     }
+    nf = __syncthreads_or(nf) != 0;
     lo = block_reduce(lo, OpMin(), smu, 0xffffffffu);
     hi = block_reduce(hi, OpMax(), smu, 0u);
     if (threadIdx.x == 0) {
+        if (nf) atomicOr(&wsh->nonfinite, 1u);
         if (lo != 0xffffffffu) {
             atomicMin(&wsh->xmin_ord, lo);
             atomicMax(&wsh->xmax_ord, hi);
@@ -71,10 +79,7 @@ __global__ void __launch_bounds__(256) k_range(const float* __restrict__ x, uint
     __syncthreads();
     if (last && threadIdx.x == 0) {
         __threadfence();
-        const unsigned l = atomicAdd(&wsh->xmin_ord, 0u);
-        const unsigned h = atomicAdd(&wsh->xmax_ord, 0u);
-        const bool has = l != 0xffffffffu;
-        resolve_eb(hdr, eb, true, has, has ? ord_to_float(l) : 0.0f, has ? ord_to_float(h) : 0.0f);
+        finish_range(wsh, hdr, eb);
     }
 }
 

@@ -1,8 +1,8 @@
 // recon_nd.cuh -- inverse dual-quant for 2D and 3D fields (Sec. III-A).
 //
 // Same tiles, lane layout and batches of rows as the compression walk; the
-// codes stream through a lane-private, double-buffered cp.async ring (8
-// bytes per lane and row).  Per row:
+// codes stream through a lane-private, multi-stage cp.async ring (8 bytes
+// per lane and row).  Per row:
 // residuals from the codes (code - R), outliers patched from the block's
 // slice of the outlier list, P added at the block origin, then the inverse of
 // each first-order difference:
@@ -138,14 +138,27 @@ k_recon_nd(const ReconArgs a) {
         if (C::ZSMEM)
             for (int ly = 0; ly < ylen; ++ly) zs[ly * 32 + lane] = make_int4(0, 0, 0, 0);
 
-        issue_batch(0, 0, 0);
-        int lz = 0, j = 0, h = 0;
+        int ilz = 0, ij = 0;  // next batch to issue
+#pragma unroll
+        for (int st = 0; st < C::NSR - 1; ++st) {
+            if (st < nbatch) {
+                issue_batch(ilz, ij, st);
+                if (++ij == nbpp) { ij = 0; ++ilz; }
+            } else {
+                cp_async_commit();
+            }
+        }
+        int lz = 0, j = 0, h = 0, hs = C::NSR - 1;
         for (int kb = 0; kb < nbatch; ++kb) {
             int nj = j + 1, nlz = lz;
             if (nj == nbpp) { nj = 0; ++nlz; }
-            if (kb + 1 < nbatch) issue_batch(nlz, nj, h ^ 1);
-            else cp_async_commit();
-            cp_async_wait<1>();
+            if (kb + C::NSR - 1 < nbatch) {
+                issue_batch(ilz, ij, hs);
+                if (++ij == nbpp) { ij = 0; ++ilz; }
+            } else {
+                cp_async_commit();
+            }
+            cp_async_wait<C::NSR - 1>();
             if (cached && kb == 0) __syncwarp();  // every lane's share of the outlier slice has landed
             if (j == 0) {
 #pragma unroll
@@ -282,7 +295,8 @@ k_recon_nd(const ReconArgs a) {
                 for (int u = 0; u < U; ++u)
                     if (j * U + u < ylen) row(std::false_type{}, u);
             }
-            h ^= 1;
+            h = h + 1 == C::NSR ? 0 : h + 1;
+            hs = hs + 1 == C::NSR ? 0 : hs + 1;
             lz = nlz;
             j = nj;
         }

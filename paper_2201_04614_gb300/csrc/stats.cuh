@@ -26,6 +26,21 @@ __device__ __forceinline__ void resolve_eb(vsz_header* h, double eb, bool rel, b
     h->xmax = has ? xmax : 0.0f;
 }
 
+// After a range pass: resolve the relative error bound and record whether
+// the whole field qualifies for the exact fp32 arithmetic of the compression
+// walk (no NaN/Inf and every |fl(x * inv2eb)| < 2^20).  The product is
+// monotone in x, so the extremes of x bound it for every element.
+__device__ __forceinline__ void finish_range(WsHeader* w, vsz_header* h, double eb) {
+    const unsigned l = atomicAdd(&w->xmin_ord, 0u);
+    const unsigned u = atomicAdd(&w->xmax_ord, 0u);
+    const bool has = l != 0xffffffffu;
+    const float lo = has ? ord_to_float(l) : 0.0f, hi = has ? ord_to_float(u) : 0.0f;
+    resolve_eb(h, eb, true, has, lo, hi);
+    const float inv2eb = h->inv2eb;
+    const bool small = fabsf(__fmul_rn(lo, inv2eb)) < 1048576.0f && fabsf(__fmul_rn(hi, inv2eb)) < 1048576.0f;
+    w->fp32_ok = (has && atomicAdd(&w->nonfinite, 0u) == 0u && small) ? 1u : 0u;
+}
+
 // Block-wide reductions through shared memory (blockDim.x == 256).
 template <typename T, typename Op>
 __device__ __forceinline__ T block_reduce(T v, Op op, T* sm, T identity) {
