@@ -61,7 +61,7 @@
 #define VSZ_ND_MINB_C 4
 #endif
 #ifndef VSZ_ND_MINB_R
-#define VSZ_ND_MINB_R 7
+#define VSZ_ND_MINB_R 5
 #endif
 #ifndef VSZ_ND_STASH
 #define VSZ_ND_STASH 256
@@ -70,7 +70,7 @@
 #define VSZ_ND_STAGES 2
 #endif
 #ifndef VSZ_ND_STAGES_R
-#define VSZ_ND_STAGES_R 4
+#define VSZ_ND_STAGES_R 6
 #endif
 
 namespace vsz {

@@ -63,4 +63,17 @@ __device__ __forceinline__ void load4c(const uint16_t* p, int valid, bool vec, u
     }
 }
 
+// 16-byte store of a streamed output (written once, not read again by the
+// kernel): evict-first when VSZ_STORE_CS is set, a plain store otherwise.
+#ifndef VSZ_STORE_CS
+#define VSZ_STORE_CS 1
+#endif
+__device__ __forceinline__ void st_out4(int4* p, int4 v) {
+#if VSZ_STORE_CS
+    __stcs(p, v);
+#else
+    *p = v;
+#endif
+}
+
 }  // namespace vsz

@@ -42,6 +42,12 @@ k_recon_nd(const ReconArgs a) {
     const Geom& g = a.g;
     const float ebx2 = a.hdr->ebx2;
     const int32_t Pg = a.hdr->pad_global;
+    // every finite value had |x * inv2eb| < 2^20 (the range recorded by a
+    // relative-mode compression), so every q of a finite value converts to
+    // float exactly by the bias trick; non-finite values are fixups
+    const float inv2eb_h = a.hdr->inv2eb;
+    const bool fastcvt = a.hdr->has_range != 0u && fabsf(__fmul_rn(a.hdr->xmin, inv2eb_h)) < 1048576.0f &&
+                         fabsf(__fmul_rn(a.hdr->xmax, inv2eb_h)) < 1048576.0f;
     const int32_t R = a.R;
     const bool bp = is_block_pad(a.pad_mode);
     const uint64_t nx = g.nx;
@@ -133,6 +139,172 @@ k_recon_nd(const ReconArgs a) {
             }
             cp_async_commit();
         };
+
+        const bool interior = vec && s * kSegCols + kSegCols <= nx && ylen == B && (ND == 2 || zlen == B);
+        if (interior) {
+            // Lean walk of an interior tile: compile-time trip counts, 32-bit
+            // offsets, and P carried in the running-sum state (the z sums of
+            // 3D blocks start from P, the y sums of 2D blocks), which adds P
+            // to every element of the block exactly as adding it to the
+            // origin's residual before the sums does.  3D blocks of up to 8
+            // keep their z sums in registers (the rows of a plane unrolled).
+            constexpr int BPP = B / U;
+            constexpr int NPL = ND == 3 ? B : 1;
+            constexpr bool ZREG = ND == 3 && B <= 8;
+            constexpr int NB = NPL * BPP;
+            const uint32_t nx32 = (uint32_t)nx, pl32 = (uint32_t)plane;
+            const uint16_t* cl = a.codes + tile_base;
+            auto issue_fast = [&](int kb, int st) {
+                const uint16_t* src0 = cl + (uint32_t)(kb / BPP) * pl32 + (uint32_t)((kb % BPP) * U) * nx32;
+                const uint32_t dst0 = ring_wr + (uint32_t)(st * U * 32 * 8);
+#pragma unroll
+                for (int u = 0; u < U; ++u) cp_async8(dst0 + u * 32 * 8, src0 + (uint32_t)u * nx32, 8u);
+                cp_async_commit();
+            };
+#pragma unroll
+            for (int st = 0; st < C::NSR - 1; ++st) {
+                if (st < NB) issue_fast(st, st);
+                else cp_async_commit();
+            }
+            int32_t zr[ZREG ? B : 1][4];
+#pragma unroll
+            for (int ly = 0; ly < (ZREG ? B : 1); ++ly)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) zr[ly][k] = P;
+            if (ND == 3 && !ZREG) {
+#pragma unroll 4
+                for (int ly = 0; ly < B; ++ly) zs[ly * 32 + lane] = make_int4(P, P, P, P);
+            }
+            int32_t ys[4];
+            int h = 0, kb = 0;
+            for (int lz = 0; lz < NPL; ++lz) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) ys[k] = ND == 3 ? 0 : P;
+#pragma unroll(ZREG ? BPP : 1)
+                for (int jb = 0; jb < BPP; ++jb, ++kb) {
+                    if (kb + C::NSR - 1 < NB) issue_fast(kb + C::NSR - 1, (kb + C::NSR - 1) % C::NSR);
+                    else cp_async_commit();
+                    cp_async_wait<C::NSR - 1>();
+                    if (cached && kb == 0) __syncwarp();  // every lane's share of the outlier slice has landed
+                    const uint32_t boff = (uint32_t)lz * pl32 + (uint32_t)(jb * U) * nx32;
+                    const uint2* rr = ring_rd + h * U * 32;
+                    uint2 cw[U];
+                    uint32_t hz = 0;
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        cw[u] = rr[u * 32];
+                        hz |= ((cw[u].x - 0x00010001u) & ~cw[u].x & 0x80008000u) |
+                              ((cw[u].y - 0x00010001u) & ~cw[u].y & 0x80008000u);
+                    }
+                    const bool patch = anyout && __any_sync(VSZ_FULL, hz != 0u);
+                    auto lrow = [&](auto patch_tag, int u) {
+                        constexpr bool PATCH = decltype(patch_tag)::value;
+                        const uint32_t c[4] = {cw[u].x & 0xffffu, cw[u].x >> 16, cw[u].y & 0xffffu, cw[u].y >> 16};
+                        int32_t d[4];
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) d[k] = (int32_t)c[k] - R;
+                        if (PATCH) {
+                            uint32_t zm = 0;
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) zm |= (c[k] == 0u ? 1u : 0u) << k;
+                            if (__any_sync(VSZ_FULL, zm != 0u)) {
+                                const uint32_t cz = __popc(zm);
+                                uint32_t iz = cz;
+#pragma unroll
+                                for (int off = 1; off < G; off <<= 1) {
+                                    const uint32_t y = __shfl_up_sync(VSZ_FULL, iz, off);
+                                    if (glane >= off) iz += y;
+                                }
+                                const uint32_t gtot = __shfl_sync(VSZ_FULL, iz, src + G - 1);
+                                uint32_t r = rank + (iz - cz);
+                                const uint32_t roff = (uint32_t)tile_base + boff + (uint32_t)u * nx32;
+#pragma unroll
+                                for (int k = 0; k < 4; ++k) {
+                                    if (zm & (1u << k)) {
+                                        const bool in = r < hi && r < a.out_cap;
+                                        const uint32_t oi = !in ? ~0u : cached ? oc_idx[r - lo_t] : a.out_idx[r];
+                                        if (in && oi == roff + k) {
+                                            d[k] = cached ? oc_del[r - lo_t] : a.out_delta[r];
+                                        } else {
+                                            atomicMax(&a.hdr->recon_status, (unsigned)VSZ_ERR_CORRUPT);
+                                            d[k] = 0;
+                                        }
+                                        ++r;
+                                    }
+                                }
+                                rank += gtot;
+                            }
+                        }
+                        // Sx
+                        d[1] = wadd(d[1], d[0]);
+                        d[2] = wadd(d[2], d[1]);
+                        d[3] = wadd(d[3], d[2]);
+                        {
+                            const uint32_t tot = (uint32_t)d[3];
+                            uint32_t inc = tot;
+#pragma unroll
+                            for (int off = 1; off < G; off <<= 1) {
+                                const uint32_t y = __shfl_up_sync(VSZ_FULL, inc, off);
+                                if (glane >= off) inc += y;
+                            }
+                            const int32_t ex = (int32_t)(inc - tot);
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) d[k] = wadd(d[k], ex);
+                        }
+                        // Sy
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            d[k] = wadd(d[k], ys[k]);
+                            ys[k] = d[k];
+                        }
+                        // Sz
+                        if (ZREG) {
+                            const int ly = ZREG ? jb * U + u : 0;
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) {
+                                d[k] = wadd(d[k], zr[ly][k]);
+                                zr[ly][k] = d[k];
+                            }
+                        } else if (ND == 3) {
+                            int4& stz = zs[(jb * U + u) * 32 + lane];
+                            const int4 pv = stz;
+                            d[0] = wadd(d[0], pv.x); d[1] = wadd(d[1], pv.y);
+                            d[2] = wadd(d[2], pv.z); d[3] = wadd(d[3], pv.w);
+                            stz = make_int4(d[0], d[1], d[2], d[3]);
+                        }
+                        const uint32_t ro = boff + (uint32_t)u * nx32;
+                        if (QOUT) {
+                            st_out4(reinterpret_cast<int4*>(reinterpret_cast<int32_t*>(a.out) + tile_base + ro),
+                                    make_int4(d[0], d[1], d[2], d[3]));
+                        } else {
+                            int4 vv;
+                            if (fastcvt) {  // (float)q by the 1.5 * 2^23 bias, exact for |q| < 2^22
+                                vv.x = __float_as_int(__fmul_rn(__fsub_rn(__int_as_float(d[0] + 0x4B400000), 12582912.0f), ebx2));
+                                vv.y = __float_as_int(__fmul_rn(__fsub_rn(__int_as_float(d[1] + 0x4B400000), 12582912.0f), ebx2));
+                                vv.z = __float_as_int(__fmul_rn(__fsub_rn(__int_as_float(d[2] + 0x4B400000), 12582912.0f), ebx2));
+                                vv.w = __float_as_int(__fmul_rn(__fsub_rn(__int_as_float(d[3] + 0x4B400000), 12582912.0f), ebx2));
+                            } else {
+                                vv.x = __float_as_int(__fmul_rn(q2f(d[0]), ebx2));
+                                vv.y = __float_as_int(__fmul_rn(q2f(d[1]), ebx2));
+                                vv.z = __float_as_int(__fmul_rn(q2f(d[2]), ebx2));
+                                vv.w = __float_as_int(__fmul_rn(q2f(d[3]), ebx2));
+                            }
+                            st_out4(reinterpret_cast<int4*>(reinterpret_cast<float*>(a.out) + tile_base + ro), vv);
+                        }
+                    };
+                    if (patch) {
+#pragma unroll
+                        for (int u = 0; u < U; ++u) lrow(std::true_type{}, u);
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < U; ++u) lrow(std::false_type{}, u);
+                    }
+                    h = h + 1 == C::NSR ? 0 : h + 1;
+                }
+            }
+            cp_async_wait<0>();
+            continue;
+        }
 
         int32_t ys[4] = {0, 0, 0, 0};
         if (C::ZSMEM)
