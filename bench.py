@@ -53,6 +53,8 @@ def parse_args():
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched+tuned vs plain comparison")
+    ap.add_argument("--batch-steps", type=int, default=20)
     return ap.parse_args()
 
 
@@ -231,6 +233,115 @@ def run_reference(a):
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- batched + tuned vs plain
+def run_batch_compare(a, log_fn=log) -> dict:
+    """The mixed stream of fields (one 1D field of 280,953,867 random-walk
+    values, 13 fields of 100x500x500, 20 of 1800x3600; relative eb 1e-3 and
+    1e-5, R = 512): compression throughput of plain per-field launches with
+    the default class (block 256 / 8 / 16, zero padding), of the same
+    launches replayed as one CUDA graph, of one batch plan with the default
+    classes, and of one batch plan with the tuner's classes; outlier counts
+    per field for the tuned and the default classes."""
+    import numpy as np
+    import torch
+    import paper_2201_04614_gb300 as vsz
+    from paper_2201_04614_gb300 import tuner as T
+    import synth
+
+    t0 = time.time()
+    specs = synth.cfg5_fields()
+    xs, shapes, names = [], [], []
+    for name, shape, maker in specs:
+        xs.append(torch.from_numpy(np.ascontiguousarray(maker(), np.float32).reshape(-1)).cuda())
+        shapes.append(shape)
+        names.append(name)
+    n_total = sum(x.numel() for x in xs)
+    log_fn(f"[bench] batch stream: {len(xs)} fields, {n_total} values, generated in {time.time() - t0:.1f}s")
+    steps = max(5, min(a.batch_steps, 50))
+    stream = torch.cuda.Stream()
+
+    def timed(fn):
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                fn()
+            stream.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                fn()
+            e1.record(stream)
+            stream.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    def make_fields(classes, eb):
+        out = []
+        for shape, c in zip(shapes, classes):
+            b, pad = T.class_params(len(shape), c)
+            n = int(np.prod(shape))
+            out.append(vsz.Field(vsz.Params.make(shape, b, eb, "rel", 512, pad), out_cap=max(1 << 16, n // 4),
+                                 fix_cap=max(1 << 16, n // 64)))
+        return out
+
+    res = {"workload": "1D 280,953,867 random walk + 13 x 100x500x500 GRF + 20 x 1800x3600 Fourier fields "
+                       "(2.94 GB fp32), relative eb, R=512", "values": n_total, "steps": steps, "by_eb": {}}
+    for eb in (1e-3, 1e-5):
+        dflt = [T.default_class(len(sh)) for sh in shapes]
+        plain = make_fields(dflt, eb)
+
+        def plain_step():
+            for f, x in zip(plain, xs):
+                f.compress(x)
+        ms_plain = timed(plain_step)
+        # the same per-field launches captured once into a CUDA graph
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(stream):
+            plain_step()
+            stream.synchronize()
+            with torch.cuda.graph(g, stream=stream):
+                plain_step()
+        ms_plain_graph = timed(g.replay)
+        del g
+        nout_def = [int(f.header()["n_out"]) for f in plain]
+        st_def = [int(f.header()["status"]) for f in plain]
+        bd = vsz.Batch(plain, xs, use_graph=True)
+        ms_batch_def = timed(lambda: bd.submit(stream))
+        bd.close()
+        # tuned classes: features, one MLP inference, guard (timed on its own)
+        torch.cuda.synchronize()
+        tt = time.time()
+        picks = T.choose([(vsz.Params.make(sh, 8, eb, "rel", 512, "zero"), x) for sh, x in zip(shapes, xs)])
+        torch.cuda.synchronize()
+        tune_ms = (time.time() - tt) * 1e3
+        classes = [r["class"] for r in picks]
+        tuned = make_fields(classes, eb)
+        bt = vsz.Batch(tuned, xs, use_graph=True)
+        ms_batch_tuned = timed(lambda: bt.submit(stream))
+        bt.close()
+        nout_tuned = [int(f.header()["n_out"]) for f in tuned]
+        st_tuned = [int(f.header()["status"]) for f in tuned]
+        gb = n_total * 4 / 1e9
+        res["by_eb"][f"{eb:g}"] = {
+            "plain_GBps": gb / (ms_plain * 1e-3), "plain_graph_GBps": gb / (ms_plain_graph * 1e-3),
+            "batched_default_GBps": gb / (ms_batch_def * 1e-3), "batched_tuned_GBps": gb / (ms_batch_tuned * 1e-3),
+            "ms": {"plain": ms_plain, "plain_graph": ms_plain_graph, "batched_default": ms_batch_def,
+                   "batched_tuned": ms_batch_tuned},
+            "tune_ms_once": tune_ms,
+            "classes_tuned": {nm: T.class_params(len(sh), c) for nm, sh, c in zip(names, shapes, classes)
+                              if c != T.default_class(len(sh))},
+            "guard_fallbacks": sum(1 for r in picks if r["class"] != r["predicted"]),
+            "n_out_default_total": sum(nout_def), "n_out_tuned_total": sum(nout_tuned),
+            "fields_n_out_tuned_le_default": sum(1 for u, v in zip(nout_tuned, nout_def) if u <= v),
+            "fields": len(xs), "status_nonzero": sum(1 for v in st_def + st_tuned if v),
+        }
+        log_fn(f"[bench] batch eb={eb:g}: {res['by_eb'][f'{eb:g}']}")
+        del plain, tuned
+        torch.cuda.empty_cache()
+    del xs
+    torch.cuda.empty_cache()
+    return res
 
 
 # ---------------------------------------------------------------- GPU arm
@@ -420,6 +531,12 @@ def run_gpu(a):
                 del fs
                 torch.cuda.empty_cache()
 
+    batched = None
+    if not a.no_batch and rank == 0:
+        del xh
+        torch.cuda.empty_cache()
+        batched = run_batch_compare(a)
+
     # CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and a.cpu_seconds > 0:
@@ -442,7 +559,7 @@ def run_gpu(a):
                                       / a.steps * 1e-3) / 1e9,
             "reconstruct_GBps": n * 4 / (sum(per[k]["ms"] for k in ("recon", "fixups") if k in per)
                                          / a.steps * 1e-3) / 1e9,
-            "sweep": sweep,
+            "sweep": sweep, "batched": batched,
         }
         print(json.dumps(line), flush=True)
     if dist:

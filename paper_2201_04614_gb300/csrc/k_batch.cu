@@ -27,7 +27,7 @@
 
 namespace vsz {
 
-constexpr uint64_t kItemElems = 1ull << 20;  // elements per statistics work item
+constexpr uint64_t kItemElems = 1ull << 18;  // elements per statistics work item
 constexpr int kMaxClasses = 28;               // tickets in the batch header
 
 struct BatchField {
@@ -101,11 +101,20 @@ __global__ void __launch_bounds__(256) k_batch_range(const BatchField* __restric
             }
         };
         if (b.a.vec) {
-            for (uint64_t i = i0 + 4 * threadIdx.x; i + 3 < i1; i += 4 * blockDim.x) {
+            // four 16-byte loads in flight per thread
+            uint64_t i = i0 + 4 * threadIdx.x;
+            for (; i + 12 * blockDim.x + 3 < i1; i += 16 * blockDim.x) {
+                float4 v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) v[u] = ld_stream_f4(x + i + 4 * u * blockDim.x);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) { take(v[u].x); take(v[u].y); take(v[u].z); take(v[u].w); }
+            }
+            for (; i + 3 < i1; i += 4 * blockDim.x) {
                 const float4 v = ld_stream_f4(x + i);
                 take(v.x); take(v.y); take(v.z); take(v.w);
             }
-            for (uint64_t i = i0 + ((i1 - i0) & ~3ull) + threadIdx.x; i < i1; i += blockDim.x) take(x[i]);
+            for (uint64_t k = i0 + ((i1 - i0) & ~3ull) + threadIdx.x; k < i1; k += blockDim.x) take(x[k]);
         } else {
             for (uint64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) take(x[i]);
         }
@@ -145,9 +154,29 @@ __global__ void __launch_bounds__(256) k_batch_qstats(const BatchField* __restri
         const float inv2eb = b.a.hdr->inv2eb;
         int qlo = INT_MAX, qhi = INT_MIN;
         long long qs = 0;
-        for (uint64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-            const int q = prequant(x[i], inv2eb);
-            qlo = min(qlo, q); qhi = max(qhi, q); qs += q;
+        auto take = [&](float v) {
+            const int q = prequant(v, inv2eb);
+            qlo = min(qlo, q);
+            qhi = max(qhi, q);
+            qs += q;
+        };
+        if (b.a.vec) {
+            // four 16-byte loads in flight per thread
+            uint64_t i = i0 + 4 * threadIdx.x;
+            for (; i + 12 * blockDim.x + 3 < i1; i += 16 * blockDim.x) {
+                float4 v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) v[u] = ld_stream_f4(x + i + 4 * u * blockDim.x);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) { take(v[u].x); take(v[u].y); take(v[u].z); take(v[u].w); }
+            }
+            for (; i + 3 < i1; i += 4 * blockDim.x) {
+                const float4 v = ld_stream_f4(x + i);
+                take(v.x); take(v.y); take(v.z); take(v.w);
+            }
+            for (uint64_t k = i0 + ((i1 - i0) & ~3ull) + threadIdx.x; k < i1; k += blockDim.x) take(x[k]);
+        } else {
+            for (uint64_t k = i0 + threadIdx.x; k < i1; k += blockDim.x) take(x[k]);
         }
         qlo = block_reduce(qlo, OpMin(), smi, INT_MAX);
         qhi = block_reduce(qhi, OpMax(), smi, INT_MIN);
