@@ -187,6 +187,45 @@ size_t vsz_workspace_size(const vsz_params* p, uint64_t out_cap, uint64_t fix_ca
 }
 
 
+}  // extern "C"
+
+namespace vsz {
+// Kernel arguments of one field's compression over its workspace.
+static CompressArgs compress_args(const Geom& g, const vsz_params* p, const float* d_x, const vsz_compressed* c,
+                                  char* ws, const WsLayout& L) {
+    CompressArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.x = d_x;
+    a.codes = c->codes;
+    a.pad = c->pad;
+    a.blk_off = c->blk_off;
+    a.hdr = c->hdr;
+    a.wsh = (WsHeader*)ws;
+    a.tiles = (uint4*)(ws + L.tiles);
+    a.chunks = (uint4*)(ws + L.chunks);
+    a.stage_out = (uint2*)(ws + L.stage_out);
+    a.stage_fix = (uint2*)(ws + L.stage_fix);
+    if (is_global_pad(p->pad)) {
+        a.tstats = (TileStats*)(ws + L.tstats);
+        a.origin = (int32_t*)(ws + L.origin);
+        a.oflag = (uint8_t*)(ws + L.oflag);
+    }
+    a.out_idx = c->out_idx;
+    a.out_delta = c->out_delta;
+    a.fix_idx = c->fix_idx;
+    a.fix_bits = c->fix_bits;
+    a.out_cap = c->out_cap;
+    a.fix_cap = c->fix_cap;
+    a.g = g;
+    a.R = (int32_t)p->radius;
+    a.pad_mode = p->pad;
+    a.vec = (aligned(d_x, 16) && aligned(c->codes, 16) && (g.nd == 1 || g.nx % 4 == 0)) ? 1 : 0;
+    return a;
+}
+}  // namespace vsz
+
+extern "C" {
+
 vsz_status vsz_prequant_lorenzo(const vsz_params* p, const float* d_x, vsz_compressed* c, void* d_ws,
                                 size_t ws_bytes, void* stream) {
     Geom g;
@@ -199,7 +238,6 @@ vsz_status vsz_prequant_lorenzo(const vsz_params* p, const float* d_x, vsz_compr
     cudaStream_t s = (cudaStream_t)stream;
     char* ws = (char*)d_ws;
     WsHeader* wsh = (WsHeader*)ws;
-    uint4* tiles = (uint4*)(ws + L.tiles);
     uint4* chunks = (uint4*)(ws + L.chunks);
     const bool rel = p->eb_mode == VSZ_EB_REL;
     const bool xvec = aligned(d_x, 16);
@@ -215,40 +253,20 @@ vsz_status vsz_prequant_lorenzo(const vsz_params* p, const float* d_x, vsz_compr
         e = launch_range(d_x, g.n, wsh, c->hdr, p->eb, xvec, s);
         if (e != cudaSuccess) return cuda_fail(e);
     }
-    if (p->pad == VSZ_PAD_GLOBAL_MIN || p->pad == VSZ_PAD_GLOBAL_MAX || p->pad == VSZ_PAD_GLOBAL_AVG) {
-        TraceScope ts("qstats", s, g.nd, g.b, g.n);
-        e = launch_qstats(d_x, g.n, wsh, c->hdr, p->pad, xvec, s);
-        if (e != cudaSuccess) return cuda_fail(e);
-    }
     if (g.ntiles == 0) return VSZ_OK;
 
-    CompressArgs a;
-    std::memset(&a, 0, sizeof a);
-    a.x = d_x;
-    a.codes = c->codes;
-    a.pad = c->pad;
-    a.blk_off = c->blk_off;
-    a.hdr = c->hdr;
-    a.wsh = wsh;
-    a.tiles = tiles;
-    a.chunks = chunks;
-    a.stage_out = (uint2*)(ws + L.stage_out);
-    a.stage_fix = (uint2*)(ws + L.stage_fix);
-    a.out_idx = c->out_idx;
-    a.out_delta = c->out_delta;
-    a.fix_idx = c->fix_idx;
-    a.fix_bits = c->fix_bits;
-    a.out_cap = c->out_cap;
-    a.fix_cap = c->fix_cap;
-    a.g = g;
-    a.R = (int32_t)p->radius;
-    a.pad_mode = p->pad;
-    a.vec = (xvec && aligned(c->codes, 16) && (g.nd == 1 || g.nx % 4 == 0)) ? 1 : 0;
+    const CompressArgs a = compress_args(g, p, d_x, c, ws, L);
     {
         TraceScope ts("lorenzo", s, g.nd, g.b, g.n);
         e = g.nd == 1 ? launch_lorenzo_1d(a, s) : g.nd == 2 ? launch_lorenzo_2d(a, s) : launch_lorenzo_3d(a, s);
     }
     if (e != cudaSuccess) return cuda_fail(e);
+    if (is_global_pad(p->pad)) {
+        // the global padding value is known once every tile is walked
+        TraceScope ts("origin_fix", s, g.nd, g.b, g.n);
+        e = launch_origin_fix(a, s);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
     return VSZ_OK;
 }
 
@@ -270,9 +288,7 @@ vsz_status vsz_outlier_compact(const vsz_params* p, vsz_compressed* c, void* d_w
     if (e != cudaSuccess) return cuda_fail(e);
     if (g.nchunks > 0) {
         TraceScope ts("compact_move", s, g.nd, g.b, g.n);
-        e = launch_compact_move(g, (const uint4*)(ws + L.tiles), (const uint4*)(ws + L.chunks), c->blk_off,
-                                (const uint2*)(ws + L.stage_out), (const uint2*)(ws + L.stage_fix), c->out_idx,
-                                c->out_delta, c->out_cap, c->fix_idx, c->fix_bits, c->fix_cap, s);
+        e = launch_compact_move(compress_args(g, p, nullptr, c, ws, L), s);
     }
     if (e != cudaSuccess) return cuda_fail(e);
     return VSZ_OK;

@@ -50,9 +50,18 @@ struct WsHeader {
 };
 static_assert(sizeof(WsHeader) <= 256, "ws header");
 
+// q statistics of one tile (global padding modes).
+struct __align__(16) TileStats {
+    int32_t qmin, qmax;
+    long long qsum;
+};
+
 struct WsLayout {
     size_t tiles;      // uint4 per tile {stage_base_out, tot_out, stage_base_fix, tot_fix}
     size_t chunks;     // uint4 per chunk {sum_out, sum_fix, off_out, off_fix}
+    size_t tstats;     // TileStats per tile: q statistics (global padding)
+    size_t origin;     // int32 per block: q at the block origin, then its residual (global padding)
+    size_t oflag;      // uint8 per block: the origin is an outlier (global padding)
     size_t stage_out;  // uint2 per outlier {idx, delta}
     size_t stage_fix;  // uint2 per fixup {idx, bits}
     size_t total;
@@ -67,6 +76,12 @@ inline WsLayout ws_layout(const Geom& g, uint64_t out_cap, uint64_t fix_cap) {
     off = align256(off + g.ntiles * 16);
     L.chunks = off;
     off = align256(off + g.nchunks * 16);
+    L.tstats = off;
+    off = align256(off + g.ntiles * 16);
+    L.origin = off;
+    off = align256(off + g.nb * 4);
+    L.oflag = off;
+    off = align256(off + g.nb);
     L.stage_out = off;
     off = align256(off + out_cap * 8);
     L.stage_fix = off;
@@ -145,6 +160,9 @@ struct CompressArgs {
     uint4* chunks;
     uint2* stage_out;
     uint2* stage_fix;
+    TileStats* tstats;     // [ntiles] q statistics per tile (global padding modes)
+    int32_t* origin;       // [nb] block-origin q / residual (global padding modes)
+    uint8_t* oflag;        // [nb] origin-outlier flags (global padding modes)
     uint32_t* out_idx;     // final lists (used by the batch compaction)
     int32_t* out_delta;
     uint32_t* fix_idx;
@@ -175,6 +193,25 @@ struct ReconArgs {
 __host__ __device__ inline bool is_block_pad(int m) {
     return m == VSZ_PAD_BLOCK_MIN || m == VSZ_PAD_BLOCK_MAX || m == VSZ_PAD_BLOCK_AVG;
 }
+__host__ __device__ inline bool is_global_pad(int m) {
+    return m == VSZ_PAD_GLOBAL_MIN || m == VSZ_PAD_GLOBAL_MAX || m == VSZ_PAD_GLOBAL_AVG;
+}
+
+// Element index of the origin of block `blk` and the tile holding it.
+__host__ __device__ inline void block_origin(const Geom& g, uint64_t blk, uint64_t* idx, uint64_t* tile) {
+    if (g.nd == 1) {
+        *idx = blk * g.b;
+        *tile = (blk * g.b) / kChunk1D;
+        return;
+    }
+    // block counts are below 2^32: 32-bit divisions
+    const uint32_t b32 = (uint32_t)blk, nbx = (uint32_t)g.nbx, nby = (uint32_t)g.nby;
+    const uint32_t r32 = b32 / nbx;
+    const uint64_t bx = b32 - r32 * nbx, r = r32;
+    const uint64_t bz = r32 / nby, by = r32 - (uint32_t)bz * nby;
+    *idx = (bz * g.b * g.ny + by * g.b) * g.nx + bx * g.b;
+    *tile = r * g.nseg + (bx * g.b) / kSegCols;
+}
 
 // Host launchers implemented in the per-rank translation units.
 cudaError_t launch_lorenzo_1d(const CompressArgs& a, cudaStream_t s);
@@ -184,11 +221,11 @@ cudaError_t launch_recon_1d(const ReconArgs& a, bool q_out, cudaStream_t s);
 cudaError_t launch_recon_2d(const ReconArgs& a, bool q_out, cudaStream_t s);
 cudaError_t launch_recon_3d(const ReconArgs& a, bool q_out, cudaStream_t s);
 
-cudaError_t launch_lorenzo_batch_1d(uint32_t b, bool bp, const CompressArgs* fields, const uint64_t* tile_prefix,
+cudaError_t launch_lorenzo_batch_1d(uint32_t b, int pk, const CompressArgs* fields, const uint64_t* tile_prefix,
                                     int nfields, uint64_t total_tiles, unsigned long long* ticket, cudaStream_t s);
-cudaError_t launch_lorenzo_batch_2d(uint32_t b, bool bp, const CompressArgs* fields, const uint64_t* tile_prefix,
+cudaError_t launch_lorenzo_batch_2d(uint32_t b, int pk, const CompressArgs* fields, const uint64_t* tile_prefix,
                                     int nfields, uint64_t total_tiles, unsigned long long* ticket, cudaStream_t s);
-cudaError_t launch_lorenzo_batch_3d(uint32_t b, bool bp, const CompressArgs* fields, const uint64_t* tile_prefix,
+cudaError_t launch_lorenzo_batch_3d(uint32_t b, int pk, const CompressArgs* fields, const uint64_t* tile_prefix,
                                     int nfields, uint64_t total_tiles, unsigned long long* ticket, cudaStream_t s);
 
 int num_sms();

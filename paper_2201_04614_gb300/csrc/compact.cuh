@@ -8,6 +8,8 @@
 // (k_misc.cu) and the batch kernels (k_batch.cu).
 #pragma once
 
+#include <climits>
+
 #include "common.cuh"
 
 namespace vsz {
@@ -62,23 +64,24 @@ __device__ __forceinline__ void compact_scan_body(uint4* chunks, uint64_t nchunk
 
 // Compaction, part 2: per chunk of tiles (one CTA), the tiles' offsets, the blocks'
 // final offsets (in-tile prefix + tile offset) and the move of each tile's
-// staged entries to their canonical place.
-__device__ __forceinline__ void compact_chunk_body(uint64_t chunk, const uint4* __restrict__ tiles,
-                                                   const uint4* __restrict__ chunks, uint64_t ntiles, uint64_t nseg,
-                                                   uint64_t nbx, uint32_t bpt, uint32_t* blk_off,
-                                                   const uint2* __restrict__ stage_out,
-                                                   const uint2* __restrict__ stage_fix, uint32_t* out_idx,
-                                                   int32_t* out_delta, uint64_t out_cap, uint32_t* fix_idx,
-                                                   uint32_t* fix_bits, uint64_t fix_cap) {
+// staged entries to their canonical place.  With a global padding mode, the
+// origin pass may have added an outlier at the origin of some blocks: it
+// goes first in its block, so the block's staged entries and every later
+// block of the tile shift by the number of such origins before them.
+__device__ __forceinline__ void compact_chunk_body(uint64_t chunk, const CompressArgs& a) {
     __shared__ uint4 rec[kTilesPerChunk];
     __shared__ uint32_t toff_o[kTilesPerChunk], toff_f[kTilesPerChunk];
+    __shared__ uint32_t fw[8][32], fpre[8][32];  // per warp: origin-outlier bits of a tile, prefix popcounts
+    const Geom& g = a.g;
+    const uint64_t ntiles = g.ntiles, nseg = g.nseg, nbx = g.nbx;
+    const uint32_t bpt = g.bpt;
     const uint64_t t0 = chunk * kTilesPerChunk;
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     if (w == 0) {  // the chunk's tile offsets: chunk offset + exclusive scan of the tile totals
-        uint32_t bo = chunks[chunk].z, bf = chunks[chunk].w;
+        uint32_t bo = a.chunks[chunk].z, bf = a.chunks[chunk].w;
         for (int i0 = 0; i0 < kTilesPerChunk; i0 += 32) {
             const uint64_t t = t0 + i0 + l;
-            const uint4 r = t < ntiles ? tiles[t] : make_uint4(0, 0, 0, 0);
+            const uint4 r = t < ntiles ? a.tiles[t] : make_uint4(0, 0, 0, 0);
             uint32_t io = r.y, iff = r.w;
 #pragma unroll
             for (int off = 1; off < 32; off <<= 1) {
@@ -102,21 +105,156 @@ __device__ __forceinline__ void compact_chunk_body(uint64_t chunk, const uint4* 
         const uint32_t to = toff_o[j], tf = toff_f[j];
         const uint64_t s = tt % nseg;
         const uint64_t fb = (tt / nseg) * nbx + s * bpt;
-        const uint64_t nblk = umin64(bpt, nbx - s * bpt);
-        for (uint64_t k = l; k < nblk; k += 32) blk_off[fb + k] += to;
-        if (rr.y && (uint64_t)rr.x + rr.y <= out_cap && (uint64_t)to + rr.y <= out_cap) {
-            for (uint32_t k = l; k < rr.y; k += 32) {
-                const uint2 e = stage_out[rr.x + k];
-                out_idx[to + k] = e.x;
-                out_delta[to + k] = (int32_t)e.y;
+        const uint32_t nblk = (uint32_t)umin64(bpt, nbx - s * bpt);
+        // origin outliers of this tile's blocks (global padding only)
+        uint32_t nflag = 0;
+        const uint32_t nwords = (nblk + 31) / 32;
+        if (a.oflag) {
+            for (uint32_t wd = 0; wd < nwords; ++wd) {
+                const uint32_t k = wd * 32 + l;
+                const uint32_t bits = __ballot_sync(VSZ_FULL, k < nblk && a.oflag[fb + k] != 0);
+                if (l == 0) fw[w][wd] = bits;
+                nflag += __popc(bits);
             }
         }
-        if (rr.w && (uint64_t)rr.z + rr.w <= fix_cap && (uint64_t)tf + rr.w <= fix_cap) {
-            for (uint32_t k = l; k < rr.w; k += 32) {
-                const uint2 e = stage_fix[rr.z + k];
-                fix_idx[tf + k] = e.x;
-                fix_bits[tf + k] = e.y;
+        const uint32_t staged = rr.y - nflag;
+        if (nflag == 0) {
+            for (uint32_t k = l; k < nblk; k += 32) a.blk_off[fb + k] += to;
+            if (rr.y && (uint64_t)rr.x + rr.y <= a.out_cap && (uint64_t)to + rr.y <= a.out_cap) {
+                uint32_t k = l;
+                for (; k + 96 < rr.y; k += 128) {  // four loads in flight per lane
+                    uint2 e[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) e[u] = a.stage_out[rr.x + k + 32 * u];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        a.out_idx[to + k + 32 * u] = e[u].x;
+                        a.out_delta[to + k + 32 * u] = (int32_t)e[u].y;
+                    }
+                }
+                for (; k < rr.y; k += 32) {
+                    const uint2 e = a.stage_out[rr.x + k];
+                    a.out_idx[to + k] = e.x;
+                    a.out_delta[to + k] = (int32_t)e.y;
+                }
             }
+        } else {
+            __syncwarp();
+            {  // exclusive prefix of the words' popcounts (nwords <= 32)
+                const uint32_t c = l < (int)nwords ? __popc(fw[w][l]) : 0u;
+                uint32_t inc = c;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const uint32_t y = __shfl_up_sync(VSZ_FULL, inc, off);
+                    if (l >= off) inc += y;
+                }
+                if (l < (int)nwords) fpre[w][l] = inc - c;
+            }
+            __syncwarp();
+            // flagged origins before block k, and k's own flag
+            auto before = [&](uint32_t k) {
+                return fpre[w][k >> 5] + __popc(fw[w][k >> 5] & ((1u << (k & 31)) - 1u));
+            };
+            const bool fits = (uint64_t)to + rr.y <= a.out_cap;
+            for (uint32_t k = l; k < nblk; k += 32) {
+                const uint32_t np = a.blk_off[fb + k] + before(k);
+                a.blk_off[fb + k] = to + np;
+                if (fits && ((fw[w][k >> 5] >> (k & 31)) & 1u)) {
+                    uint64_t idx, tile;
+                    block_origin(g, fb + k, &idx, &tile);
+                    a.out_idx[to + np] = (uint32_t)idx;
+                    a.out_delta[to + np] = a.origin[fb + k];
+                }
+            }
+            if (staged && (uint64_t)rr.x + staged <= a.out_cap && fits) {
+                // block of an entry inside the tile, from its element index
+                const uint32_t nx32 = (uint32_t)g.nx, c0 = (uint32_t)(s * kSegCols), e0 = (uint32_t)(tt * kChunk1D);
+                auto place = [&](uint32_t i, uint2 e) {
+                    const uint32_t k = (g.nd == 1 ? e.x - e0 : e.x % nx32 - c0) / g.b;
+                    const uint32_t pos = to + i + before(k) + ((fw[w][k >> 5] >> (k & 31)) & 1u);
+                    a.out_idx[pos] = e.x;
+                    a.out_delta[pos] = (int32_t)e.y;
+                };
+                uint32_t i = l;
+                for (; i + 96 < staged; i += 128) {  // four loads in flight per lane
+                    uint2 e[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) e[u] = a.stage_out[rr.x + i + 32 * u];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) place(i + 32 * u, e[u]);
+                }
+                for (; i < staged; i += 32) place(i, a.stage_out[rr.x + i]);
+            }
+        }
+        if (rr.w && (uint64_t)rr.z + rr.w <= a.fix_cap && (uint64_t)tf + rr.w <= a.fix_cap) {
+            for (uint32_t k = l; k < rr.w; k += 32) {
+                const uint2 e = a.stage_fix[rr.z + k];
+                a.fix_idx[tf + k] = e.x;
+                a.fix_bits[tf + k] = e.y;
+            }
+        }
+    }
+}
+
+// The origin pass of a global padding mode, for block `blk`: the residual
+// of the block origin q - P, its code, and whether it is an outlier (then
+// counted in its tile and chunk before the compaction).
+__device__ __forceinline__ void origin_fix_block(const CompressArgs& a, uint64_t blk, int32_t P) {
+    uint64_t idx, tile;
+    block_origin(a.g, blk, &idx, &tile);
+    const int32_t d = (int32_t)((uint32_t)a.origin[blk] - (uint32_t)P);
+    const uint32_t c = code_of(d, a.R);
+    a.codes[idx] = (uint16_t)c;
+    const bool out = c == 0u;
+    a.oflag[blk] = out ? 1 : 0;
+    if (out) {
+        a.origin[blk] = d;
+        atomicAdd(&a.tiles[tile].y, 1u);
+        atomicAdd(&a.chunks[tile / kTilesPerChunk].x, 1u);
+    }
+}
+
+// The global padding value (Sec. IV-B-1) from the tiles' q statistics (one
+// CTA of 1024 threads per field, a fixed reduction order): the minimum, the
+// maximum, or the rounded mean of q; written to the field's header.
+__device__ __forceinline__ void pad_reduce_body(const CompressArgs& a) {
+    __shared__ int smn[32], smx[32];
+    __shared__ long long ssm[32];
+    int mn = INT_MAX, mx = INT_MIN;
+    long long sm = 0;
+    for (uint64_t t = threadIdx.x; t < a.g.ntiles; t += blockDim.x) {
+        const TileStats st = a.tstats[t];
+        mn = min(mn, st.qmin);
+        mx = max(mx, st.qmax);
+        sm += st.qsum;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        mn = min(mn, __shfl_xor_sync(VSZ_FULL, mn, off));
+        mx = max(mx, __shfl_xor_sync(VSZ_FULL, mx, off));
+        sm += __shfl_xor_sync(VSZ_FULL, sm, off);
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) { smn[w] = mn; smx[w] = mx; ssm[w] = sm; }
+    __syncthreads();
+    if (w == 0) {
+        const int nw = (int)(blockDim.x >> 5);
+        mn = l < nw ? smn[l] : INT_MAX;
+        mx = l < nw ? smx[l] : INT_MIN;
+        sm = l < nw ? ssm[l] : 0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            mn = min(mn, __shfl_xor_sync(VSZ_FULL, mn, off));
+            mx = max(mx, __shfl_xor_sync(VSZ_FULL, mx, off));
+            sm += __shfl_xor_sync(VSZ_FULL, sm, off);
+        }
+        if (l == 0) {
+            int32_t P = 0;
+            if (a.g.n > 0)
+                P = a.pad_mode == VSZ_PAD_GLOBAL_MIN ? mn
+                  : a.pad_mode == VSZ_PAD_GLOBAL_MAX ? mx
+                  : rounded_mean(sm, (long long)a.g.n);
+            const_cast<vsz_header*>(a.hdr)->pad_global = P;
         }
     }
 }

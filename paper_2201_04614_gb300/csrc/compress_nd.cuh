@@ -114,8 +114,11 @@ __device__ __forceinline__ uint32_t stash_key(uint32_t fix, uint32_t g, uint32_t
 }
 
 // All the work of one tile t of one field: the walk(s), the per-block
-// padding and counts, and the tile's staged outliers and fixups.
-template <int ND, int B, bool BP>
+// padding and counts, and the tile's staged outliers and fixups.  BP: a
+// per-block padding mode; GP: a global padding mode, whose value is known
+// only once every tile has been walked, so block origins are deferred to
+// the origin pass (their q and the tile's q statistics are recorded here).
+template <int ND, int B, bool BP, bool GP>
 __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t t, unsigned char* wsm, int lane) {
     using C = NdCfg<ND, B>;
     constexpr int G = C::G;
@@ -148,8 +151,8 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
     const uint32_t lt = lanemask_lt();
     const bool vec = a.vec != 0;
     // the fp32 mode needs the global padding value itself to be small
-    const bool pg_small = BP || (Pg >= -(1 << 20) && Pg <= (1 << 20));
-    const float Pgf = (float)(BP ? 0 : Pg);
+    const bool pg_small = BP || GP || (Pg >= -(1 << 20) && Pg <= (1 << 20));
+    const float Pgf = (float)(BP || GP ? 0 : Pg);
     // a range pass that proved every |x * inv2eb| < 2^20 (and no NaN/Inf)
     // lets the fp32 mode skip its per-batch check
     const bool fast = pg_small && a.wsh->fp32_ok != 0u;
@@ -197,7 +200,7 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
 
     // results of the first pass that the second pass needs
     uint32_t cnt_out = 0, cnt_fix = 0, nst = 0;
-    int32_t Pb = BP ? 0 : Pg;
+    int32_t Pb = BP || GP ? 0 : Pg;
     uint32_t eo_g = 0, ef_g = 0;
     unsigned long long base_out = 0, base_fix = 0;
     int32_t qcorner = 0;
@@ -247,7 +250,7 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
                     store4c(a.codes + boff + (uint64_t)u * nx, valid, vst, c01, c23);
                 }
             }
-            if (BP && !emit && b0 && u == 0 && first) om &= ~1u;  // the origin waits for P
+            if (((BP && !emit) || GP) && b0 && u == 0 && first) om &= ~1u;  // the origin waits for P
             const uint32_t co = __popc(om), cf = __popc(fm);
             if (!emit) {
                 cnt_out += co;
@@ -338,11 +341,12 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
             // the padding value only enters at the tile's origin: preload it
             // into the carried difference state (3D: plane state of row 0;
             // 2D: row state)
-            if (!BP && first) {
+            if (!BP && !GP && first) {
                 if (ND == 3) zs[lane] = make_int4(__float_as_int(Pgf), 0, 0, 0);
                 else pf[0] = Pgf;
             }
             int h = 0;
+            int32_t lsum = 0;
             for (int kb = 0; kb < NB; ++kb) {
                 const int jb = kb % BPP;
                 if (kb + C::NS - 1 < NB) issue_fast(kb + C::NS - 1, (kb + C::NS - 1) % C::NS);
@@ -392,10 +396,13 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
                         const float xh = __fmul_rn(rp[k], ebx2);
                         flag |= !(fabsf(d[k]) < Rf) | !(fabsf(__fsub_rn(xv[k], xh)) <= ebf);
                     }
-                    if (BP) {
+                    if (BP || GP) {
                         sminf = fminf(sminf, fminf(fminf(rp[0], rp[1]), fminf(rp[2], rp[3])));
                         smaxf = fmaxf(smaxf, fmaxf(fmaxf(rp[0], rp[1]), fmaxf(rp[2], rp[3])));
-                        ssum += __float2int_rn(__fadd_rn(__fadd_rn(__fadd_rn(rp[0], rp[1]), rp[2]), rp[3]));
+                        // the row sum is an integer below 2^22: exact in fp32, converted by the
+                        // 1.5 * 2^23 bias; a batch's sum stays below 2^24
+                        const float rs = __fadd_rn(__fadd_rn(__fadd_rn(rp[0], rp[1]), rp[2]), rp[3]);
+                        lsum += __float_as_int(__fadd_rn(rs, kMagic)) - 0x4B400000;
                     }
                     fmask |= flag ? (1u << u) : 0u;
                     const uint32_t c01 = __byte_perm(cb[0], cb[1], 0x5410), c23 = __byte_perm(cb[2], cb[3], 0x5410);
@@ -405,10 +412,14 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
                     }
                     *reinterpret_cast<uint2*>(crow + (uint32_t)u * nx32) = make_uint2(c01, c23);
                 }
-                if (BP && kb == 0) qcorner = __float2int_rn(__int_as_float(dh[0].x));
+                if ((BP || GP) && kb == 0) qcorner = __float2int_rn(__int_as_float(dh[0].x));
                 const uint32_t rows = __reduce_or_sync(VSZ_FULL, fmask);
                 if (rows) rare_rows(rows, h, tile_base + off32(kb), jb, kb / BPP, kb == 0, false, true, false);
                 h = h + 1 == C::NS ? 0 : h + 1;
+                if (BP || GP) {
+                    ssum += lsum;
+                    lsum = 0;
+                }
             }
         } else {
         // NS-stage ring: batches kb+1 .. kb+NS-1 are in flight while batch kb is processed
@@ -502,7 +513,7 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
                         d[2] = __fsub_rn(d[2], __int_as_float(pv.z)); d[3] = __fsub_rn(d[3], __int_as_float(pv.w));
                     }
                     if (u == 0 && b0 && first) {
-                        if (BP) qcorner = __float2int_rn(rp[0]);
+                        if (BP || GP) qcorner = __float2int_rn(rp[0]);
                         else d[0] = __fsub_rn(d[0], Pgf);
                     }
                     dh[u * 32] = make_int4(__float_as_int(d[0]), __float_as_int(d[1]), __float_as_int(d[2]), __float_as_int(d[3]));
@@ -516,7 +527,7 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
                         const float xh = __fmul_rn(rp[k], ebx2);
                         flag |= !(fabsf(d[k]) < Rf) | !(fabsf(__fsub_rn(xr[u][k], xh)) <= ebf);
                     }
-                    if (BP) {
+                    if (BP || GP) {
                         float rs = 0.f;
 #pragma unroll
                         for (int k = 0; k < 4; ++k) {
@@ -566,7 +577,7 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
                         d[2] = wsub(d[2], pv.z); d[3] = wsub(d[3], pv.w);
                     }
                     if (u == 0 && b0 && first) {
-                        if (BP && !emit) qcorner = q[0];
+                        if ((BP || GP) && !emit) qcorner = q[0];
                         else d[0] = wsub(d[0], Pb);
                     }
                     dh[u * 32] = make_int4(d[0], d[1], d[2], d[3]);
@@ -576,7 +587,7 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
                     for (int k = 0; k < 4; ++k) {
                         c[k] = code_of(d[k], R);
                         flag |= (c[k] == 0u) | needs_fixup(xr[u][k], q[k], ebx2, ebf);
-                        if (BP && !emit && k < valid) {
+                        if ((BP || GP) && !emit && k < valid) {
                             smin = min(smin, q[k]);
                             smax = max(smax, q[k]);
                             ssum += q[k];
@@ -633,6 +644,21 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
                 r0c01 = (r0c01 & 0xffff0000u) | cc;
             }
             store4c(a.codes + tile_base, valid, vst, r0c01, r0c23);
+        }
+
+        if (GP) {
+            // the tile's q statistics for the global padding value; the
+            // block origins wait for it in the origin table
+            smin = min(smin, __float2int_rn(sminf));
+            smax = max(smax, __float2int_rn(smaxf));
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                smin = min(smin, __shfl_xor_sync(VSZ_FULL, smin, off));
+                smax = max(smax, __shfl_xor_sync(VSZ_FULL, smax, off));
+                ssum += __shfl_xor_sync(VSZ_FULL, ssum, off);
+            }
+            if (lane == 0) a.tstats[t] = TileStats{smin, smax, ssum};
+            if (first && bexists) a.origin[blk] = qcorner;
         }
 
         // Per-block counts, in-tile exclusive offsets (blk_off), tile totals.
@@ -720,7 +746,7 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
 }
 
 // One field: tiles handed out by the field's own ticket.
-template <int ND, int B, bool BP>
+template <int ND, int B, bool BP, bool GP>
 __global__ void __launch_bounds__(NdCfg<ND, B>::THREADS, NdCfg<ND, B>::MINB_C)
 k_lorenzo_nd(const CompressArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -731,14 +757,14 @@ k_lorenzo_nd(const CompressArgs a) {
         if (lane == 0) tk = atomicAdd(&a.wsh->ticket, 1ull);
         const uint64_t t = __shfl_sync(VSZ_FULL, tk, 0);
         if (t >= a.g.ntiles) break;
-        nd_compress_tile<ND, B, BP>(a, t, wsm, lane);
+        nd_compress_tile<ND, B, BP, GP>(a, t, wsm, lane);
     }
 }
 
 // Many fields of one class (rank, block edge, padding kind): one queue over
 // the tiles of all of them.  tile_prefix[f] is the first global tile of field
 // f, tile_prefix[nfields] the total.
-template <int ND, int B, bool BP>
+template <int ND, int B, bool BP, bool GP>
 __global__ void __launch_bounds__(NdCfg<ND, B>::THREADS, NdCfg<ND, B>::MINB_C)
 k_lorenzo_nd_batch(const CompressArgs* __restrict__ fields, const uint64_t* __restrict__ tile_prefix, int nfields,
                    unsigned long long* ticket) {
@@ -756,7 +782,7 @@ k_lorenzo_nd_batch(const CompressArgs* __restrict__ fields, const uint64_t* __re
             const int mid = (lo + hi + 1) >> 1;
             if (tile_prefix[mid] <= gt) lo = mid; else hi = mid - 1;
         }
-        nd_compress_tile<ND, B, BP>(fields[lo], gt - tile_prefix[lo], wsm, lane);
+        nd_compress_tile<ND, B, BP, GP>(fields[lo], gt - tile_prefix[lo], wsm, lane);
     }
 }
 

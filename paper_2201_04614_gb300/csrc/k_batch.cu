@@ -7,9 +7,10 @@
 //   k_batch_begin         one CTA per field: workspace and header set-up;
 //   k_batch_range         value range of every relative-eb field, items of
 //                         1M elements; the last item of a field resolves eb;
-//   k_batch_qstats        min / max / sum of q of every global-padding field;
 //   k_lorenzo_*_batch     per class, one persistent kernel drawing tiles of
 //                         all the class's fields from one ticket;
+//   k_batch_origin_fix    block origins of every global-padding field, once
+//                         the field's padding value is known;
 //   k_batch_compact_scan  one CTA per field: chunk offsets and totals;
 //   k_batch_compact_move  one CTA per chunk of any field: final placement.
 // The sequence can be captured into a CUDA graph once and replayed.
@@ -34,7 +35,7 @@ struct BatchField {
     CompressArgs a;     // the field's pointers, geometry and workspace
     double eb;          // user error bound
     int32_t rel;        // value-range relative bound
-    int32_t gpad;       // a global padding mode (needs the q statistics)
+    int32_t gpad;       // a global padding mode (its block origins wait for the origin pass)
 };
 
 // Index of the last entry of prefix[0..n) that is <= v (prefix[0] == 0).
@@ -139,68 +140,19 @@ __global__ void __launch_bounds__(256) k_batch_range(const BatchField* __restric
     }
 }
 
-// Min / max / sum of q of every global-padding field; the last item of a
-// field sets its padding value.
-__global__ void __launch_bounds__(256) k_batch_qstats(const BatchField* __restrict__ F, int nf,
-                                                      const uint64_t* __restrict__ prefix, uint64_t nitems) {
-    __shared__ int smi[32];
-    __shared__ long long sml[32];
-    for (uint64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
+// Global padding value of every global-padding field (one CTA per field).
+__global__ void __launch_bounds__(1024) k_batch_pad_reduce(const BatchField* __restrict__ F) {
+    if (F[blockIdx.x].gpad) pad_reduce_body(F[blockIdx.x].a);
+}
+
+// Origin pass of every global-padding field: items are blocks.
+__global__ void __launch_bounds__(256) k_batch_origin_fix(const BatchField* __restrict__ F, int nf,
+                                                          const uint64_t* __restrict__ prefix, uint64_t nitems) {
+    for (uint64_t item = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; item < nitems;
+         item += (uint64_t)gridDim.x * blockDim.x) {
         const int f = find_field(prefix, nf, item);
-        const BatchField& b = F[f];
-        const uint64_t n = b.a.g.n;
-        const uint64_t i0 = (item - prefix[f]) * kItemElems, i1 = umin64(n, i0 + kItemElems);
-        const float* x = b.a.x;
-        const float inv2eb = b.a.hdr->inv2eb;
-        int qlo = INT_MAX, qhi = INT_MIN;
-        long long qs = 0;
-        auto take = [&](float v) {
-            const int q = prequant(v, inv2eb);
-            qlo = min(qlo, q);
-            qhi = max(qhi, q);
-            qs += q;
-        };
-        if (b.a.vec) {
-            // four 16-byte loads in flight per thread
-            uint64_t i = i0 + 4 * threadIdx.x;
-            for (; i + 12 * blockDim.x + 3 < i1; i += 16 * blockDim.x) {
-                float4 v[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) v[u] = ld_stream_f4(x + i + 4 * u * blockDim.x);
-#pragma unroll
-                for (int u = 0; u < 4; ++u) { take(v[u].x); take(v[u].y); take(v[u].z); take(v[u].w); }
-            }
-            for (; i + 3 < i1; i += 4 * blockDim.x) {
-                const float4 v = ld_stream_f4(x + i);
-                take(v.x); take(v.y); take(v.z); take(v.w);
-            }
-            for (uint64_t k = i0 + ((i1 - i0) & ~3ull) + threadIdx.x; k < i1; k += blockDim.x) take(x[k]);
-        } else {
-            for (uint64_t k = i0 + threadIdx.x; k < i1; k += blockDim.x) take(x[k]);
-        }
-        qlo = block_reduce(qlo, OpMin(), smi, INT_MAX);
-        qhi = block_reduce(qhi, OpMax(), smi, INT_MIN);
-        qs = block_reduce(qs, OpAdd(), sml, 0ll);
-        if (threadIdx.x == 0) {
-            WsHeader* w = b.a.wsh;
-            atomicMin(&w->qmin, qlo);
-            atomicMax(&w->qmax, qhi);
-            atomicAdd(&w->qsum, (unsigned long long)qs);
-            __threadfence();
-            if (atomicAdd(&w->done1, 1u) == (unsigned)(prefix[f + 1] - prefix[f] - 1)) {
-                __threadfence();
-                const int l = atomicAdd(&w->qmin, 0);
-                const int h = atomicAdd(&w->qmax, 0);
-                const long long S = (long long)atomicAdd(&w->qsum, 0ull);
-                int32_t P = 0;
-                if (n > 0) {
-                    const int m = b.a.pad_mode;
-                    P = m == VSZ_PAD_GLOBAL_MIN ? l : m == VSZ_PAD_GLOBAL_MAX ? h : rounded_mean(S, (long long)n);
-                }
-                const_cast<vsz_header*>(b.a.hdr)->pad_global = P;
-            }
-        }
-        __syncthreads();
+        const CompressArgs& a = F[f].a;
+        origin_fix_block(a, item - prefix[f], a.hdr->pad_global);
     }
 }
 
@@ -216,9 +168,7 @@ __global__ void __launch_bounds__(256) k_batch_compact_move(const BatchField* __
     for (uint64_t item = blockIdx.x; item < nchunks; item += gridDim.x) {
         const int f = find_field(prefix, nf, item);
         const CompressArgs& a = F[f].a;
-        compact_chunk_body(item - prefix[f], a.tiles, a.chunks, a.g.ntiles, a.g.nseg, a.g.nbx, a.g.bpt, a.blk_off,
-                           a.stage_out, a.stage_fix, a.out_idx, a.out_delta, a.out_cap, a.fix_idx, a.fix_bits,
-                           a.fix_cap);
+        compact_chunk_body(item - prefix[f], a);
         __syncthreads();
     }
 }
@@ -233,7 +183,7 @@ using namespace vsz;
 struct BatchClass {
     int nd;
     uint32_t b;
-    bool bp;
+    int pk;                        // 0 zero padding, 1 per-block padding, 2 global padding
     std::vector<int> fields;       // indices into the batch
     CompressArgs* d_args = nullptr;
     uint64_t* d_prefix = nullptr;
@@ -247,9 +197,9 @@ struct vsz_batch_st {
     std::vector<BatchClass> classes;
     BatchField* d_fields = nullptr;
     uint64_t* d_range_prefix = nullptr;
-    uint64_t* d_q_prefix = nullptr;
+    uint64_t* d_ob_prefix = nullptr;    // blocks of the global-padding fields
     uint64_t* d_chunk_prefix = nullptr;
-    uint64_t range_items = 0, q_items = 0, chunks = 0;
+    uint64_t range_items = 0, origin_items = 0, chunks = 0;
     unsigned long long* tickets = nullptr;  // in the caller's workspace
     bool use_graph = false;
     cudaGraphExec_t exec = nullptr;
@@ -277,7 +227,7 @@ static void free_batch(vsz_batch_st* b) {
     }
     if (b->d_fields) cudaFree(b->d_fields);
     if (b->d_range_prefix) cudaFree(b->d_range_prefix);
-    if (b->d_q_prefix) cudaFree(b->d_q_prefix);
+    if (b->d_ob_prefix) cudaFree(b->d_ob_prefix);
     if (b->d_chunk_prefix) cudaFree(b->d_chunk_prefix);
     delete b;
 }
@@ -304,23 +254,24 @@ static vsz_status launch_sequence(vsz_batch_st* b, cudaStream_t s) {
         k_batch_range<<<grid, 256, 0, s>>>(b->d_fields, b->n, b->d_range_prefix, b->range_items);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
     }
-    if (b->q_items) {
-        TraceScope ts("batch_qstats", s);
-        const int grid = grid_for((const void*)k_batch_qstats, 256, 0, 1, b->q_items);
-        k_batch_qstats<<<grid, 256, 0, s>>>(b->d_fields, b->n, b->d_q_prefix, b->q_items);
-        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
-    }
     for (size_t c = 0; c < b->classes.size(); ++c) {
         BatchClass& k = b->classes[c];
         if (!k.total_tiles) continue;
         TraceScope ts("batch_lorenzo", s, k.nd, k.b);
-        e = k.nd == 1 ? launch_lorenzo_batch_1d(k.b, k.bp, k.d_args, k.d_prefix, (int)k.fields.size(), k.total_tiles,
+        e = k.nd == 1 ? launch_lorenzo_batch_1d(k.b, k.pk, k.d_args, k.d_prefix, (int)k.fields.size(), k.total_tiles,
                                                 b->tickets + c, s)
-          : k.nd == 2 ? launch_lorenzo_batch_2d(k.b, k.bp, k.d_args, k.d_prefix, (int)k.fields.size(), k.total_tiles,
+          : k.nd == 2 ? launch_lorenzo_batch_2d(k.b, k.pk, k.d_args, k.d_prefix, (int)k.fields.size(), k.total_tiles,
                                                 b->tickets + c, s)
-                      : launch_lorenzo_batch_3d(k.b, k.bp, k.d_args, k.d_prefix, (int)k.fields.size(), k.total_tiles,
+                      : launch_lorenzo_batch_3d(k.b, k.pk, k.d_args, k.d_prefix, (int)k.fields.size(), k.total_tiles,
                                                 b->tickets + c, s);
         if (e != cudaSuccess) return cuda_fail(e);
+    }
+    if (b->origin_items) {
+        TraceScope ts("batch_origin_fix", s);
+        k_batch_pad_reduce<<<b->n, 1024, 0, s>>>(b->d_fields);
+        const int grid = grid_for((const void*)k_batch_origin_fix, 256, 0, 256, b->origin_items);
+        k_batch_origin_fix<<<grid, 256, 0, s>>>(b->d_fields, b->n, b->d_ob_prefix, b->origin_items);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
     }
     {
         TraceScope ts("batch_compact_scan", s);
@@ -366,7 +317,7 @@ vsz_status vsz_batch_create(const vsz_field_job* jobs, int njobs, void* d_ws, si
     char* ws = (char*)d_ws;
     b->tickets = (unsigned long long*)ws;
     std::vector<uint64_t> rp(1, 0), qp(1, 0), cp(1, 0);
-    std::map<std::tuple<int, uint32_t, bool>, int> cls;
+    std::map<std::tuple<int, uint32_t, int>, int> cls;
     for (int i = 0; i < njobs; ++i) {
         const vsz_field_job& j = jobs[i];
         const Geom& g = geoms[i];
@@ -385,6 +336,11 @@ vsz_status vsz_batch_create(const vsz_field_job* jobs, int njobs, void* d_ws, si
         a.chunks = (uint4*)(fw + L.chunks);
         a.stage_out = (uint2*)(fw + L.stage_out);
         a.stage_fix = (uint2*)(fw + L.stage_fix);
+        if (is_global_pad(j.params.pad)) {
+            a.tstats = (TileStats*)(fw + L.tstats);
+            a.origin = (int32_t*)(fw + L.origin);
+            a.oflag = (uint8_t*)(fw + L.oflag);
+        }
         a.out_idx = j.out.out_idx;
         a.out_delta = j.out.out_delta;
         a.fix_idx = j.out.fix_idx;
@@ -402,15 +358,16 @@ vsz_status vsz_batch_create(const vsz_field_job* jobs, int njobs, void* d_ws, si
         b->fields.push_back(bf);
         const uint64_t items = (g.n + kItemElems - 1) / kItemElems;
         rp.push_back(rp.back() + (bf.rel ? (items ? items : 1) : 0));
-        qp.push_back(qp.back() + (bf.gpad ? (items ? items : 1) : 0));
+        qp.push_back(qp.back() + (bf.gpad ? g.nb : 0));
         cp.push_back(cp.back() + g.nchunks);
-        const auto key = std::make_tuple(g.nd, g.b, is_block_pad(j.params.pad));
+        const int pk = is_block_pad(j.params.pad) ? 1 : bf.gpad ? 2 : 0;
+        const auto key = std::make_tuple(g.nd, g.b, pk);
         auto it = cls.find(key);
         if (it == cls.end()) {
             BatchClass c;
             c.nd = g.nd;
             c.b = g.b;
-            c.bp = is_block_pad(j.params.pad);
+            c.pk = pk;
             b->classes.push_back(c);
             it = cls.emplace(key, (int)b->classes.size() - 1).first;
         }
@@ -418,11 +375,11 @@ vsz_status vsz_batch_create(const vsz_field_job* jobs, int njobs, void* d_ws, si
     }
     if ((int)b->classes.size() > kMaxClasses) { free_batch(b); return VSZ_ERR_UNSUPPORTED; }
     b->range_items = rp.back();
-    b->q_items = qp.back();
+    b->origin_items = qp.back();
     b->chunks = cp.back();
     cudaError_t e = upload(&b->d_fields, b->fields);
     if (e == cudaSuccess) e = upload(&b->d_range_prefix, rp);
-    if (e == cudaSuccess) e = upload(&b->d_q_prefix, qp);
+    if (e == cudaSuccess) e = upload(&b->d_ob_prefix, qp);
     if (e == cudaSuccess) e = upload(&b->d_chunk_prefix, cp);
     for (BatchClass& c : b->classes) {
         if (e != cudaSuccess) break;

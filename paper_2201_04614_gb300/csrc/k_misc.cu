@@ -83,64 +83,6 @@ __global__ void __launch_bounds__(256) k_range(const float* __restrict__ x, uint
     }
 }
 
-// Global min / max / sum of q (Sec. IV-B-1); the last block sets P.
-__global__ void __launch_bounds__(256) k_qstats(const float* __restrict__ x, uint64_t n, WsHeader* wsh,
-                                                vsz_header* hdr, int pad_mode, int vec) {
-    __shared__ int smi[32];
-    __shared__ long long sml[32];
-    __shared__ bool last;
-    const float inv2eb = hdr->inv2eb;
-    int qlo = INT_MAX, qhi = INT_MIN;
-    long long qs = 0;
-    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const uint64_t nth = (uint64_t)gridDim.x * blockDim.x;
-    if (vec) {
-        const uint64_t n4 = n / 4;
-        for (uint64_t i = tid; i < n4; i += nth) {
-            const float4 v = ld_stream_f4(x + 4 * i);
-            const float a[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int q = prequant(a[k], inv2eb);
-                qlo = min(qlo, q); qhi = max(qhi, q); qs += q;
-            }
-        }
-        for (uint64_t i = 4 * n4 + tid; i < n; i += nth) {
-            const int q = prequant(x[i], inv2eb);
-            qlo = min(qlo, q); qhi = max(qhi, q); qs += q;
-        }
-    } else {
-        for (uint64_t i = tid; i < n; i += nth) {
-            const int q = prequant(x[i], inv2eb);
-            qlo = min(qlo, q); qhi = max(qhi, q); qs += q;
-        }
-    }
-    qlo = block_reduce(qlo, OpMin(), smi, INT_MAX);
-    qhi = block_reduce(qhi, OpMax(), smi, INT_MIN);
-    qs = block_reduce(qs, OpAdd(), sml, 0ll);
-    if (threadIdx.x == 0) {
-        atomicMin(&wsh->qmin, qlo);
-        atomicMax(&wsh->qmax, qhi);
-        atomicAdd(&wsh->qsum, (unsigned long long)qs);
-        __threadfence();
-        last = atomicAdd(&wsh->done1, 1u) == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (last && threadIdx.x == 0) {
-        __threadfence();
-        const int l = atomicAdd(&wsh->qmin, 0);
-        const int h = atomicAdd(&wsh->qmax, 0);
-        const long long S = (long long)atomicAdd(&wsh->qsum, 0ull);
-        int32_t P = 0;
-        if (n > 0) {
-            P = pad_mode == VSZ_PAD_GLOBAL_MIN ? l
-              : pad_mode == VSZ_PAD_GLOBAL_MAX ? h
-              : rounded_mean(S, (long long)n);
-        }
-        hdr->pad_global = P;
-    }
-}
-
 // Compaction of one field (bodies in compact.cuh).
 __global__ void __launch_bounds__(1024) k_compact_scan(uint4* chunks, uint64_t nchunks, vsz_header* hdr,
                                                        uint32_t* blk_off, uint64_t nb, uint64_t out_cap,
@@ -148,14 +90,17 @@ __global__ void __launch_bounds__(1024) k_compact_scan(uint4* chunks, uint64_t n
     compact_scan_body(chunks, nchunks, hdr, blk_off, nb, out_cap, fix_cap);
 }
 
-__global__ void __launch_bounds__(256) k_compact(const uint4* __restrict__ tiles, const uint4* __restrict__ chunks,
-                                                 uint64_t ntiles, uint64_t nseg, uint64_t nbx, uint32_t bpt,
-                                                 uint32_t* blk_off, const uint2* __restrict__ stage_out,
-                                                 const uint2* __restrict__ stage_fix, uint32_t* out_idx,
-                                                 int32_t* out_delta, uint64_t out_cap, uint32_t* fix_idx,
-                                                 uint32_t* fix_bits, uint64_t fix_cap) {
-    compact_chunk_body(blockIdx.x, tiles, chunks, ntiles, nseg, nbx, bpt, blk_off, stage_out, stage_fix, out_idx,
-                       out_delta, out_cap, fix_idx, fix_bits, fix_cap);
+__global__ void __launch_bounds__(256) k_compact(const CompressArgs a) { compact_chunk_body(blockIdx.x, a); }
+
+// Global padding value of one field from its tiles' q statistics.
+__global__ void __launch_bounds__(1024) k_pad_reduce(const CompressArgs a) { pad_reduce_body(a); }
+
+// Origin pass of a global padding mode (one field): every block origin's
+// residual q - P and its code, P from the field's header.
+__global__ void __launch_bounds__(256) k_origin_fix(const CompressArgs a) {
+    const int32_t P = a.hdr->pad_global;
+    for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < a.g.nb; b += (uint64_t)gridDim.x * blockDim.x)
+        origin_fix_block(a, b, P);
 }
 
 // Fixups restore their values verbatim after the inverse.
@@ -210,27 +155,24 @@ cudaError_t launch_range(const float* x, uint64_t n, WsHeader* wsh, vsz_header* 
     return cudaGetLastError();
 }
 
-cudaError_t launch_qstats(const float* x, uint64_t n, WsHeader* wsh, vsz_header* hdr, int pad_mode, bool vec,
-                          cudaStream_t s) {
-    const int grid = grid_for((const void*)k_qstats, 256, 0, 256 * 16, n);
-    k_qstats<<<grid, 256, 0, s>>>(x, n, wsh, hdr, pad_mode, vec ? 1 : 0);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_compact_scan(const Geom& g, uint4* chunks, vsz_header* hdr, uint32_t* blk_off,
                                 uint64_t out_cap, uint64_t fix_cap, cudaStream_t s) {
     k_compact_scan<<<1, 1024, 0, s>>>(chunks, g.nchunks, hdr, blk_off, g.nb, out_cap, fix_cap);
     return cudaGetLastError();
 }
 
-cudaError_t launch_compact_move(const Geom& g, const uint4* tiles, const uint4* chunks, uint32_t* blk_off,
-                                const uint2* stage_out, const uint2* stage_fix, uint32_t* out_idx,
-                                int32_t* out_delta, uint64_t out_cap, uint32_t* fix_idx, uint32_t* fix_bits,
-                                uint64_t fix_cap, cudaStream_t s) {
-    if (g.nchunks == 0) return cudaSuccess;
-    k_compact<<<(unsigned)g.nchunks, 256, 0, s>>>(tiles, chunks, g.ntiles, g.nseg, g.nbx, g.bpt, blk_off,
-                                                  stage_out, stage_fix, out_idx, out_delta, out_cap, fix_idx,
-                                                  fix_bits, fix_cap);
+cudaError_t launch_compact_move(const CompressArgs& a, cudaStream_t s) {
+    if (a.g.nchunks == 0) return cudaSuccess;
+    k_compact<<<(unsigned)a.g.nchunks, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_origin_fix(const CompressArgs& a, cudaStream_t s) {
+    k_pad_reduce<<<1, 1024, 0, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || a.g.nb == 0) return e;
+    const int grid = grid_for((const void*)k_origin_fix, 256, 0, 256, a.g.nb);
+    k_origin_fix<<<grid, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 

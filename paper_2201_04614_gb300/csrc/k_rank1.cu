@@ -41,7 +41,9 @@ __device__ __forceinline__ void load_epl(const float* __restrict__ p, int valid,
 }
 
 // One step of 32*EPL elements: prequant, padding value, residual, codes.
-template <int B, bool BP>
+// GP (a global padding mode): the residual at each block origin is left as
+// q itself; the origin pass settles it once the field's statistics are known.
+template <int B, bool BP, bool GP>
 struct Step1 {
     static constexpr int EPL = Cfg1<B>::EPL;
     static constexpr int G = Cfg1<B>::G;
@@ -58,7 +60,7 @@ struct Step1 {
 #pragma unroll
         for (int k = 0; k < EPL; ++k) q[k] = prequant(x[k], inv2eb);
         const int glane = lane & (G - 1);
-        P = Pg;
+        P = GP ? 0 : Pg;
         if (BP) {
             int32_t smin = INT_MAX, smax = INT_MIN;
             long long ssum = 0;
@@ -85,7 +87,7 @@ struct Step1 {
 };
 
 // All the work of one 4096-element tile t of a 1D field.
-template <int B, bool BP>
+template <int B, bool BP, bool GP>
 __device__ __forceinline__ void compress_1d_tile(const CompressArgs& a, uint64_t t, int lane) {
     using C = Cfg1<B>;
     constexpr int EPL = C::EPL, G = C::G, SPAN = C::SPAN;
@@ -98,12 +100,14 @@ __device__ __forceinline__ void compress_1d_tile(const CompressArgs& a, uint64_t
     const int glane = lane & (G - 1);
     const uint64_t start = t * kChunk1D;
     uint32_t run_out = 0, run_fix = 0, stepmask = 0;
+    int32_t gmin = INT_MAX, gmax = INT_MIN;  // q statistics of the tile (global padding)
+    long long gsum = 0;
 #pragma unroll 2
     for (int st = 0; st < C::STEPS; ++st) {
         const uint64_t s0 = start + (uint64_t)st * SPAN;
         if (s0 >= n) break;
         const uint64_t base = s0 + (uint64_t)lane * EPL;
-        Step1<B, BP> S;
+        Step1<B, BP, GP> S;
         S.run(a, base, lane, inv2eb, Pg);
         uint32_t co = 0, cf = 0;
         uint32_t c[EPL];
@@ -111,8 +115,13 @@ __device__ __forceinline__ void compress_1d_tile(const CompressArgs& a, uint64_t
         for (int k = 0; k < EPL; ++k) {
             c[k] = code_of(S.d[k], R);
             if (k < S.valid) {
-                co += (c[k] == 0u);
+                co += (c[k] == 0u && !(GP && k == 0 && glane == 0));
                 cf += needs_fixup(S.x[k], S.q[k], ebx2, ebf) ? 1u : 0u;
+                if (GP) {
+                    gmin = min(gmin, S.q[k]);
+                    gmax = max(gmax, S.q[k]);
+                    gsum += S.q[k];
+                }
             }
         }
         // in-step exclusive prefix of outliers -> per-block offsets
@@ -129,6 +138,7 @@ __device__ __forceinline__ void compress_1d_tile(const CompressArgs& a, uint64_t
             const uint64_t blk = base / B;
             a.blk_off[blk] = run_out + (io - co);
             if (BP) a.pad[blk] = S.P;
+            if (GP) a.origin[blk] = S.q[0];
         }
         run_out += so;
         run_fix += sf;
@@ -150,6 +160,15 @@ __device__ __forceinline__ void compress_1d_tile(const CompressArgs& a, uint64_t
         }
     }
 
+    if (GP) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            gmin = min(gmin, __shfl_xor_sync(VSZ_FULL, gmin, off));
+            gmax = max(gmax, __shfl_xor_sync(VSZ_FULL, gmax, off));
+            gsum += __shfl_xor_sync(VSZ_FULL, gsum, off);
+        }
+        if (lane == 0) a.tstats[t] = TileStats{gmin, gmax, gsum};
+    }
     unsigned long long base_out = 0, base_fix = 0;
     if (run_out | run_fix) {
         if (lane == 0) {
@@ -170,13 +189,13 @@ __device__ __forceinline__ void compress_1d_tile(const CompressArgs& a, uint64_t
         const int st = __ffs(stepmask) - 1;
         stepmask &= stepmask - 1;
         const uint64_t base = start + (uint64_t)st * SPAN + (uint64_t)lane * EPL;
-        Step1<B, BP> S;
+        Step1<B, BP, GP> S;
         S.run(a, base, lane, inv2eb, Pg);
         uint32_t mo = 0, mf = 0;  // per-element flags of this lane
 #pragma unroll
         for (int k = 0; k < EPL; ++k) {
             if (k < S.valid) {
-                if (code_of(S.d[k], R) == 0u) mo |= 1u << k;
+                if (code_of(S.d[k], R) == 0u && !(GP && k == 0 && glane == 0)) mo |= 1u << k;
                 if (needs_fixup(S.x[k], S.q[k], ebx2, ebf)) mf |= 1u << k;
             }
         }
@@ -206,7 +225,7 @@ __device__ __forceinline__ void compress_1d_tile(const CompressArgs& a, uint64_t
 }
 
 // One field: tiles handed out by the field's own ticket.
-template <int B, bool BP>
+template <int B, bool BP, bool GP>
 __global__ void __launch_bounds__(256) k_lorenzo_1d(const CompressArgs a) {
     const int lane = threadIdx.x & 31;
     for (;;) {
@@ -214,13 +233,13 @@ __global__ void __launch_bounds__(256) k_lorenzo_1d(const CompressArgs a) {
         if (lane == 0) tk = atomicAdd(&a.wsh->ticket, 1ull);
         const uint64_t t = __shfl_sync(VSZ_FULL, tk, 0);
         if (t >= a.g.ntiles) break;
-        compress_1d_tile<B, BP>(a, t, lane);
+        compress_1d_tile<B, BP, GP>(a, t, lane);
     }
 }
 
 // Many 1D fields with the same block length and padding kind: one queue
 // over all their tiles (tile_prefix as for the 2D/3D batch kernel).
-template <int B, bool BP>
+template <int B, bool BP, bool GP>
 __global__ void __launch_bounds__(256) k_lorenzo_1d_batch(const CompressArgs* __restrict__ fields,
                                                           const uint64_t* __restrict__ tile_prefix, int nfields,
                                                           unsigned long long* ticket) {
@@ -236,7 +255,7 @@ __global__ void __launch_bounds__(256) k_lorenzo_1d_batch(const CompressArgs* __
             const int mid = (lo + hi + 1) >> 1;
             if (tile_prefix[mid] <= gt) lo = mid; else hi = mid - 1;
         }
-        compress_1d_tile<B, BP>(fields[lo], gt - tile_prefix[lo], lane);
+        compress_1d_tile<B, BP, GP>(fields[lo], gt - tile_prefix[lo], lane);
     }
 }
 
@@ -356,24 +375,37 @@ __global__ void __launch_bounds__(256) k_recon_1d(const ReconArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-template <int B>
-static cudaError_t launch_c1(const CompressArgs& a, cudaStream_t s) {
-    const bool bp = is_block_pad(a.pad_mode);
-    const void* k = bp ? (const void*)k_lorenzo_1d<B, true> : (const void*)k_lorenzo_1d<B, false>;
+template <int B, bool BP, bool GP>
+static cudaError_t launch_c1_k(const CompressArgs& a, cudaStream_t s) {
+    const void* k = (const void*)k_lorenzo_1d<B, BP, GP>;
     const int grid = grid_for(k, 256, 0, Cfg1<B>::WARPS, a.g.ntiles);
-    if (bp) k_lorenzo_1d<B, true><<<grid, 256, 0, s>>>(a);
-    else k_lorenzo_1d<B, false><<<grid, 256, 0, s>>>(a);
+    k_lorenzo_1d<B, BP, GP><<<grid, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 
 template <int B>
-static cudaError_t launch_c1_batch(bool bp, const CompressArgs* fields, const uint64_t* tile_prefix, int nfields,
-                                   uint64_t total_tiles, unsigned long long* ticket, cudaStream_t s) {
-    const void* k = bp ? (const void*)k_lorenzo_1d_batch<B, true> : (const void*)k_lorenzo_1d_batch<B, false>;
+static cudaError_t launch_c1(const CompressArgs& a, cudaStream_t s) {
+    if (is_block_pad(a.pad_mode)) return launch_c1_k<B, true, false>(a, s);
+    if (is_global_pad(a.pad_mode)) return launch_c1_k<B, false, true>(a, s);
+    return launch_c1_k<B, false, false>(a, s);
+}
+
+template <int B, bool BP, bool GP>
+static cudaError_t launch_c1_batch_k(const CompressArgs* fields, const uint64_t* tile_prefix, int nfields,
+                                     uint64_t total_tiles, unsigned long long* ticket, cudaStream_t s) {
+    const void* k = (const void*)k_lorenzo_1d_batch<B, BP, GP>;
     const int grid = grid_for(k, 256, 0, Cfg1<B>::WARPS, total_tiles);
-    if (bp) k_lorenzo_1d_batch<B, true><<<grid, 256, 0, s>>>(fields, tile_prefix, nfields, ticket);
-    else k_lorenzo_1d_batch<B, false><<<grid, 256, 0, s>>>(fields, tile_prefix, nfields, ticket);
+    k_lorenzo_1d_batch<B, BP, GP><<<grid, 256, 0, s>>>(fields, tile_prefix, nfields, ticket);
     return cudaGetLastError();
+}
+
+// pk: 0 zero padding, 1 per-block padding, 2 global padding
+template <int B>
+static cudaError_t launch_c1_batch(int pk, const CompressArgs* fields, const uint64_t* tile_prefix, int nfields,
+                                   uint64_t total_tiles, unsigned long long* ticket, cudaStream_t s) {
+    if (pk == 1) return launch_c1_batch_k<B, true, false>(fields, tile_prefix, nfields, total_tiles, ticket, s);
+    if (pk == 2) return launch_c1_batch_k<B, false, true>(fields, tile_prefix, nfields, total_tiles, ticket, s);
+    return launch_c1_batch_k<B, false, false>(fields, tile_prefix, nfields, total_tiles, ticket, s);
 }
 
 template <int B>
@@ -399,16 +431,16 @@ cudaError_t launch_lorenzo_1d(const CompressArgs& a, cudaStream_t s) {
     }
 }
 
-cudaError_t launch_lorenzo_batch_1d(uint32_t b, bool bp, const CompressArgs* fields, const uint64_t* tile_prefix,
+cudaError_t launch_lorenzo_batch_1d(uint32_t b, int pk, const CompressArgs* fields, const uint64_t* tile_prefix,
                                     int nfields, uint64_t total_tiles, unsigned long long* ticket, cudaStream_t s) {
     switch (b) {
-    case 4: return launch_c1_batch<4>(bp, fields, tile_prefix, nfields, total_tiles, ticket, s);
-    case 8: return launch_c1_batch<8>(bp, fields, tile_prefix, nfields, total_tiles, ticket, s);
-    case 16: return launch_c1_batch<16>(bp, fields, tile_prefix, nfields, total_tiles, ticket, s);
-    case 32: return launch_c1_batch<32>(bp, fields, tile_prefix, nfields, total_tiles, ticket, s);
-    case 64: return launch_c1_batch<64>(bp, fields, tile_prefix, nfields, total_tiles, ticket, s);
-    case 128: return launch_c1_batch<128>(bp, fields, tile_prefix, nfields, total_tiles, ticket, s);
-    case 256: return launch_c1_batch<256>(bp, fields, tile_prefix, nfields, total_tiles, ticket, s);
+    case 4: return launch_c1_batch<4>(pk, fields, tile_prefix, nfields, total_tiles, ticket, s);
+    case 8: return launch_c1_batch<8>(pk, fields, tile_prefix, nfields, total_tiles, ticket, s);
+    case 16: return launch_c1_batch<16>(pk, fields, tile_prefix, nfields, total_tiles, ticket, s);
+    case 32: return launch_c1_batch<32>(pk, fields, tile_prefix, nfields, total_tiles, ticket, s);
+    case 64: return launch_c1_batch<64>(pk, fields, tile_prefix, nfields, total_tiles, ticket, s);
+    case 128: return launch_c1_batch<128>(pk, fields, tile_prefix, nfields, total_tiles, ticket, s);
+    case 256: return launch_c1_batch<256>(pk, fields, tile_prefix, nfields, total_tiles, ticket, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -15,15 +15,15 @@ cudaError_t launch_lorenzo_2d(const CompressArgs& a, cudaStream_t s) {
     }
 }
 
-cudaError_t launch_lorenzo_batch_2d(uint32_t b, bool bp, const CompressArgs* fields, const uint64_t* tile_prefix,
+cudaError_t launch_lorenzo_batch_2d(uint32_t b, int pk, const CompressArgs* fields, const uint64_t* tile_prefix,
                                     int nfields, uint64_t total_tiles, unsigned long long* ticket, cudaStream_t s) {
     switch (b) {
-    case 4: return launch_nd_compress_batch<2, 4>(bp, fields, tile_prefix, nfields, total_tiles, ticket, s);
-    case 8: return launch_nd_compress_batch<2, 8>(bp, fields, tile_prefix, nfields, total_tiles, ticket, s);
-    case 16: return launch_nd_compress_batch<2, 16>(bp, fields, tile_prefix, nfields, total_tiles, ticket, s);
-    case 32: return launch_nd_compress_batch<2, 32>(bp, fields, tile_prefix, nfields, total_tiles, ticket, s);
-    case 64: return launch_nd_compress_batch<2, 64>(bp, fields, tile_prefix, nfields, total_tiles, ticket, s);
-    case 128: return launch_nd_compress_batch<2, 128>(bp, fields, tile_prefix, nfields, total_tiles, ticket, s);
+    case 4: return launch_nd_compress_batch<2, 4>(pk, fields, tile_prefix, nfields, total_tiles, ticket, s);
+    case 8: return launch_nd_compress_batch<2, 8>(pk, fields, tile_prefix, nfields, total_tiles, ticket, s);
+    case 16: return launch_nd_compress_batch<2, 16>(pk, fields, tile_prefix, nfields, total_tiles, ticket, s);
+    case 32: return launch_nd_compress_batch<2, 32>(pk, fields, tile_prefix, nfields, total_tiles, ticket, s);
+    case 64: return launch_nd_compress_batch<2, 64>(pk, fields, tile_prefix, nfields, total_tiles, ticket, s);
+    case 128: return launch_nd_compress_batch<2, 128>(pk, fields, tile_prefix, nfields, total_tiles, ticket, s);
     default: return cudaErrorInvalidValue;
     }
 }

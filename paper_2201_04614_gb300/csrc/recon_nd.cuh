@@ -34,8 +34,11 @@ k_recon_nd(const ReconArgs a) {
     const int wib = threadIdx.x >> 5;
     unsigned char* wsm = smem_raw + (size_t)wib * C::WARP_R;
     int4* zs = reinterpret_cast<int4*>(wsm + C::RING_R);
-    uint32_t* oc_idx = reinterpret_cast<uint32_t*>(wsm + C::RING_R + C::ZS_B);
-    int32_t* oc_del = reinterpret_cast<int32_t*>(oc_idx + C::OCAP);
+    uint32_t* const oc_idx0 = reinterpret_cast<uint32_t*>(wsm + C::RING_R + C::ZS_B);
+    // interior tiles of 3D blocks up to 8 keep their z sums in registers, so
+    // their outlier cache may also take the z-state area in front of it
+    constexpr bool ZREG_R = ND == 3 && B <= 8;
+    constexpr uint32_t OCAP_BIG = (uint32_t)((C::ZS_B + C::OC_B) / 8);
     const uint2* ring_rd = reinterpret_cast<const uint2*>(wsm) + lane;  // slot (h*U + u)*32
     const uint32_t ring_wr = smem_addr(wsm) + lane * 8;
 
@@ -104,6 +107,10 @@ k_recon_nd(const ReconArgs a) {
         // batch when it is short enough.
         uint32_t lo_t = 0;
         bool cached = false;
+        const bool interior = vec && s * kSegCols + kSegCols <= nx && ylen == B && (ND == 2 || zlen == B);
+        const uint32_t ocap = ZREG_R && interior ? OCAP_BIG : (uint32_t)C::OCAP;
+        uint32_t* const oc_idx = ZREG_R && interior ? reinterpret_cast<uint32_t*>(zs) : oc_idx0;
+        int32_t* const oc_del = reinterpret_cast<int32_t*>(oc_idx + ocap);
         if (anyout) {
             const uint64_t fb = (bz * g.nby + by) * g.nbx + (s * kSegCols) / B;
             const uint64_t nblk = umin64(kSegCols / B, g.nbx - (s * kSegCols) / B);
@@ -114,7 +121,7 @@ k_recon_nd(const ReconArgs a) {
             }
             lo_t = __shfl_sync(VSZ_FULL, lo_t, 0);
             hi_t = __shfl_sync(VSZ_FULL, hi_t, 0);
-            cached = hi_t >= lo_t && hi_t - lo_t <= (uint32_t)C::OCAP && (uint64_t)hi_t <= a.out_cap;
+            cached = hi_t >= lo_t && hi_t - lo_t <= ocap && (uint64_t)hi_t <= a.out_cap;
             if (cached) {
                 const uint32_t sidx = smem_addr(oc_idx), sdel = smem_addr(oc_del);
                 for (uint32_t i = lane; i < hi_t - lo_t; i += 32) {
@@ -140,7 +147,6 @@ k_recon_nd(const ReconArgs a) {
             cp_async_commit();
         };
 
-        const bool interior = vec && s * kSegCols + kSegCols <= nx && ylen == B && (ND == 2 || zlen == B);
         if (interior) {
             // Lean walk of an interior tile: compile-time trip counts, 32-bit
             // offsets, and P carried in the running-sum state (the z sums of
@@ -197,13 +203,14 @@ k_recon_nd(const ReconArgs a) {
                               ((cw[u].y - 0x00010001u) & ~cw[u].y & 0x80008000u);
                     }
                     const bool patch = anyout && __any_sync(VSZ_FULL, hz != 0u);
-                    auto lrow = [&](auto patch_tag, int u) {
-                        constexpr bool PATCH = decltype(patch_tag)::value;
+                    // one copy of the row code (the patch test is a uniform
+                    // branch), which keeps the unrolled plane loop small
+                    auto lrow = [&](int u) {
                         const uint32_t c[4] = {cw[u].x & 0xffffu, cw[u].x >> 16, cw[u].y & 0xffffu, cw[u].y >> 16};
                         int32_t d[4];
 #pragma unroll
                         for (int k = 0; k < 4; ++k) d[k] = (int32_t)c[k] - R;
-                        if (PATCH) {
+                        if (patch) {
                             uint32_t zm = 0;
 #pragma unroll
                             for (int k = 0; k < 4; ++k) zm |= (c[k] == 0u ? 1u : 0u) << k;
@@ -292,13 +299,8 @@ k_recon_nd(const ReconArgs a) {
                             st_out4(reinterpret_cast<int4*>(reinterpret_cast<float*>(a.out) + tile_base + ro), vv);
                         }
                     };
-                    if (patch) {
 #pragma unroll
-                        for (int u = 0; u < U; ++u) lrow(std::true_type{}, u);
-                    } else {
-#pragma unroll
-                        for (int u = 0; u < U; ++u) lrow(std::false_type{}, u);
-                    }
+                    for (int u = 0; u < U; ++u) lrow(u);
                     h = h + 1 == C::NSR ? 0 : h + 1;
                 }
             }
@@ -477,30 +479,43 @@ k_recon_nd(const ReconArgs a) {
 }
 
 // Host-side launch helpers for one rank, instantiated by k_rank2.cu / k_rank3.cu.
-template <int ND, int B>
-cudaError_t launch_nd_compress(const CompressArgs& a, cudaStream_t s) {
+template <int ND, int B, bool BP, bool GP>
+cudaError_t launch_nd_compress_k(const CompressArgs& a, cudaStream_t s) {
     using C = NdCfg<ND, B>;
-    const bool bp = is_block_pad(a.pad_mode);
-    const void* k = bp ? (const void*)k_lorenzo_nd<ND, B, true> : (const void*)k_lorenzo_nd<ND, B, false>;
+    const void* k = (const void*)k_lorenzo_nd<ND, B, BP, GP>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM_C);
     if (e != cudaSuccess) return e;
     const int grid = grid_for(k, C::THREADS, C::SMEM_C, C::WARPS, a.g.ntiles);
-    if (bp) k_lorenzo_nd<ND, B, true><<<grid, C::THREADS, C::SMEM_C, s>>>(a);
-    else k_lorenzo_nd<ND, B, false><<<grid, C::THREADS, C::SMEM_C, s>>>(a);
+    k_lorenzo_nd<ND, B, BP, GP><<<grid, C::THREADS, C::SMEM_C, s>>>(a);
     return cudaGetLastError();
 }
 
 template <int ND, int B>
-cudaError_t launch_nd_compress_batch(bool bp, const CompressArgs* fields, const uint64_t* tile_prefix, int nfields,
-                                     uint64_t total_tiles, unsigned long long* ticket, cudaStream_t s) {
+cudaError_t launch_nd_compress(const CompressArgs& a, cudaStream_t s) {
+    if (is_block_pad(a.pad_mode)) return launch_nd_compress_k<ND, B, true, false>(a, s);
+    if (is_global_pad(a.pad_mode)) return launch_nd_compress_k<ND, B, false, true>(a, s);
+    return launch_nd_compress_k<ND, B, false, false>(a, s);
+}
+
+template <int ND, int B, bool BP, bool GP>
+cudaError_t launch_nd_compress_batch_k(const CompressArgs* fields, const uint64_t* tile_prefix, int nfields,
+                                       uint64_t total_tiles, unsigned long long* ticket, cudaStream_t s) {
     using C = NdCfg<ND, B>;
-    const void* k = bp ? (const void*)k_lorenzo_nd_batch<ND, B, true> : (const void*)k_lorenzo_nd_batch<ND, B, false>;
+    const void* k = (const void*)k_lorenzo_nd_batch<ND, B, BP, GP>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM_C);
     if (e != cudaSuccess) return e;
     const int grid = grid_for(k, C::THREADS, C::SMEM_C, C::WARPS, total_tiles);
-    if (bp) k_lorenzo_nd_batch<ND, B, true><<<grid, C::THREADS, C::SMEM_C, s>>>(fields, tile_prefix, nfields, ticket);
-    else k_lorenzo_nd_batch<ND, B, false><<<grid, C::THREADS, C::SMEM_C, s>>>(fields, tile_prefix, nfields, ticket);
+    k_lorenzo_nd_batch<ND, B, BP, GP><<<grid, C::THREADS, C::SMEM_C, s>>>(fields, tile_prefix, nfields, ticket);
     return cudaGetLastError();
+}
+
+// pk: 0 zero padding, 1 per-block padding, 2 global padding
+template <int ND, int B>
+cudaError_t launch_nd_compress_batch(int pk, const CompressArgs* fields, const uint64_t* tile_prefix, int nfields,
+                                     uint64_t total_tiles, unsigned long long* ticket, cudaStream_t s) {
+    if (pk == 1) return launch_nd_compress_batch_k<ND, B, true, false>(fields, tile_prefix, nfields, total_tiles, ticket, s);
+    if (pk == 2) return launch_nd_compress_batch_k<ND, B, false, true>(fields, tile_prefix, nfields, total_tiles, ticket, s);
+    return launch_nd_compress_batch_k<ND, B, false, false>(fields, tile_prefix, nfields, total_tiles, ticket, s);
 }
 
 template <int ND, int B>
