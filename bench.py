@@ -128,6 +128,28 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(win)}
 
 
+# ---------------------------------------------------------------- ranks
+def rank_field_seed(rank: int) -> int:
+    """Each rank compresses its own field: blocks (and fields) are
+    independent, so the path shards with no collective on the data path."""
+    return 2 + rank
+
+
+def max_over_ranks(value: float, dist, device: str) -> float:
+    """The slowest rank's time (the job's time); identity without dist."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_gbps(world: int, n_per_rank: int, ms: float) -> float:
+    """Whole-job GB/s of fp32 input: all ranks' values over the max time."""
+    return world * n_per_rank * 4 / (ms * 1e-3) / 1e9
+
+
 # ---------------------------------------------------------------- roofline
 def algorithmic_bytes(name: str, n: int, nb: int, n_out: int, n_fix: int, block_pad: bool) -> int:
     """Bytes a launch must move at minimum (each input read once, each output
@@ -369,7 +391,7 @@ def run_gpu(a):
 
     vsz.lib()
     t = time.time()
-    x3 = synth.lognormal3d(a.size, seed=2 + rank)
+    x3 = synth.lognormal3d(a.size, seed=rank_field_seed(rank))
     log(f"[bench] rank {rank}: generated {a.size}^3 field in {time.time() - t:.1f}s")
     n = x3.size
     p = vsz.Params.make(x3.shape, a.block, a.eb, "rel", a.radius, a.pad)
@@ -414,13 +436,9 @@ def run_gpu(a):
     t1 = time.time()
     vsz.trace_enable(False)
     recs = vsz.trace_read(1 << 20)
-    ms = ev0.elapsed_time(ev1)
-    if dist:
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dist, "cuda")
     ms_step = ms / a.steps
-    value = world * n * 4 / (ms_step * 1e-3) / 1e9
+    value = job_gbps(world, n, ms_step)
 
     # per-kernel device times, and the roofline of the dominant kernel
     per = {}
@@ -444,7 +462,8 @@ def run_gpu(a):
     dom_avg_s = per[dom]["ms"] / per[dom]["launches"] * 1e-3
     dom_bytes = algorithmic_bytes(dom, n, nb, n_out, n_fix, bp)
     achieved = dom_bytes / dom_avg_s / 1e9
-    kname = {"lorenzo": f"k_lorenzo_nd<3,{a.block},{str(bp).lower()}>",
+    gp = a.pad.startswith("global")
+    kname = {"lorenzo": f"k_lorenzo_nd<3,{a.block},{str(bp).lower()},{str(gp).lower()}>",
              "recon": f"k_recon_nd<3,{a.block},false>"}[dom]
     wl = f"{a.size}^3 b{a.block} eb{a.eb:g} {a.pad}"
     roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
@@ -489,12 +508,8 @@ def run_gpu(a):
             e2e_step()
         e1.record()
         barrier()
-        ems = e0.elapsed_time(e1) / ke
-        if dist:
-            tt = torch.tensor([ems], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ems = float(tt.item())
-        e2e = {"value": world * n * 4 / (ems * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": bi,
+        ems = max_over_ranks(e0.elapsed_time(e1) / ke, dist, "cuda")
+        e2e = {"value": job_gbps(world, n, ems), "unit": UNIT, "h2d_bytes_per_step": bi,
                "d2h_bytes_per_step": bo, "ms_per_step": ems,
                "what": "pinned host x -> device, compress, read header, reconstruct, codes + blk_off + "
                        "outlier indices + x_hat -> pinned host"}

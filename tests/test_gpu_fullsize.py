@@ -1,0 +1,92 @@
+"""GPU parity at the benchmark's full size: the 512^3 NYX-like field, block
+8^3, R = 512, relative eb 1e-4, in the launch configuration bench.py times.
+
+The oracle cannot compress 134M values in a test's time, so:
+* the error bound resolution (a pass over the whole field) is compared
+  exactly with the oracle's;
+* a sample of blocks is compared element by element: blocks are independent
+  (Sec. III-A), so the oracle compresses each sampled block alone, in
+  absolute mode with the eb_abs it resolved for the whole field, and its
+  codes and outliers must equal the GPU's for that block (the canonical
+  outlier slice blk_off[b]..blk_off[b+1]);
+* properties that hold at any size are checked on every element: the inverse
+  reproduces the prequantized integers q = rint(x * inv2eb) exactly, and
+  |x - x_hat| <= eb_abs (1 + 2^-20).
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import oracle  # noqa: E402
+import paper_2201_04614_gb300 as vsz  # noqa: E402
+
+N, B = 512, 8
+
+
+@pytest.fixture(scope="module")
+def run():
+    x3 = synth.cfg2_field(N)
+    x = x3.reshape(-1)
+    p = vsz.Params.make((N, N, N), B, 1e-4, "rel", 512, "zero")
+    f = vsz.Field(p, out_cap=N ** 3 // 8, fix_cap=N ** 3 // 64)
+    xd = torch.from_numpy(x).cuda()
+    f.compress(xd)
+    h = f.header()
+    assert h["status"] == 0
+    xh = f.reconstruct()
+    qh = f.reconstruct_q()
+    torch.cuda.synchronize()
+    return x3, xd, f, h, xh, qh
+
+
+def test_eb_resolution_matches_oracle(run):
+    x3, _, _, h, _, _ = run
+    e = oracle.resolve_eb(oracle.Params((N, N, N), B, 1e-4, oracle.EB_REL, 512, oracle.PAD_ZERO), x3)
+    assert h["eb_abs"] == e.eb_abs
+    assert np.float32(h["inv2eb"]) == e.inv2eb and np.float32(h["ebx2"]) == e.ebx2
+    assert np.float32(h["eb_f32"]) == e.eb_f32
+
+
+def test_sampled_blocks_match_oracle(run):
+    x3, _, f, h, _, _ = run
+    nbx = N // B
+    rng = np.random.default_rng(123)
+    blocks = rng.choice(nbx ** 3, size=96, replace=False)
+    codes = f.codes[: N ** 3].view(torch.int16)
+    blk_off = f.blk_off.cpu().numpy().view(np.uint32)
+    out_idx = f.out_idx.cpu().numpy().view(np.uint32)
+    out_delta = f.out_delta.cpu().numpy()
+    cg = codes.view(N, N, N)
+    for b in blocks:
+        bz, by, bx = b // (nbx * nbx), (b // nbx) % nbx, b % nbx
+        sl = (slice(bz * B, bz * B + B), slice(by * B, by * B + B), slice(bx * B, bx * B + B))
+        sub = np.ascontiguousarray(x3[sl])
+        po = oracle.Params((B, B, B), B, h["eb_abs"], oracle.EB_ABS, 512, oracle.PAD_ZERO)
+        c = oracle.compress(po, sub)
+        got = cg[sl].cpu().numpy().view(np.uint16).reshape(-1)
+        assert np.array_equal(got, c.codes), b
+        lo, hi = blk_off[b], blk_off[b + 1]
+        # the oracle's local indices, mapped to the field's linear indices
+        li = c.out_idx.astype(np.int64)
+        lz, ly, lx = li // (B * B), (li // B) % B, li % B
+        gi = ((bz * B + lz) * N + (by * B + ly)) * N + (bx * B + lx)
+        assert np.array_equal(out_idx[lo:hi].astype(np.int64), gi), b
+        assert np.array_equal(out_delta[lo:hi], c.out_delta), b
+
+
+def test_every_element_round_trips(run):
+    x3, xd, f, h, xh, qh = run
+    inv2eb = torch.tensor(np.float32(h["inv2eb"]), device="cuda")
+    q = torch.round(xd * inv2eb).to(torch.int32)  # one fp32 product, round half to even
+    assert torch.equal(qh, q)
+    err = (xd.double() - xh.double()).abs()
+    assert float(err.max()) <= h["eb_abs"] * (1 + 2.0 ** -20)
+    # outlier count equals the number of code-0 elements
+    assert int((f.codes[: N ** 3] == 0).sum()) == h["n_out"]
