@@ -261,11 +261,14 @@ def run_reference(a):
 def run_batch_compare(a, log_fn=log) -> dict:
     """The mixed stream of fields (one 1D field of 280,953,867 random-walk
     values, 13 fields of 100x500x500, 20 of 1800x3600; relative eb 1e-3 and
-    1e-5, R = 512): compression throughput of plain per-field launches with
-    the default class (block 256 / 8 / 16, zero padding), of the same
-    launches replayed as one CUDA graph, of one batch plan with the default
-    classes, and of one batch plan with the tuner's classes; outlier counts
-    per field for the tuned and the default classes."""
+    1e-5, R = 512).  Compression: plain per-field launches with the default
+    class (block 256 / 8 / 16, zero padding), the same launches replayed as
+    one CUDA graph, one batch plan with the default classes (default launch
+    shapes, then autotuned shapes), and one batch plan with the tuner's
+    classes and autotuned shapes.  Reconstruction: plain per-field launches
+    and the batch plans.  Outlier counts per field for the tuner's and the
+    default classes.  Every list has room for every element, so no field
+    overflows (status 0)."""
     import numpy as np
     import torch
     import paper_2201_04614_gb300 as vsz
@@ -283,6 +286,7 @@ def run_batch_compare(a, log_fn=log) -> dict:
     log_fn(f"[bench] batch stream: {len(xs)} fields, {n_total} values, generated in {time.time() - t0:.1f}s")
     steps = max(5, min(a.batch_steps, 50))
     stream = torch.cuda.Stream()
+    outs = [torch.empty(x.numel(), dtype=torch.float32, device="cuda") for x in xs]
 
     def timed(fn):
         with torch.cuda.stream(stream):
@@ -303,20 +307,33 @@ def run_batch_compare(a, log_fn=log) -> dict:
         for shape, c in zip(shapes, classes):
             b, pad = T.class_params(len(shape), c)
             n = int(np.prod(shape))
-            out.append(vsz.Field(vsz.Params.make(shape, b, eb, "rel", 512, pad), out_cap=max(1 << 16, n // 4),
-                                 fix_cap=max(1 << 16, n // 64)))
+            out.append(vsz.Field(vsz.Params.make(shape, b, eb, "rel", 512, pad), out_cap=n, fix_cap=max(1 << 16, n // 64)))
         return out
+
+    def autotuned(fields):
+        bt = vsz.Batch(fields, xs, use_graph=True)
+        bt.set_outputs(outs)
+        torch.cuda.synchronize()
+        tt = time.time()
+        cls = bt.autotune(stream, reps=3)
+        return bt, cls, (time.time() - tt) * 1e3
+
+    def shapes_of(cls):
+        return [{k: c[k] for k in ("kind", "ndim", "block", "pad_kind", "warps", "ctas_per_sm", "concurrent",
+                                   "ms", "ms_default")} for c in cls if c["tiles"]]
 
     res = {"workload": "1D 280,953,867 random walk + 13 x 100x500x500 GRF + 20 x 1800x3600 Fourier fields "
                        "(2.94 GB fp32), relative eb, R=512", "values": n_total, "steps": steps, "by_eb": {}}
+    gb = n_total * 4 / 1e9
     for eb in (1e-3, 1e-5):
+        r = {}
         dflt = [T.default_class(len(sh)) for sh in shapes]
         plain = make_fields(dflt, eb)
 
         def plain_step():
             for f, x in zip(plain, xs):
                 f.compress(x)
-        ms_plain = timed(plain_step)
+        r["plain"] = timed(plain_step)
         # the same per-field launches captured once into a CUDA graph
         g = torch.cuda.CUDAGraph()
         with torch.cuda.stream(stream):
@@ -324,44 +341,59 @@ def run_batch_compare(a, log_fn=log) -> dict:
             stream.synchronize()
             with torch.cuda.graph(g, stream=stream):
                 plain_step()
-        ms_plain_graph = timed(g.replay)
+        r["plain_graph"] = timed(g.replay)
         del g
+
+        def plain_recon():
+            for f, o in zip(plain, outs):
+                f.reconstruct(out=o)
+        r["plain_recon"] = timed(plain_recon)
         nout_def = [int(f.header()["n_out"]) for f in plain]
         st_def = [int(f.header()["status"]) for f in plain]
         bd = vsz.Batch(plain, xs, use_graph=True)
-        ms_batch_def = timed(lambda: bd.submit(stream))
+        bd.set_outputs(outs)
+        r["batched_default"] = timed(lambda: bd.submit(stream))
+        r["batched_default_recon"] = timed(lambda: bd.reconstruct(stream))
         bd.close()
-        # tuned classes: features, one MLP inference, guard (timed on its own)
+        del bd
+        bda, cls_def, at_def_ms = autotuned(plain)
+        r["batched_default_autotuned"] = timed(lambda: bda.submit(stream))
+        r["batched_default_autotuned_recon"] = timed(lambda: bda.reconstruct(stream))
+        bda.close()
+        del bda
+        # the tuner's classes: features, one MLP inference, guard (timed on its own)
         torch.cuda.synchronize()
         tt = time.time()
         picks = T.choose([(vsz.Params.make(sh, 8, eb, "rel", 512, "zero"), x) for sh, x in zip(shapes, xs)])
         torch.cuda.synchronize()
         tune_ms = (time.time() - tt) * 1e3
-        classes = [r["class"] for r in picks]
+        classes = [p["class"] for p in picks]
         tuned = make_fields(classes, eb)
-        bt = vsz.Batch(tuned, xs, use_graph=True)
-        ms_batch_tuned = timed(lambda: bt.submit(stream))
+        bt, cls_tuned, at_tuned_ms = autotuned(tuned)
+        r["batched_tuned"] = timed(lambda: bt.submit(stream))
+        r["batched_tuned_recon"] = timed(lambda: bt.reconstruct(stream))
         bt.close()
+        del bt
         nout_tuned = [int(f.header()["n_out"]) for f in tuned]
         st_tuned = [int(f.header()["status"]) for f in tuned]
-        gb = n_total * 4 / 1e9
         res["by_eb"][f"{eb:g}"] = {
-            "plain_GBps": gb / (ms_plain * 1e-3), "plain_graph_GBps": gb / (ms_plain_graph * 1e-3),
-            "batched_default_GBps": gb / (ms_batch_def * 1e-3), "batched_tuned_GBps": gb / (ms_batch_tuned * 1e-3),
-            "ms": {"plain": ms_plain, "plain_graph": ms_plain_graph, "batched_default": ms_batch_def,
-                   "batched_tuned": ms_batch_tuned},
-            "tune_ms_once": tune_ms,
+            **{f"{k}_GBps": gb / (v * 1e-3) for k, v in r.items()},
+            "ms": r,
+            "tune_ms_once": tune_ms, "autotune_ms_once": {"default": at_def_ms, "tuned": at_tuned_ms},
+            "shapes_default_classes": shapes_of(cls_def), "shapes_tuned_classes": shapes_of(cls_tuned),
             "classes_tuned": {nm: T.class_params(len(sh), c) for nm, sh, c in zip(names, shapes, classes)
                               if c != T.default_class(len(sh))},
-            "guard_fallbacks": sum(1 for r in picks if r["class"] != r["predicted"]),
+            "guard_fallbacks": sum(1 for p in picks if p["class"] != p["predicted"]),
             "n_out_default_total": sum(nout_def), "n_out_tuned_total": sum(nout_tuned),
             "fields_n_out_tuned_le_default": sum(1 for u, v in zip(nout_tuned, nout_def) if u <= v),
             "fields": len(xs), "status_nonzero": sum(1 for v in st_def + st_tuned if v),
         }
-        log_fn(f"[bench] batch eb={eb:g}: {res['by_eb'][f'{eb:g}']}")
+        log_fn(f"[bench] batch eb={eb:g}: " + json.dumps({k: v for k, v in res["by_eb"][f"{eb:g}"].items()
+                                                          if k.endswith("GBps") or k.startswith("n_out")
+                                                          or k == "status_nonzero"}))
         del plain, tuned
         torch.cuda.empty_cache()
-    del xs
+    del xs, outs
     torch.cuda.empty_cache()
     return res
 

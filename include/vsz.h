@@ -242,6 +242,82 @@ VSZ_API vsz_status vsz_batch_submit(vsz_batch b, void* stream);
 /* Free the plan (waits for nothing; do not destroy a plan with work in flight). */
 VSZ_API vsz_status vsz_batch_destroy(vsz_batch b);
 
+/*
+ * Launch shapes of a batch and their autotuner (the batching pattern's tile
+ * autotuner; the paper tunes only block size and vector length, by timing,
+ * Sec. III-D).  Each class kernel is persistent: its warps claim tiles (a
+ * 128-column segment of a row of blocks; 4096 values in 1D) from the
+ * class's queue.  What is tuned is how that queue is served: warps per CTA
+ * (2, 4 or 8), resident CTAs per SM, and whether the class kernels run one
+ * after another or as parallel branches (so one class's tail overlaps the
+ * next).  No shape changes any result.
+ */
+typedef struct {
+    int32_t  ndim;
+    uint32_t block;
+    int32_t  pad_kind;     /* 0 zero padding, 1 per-block padding, 2 global padding */
+    int32_t  nfields;      /* fields in the class */
+    uint64_t tiles;        /* tiles of all of them */
+    int32_t  warps;        /* warps per CTA of the class kernel (0 = default: 4, or 8 in 1D) */
+    int32_t  ctas_per_sm;  /* resident CTAs per SM (0 = as many as fit) */
+    float    ms;           /* last autotune: median device time of the class kernel with the chosen shape */
+    float    ms_default;   /* last autotune: the same with the default shape (0 if never tuned) */
+    int32_t  concurrent;   /* the plan runs this sequence's class kernels as parallel branches */
+    int32_t  kind;         /* 0 compression class, 1 reconstruction class */
+} vsz_batch_class;
+
+/* Number of classes of a plan (0 if b is NULL), and one class's description.
+ * Classes 0..k-1 are the compression classes (rank, block edge, padding
+ * kind); after vsz_batch_set_outputs, the reconstruction classes (rank,
+ * block edge) follow. */
+VSZ_API int vsz_batch_num_classes(vsz_batch b);
+VSZ_API vsz_status vsz_batch_get_class(vsz_batch b, int c, vsz_batch_class* out);
+
+/* Set class c's launch shape (either kind): warps in {0, 2, 4, 8} (0 = default), ctas_per_sm
+ * in 0..64 (0 = as many as fit; larger values are capped at what fits).
+ * VSZ_ERR_UNSUPPORTED if the shape cannot launch (shared memory).  Drops
+ * the cached graph (re-captured by the next submit). */
+VSZ_API vsz_status vsz_batch_set_shape(vsz_batch b, int c, int warps, int ctas_per_sm);
+
+/* Run the class kernels one after another (0) or as parallel branches (1):
+ * in compression forked after the value-range pass and joined before the
+ * origin pass, in reconstruction joined before the fixups.  Both sequences.
+ * Drops the cached graphs. */
+VSZ_API vsz_status vsz_batch_set_concurrent(vsz_batch b, int on);
+
+/*
+ * Autotune the plan on its own inputs: for each class (compression, and
+ * reconstruction when outputs are set), run its whole sequence `reps` times
+ * (1..50) per candidate shape (warps 2, 4, 8 x CTAs per SM 1, 2, 4 and the
+ * most that fit) and keep the shape with the smallest median device time of
+ * the class kernel (the default shape unless another is faster); then time
+ * each sequence serial and concurrent and keep the faster.  Synchronous: it
+ * waits for its own runs on `stream`, which must not be capturing
+ * (VSZ_ERR_INVALID_ARG).  It compresses (and reconstructs) the batch many
+ * times, with the same results each time, and drops the cached graphs.
+ * Read the choices and times with vsz_batch_get_class.
+ */
+VSZ_API vsz_status vsz_batch_autotune(vsz_batch b, void* stream, int reps);
+
+/*
+ * Batch decompression (the inverse of Sec. III-A for every field of the
+ * plan; the paper leaves decompression sequential).  vsz_batch_set_outputs
+ * records one fp32 output per job (h_xhat: host array of njobs device
+ * pointers, each [n_i] floats, 16-byte aligned for the vector path; NULL
+ * allowed where n_i = 0), groups the fields by (rank, block edge) and
+ * uploads one descriptor table per class (freed by vsz_batch_destroy or the
+ * next vsz_batch_set_outputs).  vsz_batch_reconstruct then runs a fixed
+ * sequence whatever the number of fields: one persistent inverse kernel per
+ * class whose warps draw tiles of all the class's fields from one queue,
+ * and one fixup kernel over every field.  It reads what the last
+ * compression of the plan wrote (codes, lists, headers) and gives each
+ * field exactly what vsz_reconstruct gives it.  Captured into a CUDA graph
+ * on the first call and replayed, as vsz_batch_submit.  Errors only the
+ * device sees go to each field's header (recon_status).
+ */
+VSZ_API vsz_status vsz_batch_set_outputs(vsz_batch b, float* const* h_xhat);
+VSZ_API vsz_status vsz_batch_reconstruct(vsz_batch b, void* stream);
+
 /* Bytes of the optional reconstruction workspace. */
 #define VSZ_RECON_WS_BYTES 256
 

@@ -61,6 +61,13 @@ class _CFieldJob(ctypes.Structure):
     _fields_ = [("params", _CParams), ("d_x", ctypes.c_void_p), ("out", _CCompressed)]
 
 
+class _CBatchClass(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int32), ("block", ctypes.c_uint32), ("pad_kind", ctypes.c_int32),
+                ("nfields", ctypes.c_int32), ("tiles", ctypes.c_uint64), ("warps", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32), ("ms", ctypes.c_float), ("ms_default", ctypes.c_float),
+                ("concurrent", ctypes.c_int32), ("kind", ctypes.c_int32)]
+
+
 class _CTrace(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 24), ("ndim", ctypes.c_int32), ("block", ctypes.c_uint32),
                 ("n", ctypes.c_uint64), ("ms", ctypes.c_float), ("reserved", ctypes.c_uint32)]
@@ -72,7 +79,9 @@ EXPORTED = ["vsz_status_string", "vsz_last_cuda_error", "vsz_abi_version", "vsz_
             "vsz_outlier_compact", "vsz_compress", "vsz_reconstruct", "vsz_reconstruct_q",
             "vsz_code_histogram", "vsz_read_header", "vsz_trace_enable", "vsz_trace_read",
             "vsz_compress_noalloc", "vsz_batch_workspace_size", "vsz_batch_create", "vsz_batch_submit",
-            "vsz_batch_destroy", "vsz_tuner_features_workspace_size", "vsz_tuner_features",
+            "vsz_batch_destroy", "vsz_batch_num_classes", "vsz_batch_get_class", "vsz_batch_set_shape",
+            "vsz_batch_set_concurrent", "vsz_batch_autotune", "vsz_batch_set_outputs", "vsz_batch_reconstruct",
+            "vsz_tuner_features_workspace_size", "vsz_tuner_features",
             "vsz_tuner_sweep_workspace_size", "vsz_tuner_sweep", "vsz_tuner_guard_workspace_size",
             "vsz_tuner_guard", "vsz_tuner_guard_sample_dims", "vsz_mlp_forward", "vsz_mlp_grad_workspace_size",
             "vsz_mlp_grad", "vsz_mlp_adam"]
@@ -120,13 +129,20 @@ def lib():
     L.vsz_batch_create.argtypes = [P(_CFieldJob), ctypes.c_int, vp, sz, ctypes.c_int, P(ctypes.c_void_p)]
     L.vsz_batch_submit.argtypes = [vp, vp]
     L.vsz_batch_destroy.argtypes = [vp]
+    L.vsz_batch_num_classes.argtypes = [vp]
+    L.vsz_batch_get_class.argtypes = [vp, ctypes.c_int, P(_CBatchClass)]
+    L.vsz_batch_set_shape.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    L.vsz_batch_set_concurrent.argtypes = [vp, ctypes.c_int]
+    L.vsz_batch_autotune.argtypes = [vp, vp, ctypes.c_int]
+    L.vsz_batch_set_outputs.argtypes = [vp, P(ctypes.c_void_p)]
+    L.vsz_batch_reconstruct.argtypes = [vp, vp]
     L.vsz_trace_enable.argtypes = [ctypes.c_int]
     L.vsz_trace_read.argtypes = [P(_CTrace), ctypes.c_int]
     for name in EXPORTED:
         if name.startswith(("vsz_tuner", "vsz_mlp")):
             continue  # bound by tuner.py
         if name not in ("vsz_status_string", "vsz_last_cuda_error", "vsz_abi_version",
-                        "vsz_num_elems", "vsz_num_blocks", "vsz_workspace_size"):
+                        "vsz_num_elems", "vsz_num_blocks", "vsz_workspace_size", "vsz_batch_workspace_size"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -354,6 +370,43 @@ class Batch:
 
     def submit(self, stream=None):
         _check(lib().vsz_batch_submit(self._h, _stream_handle(stream)), "vsz_batch_submit")
+
+    def set_outputs(self, outs):
+        """One contiguous float32 CUDA output per field (vsz_batch_set_outputs);
+        they must stay alive and in place while the plan uses them."""
+        if len(outs) != len(self.fields):
+            raise ValueError("one output per field")
+        for f, o in zip(self.fields, outs):
+            if f.n and (o is None or o.dtype.itemsize != 4 or not o.is_contiguous() or o.numel() < f.n):
+                raise ValueError("each output must be a contiguous float32 tensor of n values")
+        arr = (ctypes.c_void_p * len(outs))(*[(o.data_ptr() if o is not None and o.numel() else None) for o in outs])
+        _check(lib().vsz_batch_set_outputs(self._h, arr), "vsz_batch_set_outputs")
+        self.outs = list(outs)
+
+    def reconstruct(self, stream=None):
+        _check(lib().vsz_batch_reconstruct(self._h, _stream_handle(stream)), "vsz_batch_reconstruct")
+
+    def classes(self) -> list:
+        """The plan's classes (rank, block, padding kind) with their launch
+        shapes and the last autotune's times (vsz_batch_get_class)."""
+        L = lib()
+        out = []
+        for c in range(L.vsz_batch_num_classes(self._h)):
+            k = _CBatchClass()
+            _check(L.vsz_batch_get_class(self._h, c, ctypes.byref(k)), "vsz_batch_get_class")
+            out.append({f: getattr(k, f) for f, _ in _CBatchClass._fields_})
+        return out
+
+    def set_shape(self, c: int, warps: int = 0, ctas_per_sm: int = 0):
+        _check(lib().vsz_batch_set_shape(self._h, c, warps, ctas_per_sm), "vsz_batch_set_shape")
+
+    def set_concurrent(self, on: bool):
+        _check(lib().vsz_batch_set_concurrent(self._h, 1 if on else 0), "vsz_batch_set_concurrent")
+
+    def autotune(self, stream=None, reps: int = 3) -> list:
+        """Tile autotuner (vsz_batch_autotune): synchronous; returns classes()."""
+        _check(lib().vsz_batch_autotune(self._h, _stream_handle(stream), reps), "vsz_batch_autotune")
+        return self.classes()
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

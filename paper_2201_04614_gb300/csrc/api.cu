@@ -2,7 +2,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <unordered_map>
 
 #include "common.cuh"
@@ -45,6 +47,51 @@ int grid_for(const void* kernel, int threads, size_t smem, uint64_t per_cta, uin
     uint64_t g = want < cap ? want : cap;
     if (g < 1) g = 1;
     return (int)g;
+}
+
+int occupancy(const void* kernel, int threads, size_t smem) {
+    static std::mutex mu;
+    static std::map<std::tuple<const void*, int, size_t>, int> cache;
+    const auto key = std::make_tuple(kernel, threads, smem);
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, smem) != cudaSuccess) {
+        (void)cudaGetLastError();
+        occ = 0;
+    }
+    cache[key] = occ;
+    return occ;
+}
+
+int grid_shape(const void* kernel, int threads, size_t smem, uint64_t per_cta, uint64_t work, int ctas) {
+    int occ = occupancy(kernel, threads, smem);
+    if (occ < 1) occ = 1;
+    if (ctas > 0 && ctas < occ) occ = ctas;
+    const uint64_t want = (work + per_cta - 1) / (per_cta ? per_cta : 1);
+    const uint64_t cap = (uint64_t)num_sms() * (uint64_t)occ;
+    uint64_t g = want < cap ? want : cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+cudaError_t raise_smem_attr(const void* kernel, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, size_t> set;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    int optin = 0;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    if (bytes > (size_t)optin) return cudaErrorInvalidValue;
+    std::lock_guard<std::mutex> lk(mu);
+    size_t& cur = set[std::make_pair(dev, kernel)];
+    if (bytes <= cur) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) cur = bytes;
+    return e;
 }
 
 static thread_local char g_last_err[256] = "";

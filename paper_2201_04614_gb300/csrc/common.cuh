@@ -221,15 +221,47 @@ cudaError_t launch_recon_1d(const ReconArgs& a, bool q_out, cudaStream_t s);
 cudaError_t launch_recon_2d(const ReconArgs& a, bool q_out, cudaStream_t s);
 cudaError_t launch_recon_3d(const ReconArgs& a, bool q_out, cudaStream_t s);
 
+// Launch shape of a persistent batch kernel, the knobs of the batch
+// autotuner: warps per CTA (0 = the kernel's default) and resident CTAs per
+// SM (0 = as many as fit).  Tiles are claimed per warp from a ticket, so the
+// shape changes only how the work is spread, never a result.
+struct LaunchShape {
+    int warps = 0;
+    int ctas = 0;
+};
+
+// Batch launchers.  With occ != nullptr nothing is launched: *occ receives
+// the CTAs per SM that fit with sh.warps (0 if the shape cannot launch).
 cudaError_t launch_lorenzo_batch_1d(uint32_t b, int pk, const CompressArgs* fields, const uint64_t* tile_prefix,
-                                    int nfields, uint64_t total_tiles, unsigned long long* ticket, cudaStream_t s);
+                                    int nfields, uint64_t total_tiles, unsigned long long* ticket, LaunchShape sh,
+                                    cudaStream_t s, int* occ = nullptr);
 cudaError_t launch_lorenzo_batch_2d(uint32_t b, int pk, const CompressArgs* fields, const uint64_t* tile_prefix,
-                                    int nfields, uint64_t total_tiles, unsigned long long* ticket, cudaStream_t s);
+                                    int nfields, uint64_t total_tiles, unsigned long long* ticket, LaunchShape sh,
+                                    cudaStream_t s, int* occ = nullptr);
 cudaError_t launch_lorenzo_batch_3d(uint32_t b, int pk, const CompressArgs* fields, const uint64_t* tile_prefix,
-                                    int nfields, uint64_t total_tiles, unsigned long long* ticket, cudaStream_t s);
+                                    int nfields, uint64_t total_tiles, unsigned long long* ticket, LaunchShape sh,
+                                    cudaStream_t s, int* occ = nullptr);
+
+cudaError_t launch_recon_batch_1d(uint32_t b, const ReconArgs* fields, const uint64_t* tile_prefix, int nfields,
+                                  uint64_t total_tiles, unsigned long long* ticket, LaunchShape sh, cudaStream_t s,
+                                  int* occ = nullptr);
+cudaError_t launch_recon_batch_2d(uint32_t b, const ReconArgs* fields, const uint64_t* tile_prefix, int nfields,
+                                  uint64_t total_tiles, unsigned long long* ticket, LaunchShape sh, cudaStream_t s,
+                                  int* occ = nullptr);
+cudaError_t launch_recon_batch_3d(uint32_t b, const ReconArgs* fields, const uint64_t* tile_prefix, int nfields,
+                                  uint64_t total_tiles, unsigned long long* ticket, LaunchShape sh, cudaStream_t s,
+                                  int* occ = nullptr);
 
 int num_sms();
 int grid_for(const void* kernel, int threads, size_t smem, uint64_t work_items_per_cta, uint64_t work);
+// Resident CTAs per SM of `kernel` at this block size and dynamic shared
+// memory (0 if it cannot launch), cached per (kernel, threads, smem).
+int occupancy(const void* kernel, int threads, size_t smem);
+// As grid_for, with at most `ctas` resident CTAs per SM (0 = no cap).
+int grid_shape(const void* kernel, int threads, size_t smem, uint64_t per_cta, uint64_t work, int ctas);
+// Raise the kernel's dynamic shared memory limit to at least `bytes`
+// (never lowers it, so graphs captured with a larger shape stay valid).
+cudaError_t raise_smem_attr(const void* kernel, size_t bytes);
 
 // Host helpers of the C ABI (api.cu).
 vsz_status make_geom(const vsz_params* p, Geom* g);

@@ -761,11 +761,23 @@ k_lorenzo_nd(const CompressArgs a) {
     }
 }
 
+// Block-size bounds of the batch kernels: up to 8 warps per CTA, chosen at
+// launch, under the register cap of the one-field kernel (the same threads
+// per SM times registers per thread).
+template <int ND, int B>
+struct NdBatchBounds {
+    static constexpr int MAXT = 256;
+    static constexpr int PER_SM = NdCfg<ND, B>::THREADS * NdCfg<ND, B>::MINB_C;
+    static constexpr int MINB = PER_SM / MAXT > 0 ? PER_SM / MAXT : 1;
+    static constexpr int MINB_R = NdCfg<ND, B>::THREADS * NdCfg<ND, B>::MINB_R / MAXT > 0
+                                      ? NdCfg<ND, B>::THREADS * NdCfg<ND, B>::MINB_R / MAXT : 1;
+};
+
 // Many fields of one class (rank, block edge, padding kind): one queue over
 // the tiles of all of them.  tile_prefix[f] is the first global tile of field
-// f, tile_prefix[nfields] the total.
+// f, tile_prefix[nfields] the total.  Any warps per CTA up to 8.
 template <int ND, int B, bool BP, bool GP>
-__global__ void __launch_bounds__(NdCfg<ND, B>::THREADS, NdCfg<ND, B>::MINB_C)
+__global__ void __launch_bounds__(NdBatchBounds<ND, B>::MAXT, NdBatchBounds<ND, B>::MINB)
 k_lorenzo_nd_batch(const CompressArgs* __restrict__ fields, const uint64_t* __restrict__ tile_prefix, int nfields,
                    unsigned long long* ticket) {
     extern __shared__ __align__(16) unsigned char smem_raw[];

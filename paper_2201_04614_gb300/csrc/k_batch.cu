@@ -13,7 +13,12 @@
 //                         the field's padding value is known;
 //   k_batch_compact_scan  one CTA per field: chunk offsets and totals;
 //   k_batch_compact_move  one CTA per chunk of any field: final placement.
-// The sequence can be captured into a CUDA graph once and replayed.
+// Reconstruction of the batch (once output buffers are set) is a second
+// fixed sequence: one persistent inverse kernel per class (rank, block edge)
+// drawing tiles of all the class's fields from one queue, then one fixup
+// kernel over every field.  Each sequence can be captured into a CUDA graph
+// once and replayed.
+#include <algorithm>
 #include <climits>
 #include <cstring>
 #include <map>
@@ -29,7 +34,9 @@
 namespace vsz {
 
 constexpr uint64_t kItemElems = 1ull << 18;  // elements per statistics work item
-constexpr int kMaxClasses = 28;               // tickets in the batch header
+constexpr int kMaxClasses = 28;               // tickets in the batch header, per sequence
+constexpr size_t kBatchHeader = 512;          // compression tickets, then reconstruction tickets
+constexpr size_t kReconTickets = 256;         // byte offset of the reconstruction tickets
 
 struct BatchField {
     CompressArgs a;     // the field's pointers, geometry and workspace
@@ -173,6 +180,27 @@ __global__ void __launch_bounds__(256) k_batch_compact_move(const BatchField* __
     }
 }
 
+// Fixups of every field of a batch (blockIdx.x: field; blockIdx.y strides
+// over its list): the verbatim values of the error-bound guard.
+struct BatchFix {
+    const vsz_header* hdr;
+    const uint32_t* fix_idx;
+    const uint32_t* fix_bits;
+    uint64_t fix_cap;
+    float* out;
+    uint64_t n;
+};
+
+__global__ void __launch_bounds__(256) k_batch_fixups(const BatchFix* __restrict__ F) {
+    const BatchFix& f = F[blockIdx.x];
+    if (!f.out) return;
+    const uint64_t cnt = umin64(f.hdr->n_fix, f.fix_cap);
+    for (uint64_t i = (uint64_t)blockIdx.y * blockDim.x + threadIdx.x; i < cnt; i += (uint64_t)gridDim.y * blockDim.x) {
+        const uint32_t j = f.fix_idx[i];
+        if (j < f.n) f.out[j] = __uint_as_float(f.fix_bits[i]);
+    }
+}
+
 }  // namespace vsz
 
 // ---------------------------------------------------------------------------
@@ -183,11 +211,15 @@ using namespace vsz;
 struct BatchClass {
     int nd;
     uint32_t b;
-    int pk;                        // 0 zero padding, 1 per-block padding, 2 global padding
+    int pk;                        // 0 zero padding, 1 per-block padding, 2 global padding (compression)
+    int kind = 0;                  // 0 compression, 1 reconstruction
     std::vector<int> fields;       // indices into the batch
     CompressArgs* d_args = nullptr;
+    ReconArgs* d_rargs = nullptr;
     uint64_t* d_prefix = nullptr;
     uint64_t total_tiles = 0;
+    LaunchShape shape;             // launch shape of the class kernel (autotuned or set)
+    float ms_best = 0.0f, ms_default = 0.0f;  // autotuner measurements
 };
 
 struct vsz_batch_st {
@@ -203,10 +235,18 @@ struct vsz_batch_st {
     unsigned long long* tickets = nullptr;  // in the caller's workspace
     bool use_graph = false;
     cudaGraphExec_t exec = nullptr;
+    bool concurrent = false;             // class kernels as parallel branches
+    std::vector<cudaStream_t> side;      // one per class after the first (concurrent mode)
+    std::vector<cudaEvent_t> ev;         // fork event, then one join event per side stream
+    // reconstruction (after vsz_batch_set_outputs)
+    std::vector<BatchClass> rclasses;
+    BatchFix* d_fix = nullptr;
+    bool rconcurrent = false;
+    cudaGraphExec_t rexec = nullptr;
 };
 
 static size_t batch_layout(const vsz_field_job* jobs, int n, std::vector<size_t>* offs, std::vector<Geom>* geoms) {
-    size_t off = 256;  // batch header: class tickets
+    size_t off = kBatchHeader;  // batch header: class tickets
     for (int i = 0; i < n; ++i) {
         Geom g;
         if (make_geom(&jobs[i].params, &g) != VSZ_OK) return 0;
@@ -218,9 +258,24 @@ static size_t batch_layout(const vsz_field_job* jobs, int n, std::vector<size_t>
     return off;
 }
 
+static void free_recon(vsz_batch_st* b) {
+    if (b->rexec) cudaGraphExecDestroy(b->rexec);
+    b->rexec = nullptr;
+    for (BatchClass& c : b->rclasses) {
+        if (c.d_rargs) cudaFree(c.d_rargs);
+        if (c.d_prefix) cudaFree(c.d_prefix);
+    }
+    b->rclasses.clear();
+    if (b->d_fix) cudaFree(b->d_fix);
+    b->d_fix = nullptr;
+}
+
 static void free_batch(vsz_batch_st* b) {
     if (!b) return;
     if (b->exec) cudaGraphExecDestroy(b->exec);
+    free_recon(b);  // also the reconstruction graph
+    for (cudaStream_t t : b->side) cudaStreamDestroy(t);
+    for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
     for (BatchClass& c : b->classes) {
         if (c.d_args) cudaFree(c.d_args);
         if (c.d_prefix) cudaFree(c.d_prefix);
@@ -240,7 +295,103 @@ static cudaError_t upload(T** dst, const std::vector<T>& v) {
     return e;
 }
 
-static vsz_status launch_sequence(vsz_batch_st* b, cudaStream_t s) {
+// Side streams and fork/join events of the concurrent mode (created once).
+static cudaError_t ensure_side_streams(vsz_batch_st* b) {
+    const size_t nc = std::max(b->classes.size(), b->rclasses.size());
+    const size_t want = nc ? nc - 1 : 0;
+    while (b->side.size() < want) {
+        cudaStream_t t = nullptr;
+        const cudaError_t e = cudaStreamCreateWithFlags(&t, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return e;
+        b->side.push_back(t);
+    }
+    while (b->ev.size() < want + 1) {
+        cudaEvent_t v = nullptr;
+        const cudaError_t e = cudaEventCreateWithFlags(&v, cudaEventDisableTiming);
+        if (e != cudaSuccess) return e;
+        b->ev.push_back(v);
+    }
+    return cudaSuccess;
+}
+
+static unsigned long long* recon_tickets(vsz_batch_st* b) {
+    return (unsigned long long*)((char*)b->tickets + kReconTickets);
+}
+
+static cudaError_t launch_rclass(vsz_batch_st* b, size_t c, cudaStream_t s) {
+    BatchClass& k = b->rclasses[c];
+    TraceScope ts("batch_recon", s, k.nd, k.b);
+    unsigned long long* t = recon_tickets(b) + c;
+    return k.nd == 1 ? launch_recon_batch_1d(k.b, k.d_rargs, k.d_prefix, (int)k.fields.size(), k.total_tiles, t,
+                                             k.shape, s)
+         : k.nd == 2 ? launch_recon_batch_2d(k.b, k.d_rargs, k.d_prefix, (int)k.fields.size(), k.total_tiles, t,
+                                             k.shape, s)
+                     : launch_recon_batch_3d(k.b, k.d_rargs, k.d_prefix, (int)k.fields.size(), k.total_tiles, t,
+                                             k.shape, s);
+}
+
+static cudaError_t launch_class(vsz_batch_st* b, size_t c, cudaStream_t s) {
+    BatchClass& k = b->classes[c];
+    TraceScope ts("batch_lorenzo", s, k.nd, k.b);
+    return k.nd == 1 ? launch_lorenzo_batch_1d(k.b, k.pk, k.d_args, k.d_prefix, (int)k.fields.size(), k.total_tiles,
+                                               b->tickets + c, k.shape, s)
+         : k.nd == 2 ? launch_lorenzo_batch_2d(k.b, k.pk, k.d_args, k.d_prefix, (int)k.fields.size(), k.total_tiles,
+                                               b->tickets + c, k.shape, s)
+                     : launch_lorenzo_batch_3d(k.b, k.pk, k.d_args, k.d_prefix, (int)k.fields.size(), k.total_tiles,
+                                               b->tickets + c, k.shape, s);
+}
+
+// Optional events around one class kernel (the autotuner's measurement).
+struct ClassTimer {
+    int kind = 0;  // 0 compression, 1 reconstruction
+    int cls = -1;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+};
+
+// The class kernels of one sequence (kind 0: compression, 1: reconstruction),
+// one after another, or as parallel branches forked from `s` and joined back.
+static vsz_status run_classes(vsz_batch_st* b, int kind, cudaStream_t s, const ClassTimer* tm) {
+    std::vector<BatchClass>& cls = kind ? b->rclasses : b->classes;
+    const bool conc = kind ? b->rconcurrent : b->concurrent;
+    auto launch = [&](size_t c, cudaStream_t t) { return kind ? launch_rclass(b, c, t) : launch_class(b, c, t); };
+    cudaError_t e;
+    std::vector<size_t> run;
+    for (size_t c = 0; c < cls.size(); ++c)
+        if (cls[c].total_tiles) run.push_back(c);
+    if (conc && run.size() > 1 && !tm) {
+        // the first class on `s`, every other on its own side stream
+        if ((e = ensure_side_streams(b)) != cudaSuccess) return cuda_fail(e);
+        if ((e = cudaEventRecord(b->ev[0], s)) != cudaSuccess) return cuda_fail(e);
+        for (size_t i = 1; i < run.size(); ++i)
+            if ((e = cudaStreamWaitEvent(b->side[i - 1], b->ev[0], 0)) != cudaSuccess) return cuda_fail(e);
+        for (size_t i = 0; i < run.size(); ++i)
+            if ((e = launch(run[i], i == 0 ? s : b->side[i - 1])) != cudaSuccess) return cuda_fail(e);
+        for (size_t i = 1; i < run.size(); ++i) {
+            if ((e = cudaEventRecord(b->ev[i], b->side[i - 1])) != cudaSuccess) return cuda_fail(e);
+            if ((e = cudaStreamWaitEvent(s, b->ev[i], 0)) != cudaSuccess) return cuda_fail(e);
+        }
+        return VSZ_OK;
+    }
+    for (size_t c : run) {
+        const bool timed = tm && tm->kind == kind && tm->cls == (int)c;
+        if (timed && (e = cudaEventRecord(tm->e0, s)) != cudaSuccess) return cuda_fail(e);
+        if ((e = launch(c, s)) != cudaSuccess) return cuda_fail(e);
+        if (timed && (e = cudaEventRecord(tm->e1, s)) != cudaSuccess) return cuda_fail(e);
+    }
+    return VSZ_OK;
+}
+
+static vsz_status launch_recon_sequence(vsz_batch_st* b, cudaStream_t s, const ClassTimer* tm = nullptr) {
+    cudaError_t e = cudaMemsetAsync(recon_tickets(b), 0, kMaxClasses * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    const vsz_status st = run_classes(b, 1, s, tm);
+    if (st != VSZ_OK) return st;
+    TraceScope ts("batch_fixups", s);
+    k_batch_fixups<<<dim3((unsigned)b->n, 4), 256, 0, s>>>(b->d_fix);
+    return (e = cudaGetLastError()) == cudaSuccess ? VSZ_OK : cuda_fail(e);
+}
+
+static vsz_status launch_sequence(vsz_batch_st* b, cudaStream_t s, const ClassTimer* tm = nullptr) {
     cudaError_t e;
     {
         TraceScope ts("batch_begin", s);
@@ -254,17 +405,10 @@ static vsz_status launch_sequence(vsz_batch_st* b, cudaStream_t s) {
         k_batch_range<<<grid, 256, 0, s>>>(b->d_fields, b->n, b->d_range_prefix, b->range_items);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
     }
-    for (size_t c = 0; c < b->classes.size(); ++c) {
-        BatchClass& k = b->classes[c];
-        if (!k.total_tiles) continue;
-        TraceScope ts("batch_lorenzo", s, k.nd, k.b);
-        e = k.nd == 1 ? launch_lorenzo_batch_1d(k.b, k.pk, k.d_args, k.d_prefix, (int)k.fields.size(), k.total_tiles,
-                                                b->tickets + c, s)
-          : k.nd == 2 ? launch_lorenzo_batch_2d(k.b, k.pk, k.d_args, k.d_prefix, (int)k.fields.size(), k.total_tiles,
-                                                b->tickets + c, s)
-                      : launch_lorenzo_batch_3d(k.b, k.pk, k.d_args, k.d_prefix, (int)k.fields.size(), k.total_tiles,
-                                                b->tickets + c, s);
-        if (e != cudaSuccess) return cuda_fail(e);
+    {
+        // forked after the range pass, joined before the origin pass
+        const vsz_status st = run_classes(b, 0, s, tm);
+        if (st != VSZ_OK) return st;
     }
     if (b->origin_items) {
         TraceScope ts("batch_origin_fix", s);
@@ -425,6 +569,256 @@ vsz_status vsz_batch_submit(vsz_batch b, void* stream) {
     }
     const cudaError_t e = cudaGraphLaunch(b->exec, s);
     return e == cudaSuccess ? VSZ_OK : cuda_fail(e);
+}
+
+vsz_status vsz_batch_set_outputs(vsz_batch b, float* const* h_xhat) {
+    if (!b || !h_xhat) return VSZ_ERR_INVALID_ARG;
+    for (int i = 0; i < b->n; ++i)
+        if (b->fields[i].a.g.n > 0 && !h_xhat[i]) return VSZ_ERR_INVALID_ARG;
+    free_recon(b);
+    std::map<std::pair<int, uint32_t>, int> cls;
+    std::vector<BatchFix> fix((size_t)b->n);
+    std::vector<ReconArgs> ra((size_t)b->n);
+    for (int i = 0; i < b->n; ++i) {
+        const vsz_field_job& j = b->jobs[i];
+        const Geom& g = b->fields[i].a.g;
+        ReconArgs& a = ra[i];
+        std::memset(&a, 0, sizeof a);
+        a.codes = j.out.codes;
+        a.pad = j.out.pad;
+        a.blk_off = j.out.blk_off;
+        a.out_idx = j.out.out_idx;
+        a.out_delta = j.out.out_delta;
+        a.out_cap = j.out.out_cap;
+        a.ticket = nullptr;
+        a.hdr = j.out.hdr;
+        a.out = h_xhat[i];
+        a.g = g;
+        a.R = (int32_t)j.params.radius;
+        a.pad_mode = j.params.pad;
+        a.vec = (aligned(j.out.codes, 16) && aligned(h_xhat[i], 16) && (g.nd == 1 || g.nx % 4 == 0)) ? 1 : 0;
+        fix[i] = BatchFix{j.out.hdr, j.out.fix_idx, j.out.fix_bits, j.out.fix_cap,
+                          g.n > 0 && j.out.fix_cap > 0 ? h_xhat[i] : nullptr, g.n};
+        if (!g.ntiles) continue;
+        const auto key = std::make_pair(g.nd, g.b);
+        auto it = cls.find(key);
+        if (it == cls.end()) {
+            BatchClass c;
+            c.nd = g.nd;
+            c.b = g.b;
+            c.pk = 0;
+            c.kind = 1;
+            b->rclasses.push_back(c);
+            it = cls.emplace(key, (int)b->rclasses.size() - 1).first;
+        }
+        b->rclasses[it->second].fields.push_back(i);
+    }
+    cudaError_t e = upload(&b->d_fix, fix);
+    for (BatchClass& c : b->rclasses) {
+        if (e != cudaSuccess) break;
+        std::vector<ReconArgs> args;
+        std::vector<uint64_t> pre(1, 0);
+        for (int i : c.fields) {
+            args.push_back(ra[i]);
+            pre.push_back(pre.back() + ra[i].g.ntiles);
+        }
+        c.total_tiles = pre.back();
+        e = upload(&c.d_rargs, args);
+        if (e == cudaSuccess) e = upload(&c.d_prefix, pre);
+    }
+    if (e != cudaSuccess) {
+        free_recon(b);
+        return cuda_fail(e);
+    }
+    return VSZ_OK;
+}
+
+vsz_status vsz_batch_reconstruct(vsz_batch b, void* stream) {
+    if (!b || !b->d_fix) return VSZ_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!b->use_graph || s == nullptr || s == cudaStreamLegacy || Tracer::get().on())
+        return launch_recon_sequence(b, s);
+    if (!b->rexec) {
+        cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(e);
+        const vsz_status st = launch_recon_sequence(b, s);
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(s, &graph);
+        if (st != VSZ_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (e != cudaSuccess) return cuda_fail(e);
+        e = cudaGraphInstantiate(&b->rexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            b->rexec = nullptr;
+            return cuda_fail(e);
+        }
+    }
+    const cudaError_t e = cudaGraphLaunch(b->rexec, s);
+    return e == cudaSuccess ? VSZ_OK : cuda_fail(e);
+}
+
+int vsz_batch_num_classes(vsz_batch b) { return b ? (int)(b->classes.size() + b->rclasses.size()) : 0; }
+
+// Class c of the combined list: compression classes, then reconstruction ones.
+static BatchClass* class_at(vsz_batch_st* b, int c) {
+    if (!b || c < 0) return nullptr;
+    if ((size_t)c < b->classes.size()) return &b->classes[c];
+    c -= (int)b->classes.size();
+    return (size_t)c < b->rclasses.size() ? &b->rclasses[c] : nullptr;
+}
+
+vsz_status vsz_batch_get_class(vsz_batch b, int c, vsz_batch_class* out) {
+    const BatchClass* k = class_at(b, c);
+    if (!k || !out) return VSZ_ERR_INVALID_ARG;
+    std::memset(out, 0, sizeof *out);
+    out->ndim = k->nd;
+    out->block = k->b;
+    out->pad_kind = k->pk;
+    out->nfields = (int32_t)k->fields.size();
+    out->tiles = k->total_tiles;
+    out->warps = k->shape.warps;
+    out->ctas_per_sm = k->shape.ctas;
+    out->ms = k->ms_best;
+    out->ms_default = k->ms_default;
+    out->concurrent = (k->kind ? b->rconcurrent : b->concurrent) ? 1 : 0;
+    out->kind = k->kind;
+    return VSZ_OK;
+}
+
+static void drop_graphs(vsz_batch_st* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+    if (b->rexec) cudaGraphExecDestroy(b->rexec);
+    b->rexec = nullptr;
+}
+
+static int class_occupancy(const BatchClass& k, int warps) {
+    int occ = 0;
+    const LaunchShape sh{warps, 0};
+    cudaError_t e;
+    if (k.kind == 0)
+        e = k.nd == 1 ? launch_lorenzo_batch_1d(k.b, k.pk, nullptr, nullptr, 0, 0, nullptr, sh, nullptr, &occ)
+          : k.nd == 2 ? launch_lorenzo_batch_2d(k.b, k.pk, nullptr, nullptr, 0, 0, nullptr, sh, nullptr, &occ)
+                      : launch_lorenzo_batch_3d(k.b, k.pk, nullptr, nullptr, 0, 0, nullptr, sh, nullptr, &occ);
+    else
+        e = k.nd == 1 ? launch_recon_batch_1d(k.b, nullptr, nullptr, 0, 0, nullptr, sh, nullptr, &occ)
+          : k.nd == 2 ? launch_recon_batch_2d(k.b, nullptr, nullptr, 0, 0, nullptr, sh, nullptr, &occ)
+                      : launch_recon_batch_3d(k.b, nullptr, nullptr, 0, 0, nullptr, sh, nullptr, &occ);
+    return e == cudaSuccess ? occ : 0;
+}
+
+vsz_status vsz_batch_set_shape(vsz_batch b, int c, int warps, int ctas_per_sm) {
+    BatchClass* k = class_at(b, c);
+    if (!k) return VSZ_ERR_INVALID_ARG;
+    if (!(warps == 0 || warps == 2 || warps == 4 || warps == 8) || ctas_per_sm < 0 || ctas_per_sm > 64)
+        return VSZ_ERR_INVALID_ARG;
+    if (class_occupancy(*k, warps) < 1) return VSZ_ERR_UNSUPPORTED;
+    k->shape = LaunchShape{warps, ctas_per_sm};
+    drop_graphs(b);
+    return VSZ_OK;
+}
+
+vsz_status vsz_batch_set_concurrent(vsz_batch b, int on) {
+    if (!b) return VSZ_ERR_INVALID_ARG;
+    b->concurrent = b->rconcurrent = on != 0;
+    drop_graphs(b);
+    return VSZ_OK;
+}
+
+vsz_status vsz_batch_autotune(vsz_batch b, void* stream, int reps) {
+    if (!b || reps < 1 || reps > 50) return VSZ_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (cs != cudaStreamCaptureStatusNone) return VSZ_ERR_INVALID_ARG;
+    drop_graphs(b);
+    ClassTimer tm;
+    if ((e = cudaEventCreate(&tm.e0)) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaEventCreate(&tm.e1)) != cudaSuccess) {
+        cudaEventDestroy(tm.e0);
+        return cuda_fail(e);
+    }
+    // median device time of `reps` runs of a sequence (kind 0 compression,
+    // 1 reconstruction), with events around class `cls` or, when cls < 0,
+    // around the whole sequence
+    auto measure = [&](int kind, int cls, float* ms) -> vsz_status {
+        std::vector<float> t;
+        for (int r = 0; r < reps; ++r) {
+            tm.kind = kind;
+            tm.cls = cls;
+            cudaError_t e2 = cudaSuccess;
+            if (cls < 0 && (e2 = cudaEventRecord(tm.e0, s)) != cudaSuccess) return cuda_fail(e2);
+            const ClassTimer* tp = cls < 0 ? nullptr : &tm;
+            const vsz_status st2 = kind ? launch_recon_sequence(b, s, tp) : launch_sequence(b, s, tp);
+            if (st2 != VSZ_OK) return st2;
+            if (cls < 0 && (e2 = cudaEventRecord(tm.e1, s)) != cudaSuccess) return cuda_fail(e2);
+            if ((e2 = cudaEventSynchronize(tm.e1)) != cudaSuccess) return cuda_fail(e2);
+            float v = 0.0f;
+            if ((e2 = cudaEventElapsedTime(&v, tm.e0, tm.e1)) != cudaSuccess) return cuda_fail(e2);
+            t.push_back(v);
+        }
+        std::sort(t.begin(), t.end());
+        *ms = t[t.size() / 2];
+        return VSZ_OK;
+    };
+    const bool conc0 = b->concurrent, rconc0 = b->rconcurrent;
+    b->concurrent = b->rconcurrent = false;
+    vsz_status st = launch_sequence(b, s);  // warm-up; the compressed data the inverse reads
+    for (int kind = 0; kind < 2 && st == VSZ_OK; ++kind) {
+        std::vector<BatchClass>& cls = kind ? b->rclasses : b->classes;
+        for (size_t c = 0; st == VSZ_OK && c < cls.size(); ++c) {
+            BatchClass& k = cls[c];
+            if (!k.total_tiles) continue;
+            k.shape = LaunchShape{};
+            float best = 0.0f;
+            if ((st = measure(kind, (int)c, &best)) != VSZ_OK) break;
+            k.ms_default = best;
+            LaunchShape pick{};
+            for (int w : {2, 4, 8}) {
+                const int occ = class_occupancy(k, w);
+                if (occ < 1) continue;
+                std::vector<int> cands = {1, 2, 4, occ};
+                std::sort(cands.begin(), cands.end());
+                cands.erase(std::unique(cands.begin(), cands.end()), cands.end());
+                for (int ct : cands) {
+                    if (ct > occ) continue;
+                    k.shape = LaunchShape{w, ct};
+                    float ms = 0.0f;
+                    if ((st = measure(kind, (int)c, &ms)) != VSZ_OK) break;
+                    if (ms < best) {
+                        best = ms;
+                        pick = k.shape;
+                    }
+                }
+                if (st != VSZ_OK) break;
+            }
+            k.shape = pick;
+            k.ms_best = best;
+        }
+        if (st != VSZ_OK) break;
+        int active = 0;
+        for (const BatchClass& k : cls) active += k.total_tiles ? 1 : 0;
+        if (active > 1) {
+            bool& flag = kind ? b->rconcurrent : b->concurrent;
+            float ser = 0.0f, con = 0.0f;
+            flag = false;
+            if ((st = measure(kind, -1, &ser)) != VSZ_OK) break;
+            flag = true;
+            if ((st = measure(kind, -1, &con)) != VSZ_OK) break;
+            flag = con < ser;
+        }
+    }
+    if (st != VSZ_OK) {
+        b->concurrent = conc0;
+        b->rconcurrent = rconc0;
+    }
+    cudaEventDestroy(tm.e0);
+    cudaEventDestroy(tm.e1);
+    return st;
 }
 
 vsz_status vsz_batch_destroy(vsz_batch b) {

@@ -262,21 +262,17 @@ __global__ void __launch_bounds__(256) k_lorenzo_1d_batch(const CompressArgs* __
 // ---------------------------------------------------------------------------
 // Inverse: codes -> residuals (outliers patched by their rank inside the
 // block), block origin += P, segmented inclusive scan, x_hat = q * ebx2.
+// One step st (32*EPL elements) of one field; ebx2 and Pg from its header.
 template <int B, bool QOUT>
-__global__ void __launch_bounds__(256) k_recon_1d(const ReconArgs a) {
+__device__ __forceinline__ void recon_1d_step(const ReconArgs& a, const uint64_t st, const int lane,
+                                              const float ebx2, const int32_t Pg) {
     using C = Cfg1<B>;
     constexpr int EPL = C::EPL, G = C::G, SPAN = C::SPAN;
-    const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    const float ebx2 = a.hdr->ebx2;
-    const int32_t Pg = a.hdr->pad_global;
     const int32_t R = a.R;
     const uint64_t n = a.g.n;
     const int glane = lane & (G - 1);
     const bool bp = is_block_pad(a.pad_mode);
-    const uint64_t nsteps = (n + SPAN - 1) / SPAN;
-
-    for (uint64_t st = (uint64_t)blockIdx.x * C::WARPS + wib; st < nsteps; st += (uint64_t)gridDim.x * C::WARPS) {
+    {
         const uint64_t base = st * SPAN + (uint64_t)lane * EPL;
         const int valid = base < n ? (int)umin64(EPL, n - base) : 0;
         const bool vec = a.vec && valid == EPL;
@@ -374,6 +370,47 @@ __global__ void __launch_bounds__(256) k_recon_1d(const ReconArgs a) {
     }
 }
 
+template <int B, bool QOUT>
+__global__ void __launch_bounds__(256) k_recon_1d(const ReconArgs a) {
+    using C = Cfg1<B>;
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const float ebx2 = a.hdr->ebx2;
+    const int32_t Pg = a.hdr->pad_global;
+    const uint64_t nsteps = (a.g.n + C::SPAN - 1) / C::SPAN;
+    for (uint64_t st = (uint64_t)blockIdx.x * C::WARPS + wib; st < nsteps; st += (uint64_t)gridDim.x * C::WARPS)
+        recon_1d_step<B, QOUT>(a, st, lane, ebx2, Pg);
+}
+
+// Many 1D fields with the same block length: one queue over their tiles of
+// kChunk1D values (tile_prefix as for the batch compression).
+template <int B>
+__global__ void __launch_bounds__(256) k_recon_1d_batch(const ReconArgs* __restrict__ fields,
+                                                        const uint64_t* __restrict__ tile_prefix, int nfields,
+                                                        unsigned long long* ticket) {
+    using C = Cfg1<B>;
+    const int lane = threadIdx.x & 31;
+    const uint64_t total = tile_prefix[nfields];
+    for (;;) {
+        unsigned long long tk = 0;
+        if (lane == 0) tk = atomicAdd(ticket, 1ull);
+        const uint64_t gt = __shfl_sync(VSZ_FULL, tk, 0);
+        if (gt >= total) break;
+        int lo = 0, hi = nfields - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (tile_prefix[mid] <= gt) lo = mid; else hi = mid - 1;
+        }
+        const ReconArgs& a = fields[lo];
+        const float ebx2 = a.hdr->ebx2;
+        const int32_t Pg = a.hdr->pad_global;
+        const uint64_t st0 = (gt - tile_prefix[lo]) * C::STEPS;
+        const uint64_t nsteps = (a.g.n + C::SPAN - 1) / C::SPAN;
+        const uint64_t st1 = umin64(nsteps, st0 + C::STEPS);
+        for (uint64_t st = st0; st < st1; ++st) recon_1d_step<B, false>(a, st, lane, ebx2, Pg);
+    }
+}
+
 // ---------------------------------------------------------------------------
 template <int B, bool BP, bool GP>
 static cudaError_t launch_c1_k(const CompressArgs& a, cudaStream_t s) {
@@ -392,20 +429,50 @@ static cudaError_t launch_c1(const CompressArgs& a, cudaStream_t s) {
 
 template <int B, bool BP, bool GP>
 static cudaError_t launch_c1_batch_k(const CompressArgs* fields, const uint64_t* tile_prefix, int nfields,
-                                     uint64_t total_tiles, unsigned long long* ticket, cudaStream_t s) {
+                                     uint64_t total_tiles, unsigned long long* ticket, LaunchShape sh,
+                                     cudaStream_t s, int* occ) {
     const void* k = (const void*)k_lorenzo_1d_batch<B, BP, GP>;
-    const int grid = grid_for(k, 256, 0, Cfg1<B>::WARPS, total_tiles);
-    k_lorenzo_1d_batch<B, BP, GP><<<grid, 256, 0, s>>>(fields, tile_prefix, nfields, ticket);
+    const int warps = sh.warps > 0 ? sh.warps : Cfg1<B>::WARPS;
+    if (warps > 8) {
+        if (occ) *occ = 0;
+        return occ ? cudaSuccess : cudaErrorInvalidValue;
+    }
+    if (occ) {
+        *occ = occupancy(k, warps * 32, 0);
+        return cudaSuccess;
+    }
+    const int grid = grid_shape(k, warps * 32, 0, (uint64_t)warps, total_tiles, sh.ctas);
+    k_lorenzo_1d_batch<B, BP, GP><<<grid, warps * 32, 0, s>>>(fields, tile_prefix, nfields, ticket);
     return cudaGetLastError();
 }
 
 // pk: 0 zero padding, 1 per-block padding, 2 global padding
 template <int B>
 static cudaError_t launch_c1_batch(int pk, const CompressArgs* fields, const uint64_t* tile_prefix, int nfields,
-                                   uint64_t total_tiles, unsigned long long* ticket, cudaStream_t s) {
-    if (pk == 1) return launch_c1_batch_k<B, true, false>(fields, tile_prefix, nfields, total_tiles, ticket, s);
-    if (pk == 2) return launch_c1_batch_k<B, false, true>(fields, tile_prefix, nfields, total_tiles, ticket, s);
-    return launch_c1_batch_k<B, false, false>(fields, tile_prefix, nfields, total_tiles, ticket, s);
+                                   uint64_t total_tiles, unsigned long long* ticket, LaunchShape sh, cudaStream_t s,
+                                   int* occ) {
+    if (pk == 1) return launch_c1_batch_k<B, true, false>(fields, tile_prefix, nfields, total_tiles, ticket, sh, s, occ);
+    if (pk == 2) return launch_c1_batch_k<B, false, true>(fields, tile_prefix, nfields, total_tiles, ticket, sh, s, occ);
+    return launch_c1_batch_k<B, false, false>(fields, tile_prefix, nfields, total_tiles, ticket, sh, s, occ);
+}
+
+template <int B>
+static cudaError_t launch_r1_batch(const ReconArgs* fields, const uint64_t* tile_prefix, int nfields,
+                                   uint64_t total_tiles, unsigned long long* ticket, LaunchShape sh, cudaStream_t s,
+                                   int* occ) {
+    const void* k = (const void*)k_recon_1d_batch<B>;
+    const int warps = sh.warps > 0 ? sh.warps : Cfg1<B>::WARPS;
+    if (warps > 8) {
+        if (occ) *occ = 0;
+        return occ ? cudaSuccess : cudaErrorInvalidValue;
+    }
+    if (occ) {
+        *occ = occupancy(k, warps * 32, 0);
+        return cudaSuccess;
+    }
+    const int grid = grid_shape(k, warps * 32, 0, (uint64_t)warps, total_tiles, sh.ctas);
+    k_recon_1d_batch<B><<<grid, warps * 32, 0, s>>>(fields, tile_prefix, nfields, ticket);
+    return cudaGetLastError();
 }
 
 template <int B>
@@ -432,15 +499,16 @@ cudaError_t launch_lorenzo_1d(const CompressArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_lorenzo_batch_1d(uint32_t b, int pk, const CompressArgs* fields, const uint64_t* tile_prefix,
-                                    int nfields, uint64_t total_tiles, unsigned long long* ticket, cudaStream_t s) {
+                                    int nfields, uint64_t total_tiles, unsigned long long* ticket, LaunchShape sh,
+                                    cudaStream_t s, int* occ) {
     switch (b) {
-    case 4: return launch_c1_batch<4>(pk, fields, tile_prefix, nfields, total_tiles, ticket, s);
-    case 8: return launch_c1_batch<8>(pk, fields, tile_prefix, nfields, total_tiles, ticket, s);
-    case 16: return launch_c1_batch<16>(pk, fields, tile_prefix, nfields, total_tiles, ticket, s);
-    case 32: return launch_c1_batch<32>(pk, fields, tile_prefix, nfields, total_tiles, ticket, s);
-    case 64: return launch_c1_batch<64>(pk, fields, tile_prefix, nfields, total_tiles, ticket, s);
-    case 128: return launch_c1_batch<128>(pk, fields, tile_prefix, nfields, total_tiles, ticket, s);
-    case 256: return launch_c1_batch<256>(pk, fields, tile_prefix, nfields, total_tiles, ticket, s);
+    case 4: return launch_c1_batch<4>(pk, fields, tile_prefix, nfields, total_tiles, ticket, sh, s, occ);
+    case 8: return launch_c1_batch<8>(pk, fields, tile_prefix, nfields, total_tiles, ticket, sh, s, occ);
+    case 16: return launch_c1_batch<16>(pk, fields, tile_prefix, nfields, total_tiles, ticket, sh, s, occ);
+    case 32: return launch_c1_batch<32>(pk, fields, tile_prefix, nfields, total_tiles, ticket, sh, s, occ);
+    case 64: return launch_c1_batch<64>(pk, fields, tile_prefix, nfields, total_tiles, ticket, sh, s, occ);
+    case 128: return launch_c1_batch<128>(pk, fields, tile_prefix, nfields, total_tiles, ticket, sh, s, occ);
+    case 256: return launch_c1_batch<256>(pk, fields, tile_prefix, nfields, total_tiles, ticket, sh, s, occ);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -454,6 +522,21 @@ cudaError_t launch_recon_1d(const ReconArgs& a, bool q_out, cudaStream_t s) {
     case 64: return launch_r1<64>(a, q_out, s);
     case 128: return launch_r1<128>(a, q_out, s);
     case 256: return launch_r1<256>(a, q_out, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_recon_batch_1d(uint32_t b, const ReconArgs* fields, const uint64_t* tile_prefix, int nfields,
+                                  uint64_t total_tiles, unsigned long long* ticket, LaunchShape sh, cudaStream_t s,
+                                  int* occ) {
+    switch (b) {
+    case 4: return launch_r1_batch<4>(fields, tile_prefix, nfields, total_tiles, ticket, sh, s, occ);
+    case 8: return launch_r1_batch<8>(fields, tile_prefix, nfields, total_tiles, ticket, sh, s, occ);
+    case 16: return launch_r1_batch<16>(fields, tile_prefix, nfields, total_tiles, ticket, sh, s, occ);
+    case 32: return launch_r1_batch<32>(fields, tile_prefix, nfields, total_tiles, ticket, sh, s, occ);
+    case 64: return launch_r1_batch<64>(fields, tile_prefix, nfields, total_tiles, ticket, sh, s, occ);
+    case 128: return launch_r1_batch<128>(fields, tile_prefix, nfields, total_tiles, ticket, sh, s, occ);
+    case 256: return launch_r1_batch<256>(fields, tile_prefix, nfields, total_tiles, ticket, sh, s, occ);
     default: return cudaErrorInvalidValue;
     }
 }

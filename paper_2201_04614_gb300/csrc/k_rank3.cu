@@ -1,4 +1,5 @@
-// k_rank3.cu -- 3D instantiations of the fused compression and the inverse.
+// k_rank3.cu -- 3D instantiations of the fused compression and the inverse
+// (one field, and batches of fields).
 #include "recon_nd.cuh"
 
 namespace vsz {
@@ -14,12 +15,13 @@ cudaError_t launch_lorenzo_3d(const CompressArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_lorenzo_batch_3d(uint32_t b, int pk, const CompressArgs* fields, const uint64_t* tile_prefix,
-                                    int nfields, uint64_t total_tiles, unsigned long long* ticket, cudaStream_t s) {
+                                    int nfields, uint64_t total_tiles, unsigned long long* ticket, LaunchShape sh,
+                                    cudaStream_t s, int* occ) {
     switch (b) {
-    case 4: return launch_nd_compress_batch<3, 4>(pk, fields, tile_prefix, nfields, total_tiles, ticket, s);
-    case 8: return launch_nd_compress_batch<3, 8>(pk, fields, tile_prefix, nfields, total_tiles, ticket, s);
-    case 16: return launch_nd_compress_batch<3, 16>(pk, fields, tile_prefix, nfields, total_tiles, ticket, s);
-    case 32: return launch_nd_compress_batch<3, 32>(pk, fields, tile_prefix, nfields, total_tiles, ticket, s);
+    case 4: return launch_nd_compress_batch<3, 4>(pk, fields, tile_prefix, nfields, total_tiles, ticket, sh, s, occ);
+    case 8: return launch_nd_compress_batch<3, 8>(pk, fields, tile_prefix, nfields, total_tiles, ticket, sh, s, occ);
+    case 16: return launch_nd_compress_batch<3, 16>(pk, fields, tile_prefix, nfields, total_tiles, ticket, sh, s, occ);
+    case 32: return launch_nd_compress_batch<3, 32>(pk, fields, tile_prefix, nfields, total_tiles, ticket, sh, s, occ);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -30,6 +32,18 @@ cudaError_t launch_recon_3d(const ReconArgs& a, bool q_out, cudaStream_t s) {
     case 8: return launch_nd_recon<3, 8>(a, q_out, s);
     case 16: return launch_nd_recon<3, 16>(a, q_out, s);
     case 32: return launch_nd_recon<3, 32>(a, q_out, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_recon_batch_3d(uint32_t b, const ReconArgs* fields, const uint64_t* tile_prefix, int nfields,
+                                  uint64_t total_tiles, unsigned long long* ticket, LaunchShape sh, cudaStream_t s,
+                                  int* occ) {
+    switch (b) {
+    case 4: return launch_nd_recon_batch<3, 4>(fields, tile_prefix, nfields, total_tiles, ticket, sh, s, occ);
+    case 8: return launch_nd_recon_batch<3, 8>(fields, tile_prefix, nfields, total_tiles, ticket, sh, s, occ);
+    case 16: return launch_nd_recon_batch<3, 16>(fields, tile_prefix, nfields, total_tiles, ticket, sh, s, occ);
+    case 32: return launch_nd_recon_batch<3, 32>(fields, tile_prefix, nfields, total_tiles, ticket, sh, s, occ);
     default: return cudaErrorInvalidValue;
     }
 }

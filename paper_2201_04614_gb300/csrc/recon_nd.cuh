@@ -23,16 +23,14 @@
 
 namespace vsz {
 
+// The inverse of one tile t of one field, by one warp whose shared memory
+// slice is wsm.
 template <int ND, int B, bool QOUT>
-__global__ void __launch_bounds__(NdCfg<ND, B>::THREADS, NdCfg<ND, B>::MINB_R)
-k_recon_nd(const ReconArgs a) {
+__device__ __forceinline__ void nd_recon_tile(const ReconArgs& a, const uint64_t t, unsigned char* wsm,
+                                              const int lane) {
     using C = NdCfg<ND, B>;
     constexpr int G = C::G;
     constexpr int U = C::U;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    unsigned char* wsm = smem_raw + (size_t)wib * C::WARP_R;
     int4* zs = reinterpret_cast<int4*>(wsm + C::RING_R);
     uint32_t* const oc_idx0 = reinterpret_cast<uint32_t*>(wsm + C::RING_R + C::ZS_B);
     // interior tiles of 3D blocks up to 8 keep their z sums in registers, so
@@ -60,10 +58,423 @@ k_recon_nd(const ReconArgs a) {
     const int src = lane & ~(G - 1);
     const bool vec = a.vec != 0;
 
+    const uint64_t s = t % g.nseg;
+    const uint64_t rb = t / g.nseg;
+    const uint64_t by = rb % g.nby;
+    const uint64_t bz = rb / g.nby;
+    const uint64_t x0 = s * kSegCols + (uint64_t)lane * 4;
+    const uint64_t bx = (s * kSegCols) / B + (uint64_t)(lane / G);
+    const bool bexists = bx < g.nbx;
+    const int valid = x0 < nx ? (int)umin64(4, nx - x0) : 0;
+    const uint32_t vmask = (1u << valid) - 1u;
+    const bool full = vec && valid == 4;
+    const int ylen = (int)umin64(B, g.ny - by * B);
+    const int zlen = ND == 3 ? (int)umin64(B, g.nz - bz * B) : 1;
+    const int nbpp = (ylen + U - 1) / U;
+    const int nbatch = zlen * nbpp;
+    const uint64_t blk = (bz * g.nby + by) * g.nbx + bx;
+    const uint64_t tile_base = (ND == 3 ? bz * B * plane : 0) + by * B * nx + x0;
+
+    uint32_t lo = 0, hi = 0;
+    int32_t P = Pg;
+    if (first && bexists) {
+        lo = a.blk_off[blk];
+        hi = a.blk_off[blk + 1];
+        if (bp) P = a.pad[blk];
+    }
+    lo = __shfl_sync(VSZ_FULL, lo, src);
+    hi = __shfl_sync(VSZ_FULL, hi, src);
+    P = __shfl_sync(VSZ_FULL, P, src);
+    const bool anyout = __any_sync(VSZ_FULL, hi > lo);
+    uint32_t rank = lo;
+
+    // The tile's blocks are consecutive in canonical order, so its outliers
+    // are one slice of the list: bring it into shared memory with the first
+    // batch when it is short enough.
+    uint32_t lo_t = 0;
+    bool cached = false;
+    const bool interior = vec && s * kSegCols + kSegCols <= nx && ylen == B && (ND == 2 || zlen == B);
+    const uint32_t ocap = ZREG_R && interior ? OCAP_BIG : (uint32_t)C::OCAP;
+    uint32_t* const oc_idx = ZREG_R && interior ? reinterpret_cast<uint32_t*>(zs) : oc_idx0;
+    int32_t* const oc_del = reinterpret_cast<int32_t*>(oc_idx + ocap);
+    if (anyout) {
+        const uint64_t fb = (bz * g.nby + by) * g.nbx + (s * kSegCols) / B;
+        const uint64_t nblk = umin64(kSegCols / B, g.nbx - (s * kSegCols) / B);
+        uint32_t hi_t = 0;
+        if (lane == 0) {
+            lo_t = a.blk_off[fb];
+            hi_t = a.blk_off[fb + nblk];
+        }
+        lo_t = __shfl_sync(VSZ_FULL, lo_t, 0);
+        hi_t = __shfl_sync(VSZ_FULL, hi_t, 0);
+        cached = hi_t >= lo_t && hi_t - lo_t <= ocap && (uint64_t)hi_t <= a.out_cap;
+        if (cached) {
+            const uint32_t sidx = smem_addr(oc_idx), sdel = smem_addr(oc_del);
+            for (uint32_t i = lane; i < hi_t - lo_t; i += 32) {
+                cp_async4(sidx + 4 * i, a.out_idx + lo_t + i, 4u);
+                cp_async4(sdel + 4 * i, a.out_delta + lo_t + i, 4u);
+            }
+        }
+    }
+
+    // copy the codes of batch (lz, j) into ring half h (vector path only)
+    auto issue_batch = [&](int lz, int j, int h) {
+        if (vec) {
+            const uint64_t off0 = tile_base + (uint64_t)lz * plane + (uint64_t)(j * U) * nx;
+            const uint32_t dst0 = ring_wr + (uint32_t)(h * U * 32 * 8);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (j * U + u < ylen) {
+                    const uint64_t off = off0 + (uint64_t)u * nx;
+                    cp_async8(dst0 + u * 32 * 8, valid ? a.codes + off : a.codes, valid ? 8u : 0u);
+                }
+            }
+        }
+        cp_async_commit();
+    };
+
+    if (interior) {
+        // Lean walk of an interior tile: compile-time trip counts, 32-bit
+        // offsets, and P carried in the running-sum state (the z sums of
+        // 3D blocks start from P, the y sums of 2D blocks), which adds P
+        // to every element of the block exactly as adding it to the
+        // origin's residual before the sums does.  3D blocks of up to 8
+        // keep their z sums in registers (the rows of a plane unrolled).
+        constexpr int BPP = B / U;
+        constexpr int NPL = ND == 3 ? B : 1;
+        constexpr bool ZREG = ND == 3 && B <= 8;
+        constexpr int NB = NPL * BPP;
+        const uint32_t nx32 = (uint32_t)nx, pl32 = (uint32_t)plane;
+        const uint16_t* cl = a.codes + tile_base;
+        auto issue_fast = [&](int kb, int st) {
+            const uint16_t* src0 = cl + (uint32_t)(kb / BPP) * pl32 + (uint32_t)((kb % BPP) * U) * nx32;
+            const uint32_t dst0 = ring_wr + (uint32_t)(st * U * 32 * 8);
+#pragma unroll
+            for (int u = 0; u < U; ++u) cp_async8(dst0 + u * 32 * 8, src0 + (uint32_t)u * nx32, 8u);
+            cp_async_commit();
+        };
+#pragma unroll
+        for (int st = 0; st < C::NSR - 1; ++st) {
+            if (st < NB) issue_fast(st, st);
+            else cp_async_commit();
+        }
+        int32_t zr[ZREG ? B : 1][4];
+#pragma unroll
+        for (int ly = 0; ly < (ZREG ? B : 1); ++ly)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) zr[ly][k] = P;
+        if (ND == 3 && !ZREG) {
+#pragma unroll 4
+            for (int ly = 0; ly < B; ++ly) zs[ly * 32 + lane] = make_int4(P, P, P, P);
+        }
+        int32_t ys[4];
+        int h = 0, kb = 0;
+        for (int lz = 0; lz < NPL; ++lz) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) ys[k] = ND == 3 ? 0 : P;
+#pragma unroll(ZREG ? BPP : 1)
+            for (int jb = 0; jb < BPP; ++jb, ++kb) {
+                if (kb + C::NSR - 1 < NB) issue_fast(kb + C::NSR - 1, (kb + C::NSR - 1) % C::NSR);
+                else cp_async_commit();
+                cp_async_wait<C::NSR - 1>();
+                if (cached && kb == 0) __syncwarp();  // every lane's share of the outlier slice has landed
+                const uint32_t boff = (uint32_t)lz * pl32 + (uint32_t)(jb * U) * nx32;
+                const uint2* rr = ring_rd + h * U * 32;
+                uint2 cw[U];
+                uint32_t hz = 0;
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    cw[u] = rr[u * 32];
+                    hz |= ((cw[u].x - 0x00010001u) & ~cw[u].x & 0x80008000u) |
+                          ((cw[u].y - 0x00010001u) & ~cw[u].y & 0x80008000u);
+                }
+                const bool patch = anyout && __any_sync(VSZ_FULL, hz != 0u);
+                // one copy of the row code (the patch test is a uniform
+                // branch), which keeps the unrolled plane loop small
+                auto lrow = [&](int u) {
+                    const uint32_t c[4] = {cw[u].x & 0xffffu, cw[u].x >> 16, cw[u].y & 0xffffu, cw[u].y >> 16};
+                    int32_t d[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) d[k] = (int32_t)c[k] - R;
+                    if (patch) {
+                        uint32_t zm = 0;
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) zm |= (c[k] == 0u ? 1u : 0u) << k;
+                        if (__any_sync(VSZ_FULL, zm != 0u)) {
+                            const uint32_t cz = __popc(zm);
+                            uint32_t iz = cz;
+#pragma unroll
+                            for (int off = 1; off < G; off <<= 1) {
+                                const uint32_t y = __shfl_up_sync(VSZ_FULL, iz, off);
+                                if (glane >= off) iz += y;
+                            }
+                            const uint32_t gtot = __shfl_sync(VSZ_FULL, iz, src + G - 1);
+                            uint32_t r = rank + (iz - cz);
+                            const uint32_t roff = (uint32_t)tile_base + boff + (uint32_t)u * nx32;
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) {
+                                if (zm & (1u << k)) {
+                                    const bool in = r < hi && r < a.out_cap;
+                                    const uint32_t oi = !in ? ~0u : cached ? oc_idx[r - lo_t] : a.out_idx[r];
+                                    if (in && oi == roff + k) {
+                                        d[k] = cached ? oc_del[r - lo_t] : a.out_delta[r];
+                                    } else {
+                                        atomicMax(&a.hdr->recon_status, (unsigned)VSZ_ERR_CORRUPT);
+                                        d[k] = 0;
+                                    }
+                                    ++r;
+                                }
+                            }
+                            rank += gtot;
+                        }
+                    }
+                    // Sx
+                    d[1] = wadd(d[1], d[0]);
+                    d[2] = wadd(d[2], d[1]);
+                    d[3] = wadd(d[3], d[2]);
+                    {
+                        const uint32_t tot = (uint32_t)d[3];
+                        uint32_t inc = tot;
+#pragma unroll
+                        for (int off = 1; off < G; off <<= 1) {
+                            const uint32_t y = __shfl_up_sync(VSZ_FULL, inc, off);
+                            if (glane >= off) inc += y;
+                        }
+                        const int32_t ex = (int32_t)(inc - tot);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) d[k] = wadd(d[k], ex);
+                    }
+                    // Sy
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        d[k] = wadd(d[k], ys[k]);
+                        ys[k] = d[k];
+                    }
+                    // Sz
+                    if (ZREG) {
+                        const int ly = ZREG ? jb * U + u : 0;
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            d[k] = wadd(d[k], zr[ly][k]);
+                            zr[ly][k] = d[k];
+                        }
+                    } else if (ND == 3) {
+                        int4& stz = zs[(jb * U + u) * 32 + lane];
+                        const int4 pv = stz;
+                        d[0] = wadd(d[0], pv.x); d[1] = wadd(d[1], pv.y);
+                        d[2] = wadd(d[2], pv.z); d[3] = wadd(d[3], pv.w);
+                        stz = make_int4(d[0], d[1], d[2], d[3]);
+                    }
+                    const uint32_t ro = boff + (uint32_t)u * nx32;
+                    if (QOUT) {
+                        st_out4(reinterpret_cast<int4*>(reinterpret_cast<int32_t*>(a.out) + tile_base + ro),
+                                make_int4(d[0], d[1], d[2], d[3]));
+                    } else {
+                        int4 vv;
+                        if (fastcvt) {  // (float)q by the 1.5 * 2^23 bias, exact for |q| < 2^22
+                            vv.x = __float_as_int(__fmul_rn(__fsub_rn(__int_as_float(d[0] + 0x4B400000), 12582912.0f), ebx2));
+                            vv.y = __float_as_int(__fmul_rn(__fsub_rn(__int_as_float(d[1] + 0x4B400000), 12582912.0f), ebx2));
+                            vv.z = __float_as_int(__fmul_rn(__fsub_rn(__int_as_float(d[2] + 0x4B400000), 12582912.0f), ebx2));
+                            vv.w = __float_as_int(__fmul_rn(__fsub_rn(__int_as_float(d[3] + 0x4B400000), 12582912.0f), ebx2));
+                        } else {
+                            vv.x = __float_as_int(__fmul_rn(q2f(d[0]), ebx2));
+                            vv.y = __float_as_int(__fmul_rn(q2f(d[1]), ebx2));
+                            vv.z = __float_as_int(__fmul_rn(q2f(d[2]), ebx2));
+                            vv.w = __float_as_int(__fmul_rn(q2f(d[3]), ebx2));
+                        }
+                        st_out4(reinterpret_cast<int4*>(reinterpret_cast<float*>(a.out) + tile_base + ro), vv);
+                    }
+                };
+#pragma unroll
+                for (int u = 0; u < U; ++u) lrow(u);
+                h = h + 1 == C::NSR ? 0 : h + 1;
+            }
+        }
+        cp_async_wait<0>();
+        return;
+    }
+
+    int32_t ys[4] = {0, 0, 0, 0};
+    if (C::ZSMEM)
+        for (int ly = 0; ly < ylen; ++ly) zs[ly * 32 + lane] = make_int4(0, 0, 0, 0);
+
+    int ilz = 0, ij = 0;  // next batch to issue
+#pragma unroll
+    for (int st = 0; st < C::NSR - 1; ++st) {
+        if (st < nbatch) {
+            issue_batch(ilz, ij, st);
+            if (++ij == nbpp) { ij = 0; ++ilz; }
+        } else {
+            cp_async_commit();
+        }
+    }
+    int lz = 0, j = 0, h = 0, hs = C::NSR - 1;
+    for (int kb = 0; kb < nbatch; ++kb) {
+        int nj = j + 1, nlz = lz;
+        if (nj == nbpp) { nj = 0; ++nlz; }
+        if (kb + C::NSR - 1 < nbatch) {
+            issue_batch(ilz, ij, hs);
+            if (++ij == nbpp) { ij = 0; ++ilz; }
+        } else {
+            cp_async_commit();
+        }
+        cp_async_wait<C::NSR - 1>();
+        if (cached && kb == 0) __syncwarp();  // every lane's share of the outlier slice has landed
+        if (j == 0) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) ys[k] = 0;
+        }
+        const uint64_t boff = tile_base + (uint64_t)lz * plane + (uint64_t)(j * U) * nx;
+        const bool b0 = kb == 0;
+        // Codes of the batch; rows past the edge read as "no outlier".
+        uint2 cw[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (j * U + u < ylen) {
+                if (vec) {
+                    cw[u] = ring_rd[(h * U + u) * 32];
+                } else {
+                    uint32_t c4[4];
+                    load4c(a.codes + boff + (uint64_t)u * nx, valid, false, c4);
+                    const uint32_t rr = (uint32_t)R;
+                    cw[u] = make_uint2((valid > 0 ? c4[0] : rr) | ((valid > 1 ? c4[1] : rr) << 16),
+                                       (valid > 2 ? c4[2] : rr) | ((valid > 3 ? c4[3] : rr) << 16));
+                }
+            } else {
+                cw[u] = make_uint2(0x00010001u, 0x00010001u);
+            }
+        }
+        // Does any code 0 (an outlier) occur in this batch?
+        uint32_t hz = 0;
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            hz |= ((cw[u].x - 0x00010001u) & ~cw[u].x & 0x80008000u) |
+                  ((cw[u].y - 0x00010001u) & ~cw[u].y & 0x80008000u);
+        const bool patch = anyout && __any_sync(VSZ_FULL, valid > 0 && hz != 0u);
+
+        auto row = [&](auto patch_tag, int u) {
+            constexpr bool PATCH = decltype(patch_tag)::value;
+            const int ly = j * U + u;
+            const uint64_t roff = boff + (uint64_t)u * nx;
+            const uint32_t c[4] = {cw[u].x & 0xffffu, cw[u].x >> 16, cw[u].y & 0xffffu, cw[u].y >> 16};
+            int32_t d[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) d[k] = (int32_t)c[k] - R;
+            if (PATCH) {
+                uint32_t zm = 0;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) zm |= (c[k] == 0u ? 1u : 0u) << k;
+                zm &= vmask;
+                if (__any_sync(VSZ_FULL, zm != 0u)) {
+                    const uint32_t cz = __popc(zm);
+                    uint32_t iz = cz;
+#pragma unroll
+                    for (int off = 1; off < G; off <<= 1) {
+                        const uint32_t y = __shfl_up_sync(VSZ_FULL, iz, off);
+                        if (glane >= off) iz += y;
+                    }
+                    const uint32_t gtot = __shfl_sync(VSZ_FULL, iz, src + G - 1);
+                    uint32_t r = rank + (iz - cz);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        if (zm & (1u << k)) {
+                            const bool in = r < hi && r < a.out_cap;
+                            const uint32_t oi = !in ? ~0u : cached ? oc_idx[r - lo_t] : a.out_idx[r];
+                            if (in && oi == (uint32_t)(roff + k)) {
+                                d[k] = cached ? oc_del[r - lo_t] : a.out_delta[r];
+                            } else {
+                                atomicMax(&a.hdr->recon_status, (unsigned)VSZ_ERR_CORRUPT);
+                                d[k] = 0;
+                            }
+                            ++r;
+                        }
+                    }
+                    rank += gtot;
+                }
+            }
+            if (b0 && u == 0 && first) d[0] = wadd(d[0], P);
+            // Sx
+            d[1] = wadd(d[1], d[0]);
+            d[2] = wadd(d[2], d[1]);
+            d[3] = wadd(d[3], d[2]);
+            {
+                const uint32_t tot = (uint32_t)d[3];
+                uint32_t inc = tot;
+#pragma unroll
+                for (int off = 1; off < G; off <<= 1) {
+                    const uint32_t y = __shfl_up_sync(VSZ_FULL, inc, off);
+                    if (glane >= off) inc += y;
+                }
+                const int32_t ex = (int32_t)(inc - tot);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) d[k] = wadd(d[k], ex);
+            }
+            // Sy
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                d[k] = wadd(d[k], ys[k]);
+                ys[k] = d[k];
+            }
+            // Sz
+            if (C::ZSMEM) {
+                int4& stz = zs[ly * 32 + lane];
+                const int4 pv = stz;
+                d[0] = wadd(d[0], pv.x); d[1] = wadd(d[1], pv.y);
+                d[2] = wadd(d[2], pv.z); d[3] = wadd(d[3], pv.w);
+                stz = make_int4(d[0], d[1], d[2], d[3]);
+            }
+            if (QOUT) {
+                int32_t* o = reinterpret_cast<int32_t*>(a.out) + roff;
+                if (full) {
+                    *reinterpret_cast<int4*>(o) = make_int4(d[0], d[1], d[2], d[3]);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if (k < valid) o[k] = d[k];
+                }
+            } else {
+                float vv[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) vv[k] = __fmul_rn(q2f(d[k]), ebx2);
+                float* o = reinterpret_cast<float*>(a.out) + roff;
+                if (full) {
+                    *reinterpret_cast<float4*>(o) = make_float4(vv[0], vv[1], vv[2], vv[3]);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if (k < valid) o[k] = vv[k];
+                }
+            }
+        };
+        if (patch) {
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (j * U + u < ylen) row(std::true_type{}, u);
+        } else {
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (j * U + u < ylen) row(std::false_type{}, u);
+        }
+        h = h + 1 == C::NSR ? 0 : h + 1;
+        hs = hs + 1 == C::NSR ? 0 : hs + 1;
+        lz = nlz;
+        j = nj;
+    }
+    cp_async_wait<0>();
+}
+
+// One field: tiles from the ticket when there is one (evens out tiles with
+// many outliers), else a static grid stride.
+template <int ND, int B, bool QOUT>
+__global__ void __launch_bounds__(NdCfg<ND, B>::THREADS, NdCfg<ND, B>::MINB_R)
+k_recon_nd(const ReconArgs a) {
+    using C = NdCfg<ND, B>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    unsigned char* wsm = smem_raw + (size_t)wib * C::WARP_R;
     uint64_t tnext = (uint64_t)blockIdx.x * C::WARPS + wib;
     for (;;) {
-        // next tile: from the ticket when there is one (evens out tiles with
-        // many outliers), else a static grid stride
         uint64_t t = tnext;
         if (a.ticket) {
             unsigned int tk = 0;
@@ -71,410 +482,33 @@ k_recon_nd(const ReconArgs a) {
             t = __shfl_sync(VSZ_FULL, tk, 0);
         }
         tnext += (uint64_t)gridDim.x * C::WARPS;
-        if (t >= g.ntiles) break;
-        const uint64_t s = t % g.nseg;
-        const uint64_t rb = t / g.nseg;
-        const uint64_t by = rb % g.nby;
-        const uint64_t bz = rb / g.nby;
-        const uint64_t x0 = s * kSegCols + (uint64_t)lane * 4;
-        const uint64_t bx = (s * kSegCols) / B + (uint64_t)(lane / G);
-        const bool bexists = bx < g.nbx;
-        const int valid = x0 < nx ? (int)umin64(4, nx - x0) : 0;
-        const uint32_t vmask = (1u << valid) - 1u;
-        const bool full = vec && valid == 4;
-        const int ylen = (int)umin64(B, g.ny - by * B);
-        const int zlen = ND == 3 ? (int)umin64(B, g.nz - bz * B) : 1;
-        const int nbpp = (ylen + U - 1) / U;
-        const int nbatch = zlen * nbpp;
-        const uint64_t blk = (bz * g.nby + by) * g.nbx + bx;
-        const uint64_t tile_base = (ND == 3 ? bz * B * plane : 0) + by * B * nx + x0;
+        if (t >= a.g.ntiles) break;
+        nd_recon_tile<ND, B, QOUT>(a, t, wsm, lane);
+    }
+}
 
-        uint32_t lo = 0, hi = 0;
-        int32_t P = Pg;
-        if (first && bexists) {
-            lo = a.blk_off[blk];
-            hi = a.blk_off[blk + 1];
-            if (bp) P = a.pad[blk];
+// Many fields of one class (rank, block edge): one queue over the tiles of
+// all of them (tile_prefix as for the batch compression); any warps per CTA
+// up to 8.
+template <int ND, int B>
+__global__ void __launch_bounds__(NdBatchBounds<ND, B>::MAXT, NdBatchBounds<ND, B>::MINB_R)
+k_recon_nd_batch(const ReconArgs* __restrict__ fields, const uint64_t* __restrict__ tile_prefix, int nfields,
+                 unsigned long long* ticket) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    unsigned char* wsm = smem_raw + (size_t)(threadIdx.x >> 5) * NdCfg<ND, B>::WARP_R;
+    const uint64_t total = tile_prefix[nfields];
+    for (;;) {
+        unsigned long long tk = 0;
+        if (lane == 0) tk = atomicAdd(ticket, 1ull);
+        const uint64_t gt = __shfl_sync(VSZ_FULL, tk, 0);
+        if (gt >= total) break;
+        int lo = 0, hi = nfields - 1;  // last field whose first tile is <= gt
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (tile_prefix[mid] <= gt) lo = mid; else hi = mid - 1;
         }
-        lo = __shfl_sync(VSZ_FULL, lo, src);
-        hi = __shfl_sync(VSZ_FULL, hi, src);
-        P = __shfl_sync(VSZ_FULL, P, src);
-        const bool anyout = __any_sync(VSZ_FULL, hi > lo);
-        uint32_t rank = lo;
-
-        // The tile's blocks are consecutive in canonical order, so its outliers
-        // are one slice of the list: bring it into shared memory with the first
-        // batch when it is short enough.
-        uint32_t lo_t = 0;
-        bool cached = false;
-        const bool interior = vec && s * kSegCols + kSegCols <= nx && ylen == B && (ND == 2 || zlen == B);
-        const uint32_t ocap = ZREG_R && interior ? OCAP_BIG : (uint32_t)C::OCAP;
-        uint32_t* const oc_idx = ZREG_R && interior ? reinterpret_cast<uint32_t*>(zs) : oc_idx0;
-        int32_t* const oc_del = reinterpret_cast<int32_t*>(oc_idx + ocap);
-        if (anyout) {
-            const uint64_t fb = (bz * g.nby + by) * g.nbx + (s * kSegCols) / B;
-            const uint64_t nblk = umin64(kSegCols / B, g.nbx - (s * kSegCols) / B);
-            uint32_t hi_t = 0;
-            if (lane == 0) {
-                lo_t = a.blk_off[fb];
-                hi_t = a.blk_off[fb + nblk];
-            }
-            lo_t = __shfl_sync(VSZ_FULL, lo_t, 0);
-            hi_t = __shfl_sync(VSZ_FULL, hi_t, 0);
-            cached = hi_t >= lo_t && hi_t - lo_t <= ocap && (uint64_t)hi_t <= a.out_cap;
-            if (cached) {
-                const uint32_t sidx = smem_addr(oc_idx), sdel = smem_addr(oc_del);
-                for (uint32_t i = lane; i < hi_t - lo_t; i += 32) {
-                    cp_async4(sidx + 4 * i, a.out_idx + lo_t + i, 4u);
-                    cp_async4(sdel + 4 * i, a.out_delta + lo_t + i, 4u);
-                }
-            }
-        }
-
-        // copy the codes of batch (lz, j) into ring half h (vector path only)
-        auto issue_batch = [&](int lz, int j, int h) {
-            if (vec) {
-                const uint64_t off0 = tile_base + (uint64_t)lz * plane + (uint64_t)(j * U) * nx;
-                const uint32_t dst0 = ring_wr + (uint32_t)(h * U * 32 * 8);
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    if (j * U + u < ylen) {
-                        const uint64_t off = off0 + (uint64_t)u * nx;
-                        cp_async8(dst0 + u * 32 * 8, valid ? a.codes + off : a.codes, valid ? 8u : 0u);
-                    }
-                }
-            }
-            cp_async_commit();
-        };
-
-        if (interior) {
-            // Lean walk of an interior tile: compile-time trip counts, 32-bit
-            // offsets, and P carried in the running-sum state (the z sums of
-            // 3D blocks start from P, the y sums of 2D blocks), which adds P
-            // to every element of the block exactly as adding it to the
-            // origin's residual before the sums does.  3D blocks of up to 8
-            // keep their z sums in registers (the rows of a plane unrolled).
-            constexpr int BPP = B / U;
-            constexpr int NPL = ND == 3 ? B : 1;
-            constexpr bool ZREG = ND == 3 && B <= 8;
-            constexpr int NB = NPL * BPP;
-            const uint32_t nx32 = (uint32_t)nx, pl32 = (uint32_t)plane;
-            const uint16_t* cl = a.codes + tile_base;
-            auto issue_fast = [&](int kb, int st) {
-                const uint16_t* src0 = cl + (uint32_t)(kb / BPP) * pl32 + (uint32_t)((kb % BPP) * U) * nx32;
-                const uint32_t dst0 = ring_wr + (uint32_t)(st * U * 32 * 8);
-#pragma unroll
-                for (int u = 0; u < U; ++u) cp_async8(dst0 + u * 32 * 8, src0 + (uint32_t)u * nx32, 8u);
-                cp_async_commit();
-            };
-#pragma unroll
-            for (int st = 0; st < C::NSR - 1; ++st) {
-                if (st < NB) issue_fast(st, st);
-                else cp_async_commit();
-            }
-            int32_t zr[ZREG ? B : 1][4];
-#pragma unroll
-            for (int ly = 0; ly < (ZREG ? B : 1); ++ly)
-#pragma unroll
-                for (int k = 0; k < 4; ++k) zr[ly][k] = P;
-            if (ND == 3 && !ZREG) {
-#pragma unroll 4
-                for (int ly = 0; ly < B; ++ly) zs[ly * 32 + lane] = make_int4(P, P, P, P);
-            }
-            int32_t ys[4];
-            int h = 0, kb = 0;
-            for (int lz = 0; lz < NPL; ++lz) {
-#pragma unroll
-                for (int k = 0; k < 4; ++k) ys[k] = ND == 3 ? 0 : P;
-#pragma unroll(ZREG ? BPP : 1)
-                for (int jb = 0; jb < BPP; ++jb, ++kb) {
-                    if (kb + C::NSR - 1 < NB) issue_fast(kb + C::NSR - 1, (kb + C::NSR - 1) % C::NSR);
-                    else cp_async_commit();
-                    cp_async_wait<C::NSR - 1>();
-                    if (cached && kb == 0) __syncwarp();  // every lane's share of the outlier slice has landed
-                    const uint32_t boff = (uint32_t)lz * pl32 + (uint32_t)(jb * U) * nx32;
-                    const uint2* rr = ring_rd + h * U * 32;
-                    uint2 cw[U];
-                    uint32_t hz = 0;
-#pragma unroll
-                    for (int u = 0; u < U; ++u) {
-                        cw[u] = rr[u * 32];
-                        hz |= ((cw[u].x - 0x00010001u) & ~cw[u].x & 0x80008000u) |
-                              ((cw[u].y - 0x00010001u) & ~cw[u].y & 0x80008000u);
-                    }
-                    const bool patch = anyout && __any_sync(VSZ_FULL, hz != 0u);
-                    // one copy of the row code (the patch test is a uniform
-                    // branch), which keeps the unrolled plane loop small
-                    auto lrow = [&](int u) {
-                        const uint32_t c[4] = {cw[u].x & 0xffffu, cw[u].x >> 16, cw[u].y & 0xffffu, cw[u].y >> 16};
-                        int32_t d[4];
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) d[k] = (int32_t)c[k] - R;
-                        if (patch) {
-                            uint32_t zm = 0;
-#pragma unroll
-                            for (int k = 0; k < 4; ++k) zm |= (c[k] == 0u ? 1u : 0u) << k;
-                            if (__any_sync(VSZ_FULL, zm != 0u)) {
-                                const uint32_t cz = __popc(zm);
-                                uint32_t iz = cz;
-#pragma unroll
-                                for (int off = 1; off < G; off <<= 1) {
-                                    const uint32_t y = __shfl_up_sync(VSZ_FULL, iz, off);
-                                    if (glane >= off) iz += y;
-                                }
-                                const uint32_t gtot = __shfl_sync(VSZ_FULL, iz, src + G - 1);
-                                uint32_t r = rank + (iz - cz);
-                                const uint32_t roff = (uint32_t)tile_base + boff + (uint32_t)u * nx32;
-#pragma unroll
-                                for (int k = 0; k < 4; ++k) {
-                                    if (zm & (1u << k)) {
-                                        const bool in = r < hi && r < a.out_cap;
-                                        const uint32_t oi = !in ? ~0u : cached ? oc_idx[r - lo_t] : a.out_idx[r];
-                                        if (in && oi == roff + k) {
-                                            d[k] = cached ? oc_del[r - lo_t] : a.out_delta[r];
-                                        } else {
-                                            atomicMax(&a.hdr->recon_status, (unsigned)VSZ_ERR_CORRUPT);
-                                            d[k] = 0;
-                                        }
-                                        ++r;
-                                    }
-                                }
-                                rank += gtot;
-                            }
-                        }
-                        // Sx
-                        d[1] = wadd(d[1], d[0]);
-                        d[2] = wadd(d[2], d[1]);
-                        d[3] = wadd(d[3], d[2]);
-                        {
-                            const uint32_t tot = (uint32_t)d[3];
-                            uint32_t inc = tot;
-#pragma unroll
-                            for (int off = 1; off < G; off <<= 1) {
-                                const uint32_t y = __shfl_up_sync(VSZ_FULL, inc, off);
-                                if (glane >= off) inc += y;
-                            }
-                            const int32_t ex = (int32_t)(inc - tot);
-#pragma unroll
-                            for (int k = 0; k < 4; ++k) d[k] = wadd(d[k], ex);
-                        }
-                        // Sy
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            d[k] = wadd(d[k], ys[k]);
-                            ys[k] = d[k];
-                        }
-                        // Sz
-                        if (ZREG) {
-                            const int ly = ZREG ? jb * U + u : 0;
-#pragma unroll
-                            for (int k = 0; k < 4; ++k) {
-                                d[k] = wadd(d[k], zr[ly][k]);
-                                zr[ly][k] = d[k];
-                            }
-                        } else if (ND == 3) {
-                            int4& stz = zs[(jb * U + u) * 32 + lane];
-                            const int4 pv = stz;
-                            d[0] = wadd(d[0], pv.x); d[1] = wadd(d[1], pv.y);
-                            d[2] = wadd(d[2], pv.z); d[3] = wadd(d[3], pv.w);
-                            stz = make_int4(d[0], d[1], d[2], d[3]);
-                        }
-                        const uint32_t ro = boff + (uint32_t)u * nx32;
-                        if (QOUT) {
-                            st_out4(reinterpret_cast<int4*>(reinterpret_cast<int32_t*>(a.out) + tile_base + ro),
-                                    make_int4(d[0], d[1], d[2], d[3]));
-                        } else {
-                            int4 vv;
-                            if (fastcvt) {  // (float)q by the 1.5 * 2^23 bias, exact for |q| < 2^22
-                                vv.x = __float_as_int(__fmul_rn(__fsub_rn(__int_as_float(d[0] + 0x4B400000), 12582912.0f), ebx2));
-                                vv.y = __float_as_int(__fmul_rn(__fsub_rn(__int_as_float(d[1] + 0x4B400000), 12582912.0f), ebx2));
-                                vv.z = __float_as_int(__fmul_rn(__fsub_rn(__int_as_float(d[2] + 0x4B400000), 12582912.0f), ebx2));
-                                vv.w = __float_as_int(__fmul_rn(__fsub_rn(__int_as_float(d[3] + 0x4B400000), 12582912.0f), ebx2));
-                            } else {
-                                vv.x = __float_as_int(__fmul_rn(q2f(d[0]), ebx2));
-                                vv.y = __float_as_int(__fmul_rn(q2f(d[1]), ebx2));
-                                vv.z = __float_as_int(__fmul_rn(q2f(d[2]), ebx2));
-                                vv.w = __float_as_int(__fmul_rn(q2f(d[3]), ebx2));
-                            }
-                            st_out4(reinterpret_cast<int4*>(reinterpret_cast<float*>(a.out) + tile_base + ro), vv);
-                        }
-                    };
-#pragma unroll
-                    for (int u = 0; u < U; ++u) lrow(u);
-                    h = h + 1 == C::NSR ? 0 : h + 1;
-                }
-            }
-            cp_async_wait<0>();
-            continue;
-        }
-
-        int32_t ys[4] = {0, 0, 0, 0};
-        if (C::ZSMEM)
-            for (int ly = 0; ly < ylen; ++ly) zs[ly * 32 + lane] = make_int4(0, 0, 0, 0);
-
-        int ilz = 0, ij = 0;  // next batch to issue
-#pragma unroll
-        for (int st = 0; st < C::NSR - 1; ++st) {
-            if (st < nbatch) {
-                issue_batch(ilz, ij, st);
-                if (++ij == nbpp) { ij = 0; ++ilz; }
-            } else {
-                cp_async_commit();
-            }
-        }
-        int lz = 0, j = 0, h = 0, hs = C::NSR - 1;
-        for (int kb = 0; kb < nbatch; ++kb) {
-            int nj = j + 1, nlz = lz;
-            if (nj == nbpp) { nj = 0; ++nlz; }
-            if (kb + C::NSR - 1 < nbatch) {
-                issue_batch(ilz, ij, hs);
-                if (++ij == nbpp) { ij = 0; ++ilz; }
-            } else {
-                cp_async_commit();
-            }
-            cp_async_wait<C::NSR - 1>();
-            if (cached && kb == 0) __syncwarp();  // every lane's share of the outlier slice has landed
-            if (j == 0) {
-#pragma unroll
-                for (int k = 0; k < 4; ++k) ys[k] = 0;
-            }
-            const uint64_t boff = tile_base + (uint64_t)lz * plane + (uint64_t)(j * U) * nx;
-            const bool b0 = kb == 0;
-            // Codes of the batch; rows past the edge read as "no outlier".
-            uint2 cw[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                if (j * U + u < ylen) {
-                    if (vec) {
-                        cw[u] = ring_rd[(h * U + u) * 32];
-                    } else {
-                        uint32_t c4[4];
-                        load4c(a.codes + boff + (uint64_t)u * nx, valid, false, c4);
-                        const uint32_t rr = (uint32_t)R;
-                        cw[u] = make_uint2((valid > 0 ? c4[0] : rr) | ((valid > 1 ? c4[1] : rr) << 16),
-                                           (valid > 2 ? c4[2] : rr) | ((valid > 3 ? c4[3] : rr) << 16));
-                    }
-                } else {
-                    cw[u] = make_uint2(0x00010001u, 0x00010001u);
-                }
-            }
-            // Does any code 0 (an outlier) occur in this batch?
-            uint32_t hz = 0;
-#pragma unroll
-            for (int u = 0; u < U; ++u)
-                hz |= ((cw[u].x - 0x00010001u) & ~cw[u].x & 0x80008000u) |
-                      ((cw[u].y - 0x00010001u) & ~cw[u].y & 0x80008000u);
-            const bool patch = anyout && __any_sync(VSZ_FULL, valid > 0 && hz != 0u);
-
-            auto row = [&](auto patch_tag, int u) {
-                constexpr bool PATCH = decltype(patch_tag)::value;
-                const int ly = j * U + u;
-                const uint64_t roff = boff + (uint64_t)u * nx;
-                const uint32_t c[4] = {cw[u].x & 0xffffu, cw[u].x >> 16, cw[u].y & 0xffffu, cw[u].y >> 16};
-                int32_t d[4];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) d[k] = (int32_t)c[k] - R;
-                if (PATCH) {
-                    uint32_t zm = 0;
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) zm |= (c[k] == 0u ? 1u : 0u) << k;
-                    zm &= vmask;
-                    if (__any_sync(VSZ_FULL, zm != 0u)) {
-                        const uint32_t cz = __popc(zm);
-                        uint32_t iz = cz;
-#pragma unroll
-                        for (int off = 1; off < G; off <<= 1) {
-                            const uint32_t y = __shfl_up_sync(VSZ_FULL, iz, off);
-                            if (glane >= off) iz += y;
-                        }
-                        const uint32_t gtot = __shfl_sync(VSZ_FULL, iz, src + G - 1);
-                        uint32_t r = rank + (iz - cz);
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            if (zm & (1u << k)) {
-                                const bool in = r < hi && r < a.out_cap;
-                                const uint32_t oi = !in ? ~0u : cached ? oc_idx[r - lo_t] : a.out_idx[r];
-                                if (in && oi == (uint32_t)(roff + k)) {
-                                    d[k] = cached ? oc_del[r - lo_t] : a.out_delta[r];
-                                } else {
-                                    atomicMax(&a.hdr->recon_status, (unsigned)VSZ_ERR_CORRUPT);
-                                    d[k] = 0;
-                                }
-                                ++r;
-                            }
-                        }
-                        rank += gtot;
-                    }
-                }
-                if (b0 && u == 0 && first) d[0] = wadd(d[0], P);
-                // Sx
-                d[1] = wadd(d[1], d[0]);
-                d[2] = wadd(d[2], d[1]);
-                d[3] = wadd(d[3], d[2]);
-                {
-                    const uint32_t tot = (uint32_t)d[3];
-                    uint32_t inc = tot;
-#pragma unroll
-                    for (int off = 1; off < G; off <<= 1) {
-                        const uint32_t y = __shfl_up_sync(VSZ_FULL, inc, off);
-                        if (glane >= off) inc += y;
-                    }
-                    const int32_t ex = (int32_t)(inc - tot);
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) d[k] = wadd(d[k], ex);
-                }
-                // Sy
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    d[k] = wadd(d[k], ys[k]);
-                    ys[k] = d[k];
-                }
-                // Sz
-                if (C::ZSMEM) {
-                    int4& stz = zs[ly * 32 + lane];
-                    const int4 pv = stz;
-                    d[0] = wadd(d[0], pv.x); d[1] = wadd(d[1], pv.y);
-                    d[2] = wadd(d[2], pv.z); d[3] = wadd(d[3], pv.w);
-                    stz = make_int4(d[0], d[1], d[2], d[3]);
-                }
-                if (QOUT) {
-                    int32_t* o = reinterpret_cast<int32_t*>(a.out) + roff;
-                    if (full) {
-                        *reinterpret_cast<int4*>(o) = make_int4(d[0], d[1], d[2], d[3]);
-                    } else {
-#pragma unroll
-                        for (int k = 0; k < 4; ++k)
-                            if (k < valid) o[k] = d[k];
-                    }
-                } else {
-                    float vv[4];
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) vv[k] = __fmul_rn(q2f(d[k]), ebx2);
-                    float* o = reinterpret_cast<float*>(a.out) + roff;
-                    if (full) {
-                        *reinterpret_cast<float4*>(o) = make_float4(vv[0], vv[1], vv[2], vv[3]);
-                    } else {
-#pragma unroll
-                        for (int k = 0; k < 4; ++k)
-                            if (k < valid) o[k] = vv[k];
-                    }
-                }
-            };
-            if (patch) {
-#pragma unroll
-                for (int u = 0; u < U; ++u)
-                    if (j * U + u < ylen) row(std::true_type{}, u);
-            } else {
-#pragma unroll
-                for (int u = 0; u < U; ++u)
-                    if (j * U + u < ylen) row(std::false_type{}, u);
-            }
-            h = h + 1 == C::NSR ? 0 : h + 1;
-            hs = hs + 1 == C::NSR ? 0 : hs + 1;
-            lz = nlz;
-            j = nj;
-        }
-        cp_async_wait<0>();
+        nd_recon_tile<ND, B, false>(fields[lo], gt - tile_prefix[lo], wsm, lane);
     }
 }
 
@@ -499,23 +533,37 @@ cudaError_t launch_nd_compress(const CompressArgs& a, cudaStream_t s) {
 
 template <int ND, int B, bool BP, bool GP>
 cudaError_t launch_nd_compress_batch_k(const CompressArgs* fields, const uint64_t* tile_prefix, int nfields,
-                                       uint64_t total_tiles, unsigned long long* ticket, cudaStream_t s) {
+                                       uint64_t total_tiles, unsigned long long* ticket, LaunchShape sh,
+                                       cudaStream_t s, int* occ) {
     using C = NdCfg<ND, B>;
     const void* k = (const void*)k_lorenzo_nd_batch<ND, B, BP, GP>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM_C);
+    const int warps = sh.warps > 0 ? sh.warps : C::WARPS;
+    if (warps * 32 > NdBatchBounds<ND, B>::MAXT) {
+        if (occ) *occ = 0;
+        return occ ? cudaSuccess : cudaErrorInvalidValue;
+    }
+    const size_t smem = C::WARP_C * (size_t)warps;
+    cudaError_t e = raise_smem_attr(k, smem);
+    if (occ) {
+        *occ = e == cudaSuccess ? occupancy(k, warps * 32, smem) : 0;
+        return cudaSuccess;
+    }
     if (e != cudaSuccess) return e;
-    const int grid = grid_for(k, C::THREADS, C::SMEM_C, C::WARPS, total_tiles);
-    k_lorenzo_nd_batch<ND, B, BP, GP><<<grid, C::THREADS, C::SMEM_C, s>>>(fields, tile_prefix, nfields, ticket);
+    const int grid = grid_shape(k, warps * 32, smem, (uint64_t)warps, total_tiles, sh.ctas);
+    k_lorenzo_nd_batch<ND, B, BP, GP><<<grid, warps * 32, smem, s>>>(fields, tile_prefix, nfields, ticket);
     return cudaGetLastError();
 }
 
 // pk: 0 zero padding, 1 per-block padding, 2 global padding
 template <int ND, int B>
 cudaError_t launch_nd_compress_batch(int pk, const CompressArgs* fields, const uint64_t* tile_prefix, int nfields,
-                                     uint64_t total_tiles, unsigned long long* ticket, cudaStream_t s) {
-    if (pk == 1) return launch_nd_compress_batch_k<ND, B, true, false>(fields, tile_prefix, nfields, total_tiles, ticket, s);
-    if (pk == 2) return launch_nd_compress_batch_k<ND, B, false, true>(fields, tile_prefix, nfields, total_tiles, ticket, s);
-    return launch_nd_compress_batch_k<ND, B, false, false>(fields, tile_prefix, nfields, total_tiles, ticket, s);
+                                     uint64_t total_tiles, unsigned long long* ticket, LaunchShape sh,
+                                     cudaStream_t s, int* occ) {
+    if (pk == 1)
+        return launch_nd_compress_batch_k<ND, B, true, false>(fields, tile_prefix, nfields, total_tiles, ticket, sh, s, occ);
+    if (pk == 2)
+        return launch_nd_compress_batch_k<ND, B, false, true>(fields, tile_prefix, nfields, total_tiles, ticket, sh, s, occ);
+    return launch_nd_compress_batch_k<ND, B, false, false>(fields, tile_prefix, nfields, total_tiles, ticket, sh, s, occ);
 }
 
 template <int ND, int B>
@@ -527,6 +575,29 @@ cudaError_t launch_nd_recon(const ReconArgs& a, bool q_out, cudaStream_t s) {
     const int grid = grid_for(k, C::THREADS, C::SMEM_R, C::WARPS, a.g.ntiles);
     if (q_out) k_recon_nd<ND, B, true><<<grid, C::THREADS, C::SMEM_R, s>>>(a);
     else k_recon_nd<ND, B, false><<<grid, C::THREADS, C::SMEM_R, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int ND, int B>
+cudaError_t launch_nd_recon_batch(const ReconArgs* fields, const uint64_t* tile_prefix, int nfields,
+                                  uint64_t total_tiles, unsigned long long* ticket, LaunchShape sh, cudaStream_t s,
+                                  int* occ) {
+    using C = NdCfg<ND, B>;
+    const void* k = (const void*)k_recon_nd_batch<ND, B>;
+    const int warps = sh.warps > 0 ? sh.warps : C::WARPS;
+    if (warps * 32 > NdBatchBounds<ND, B>::MAXT) {
+        if (occ) *occ = 0;
+        return occ ? cudaSuccess : cudaErrorInvalidValue;
+    }
+    const size_t smem = C::WARP_R * (size_t)warps;
+    cudaError_t e = raise_smem_attr(k, smem);
+    if (occ) {
+        *occ = e == cudaSuccess ? occupancy(k, warps * 32, smem) : 0;
+        return cudaSuccess;
+    }
+    if (e != cudaSuccess) return e;
+    const int grid = grid_shape(k, warps * 32, smem, (uint64_t)warps, total_tiles, sh.ctas);
+    k_recon_nd_batch<ND, B><<<grid, warps * 32, smem, s>>>(fields, tile_prefix, nfields, ticket);
     return cudaGetLastError();
 }
 

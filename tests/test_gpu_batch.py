@@ -1,6 +1,7 @@
 """GPU tests of the batch path (vsz_batch_*): every field's outputs must be
-identical to compressing that field alone with vsz_compress, which the
-parity tests tie to the oracle."""
+identical to compressing (reconstructing) that field alone with vsz_compress
+(vsz_reconstruct), which the parity tests tie to the oracle, and the batch
+reconstruction is also checked against the oracle's decompression."""
 import numpy as np
 import pytest
 
@@ -74,6 +75,48 @@ def test_batch_equals_per_field(use_graph):
     b.close()
 
 
+def _outs(fields):
+    return [torch.full((max(1, f.n),), float("nan"), dtype=torch.float32, device="cuda") for f in fields]
+
+
+def _assert_recon(fields, outs, want, what):
+    for i, f in enumerate(fields):
+        if f.n:
+            got = outs[i][: f.n].cpu().numpy().view(np.uint32)
+            assert np.array_equal(got, want[i]), (what, MIX[i])
+            assert f.header()["recon_status"] == 0, (what, MIX[i])
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_batch_reconstruct_equals_per_field_and_oracle(use_graph):
+    fields, xs = _make()
+    outs = _outs(fields)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        b = vsz.Batch(fields, xs, use_graph=use_graph)
+        b.set_outputs(outs)
+        b.submit()
+        b.reconstruct()
+        b.reconstruct()  # a replay gives the same values
+    stream.synchronize()
+    kinds = [c["kind"] for c in b.classes()]
+    assert 0 in kinds and 1 in kinds
+    want = []
+    for i, f in enumerate(fields):
+        if not f.n:
+            want.append(None)
+            continue
+        single = f.reconstruct().cpu().numpy().view(np.uint32)
+        dims, blk, eb, mode, R, pad = MIX[i]
+        po = oracle.Params(dims, blk, eb, oracle.EB_REL if mode == "rel" else oracle.EB_ABS, R, oracle.PAD_NAMES[pad])
+        x = xs[i].cpu().numpy()
+        xo = oracle.decompress(po, oracle.compress(po, x)).view(np.uint32)
+        assert np.array_equal(single, xo), MIX[i]
+        want.append(xo)
+    _assert_recon(fields, outs, want, "batch")
+    b.close()
+
+
 def test_batch_replay_with_new_inputs():
     """The plan (and its graph) keeps the input pointers: new values written
     into the same buffers are compressed by the next submit."""
@@ -102,4 +145,79 @@ def test_batch_replay_with_new_inputs():
         assert np.array_equal(got["out_idx"], c.out_idx), MIX[i]
         assert np.array_equal(got["out_delta"], c.out_delta), MIX[i]
         assert np.array_equal(got["fix_idx"], c.fix_idx), MIX[i]
+    b.close()
+
+
+def _scramble(fields):
+    for f in fields:
+        for t in (f.codes, f.blk_off, f.out_idx, f.out_delta, f.fix_idx, f.fix_bits, f.pad):
+            if t is not None:
+                t.fill_(-7)
+
+
+def _assert_same(fields, want, what):
+    for i, (f, w) in enumerate(zip(fields, want)):
+        got = _host(f)
+        for k in KEYS:
+            if w[k] is not None:
+                assert np.array_equal(got[k], w[k]), (what, MIX[i], k)
+        for k in ("pad_global", "n_out", "n_fix", "status"):
+            assert got["header"][k] == w["header"][k], (what, MIX[i], k)
+
+
+def test_launch_shapes_and_autotune_change_no_result():
+    """Every launch shape of the class kernels (warps per CTA, CTAs per SM),
+    the concurrent mode and the autotuner's choice give the same outputs."""
+    fields, xs = _make()
+    outs = _outs(fields)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        b = vsz.Batch(fields, xs, use_graph=True)
+        b.set_outputs(outs)
+        b.submit()
+        b.reconstruct()
+    stream.synchronize()
+    want = [_host(f) for f in fields]
+    rwant = [o[: f.n].cpu().numpy().view(np.uint32).copy() if f.n else None for f, o in zip(fields, outs)]
+    cls = b.classes()
+    comp = [c for c in cls if c["kind"] == 0]
+    assert len(comp) >= 6 and sum(c["nfields"] for c in comp) == len(MIX)
+    assert sum(c["nfields"] for c in cls if c["kind"] == 1) == sum(1 for f in fields if f.n)
+    assert {(c["ndim"], c["pad_kind"]) for c in comp} >= {(1, 0), (2, 1), (3, 2)}
+
+    def run_and_check(what):
+        _scramble(fields)
+        for o in outs:
+            o.fill_(float("nan"))
+        with torch.cuda.stream(stream):
+            b.submit()
+            b.reconstruct()
+        stream.synchronize()
+        _assert_same(fields, want, what)
+        _assert_recon(fields, outs, rwant, what)
+
+    for warps, ctas in ((2, 1), (8, 0), (4, 2), (8, 1), (2, 0)):
+        for c in range(len(cls)):
+            try:
+                b.set_shape(c, warps, ctas)
+            except vsz.VszError as e:  # shared memory of 8 warps of 3D blocks of 32
+                assert e.status == 2 and warps == 8
+        run_and_check((warps, ctas))
+    for c in range(len(cls)):
+        b.set_shape(c, 0, 0)
+    b.set_concurrent(True)
+    for _ in range(2):  # capture, then replay
+        run_and_check("concurrent")
+    tuned = b.autotune(stream, reps=2)
+    assert len(tuned) == len(cls)
+    for c in tuned:
+        if c["tiles"]:
+            assert c["warps"] in (0, 2, 4, 8) and c["ctas_per_sm"] >= 0
+            assert 0 < c["ms"] <= c["ms_default"]
+    for _ in range(2):
+        run_and_check("autotuned")
+    with pytest.raises(vsz.VszError):
+        b.set_shape(0, 3, 0)
+    with pytest.raises(vsz.VszError):
+        b.set_shape(len(cls), 4, 0)
     b.close()
