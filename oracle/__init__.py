@@ -30,10 +30,12 @@ _lib = None
 EB_ABS, EB_REL = 0, 1
 PAD_ZERO, PAD_GLOBAL_MIN, PAD_GLOBAL_MAX, PAD_GLOBAL_AVG = 0, 1, 2, 3
 PAD_BLOCK_MIN, PAD_BLOCK_MAX, PAD_BLOCK_AVG = 4, 5, 6
+PAD_EDGE_MIN, PAD_EDGE_MAX, PAD_EDGE_AVG = 7, 8, 9
 PAD_NAMES = {
     "zero": PAD_ZERO, "global_min": PAD_GLOBAL_MIN, "global_max": PAD_GLOBAL_MAX,
     "global_avg": PAD_GLOBAL_AVG, "block_min": PAD_BLOCK_MIN,
     "block_max": PAD_BLOCK_MAX, "block_avg": PAD_BLOCK_AVG,
+    "edge_min": PAD_EDGE_MIN, "edge_max": PAD_EDGE_MAX, "edge_avg": PAD_EDGE_AVG,
 }
 
 
@@ -119,6 +121,19 @@ class Params:
     def is_block_pad(self) -> bool:
         return self.pad in (PAD_BLOCK_MIN, PAD_BLOCK_MAX, PAD_BLOCK_AVG)
 
+    @property
+    def is_edge_pad(self) -> bool:
+        return self.pad in (PAD_EDGE_MIN, PAD_EDGE_MAX, PAD_EDGE_AVG)
+
+    @property
+    def pad_len(self) -> int:
+        """Entries of the padding table: nb (block), nb * ndim (edge), else 1."""
+        if self.is_block_pad:
+            return max(self.nblocks, 1)
+        if self.is_edge_pad:
+            return max(self.nblocks * self.ndim, 1)
+        return 1
+
 
 @dataclass
 class EbInfo:
@@ -145,7 +160,7 @@ class Compressed:
     eb: EbInfo
     codes: np.ndarray      # uint16[n], field layout
     q: np.ndarray          # int32[n], prequantized values
-    pad: np.ndarray        # int32[nb] (block modes) or int32[1]
+    pad: np.ndarray        # int32[nb] (block modes), int32[nb*ndim] (edge modes) or int32[1]
     blk_off: np.ndarray    # uint32[nb+1]
     out_idx: np.ndarray    # uint32[n_out], canonical order
     out_delta: np.ndarray  # int32[n_out]
@@ -175,7 +190,7 @@ def prequant(x, inv2eb) -> np.ndarray:
 
 def pad_values(p: Params, q) -> np.ndarray:
     q = np.ascontiguousarray(q, dtype=np.int32).reshape(-1)
-    pad = np.zeros(max(p.nblocks, 1) if p.is_block_pad else 1, np.int32)
+    pad = np.zeros(p.pad_len, np.int32)
     rc = _load().vszo_pad_values(ctypes.byref(p._c()), q.ctypes.data, pad.ctypes.data)
     if rc:
         raise ValueError(f"oracle pad_values failed rc={rc}")
@@ -201,7 +216,7 @@ def compress(p: Params, x) -> Compressed:
     e = _Eb()
     codes = np.zeros(n, np.uint16)
     q = np.zeros(n, np.int32)
-    pad = np.zeros(max(nb, 1) if p.is_block_pad else 1, np.int32)
+    pad = np.zeros(p.pad_len, np.int32)
     blk_off = np.zeros(nb + 1, np.uint32)
     cap = max(n, 1)
     out_idx = np.zeros(cap, np.uint32)

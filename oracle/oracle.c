@@ -7,7 +7,8 @@
  *               the prequantized values with a Lorenzo predictor inside each
  *               block, post-quantize the residual into an integer code, keep
  *               out-of-range residuals aside; decompression reverses it;
- *   Sec. IV     padding values (zero, min, max, average; global or block).
+ *   Sec. IV     padding values (zero, min, max, average; global, block or
+ *               edge granularity).
  * Where the paper is silent (rounding, tie-breaking, the sentinel, the
  * outlier payload and order, the average's rounding, the fp32 guard), the
  * readings below are the ones the design notes list; each is marked
@@ -189,6 +190,11 @@ static int is_block_mode(int pad)
     return pad == VSZO_PAD_BLOCK_MIN || pad == VSZO_PAD_BLOCK_MAX || pad == VSZO_PAD_BLOCK_AVG;
 }
 
+static int is_edge_mode(int pad)
+{
+    return pad == VSZO_PAD_EDGE_MIN || pad == VSZO_PAD_EDGE_MAX || pad == VSZO_PAD_EDGE_AVG;
+}
+
 /* Min, max or rounded mean of the listed q values. */
 static int32_t statistic(int kind_min_max_avg, const int32_t* vals, uint64_t m)
 {
@@ -244,6 +250,34 @@ int vszo_pad_values(const vszo_params* p, const int32_t* q, int32_t* pad)
         free(tmp);
         return VSZO_OK;
     }
+    case VSZO_PAD_EDGE_MIN: /* Sec. IV-B-3: one scalar per set of border values */
+    case VSZO_PAD_EDGE_MAX:
+    case VSZO_PAD_EDGE_AVG: {
+        /* reading: the border values of a block along axis k are its
+         * in-field elements at local coordinate 0 along k (those whose
+         * predecessor along k lies outside the block); the scalar is their
+         * min, max or rounded mean.  nb * ndim scalars in all. */
+        int kind = p->pad - VSZO_PAD_EDGE_MIN;
+        uint64_t nb = vszo_num_blocks(p);
+        int32_t* tmp = (int32_t*)malloc(sizeof(int32_t) * (size_t)(g.b) *
+                                        (g.d > 1 ? g.b : 1) * (g.d > 2 ? g.b : 1));
+        if (!tmp) return VSZO_ERR_ARG;
+        for (uint64_t blk = 0; blk < nb; ++blk) {
+            uint64_t org[3], ext[3], l[3];
+            block_box(&g, blk, org, ext);
+            uint64_t m = box_size(&g, ext);
+            for (int k = 0; k < g.d; ++k) {
+                uint64_t c = 0;
+                for (uint64_t i = 0; i < m; ++i) {
+                    local_coord(&g, i, ext, l);
+                    if (l[k] == 0) tmp[c++] = q[lin_index(&g, org, l)];
+                }
+                pad[blk * (uint64_t)g.d + (uint64_t)k] = statistic(kind, tmp, c);
+            }
+        }
+        free(tmp);
+        return VSZO_OK;
+    }
     default:
         return VSZO_ERR_ARG;
     }
@@ -286,6 +320,55 @@ static int32_t block_pad(const vszo_params* p, const int32_t* pad, uint64_t blk)
     return is_block_mode(p->pad) ? pad[blk] : pad[0];
 }
 
+/* Edge granularity (Sec. IV-B-3): the value standing in for a neighbour
+ * outside the block.  A neighbour outside along exactly one axis k takes
+ * that axis's scalar Pk.  reading (the paper leaves the corners open): a
+ * neighbour outside along a set S of several axes takes the rounded mean of
+ * the scalars of the axes in S. */
+static int32_t edge_value(int d, const int32_t* Pk, unsigned outside)
+{
+    __int128 sum = 0;
+    uint64_t m = 0;
+    for (int k = 0; k < d; ++k)
+        if (outside & (1u << k)) {
+            sum += Pk[k];
+            ++m;
+        }
+    return rounded_mean(sum, m);
+}
+
+/* Lorenzo residual under edge padding: the same signed sum over the 2^d
+ * neighbours at offsets s in {0,1}^d, on raw values, with every neighbour
+ * outside the block replaced by its edge value:
+ *     delta = sum_{s} (-1)^|s| v[l - s]. */
+static int32_t lorenzo_residual_edge(const geom* g, const int32_t* q, const int32_t* Pk,
+                                     const uint64_t org[3], const uint64_t l[3])
+{
+    uint32_t acc = 0;
+    for (unsigned s = 0; s < (1u << g->d); ++s) {
+        uint64_t nbr[3];
+        unsigned outside = 0;
+        int parity = 0;
+        for (int k = 0; k < g->d; ++k) {
+            unsigned sk = (s >> (g->d - 1 - k)) & 1u;
+            parity ^= (int)sk;
+            if (sk && l[k] == 0) outside |= 1u << k;
+            nbr[k] = l[k] - (sk ? 1 : 0);
+        }
+        uint32_t v = outside ? (uint32_t)edge_value(g->d, Pk, outside) : (uint32_t)q[lin_index(g, org, nbr)];
+        acc = parity ? acc - v : acc + v;
+    }
+    return (int32_t)acc;
+}
+
+/* Residual of one element under any padding mode. */
+static int32_t residual(const vszo_params* p, const geom* g, const int32_t* q, const int32_t* pad,
+                        uint64_t blk, const uint64_t org[3], const uint64_t l[3])
+{
+    if (is_edge_mode(p->pad)) return lorenzo_residual_edge(g, q, pad + blk * (uint64_t)g->d, org, l);
+    return lorenzo_residual(g, q, block_pad(p, pad, blk), org, l);
+}
+
 int vszo_lorenzo_delta(const vszo_params* p, const int32_t* q, const int32_t* pad,
                        int32_t* delta)
 {
@@ -295,11 +378,10 @@ int vszo_lorenzo_delta(const vszo_params* p, const int32_t* q, const int32_t* pa
     for (uint64_t blk = 0; blk < nb; ++blk) {
         uint64_t org[3], ext[3], l[3];
         block_box(&g, blk, org, ext);
-        int32_t P = block_pad(p, pad, blk);
         uint64_t m = box_size(&g, ext);
         for (uint64_t i = 0; i < m; ++i) {
             local_coord(&g, i, ext, l);
-            delta[lin_index(&g, org, l)] = lorenzo_residual(&g, q, P, org, l);
+            delta[lin_index(&g, org, l)] = residual(p, &g, q, pad, blk, org, l);
         }
     }
     return VSZO_OK;
@@ -353,7 +435,6 @@ int vszo_compress(const vszo_params* p, const float* x, vszo_eb* eb,
     for (uint64_t blk = 0; blk < nb; ++blk) {
         uint64_t org[3], ext[3], l[3];
         block_box(&g, blk, org, ext);
-        int32_t P = block_pad(p, pad, blk);
         blk_off[blk] = (uint32_t)no;
         uint64_t m = box_size(&g, ext);
         for (uint64_t i = 0; i < m; ++i) {
@@ -363,7 +444,7 @@ int vszo_compress(const vszo_params* p, const float* x, vszo_eb* eb,
              * reading: a residual with |delta| < R becomes the uint16 code
              * delta + R in [1, 2R-1]; otherwise the code is 0 and the pair
              * (index, delta) is kept aside as an outlier. */
-            int32_t delta = lorenzo_residual(&g, q, P, org, l);
+            int32_t delta = residual(p, &g, q, pad, blk, org, l);
             if (delta > -R && delta < R) {
                 codes[idx] = (uint16_t)(delta + R);
             } else {
@@ -439,6 +520,47 @@ int vszo_decompress(const vszo_params* p, const vszo_eb* eb,
             }
         }
         if (rc) break;
+
+        if (is_edge_mode(p->pad)) {
+            /* Edge granularity: invert delta = sum_s (-1)^|s| v[l - s]
+             * element by element in row-major order, where every in-block
+             * neighbour l - s (s != 0) is already reconstructed:
+             *     q[l] = delta[l] - sum_{s != 0} (-1)^|s| v[l - s]. */
+            const int32_t* Pk = pad + blk * (uint64_t)g.d;
+            for (uint64_t i = 0; i < m; ++i) {
+                local_coord(&g, i, ext, l);
+                uint32_t acc = e[i];
+                for (unsigned s = 1; s < (1u << g.d); ++s) {
+                    uint64_t nbr[3];
+                    unsigned outside = 0;
+                    int parity = 0;
+                    for (int k = 0; k < g.d; ++k) {
+                        unsigned sk = (s >> (g.d - 1 - k)) & 1u;
+                        parity ^= (int)sk;
+                        if (sk && l[k] == 0) outside |= 1u << k;
+                        nbr[k] = l[k] - (sk ? 1 : 0);
+                    }
+                    uint32_t v;
+                    if (outside) {
+                        v = (uint32_t)edge_value(g.d, Pk, outside);
+                    } else {
+                        uint64_t j = 0; /* local row-major index of the neighbour */
+                        for (int k = 0; k < g.d; ++k) j = j * ext[k] + nbr[k];
+                        v = e[j];
+                    }
+                    acc = parity ? acc + v : acc - v;
+                }
+                e[i] = acc;
+            }
+            for (uint64_t i = 0; i < m; ++i) {
+                local_coord(&g, i, ext, l);
+                uint64_t idx = lin_index(&g, org, l);
+                int32_t qv = (int32_t)e[i];
+                if (q_out) q_out[idx] = qv;
+                xhat[idx] = (float)qv * eb->ebx2;
+            }
+            continue;
+        }
 
         /* Inclusive cumulative sums along each axis, fastest axis first.
          * Visiting the box in row-major order, the element one step back

@@ -35,7 +35,10 @@ enum {
     VSZO_PAD_GLOBAL_AVG = 3,
     VSZO_PAD_BLOCK_MIN = 4,
     VSZO_PAD_BLOCK_MAX = 5,
-    VSZO_PAD_BLOCK_AVG = 6
+    VSZO_PAD_BLOCK_AVG = 6,
+    VSZO_PAD_EDGE_MIN = 7,
+    VSZO_PAD_EDGE_MAX = 8,
+    VSZO_PAD_EDGE_AVG = 9
 };
 enum { VSZO_OK = 0, VSZO_ERR_ARG = 1, VSZO_ERR_DATA = 2 };
 
@@ -69,7 +72,10 @@ int vszo_resolve_eb(const vszo_params* p, const float* x, vszo_eb* out);
 void vszo_prequant(const float* x, uint64_t n, float inv2eb, int32_t* q);
 
 /* Padding values, Sec. IV-A/B.  pad receives 1 value for ZERO and GLOBAL_*
- * modes, one value per block (canonical block order) for BLOCK_* modes. */
+ * modes, one value per block (canonical block order) for BLOCK_* modes, and
+ * ndim values per block for EDGE_* modes (Sec. IV-B-3): pad[blk*ndim + k]
+ * is the statistic of the block's face at local coordinate 0 along axis k
+ * (k = 0 the slowest axis). */
 int vszo_pad_values(const vszo_params* p, const int32_t* q, int32_t* pad);
 
 /* Lorenzo residuals δ° for every element (field layout), Sec. III-A. */
@@ -77,7 +83,7 @@ int vszo_lorenzo_delta(const vszo_params* p, const int32_t* q,
                        const int32_t* pad, int32_t* delta);
 
 /* Whole compression-side dual-quant.  Array sizes: codes[n], q_out[n] (may be
- * NULL), pad[nb] (or [1]), blk_off[nb+1], out_idx/out_delta[n],
+ * NULL), pad[nb] (EDGE_*: [nb*ndim]; else [1]), blk_off[nb+1], out_idx/out_delta[n],
  * fix_idx/fix_bits[n].  Outliers and fixups are written in canonical order:
  * blocks in row-major block order, elements row-major inside a block. */
 int vszo_compress(const vszo_params* p, const float* x, vszo_eb* eb,

@@ -403,3 +403,120 @@ def test_padding_trend_unpinned(orc):
     nz = len(orc.compress(orc.Params((256, 256), 16, 1e-4, orc.EB_REL, 512, orc.PAD_ZERO), x).out_idx)
     na = len(orc.compress(orc.Params((256, 256), 16, 1e-4, orc.EB_REL, 512, orc.PAD_BLOCK_AVG), x).out_idx)
     assert na <= nz
+
+
+# ------------------------------------------------------- edge granularity (Sec. IV-B-3)
+def half_up_mean(vals):
+    return math.floor(Fraction(int(sum(int(v) for v in vals)), len(vals)) + Fraction(1, 2))
+
+
+def face_stats(q, dims, b, kind):
+    """Per block and axis k (k = 0 slowest): the statistic of the block's
+    in-field elements at local coordinate 0 along k."""
+    qf = np.asarray(q, np.int64).reshape(dims)
+    out = []
+    for sl in block_slices(dims, b):
+        box = qf[sl]
+        for k in range(len(dims)):
+            face = np.take(box, 0, axis=k).reshape(-1)
+            out.append(int(face.min()) if kind == "min" else int(face.max()) if kind == "max"
+                       else half_up_mean(face))
+    return out
+
+
+def edge_padded_delta(q, dims, b, pads):
+    """Second formulation of the edge-padded residual: surround each block on
+    its low sides with a layer whose cells outside along the axis set S hold
+    the half-up mean of those axes' scalars, then take first differences
+    along every axis in turn."""
+    qf = np.asarray(q, np.int64).reshape(dims)
+    d = len(dims)
+    out = np.zeros(dims, np.int64)
+    for bi, sl in enumerate(block_slices(dims, b)):
+        Pk = [int(v) for v in pads[bi * d:(bi + 1) * d]]
+        ext = tuple(s.stop - s.start for s in sl)
+        box = np.zeros(tuple(e + 1 for e in ext), np.int64)
+        for cell in itertools.product(*[range(e + 1) for e in ext]):
+            S = [k for k in range(d) if cell[k] == 0]
+            box[cell] = half_up_mean([Pk[k] for k in S]) if S else qf[sl][tuple(c - 1 for c in cell)]
+        for ax in range(d):
+            box = np.diff(box, axis=ax)
+        out[sl] = box
+    return to_i32(out.reshape(-1))
+
+
+def origin_mask(dims, b):
+    m = np.zeros(dims, bool)
+    for sl in block_slices(dims, b):
+        m[tuple(s.start for s in sl)] = True
+    return m.reshape(-1)
+
+
+def _edge_cases():
+    rng = np.random.default_rng(77)
+    out = []
+    for ndim in (1, 2, 3):
+        for _ in range(8):
+            dims = tuple(int(v) for v in rng.integers(1, 10 if ndim < 3 else 8, ndim))
+            out.append((dims, int(rng.integers(1, 7)), int(rng.integers(0, 1 << 30))))
+    return out
+
+
+@pytest.mark.parametrize("dims,b,seed", _edge_cases())
+def test_edge_pad_values_and_residuals(orc, dims, b, seed):
+    """Face statistics recomputed directly; residuals by the padded-layer
+    formulation; and the consequence of first-order Lorenzo that a padding
+    layer constant on each face changes only the block origin's residual:
+    every other residual equals the zero-padding one, and the origin's is
+    q - (sum over non-empty axis sets S of (-1)^(|S|+1) V(S))."""
+    rng = np.random.default_rng(seed)
+    n = int(np.prod(dims))
+    q = rng.integers(-5000, 5000, n).astype(np.int32)
+    pz = _abs_half(dims, b, orc.PAD_ZERO)
+    dz = orc.lorenzo_delta(pz, q, np.zeros(1, np.int32))
+    org = origin_mask(dims, b)
+    for kind, mode in (("min", orc.PAD_EDGE_MIN), ("max", orc.PAD_EDGE_MAX), ("avg", orc.PAD_EDGE_AVG)):
+        p = _abs_half(dims, b, mode)
+        pads = orc.pad_values(p, q)
+        assert pads.tolist() == face_stats(q, dims, b, kind)
+        de = orc.lorenzo_delta(p, q, pads)
+        assert de.tolist() == edge_padded_delta(q, dims, b, pads).tolist()
+        assert (de[~org] == dz[~org]).all()
+        d = len(dims)
+        for bi, sl in enumerate(block_slices(dims, b)):
+            Pk = [int(v) for v in pads[bi * d:(bi + 1) * d]]
+            pred = sum((-1) ** (r + 1) * half_up_mean([Pk[k] for k in S])
+                       for r in range(1, d + 1) for S in itertools.combinations(range(d), r))
+            i0 = int(np.ravel_multi_index(tuple(s.start for s in sl), dims))
+            assert int(de[i0]) == int(to_i32([int(q[i0]) - pred])[0])
+
+
+@pytest.mark.parametrize("dims,b,seed", _edge_cases()[::2])
+@pytest.mark.parametrize("R", [1, 3, 512])
+def test_edge_round_trip_tiny(orc, dims, b, seed, R):
+    """Codes, outliers and blk_off from the residuals; the inverse (element by
+    element in row-major order) gives q back exactly."""
+    rng = np.random.default_rng(seed + R)
+    n = int(np.prod(dims))
+    x = (np.cumsum(rng.integers(-R - 1, R + 2, n)) + rng.integers(-3 * R, 3 * R)).astype(np.float32)
+    for mode in (orc.PAD_EDGE_MIN, orc.PAD_EDGE_MAX, orc.PAD_EDGE_AVG):
+        p = _abs_half(dims, b, mode, R)
+        c = orc.compress(p, x)
+        assert len(c.pad) == max(1, p.nblocks * len(dims))
+        d = edge_padded_delta(c.q, dims, b, c.pad)
+        is_out = np.abs(d.astype(np.int64)) >= R
+        assert (c.codes.astype(np.int64) == np.where(is_out, 0, d.astype(np.int64) + R)).all()
+        canon = canonical_order(dims, b)
+        assert c.out_idx.tolist() == canon[is_out[canon]].tolist()
+        xh, qh = orc.decompress(p, c, return_q=True)
+        assert (qh == c.q).all() and (xh == x).all()
+
+
+@pytest.mark.parametrize("dims,b", [((37,), 8), ((10, 13), 4), ((5, 6, 7), 3)])
+def test_edge_constant_field(orc, dims, b):
+    """On a constant field every face scalar and corner value equals q, the
+    inclusion-exclusion sum at the origin is q, and no residual is left."""
+    x = np.full(dims, 40.0, np.float32)
+    for mode in (orc.PAD_EDGE_MIN, orc.PAD_EDGE_MAX, orc.PAD_EDGE_AVG):
+        c = orc.compress(_abs_half(dims, b, mode, 16), x)
+        assert len(c.out_idx) == 0 and (c.codes == 16).all() and (c.pad == 40).all()
