@@ -57,7 +57,15 @@ typedef enum { VSZ_EB_ABS = 0, VSZ_EB_REL = 1 } vsz_eb_mode;
 
 /* Sec. IV: padding value standing in for every Lorenzo neighbour outside a
  * block: zero (cuSZ), or the min / max / average of the prequantized data,
- * over the whole field (global, Sec. IV-B-1) or per block (Sec. IV-B-2). */
+ * over the whole field (global, Sec. IV-B-1), per block (Sec. IV-B-2), or
+ * per block and axis (edge, Sec. IV-B-3).
+ * Edge granularity keeps ndim scalars per block: the scalar of axis k is the
+ * statistic of the block's face at local coordinate 0 along k (k = 0 the
+ * slowest axis), and a neighbour outside along several axes takes the
+ * rounded mean of their scalars (the paper leaves those corners open).  With
+ * the first-order Lorenzo predictor such a layer changes only the residual
+ * of the block origin: it is q minus the inclusion-exclusion sum, over the
+ * non-empty sets S of axes, of (-1)^(|S|+1) times the value of S. */
 typedef enum {
     VSZ_PAD_ZERO = 0,
     VSZ_PAD_GLOBAL_MIN = 1,
@@ -65,7 +73,10 @@ typedef enum {
     VSZ_PAD_GLOBAL_AVG = 3,
     VSZ_PAD_BLOCK_MIN = 4,
     VSZ_PAD_BLOCK_MAX = 5,
-    VSZ_PAD_BLOCK_AVG = 6
+    VSZ_PAD_BLOCK_AVG = 6,
+    VSZ_PAD_EDGE_MIN = 7,
+    VSZ_PAD_EDGE_MAX = 8,
+    VSZ_PAD_EDGE_AVG = 9
 } vsz_pad_mode;
 
 /* The paper's statement of the problem: field dims, block size, error bound
@@ -101,7 +112,8 @@ typedef struct {
 /* A compressed field: caller-owned device buffers. */
 typedef struct {
     uint16_t*   codes;     /* [n] quantization codes, field layout */
-    int32_t*    pad;       /* [nb] per-block padding values (BLOCK_* modes only; else may be NULL) */
+    int32_t*    pad;       /* [nb] per-block padding values (BLOCK_* modes), [nb * ndim] (EDGE_* modes);
+                              else may be NULL */
     uint32_t*   blk_off;   /* [nb+1] outlier offsets per block, canonical order */
     uint32_t*   out_idx;   /* [out_cap] global linear index of each outlier */
     int32_t*    out_delta; /* [out_cap] its residual delta */
@@ -226,7 +238,9 @@ VSZ_API size_t vsz_batch_workspace_size(const vsz_field_job* jobs, int njobs);
  * field, one global-statistics pass over every global-padding field, one
  * persistent compression kernel per class whose warps draw tiles of all the
  * class's fields from one queue, and two compaction kernels.  Results are
- * identical to vsz_compress on each field.  The plan keeps the jobs' pointers;
+ * identical to vsz_compress on each field.  Edge padding modes are not
+ * batched (VSZ_ERR_UNSUPPORTED; compress such fields with vsz_compress).  The
+ * plan keeps the jobs' pointers;
  * their buffers must outlive it.  The plan allocates its descriptor tables on
  * the device (freed by vsz_batch_destroy); d_ws (caller-owned, 256-byte
  * aligned) holds every field's compression workspace.  use_graph != 0

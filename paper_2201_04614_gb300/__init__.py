@@ -22,7 +22,7 @@ __all__ = [
 EB_ABS, EB_REL = 0, 1
 PAD_MODES = {
     "zero": 0, "global_min": 1, "global_max": 2, "global_avg": 3,
-    "block_min": 4, "block_max": 5, "block_avg": 6,
+    "block_min": 4, "block_max": 5, "block_avg": 6, "edge_min": 7, "edge_max": 8, "edge_avg": 9,
 }
 _STATUS = {0: "VSZ_OK", 1: "VSZ_ERR_INVALID_ARG", 2: "VSZ_ERR_UNSUPPORTED",
            3: "VSZ_ERR_CAPACITY", 4: "VSZ_ERR_CUDA", 5: "VSZ_ERR_CORRUPT", 6: "VSZ_ERR_TOO_LARGE"}
@@ -201,6 +201,15 @@ class Params:
     def is_block_pad(self) -> bool:
         return self.pad in (4, 5, 6)
 
+    @property
+    def is_edge_pad(self) -> bool:
+        return self.pad in (7, 8, 9)
+
+    @property
+    def pad_len(self) -> int:
+        """Entries of the padding table: nb (block), nb * ndim (edge), 0 otherwise."""
+        return self.nblocks if self.is_block_pad else self.nblocks * len(self.dims) if self.is_edge_pad else 0
+
     def validate(self) -> int:
         return int(lib().vsz_validate(ctypes.byref(self.c())))
 
@@ -246,7 +255,8 @@ class Field:
         self.fix_cap = int(fix_cap if fix_cap is not None else max(1024, n // 64))
         i32 = torch.int32
         self.codes = torch.empty(max(n, 1), dtype=torch.int16, device=dev)
-        self.pad = torch.empty(max(nb, 1), dtype=i32, device=dev) if params.is_block_pad else None
+        self.pad = torch.empty(max(params.pad_len, 1), dtype=i32, device=dev) if params.pad_len or \
+            params.is_block_pad or params.is_edge_pad else None
         self.blk_off = torch.empty(nb + 1, dtype=i32, device=dev)
         self.out_idx = torch.empty(max(self.out_cap, 1), dtype=i32, device=dev)
         self.out_delta = torch.empty(max(self.out_cap, 1), dtype=i32, device=dev)
@@ -331,7 +341,7 @@ class Field:
         return {
             "header": h,
             "codes": self.codes[: self.n].cpu().numpy().view(np.uint16),
-            "pad": self.pad[: self.nb].cpu().numpy() if self.pad is not None else None,
+            "pad": self.pad[: max(self.p.pad_len, 0)].cpu().numpy() if self.pad is not None else None,
             "blk_off": self.blk_off.cpu().numpy().view(np.uint32),
             "out_idx": self.out_idx[:no].cpu().numpy().view(np.uint32),
             "out_delta": self.out_delta[:no].cpu().numpy(),

@@ -111,7 +111,7 @@ vsz_status make_geom(const vsz_params* p, Geom* g) {
     if (!(p->eb > 0.0) || !std::isfinite(p->eb)) return VSZ_ERR_INVALID_ARG;
     if (p->eb_mode != VSZ_EB_ABS && p->eb_mode != VSZ_EB_REL) return VSZ_ERR_INVALID_ARG;
     if (p->radius < 1 || p->radius > 32768) return VSZ_ERR_INVALID_ARG;
-    if (p->pad < VSZ_PAD_ZERO || p->pad > VSZ_PAD_BLOCK_AVG) return VSZ_ERR_INVALID_ARG;
+    if (p->pad < VSZ_PAD_ZERO || p->pad > VSZ_PAD_EDGE_AVG) return VSZ_ERR_INVALID_ARG;
     if (p->block < 1) return VSZ_ERR_INVALID_ARG;
     const uint32_t bmax = p->ndim == 1 ? 256u : p->ndim == 2 ? 128u : 32u;
     if (!pow2(p->block) || p->block < 4 || p->block > bmax) return VSZ_ERR_UNSUPPORTED;
@@ -157,7 +157,7 @@ vsz_status check_compressed(const Geom& g, const vsz_params* p, const vsz_compre
     if (!c || !c->hdr || !c->blk_off) return VSZ_ERR_INVALID_ARG;
     if (!aligned(c->hdr, 8)) return VSZ_ERR_INVALID_ARG;
     if (g.n > 0 && !c->codes) return VSZ_ERR_INVALID_ARG;
-    if (is_block_pad(p->pad) && g.nb > 0 && !c->pad) return VSZ_ERR_INVALID_ARG;
+    if ((is_block_pad(p->pad) || is_edge_pad(p->pad)) && g.nb > 0 && !c->pad) return VSZ_ERR_INVALID_ARG;
     if (c->out_cap > 0 && (!c->out_idx || !c->out_delta)) return VSZ_ERR_INVALID_ARG;
     if (c->fix_cap > 0 && (!c->fix_idx || !c->fix_bits)) return VSZ_ERR_INVALID_ARG;
     if (c->out_cap >= (1ull << 32) || c->fix_cap >= (1ull << 32)) return VSZ_ERR_INVALID_ARG;
@@ -252,7 +252,7 @@ static CompressArgs compress_args(const Geom& g, const vsz_params* p, const floa
     a.chunks = (uint4*)(ws + L.chunks);
     a.stage_out = (uint2*)(ws + L.stage_out);
     a.stage_fix = (uint2*)(ws + L.stage_fix);
-    if (is_global_pad(p->pad)) {
+    if (defers_origin(p->pad)) {
         a.tstats = (TileStats*)(ws + L.tstats);
         a.origin = (int32_t*)(ws + L.origin);
         a.oflag = (uint8_t*)(ws + L.oflag);
@@ -308,8 +308,9 @@ vsz_status vsz_prequant_lorenzo(const vsz_params* p, const float* d_x, vsz_compr
         e = g.nd == 1 ? launch_lorenzo_1d(a, s) : g.nd == 2 ? launch_lorenzo_2d(a, s) : launch_lorenzo_3d(a, s);
     }
     if (e != cudaSuccess) return cuda_fail(e);
-    if (is_global_pad(p->pad)) {
-        // the global padding value is known once every tile is walked
+    if (defers_origin(p->pad)) {
+        // the global padding value is known once every tile is walked; edge
+        // scalars come from a face-statistics pass
         TraceScope ts("origin_fix", s, g.nd, g.b, g.n);
         e = launch_origin_fix(a, s);
         if (e != cudaSuccess) return cuda_fail(e);

@@ -132,6 +132,27 @@ __device__ __forceinline__ int32_t rounded_mean(long long S, long long m) {
     return (int32_t)(qt + ((2 * r >= m) ? 1 : 0));
 }
 
+// Edge granularity (Sec. IV-B-3): the block origin's prediction from the
+// block's per-axis scalars Pk[0..nd): the inclusion-exclusion sum over the
+// non-empty sets S of axes of (-1)^(|S|+1) times the rounded mean of the
+// scalars in S (the value of a neighbour outside along exactly the axes in
+// S), modulo 2^32.  Every other residual does not depend on the scalars.
+__device__ __forceinline__ int32_t edge_origin_pred(const int32_t* __restrict__ Pk, int nd) {
+    uint32_t acc = 0;
+    for (unsigned S = 1; S < (1u << nd); ++S) {
+        long long sum = 0;
+        int m = 0;
+        for (int k = 0; k < nd; ++k)
+            if ((S >> k) & 1u) {
+                sum += Pk[k];
+                ++m;
+            }
+        const uint32_t v = (uint32_t)rounded_mean(sum, m);
+        acc = (__popc(S) & 1) ? acc + v : acc - v;
+    }
+    return (int32_t)acc;
+}
+
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
@@ -196,6 +217,12 @@ __host__ __device__ inline bool is_block_pad(int m) {
 __host__ __device__ inline bool is_global_pad(int m) {
     return m == VSZ_PAD_GLOBAL_MIN || m == VSZ_PAD_GLOBAL_MAX || m == VSZ_PAD_GLOBAL_AVG;
 }
+__host__ __device__ inline bool is_edge_pad(int m) {
+    return m == VSZ_PAD_EDGE_MIN || m == VSZ_PAD_EDGE_MAX || m == VSZ_PAD_EDGE_AVG;
+}
+// Modes whose padding is known only after the walk: the walk leaves the block
+// origins to an origin pass (global statistics, or per-block face statistics).
+__host__ __device__ inline bool defers_origin(int m) { return is_global_pad(m) || is_edge_pad(m); }
 
 // Element index of the origin of block `blk` and the tile holding it.
 __host__ __device__ inline void block_origin(const Geom& g, uint64_t blk, uint64_t* idx, uint64_t* tile) {

@@ -450,6 +450,7 @@ vsz_status vsz_batch_create(const vsz_field_job* jobs, int njobs, void* d_ws, si
         if (st != VSZ_OK) return st;
         if ((st = check_compressed(g, &jobs[i].params, &jobs[i].out)) != VSZ_OK) return st;
         if (g.n > 0 && !jobs[i].d_x) return VSZ_ERR_INVALID_ARG;
+        if (is_edge_pad(jobs[i].params.pad)) return VSZ_ERR_UNSUPPORTED;  // one-field path only
     }
     const size_t need = batch_layout(jobs, njobs, &offs, &geoms);
     if (!need || ws_bytes < need) return VSZ_ERR_INVALID_ARG;

@@ -271,7 +271,7 @@ __device__ __forceinline__ void recon_1d_step(const ReconArgs& a, const uint64_t
     const int32_t R = a.R;
     const uint64_t n = a.g.n;
     const int glane = lane & (G - 1);
-    const bool bp = is_block_pad(a.pad_mode);
+    const bool bp = is_block_pad(a.pad_mode) || is_edge_pad(a.pad_mode);  // 1D edge: one scalar per block
     {
         const uint64_t base = st * SPAN + (uint64_t)lane * EPL;
         const int valid = base < n ? (int)umin64(EPL, n - base) : 0;
@@ -423,7 +423,7 @@ static cudaError_t launch_c1_k(const CompressArgs& a, cudaStream_t s) {
 template <int B>
 static cudaError_t launch_c1(const CompressArgs& a, cudaStream_t s) {
     if (is_block_pad(a.pad_mode)) return launch_c1_k<B, true, false>(a, s);
-    if (is_global_pad(a.pad_mode)) return launch_c1_k<B, false, true>(a, s);
+    if (defers_origin(a.pad_mode)) return launch_c1_k<B, false, true>(a, s);
     return launch_c1_k<B, false, false>(a, s);
 }
 

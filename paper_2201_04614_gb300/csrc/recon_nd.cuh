@@ -51,6 +51,7 @@ __device__ __forceinline__ void nd_recon_tile(const ReconArgs& a, const uint64_t
                          fabsf(__fmul_rn(a.hdr->xmax, inv2eb_h)) < 1048576.0f;
     const int32_t R = a.R;
     const bool bp = is_block_pad(a.pad_mode);
+    const bool ep = is_edge_pad(a.pad_mode);
     const uint64_t nx = g.nx;
     const uint64_t plane = g.ny * g.nx;
     const int glane = lane & (G - 1);
@@ -81,6 +82,7 @@ __device__ __forceinline__ void nd_recon_tile(const ReconArgs& a, const uint64_t
         lo = a.blk_off[blk];
         hi = a.blk_off[blk + 1];
         if (bp) P = a.pad[blk];
+        else if (ep) P = edge_origin_pred(a.pad + blk * ND, ND);
     }
     lo = __shfl_sync(VSZ_FULL, lo, src);
     hi = __shfl_sync(VSZ_FULL, hi, src);
@@ -527,7 +529,7 @@ cudaError_t launch_nd_compress_k(const CompressArgs& a, cudaStream_t s) {
 template <int ND, int B>
 cudaError_t launch_nd_compress(const CompressArgs& a, cudaStream_t s) {
     if (is_block_pad(a.pad_mode)) return launch_nd_compress_k<ND, B, true, false>(a, s);
-    if (is_global_pad(a.pad_mode)) return launch_nd_compress_k<ND, B, false, true>(a, s);
+    if (defers_origin(a.pad_mode)) return launch_nd_compress_k<ND, B, false, true>(a, s);
     return launch_nd_compress_k<ND, B, false, false>(a, s);
 }
 

@@ -58,7 +58,8 @@ def test_abi_version_and_status_strings(vsz):
     (dict(dims=(10,), block=8, eb=float("nan")), 1),
     (dict(dims=(10,), block=8, eb=1e-3, radius=0), 1),
     (dict(dims=(10,), block=8, eb=1e-3, radius=32769), 1),
-    (dict(dims=(10,), block=8, eb=1e-3, pad=7), 1),
+    (dict(dims=(10,), block=8, eb=1e-3, pad=9), 0),   # edge average (Sec. IV-B-3)
+    (dict(dims=(10,), block=8, eb=1e-3, pad=10), 1),
     (dict(dims=(1 << 16, 1 << 16), block=8, eb=1e-3), 1),  # n >= 2^32
     (dict(dims=(0,), block=8, eb=1e-3), 0),          # empty field
 ])

@@ -221,3 +221,12 @@ def test_launch_shapes_and_autotune_change_no_result():
     with pytest.raises(vsz.VszError):
         b.set_shape(len(cls), 4, 0)
     b.close()
+
+
+def test_batch_rejects_edge_padding():
+    """Edge padding runs on the one-field path only."""
+    x = torch.from_numpy(np.ascontiguousarray(field_for((64, 64), 5).reshape(-1), np.float32)).cuda()
+    f = vsz.Field(vsz.Params.make((64, 64), 16, 1e-4, "rel", 512, "edge_avg"))
+    with pytest.raises(vsz.VszError) as e:
+        vsz.Batch([f], [x])
+    assert e.value.status == 2

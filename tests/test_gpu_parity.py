@@ -21,7 +21,8 @@ if not torch.cuda.is_available():  # pragma: no cover
 import oracle  # noqa: E402
 import paper_2201_04614_gb300 as vsz  # noqa: E402
 
-PADS = ["zero", "global_min", "global_max", "global_avg", "block_min", "block_max", "block_avg"]
+PADS = ["zero", "global_min", "global_max", "global_avg", "block_min", "block_max", "block_avg",
+        "edge_min", "edge_max", "edge_avg"]
 
 
 def run_both(x, dims, block, eb, eb_mode="rel", radius=512, pad="zero", out_cap=None, fix_cap=None):
@@ -98,7 +99,7 @@ def test_parity_shapes_pads(dims, block, pad):
 @pytest.mark.parametrize("dims,block", [((5000,), 64), ((90, 130), 16), ((12, 20, 68), 8)])
 def test_parity_radius_extremes(dims, block, radius):
     x = field_for(dims, seed=7)
-    for pad in ("zero", "block_avg", "global_max"):
+    for pad in ("zero", "block_avg", "global_max", "edge_avg"):
         f, c, g, o, xx = run_both(x, dims, block, 1e-4, "rel", radius, pad)
         assert_parity(f, c, g, o, xx, pad)
 
@@ -116,7 +117,7 @@ def test_parity_adversarial(dims, block, eb_abs):
 
 def test_parity_all_nan_and_constant():
     for x in (np.full(3000, np.nan, np.float32), np.full(3000, 2.5, np.float32)):
-        for pad in ("zero", "block_avg", "global_avg"):
+        for pad in ("zero", "block_avg", "global_avg", "edge_avg"):
             f, c, g, o, xx = run_both(x, (50, 60), 16, 1e-3, "rel", 512, pad, out_cap=3000, fix_cap=3000)
             assert_parity(f, c, g, o, xx, pad)
 
