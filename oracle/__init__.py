@@ -86,6 +86,11 @@ def _load():
                                       P(ctypes.c_uint64), vp, vp, P(ctypes.c_uint64)]
         lib.vszo_decompress.argtypes = [P(_Params), P(_Eb), vp, vp, vp, vp, vp,
                                         ctypes.c_uint64, vp, vp, ctypes.c_uint64, vp, vp]
+        u32, u64 = ctypes.c_uint32, ctypes.c_uint64
+        lib.vszo_huffman_lengths.argtypes = [vp, u32, vp]
+        lib.vszo_huffman_codes.argtypes = [vp, u32, vp]
+        lib.vszo_huffman_encode.argtypes = [vp, u64, vp, vp, u32, u32, vp, vp]
+        lib.vszo_huffman_decode.argtypes = [vp, vp, u64, vp, vp, u32, u32, vp]
         _lib = lib
     return _lib
 
@@ -259,3 +264,52 @@ def decompress(p: Params, c: Compressed, return_q: bool = False):
     if rc:
         raise ValueError(f"oracle decompress failed rc={rc}")
     return (xhat, q) if return_q else xhat
+
+
+# ---------------------------------------------------------------- entropy stage
+HUFF_CHUNK = 4096  # symbols per word-aligned chunk of the bitstream
+
+
+def huffman_book(hist):
+    """Canonical Huffman code of a histogram: (lengths uint8[nsym],
+    codewords uint64[nsym]) -- Sec. II-B's entropy stage."""
+    hist = np.ascontiguousarray(hist, dtype=np.uint32).reshape(-1)
+    nsym = hist.size
+    ln = np.zeros(max(nsym, 1), np.uint8)
+    cw = np.zeros(max(nsym, 1), np.uint64)
+    if _load().vszo_huffman_lengths(hist.ctypes.data, nsym, ln.ctypes.data):
+        raise ValueError("oracle huffman_lengths failed")
+    _load().vszo_huffman_codes(ln.ctypes.data, nsym, cw.ctypes.data)
+    return ln[:nsym], cw[:nsym]
+
+
+def huffman_encode(sym, lengths, codes, chunk: int = HUFF_CHUNK):
+    """Word-aligned chunks, MSB first: (words uint32[], chunk_off uint64[nchunks+1])."""
+    sym = np.ascontiguousarray(sym, dtype=np.uint16).reshape(-1)
+    lengths = np.ascontiguousarray(lengths, np.uint8)
+    codes = np.ascontiguousarray(codes, np.uint64)
+    n = sym.size
+    nchunks = (n + chunk - 1) // chunk
+    bits = int(lengths.astype(np.int64)[sym].sum()) if n else 0
+    words = np.zeros(max(1, bits // 32 + nchunks + 1), np.uint32)
+    off = np.zeros(nchunks + 1, np.uint64)
+    rc = _load().vszo_huffman_encode(sym.ctypes.data if n else None, n, lengths.ctypes.data, codes.ctypes.data,
+                                     lengths.size, chunk, words.ctypes.data, off.ctypes.data)
+    if rc:
+        raise ValueError(f"oracle huffman_encode failed rc={rc}")
+    return words[: int(off[-1])].copy(), off
+
+
+def huffman_decode(words, chunk_off, n, lengths, codes, chunk: int = HUFF_CHUNK):
+    words = np.ascontiguousarray(words, np.uint32)
+    if words.size == 0:
+        words = np.zeros(1, np.uint32)
+    chunk_off = np.ascontiguousarray(chunk_off, np.uint64)
+    lengths = np.ascontiguousarray(lengths, np.uint8)
+    codes = np.ascontiguousarray(codes, np.uint64)
+    out = np.zeros(max(n, 1), np.uint16)
+    rc = _load().vszo_huffman_decode(words.ctypes.data, chunk_off.ctypes.data, n, lengths.ctypes.data,
+                                     codes.ctypes.data, lengths.size, chunk, out.ctypes.data)
+    if rc:
+        raise ValueError(f"oracle huffman_decode failed rc={rc}")
+    return out[:n]

@@ -591,3 +591,137 @@ int vszo_decompress(const vszo_params* p, const vszo_eb* eb,
     }
     return VSZO_OK;
 }
+
+/* ------------------------------------------------------------------ */
+/* Entropy stage: canonical Huffman coding of the quantization codes   */
+/* ------------------------------------------------------------------ */
+
+/* Sec. II-B: SZ entropy-codes the quantization codes with Huffman coding.
+ * reading: the code is a plain Huffman code built from the code histogram
+ * by repeatedly merging the two lightest nodes; among nodes of equal weight
+ * leaves come before merged nodes, leaves in symbol order, merged nodes in
+ * the order they were made.  A leaf's length is its depth (a lone symbol
+ * gets length 1).  Codewords are canonical: symbols sorted by (length,
+ * symbol) get consecutive codes, each shifted left when the length grows. */
+int vszo_huffman_lengths(const uint32_t* hist, uint32_t nsym, uint8_t* len)
+{
+    /* nodes 0..nsym-1 are the leaves, nsym.. the merged nodes */
+    uint64_t* w = (uint64_t*)malloc(sizeof(uint64_t) * 2 * (size_t)nsym);
+    int32_t* parent = (int32_t*)malloc(sizeof(int32_t) * 2 * (size_t)nsym);
+    uint8_t* alive = (uint8_t*)malloc(2 * (size_t)nsym);
+    if (!w || !parent || !alive) { free(w); free(parent); free(alive); return VSZO_ERR_ARG; }
+    uint32_t live = 0, next = nsym;
+    for (uint32_t s = 0; s < nsym; ++s) {
+        w[s] = hist[s];
+        parent[s] = -1;
+        alive[s] = hist[s] > 0;
+        live += alive[s];
+        len[s] = 0;
+    }
+    if (live == 1) {
+        for (uint32_t s = 0; s < nsym; ++s) if (alive[s]) len[s] = 1;
+    }
+    while (live > 1) {
+        /* the two lightest live nodes; node ids order the ties as the
+         * reading says (leaves < merged; symbols ascending; merge order) */
+        int64_t a = -1, b = -1;
+        for (uint32_t i = 0; i < next; ++i) {
+            if (!alive[i]) continue;
+            if (a < 0 || w[i] < w[a]) { b = a; a = i; }
+            else if (b < 0 || w[i] < w[b]) { b = i; }
+        }
+        w[next] = w[a] + w[b];
+        parent[next] = -1;
+        alive[next] = 1;
+        parent[a] = (int32_t)next;
+        parent[b] = (int32_t)next;
+        alive[a] = alive[b] = 0;
+        ++next;
+        --live;
+    }
+    if (next > nsym) {
+        for (uint32_t s = 0; s < nsym; ++s) {
+            if (hist[s] == 0) continue;
+            uint32_t d = 0;
+            for (int32_t v = (int32_t)s; parent[v] >= 0; v = parent[v]) ++d;
+            if (d > 64) { free(w); free(parent); free(alive); return VSZO_ERR_ARG; }
+            len[s] = (uint8_t)d;
+        }
+    }
+    free(w);
+    free(parent);
+    free(alive);
+    return VSZO_OK;
+}
+
+int vszo_huffman_codes(const uint8_t* len, uint32_t nsym, uint64_t* code)
+{
+    uint64_t c = 0;
+    int prev = 0, first = 1;
+    for (int L = 1; L <= 64; ++L) {
+        for (uint32_t s = 0; s < nsym; ++s) {
+            if (len[s] != L) continue;
+            if (first) { c = 0; first = 0; }
+            else { c = (c + 1) << (L - prev); }
+            prev = L;
+            code[s] = c;
+        }
+    }
+    for (uint32_t s = 0; s < nsym; ++s) if (len[s] == 0) code[s] = 0;
+    return VSZO_OK;
+}
+
+/* reading: the stream is cut into chunks of `chunk` symbols; each chunk
+ * starts on a 32-bit word boundary and its bits fill words from the most
+ * significant bit down; chunk_off[c] is the first word of chunk c and
+ * chunk_off[nchunks] the total.  A chunk's unused tail bits are zero. */
+int vszo_huffman_encode(const uint16_t* sym, uint64_t n, const uint8_t* len, const uint64_t* code,
+                        uint32_t nsym, uint32_t chunk, uint32_t* words, uint64_t* chunk_off)
+{
+    uint64_t nchunks = (n + chunk - 1) / chunk, wpos = 0;
+    for (uint64_t c = 0; c < nchunks; ++c) {
+        chunk_off[c] = wpos;
+        uint64_t bit = 0; /* bits written in this chunk */
+        uint64_t i1 = (c + 1) * chunk < n ? (c + 1) * chunk : n;
+        for (uint64_t i = c * chunk; i < i1; ++i) {
+            uint32_t s = sym[i];
+            if (s >= nsym || len[s] == 0) return VSZO_ERR_DATA;
+            for (int k = len[s] - 1; k >= 0; --k) {
+                uint64_t wi = wpos + bit / 32;
+                if (bit % 32 == 0) words[wi] = 0;
+                if ((code[s] >> k) & 1u) words[wi] |= 1u << (31 - bit % 32);
+                ++bit;
+            }
+        }
+        wpos += (bit + 31) / 32;
+    }
+    chunk_off[nchunks] = wpos;
+    return VSZO_OK;
+}
+
+/* Decoding reads bits one at a time and matches the accumulated prefix
+ * against every symbol's (length, codeword); the code is prefix-free, so
+ * the first match is the symbol. */
+int vszo_huffman_decode(const uint32_t* words, const uint64_t* chunk_off, uint64_t n, const uint8_t* len,
+                        const uint64_t* code, uint32_t nsym, uint32_t chunk, uint16_t* sym)
+{
+    uint64_t nchunks = (n + chunk - 1) / chunk;
+    for (uint64_t c = 0; c < nchunks; ++c) {
+        uint64_t bit = 0, wbase = chunk_off[c], wend = chunk_off[c + 1];
+        uint64_t i1 = (c + 1) * chunk < n ? (c + 1) * chunk : n;
+        for (uint64_t i = c * chunk; i < i1; ++i) {
+            uint64_t acc = 0;
+            int L = 0, found = 0;
+            while (!found) {
+                if (L == 64 || wbase + bit / 32 >= wend) return VSZO_ERR_DATA;
+                acc = (acc << 1) | ((words[wbase + bit / 32] >> (31 - bit % 32)) & 1u);
+                ++bit;
+                ++L;
+                for (uint32_t s = 0; s < nsym; ++s) {
+                    if (len[s] == L && code[s] == acc) { sym[i] = (uint16_t)s; found = 1; break; }
+                }
+            }
+        }
+    }
+    return VSZO_OK;
+}

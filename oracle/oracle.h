@@ -101,6 +101,18 @@ int vszo_decompress(const vszo_params* p, const vszo_eb* eb,
                     const uint32_t* fix_idx, const uint32_t* fix_bits,
                     uint64_t n_fix, int32_t* q_out, float* xhat);
 
+/* Entropy stage (Sec. II-B): canonical Huffman code of the quantization
+ * codes.  lengths: len[s] in 0..64 (0 = unused symbol); codes: canonical
+ * codewords (right-aligned).  encode/decode: chunks of `chunk` symbols,
+ * each starting on a 32-bit word, MSB first; chunk_off[nchunks + 1] word
+ * offsets. */
+int vszo_huffman_lengths(const uint32_t* hist, uint32_t nsym, uint8_t* len);
+int vszo_huffman_codes(const uint8_t* len, uint32_t nsym, uint64_t* code);
+int vszo_huffman_encode(const uint16_t* sym, uint64_t n, const uint8_t* len, const uint64_t* code,
+                        uint32_t nsym, uint32_t chunk, uint32_t* words, uint64_t* chunk_off);
+int vszo_huffman_decode(const uint32_t* words, const uint64_t* chunk_off, uint64_t n, const uint8_t* len,
+                        const uint64_t* code, uint32_t nsym, uint32_t chunk, uint16_t* sym);
+
 #ifdef __cplusplus
 }
 #endif
