@@ -55,6 +55,7 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-batch", action="store_true", help="skip the batched+tuned vs plain comparison")
     ap.add_argument("--batch-steps", type=int, default=20)
+    ap.add_argument("--no-entropy", action="store_true", help="skip the Huffman stage and rate-distortion curve")
     return ap.parse_args()
 
 
@@ -400,6 +401,76 @@ def run_batch_compare(a, log_fn=log) -> dict:
     return res
 
 
+# ---------------------------------------------------------------- entropy stage
+def run_entropy(a, x3, xd, log_fn=log) -> dict:
+    """The entropy stage (Sec. II-B) on the codes of the bench field: code
+    histogram, Huffman codebook, encode and decode throughput (CUDA events,
+    median of 10), and the rate-distortion curve: PSNR against total bits per
+    value (Huffman stream + outliers + fixups + block offsets + chunk
+    offsets + padding table), relative eb 1e-2..1e-5."""
+    import numpy as np
+    import torch
+    import paper_2201_04614_gb300 as vsz
+
+    n = x3.size
+    vrange = float(x3.max()) - float(x3.min())
+    xh = torch.empty(n, dtype=torch.float32, device="cuda")
+    out = {"curve": []}
+
+    def ev_ms(fn, k=10):
+        ts = []
+        for _ in range(2):
+            fn()
+        for _ in range(k):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return sorted(ts)[len(ts) // 2]
+
+    for eb in (1e-2, 1e-3, 1e-4, 1e-5):
+        p = vsz.Params.make(x3.shape, a.block, eb, "rel", a.radius, a.pad)
+        f = vsz.Field(p, out_cap=n // 2, fix_cap=max(1 << 16, n // 64))
+        f.compress(xd)
+        f.reconstruct(out=xh)
+        h = f.header()
+        nsym = 2 * a.radius
+        hist = f.code_histogram()
+        book = vsz.HuffmanBook(hist, nsym)
+        words, off, st = vsz.huffman_encode(f.codes, n, book)
+        nwords = int(off[-1].item())
+        dec, st2 = vsz.huffman_decode(words, off, n, book)
+        ok = int(st.item()) == 0 and int(st2.item()) == 0 and bool(torch.equal(dec[:n], f.codes[:n]))
+        nc = off.numel() - 1
+        table_bits = 32 * (p.nblocks + 1) + 64 * (nc + 1) + 32 * p.pad_len
+        bits = 32 * nwords + 64 * int(h["n_out"]) + 64 * int(h["n_fix"]) + table_bits
+        mse = float(((xh.double() - xd.double()) ** 2).mean().item())
+        psnr = 20 * math.log10(vrange) - 10 * math.log10(mse) if mse > 0 else float("inf")
+        row = {"eb": eb, "bits_per_value": bits / n, "ratio": 32.0 * n / bits, "huffman_bits_per_value": 32 * nwords / n,
+               "psnr_db": psnr, "n_out": int(h["n_out"]), "n_fix": int(h["n_fix"]), "round_trip_ok": ok}
+        if eb == a.eb:
+            ms_hist = ev_ms(lambda: f.code_histogram(out=hist))
+            ms_book = ev_ms(lambda: vsz.HuffmanBook(hist, nsym))
+            ms_enc = ev_ms(lambda: vsz.huffman_encode(f.codes, n, book, words=words))
+            ms_dec = ev_ms(lambda: vsz.huffman_decode(words, off, n, book, out=dec))
+            # bytes each pass must move: encode reads the codes twice (bit
+            # counts, then packing) and writes the stream; decode reads the
+            # stream and writes the codes
+            enc_bytes, dec_bytes = 4 * n + 4 * nwords, 4 * nwords + 2 * n
+            row["timing"] = {
+                "histogram_us": ms_hist * 1e3, "book_us": ms_book * 1e3,
+                "encode_us": ms_enc * 1e3, "decode_us": ms_dec * 1e3,
+                "encode_GBps_fp32_in": 4 * n / (ms_enc * 1e-3) / 1e9, "decode_GBps_fp32_out": 4 * n / (ms_dec * 1e-3) / 1e9,
+                "encode_hbm_GBps": enc_bytes / (ms_enc * 1e-3) / 1e9, "decode_hbm_GBps": dec_bytes / (ms_dec * 1e-3) / 1e9}
+        out["curve"].append(row)
+        log_fn(f"[bench] entropy eb={eb:g}: {row}")
+        del f, book, words, off, dec
+        torch.cuda.empty_cache()
+    return out
+
+
 # ---------------------------------------------------------------- GPU arm
 def run_gpu(a):
     import numpy as np
@@ -601,6 +672,10 @@ def run_gpu(a):
                 del fs
                 torch.cuda.empty_cache()
 
+    entropy = None
+    if not a.no_entropy and rank == 0:
+        entropy = run_entropy(a, x3, xd)
+
     batched = None
     if not a.no_batch and rank == 0:
         del xh
@@ -633,7 +708,7 @@ def run_gpu(a):
                                       / a.steps * 1e-3) / 1e9,
             "reconstruct_GBps": n * 4 / (sum(per[k]["ms"] for k in ("recon", "fixups") if k in per)
                                          / a.steps * 1e-3) / 1e9,
-            "sweep": sweep, "batched": batched,
+            "sweep": sweep, "entropy": entropy, "batched": batched,
         }
         print(json.dumps(line), flush=True)
     if dist:

@@ -368,6 +368,60 @@ VSZ_API vsz_status vsz_code_histogram(const vsz_params* p, const uint16_t* d_cod
                               void* stream);
 
 /* ------------------------------------------------------------------------ */
+/* Entropy stage: canonical Huffman coding of the quantization codes.       */
+/* ------------------------------------------------------------------------ */
+/*
+ * Sec. II-B: SZ follows the prediction and quantization with Huffman coding
+ * of the integer codes.  Symbols are the codes 0..nsym-1 (nsym = 2R for
+ * dual-quant codes).  The codebook is a Huffman code of the symbols'
+ * histogram (vsz_code_histogram), built by repeatedly merging the two
+ * lightest nodes; among equal weights leaves come before merged nodes,
+ * leaves in symbol order, merged nodes in the order they were made.
+ * Codewords are canonical: symbols sorted by (length, symbol) get
+ * consecutive codes.  A lone symbol gets length 1.  Lengths never exceed 64
+ * for counts below 2^32.
+ * The stream is cut into chunks of VSZ_HUFF_CHUNK symbols; each chunk starts
+ * on a 32-bit word and fills words from the most significant bit down (the
+ * unused tail bits are zero); chunk_off[c] is the first word of chunk c and
+ * chunk_off[nchunks] the total, so chunks encode and decode independently.
+ */
+#define VSZ_HUFF_CHUNK 4096
+#define VSZ_HUFF_MAX_SYMBOLS 8192   /* codebooks for R <= 4096 */
+
+/* Bytes of a device codebook for nsym symbols (0 if nsym is 0 or above
+ * VSZ_HUFF_MAX_SYMBOLS). */
+VSZ_API size_t vsz_huffman_book_bytes(uint32_t nsym);
+
+/* Build the codebook of d_hist[nsym] (uint32 counts, device) into d_book
+ * (device, 16-byte aligned, vsz_huffman_book_bytes(nsym) bytes; opaque) on
+ * one CTA.  VSZ_ERR_UNSUPPORTED if nsym > VSZ_HUFF_MAX_SYMBOLS. */
+VSZ_API vsz_status vsz_huffman_book(const uint32_t* d_hist, uint32_t nsym, void* d_book, size_t book_bytes,
+                                    void* stream);
+
+/* Copy a codebook's lengths (h_len[nsym], 0 = unused symbol), codewords
+ * (h_code[nsym], right-aligned) and longest length to the host; any of them
+ * may be NULL.  Synchronizes the stream. */
+VSZ_API vsz_status vsz_huffman_book_read(const void* d_book, uint32_t nsym, uint8_t* h_len, uint64_t* h_code,
+                                         uint32_t* h_max_len, void* stream);
+
+/* Encode d_sym[n] (uint16 symbols < nsym, device) into d_words (uint32,
+ * word_cap words) and d_chunk_off[ceil(n / VSZ_HUFF_CHUNK) + 1] (uint64).
+ * *d_status (device uint32) receives bit 1 if a symbol has no codeword and
+ * bit 2 if the stream is longer than word_cap words (the offsets are still
+ * exact, so the caller can retry with chunk_off[nchunks] words). */
+VSZ_API vsz_status vsz_huffman_encode(const uint16_t* d_sym, uint64_t n, const void* d_book, uint32_t nsym,
+                                      uint32_t* d_words, uint64_t word_cap, uint64_t* d_chunk_off,
+                                      uint32_t* d_status, void* stream);
+
+/* Decode n symbols from d_words (word_cap words readable) / d_chunk_off into
+ * d_sym (uint16, device).  *d_status receives bit 4 if a chunk holds no
+ * valid codeword where one is expected or runs past its words (or past
+ * word_cap).  Both calls set bit 8 if d_book was built for another nsym. */
+VSZ_API vsz_status vsz_huffman_decode(const uint32_t* d_words, uint64_t word_cap, const uint64_t* d_chunk_off,
+                                      uint64_t n, const void* d_book, uint32_t nsym, uint16_t* d_sym,
+                                      uint32_t* d_status, void* stream);
+
+/* ------------------------------------------------------------------------ */
 /* Learned tuner of block size and padding mode.                            */
 /* ------------------------------------------------------------------------ */
 /*

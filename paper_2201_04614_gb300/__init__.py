@@ -81,6 +81,8 @@ EXPORTED = ["vsz_status_string", "vsz_last_cuda_error", "vsz_abi_version", "vsz_
             "vsz_compress_noalloc", "vsz_batch_workspace_size", "vsz_batch_create", "vsz_batch_submit",
             "vsz_batch_destroy", "vsz_batch_num_classes", "vsz_batch_get_class", "vsz_batch_set_shape",
             "vsz_batch_set_concurrent", "vsz_batch_autotune", "vsz_batch_set_outputs", "vsz_batch_reconstruct",
+            "vsz_huffman_book_bytes", "vsz_huffman_book", "vsz_huffman_book_read", "vsz_huffman_encode",
+            "vsz_huffman_decode",
             "vsz_tuner_features_workspace_size", "vsz_tuner_features",
             "vsz_tuner_sweep_workspace_size", "vsz_tuner_sweep", "vsz_tuner_guard_workspace_size",
             "vsz_tuner_guard", "vsz_tuner_guard_sample_dims", "vsz_mlp_forward", "vsz_mlp_grad_workspace_size",
@@ -135,6 +137,12 @@ def lib():
     L.vsz_batch_set_concurrent.argtypes = [vp, ctypes.c_int]
     L.vsz_batch_autotune.argtypes = [vp, vp, ctypes.c_int]
     L.vsz_batch_set_outputs.argtypes = [vp, P(ctypes.c_void_p)]
+    L.vsz_huffman_book_bytes.restype = sz
+    L.vsz_huffman_book_bytes.argtypes = [ctypes.c_uint32]
+    L.vsz_huffman_book.argtypes = [vp, ctypes.c_uint32, vp, sz, vp]
+    L.vsz_huffman_book_read.argtypes = [vp, ctypes.c_uint32, vp, vp, P(ctypes.c_uint32), vp]
+    L.vsz_huffman_encode.argtypes = [vp, u64, vp, ctypes.c_uint32, vp, u64, vp, vp, vp]
+    L.vsz_huffman_decode.argtypes = [vp, u64, vp, u64, vp, ctypes.c_uint32, vp, vp, vp]
     L.vsz_batch_reconstruct.argtypes = [vp, vp]
     L.vsz_trace_enable.argtypes = [ctypes.c_int]
     L.vsz_trace_read.argtypes = [P(_CTrace), ctypes.c_int]
@@ -142,7 +150,8 @@ def lib():
         if name.startswith(("vsz_tuner", "vsz_mlp")):
             continue  # bound by tuner.py
         if name not in ("vsz_status_string", "vsz_last_cuda_error", "vsz_abi_version",
-                        "vsz_num_elems", "vsz_num_blocks", "vsz_workspace_size", "vsz_batch_workspace_size"):
+                        "vsz_num_elems", "vsz_num_blocks", "vsz_workspace_size", "vsz_batch_workspace_size",
+                        "vsz_huffman_book_bytes"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -428,3 +437,57 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------- entropy stage
+HUFF_CHUNK = 4096            # VSZ_HUFF_CHUNK
+HUFF_MAX_SYMBOLS = 8192      # VSZ_HUFF_MAX_SYMBOLS
+
+
+class HuffmanBook:
+    """Canonical Huffman codebook of a device histogram (vsz_huffman_book)."""
+
+    def __init__(self, hist, nsym: int | None = None, stream=None):
+        import torch
+        self.nsym = int(nsym if nsym is not None else hist.numel())
+        nb = int(lib().vsz_huffman_book_bytes(self.nsym))
+        if nb == 0:
+            raise VszError(2 if self.nsym > HUFF_MAX_SYMBOLS else 1, "vsz_huffman_book_bytes")
+        self.buf = torch.empty(nb, dtype=torch.uint8, device=hist.device)
+        _check(lib().vsz_huffman_book(_ptr(hist), self.nsym, _ptr(self.buf), nb, _stream_handle(stream)),
+               "vsz_huffman_book")
+
+    def read(self, stream=None):
+        """(lengths uint8[nsym], codewords uint64[nsym], longest length) on the host."""
+        import numpy as np
+        ln = np.zeros(self.nsym, np.uint8)
+        cw = np.zeros(self.nsym, np.uint64)
+        mx = ctypes.c_uint32(0)
+        _check(lib().vsz_huffman_book_read(_ptr(self.buf), self.nsym, ln.ctypes.data, cw.ctypes.data,
+                                           ctypes.byref(mx), _stream_handle(stream)), "vsz_huffman_book_read")
+        return ln, cw, int(mx.value)
+
+
+def huffman_encode(sym, n: int, book: HuffmanBook, words=None, stream=None):
+    """Encode n uint16 symbols (a CUDA tensor viewed as int16/uint16).
+    Returns (words, chunk_off, status) as CUDA tensors; status is read by
+    the caller (bit 1: a symbol without a codeword, bit 2: words too short)."""
+    import torch
+    nc = (n + HUFF_CHUNK - 1) // HUFF_CHUNK
+    off = torch.empty(nc + 1, dtype=torch.int64, device=sym.device)
+    if words is None:
+        words = torch.empty(max(1, n // 2 + nc + 16), dtype=torch.int32, device=sym.device)  # 16 bits/symbol
+    st = torch.empty(1, dtype=torch.int32, device=sym.device)
+    _check(lib().vsz_huffman_encode(_ptr(sym), n, _ptr(book.buf), book.nsym, _ptr(words), words.numel(),
+                                    _ptr(off), _ptr(st), _stream_handle(stream)), "vsz_huffman_encode")
+    return words, off, st
+
+
+def huffman_decode(words, chunk_off, n: int, book: HuffmanBook, out=None, stream=None):
+    import torch
+    if out is None:
+        out = torch.empty(max(n, 1), dtype=torch.int16, device=words.device)
+    st = torch.empty(1, dtype=torch.int32, device=words.device)
+    _check(lib().vsz_huffman_decode(_ptr(words), words.numel(), _ptr(chunk_off), n, _ptr(book.buf), book.nsym,
+                                    _ptr(out), _ptr(st), _stream_handle(stream)), "vsz_huffman_decode")
+    return out, st

@@ -19,7 +19,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(HERE, "libvsz.so")
 
-SOURCES = ["api.cu", "k_misc.cu", "k_batch.cu", "k_rank1.cu", "k_rank2.cu", "k_rank3.cu", "k_tuner.cu"]
+SOURCES = ["api.cu", "k_misc.cu", "k_batch.cu", "k_rank1.cu", "k_rank2.cu", "k_rank3.cu", "k_tuner.cu",
+           "k_huffman.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC",
               "-Xcompiler", "-fvisibility=hidden"]

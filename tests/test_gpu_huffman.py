@@ -1,0 +1,120 @@
+"""GPU parity of the entropy stage (Sec. II-B): codebook, bitstream and
+decoding through the C ABI against the oracle's canonical Huffman coder,
+bit for bit."""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import oracle  # noqa: E402
+import paper_2201_04614_gb300 as vsz  # noqa: E402
+
+
+def _fib(k):
+    f = [1, 1]
+    while len(f) < k:
+        f.append(f[-1] + f[-2])
+    return f
+
+
+def _hists():
+    rng = np.random.default_rng(9)
+    out = [("textbook", np.array([45, 13, 12, 16, 9, 5, 0, 0], np.uint32)),
+           ("lone", np.array([0, 0, 0, 77], np.uint32)),
+           ("fibonacci40", np.array(_fib(40), np.uint32)),
+           ("equal", np.full(64, 5, np.uint32)),
+           ("random1024", rng.integers(0, 5000, 1024).astype(np.uint32)),
+           ("sparse8192", (rng.random(8192) < 0.05) * rng.integers(1, 1 << 20, 8192)),
+           ("peaked1024", (1e7 * np.exp(-np.abs(np.arange(1024) - 512) / 3.0)).astype(np.uint32))]
+    return [(k, np.asarray(h, np.uint32)) for k, h in out]
+
+
+@pytest.mark.parametrize("name,hist", _hists(), ids=lambda v: v if isinstance(v, str) else "")
+def test_book_matches_oracle(name, hist):
+    book = vsz.HuffmanBook(torch.from_numpy(hist.view(np.int32)).cuda(), hist.size)
+    ln, cw, mx = book.read()
+    lo, co = oracle.huffman_book(hist)
+    assert np.array_equal(ln, lo), name
+    assert np.array_equal(cw, co), name
+    assert mx == int(lo.max())
+
+
+def _dq_codes(dims, block, eb, R, seed):
+    x = synth.fourier2d(*dims, seed=seed, value_range=10.0, offset=1.0) if len(dims) == 2 else \
+        np.exp(synth.grf3d(dims, seed))
+    f = vsz.Field(vsz.Params.make(dims, block, eb, "rel", R, "zero"))
+    f.compress(torch.from_numpy(np.ascontiguousarray(x, np.float32).reshape(-1)).cuda())
+    return f.codes[: f.n], f.n, 2 * R
+
+
+def _streams():
+    rng = np.random.default_rng(4)
+    out = []
+    for dims, block, eb, R in [((300, 519), 16, 1e-4, 512), ((19, 37, 260), 8, 1e-5, 512),
+                               ((64, 64), 16, 1e-2, 4096), ((1, 5), 4, 1e-3, 2)]:
+        out.append(("dq", dims, block, eb, R))
+    for n, nsym in [(4096 * 3 + 5, 300), (1, 4), (4096, 2), (70001, 1024)]:
+        out.append(("rand", n, nsym, int(rng.integers(0, 1 << 30)), 0))
+    return out
+
+
+@pytest.mark.parametrize("case", _streams(), ids=lambda c: f"{c[0]}-{c[1]}")
+def test_stream_matches_oracle_and_round_trips(case):
+    if case[0] == "dq":
+        _, dims, block, eb, R = case
+        sym_t, n, nsym = _dq_codes(dims, block, eb, R, seed=3)
+        sym = sym_t.cpu().numpy().view(np.uint16)
+    else:
+        _, n, nsym, seed, _ = case
+        rng = np.random.default_rng(seed)
+        sym = np.minimum(rng.geometric(0.3, n) - 1, nsym - 1).astype(np.uint16)
+        sym_t = torch.from_numpy(sym.view(np.int16)).cuda()
+    hist = np.bincount(sym, minlength=nsym).astype(np.uint32)
+    book = vsz.HuffmanBook(torch.from_numpy(hist.view(np.int32)).cuda(), nsym)
+    words, off, st = vsz.huffman_encode(sym_t, n, book)
+    assert int(st.item()) == 0
+    lo, co = oracle.huffman_book(hist)
+    ow, ooff = oracle.huffman_encode(sym, lo, co)
+    goff = off.cpu().numpy().view(np.uint64)
+    assert np.array_equal(goff, ooff)
+    assert np.array_equal(words[: int(goff[-1])].cpu().numpy().view(np.uint32), ow)
+    dec, st2 = vsz.huffman_decode(words, off, n, book)
+    assert int(st2.item()) == 0
+    assert np.array_equal(dec[:n].cpu().numpy().view(np.uint16), sym)
+
+
+def test_capacity_and_bad_symbols():
+    rng = np.random.default_rng(1)
+    n, nsym = 20000, 64
+    sym = rng.integers(0, nsym, n).astype(np.uint16)
+    hist = np.bincount(sym, minlength=nsym).astype(np.uint32)
+    book = vsz.HuffmanBook(torch.from_numpy(hist.view(np.int32)).cuda(), nsym)
+    sym_t = torch.from_numpy(sym.view(np.int16)).cuda()
+    small = torch.zeros(100, dtype=torch.int32, device="cuda")
+    words, off, st = vsz.huffman_encode(sym_t, n, book, words=small)
+    assert int(st.item()) & 2
+    lo, co = oracle.huffman_book(hist)
+    assert np.array_equal(off.cpu().numpy().view(np.uint64), oracle.huffman_encode(sym, lo, co)[1])
+    bad = sym.copy()
+    bad[123] = nsym - 1
+    hist2 = hist.copy()
+    hist2[nsym - 1] = 0
+    book2 = vsz.HuffmanBook(torch.from_numpy(hist2.view(np.int32)).cuda(), nsym)
+    _, _, st = vsz.huffman_encode(torch.from_numpy(bad.view(np.int16)).cuda(), n, book2)
+    assert int(st.item()) & 1
+
+
+def test_limits():
+    with pytest.raises(vsz.VszError) as e:
+        vsz.HuffmanBook(torch.zeros(16384, dtype=torch.int32, device="cuda"), 16384)
+    assert e.value.status == 2
+    hist = torch.tensor([3, 1], dtype=torch.int32, device="cuda")
+    book = vsz.HuffmanBook(hist, 2)
+    words, off, st = vsz.huffman_encode(torch.zeros(0, dtype=torch.int16, device="cuda"), 0, book)
+    assert int(st.item()) == 0 and int(off[0].item()) == 0
