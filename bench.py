@@ -404,8 +404,8 @@ def run_batch_compare(a, log_fn=log) -> dict:
 # ---------------------------------------------------------------- entropy stage
 def run_entropy(a, x3, xd, log_fn=log) -> dict:
     """The entropy stage (Sec. II-B) on the codes of the bench field: code
-    histogram, Huffman codebook, encode and decode throughput (CUDA events,
-    median of 10), and the rate-distortion curve: PSNR against total bits per
+    histogram, Huffman codebook, encode and decode throughput (CUDA events
+    around 20 calls in a row), and the rate-distortion curve: PSNR against total bits per
     value (Huffman stream + outliers + fixups + block offsets + chunk
     offsets + padding table), relative eb 1e-2..1e-5."""
     import numpy as np
@@ -417,18 +417,19 @@ def run_entropy(a, x3, xd, log_fn=log) -> dict:
     xh = torch.empty(n, dtype=torch.float32, device="cuda")
     out = {"curve": []}
 
-    def ev_ms(fn, k=10):
-        ts = []
+    def ev_ms(fn, k=20):
+        # k calls back to back between two events, so that the device time
+        # of a call does not include the host's launch latency
         for _ in range(2):
             fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
         for _ in range(k):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
             fn()
-            e1.record()
-            e1.synchronize()
-            ts.append(e0.elapsed_time(e1))
-        return sorted(ts)[len(ts) // 2]
+        e1.record()
+        e1.synchronize()
+        return e0.elapsed_time(e1) / k
 
     for eb in (1e-2, 1e-3, 1e-4, 1e-5):
         p = vsz.Params.make(x3.shape, a.block, eb, "rel", a.radius, a.pad)
@@ -459,11 +460,18 @@ def run_entropy(a, x3, xd, log_fn=log) -> dict:
             # counts, then packing) and writes the stream; decode reads the
             # stream and writes the codes
             enc_bytes, dec_bytes = 4 * n + 4 * nwords, 4 * nwords + 2 * n
+            vsz.trace_enable(True)
+            vsz.trace_read()
+            vsz.huffman_encode(f.codes, n, book, words=words)
+            vsz.huffman_decode(words, off, n, book, out=dec)
+            vsz.trace_enable(False)
+            kern = {r["name"]: round(r["ms"] * 1e3, 1) for r in vsz.trace_read(64)}
             row["timing"] = {
                 "histogram_us": ms_hist * 1e3, "book_us": ms_book * 1e3,
                 "encode_us": ms_enc * 1e3, "decode_us": ms_dec * 1e3,
                 "encode_GBps_fp32_in": 4 * n / (ms_enc * 1e-3) / 1e9, "decode_GBps_fp32_out": 4 * n / (ms_dec * 1e-3) / 1e9,
-                "encode_hbm_GBps": enc_bytes / (ms_enc * 1e-3) / 1e9, "decode_hbm_GBps": dec_bytes / (ms_dec * 1e-3) / 1e9}
+                "encode_hbm_GBps": enc_bytes / (ms_enc * 1e-3) / 1e9, "decode_hbm_GBps": dec_bytes / (ms_dec * 1e-3) / 1e9,
+                "kernels_us_one_call": kern}
         out["curve"].append(row)
         log_fn(f"[bench] entropy eb={eb:g}: {row}")
         del f, book, words, off, dec

@@ -385,7 +385,7 @@ VSZ_API vsz_status vsz_code_histogram(const vsz_params* p, const uint16_t* d_cod
  * unused tail bits are zero); chunk_off[c] is the first word of chunk c and
  * chunk_off[nchunks] the total, so chunks encode and decode independently.
  */
-#define VSZ_HUFF_CHUNK 4096
+#define VSZ_HUFF_CHUNK 1024
 #define VSZ_HUFF_MAX_SYMBOLS 8192   /* codebooks for R <= 4096 */
 
 /* Bytes of a device codebook for nsym symbols (0 if nsym is 0 or above
@@ -404,6 +404,10 @@ VSZ_API vsz_status vsz_huffman_book(const uint32_t* d_hist, uint32_t nsym, void*
 VSZ_API vsz_status vsz_huffman_book_read(const void* d_book, uint32_t nsym, uint8_t* h_len, uint64_t* h_code,
                                          uint32_t* h_max_len, void* stream);
 
+/* Bytes of the encoder's workspace (device, 8-byte aligned, caller-owned;
+ * not shared by calls in flight at once). */
+VSZ_API size_t vsz_huffman_encode_workspace_size(uint64_t n);
+
 /* Encode d_sym[n] (uint16 symbols < nsym, device) into d_words (uint32,
  * word_cap words) and d_chunk_off[ceil(n / VSZ_HUFF_CHUNK) + 1] (uint64).
  * *d_status (device uint32) receives bit 1 if a symbol has no codeword and
@@ -411,7 +415,7 @@ VSZ_API vsz_status vsz_huffman_book_read(const void* d_book, uint32_t nsym, uint
  * exact, so the caller can retry with chunk_off[nchunks] words). */
 VSZ_API vsz_status vsz_huffman_encode(const uint16_t* d_sym, uint64_t n, const void* d_book, uint32_t nsym,
                                       uint32_t* d_words, uint64_t word_cap, uint64_t* d_chunk_off,
-                                      uint32_t* d_status, void* stream);
+                                      uint32_t* d_status, void* d_ws, size_t ws_bytes, void* stream);
 
 /* Decode n symbols from d_words (word_cap words readable) / d_chunk_off into
  * d_sym (uint16, device).  *d_status receives bit 4 if a chunk holds no

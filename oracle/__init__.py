@@ -267,7 +267,7 @@ def decompress(p: Params, c: Compressed, return_q: bool = False):
 
 
 # ---------------------------------------------------------------- entropy stage
-HUFF_CHUNK = 4096  # symbols per word-aligned chunk of the bitstream
+HUFF_CHUNK = 1024  # symbols per word-aligned chunk of the bitstream
 
 
 def huffman_book(hist):

@@ -82,6 +82,7 @@ EXPORTED = ["vsz_status_string", "vsz_last_cuda_error", "vsz_abi_version", "vsz_
             "vsz_batch_destroy", "vsz_batch_num_classes", "vsz_batch_get_class", "vsz_batch_set_shape",
             "vsz_batch_set_concurrent", "vsz_batch_autotune", "vsz_batch_set_outputs", "vsz_batch_reconstruct",
             "vsz_huffman_book_bytes", "vsz_huffman_book", "vsz_huffman_book_read", "vsz_huffman_encode",
+            "vsz_huffman_encode_workspace_size",
             "vsz_huffman_decode",
             "vsz_tuner_features_workspace_size", "vsz_tuner_features",
             "vsz_tuner_sweep_workspace_size", "vsz_tuner_sweep", "vsz_tuner_guard_workspace_size",
@@ -141,7 +142,9 @@ def lib():
     L.vsz_huffman_book_bytes.argtypes = [ctypes.c_uint32]
     L.vsz_huffman_book.argtypes = [vp, ctypes.c_uint32, vp, sz, vp]
     L.vsz_huffman_book_read.argtypes = [vp, ctypes.c_uint32, vp, vp, P(ctypes.c_uint32), vp]
-    L.vsz_huffman_encode.argtypes = [vp, u64, vp, ctypes.c_uint32, vp, u64, vp, vp, vp]
+    L.vsz_huffman_encode_workspace_size.restype = sz
+    L.vsz_huffman_encode_workspace_size.argtypes = [u64]
+    L.vsz_huffman_encode.argtypes = [vp, u64, vp, ctypes.c_uint32, vp, u64, vp, vp, vp, sz, vp]
     L.vsz_huffman_decode.argtypes = [vp, u64, vp, u64, vp, ctypes.c_uint32, vp, vp, vp]
     L.vsz_batch_reconstruct.argtypes = [vp, vp]
     L.vsz_trace_enable.argtypes = [ctypes.c_int]
@@ -151,7 +154,7 @@ def lib():
             continue  # bound by tuner.py
         if name not in ("vsz_status_string", "vsz_last_cuda_error", "vsz_abi_version",
                         "vsz_num_elems", "vsz_num_blocks", "vsz_workspace_size", "vsz_batch_workspace_size",
-                        "vsz_huffman_book_bytes"):
+                        "vsz_huffman_book_bytes", "vsz_huffman_encode_workspace_size"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -440,7 +443,7 @@ class Batch:
 
 
 # ---------------------------------------------------------------- entropy stage
-HUFF_CHUNK = 4096            # VSZ_HUFF_CHUNK
+HUFF_CHUNK = 1024            # VSZ_HUFF_CHUNK
 HUFF_MAX_SYMBOLS = 8192      # VSZ_HUFF_MAX_SYMBOLS
 
 
@@ -478,8 +481,10 @@ def huffman_encode(sym, n: int, book: HuffmanBook, words=None, stream=None):
     if words is None:
         words = torch.empty(max(1, n // 2 + nc + 16), dtype=torch.int32, device=sym.device)  # 16 bits/symbol
     st = torch.empty(1, dtype=torch.int32, device=sym.device)
+    wsb = int(lib().vsz_huffman_encode_workspace_size(n))
+    ws = torch.empty(wsb, dtype=torch.uint8, device=sym.device)
     _check(lib().vsz_huffman_encode(_ptr(sym), n, _ptr(book.buf), book.nsym, _ptr(words), words.numel(),
-                                    _ptr(off), _ptr(st), _stream_handle(stream)), "vsz_huffman_encode")
+                                    _ptr(off), _ptr(st), _ptr(ws), wsb, _stream_handle(stream)), "vsz_huffman_encode")
     return words, off, st
 
 

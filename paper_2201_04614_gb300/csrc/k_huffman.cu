@@ -11,10 +11,11 @@
 // Stream: chunks of VSZ_HUFF_CHUNK symbols, each starting on a 32-bit word,
 // bits filling each word from its most significant bit; chunk_off[c] is the
 // first word of chunk c.  Encoding: per-chunk bit counts, a scan into word
-// offsets, then one CTA per chunk packs its codewords into shared memory and
-// stores the words.  Decoding: one thread per chunk walks its bits with a
-// 2^11-entry lookup table for short codewords and the canonical ranges for
-// longer ones.
+// offsets, then one CTA per chunk (eight symbols per thread, one 16-byte
+// load) packs its codewords into shared memory and stores the words.
+// Decoding: one thread per chunk walks its bits with a 2^11-entry lookup
+// table for short codewords and the canonical ranges for longer ones, its
+// words flowing through an eight-word register queue loaded ahead of use.
 #include <climits>
 
 #include "common.cuh"
@@ -117,54 +118,72 @@ __global__ void __launch_bounds__(1024) k_huff_book(const uint32_t* __restrict__
     for (uint32_t i = threadIdx.x; i < 66; i += blockDim.x) s_cnt[i] = 0;
     __syncthreads();
     bitonic_sort(key, np);
+    {
+        // number of used symbols: the first key that is ~0 (keys are sorted)
+        const uint32_t used = (uint32_t)__syncthreads_count(threadIdx.x < np && key[threadIdx.x] != ~0ull);
+        uint32_t extra = 0;
+        for (uint32_t i = blockDim.x + threadIdx.x; i < np; i += blockDim.x) extra += key[i] != ~0ull ? 1u : 0u;
+        if (threadIdx.x == 0) s_m = used;
+        __syncthreads();
+        if (extra) atomicAdd(&s_m, extra);
+        __syncthreads();
+    }
+    const uint32_t kk = s_m;
     if (threadIdx.x == 0) {
-        uint32_t k = 0;
-        while (k < np && key[k] != ~0ull) ++k;
-        s_m = k;
+        const uint32_t k = kk;
         s_ok = 1;
-        // two-queue merge: leaves key[0..m), merged nodes iw[0..m-1)
+        // two-queue merge: leaves key[0..k), merged nodes iw[0..k-1); the
+        // heads of both queues stay in registers
         uint32_t i = 0, j = 0, made = 0;
-        auto pick = [&](unsigned long long* w, int* leaf, uint32_t* idx) {
-            const bool take_leaf = i < k && (j >= made || (key[i] >> 16) <= iw[j]);
-            if (take_leaf) {
-                *w = key[i] >> 16;
-                *leaf = 1;
-                *idx = i++;
-            } else {
-                *w = iw[j];
-                *leaf = 0;
-                *idx = j++;
-            }
-        };
+        unsigned long long lw = k > 0 ? key[0] >> 16 : ~0ull, mw = ~0ull;
         for (uint32_t t = 0; k >= 2 && t + 1 < k; ++t) {
-            unsigned long long wa, wb;
-            int la, lb;
-            uint32_t ia, ib;
-            pick(&wa, &la, &ia);
-            pick(&wb, &lb, &ib);
-            iw[made] = wa + wb;
-            ipar[made] = -1;
-            if (la) lpar[ia] = (int32_t)made; else ipar[ia] = (int32_t)made;
-            if (lb) lpar[ib] = (int32_t)made; else ipar[ib] = (int32_t)made;
+            unsigned long long w2 = 0;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const bool take_leaf = i < k && (j >= made || lw <= mw);
+                unsigned long long w;
+                if (take_leaf) {
+                    w = lw;
+                    lpar[i] = (int32_t)made;
+                    ++i;
+                    lw = i < k ? key[i] >> 16 : ~0ull;
+                } else {
+                    w = mw;
+                    ipar[j] = (int32_t)made;
+                    ++j;
+                    mw = j < made ? iw[j] : ~0ull;
+                }
+                w2 += w;
+            }
+            iw[made] = w2;
+            if (j == made) mw = w2;  // the merged queue was empty: its head is the new node
             ++made;
         }
-        // depths: the last merged node is the root; parents come after children
-        uint32_t maxlen = 0;
-        if (made > 0) {
-            depth[made - 1] = 0;
-            for (int32_t c = (int32_t)made - 2; c >= 0; --c) {
-                const uint32_t d = depth[ipar[c]] + 1u;
-                depth[c] = (uint8_t)(d > 255u ? 255u : d);
-            }
+        if (made > 0) ipar[made - 1] = -1;
+        s_maxlen = made;  // number of merged nodes (the root is the last)
+    }
+    __syncthreads();
+    {
+        // every leaf's length is its number of ancestors (parallel over leaves)
+        const uint32_t k = kk, made = s_maxlen;
+        uint32_t ml = 0;
+        for (uint32_t c = threadIdx.x; c < k; c += blockDim.x) {
+            uint32_t d = 1;
+            if (made > 0)
+                for (int32_t v = lpar[c]; ipar[v] >= 0 && d <= 64; v = ipar[v]) ++d;
+            ml = max(ml, d);
+            depth[c] = (uint8_t)min(d, 255u);
         }
-        for (uint32_t c = 0; c < k; ++c) {
-            const uint32_t d = made > 0 ? depth[lpar[c]] + 1u : 1u;
-            if (d > 64) s_ok = 0;
-            maxlen = max(maxlen, d);
-            // reuse iw as the (length, symbol) key of leaf c
+        __syncthreads();
+        if (threadIdx.x == 0) s_maxlen = 0;
+        __syncthreads();
+        atomicMax(&s_maxlen, ml);
+        for (uint32_t c = threadIdx.x; c < k; c += blockDim.x) {
+            const uint32_t d = depth[c];
+            if (d > 64) atomicAnd(&s_ok, 0u);
+            // iw now holds the (length, symbol) key of leaf c
             iw[c] = ((unsigned long long)d << 16) | (key[c] & 0xffffu);
         }
-        s_maxlen = maxlen;
     }
     __syncthreads();
     const uint32_t mm = s_m;
@@ -228,60 +247,105 @@ __global__ void __launch_bounds__(1024) k_huff_book(const uint32_t* __restrict__
 
 // ---------------------------------------------------------------- encoding
 constexpr int kHC = VSZ_HUFF_CHUNK;
-constexpr int kEncThreads = 256;
-constexpr int kPerThread = kHC / kEncThreads;  // 16 symbols per thread
+constexpr int kEncThreads = 128;
+constexpr int kPerThread = kHC / kEncThreads;  // 8 symbols per thread: one 16-byte load
+static_assert(kPerThread == 8, "one uint4 of codes per thread");
+constexpr int kChunkWordsMax = kHC * 64 / 32;   // a chunk of 64-bit codewords at most
+constexpr uint64_t kEncMaxCtas = 4096;          // persistent CTAs of the encoder (ranges of chunks)
 
-// Words of each chunk (its bits rounded up to 32), into off[c].
+// The eight symbols of thread t of chunk c (0xffff past the end).
+__device__ __forceinline__ void load8(const uint16_t* __restrict__ sym, uint64_t n, uint64_t i0, bool vec,
+                                      uint32_t (&v)[8]) {
+    if (vec && i0 + 8 <= n) {
+        const uint4 q = *reinterpret_cast<const uint4*>(sym + i0);
+        const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[2 * k] = w[k] & 0xffffu;
+            v[2 * k + 1] = w[k] >> 16;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = i0 + k < n ? (uint32_t)sym[i0 + k] : 0xffffu;
+    }
+}
+
+// The chunks of persistent CTA j of G: a contiguous range.
+__device__ __forceinline__ void chunk_range(uint64_t nc, uint32_t G, uint32_t j, uint64_t* c0, uint64_t* c1) {
+    const uint64_t per = (nc + G - 1) / G;
+    *c0 = umin64(nc, (uint64_t)j * per);
+    *c1 = umin64(nc, *c0 + per);
+}
+
+// Pass 1: the words of each chunk (its bits rounded up to 32).  CTA j writes
+// off[c] = words of its chunks before c (offsets local to its range) and its
+// range's total into rt[j].
 __global__ void __launch_bounds__(kEncThreads) k_huff_chunk_words(const uint16_t* __restrict__ sym, uint64_t n,
                                                                    const void* bookp, uint32_t nsym, uint64_t* off,
-                                                                   uint32_t* status) {
+                                                                   unsigned long long* rt, uint32_t* status) {
     __shared__ uint8_t slen[kMaxSym];
-    __shared__ unsigned long long red[kEncThreads / 32];
+    __shared__ unsigned int red[kEncThreads / 32];
     const HuffBook bk = huff_book(bookp, nsym);
+    const uint64_t nc = (n + kHC - 1) / kHC;
+    uint64_t c0, c1;
+    chunk_range(nc, gridDim.x, blockIdx.x, &c0, &c1);
     if (bk.hdr->nsym != nsym) {  // a book built for another alphabet
+        for (uint64_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) off[c] = 0;
         if (threadIdx.x == 0) {
-            off[blockIdx.x] = 0;
+            rt[blockIdx.x] = 0;
             atomicOr(status, 8u);
         }
         return;
     }
     for (uint32_t i = threadIdx.x; i < nsym; i += blockDim.x) slen[i] = bk.len[i];
     __syncthreads();
-    const uint64_t c = blockIdx.x;
-    const uint64_t i0 = c * kHC + (uint64_t)threadIdx.x * kPerThread;
-    unsigned long long bits = 0;
+    const bool vec = (reinterpret_cast<uintptr_t>(sym) & 15) == 0;
     bool bad = false;
-    for (int k = 0; k < kPerThread; ++k) {
-        const uint64_t i = i0 + k;
-        if (i < n) {
-            const uint32_t s = sym[i];
-            const uint32_t l = s < nsym ? slen[s] : 0u;
-            bad |= l == 0;
-            bits += l;
-        }
-    }
-    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, 1u);
+    unsigned long long run = 0;  // thread 0: words of the range so far
+    uint32_t v[8];
+    if (c0 < c1) load8(sym, n, c0 * kHC + (uint64_t)threadIdx.x * kPerThread, vec, v);
+    for (uint64_t c = c0; c < c1; ++c) {
+        uint32_t nx[8];
+        if (c + 1 < c1) load8(sym, n, (c + 1) * kHC + (uint64_t)threadIdx.x * kPerThread, vec, nx);  // next chunk, in flight
+        const uint64_t i0 = c * kHC + (uint64_t)threadIdx.x * kPerThread;
+        unsigned int bits = 0;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) bits += __shfl_xor_sync(VSZ_FULL, bits, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = bits;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long t = 0;
-        for (int w = 0; w < kEncThreads / 32; ++w) t += red[w];
-        off[c] = (t + 31) / 32;
+        for (int k = 0; k < 8; ++k) {
+            if (i0 + k < n) {
+                const uint32_t l = v[k] < nsym ? slen[v[k]] : 0u;
+                bad |= l == 0;
+                bits += l;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) bits += __shfl_xor_sync(VSZ_FULL, bits, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = bits;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long t = 0;
+            for (int w = 0; w < kEncThreads / 32; ++w) t += red[w];
+            off[c] = run;
+            run += (t + 31) / 32;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = nx[k];
     }
+    if (threadIdx.x == 0) rt[blockIdx.x] = run;
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, 1u);
 }
 
-// Exclusive scan of off[0..nc) in place, total into off[nc]; capacity check.
-__global__ void __launch_bounds__(1024) k_huff_scan(uint64_t* off, uint64_t nc, uint64_t word_cap,
-                                                    uint32_t* status) {
+// Pass 2 (one CTA): exclusive scan of the G range totals in place, the
+// stream's total into rt[G] and off[nc]; capacity check.
+__global__ void __launch_bounds__(1024) k_huff_scan(unsigned long long* rt, uint32_t G, uint64_t* off, uint64_t nc,
+                                                    uint64_t word_cap, uint32_t* status) {
     __shared__ unsigned long long wsum[32];
     __shared__ unsigned long long carry;
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
-    for (uint64_t b0 = 0; b0 < nc; b0 += blockDim.x) {
-        const uint64_t i = b0 + threadIdx.x;
-        const unsigned long long v = i < nc ? off[i] : 0ull;
+    for (uint32_t b0 = 0; b0 < G; b0 += blockDim.x) {
+        const uint32_t i = b0 + threadIdx.x;
+        const unsigned long long v = i < G ? rt[i] : 0ull;
         unsigned long long x = v;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -300,68 +364,110 @@ __global__ void __launch_bounds__(1024) k_huff_scan(uint64_t* off, uint64_t nc, 
             wsum[threadIdx.x] = w;
         }
         __syncthreads();
-        const unsigned long long before = carry + (threadIdx.x >= 32 ? wsum[(threadIdx.x >> 5) - 1] : 0ull) + x - v;
-        if (i < nc) off[i] = before;
+        const unsigned long long before = carry + ((threadIdx.x >> 5) ? wsum[(threadIdx.x >> 5) - 1] : 0ull) + x - v;
+        if (i < G) rt[i] = before;
         __syncthreads();
         if (threadIdx.x == 0) carry += wsum[31];
         __syncthreads();
     }
     if (threadIdx.x == 0) {
+        rt[G] = carry;
         off[nc] = carry;
         if (carry > word_cap) atomicOr(status, 2u);
     }
 }
 
-// One CTA per chunk: codeword bits packed into shared memory, then stored.
+// Pass 3: CTA j packs its chunks (same ranges as pass 1): codeword bits into
+// shared memory, then stored; the chunk's final offset replaces its local one.
+// The next chunk's codes and offsets are loaded while the current one packs.
 __global__ void __launch_bounds__(kEncThreads) k_huff_encode(const uint16_t* __restrict__ sym, uint64_t n,
-                                                              const void* bookp, uint32_t nsym,
-                                                              const uint64_t* __restrict__ off, uint32_t* words,
-                                                              uint64_t word_cap) {
+                                                              const void* bookp, uint32_t nsym, uint64_t* off,
+                                                              const unsigned long long* __restrict__ rt,
+                                                              uint32_t* words, uint64_t word_cap) {
+    __shared__ uint32_t sw[kChunkWordsMax];
+    __shared__ unsigned int red[kEncThreads / 32];
     extern __shared__ __align__(16) unsigned char smraw[];
-    uint32_t* sw = (uint32_t*)smraw;  // [kHC * 64 / 32] words of the chunk
-    __shared__ unsigned long long red[kEncThreads / 32];
+    unsigned long long* scode = (unsigned long long*)smraw;  // [nsym]
+    uint8_t* slen = (uint8_t*)(scode + nsym);                 // [nsym]
     const HuffBook bk = huff_book(bookp, nsym);
     if (bk.hdr->nsym != nsym) return;
-    const uint64_t c = blockIdx.x;
-    const uint64_t w0 = off[c], nw = min(off[c + 1] - w0, (uint64_t)(kHC * 64 / 32));
-    for (uint32_t i = threadIdx.x; i < nw; i += blockDim.x) sw[i] = 0;
-    const uint64_t i0 = c * kHC + (uint64_t)threadIdx.x * kPerThread;
-    uint16_t s[kPerThread];
-    uint32_t mybits = 0;
-#pragma unroll
-    for (int k = 0; k < kPerThread; ++k) {
-        const uint64_t i = i0 + k;
-        s[k] = i < n ? sym[i] : (uint16_t)0xffffu;
-        mybits += (i < n && s[k] < nsym) ? bk.len[s[k]] : 0u;
+    for (uint32_t i = threadIdx.x; i < nsym; i += blockDim.x) {
+        scode[i] = bk.code[i];
+        slen[i] = bk.len[i];
     }
-    // exclusive scan of the threads' bit counts
-    unsigned long long x = mybits;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const unsigned long long y = __shfl_up_sync(VSZ_FULL, x, o);
-        if ((threadIdx.x & 31) >= (unsigned)o) x += y;
+    const uint64_t nc = (n + kHC - 1) / kHC;
+    uint64_t c0, c1;
+    chunk_range(nc, gridDim.x, blockIdx.x, &c0, &c1);
+    const unsigned long long base = rt[blockIdx.x], rend = rt[blockIdx.x + 1] - base;  // range words
+    const bool vec = (reinterpret_cast<uintptr_t>(sym) & 15) == 0;
+    uint32_t v[8];
+    uint64_t lo = 0, hi = 0;  // local offsets of the current chunk and of the next
+    if (c0 < c1) {
+        load8(sym, n, c0 * kHC + (uint64_t)threadIdx.x * kPerThread, vec, v);
+        lo = off[c0];
+        hi = c0 + 1 < c1 ? off[c0 + 1] : rend;
     }
-    if ((threadIdx.x & 31) == 31) red[threadIdx.x >> 5] = x;
-    __syncthreads();
-    unsigned long long pos = x - mybits;
-    for (uint32_t w = 0; w < (threadIdx.x >> 5); ++w) pos += red[w];
-#pragma unroll
-    for (int k = 0; k < kPerThread; ++k) {
-        if (s[k] >= nsym) continue;
-        uint32_t rem = bk.len[s[k]];
-        const unsigned long long cw = bk.code[s[k]];
-        while (rem > 0) {
-            const uint32_t wi = (uint32_t)(pos >> 5), o = (uint32_t)(pos & 31);
-            const uint32_t take = min(32u - o, rem);
-            const uint32_t bits = (uint32_t)((cw >> (rem - take)) & ((take == 32) ? 0xffffffffull : ((1ull << take) - 1)));
-            if (wi < nw) atomicOr(&sw[wi], bits << (32 - o - take));
-            pos += take;
-            rem -= take;
+    for (uint64_t c = c0; c < c1; ++c) {
+        uint32_t nx[8];
+        uint64_t hi2 = 0;
+        if (c + 1 < c1) {  // next chunk: codes and its end offset, in flight
+            load8(sym, n, (c + 1) * kHC + (uint64_t)threadIdx.x * kPerThread, vec, nx);
+            hi2 = c + 2 < c1 ? off[c + 2] : rend;
         }
+        const uint64_t w0 = base + lo, nw = min(hi - lo, (uint64_t)kChunkWordsMax);
+        for (uint32_t i = threadIdx.x; i < nw; i += blockDim.x) sw[i] = 0;
+        __syncthreads();
+        unsigned int mybits = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) mybits += v[k] < nsym ? slen[v[k]] : 0u;
+        // exclusive scan of the threads' bit counts
+        unsigned int x = mybits;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned int y = __shfl_up_sync(VSZ_FULL, x, o);
+            if ((threadIdx.x & 31) >= (unsigned)o) x += y;
+        }
+        if ((threadIdx.x & 31) == 31) red[threadIdx.x >> 5] = x;
+        __syncthreads();
+        unsigned int pos = x - mybits;
+        for (uint32_t w = 0; w < (threadIdx.x >> 5); ++w) pos += red[w];
+        // OR the low `rem` bits of cw into the chunk at bit `pos` (at most three words)
+        auto emit = [&](unsigned long long cw, uint32_t rem) {
+            while (rem > 0) {
+                const uint32_t wi = pos >> 5, o = pos & 31;
+                const uint32_t take = min(32u - o, rem);
+                const uint32_t bits =
+                    (uint32_t)((cw >> (rem - take)) & ((take == 32) ? 0xffffffffull : ((1ull << take) - 1)));
+                if (wi < nw) atomicOr(&sw[wi], bits << (32 - o - take));
+                pos += take;
+                rem -= take;
+            }
+        };
+        if (mybits <= 64) {
+            // the thread's eight codewords fit one register: a few ORs in all
+            unsigned long long acc = 0;
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (v[k] < nsym) {
+                    const uint32_t l = slen[v[k]];
+                    acc = l ? ((l == 64 ? 0ull : acc << l) | scode[v[k]]) : acc;
+                }
+            emit(acc, mybits);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (v[k] < nsym) emit(scode[v[k]], slen[v[k]]);
+        }
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < nw; i += blockDim.x)
+            if (w0 + i < word_cap) words[w0 + i] = sw[i];
+        if (threadIdx.x == 0) off[c] = w0;  // final offset (its local value was read before)
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = nx[k];
+        lo = hi;
+        hi = hi2;
     }
-    __syncthreads();
-    for (uint32_t i = threadIdx.x; i < nw; i += blockDim.x)
-        if (w0 + i < word_cap) words[w0 + i] = sw[i];
 }
 
 // ---------------------------------------------------------------- decoding
@@ -395,49 +501,53 @@ __global__ void __launch_bounds__(kDecThreads) k_huff_decode(const uint32_t* __r
     if (c >= nc) return;
     const uint64_t wb = off[c], we = umin64(off[c + 1], word_cap);
     const uint64_t i0 = c * kHC, i1 = umin64(n, i0 + kHC);
-    // 96-bit window of words [wi, wi+3)
-    uint64_t wi = 0;
-    uint32_t a = 0, b = 0, d = 0;
-    auto wd = [&](uint64_t k) -> uint32_t { return wb + k < we ? words[wb + k] : 0u; };
-    a = wd(0);
-    b = wd(1);
-    d = wd(2);
-    uint64_t pos = 0;
+    auto wd = [&](uint64_t k) -> uint32_t { return wb + k < we ? __ldg(words + wb + k) : 0u; };
+    // a 12-word register queue: the window reads q[0..5]; words are loaded
+    // four at a time, eight words ahead of use, so their latency overlaps
+    // the decoding of the words before them
+    uint32_t q[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) q[k] = wd(k);
+    uint64_t qbase = 0;  // word index of q[0]
+    uint32_t pos = 0;    // bit position inside q[0]
     const bool vec = (reinterpret_cast<uintptr_t>(out) & 15) == 0;
     uint32_t pk[4] = {0, 0, 0, 0};
-    int np = 0;
     bool bad = false;
+    uint64_t total_bits = 0;
     for (uint64_t i = i0; i < i1; ++i) {
-        const uint64_t w = pos >> 5;
-        while (wi < w) {
-            a = b;
-            b = d;
-            ++wi;
-            d = wd(wi + 2);
+        if (pos >= 128) {  // consumed q[0..3]: shift the queue, fetch four more
+#pragma unroll
+            for (int k = 0; k < 8; ++k) q[k] = q[k + 4];
+            qbase += 4;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) q[k + 8] = wd(qbase + 8 + k);
+            pos -= 128;
         }
-        const uint32_t o = (uint32_t)(pos & 31);
-        // 64 bits starting at bit o of word wi
+        const uint32_t wsel = pos >> 5, o = pos & 31;
+        const uint32_t a = wsel == 0 ? q[0] : wsel == 1 ? q[1] : wsel == 2 ? q[2] : q[3];
+        const uint32_t b = wsel == 0 ? q[1] : wsel == 1 ? q[2] : wsel == 2 ? q[3] : q[4];
+        const uint32_t d = wsel == 0 ? q[2] : wsel == 1 ? q[3] : wsel == 2 ? q[4] : q[5];
+        // 64 bits starting at bit o of word a
         const unsigned long long top = ((unsigned long long)a << 32) | b;
         const unsigned long long win = o ? (top << o) | ((unsigned long long)d >> (32 - o)) : top;
-        uint32_t e = lut[(uint32_t)(win >> (64 - kLutBits))];
+        const uint32_t e = lut[(uint32_t)(win >> (64 - kLutBits))];
         uint32_t l = e >> 16, sv = e & 0xffffu;
         if (l == 0) {
-            bool found = false;
             for (uint32_t L = kLutBits + 1; L <= maxlen; ++L) {
                 const unsigned long long cw = win >> (64 - L);
                 if (cw >= first[L] && cw - first[L] < cnt[L]) {
                     sv = sorted[base[L] + (uint32_t)(cw - first[L])];
                     l = L;
-                    found = true;
                     break;
                 }
             }
-            if (!found) {
+            if (l == 0) {
                 bad = true;
                 break;
             }
         }
         pos += l;
+        total_bits += l;
         if (vec) {
             const int slot = (int)((i - i0) & 7);
             pk[slot >> 1] |= sv << ((slot & 1) * 16);
@@ -445,21 +555,19 @@ __global__ void __launch_bounds__(kDecThreads) k_huff_decode(const uint32_t* __r
                 *reinterpret_cast<uint4*>(out + i - 7) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
                 pk[0] = pk[1] = pk[2] = pk[3] = 0;
             }
-            np = slot + 1;
         } else {
             out[i] = (uint16_t)sv;
         }
     }
     if (vec && !bad) {
-        // tail of a chunk that ends inside an 8-symbol group
+        // a last chunk that ends inside an 8-symbol group
         const uint64_t done = (i1 - i0) & ~7ull;
-        if (np < 8 && done < (i1 - i0))
-            for (uint64_t i = i0 + done; i < i1; ++i) {
-                const int slot = (int)((i - i0) & 7);
-                out[i] = (uint16_t)((pk[slot >> 1] >> ((slot & 1) * 16)) & 0xffffu);
-            }
+        for (uint64_t i = i0 + done; i < i1; ++i) {
+            const int slot = (int)((i - i0) & 7);
+            out[i] = (uint16_t)((pk[slot >> 1] >> ((slot & 1) * 16)) & 0xffffu);
+        }
     }
-    if (bad || wb > we || ((pos + 31) >> 5) > we - wb) atomicOr(status, 4u);
+    if (bad || wb > we || ((total_bits + 31) >> 5) > we - wb) atomicOr(status, 4u);
 }
 
 static size_t dec_sorted_bytes(uint32_t nsym) { return ((size_t)nsym * 2 + 15) & ~(size_t)15; }
@@ -510,11 +618,22 @@ vsz_status vsz_huffman_book_read(const void* d_book, uint32_t nsym, uint8_t* h_l
     return h.ok ? VSZ_OK : VSZ_ERR_UNSUPPORTED;
 }
 
+static uint32_t encode_ctas(uint64_t nc) {
+    const uint64_t g = umin64(nc, umin64((uint64_t)num_sms() * 8, kEncMaxCtas));
+    return (uint32_t)(g ? g : 1);
+}
+
+size_t vsz_huffman_encode_workspace_size(uint64_t n) {
+    (void)n;
+    return (kEncMaxCtas + 1) * sizeof(unsigned long long);
+}
+
 vsz_status vsz_huffman_encode(const uint16_t* d_sym, uint64_t n, const void* d_book, uint32_t nsym,
                               uint32_t* d_words, uint64_t word_cap, uint64_t* d_chunk_off, uint32_t* d_status,
-                              void* stream) {
+                              void* d_ws, size_t ws_bytes, void* stream) {
     if (nsym == 0 || nsym > kMaxSym || !d_book || !d_chunk_off || !d_status) return VSZ_ERR_INVALID_ARG;
     if (n > 0 && (!d_sym || (word_cap > 0 && !d_words))) return VSZ_ERR_INVALID_ARG;
+    if (!d_ws || !aligned(d_ws, 8) || ws_bytes < vsz_huffman_encode_workspace_size(n)) return VSZ_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const uint64_t nc = (n + kHC - 1) / kHC;
     if (nc >= (1ull << 31)) return VSZ_ERR_INVALID_ARG;
@@ -524,21 +643,23 @@ vsz_status vsz_huffman_encode(const uint16_t* d_sym, uint64_t n, const void* d_b
         e = cudaMemsetAsync(d_chunk_off, 0, sizeof(uint64_t), s);
         return e == cudaSuccess ? VSZ_OK : cuda_fail(e);
     }
+    unsigned long long* rt = (unsigned long long*)d_ws;
+    const uint32_t G = encode_ctas(nc);
     {
         TraceScope ts("huff_chunk_words", s, 0, 0, n);
-        k_huff_chunk_words<<<(unsigned)nc, kEncThreads, 0, s>>>(d_sym, n, d_book, nsym, d_chunk_off, d_status);
+        k_huff_chunk_words<<<G, kEncThreads, 0, s>>>(d_sym, n, d_book, nsym, d_chunk_off, rt, d_status);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
     }
     {
         TraceScope ts("huff_scan", s, 0, 0, n);
-        k_huff_scan<<<1, 1024, 0, s>>>(d_chunk_off, nc, word_cap, d_status);
+        k_huff_scan<<<1, 1024, 0, s>>>(rt, G, d_chunk_off, nc, word_cap, d_status);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
     }
-    const size_t smem = (size_t)kHC * 64 / 32 * 4;  // a chunk of 64-bit codewords at most
+    const size_t smem = (size_t)nsym * 9;  // codeword and length tables
     if ((e = raise_smem_attr((const void*)k_huff_encode, smem)) != cudaSuccess) return cuda_fail(e);
     {
         TraceScope ts("huff_encode", s, 0, 0, n);
-        k_huff_encode<<<(unsigned)nc, kEncThreads, smem, s>>>(d_sym, n, d_book, nsym, d_chunk_off, d_words, word_cap);
+        k_huff_encode<<<G, kEncThreads, smem, s>>>(d_sym, n, d_book, nsym, d_chunk_off, rt, d_words, word_cap);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
     }
     return VSZ_OK;

@@ -295,3 +295,30 @@ def test_reconstruct_with_and_without_workspace_agree():
     assert torch.equal(a.view(torch.int32), b.view(torch.int32))
     assert torch.equal(qa, qb)
     assert f.header()["n_out"] > 0
+
+
+@pytest.mark.parametrize("R,n,kind,offset", [(512, 1_000_003, "peaked", 0), (4, 10007, "uniform", 0),
+                                             (2, 999, "const", 0), (512, 300_001, "const", 0),
+                                             (32768, 200_000, "uniform", 0), (512, 77_777, "peaked", 1),
+                                             (7, 5000, "peaked", 3)])
+def test_code_histogram_synthetic(R, n, kind, offset):
+    """Histogram of arbitrary code arrays: counts per bin equal numpy's, codes
+    at or above 2R are not counted, any alignment of the codes."""
+    import ctypes
+    rng = np.random.default_rng(R + n)
+    if kind == "uniform":
+        c = rng.integers(0, 2 * R + 3, n)
+    elif kind == "const":
+        c = np.full(n, R)
+    else:
+        c = np.clip(np.round(rng.normal(R, 3.0, n)), 0, 2 * R + 5)
+    c = c.astype(np.uint16)
+    buf = torch.from_numpy(np.concatenate([np.zeros(offset, np.uint16), c]).view(np.int16)).cuda()
+    p = vsz.Params.make((n,), 256, 1e-3, "abs", R, "zero")
+    hist = torch.empty(2 * R, dtype=torch.int32, device="cuda")
+    L = vsz.lib()
+    rc = L.vsz_code_histogram(ctypes.byref(p.c()), ctypes.c_void_p(buf.data_ptr() + 2 * offset),
+                              ctypes.c_void_p(hist.data_ptr()), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == 0
+    want = np.bincount(c[c < 2 * R], minlength=2 * R)
+    assert np.array_equal(hist.cpu().numpy().astype(np.int64), want)
