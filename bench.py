@@ -170,18 +170,28 @@ def algorithmic_bytes(name: str, n: int, nb: int, n_out: int, n_fix: int, block_
     return 0
 
 
-def kernel_sources_digest() -> str:
+# The source files that define each profiled kernel (its body, the headers
+# it includes and its launcher): a committed ncu figure holds while these
+# files are unchanged.
+KERNEL_SOURCES = {
+    "k_lorenzo_nd": ("common.cuh", "memops.cuh", "ring.cuh", "compress_nd.cuh", "recon_nd.cuh", "k_rank3.cu"),
+    "k_recon_nd": ("common.cuh", "memops.cuh", "ring.cuh", "compress_nd.cuh", "recon_nd.cuh", "k_rank3.cu"),
+    "k_range": ("common.cuh", "memops.cuh", "stats.cuh", "k_misc.cu"),
+}
+
+
+def kernel_sources_digest(kernel: str | None = None) -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2201_04614_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    files = KERNEL_SOURCES.get(kernel.split("<")[0]) if kernel else None
+    for f in sorted(files or (f for f in os.listdir(csrc) if f.endswith((".cu", ".cuh")))):
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def profiled_traffic(kernel: str, workload: str) -> int | None:
     """dram bytes per launch from a committed ncu summary, if it was taken on
-    the current kernel sources."""
+    the current sources of that kernel."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -189,7 +199,7 @@ def profiled_traffic(kernel: str, workload: str) -> int | None:
     except Exception:
         return None
     ent = tab.get(f"{kernel}|{workload}")
-    if not ent or ent.get("src_digest") != kernel_sources_digest():
+    if not ent or ent.get("src_digest") != kernel_sources_digest(kernel):
         return None
     return int(ent["dram_bytes_per_launch"])
 
@@ -376,9 +386,27 @@ def run_batch_compare(a, log_fn=log) -> dict:
         r["batched_tuned"] = timed(lambda: bt.submit(stream))
         r["batched_tuned_recon"] = timed(lambda: bt.reconstruct(stream))
         bt.close()
-        del bt
         nout_tuned = [int(f.header()["n_out"]) for f in tuned]
         st_tuned = [int(f.header()["status"]) for f in tuned]
+        del bt
+        # the paper's own autotuner (Sec. III-D) as the baseline of the learned
+        # one: per field, the block size whose dual-quant is fastest on a 5 %
+        # sample (zero padding), then the same batch plan with autotuned shapes
+        torch.cuda.synchronize()
+        tt = time.time()
+        samp = [T.sampling_autotune(vsz.Params.make(sh, 8, eb, "rel", 512, "zero"), x, 0.05, 3)
+                for sh, x in zip(shapes, xs)]
+        samp_ms = (time.time() - tt) * 1e3
+        slots = {1: (32, 64, 128, 256), 2: (8, 16, 32, 64), 3: (8, 16, 32)}
+        samp_cls = [3 * slots[len(sh)].index(r["block"]) for sh, r in zip(shapes, samp)]
+        sampf = make_fields(samp_cls, eb)
+        bs, cls_samp, at_samp_ms = autotuned(sampf)
+        r["batched_sampling_tuned"] = timed(lambda: bs.submit(stream))
+        r["batched_sampling_tuned_recon"] = timed(lambda: bs.reconstruct(stream))
+        bs.close()
+        del bs
+        nout_samp = [int(f.header()["n_out"]) for f in sampf]
+        st_samp = [int(f.header()["status"]) for f in sampf]
         res["by_eb"][f"{eb:g}"] = {
             **{f"{k}_GBps": gb / (v * 1e-3) for k, v in r.items()},
             "ms": r,
@@ -389,12 +417,14 @@ def run_batch_compare(a, log_fn=log) -> dict:
             "guard_fallbacks": sum(1 for p in picks if p["class"] != p["predicted"]),
             "n_out_default_total": sum(nout_def), "n_out_tuned_total": sum(nout_tuned),
             "fields_n_out_tuned_le_default": sum(1 for u, v in zip(nout_tuned, nout_def) if u <= v),
-            "fields": len(xs), "status_nonzero": sum(1 for v in st_def + st_tuned if v),
+            "sampling_autotuner": {"tune_ms_once": samp_ms, "n_out_total": sum(nout_samp),
+                                   "blocks": {nm: rr["block"] for nm, rr in zip(names, samp)}},
+            "fields": len(xs), "status_nonzero": sum(1 for v in st_def + st_tuned + st_samp if v),
         }
         log_fn(f"[bench] batch eb={eb:g}: " + json.dumps({k: v for k, v in res["by_eb"][f"{eb:g}"].items()
                                                           if k.endswith("GBps") or k.startswith("n_out")
                                                           or k == "status_nonzero"}))
-        del plain, tuned
+        del plain, tuned, sampf
         torch.cuda.empty_cache()
     del xs, outs
     torch.cuda.empty_cache()

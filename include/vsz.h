@@ -504,6 +504,29 @@ VSZ_API vsz_status vsz_tuner_guard(const vsz_params* p, const float* d_x, int cl
 VSZ_API vsz_status vsz_tuner_guard_sample_dims(const vsz_params* p, uint64_t* sub_dims);
 
 /*
+ * The paper's own autotuner (Sec. III-D, Sec. V-E), kept as a baseline for
+ * the learned tuner and the batch tile autotuner: an exhaustive search that
+ * times the dual-quant (vsz_prequant_lorenzo) of every block size of the
+ * rank (1D 32..256, 2D 8..64, 3D 8..32; the padding mode is p->pad) on a
+ * sample of about sample_frac (0 < f <= 1) of the field's blocks, once to
+ * warm up and then `iters` times (1..100), and keeps the block size with the
+ * smallest mean time.  The sample is K regions spread evenly along dims[0]
+ * and aligned to every candidate block (the guard's layout, with K from the
+ * fraction); fields of at most 2^20 values, or shorter along dims[0] than
+ * one region, are sampled whole.  On the GPU
+ * the vector width the paper also tunes is fixed (16-byte lanes).
+ * Synchronous (waits for its timing events; not under stream capture).
+ *   h_best_block  the chosen block size (host)
+ *   h_ms          [4] host, mean ms per block slot (-1 for slots the rank lacks), or NULL
+ *   h_sample_elems  elements in the sample (host), or NULL
+ *   d_ws          vsz_sampling_autotune_workspace_size(p, sample_frac) bytes, 256-byte aligned
+ */
+VSZ_API size_t vsz_sampling_autotune_workspace_size(const vsz_params* p, double sample_frac);
+VSZ_API vsz_status vsz_sampling_autotune(const vsz_params* p, const float* d_x, double sample_frac, int iters,
+                                         uint32_t* h_best_block, float* h_ms, uint64_t* h_sample_elems,
+                                         void* d_ws, size_t ws_bytes, void* stream);
+
+/*
  * MLP inference: for n samples X[n][12] (fp32, device) with allowed-class
  * bit masks d_mask[n], the logits z = W3 relu(W2 relu(W1 xt + b1) + b2) + b3
  * with xt = (x - mu) / sigma (d_norm = mu[12] then sigma[12]); masked

@@ -82,7 +82,7 @@ EXPORTED = ["vsz_status_string", "vsz_last_cuda_error", "vsz_abi_version", "vsz_
             "vsz_batch_destroy", "vsz_batch_num_classes", "vsz_batch_get_class", "vsz_batch_set_shape",
             "vsz_batch_set_concurrent", "vsz_batch_autotune", "vsz_batch_set_outputs", "vsz_batch_reconstruct",
             "vsz_huffman_book_bytes", "vsz_huffman_book", "vsz_huffman_book_read", "vsz_huffman_encode",
-            "vsz_huffman_encode_workspace_size",
+            "vsz_huffman_encode_workspace_size", "vsz_sampling_autotune_workspace_size", "vsz_sampling_autotune",
             "vsz_huffman_decode",
             "vsz_tuner_features_workspace_size", "vsz_tuner_features",
             "vsz_tuner_sweep_workspace_size", "vsz_tuner_sweep", "vsz_tuner_guard_workspace_size",
@@ -150,7 +150,7 @@ def lib():
     L.vsz_trace_enable.argtypes = [ctypes.c_int]
     L.vsz_trace_read.argtypes = [P(_CTrace), ctypes.c_int]
     for name in EXPORTED:
-        if name.startswith(("vsz_tuner", "vsz_mlp")):
+        if name.startswith(("vsz_tuner", "vsz_mlp", "vsz_sampling")):
             continue  # bound by tuner.py
         if name not in ("vsz_status_string", "vsz_last_cuda_error", "vsz_abi_version",
                         "vsz_num_elems", "vsz_num_blocks", "vsz_workspace_size", "vsz_batch_workspace_size",

@@ -337,14 +337,17 @@ struct GuardGeom {
     uint64_t ny, nx;          // source extents
 };
 
-static GuardGeom guard_geom(const Geom& g, const vsz_params* p) {
+// min_slots: fewer aligned slots along dims[0] than this samples the whole
+// field; frac < 0: the guard's K (about 2 % of the field), else K regions
+// holding about frac of the elements.
+static GuardGeom region_geom(const Geom& g, const vsz_params* p, uint64_t min_slots, double frac) {
     GuardGeom G;
     std::memset(&G, 0, sizeof G);
     G.nd = g.nd;
     const uint64_t L = g.nd == 1 ? 256 : g.nd == 2 ? 64 : 32;
     G.E0 = g.nd == 1 ? 65536 : L;
     const uint64_t d0 = p->dims[0];
-    G.whole = g.n <= (1ull << 20) || d0 < 4 * G.E0;
+    G.whole = g.n <= (1ull << 20) || d0 < min_slots * G.E0;
     G.ny = g.ny;
     G.nx = g.nx;
     if (G.whole) {
@@ -358,6 +361,10 @@ static GuardGeom guard_geom(const Geom& g, const vsz_params* p) {
     G.m0 = d0 / G.E0;
     G.my = g.nd == 3 ? (g.ny <= L ? 1 : g.ny / L) : 1;
     uint64_t K = g.n / (50 * r);
+    if (frac >= 0.0) {
+        const double kd = frac * (double)g.n / (double)r;
+        K = kd < 1.0 ? 1 : (uint64_t)(kd + 0.5);
+    }
     if (K < 1) K = 1;
     if (K > G.m0) K = G.m0;
     G.K = K;
@@ -370,6 +377,8 @@ static GuardGeom guard_geom(const Geom& g, const vsz_params* p) {
     G.nsub = K * r;
     return G;
 }
+
+static GuardGeom guard_geom(const Geom& g, const vsz_params* p) { return region_geom(g, p, 4, -1.0); }
 
 // Gather of the guard's sample regions into one stacked field.
 __global__ void __launch_bounds__(256) k_gather_sample(const float* __restrict__ x, float* __restrict__ out,
@@ -721,6 +730,122 @@ vsz_status vsz_tuner_guard(const vsz_params* p, const float* d_x, int class_a, i
     }
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? VSZ_OK : cuda_fail(e);
+}
+
+// ---------------------------------------------------------------- sampling autotuner
+// The paper's autotuner (Sec. III-D, Sec. V-E): time the dual-quant of every
+// configuration on a fixed fraction of the field's blocks, several times,
+// and keep the configuration with the best mean.  The sample is K regions
+// spread evenly along dims[0] (as for the guard), aligned to every candidate
+// block, stacked into one field: about sample_frac of the elements.
+static GuardGeom sample_geom(const Geom& g, const vsz_params* p, double frac) {
+    return region_geom(g, p, 1, frac);
+}
+
+static vsz_status sampling_layout(const vsz_params* p, double frac, GuardGeom* G, CountBufs* B) {
+    if (!p || p->ndim < 1 || p->ndim > 3 || !(frac > 0.0) || frac > 1.0) return VSZ_ERR_INVALID_ARG;
+    Geom g;
+    vsz_params q = *p;
+    q.block = 8;
+    vsz_status st = make_geom(&q, &g);
+    if (st != VSZ_OK) return st;
+    *G = sample_geom(g, p, frac);
+    vsz_params sub = *p;
+    for (int k = 0; k < 3; ++k) sub.dims[k] = k < p->ndim ? G->dims[k] : 0;
+    uint64_t nb_max = 0;
+    size_t cws = 0;
+    for (int slot = 0; slot < 4; ++slot) {
+        const uint32_t b = class_block(p->ndim, slot);
+        if (!b) continue;
+        vsz_params pc = sub;
+        pc.block = b;
+        Geom gc;
+        if ((st = make_geom(&pc, &gc)) != VSZ_OK) return st;
+        nb_max = gc.nb > nb_max ? gc.nb : nb_max;
+        const size_t w = ws_layout(gc, 0, 0).total;
+        cws = w > cws ? w : cws;
+    }
+    const size_t front = G->whole ? 0 : (size_t)G->nsub * 4;
+    *B = count_bufs(G->nsub, nb_max, p->radius, cws, front);
+    return VSZ_OK;
+}
+
+size_t vsz_sampling_autotune_workspace_size(const vsz_params* p, double sample_frac) {
+    GuardGeom G;
+    CountBufs B;
+    return sampling_layout(p, sample_frac, &G, &B) == VSZ_OK ? B.total : 0;
+}
+
+vsz_status vsz_sampling_autotune(const vsz_params* p, const float* d_x, double sample_frac, int iters,
+                                 uint32_t* h_best_block, float* h_ms, uint64_t* h_sample_elems, void* d_ws,
+                                 size_t ws_bytes, void* stream) {
+    GuardGeom G;
+    CountBufs B;
+    vsz_status st = sampling_layout(p, sample_frac, &G, &B);
+    if (st != VSZ_OK) return st;
+    if (iters < 1 || iters > 100 || !h_best_block || !d_ws || ws_bytes < B.total || !aligned(d_ws, 256))
+        return VSZ_ERR_INVALID_ARG;
+    if (G.nsub > 0 && !d_x) return VSZ_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (cs != cudaStreamCaptureStatusNone) return VSZ_ERR_INVALID_ARG;
+    char* ws = (char*)d_ws;
+    const float* src = d_x;
+    if (!G.whole) {
+        float* sub = (float*)ws;
+        TraceScope ts("sample_gather", s, G.nd, 0, G.nsub);
+        const int grid = grid_for((const void*)k_gather_sample, 256, 0, 256 * 8, G.nsub);
+        k_gather_sample<<<grid, 256, 0, s>>>(d_x, sub, G);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
+        src = sub;
+    }
+    if (h_sample_elems) *h_sample_elems = G.nsub;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if ((e = cudaEventCreate(&e0)) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaEventCreate(&e1)) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(e);
+    }
+    vsz_compressed c;
+    std::memset(&c, 0, sizeof c);
+    c.codes = (uint16_t*)(ws + B.off_codes);
+    c.pad = (int32_t*)(ws + B.off_pad);
+    c.blk_off = (uint32_t*)(ws + B.off_blk);
+    c.hdr = (vsz_header*)(ws + B.off_hdr);
+    float best = INFINITY;
+    uint32_t best_b = 0;
+    for (int slot = 0; slot < 4 && st == VSZ_OK; ++slot) {
+        const uint32_t b = class_block(p->ndim, slot);
+        if (h_ms) h_ms[slot] = -1.0f;
+        if (!b) continue;
+        vsz_params pc = *p;
+        for (int k = 0; k < 3; ++k) pc.dims[k] = k < p->ndim ? G.dims[k] : 0;
+        pc.block = b;
+        // one warm-up, then `iters` timed runs of the dual-quant on the sample
+        if ((st = vsz_prequant_lorenzo(&pc, src, &c, ws + B.off_cws, B.cws_bytes, s)) != VSZ_OK) break;
+        if ((e = cudaEventRecord(e0, s)) != cudaSuccess) { st = cuda_fail(e); break; }
+        for (int it = 0; it < iters && st == VSZ_OK; ++it)
+            st = vsz_prequant_lorenzo(&pc, src, &c, ws + B.off_cws, B.cws_bytes, s);
+        if (st != VSZ_OK) break;
+        if ((e = cudaEventRecord(e1, s)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess) {
+            st = cuda_fail(e);
+            break;
+        }
+        float ms = 0.0f;
+        if ((e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) { st = cuda_fail(e); break; }
+        ms /= (float)iters;
+        if (h_ms) h_ms[slot] = ms;
+        if (ms < best) {
+            best = ms;
+            best_b = b;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st == VSZ_OK) *h_best_block = best_b;
+    return st;
 }
 
 vsz_status vsz_mlp_forward(const float* d_theta, const float* d_norm, const float* d_X, const uint32_t* d_mask, int n,

@@ -22,7 +22,7 @@ import struct
 
 import numpy as np
 
-from . import Params, _check, _ptr, _stream_handle, lib, PAD_MODES
+from . import Params, VszError, _check, _ptr, _stream_handle, lib, PAD_MODES
 
 NFEAT, NCLASS, HIDDEN = 12, 12, 64
 NPARAM = HIDDEN * NFEAT + HIDDEN + HIDDEN * HIDDEN + HIDDEN + NCLASS * HIDDEN + NCLASS
@@ -83,8 +83,12 @@ def _bind():
     L.vsz_mlp_grad_workspace_size.argtypes = [i32]
     L.vsz_mlp_grad.argtypes = [vp, vp, vp, vp, vp, vp, i32, vp, vp, vp, sz, vp]
     L.vsz_mlp_adam.argtypes = [vp, vp, vp, vp, i32, f32, f32, f32, f32, i32, vp]
+    L.vsz_sampling_autotune_workspace_size.restype = sz
+    L.vsz_sampling_autotune_workspace_size.argtypes = [P(_CParams), ctypes.c_double]
+    L.vsz_sampling_autotune.argtypes = [P(_CParams), vp, ctypes.c_double, i32, P(ctypes.c_uint32),
+                                        P(ctypes.c_float), P(ctypes.c_uint64), vp, sz, vp]
     for name in ("vsz_tuner_features", "vsz_tuner_sweep", "vsz_tuner_guard", "vsz_tuner_guard_sample_dims",
-                 "vsz_mlp_forward", "vsz_mlp_grad", "vsz_mlp_adam"):
+                 "vsz_mlp_forward", "vsz_mlp_grad", "vsz_mlp_adam", "vsz_sampling_autotune"):
         getattr(L, name).restype = ctypes.c_int
     L._tuner_bound = True
     return L
@@ -157,6 +161,27 @@ def guard_sample_dims(p: Params) -> tuple:
     d = (ctypes.c_uint64 * 3)()
     _check(L.vsz_tuner_guard_sample_dims(ctypes.byref(p.c()), d), "vsz_tuner_guard_sample_dims")
     return tuple(int(v) for v in d[: len(p.dims)])
+
+
+def sampling_autotune(p: Params, x, sample_frac: float = 0.05, iters: int = 3, stream=None) -> dict:
+    """The paper's sampling autotuner (vsz_sampling_autotune): times the
+    dual-quant of every block size of the rank on a sample of the field and
+    returns {"block", "ms" (per block size), "sample_elems"}.  Synchronous."""
+    torch = _torch()
+    L = _bind()
+    wsb = int(L.vsz_sampling_autotune_workspace_size(ctypes.byref(p.c()), float(sample_frac)))
+    if wsb == 0:
+        raise VszError(1, "vsz_sampling_autotune_workspace_size")
+    ws = torch.empty(wsb, dtype=torch.uint8, device=x.device)
+    best = ctypes.c_uint32(0)
+    ms = (ctypes.c_float * 4)()
+    ne = ctypes.c_uint64(0)
+    _check(L.vsz_sampling_autotune(ctypes.byref(p.c()), _ptr(x), float(sample_frac), int(iters), ctypes.byref(best),
+                                   ms, ctypes.byref(ne), _ptr(ws), wsb, _stream_handle(stream)),
+           "vsz_sampling_autotune")
+    blocks = {1: (32, 64, 128, 256), 2: (8, 16, 32, 64), 3: (8, 16, 32, 0)}[len(p.dims)]
+    return {"block": int(best.value), "ms": {b: float(m) for b, m in zip(blocks, ms) if b},
+            "sample_elems": int(ne.value)}
 
 
 def label_of(costs) -> int:

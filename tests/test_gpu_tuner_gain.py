@@ -51,3 +51,30 @@ def test_trained_tuner_beats_the_default_on_held_out_fields():
     mean_pick, mean_best = float(np.mean(ratios_pick)), float(np.mean(ratios_best))
     assert mean_pick < 1.0, mean_pick
     assert mean_pick <= mean_best + 0.01, (mean_pick, mean_best)
+
+
+@pytest.mark.parametrize("dims,frac", [((1800, 3600), 0.05), ((100, 500, 500), 0.05), ((3_000_000,), 0.1),
+                                       ((300, 200), 0.5)])
+def test_sampling_autotuner(dims, frac):
+    """The paper's sampling autotuner: a block size of the rank, the fastest
+    of its own timings, on a sample of about the requested fraction (whole
+    for small fields)."""
+    import numpy as np
+    import synth
+    from paper_2201_04614_gb300 import tuner as T
+    n = int(np.prod(dims))
+    if len(dims) == 1:
+        x = synth.random_walk1d(n, 3)
+    elif len(dims) == 2:
+        x = synth.fourier2d(*dims, seed=3, value_range=10.0, offset=2.0)
+    else:
+        x = np.exp(synth.grf3d(dims, 3))
+    xd = torch.from_numpy(np.ascontiguousarray(x, np.float32).reshape(-1)).cuda()
+    r = T.sampling_autotune(vsz.Params.make(dims, 8, 1e-4, "rel", 512, "zero"), xd, frac, iters=2)
+    allowed = {1: (32, 64, 128, 256), 2: (8, 16, 32, 64), 3: (8, 16, 32)}[len(dims)]
+    assert set(r["ms"]) == set(allowed) and all(v > 0 for v in r["ms"].values())
+    assert r["block"] == min(r["ms"], key=r["ms"].get)
+    if n <= (1 << 20):
+        assert r["sample_elems"] == n
+    else:
+        assert 0 < r["sample_elems"] <= n and r["sample_elems"] < 3 * frac * n + 4 * 65536
