@@ -580,6 +580,13 @@ VSZ_API int vsz_trace_read(vsz_trace_record* h_out, int max_records);
  * stream). */
 VSZ_API vsz_status vsz_read_header(const vsz_compressed* c, vsz_header* h_out, void* stream);
 
+/* The error the device recorded for this field, after the stream's work so
+ * far: VSZ_OK, VSZ_ERR_CAPACITY (lists longer than their capacities; the
+ * counts are exact) or VSZ_ERR_CORRUPT (reconstruction met a code 0 without
+ * its outlier) -- the larger of the header's status and recon_status.
+ * Synchronizes the stream; a failing copy returns VSZ_ERR_CUDA. */
+VSZ_API vsz_status vsz_sync_status(const vsz_compressed* c, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -83,6 +83,7 @@ EXPORTED = ["vsz_status_string", "vsz_last_cuda_error", "vsz_abi_version", "vsz_
             "vsz_batch_set_concurrent", "vsz_batch_autotune", "vsz_batch_set_outputs", "vsz_batch_reconstruct",
             "vsz_huffman_book_bytes", "vsz_huffman_book", "vsz_huffman_book_read", "vsz_huffman_encode",
             "vsz_huffman_encode_workspace_size", "vsz_sampling_autotune_workspace_size", "vsz_sampling_autotune",
+            "vsz_sync_status",
             "vsz_huffman_decode",
             "vsz_tuner_features_workspace_size", "vsz_tuner_features",
             "vsz_tuner_sweep_workspace_size", "vsz_tuner_sweep", "vsz_tuner_guard_workspace_size",
@@ -127,6 +128,7 @@ def lib():
     L.vsz_reconstruct_q.argtypes = [P(_CParams), P(_CCompressed), vp, vp, sz, vp]
     L.vsz_code_histogram.argtypes = [P(_CParams), vp, vp, vp]
     L.vsz_read_header.argtypes = [P(_CCompressed), P(_CHeader), vp]
+    L.vsz_sync_status.argtypes = [P(_CCompressed), vp]
     L.vsz_batch_workspace_size.restype = sz
     L.vsz_batch_workspace_size.argtypes = [P(_CFieldJob), ctypes.c_int]
     L.vsz_batch_create.argtypes = [P(_CFieldJob), ctypes.c_int, vp, sz, ctypes.c_int, P(ctypes.c_void_p)]
@@ -335,6 +337,10 @@ class Field:
         _check(lib().vsz_code_histogram(ctypes.byref(self._cp), _ptr(self.codes), _ptr(out),
                                         _stream_handle(stream)), "vsz_code_histogram")
         return out
+
+    def sync_status(self, stream=None) -> int:
+        """The device-recorded error of this field (vsz_sync_status): 0, 3 or 5."""
+        return int(lib().vsz_sync_status(ctypes.byref(self._cc), _stream_handle(stream)))
 
     def header(self, stream=None) -> dict:
         h = _CHeader()

@@ -451,4 +451,12 @@ vsz_status vsz_read_header(const vsz_compressed* c, vsz_header* h_out, void* str
     return VSZ_OK;
 }
 
+vsz_status vsz_sync_status(const vsz_compressed* c, void* stream) {
+    vsz_header h;
+    const vsz_status st = vsz_read_header(c, &h, stream);
+    if (st != VSZ_OK) return st;
+    const uint32_t v = h.status > h.recon_status ? h.status : h.recon_status;
+    return (vsz_status)v;
+}
+
 }  // extern "C"

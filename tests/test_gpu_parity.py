@@ -146,6 +146,7 @@ def test_capacity_overflow_reports_exact_counts():
     f.compress(torch.from_numpy(x.reshape(-1)).cuda())
     h = f.header()
     assert h["status"] == 3  # VSZ_ERR_CAPACITY
+    assert f.sync_status() == 3
     assert h["n_out"] == len(c.out_idx)
     assert np.array_equal(f.blk_off.cpu().numpy().view(np.uint32), c.blk_off)
     # retry with room: exact parity
@@ -166,6 +167,7 @@ def test_corrupt_outlier_list_is_reported():
     f.out_idx[0] += 1  # the first outlier no longer matches its code 0
     f.reconstruct()
     assert f.header()["recon_status"] == 5
+    assert f.sync_status() == 5
 
 
 def test_code_histogram_matches_codes():
