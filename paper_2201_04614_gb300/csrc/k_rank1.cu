@@ -102,11 +102,91 @@ __device__ __forceinline__ void compress_1d_tile(const CompressArgs& a, uint64_t
     uint32_t run_out = 0, run_fix = 0, stepmask = 0;
     int32_t gmin = INT_MAX, gmax = INT_MIN;  // q statistics of the tile (global padding)
     long long gsum = 0;
+    // The value-range pass proved every |x * inv2eb| < 2^20 and no NaN/Inf:
+    // full steps then run in exact fp32 -- rounding by the 1.5 * 2^23 bias,
+    // differences of integers below 2^21, the code as the low half of
+    // d + R + 2^23 -- and only steps whose warp holds an outlier or a fixup
+    // take the integer path below.
+    constexpr float kMagic = 12582912.0f;
+    const bool fast = a.wsh->fp32_ok != 0u && a.vec != 0 && (BP || GP || (Pg >= -(1 << 20) && Pg <= (1 << 20)));
+    const float Rf = (float)R, RB = (float)(R + 8388608), Pgf = (float)Pg;
 #pragma unroll 2
     for (int st = 0; st < C::STEPS; ++st) {
         const uint64_t s0 = start + (uint64_t)st * SPAN;
         if (s0 >= n) break;
         const uint64_t base = s0 + (uint64_t)lane * EPL;
+        if (fast && s0 + SPAN <= n) {
+            float xv[EPL], rp[EPL];
+            load_epl<EPL>(a.x + base, EPL, true, xv);
+#pragma unroll
+            for (int k = 0; k < EPL; ++k) rp[k] = __fsub_rn(__fadd_rn(__fmul_rn(xv[k], inv2eb), kMagic), kMagic);
+            const bool origin = glane == 0;  // this lane's first value opens a block
+            float Pf = GP ? 0.0f : Pgf;
+            int32_t Pb = 0;
+            if (BP) {  // block statistic over the block's G lanes (full step: whole blocks)
+                float mn = rp[0], mx = rp[0], ls = rp[0];
+#pragma unroll
+                for (int k = 1; k < EPL; ++k) {
+                    mn = fminf(mn, rp[k]);
+                    mx = fmaxf(mx, rp[k]);
+                    ls = __fadd_rn(ls, rp[k]);  // |sum| < 2^23: exact
+                }
+                int32_t smin = __float2int_rn(mn), smax = __float2int_rn(mx);
+                long long ssum = __float2int_rn(ls);
+#pragma unroll
+                for (int off = 1; off < G; off <<= 1) {
+                    smin = min(smin, __shfl_xor_sync(VSZ_FULL, smin, off));
+                    smax = max(smax, __shfl_xor_sync(VSZ_FULL, smax, off));
+                    ssum += __shfl_xor_sync(VSZ_FULL, ssum, off);
+                }
+                Pb = a.pad_mode == VSZ_PAD_BLOCK_MIN ? smin : a.pad_mode == VSZ_PAD_BLOCK_MAX ? smax
+                                                                : rounded_mean(ssum, (long long)B);
+                Pf = (float)Pb;  // |Pb| < 2^20: exact
+            }
+            const float left = __shfl_up_sync(VSZ_FULL, rp[EPL - 1], 1);
+            float d[EPL];
+            d[0] = __fsub_rn(rp[0], origin ? Pf : left);
+#pragma unroll
+            for (int k = 1; k < EPL; ++k) d[k] = __fsub_rn(rp[k], rp[k - 1]);
+            uint32_t cb[EPL];
+            bool flag = false;
+#pragma unroll
+            for (int k = 0; k < EPL; ++k) {
+                cb[k] = __float_as_uint(__fadd_rn(d[k], RB)) & 0xffffu;
+                // an outlier (the origin of a global padding mode waits for the origin pass)
+                const bool out = !(fabsf(d[k]) < Rf) && !(GP && k == 0 && origin);
+                flag |= out | !(fabsf(__fsub_rn(xv[k], __fmul_rn(rp[k], ebx2))) <= ebf);
+            }
+            if (!__any_sync(VSZ_FULL, flag)) {
+                uint16_t* cp = a.codes + base;
+                if (EPL == 4) {
+                    *reinterpret_cast<uint2*>(cp) = make_uint2(cb[0] | (cb[1] << 16), cb[2] | (cb[3 % EPL] << 16));
+                } else {
+                    *reinterpret_cast<uint4*>(cp) =
+                        make_uint4(cb[0] | (cb[1] << 16), cb[2] | (cb[3 % EPL] << 16), cb[4 % EPL] | (cb[5 % EPL] << 16),
+                                   cb[6 % EPL] | (cb[7 % EPL] << 16));
+                }
+                if (origin) {
+                    const uint64_t blk = base / B;
+                    a.blk_off[blk] = run_out;
+                    if (BP) a.pad[blk] = Pb;
+                    if (GP) a.origin[blk] = __float2int_rn(rp[0]);
+                }
+                if (GP) {
+                    float mn = rp[0], mx = rp[0], ls = rp[0];
+#pragma unroll
+                    for (int k = 1; k < EPL; ++k) {
+                        mn = fminf(mn, rp[k]);
+                        mx = fmaxf(mx, rp[k]);
+                        ls = __fadd_rn(ls, rp[k]);
+                    }
+                    gmin = min(gmin, __float2int_rn(mn));
+                    gmax = max(gmax, __float2int_rn(mx));
+                    gsum += __float2int_rn(ls);
+                }
+                continue;
+            }
+        }
         Step1<B, BP, GP> S;
         S.run(a, base, lane, inv2eb, Pg);
         uint32_t co = 0, cf = 0;
