@@ -240,6 +240,36 @@ __host__ __device__ inline void block_origin(const Geom& g, uint64_t blk, uint64
     *tile = r * g.nseg + (bx * g.b) / kSegCols;
 }
 
+// Programmatic dependent launch.  Every kernel of the one-field sequence
+// (begin, range, compression, origin pass, compaction, reconstruction,
+// fixups) starts with pdl_prologue(): it lets the next kernel in the stream
+// launch (its CTAs take the SM slots this grid frees as it drains) and then
+// waits until the previous kernel has completed and its writes are visible,
+// before touching anything.  Since a grid only launches once every CTA of its
+// predecessor has started, a waiting grid never holds resources its
+// predecessor still needs.  Outside such a launch both instructions are
+// no-ops.
+__device__ __forceinline__ void pdl_prologue() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr{};
+    attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr.val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Host launchers implemented in the per-rank translation units.
 cudaError_t launch_lorenzo_1d(const CompressArgs& a, cudaStream_t s);
 cudaError_t launch_lorenzo_2d(const CompressArgs& a, cudaStream_t s);

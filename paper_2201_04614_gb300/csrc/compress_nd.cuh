@@ -749,6 +749,7 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
 template <int ND, int B, bool BP, bool GP>
 __global__ void __launch_bounds__(NdCfg<ND, B>::THREADS, NdCfg<ND, B>::MINB_C)
 k_lorenzo_nd(const CompressArgs a) {
+    pdl_prologue();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     unsigned char* wsm = smem_raw + (size_t)(threadIdx.x >> 5) * NdCfg<ND, B>::WARP_C;

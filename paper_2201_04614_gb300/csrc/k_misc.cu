@@ -11,6 +11,7 @@
 namespace vsz {
 
 __global__ void k_begin(WsHeader* wsh, uint4* chunks, uint64_t nchunks, vsz_header* hdr, double eb, int rel) {
+    pdl_prologue();
     const uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     for (uint64_t i = i0; i < nchunks; i += (uint64_t)gridDim.x * blockDim.x) chunks[i] = make_uint4(0, 0, 0, 0);
     if (i0 == 0) {
@@ -39,6 +40,7 @@ __global__ void k_begin(WsHeader* wsh, uint4* chunks, uint64_t nchunks, vsz_head
 // Finite min/max of x; the last block resolves the relative error bound.
 __global__ void __launch_bounds__(256) k_range(const float* __restrict__ x, uint64_t n, WsHeader* wsh,
                                                vsz_header* hdr, double eb, int vec) {
+    pdl_prologue();
     __shared__ unsigned int smu[32];
     __shared__ bool last;
     unsigned int lo = 0xffffffffu, hi = 0u;
@@ -96,17 +98,25 @@ __global__ void __launch_bounds__(256) k_range(const float* __restrict__ x, uint
 __global__ void __launch_bounds__(1024) k_compact_scan(uint4* chunks, uint64_t nchunks, vsz_header* hdr,
                                                        uint32_t* blk_off, uint64_t nb, uint64_t out_cap,
                                                        uint64_t fix_cap) {
+    pdl_prologue();
     compact_scan_body(chunks, nchunks, hdr, blk_off, nb, out_cap, fix_cap);
 }
 
-__global__ void __launch_bounds__(256) k_compact(const CompressArgs a) { compact_chunk_body(blockIdx.x, a); }
+__global__ void __launch_bounds__(256) k_compact(const CompressArgs a) {
+    pdl_prologue();
+    compact_chunk_body(blockIdx.x, a);
+}
 
 // Global padding value of one field from its tiles' q statistics.
-__global__ void __launch_bounds__(1024) k_pad_reduce(const CompressArgs a) { pad_reduce_body(a); }
+__global__ void __launch_bounds__(1024) k_pad_reduce(const CompressArgs a) {
+    pdl_prologue();
+    pad_reduce_body(a);
+}
 
 // Origin pass of a global padding mode (one field): every block origin's
 // residual q - P and its code, P from the field's header.
 __global__ void __launch_bounds__(256) k_origin_fix(const CompressArgs a) {
+    pdl_prologue();
     const int32_t P = a.hdr->pad_global;
     for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < a.g.nb; b += (uint64_t)gridDim.x * blockDim.x)
         origin_fix_block(a, b, P);
@@ -120,6 +130,7 @@ __global__ void __launch_bounds__(256) k_origin_fix(const CompressArgs a) {
 // face are read whole, other rows only at each block's column 0.  1D: the
 // face of a block is its first element.
 __global__ void __launch_bounds__(256) k_edge_stats(const CompressArgs a) {
+    pdl_prologue();
     const Geom& g = a.g;
     const float inv2eb = a.hdr->inv2eb;
     const int kind = a.pad_mode - VSZ_PAD_EDGE_MIN;  // 0 min, 1 max, 2 mean
@@ -197,6 +208,7 @@ __global__ void __launch_bounds__(256) k_edge_stats(const CompressArgs a) {
 // Origin pass of an edge padding mode: every block origin's residual from
 // its block's per-axis scalars.
 __global__ void __launch_bounds__(256) k_origin_fix_edge(const CompressArgs a) {
+    pdl_prologue();
     const int nd = a.g.nd;
     for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < a.g.nb; b += (uint64_t)gridDim.x * blockDim.x)
         origin_fix_block(a, b, edge_origin_pred(a.pad + b * (uint64_t)nd, nd));
@@ -206,6 +218,7 @@ __global__ void __launch_bounds__(256) k_origin_fix_edge(const CompressArgs a) {
 __global__ void __launch_bounds__(256) k_fixups(const vsz_header* hdr, const uint32_t* __restrict__ fix_idx,
                                                 const uint32_t* __restrict__ fix_bits, uint64_t fix_cap,
                                                 float* xhat, uint64_t n) {
+    pdl_prologue();
     const uint64_t cnt = umin64(hdr->n_fix, fix_cap);
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
          i += (uint64_t)gridDim.x * blockDim.x) {
@@ -276,27 +289,23 @@ __global__ void __launch_bounds__(256) k_histogram(const uint16_t* __restrict__ 
 cudaError_t launch_begin(WsHeader* wsh, uint4* chunks, uint64_t nchunks, vsz_header* hdr, double eb, bool rel,
                          cudaStream_t s) {
     const int grid = (int)umin64(64, (nchunks + 255) / 256 + 1);
-    k_begin<<<grid, 256, 0, s>>>(wsh, chunks, nchunks, hdr, eb, rel ? 1 : 0);
-    return cudaGetLastError();
+    return launch_pdl(k_begin, grid, 256, 0, s, wsh, chunks, nchunks, hdr, eb, rel ? 1 : 0);
 }
 
 cudaError_t launch_range(const float* x, uint64_t n, WsHeader* wsh, vsz_header* hdr, double eb, bool vec,
                          cudaStream_t s) {
     const int grid = grid_for((const void*)k_range, 256, 0, 256 * 16, n);
-    k_range<<<grid, 256, 0, s>>>(x, n, wsh, hdr, eb, vec ? 1 : 0);
-    return cudaGetLastError();
+    return launch_pdl(k_range, grid, 256, 0, s, x, n, wsh, hdr, eb, vec ? 1 : 0);
 }
 
 cudaError_t launch_compact_scan(const Geom& g, uint4* chunks, vsz_header* hdr, uint32_t* blk_off,
                                 uint64_t out_cap, uint64_t fix_cap, cudaStream_t s) {
-    k_compact_scan<<<1, 1024, 0, s>>>(chunks, g.nchunks, hdr, blk_off, g.nb, out_cap, fix_cap);
-    return cudaGetLastError();
+    return launch_pdl(k_compact_scan, 1, 1024, 0, s, chunks, g.nchunks, hdr, blk_off, g.nb, out_cap, fix_cap);
 }
 
 cudaError_t launch_compact_move(const CompressArgs& a, cudaStream_t s) {
     if (a.g.nchunks == 0) return cudaSuccess;
-    k_compact<<<(unsigned)a.g.nchunks, 256, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(k_compact, (unsigned)a.g.nchunks, 256, 0, s, a);
 }
 
 cudaError_t launch_origin_fix(const CompressArgs& a, cudaStream_t s) {
@@ -304,27 +313,22 @@ cudaError_t launch_origin_fix(const CompressArgs& a, cudaStream_t s) {
         if (a.g.nb == 0) return cudaSuccess;
         const uint64_t items = a.g.nd == 1 ? (a.g.nb + 255) / 256 : (a.g.ntiles + 7) / 8;
         const int gs = grid_for((const void*)k_edge_stats, 256, 0, 1, items);
-        k_edge_stats<<<gs, 256, 0, s>>>(a);
-        cudaError_t e = cudaGetLastError();
+        cudaError_t e = launch_pdl(k_edge_stats, gs, 256, 0, s, a);
         if (e != cudaSuccess) return e;
         const int go = grid_for((const void*)k_origin_fix_edge, 256, 0, 256, a.g.nb);
-        k_origin_fix_edge<<<go, 256, 0, s>>>(a);
-        return cudaGetLastError();
+        return launch_pdl(k_origin_fix_edge, go, 256, 0, s, a);
     }
-    k_pad_reduce<<<1, 1024, 0, s>>>(a);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_pdl(k_pad_reduce, 1, 1024, 0, s, a);
     if (e != cudaSuccess || a.g.nb == 0) return e;
     const int grid = grid_for((const void*)k_origin_fix, 256, 0, 256, a.g.nb);
-    k_origin_fix<<<grid, 256, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(k_origin_fix, grid, 256, 0, s, a);
 }
 
 cudaError_t launch_fixups(const vsz_header* hdr, const uint32_t* fix_idx, const uint32_t* fix_bits,
                           uint64_t fix_cap, float* xhat, uint64_t n, cudaStream_t s) {
     const int grid = (int)umin64((uint64_t)num_sms(), (fix_cap + 255) / 256);
     if (grid == 0) return cudaSuccess;
-    k_fixups<<<grid, 256, 0, s>>>(hdr, fix_idx, fix_bits, fix_cap, xhat, n);
-    return cudaGetLastError();
+    return launch_pdl(k_fixups, grid, 256, 0, s, hdr, fix_idx, fix_bits, fix_cap, xhat, n);
 }
 
 cudaError_t launch_histogram(const uint16_t* codes, uint64_t n, uint32_t* hist, uint32_t nbins, cudaStream_t s) {

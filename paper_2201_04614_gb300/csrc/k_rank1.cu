@@ -307,6 +307,7 @@ __device__ __forceinline__ void compress_1d_tile(const CompressArgs& a, uint64_t
 // One field: tiles handed out by the field's own ticket.
 template <int B, bool BP, bool GP>
 __global__ void __launch_bounds__(256) k_lorenzo_1d(const CompressArgs a) {
+    pdl_prologue();
     const int lane = threadIdx.x & 31;
     for (;;) {
         unsigned long long tk = 0;
@@ -452,6 +453,7 @@ __device__ __forceinline__ void recon_1d_step(const ReconArgs& a, const uint64_t
 
 template <int B, bool QOUT>
 __global__ void __launch_bounds__(256) k_recon_1d(const ReconArgs a) {
+    pdl_prologue();
     using C = Cfg1<B>;
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -496,8 +498,7 @@ template <int B, bool BP, bool GP>
 static cudaError_t launch_c1_k(const CompressArgs& a, cudaStream_t s) {
     const void* k = (const void*)k_lorenzo_1d<B, BP, GP>;
     const int grid = grid_for(k, 256, 0, Cfg1<B>::WARPS, a.g.ntiles);
-    k_lorenzo_1d<B, BP, GP><<<grid, 256, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(k_lorenzo_1d<B, BP, GP>, grid, 256, 0, s, a);
 }
 
 template <int B>
@@ -560,9 +561,7 @@ static cudaError_t launch_r1(const ReconArgs& a, bool q_out, cudaStream_t s) {
     const uint64_t nsteps = (a.g.n + Cfg1<B>::SPAN - 1) / Cfg1<B>::SPAN;
     const void* k = q_out ? (const void*)k_recon_1d<B, true> : (const void*)k_recon_1d<B, false>;
     const int grid = grid_for(k, 256, 0, 8, nsteps);
-    if (q_out) k_recon_1d<B, true><<<grid, 256, 0, s>>>(a);
-    else k_recon_1d<B, false><<<grid, 256, 0, s>>>(a);
-    return cudaGetLastError();
+    return q_out ? launch_pdl(k_recon_1d<B, true>, grid, 256, 0, s, a) : launch_pdl(k_recon_1d<B, false>, grid, 256, 0, s, a);
 }
 
 cudaError_t launch_lorenzo_1d(const CompressArgs& a, cudaStream_t s) {

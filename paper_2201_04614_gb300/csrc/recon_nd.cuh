@@ -470,6 +470,7 @@ __device__ __forceinline__ void nd_recon_tile(const ReconArgs& a, const uint64_t
 template <int ND, int B, bool QOUT>
 __global__ void __launch_bounds__(NdCfg<ND, B>::THREADS, NdCfg<ND, B>::MINB_R)
 k_recon_nd(const ReconArgs a) {
+    pdl_prologue();
     using C = NdCfg<ND, B>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
@@ -522,8 +523,7 @@ cudaError_t launch_nd_compress_k(const CompressArgs& a, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM_C);
     if (e != cudaSuccess) return e;
     const int grid = grid_for(k, C::THREADS, C::SMEM_C, C::WARPS, a.g.ntiles);
-    k_lorenzo_nd<ND, B, BP, GP><<<grid, C::THREADS, C::SMEM_C, s>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(k_lorenzo_nd<ND, B, BP, GP>, grid, C::THREADS, C::SMEM_C, s, a);
 }
 
 template <int ND, int B>
@@ -575,9 +575,8 @@ cudaError_t launch_nd_recon(const ReconArgs& a, bool q_out, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM_R);
     if (e != cudaSuccess) return e;
     const int grid = grid_for(k, C::THREADS, C::SMEM_R, C::WARPS, a.g.ntiles);
-    if (q_out) k_recon_nd<ND, B, true><<<grid, C::THREADS, C::SMEM_R, s>>>(a);
-    else k_recon_nd<ND, B, false><<<grid, C::THREADS, C::SMEM_R, s>>>(a);
-    return cudaGetLastError();
+    return q_out ? launch_pdl(k_recon_nd<ND, B, true>, grid, C::THREADS, C::SMEM_R, s, a)
+                 : launch_pdl(k_recon_nd<ND, B, false>, grid, C::THREADS, C::SMEM_R, s, a);
 }
 
 template <int ND, int B>
