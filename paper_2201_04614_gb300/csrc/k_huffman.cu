@@ -13,9 +13,10 @@
 // first word of chunk c.  Encoding: per-chunk bit counts, a scan into word
 // offsets, then one CTA per chunk (eight symbols per thread, one 16-byte
 // load) packs its codewords into shared memory and stores the words.
-// Decoding: one thread per chunk walks its bits with a 2^11-entry lookup
-// table for short codewords and the canonical ranges for longer ones, its
-// words flowing through an eight-word register queue loaded ahead of use.
+// Decoding: one thread per chunk walks its bits with a 2^12-entry lookup
+// table (two codewords per entry when both fit, for alphabets up to 4096
+// symbols) and the canonical ranges for longer codewords, its words flowing
+// through a 12-word register queue loaded ahead of use.
 #include <climits>
 
 #include "common.cuh"
@@ -23,7 +24,12 @@
 
 namespace vsz {
 
-constexpr int kLutBits = 11;
+constexpr int kLutBits = 12;
+// Alphabets up to 4096 symbols (R <= 2048) use two-symbol table entries:
+// s1 | s2 << 12 | len1 << 24 | len2 << 28, len1 = 0 for a codeword longer
+// than the table, len2 = 0 when no second codeword fits in the 12 bits.
+// Larger alphabets use one-symbol entries len << 16 | s.
+constexpr uint32_t kPairMaxSym = 4096;
 constexpr uint32_t kMaxSym = VSZ_HUFF_MAX_SYMBOLS;
 
 // Device codebook layout (one caller buffer).
@@ -85,6 +91,10 @@ __device__ void bitonic_sort(unsigned long long* key, uint32_t n) {
     }
 }
 
+// Bytes of the codebook kernel's sort and tree arrays (25 per padded symbol),
+// rounded to 16; its one-symbol table follows.
+__host__ __device__ inline size_t book_smem_front(uint32_t np) { return ((size_t)np * 25 + 15) & ~(size_t)15; }
+
 __global__ void __launch_bounds__(1024) k_huff_book(const uint32_t* __restrict__ hist, uint32_t nsym, void* book) {
     extern __shared__ __align__(16) unsigned char sm[];
     const HuffLayout L = huff_layout(nsym);
@@ -105,6 +115,7 @@ __global__ void __launch_bounds__(1024) k_huff_book(const uint32_t* __restrict__
     int32_t* lpar = (int32_t*)(iw + np);                            // [np] parent of each leaf
     int32_t* ipar = lpar + np;                                      // [np] parent of each merged node
     uint8_t* depth = (uint8_t*)(ipar + np);                         // [np] depth of each merged node
+    uint32_t* slut = (uint32_t*)(sm + book_smem_front(np));         // [2^12] one-symbol table
     __shared__ uint32_t s_cnt[66];
     __shared__ unsigned long long s_first[66];
     __shared__ uint32_t s_base[66];
@@ -227,15 +238,35 @@ __global__ void __launch_bounds__(1024) k_huff_book(const uint32_t* __restrict__
         count[i] = s_cnt[i];
         base[i] = s_base[i];
     }
-    for (uint32_t i = threadIdx.x; i < (1u << kLutBits); i += blockDim.x) lut[i] = 0;
+    for (uint32_t i = threadIdx.x; i < (1u << kLutBits); i += blockDim.x) slut[i] = 0;
     __syncthreads();
     for (uint32_t r = threadIdx.x; r < mm; r += blockDim.x) {
         const uint32_t l = (uint32_t)(key[r] >> 16), s = (uint32_t)(key[r] & 0xffffu);
         if (l <= (uint32_t)kLutBits) {
             const uint32_t c0 = (uint32_t)(s_first[l] + (r - s_base[l])) << (kLutBits - l);
             const uint32_t c1 = c0 + (1u << (kLutBits - l));
-            for (uint32_t e = c0; e < c1; ++e) lut[e] = (l << 16) | s;
+            for (uint32_t e = c0; e < c1; ++e) slut[e] = (l << 16) | s;
         }
+    }
+    __syncthreads();
+    const bool pair = nsym <= kPairMaxSym;
+    for (uint32_t p = threadIdx.x; p < (1u << kLutBits); p += blockDim.x) {
+        const uint32_t e1 = slut[p];
+        if (!pair) {
+            lut[p] = e1;
+            continue;
+        }
+        const uint32_t l1 = e1 >> 16, s1 = e1 & 0xffffu;
+        uint32_t l2 = 0, s2 = 0;
+        if (l1 > 0 && l1 < (uint32_t)kLutBits) {
+            // the codeword after s1 within the same 12 bits (bits past them read as 0)
+            const uint32_t e2 = slut[(p << l1) & ((1u << kLutBits) - 1)];
+            if ((e2 >> 16) > 0 && (e2 >> 16) <= (uint32_t)kLutBits - l1) {
+                l2 = e2 >> 16;
+                s2 = e2 & 0xffffu;
+            }
+        }
+        lut[p] = l1 ? (s1 | (s2 << 12) | (l1 << 24) | (l2 << 28)) : 0u;
     }
     if (threadIdx.x == 0) {
         hdr->nsym = nsym;
@@ -514,7 +545,21 @@ __global__ void __launch_bounds__(kDecThreads) k_huff_decode(const uint32_t* __r
     uint32_t pk[4] = {0, 0, 0, 0};
     bool bad = false;
     uint64_t total_bits = 0;
-    for (uint64_t i = i0; i < i1; ++i) {
+    const bool pair = nsym <= kPairMaxSym;
+    // place symbol i (16-byte stores of eight symbols when aligned)
+    auto put = [&](uint64_t i, uint32_t sv) {
+        if (vec) {
+            const int slot = (int)((i - i0) & 7);
+            pk[slot >> 1] |= sv << ((slot & 1) * 16);
+            if (slot == 7) {
+                *reinterpret_cast<uint4*>(out + i - 7) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                pk[0] = pk[1] = pk[2] = pk[3] = 0;
+            }
+        } else {
+            out[i] = (uint16_t)sv;
+        }
+    };
+    for (uint64_t i = i0; i < i1;) {
         if (pos >= 128) {  // consumed q[0..3]: shift the queue, fetch four more
 #pragma unroll
             for (int k = 0; k < 8; ++k) q[k] = q[k + 4];
@@ -531,7 +576,16 @@ __global__ void __launch_bounds__(kDecThreads) k_huff_decode(const uint32_t* __r
         const unsigned long long top = ((unsigned long long)a << 32) | b;
         const unsigned long long win = o ? (top << o) | ((unsigned long long)d >> (32 - o)) : top;
         const uint32_t e = lut[(uint32_t)(win >> (64 - kLutBits))];
-        uint32_t l = e >> 16, sv = e & 0xffffu;
+        uint32_t l, sv, l2 = 0, sv2 = 0;
+        if (pair) {
+            l = (e >> 24) & 15u;
+            sv = e & 0xfffu;
+            l2 = e >> 28;
+            sv2 = (e >> 12) & 0xfffu;
+        } else {
+            l = e >> 16;
+            sv = e & 0xffffu;
+        }
         if (l == 0) {
             for (uint32_t L = kLutBits + 1; L <= maxlen; ++L) {
                 const unsigned long long cw = win >> (64 - L);
@@ -546,18 +600,12 @@ __global__ void __launch_bounds__(kDecThreads) k_huff_decode(const uint32_t* __r
                 break;
             }
         }
-        pos += l;
-        total_bits += l;
-        if (vec) {
-            const int slot = (int)((i - i0) & 7);
-            pk[slot >> 1] |= sv << ((slot & 1) * 16);
-            if (slot == 7) {
-                *reinterpret_cast<uint4*>(out + i - 7) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                pk[0] = pk[1] = pk[2] = pk[3] = 0;
-            }
-        } else {
-            out[i] = (uint16_t)sv;
-        }
+        if (i + 1 >= i1) l2 = 0;  // the chunk's last symbol: what follows is padding
+        put(i, sv);
+        if (l2) put(i + 1, sv2);
+        pos += l + l2;
+        total_bits += l + l2;
+        i += l2 ? 2 : 1;
     }
     if (vec && !bad) {
         // a last chunk that ends inside an 8-symbol group
@@ -589,7 +637,7 @@ vsz_status vsz_huffman_book(const uint32_t* d_hist, uint32_t nsym, void* d_book,
     if (!d_hist || !d_book || !aligned(d_book, 16) || book_bytes < huff_layout(nsym).total) return VSZ_ERR_INVALID_ARG;
     uint32_t np = 2;
     while (np < nsym) np <<= 1;
-    const size_t smem = (size_t)np * (8 + 8 + 4 + 4 + 1);
+    const size_t smem = book_smem_front(np) + ((size_t)1 << kLutBits) * 4;
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = raise_smem_attr((const void*)k_huff_book, smem);
     if (e != cudaSuccess) return cuda_fail(e);
