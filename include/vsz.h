@@ -236,11 +236,10 @@ VSZ_API size_t vsz_batch_workspace_size(const vsz_field_job* jobs, int njobs);
  * the batch then takes a fixed number of launches whatever the number of
  * fields: one initialisation, one value-range pass over every relative-eb
  * field, one global-statistics pass over every global-padding field, one
+ * face-statistics pass over every edge-padding field, one
  * persistent compression kernel per class whose warps draw tiles of all the
  * class's fields from one queue, and two compaction kernels.  Results are
- * identical to vsz_compress on each field.  Edge padding modes are not
- * batched (VSZ_ERR_UNSUPPORTED; compress such fields with vsz_compress).  The
- * plan keeps the jobs' pointers;
+ * identical to vsz_compress on each field.  The plan keeps the jobs' pointers;
  * their buffers must outlive it.  The plan allocates its descriptor tables on
  * the device (freed by vsz_batch_destroy); d_ws (caller-owned, 256-byte
  * aligned) holds every field's compression workspace.  use_graph != 0
@@ -269,7 +268,7 @@ VSZ_API vsz_status vsz_batch_destroy(vsz_batch b);
 typedef struct {
     int32_t  ndim;
     uint32_t block;
-    int32_t  pad_kind;     /* 0 zero padding, 1 per-block padding, 2 global padding */
+    int32_t  pad_kind;     /* 0 zero padding, 1 per-block padding, 2 global or edge padding (origins deferred) */
     int32_t  nfields;      /* fields in the class */
     uint64_t tiles;        /* tiles of all of them */
     int32_t  warps;        /* warps per CTA of the class kernel (0 = default: 4, or 8 in 1D) */

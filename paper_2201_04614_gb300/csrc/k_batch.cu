@@ -9,8 +9,9 @@
 //                         1M elements; the last item of a field resolves eb;
 //   k_lorenzo_*_batch     per class, one persistent kernel drawing tiles of
 //                         all the class's fields from one ticket;
-//   k_batch_origin_fix    block origins of every global-padding field, once
-//                         the field's padding value is known;
+//   k_batch_edge_stats    face statistics of every edge-padding field;
+//   k_batch_origin_fix    block origins of every global- or edge-padding
+//                         field, once its padding values are known;
 //   k_batch_compact_scan  one CTA per field: chunk offsets and totals;
 //   k_batch_compact_move  one CTA per chunk of any field: final placement.
 // Reconstruction of the batch (once output buffers are set) is a second
@@ -43,6 +44,7 @@ struct BatchField {
     double eb;          // user error bound
     int32_t rel;        // value-range relative bound
     int32_t gpad;       // a global padding mode (its block origins wait for the origin pass)
+    int32_t epad;       // an edge padding mode (the same, with per-block face scalars)
 };
 
 // Index of the last entry of prefix[0..n) that is <= v (prefix[0] == 0).
@@ -152,14 +154,28 @@ __global__ void __launch_bounds__(1024) k_batch_pad_reduce(const BatchField* __r
     if (F[blockIdx.x].gpad) pad_reduce_body(F[blockIdx.x].a);
 }
 
-// Origin pass of every global-padding field: items are blocks.
+// Face statistics of every edge-padding field: items are warp units (tiles,
+// or 32 blocks in 1D), one warp each.
+__global__ void __launch_bounds__(256) k_batch_edge_stats(const BatchField* __restrict__ F, int nf,
+                                                          const uint64_t* __restrict__ prefix, uint64_t nitems) {
+    const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    for (uint64_t item = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); item < nitems;
+         item += nwarps) {
+        const int f = find_field(prefix, nf, item);
+        edge_stats_unit(F[f].a, item - prefix[f], threadIdx.x & 31);
+    }
+}
+
+// Origin pass of every global- or edge-padding field: items are blocks.
 __global__ void __launch_bounds__(256) k_batch_origin_fix(const BatchField* __restrict__ F, int nf,
                                                           const uint64_t* __restrict__ prefix, uint64_t nitems) {
     for (uint64_t item = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; item < nitems;
          item += (uint64_t)gridDim.x * blockDim.x) {
         const int f = find_field(prefix, nf, item);
         const CompressArgs& a = F[f].a;
-        origin_fix_block(a, item - prefix[f], a.hdr->pad_global);
+        const uint64_t blk = item - prefix[f];
+        const int nd = a.g.nd;
+        origin_fix_block(a, blk, F[f].epad ? edge_origin_pred(a.pad + blk * (uint64_t)nd, nd) : a.hdr->pad_global);
     }
 }
 
@@ -229,7 +245,9 @@ struct vsz_batch_st {
     std::vector<BatchClass> classes;
     BatchField* d_fields = nullptr;
     uint64_t* d_range_prefix = nullptr;
-    uint64_t* d_ob_prefix = nullptr;    // blocks of the global-padding fields
+    uint64_t* d_ob_prefix = nullptr;    // blocks of the global- and edge-padding fields
+    uint64_t* d_edge_prefix = nullptr;  // face-statistics units of the edge-padding fields
+    uint64_t edge_items = 0;
     uint64_t* d_chunk_prefix = nullptr;
     uint64_t range_items = 0, origin_items = 0, chunks = 0;
     unsigned long long* tickets = nullptr;  // in the caller's workspace
@@ -283,6 +301,7 @@ static void free_batch(vsz_batch_st* b) {
     if (b->d_fields) cudaFree(b->d_fields);
     if (b->d_range_prefix) cudaFree(b->d_range_prefix);
     if (b->d_ob_prefix) cudaFree(b->d_ob_prefix);
+    if (b->d_edge_prefix) cudaFree(b->d_edge_prefix);
     if (b->d_chunk_prefix) cudaFree(b->d_chunk_prefix);
     delete b;
 }
@@ -410,6 +429,12 @@ static vsz_status launch_sequence(vsz_batch_st* b, cudaStream_t s, const ClassTi
         const vsz_status st = run_classes(b, 0, s, tm);
         if (st != VSZ_OK) return st;
     }
+    if (b->edge_items) {
+        TraceScope ts("batch_edge_stats", s);
+        const int grid = grid_for((const void*)k_batch_edge_stats, 256, 0, 8, b->edge_items);
+        k_batch_edge_stats<<<grid, 256, 0, s>>>(b->d_fields, b->n, b->d_edge_prefix, b->edge_items);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
+    }
     if (b->origin_items) {
         TraceScope ts("batch_origin_fix", s);
         k_batch_pad_reduce<<<b->n, 1024, 0, s>>>(b->d_fields);
@@ -450,7 +475,6 @@ vsz_status vsz_batch_create(const vsz_field_job* jobs, int njobs, void* d_ws, si
         if (st != VSZ_OK) return st;
         if ((st = check_compressed(g, &jobs[i].params, &jobs[i].out)) != VSZ_OK) return st;
         if (g.n > 0 && !jobs[i].d_x) return VSZ_ERR_INVALID_ARG;
-        if (is_edge_pad(jobs[i].params.pad)) return VSZ_ERR_UNSUPPORTED;  // one-field path only
     }
     const size_t need = batch_layout(jobs, njobs, &offs, &geoms);
     if (!need || ws_bytes < need) return VSZ_ERR_INVALID_ARG;
@@ -461,7 +485,7 @@ vsz_status vsz_batch_create(const vsz_field_job* jobs, int njobs, void* d_ws, si
     b->use_graph = use_graph != 0;
     char* ws = (char*)d_ws;
     b->tickets = (unsigned long long*)ws;
-    std::vector<uint64_t> rp(1, 0), qp(1, 0), cp(1, 0);
+    std::vector<uint64_t> rp(1, 0), qp(1, 0), cp(1, 0), ep(1, 0);
     std::map<std::tuple<int, uint32_t, int>, int> cls;
     for (int i = 0; i < njobs; ++i) {
         const vsz_field_job& j = jobs[i];
@@ -481,7 +505,7 @@ vsz_status vsz_batch_create(const vsz_field_job* jobs, int njobs, void* d_ws, si
         a.chunks = (uint4*)(fw + L.chunks);
         a.stage_out = (uint2*)(fw + L.stage_out);
         a.stage_fix = (uint2*)(fw + L.stage_fix);
-        if (is_global_pad(j.params.pad)) {
+        if (defers_origin(j.params.pad)) {
             a.tstats = (TileStats*)(fw + L.tstats);
             a.origin = (int32_t*)(fw + L.origin);
             a.oflag = (uint8_t*)(fw + L.oflag);
@@ -498,14 +522,15 @@ vsz_status vsz_batch_create(const vsz_field_job* jobs, int njobs, void* d_ws, si
         a.vec = (aligned(j.d_x, 16) && aligned(j.out.codes, 16) && (g.nd == 1 || g.nx % 4 == 0)) ? 1 : 0;
         bf.eb = j.params.eb;
         bf.rel = j.params.eb_mode == VSZ_EB_REL;
-        bf.gpad = j.params.pad == VSZ_PAD_GLOBAL_MIN || j.params.pad == VSZ_PAD_GLOBAL_MAX ||
-                  j.params.pad == VSZ_PAD_GLOBAL_AVG;
+        bf.gpad = is_global_pad(j.params.pad) ? 1 : 0;
+        bf.epad = is_edge_pad(j.params.pad) ? 1 : 0;
         b->fields.push_back(bf);
         const uint64_t items = (g.n + kItemElems - 1) / kItemElems;
         rp.push_back(rp.back() + (bf.rel ? (items ? items : 1) : 0));
-        qp.push_back(qp.back() + (bf.gpad ? g.nb : 0));
+        qp.push_back(qp.back() + (bf.gpad || bf.epad ? g.nb : 0));
+        ep.push_back(ep.back() + (bf.epad ? edge_units(g) : 0));
         cp.push_back(cp.back() + g.nchunks);
-        const int pk = is_block_pad(j.params.pad) ? 1 : bf.gpad ? 2 : 0;
+        const int pk = is_block_pad(j.params.pad) ? 1 : (bf.gpad || bf.epad) ? 2 : 0;
         const auto key = std::make_tuple(g.nd, g.b, pk);
         auto it = cls.find(key);
         if (it == cls.end()) {
@@ -521,10 +546,12 @@ vsz_status vsz_batch_create(const vsz_field_job* jobs, int njobs, void* d_ws, si
     if ((int)b->classes.size() > kMaxClasses) { free_batch(b); return VSZ_ERR_UNSUPPORTED; }
     b->range_items = rp.back();
     b->origin_items = qp.back();
+    b->edge_items = ep.back();
     b->chunks = cp.back();
     cudaError_t e = upload(&b->d_fields, b->fields);
     if (e == cudaSuccess) e = upload(&b->d_range_prefix, rp);
     if (e == cudaSuccess) e = upload(&b->d_ob_prefix, qp);
+    if (e == cudaSuccess) e = upload(&b->d_edge_prefix, ep);
     if (e == cudaSuccess) e = upload(&b->d_chunk_prefix, cp);
     for (BatchClass& c : b->classes) {
         if (e != cudaSuccess) break;

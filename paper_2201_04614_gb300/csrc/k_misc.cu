@@ -122,87 +122,12 @@ __global__ void __launch_bounds__(256) k_origin_fix(const CompressArgs a) {
         origin_fix_block(a, b, P);
 }
 
-// Edge granularity (Sec. IV-B-3): per block and axis k, the min / max /
-// rounded mean of q over the block's face at local coordinate 0 along k,
-// into a.pad[blk * nd + k] (k = 0 the slowest axis).  2D/3D: one warp per
-// tile (a 128-column segment of a row of blocks, as the compression walk):
-// lane l holds columns 4l..4l+3, b/4 lanes share a block; rows on a y or z
-// face are read whole, other rows only at each block's column 0.  1D: the
-// face of a block is its first element.
 __global__ void __launch_bounds__(256) k_edge_stats(const CompressArgs a) {
     pdl_prologue();
-    const Geom& g = a.g;
-    const float inv2eb = a.hdr->inv2eb;
-    const int kind = a.pad_mode - VSZ_PAD_EDGE_MIN;  // 0 min, 1 max, 2 mean
-    if (g.nd == 1) {
-        for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < g.nb;
-             b += (uint64_t)gridDim.x * blockDim.x)
-            a.pad[b] = prequant(a.x[b * g.b], inv2eb);
-        return;
-    }
-    const int nd = g.nd;
-    const int lane = threadIdx.x & 31;
-    const uint64_t B = g.b;
-    const int G = (int)(B / 4);
-    const int glane = lane & (G - 1);
-    const uint64_t grp = (uint64_t)(lane / G);
-    const uint64_t nx = g.nx, plane = g.ny * g.nx;
     const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
-    for (uint64_t t = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < g.ntiles; t += nwarps) {
-        const uint64_t sg = t % g.nseg, rb = t / g.nseg;
-        const uint64_t by = rb % g.nby, bz = rb / g.nby;
-        const uint64_t x0 = sg * kSegCols + (uint64_t)lane * 4;
-        const uint64_t bx = (sg * kSegCols) / B + grp;
-        const int valid = x0 < nx ? (int)umin64(4, nx - x0) : 0;
-        const int ylen = (int)umin64(B, g.ny - by * B);
-        const int zlen = nd == 3 ? (int)umin64(B, g.nz - bz * B) : 1;
-        const uint64_t base = (nd == 3 ? bz * B * plane : 0) + by * B * nx + x0;
-        // faces: 0 = x (axis nd-1), 1 = y (axis nd-2), 2 = z (axis 0 of 3D)
-        long long sm[3] = {0, 0, 0};
-        int mn[3] = {INT_MAX, INT_MAX, INT_MAX}, mx[3] = {INT_MIN, INT_MIN, INT_MIN};
-        auto take = [&](int f, int32_t v) {
-            sm[f] += v;
-            mn[f] = min(mn[f], v);
-            mx[f] = max(mx[f], v);
-        };
-        for (int lz = 0; lz < zlen; ++lz) {
-            for (int ly = 0; ly < ylen; ++ly) {
-                const bool face_row = ly == 0 || (nd == 3 && lz == 0);
-                const float* row = a.x + base + (uint64_t)lz * plane + (uint64_t)ly * nx;
-                int32_t q[4];
-                int cnt = 0;
-                if (face_row) {
-                    for (int k = 0; k < valid; ++k) q[k] = prequant(row[k], inv2eb);
-                    cnt = valid;
-                } else if (glane == 0 && valid > 0) {
-                    q[0] = prequant(row[0], inv2eb);
-                    cnt = 1;
-                }
-                if (glane == 0 && cnt > 0) take(0, q[0]);
-                if (ly == 0)
-                    for (int k = 0; k < cnt; ++k) take(1, q[k]);
-                if (nd == 3 && lz == 0)
-                    for (int k = 0; k < cnt; ++k) take(2, q[k]);
-            }
-        }
-        for (int off = 1; off < G; off <<= 1) {  // the y and z faces span the block's lanes
-#pragma unroll
-            for (int f = 1; f < 3; ++f) {
-                sm[f] += __shfl_xor_sync(VSZ_FULL, sm[f], off);
-                mn[f] = min(mn[f], __shfl_xor_sync(VSZ_FULL, mn[f], off));
-                mx[f] = max(mx[f], __shfl_xor_sync(VSZ_FULL, mx[f], off));
-            }
-        }
-        if (glane == 0 && bx < g.nbx) {
-            const uint64_t blk = (bz * g.nby + by) * g.nbx + bx;
-            const long long xw = (long long)umin64(B, nx - bx * B);
-            const long long cnt[3] = {(long long)ylen * zlen, xw * zlen, xw * ylen};
-            for (int f = 0; f < nd; ++f) {
-                const int32_t v = kind == 0 ? mn[f] : kind == 1 ? mx[f] : rounded_mean(sm[f], cnt[f]);
-                a.pad[blk * (uint64_t)nd + (uint64_t)(nd - 1 - f)] = v;
-            }
-        }
-    }
+    const uint64_t units = edge_units(a.g);
+    for (uint64_t t = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < units; t += nwarps)
+        edge_stats_unit(a, t, threadIdx.x & 31);
 }
 
 // Origin pass of an edge padding mode: every block origin's residual from
@@ -311,7 +236,7 @@ cudaError_t launch_compact_move(const CompressArgs& a, cudaStream_t s) {
 cudaError_t launch_origin_fix(const CompressArgs& a, cudaStream_t s) {
     if (is_edge_pad(a.pad_mode)) {
         if (a.g.nb == 0) return cudaSuccess;
-        const uint64_t items = a.g.nd == 1 ? (a.g.nb + 255) / 256 : (a.g.ntiles + 7) / 8;
+        const uint64_t items = (edge_units(a.g) + 7) / 8;
         const int gs = grid_for((const void*)k_edge_stats, 256, 0, 1, items);
         cudaError_t e = launch_pdl(k_edge_stats, gs, 256, 0, s, a);
         if (e != cudaSuccess) return e;

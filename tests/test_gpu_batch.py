@@ -32,7 +32,8 @@ MIX = [((300, 519), 16, 1e-4, "rel", 512, "zero"), ((160, 384), 8, 1e-5, "rel", 
        ((10007,), 256, 1e-5, "rel", 512, "zero"), ((5000,), 32, 1e-4, "rel", 8, "block_max"),
        ((64, 64), 16, 1e-4, "rel", 512, "zero"), ((0,), 16, 1e-3, "rel", 512, "zero"),
        ((3, 1, 5), 4, 1e-2, "rel", 512, "global_min"), ((1, 700), 32, 1e-4, "abs", 2, "block_avg"),
-       ((12, 20, 68), 16, 1e-5, "rel", 16, "block_min")]
+       ((12, 20, 68), 16, 1e-5, "rel", 16, "block_min"), ((150, 260), 16, 1e-4, "rel", 512, "edge_avg"),
+       ((13, 21, 140), 8, 1e-4, "rel", 64, "edge_min"), ((7000,), 64, 1e-4, "rel", 512, "edge_max")]
 
 
 def _host(f):
@@ -221,12 +222,3 @@ def test_launch_shapes_and_autotune_change_no_result():
     with pytest.raises(vsz.VszError):
         b.set_shape(len(cls), 4, 0)
     b.close()
-
-
-def test_batch_rejects_edge_padding():
-    """Edge padding runs on the one-field path only."""
-    x = torch.from_numpy(np.ascontiguousarray(field_for((64, 64), 5).reshape(-1), np.float32)).cuda()
-    f = vsz.Field(vsz.Params.make((64, 64), 16, 1e-4, "rel", 512, "edge_avg"))
-    with pytest.raises(vsz.VszError) as e:
-        vsz.Batch([f], [x])
-    assert e.value.status == 2
