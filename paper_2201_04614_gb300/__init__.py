@@ -431,10 +431,69 @@ class Batch:
     def set_concurrent(self, on: bool):
         _check(lib().vsz_batch_set_concurrent(self._h, 1 if on else 0), "vsz_batch_set_concurrent")
 
-    def autotune(self, stream=None, reps: int = 3) -> list:
-        """Tile autotuner (vsz_batch_autotune): synchronous; returns classes()."""
+    def autotune(self, stream=None, reps: int = 3, cache: str | None = None) -> list:
+        """Tile autotuner (vsz_batch_autotune): synchronous; returns classes().
+        With `cache` (a JSON file), shapes found earlier on this GPU model for
+        the same classes are applied instead of searching again, and a new
+        search is recorded there."""
+        if cache and self.load_shapes(cache):
+            return self.classes()
         _check(lib().vsz_batch_autotune(self._h, _stream_handle(stream), reps), "vsz_batch_autotune")
+        if cache:
+            self.save_shapes(cache)
         return self.classes()
+
+    @staticmethod
+    def _device_key() -> str:
+        import torch
+        pr = torch.cuda.get_device_properties(torch.cuda.current_device())
+        return f"{pr.name}|{pr.multi_processor_count} SMs"
+
+    @staticmethod
+    def _class_key(c: dict) -> str:
+        return f"{c['kind']}:{c['ndim']}:{c['block']}:{c['pad_kind']}"
+
+    def save_shapes(self, path: str) -> None:
+        """Record this plan's launch shapes and concurrent modes under the GPU
+        model (name and SM count) and each class (kind, rank, block, padding
+        kind) in the JSON file `path` (merged with what it holds)."""
+        import json
+        try:
+            with open(path) as fh:
+                tab = json.load(fh)
+        except (OSError, ValueError):
+            tab = {}
+        dev = tab.setdefault(self._device_key(), {"classes": {}, "concurrent": {}})
+        for c in self.classes():
+            dev["classes"][self._class_key(c)] = {"warps": c["warps"], "ctas_per_sm": c["ctas_per_sm"]}
+            dev["concurrent"][str(c["kind"])] = bool(c["concurrent"])
+        tmp = path + ".tmp"
+        with open(tmp, "w") as fh:
+            json.dump(tab, fh, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+
+    def load_shapes(self, path: str) -> bool:
+        """Apply recorded shapes (save_shapes) when the file holds every class
+        of this plan for this GPU model; False (nothing applied) otherwise."""
+        import json
+        try:
+            with open(path) as fh:
+                dev = json.load(fh).get(self._device_key())
+        except (OSError, ValueError):
+            return False
+        if not dev:
+            return False
+        cls = self.classes()
+        keys = [self._class_key(c) for c in cls]
+        if any(k not in dev.get("classes", {}) for k in keys):
+            return False
+        for i, k in enumerate(keys):
+            sh = dev["classes"][k]
+            self.set_shape(i, int(sh["warps"]), int(sh["ctas_per_sm"]))
+        conc = set(bool(v) for v in dev.get("concurrent", {}).values())
+        if len(conc) == 1:  # one setter serves both sequences: apply only an agreed mode
+            self.set_concurrent(conc.pop())
+        return True
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

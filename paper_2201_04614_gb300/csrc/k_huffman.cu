@@ -278,26 +278,30 @@ __global__ void __launch_bounds__(1024) k_huff_book(const uint32_t* __restrict__
 
 // ---------------------------------------------------------------- encoding
 constexpr int kHC = VSZ_HUFF_CHUNK;
-constexpr int kEncThreads = 128;
-constexpr int kPerThread = kHC / kEncThreads;  // 8 symbols per thread: one 16-byte load
-static_assert(kPerThread == 8, "one uint4 of codes per thread");
+constexpr int kEncThreads = 128;                // four warps; one warp codes one chunk at a time
+constexpr int kLaneSyms = kHC / 32;             // 32 symbols per lane: four 16-byte loads
+static_assert(kLaneSyms == 32, "a chunk is 32 lanes of 32 symbols");
 constexpr int kChunkWordsMax = kHC * 64 / 32;   // a chunk of 64-bit codewords at most
 constexpr uint64_t kEncMaxCtas = 4096;          // persistent CTAs of the encoder (ranges of chunks)
 
-// The eight symbols of thread t of chunk c (0xffff past the end).
-__device__ __forceinline__ void load8(const uint16_t* __restrict__ sym, uint64_t n, uint64_t i0, bool vec,
-                                      uint32_t (&v)[8]) {
-    if (vec && i0 + 8 <= n) {
-        const uint4 q = *reinterpret_cast<const uint4*>(sym + i0);
-        const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+// The 32 symbols of lane `lane` of chunk c (0xffff past the end).
+__device__ __forceinline__ void load32(const uint16_t* __restrict__ sym, uint64_t n, uint64_t c, int lane, bool vec,
+                                       uint32_t (&v)[kLaneSyms]) {
+    const uint64_t i0 = c * kHC + (uint64_t)lane * kLaneSyms;
+    if (vec && i0 + kLaneSyms <= n) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            v[2 * k] = w[k] & 0xffffu;
-            v[2 * k + 1] = w[k] >> 16;
+        for (int h = 0; h < 4; ++h) {
+            const uint4 q = *reinterpret_cast<const uint4*>(sym + i0 + 8 * h);
+            const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                v[8 * h + 2 * k] = w[k] & 0xffffu;
+                v[8 * h + 2 * k + 1] = w[k] >> 16;
+            }
         }
     } else {
 #pragma unroll
-        for (int k = 0; k < 8; ++k) v[k] = i0 + k < n ? (uint32_t)sym[i0 + k] : 0xffffu;
+        for (int k = 0; k < kLaneSyms; ++k) v[k] = i0 + k < n ? (uint32_t)sym[i0 + k] : 0xffffu;
     }
 }
 
@@ -308,14 +312,13 @@ __device__ __forceinline__ void chunk_range(uint64_t nc, uint32_t G, uint32_t j,
     *c1 = umin64(nc, *c0 + per);
 }
 
-// Pass 1: the words of each chunk (its bits rounded up to 32).  CTA j writes
-// off[c] = words of its chunks before c (offsets local to its range) and its
-// range's total into rt[j].
+// Pass 1: the words of each chunk (its bits rounded up to 32), one warp per
+// chunk; then CTA j turns its range's counts into offsets local to the
+// range (off[c] = words of its chunks before c) and its total into rt[j].
 __global__ void __launch_bounds__(kEncThreads) k_huff_chunk_words(const uint16_t* __restrict__ sym, uint64_t n,
                                                                    const void* bookp, uint32_t nsym, uint64_t* off,
                                                                    unsigned long long* rt, uint32_t* status) {
     __shared__ uint8_t slen[kMaxSym];
-    __shared__ unsigned int red[kEncThreads / 32];
     const HuffBook bk = huff_book(bookp, nsym);
     const uint64_t nc = (n + kHC - 1) / kHC;
     uint64_t c0, c1;
@@ -330,18 +333,16 @@ __global__ void __launch_bounds__(kEncThreads) k_huff_chunk_words(const uint16_t
     }
     for (uint32_t i = threadIdx.x; i < nsym; i += blockDim.x) slen[i] = bk.len[i];
     __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const bool vec = (reinterpret_cast<uintptr_t>(sym) & 15) == 0;
     bool bad = false;
-    unsigned long long run = 0;  // thread 0: words of the range so far
-    uint32_t v[8];
-    if (c0 < c1) load8(sym, n, c0 * kHC + (uint64_t)threadIdx.x * kPerThread, vec, v);
-    for (uint64_t c = c0; c < c1; ++c) {
-        uint32_t nx[8];
-        if (c + 1 < c1) load8(sym, n, (c + 1) * kHC + (uint64_t)threadIdx.x * kPerThread, vec, nx);  // next chunk, in flight
-        const uint64_t i0 = c * kHC + (uint64_t)threadIdx.x * kPerThread;
+    for (uint64_t c = c0 + warp; c < c1; c += kEncThreads / 32) {
+        uint32_t v[kLaneSyms];
+        load32(sym, n, c, lane, vec, v);
+        const uint64_t i0 = c * kHC + (uint64_t)lane * kLaneSyms;
         unsigned int bits = 0;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
+        for (int k = 0; k < kLaneSyms; ++k) {
             if (i0 + k < n) {
                 const uint32_t l = v[k] < nsym ? slen[v[k]] : 0u;
                 bad |= l == 0;
@@ -350,19 +351,25 @@ __global__ void __launch_bounds__(kEncThreads) k_huff_chunk_words(const uint16_t
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) bits += __shfl_xor_sync(VSZ_FULL, bits, o);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = bits;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            unsigned long long t = 0;
-            for (int w = 0; w < kEncThreads / 32; ++w) t += red[w];
-            off[c] = run;
-            run += (t + 31) / 32;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < 8; ++k) v[k] = nx[k];
+        if (lane == 0) off[c] = (bits + 31u) / 32u;
     }
-    if (threadIdx.x == 0) rt[blockIdx.x] = run;
+    __syncthreads();
+    if (warp == 0) {  // range-local exclusive offsets, in place
+        unsigned long long carry = 0;
+        for (uint64_t b0 = c0; b0 < c1; b0 += 32) {
+            const uint64_t c = b0 + lane;
+            const unsigned long long w = c < c1 ? off[c] : 0ull;
+            unsigned long long x = w;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(VSZ_FULL, x, o);
+                if (lane >= o) x += y;
+            }
+            if (c < c1) off[c] = carry + x - w;
+            carry += __shfl_sync(VSZ_FULL, x, 31);
+        }
+        if (lane == 0) rt[blockIdx.x] = carry;
+    }
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, 1u);
 }
 
@@ -408,15 +415,16 @@ __global__ void __launch_bounds__(1024) k_huff_scan(unsigned long long* rt, uint
     }
 }
 
-// Pass 3: CTA j packs its chunks (same ranges as pass 1): codeword bits into
-// shared memory, then stored; the chunk's final offset replaces its local one.
-// The next chunk's codes and offsets are loaded while the current one packs.
+// Pass 3: CTA j codes its chunks (same ranges as pass 1), one warp per
+// chunk: each lane writes its 32 codewords through a 64-bit bit-writer into
+// the warp's words in shared memory (the words it shares with its neighbour
+// lanes by OR), then the warp stores them and the chunk's final offset
+// replaces its local one.
 __global__ void __launch_bounds__(kEncThreads) k_huff_encode(const uint16_t* __restrict__ sym, uint64_t n,
                                                               const void* bookp, uint32_t nsym, uint64_t* off,
                                                               const unsigned long long* __restrict__ rt,
                                                               uint32_t* words, uint64_t word_cap) {
-    __shared__ uint32_t sw[kChunkWordsMax];
-    __shared__ unsigned int red[kEncThreads / 32];
+    __shared__ uint32_t sw[kEncThreads / 32][kChunkWordsMax];
     extern __shared__ __align__(16) unsigned char smraw[];
     unsigned long long* scode = (unsigned long long*)smraw;  // [nsym]
     uint8_t* slen = (uint8_t*)(scode + nsym);                 // [nsym]
@@ -426,78 +434,65 @@ __global__ void __launch_bounds__(kEncThreads) k_huff_encode(const uint16_t* __r
         scode[i] = bk.code[i];
         slen[i] = bk.len[i];
     }
+    __syncthreads();
     const uint64_t nc = (n + kHC - 1) / kHC;
     uint64_t c0, c1;
     chunk_range(nc, gridDim.x, blockIdx.x, &c0, &c1);
-    const unsigned long long base = rt[blockIdx.x], rend = rt[blockIdx.x + 1] - base;  // range words
+    const unsigned long long base = rt[blockIdx.x];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t* ws = sw[warp];
     const bool vec = (reinterpret_cast<uintptr_t>(sym) & 15) == 0;
-    uint32_t v[8];
-    uint64_t lo = 0, hi = 0;  // local offsets of the current chunk and of the next
-    if (c0 < c1) {
-        load8(sym, n, c0 * kHC + (uint64_t)threadIdx.x * kPerThread, vec, v);
-        lo = off[c0];
-        hi = c0 + 1 < c1 ? off[c0 + 1] : rend;
-    }
-    for (uint64_t c = c0; c < c1; ++c) {
-        uint32_t nx[8];
-        uint64_t hi2 = 0;
-        if (c + 1 < c1) {  // next chunk: codes and its end offset, in flight
-            load8(sym, n, (c + 1) * kHC + (uint64_t)threadIdx.x * kPerThread, vec, nx);
-            hi2 = c + 2 < c1 ? off[c + 2] : rend;
-        }
-        const uint64_t w0 = base + lo, nw = min(hi - lo, (uint64_t)kChunkWordsMax);
-        for (uint32_t i = threadIdx.x; i < nw; i += blockDim.x) sw[i] = 0;
-        __syncthreads();
-        unsigned int mybits = 0;
+    for (uint64_t c = c0 + warp; c < c1; c += kEncThreads / 32) {
+        uint32_t v[kLaneSyms];
+        load32(sym, n, c, lane, vec, v);
+        uint32_t mybits = 0;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) mybits += v[k] < nsym ? slen[v[k]] : 0u;
-        // exclusive scan of the threads' bit counts
-        unsigned int x = mybits;
+        for (int k = 0; k < kLaneSyms; ++k) mybits += v[k] < nsym ? slen[v[k]] : 0u;
+        uint32_t x = mybits;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const unsigned int y = __shfl_up_sync(VSZ_FULL, x, o);
-            if ((threadIdx.x & 31) >= (unsigned)o) x += y;
+            const uint32_t y = __shfl_up_sync(VSZ_FULL, x, o);
+            if (lane >= o) x += y;
         }
-        if ((threadIdx.x & 31) == 31) red[threadIdx.x >> 5] = x;
-        __syncthreads();
-        unsigned int pos = x - mybits;
-        for (uint32_t w = 0; w < (threadIdx.x >> 5); ++w) pos += red[w];
-        // OR the low `rem` bits of cw into the chunk at bit `pos` (at most three words)
-        auto emit = [&](unsigned long long cw, uint32_t rem) {
-            while (rem > 0) {
-                const uint32_t wi = pos >> 5, o = pos & 31;
-                const uint32_t take = min(32u - o, rem);
-                const uint32_t bits =
-                    (uint32_t)((cw >> (rem - take)) & ((take == 32) ? 0xffffffffull : ((1ull << take) - 1)));
-                if (wi < nw) atomicOr(&sw[wi], bits << (32 - o - take));
-                pos += take;
-                rem -= take;
+        const uint32_t total = __shfl_sync(VSZ_FULL, x, 31);
+        const uint32_t nw = min((total + 31u) / 32u, (uint32_t)kChunkWordsMax);
+        const uint32_t pos = x - mybits;  // this lane's first bit in the chunk
+        for (uint32_t i = lane; i < nw; i += 32) ws[i] = 0;
+        __syncwarp();
+        // bit-writer: acc holds nacc pending bits (nacc < 32 between codes);
+        // the lane's first word starts with pos & 31 bits of its neighbour
+        unsigned long long acc = 0;
+        uint32_t nacc = pos & 31u, wi = pos >> 5;
+        auto push = [&](unsigned long long bits, uint32_t len) {  // len <= 32
+            acc = (acc << len) | bits;
+            nacc += len;
+            if (nacc >= 32) {
+                nacc -= 32;
+                const uint32_t word = (uint32_t)(acc >> nacc);
+                if (wi < nw) atomicOr(&ws[wi], word);
+                ++wi;
+                acc &= nacc ? ((1ull << nacc) - 1) : 0ull;
             }
         };
-        if (mybits <= 64) {
-            // the thread's eight codewords fit one register: a few ORs in all
-            unsigned long long acc = 0;
 #pragma unroll
-            for (int k = 0; k < 8; ++k)
-                if (v[k] < nsym) {
-                    const uint32_t l = slen[v[k]];
-                    acc = l ? ((l == 64 ? 0ull : acc << l) | scode[v[k]]) : acc;
-                }
-            emit(acc, mybits);
-        } else {
-#pragma unroll
-            for (int k = 0; k < 8; ++k)
-                if (v[k] < nsym) emit(scode[v[k]], slen[v[k]]);
+        for (int k = 0; k < kLaneSyms; ++k) {
+            if (v[k] >= nsym) continue;
+            const uint32_t l = slen[v[k]];
+            const unsigned long long cw = scode[v[k]];
+            if (l > 32) {
+                push(cw >> 32, l - 32);
+                push(cw & 0xffffffffull, 32);
+            } else if (l) {
+                push(cw, l);
+            }
         }
-        __syncthreads();
-        for (uint32_t i = threadIdx.x; i < nw; i += blockDim.x)
-            if (w0 + i < word_cap) words[w0 + i] = sw[i];
-        if (threadIdx.x == 0) off[c] = w0;  // final offset (its local value was read before)
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < 8; ++k) v[k] = nx[k];
-        lo = hi;
-        hi = hi2;
+        if (nacc > 0 && wi < nw) atomicOr(&ws[wi], (uint32_t)(acc << (32 - nacc)));
+        __syncwarp();
+        const uint64_t w0 = base + off[c];  // the local offset, read by this warp only
+        for (uint32_t i = lane; i < nw; i += 32)
+            if (w0 + i < word_cap) words[w0 + i] = ws[i];
+        __syncwarp();
+        if (lane == 0) off[c] = w0;  // final offset
     }
 }
 
@@ -666,8 +661,11 @@ vsz_status vsz_huffman_book_read(const void* d_book, uint32_t nsym, uint8_t* h_l
     return h.ok ? VSZ_OK : VSZ_ERR_UNSUPPORTED;
 }
 
-static uint32_t encode_ctas(uint64_t nc) {
-    const uint64_t g = umin64(nc, umin64((uint64_t)num_sms() * 8, kEncMaxCtas));
+// One wave of the coding pass: the SMs times the CTAs of k_huff_encode an SM
+// holds with the book's tables in shared memory.
+static uint32_t encode_ctas(uint64_t nc, size_t smem) {
+    const int occ = occupancy((const void*)k_huff_encode, kEncThreads, smem);
+    const uint64_t g = umin64(nc, umin64((uint64_t)num_sms() * (uint64_t)(occ > 0 ? occ : 1), kEncMaxCtas));
     return (uint32_t)(g ? g : 1);
 }
 
@@ -692,7 +690,9 @@ vsz_status vsz_huffman_encode(const uint16_t* d_sym, uint64_t n, const void* d_b
         return e == cudaSuccess ? VSZ_OK : cuda_fail(e);
     }
     unsigned long long* rt = (unsigned long long*)d_ws;
-    const uint32_t G = encode_ctas(nc);
+    const size_t smem = (size_t)nsym * 9;  // codeword and length tables
+    if ((e = raise_smem_attr((const void*)k_huff_encode, smem)) != cudaSuccess) return cuda_fail(e);
+    const uint32_t G = encode_ctas(nc, smem);
     {
         TraceScope ts("huff_chunk_words", s, 0, 0, n);
         k_huff_chunk_words<<<G, kEncThreads, 0, s>>>(d_sym, n, d_book, nsym, d_chunk_off, rt, d_status);
@@ -703,8 +703,6 @@ vsz_status vsz_huffman_encode(const uint16_t* d_sym, uint64_t n, const void* d_b
         k_huff_scan<<<1, 1024, 0, s>>>(rt, G, d_chunk_off, nc, word_cap, d_status);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
     }
-    const size_t smem = (size_t)nsym * 9;  // codeword and length tables
-    if ((e = raise_smem_attr((const void*)k_huff_encode, smem)) != cudaSuccess) return cuda_fail(e);
     {
         TraceScope ts("huff_encode", s, 0, 0, n);
         k_huff_encode<<<G, kEncThreads, smem, s>>>(d_sym, n, d_book, nsym, d_chunk_off, rt, d_words, word_cap);

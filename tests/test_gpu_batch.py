@@ -222,3 +222,32 @@ def test_launch_shapes_and_autotune_change_no_result():
     with pytest.raises(vsz.VszError):
         b.set_shape(len(cls), 4, 0)
     b.close()
+
+
+def test_autotune_cache_round_trip(tmp_path):
+    """Shapes found by the autotuner are recorded per GPU model and class, and
+    a later plan with the same classes takes them without searching."""
+    fields, xs = _make()
+    outs = _outs(fields)
+    cache = str(tmp_path / "shapes.json")
+    stream = torch.cuda.Stream()
+    b1 = vsz.Batch(fields, xs, use_graph=True)
+    b1.set_outputs(outs)
+    tuned = b1.autotune(stream, reps=1, cache=cache)
+    assert all(c["ms"] > 0 for c in tuned if c["tiles"])  # searched: timings recorded
+    b2 = vsz.Batch(fields, xs, use_graph=True)
+    b2.set_outputs(outs)
+    loaded = b2.autotune(stream, reps=1, cache=cache)
+    assert all(c["ms"] == 0 for c in loaded)  # not searched again
+    assert [(c["warps"], c["ctas_per_sm"]) for c in loaded] == [(c["warps"], c["ctas_per_sm"]) for c in tuned]
+    with torch.cuda.stream(stream):
+        b1.submit()
+    stream.synchronize()
+    want = [_host(f) for f in fields]
+    _scramble(fields)
+    with torch.cuda.stream(stream):
+        b2.submit()
+    stream.synchronize()
+    _assert_same(fields, want, "cached shapes")
+    b1.close()
+    b2.close()
