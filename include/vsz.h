@@ -408,8 +408,9 @@ VSZ_API vsz_status vsz_huffman_book_read(const void* d_book, uint32_t nsym, uint
 VSZ_API size_t vsz_huffman_encode_workspace_size(uint64_t n);
 
 /* Encode d_sym[n] (uint16 symbols < nsym, device) into d_words (uint32,
- * word_cap words) and d_chunk_off[ceil(n / VSZ_HUFF_CHUNK) + 1] (uint64).
- * *d_status (device uint32) receives bit 1 if a symbol has no codeword and
+ * word_cap words) and d_chunk_off[ceil(n / VSZ_HUFF_CHUNK) + 1] (uint64);
+ * d_book as vsz_huffman_book wrote it (16-byte aligned, else
+ * VSZ_ERR_INVALID_ARG).  *d_status (device uint32) receives bit 1 if a symbol has no codeword and
  * bit 2 if the stream is longer than word_cap words (the offsets are still
  * exact, so the caller can retry with chunk_off[nchunks] words). */
 VSZ_API vsz_status vsz_huffman_encode(const uint16_t* d_sym, uint64_t n, const void* d_book, uint32_t nsym,
@@ -417,7 +418,8 @@ VSZ_API vsz_status vsz_huffman_encode(const uint16_t* d_sym, uint64_t n, const v
                                       uint32_t* d_status, void* d_ws, size_t ws_bytes, void* stream);
 
 /* Decode n symbols from d_words (word_cap words readable) / d_chunk_off into
- * d_sym (uint16, device).  *d_status receives bit 4 if a chunk holds no
+ * d_sym (uint16, device) with d_book (16-byte aligned, else
+ * VSZ_ERR_INVALID_ARG).  *d_status receives bit 4 if a chunk holds no
  * valid codeword where one is expected or runs past its words (or past
  * word_cap).  Both calls set bit 8 if d_book was built for another nsym. */
 VSZ_API vsz_status vsz_huffman_decode(const uint32_t* d_words, uint64_t word_cap, const uint64_t* d_chunk_off,

@@ -11,12 +11,12 @@
 // Stream: chunks of VSZ_HUFF_CHUNK symbols, each starting on a 32-bit word,
 // bits filling each word from its most significant bit; chunk_off[c] is the
 // first word of chunk c.  Encoding: per-chunk bit counts, a scan into word
-// offsets, then one CTA per chunk (eight symbols per thread, one 16-byte
-// load) packs its codewords into shared memory and stores the words.
+// offsets, then one warp per chunk (32 symbols per lane) packs its codewords
+// into shared memory and stores the words.
 // Decoding: one thread per chunk walks its bits with a 2^12-entry lookup
 // table (two codewords per entry when both fit, for alphabets up to 4096
-// symbols) and the canonical ranges for longer codewords, its words flowing
-// through a 12-word register queue loaded ahead of use.
+// symbols) and the canonical ranges for longer codewords, over a two-word
+// window fed by aligned 16-byte loads issued ahead of use.
 #include <climits>
 
 #include "common.cuh"
@@ -24,10 +24,10 @@
 
 namespace vsz {
 
-constexpr int kLutBits = 12;
+constexpr int kLutBits = 15;  // the decoder's table: 2^15 entries, 128 KB of shared memory
 // Alphabets up to 4096 symbols (R <= 2048) use two-symbol table entries:
 // s1 | s2 << 12 | len1 << 24 | len2 << 28, len1 = 0 for a codeword longer
-// than the table, len2 = 0 when no second codeword fits in the 12 bits.
+// than the table, len2 = 0 when no second codeword fits in the 15 bits.
 // Larger alphabets use one-symbol entries len << 16 | s.
 constexpr uint32_t kPairMaxSym = 4096;
 constexpr uint32_t kMaxSym = VSZ_HUFF_MAX_SYMBOLS;
@@ -40,15 +40,16 @@ struct HuffLayout {
     size_t code, len, first, count, base, sorted, lut, total;
 };
 __host__ __device__ inline HuffLayout huff_layout(uint32_t nsym) {
+    auto up = [](size_t v) { return (v + 15) & ~(size_t)15; };  // every table starts on 16 bytes
     HuffLayout L;
     size_t off = 64;
-    L.code = off;   off += (size_t)nsym * 8;
-    L.first = off;  off += 66 * 8;
-    L.count = off;  off += 66 * 4;
-    L.base = off;   off += 66 * 4;
-    L.lut = off;    off += ((size_t)1 << kLutBits) * 4;
-    L.len = off;    off += ((size_t)nsym + 15) & ~(size_t)15;
-    L.sorted = off; off += ((size_t)nsym * 2 + 15) & ~(size_t)15;
+    L.code = off;   off = up(off + (size_t)nsym * 8);
+    L.first = off;  off = up(off + 66 * 8);
+    L.count = off;  off = up(off + 66 * 4);
+    L.base = off;   off = up(off + 66 * 4);
+    L.lut = off;    off = up(off + ((size_t)1 << kLutBits) * 4);
+    L.len = off;    off = up(off + nsym);
+    L.sorted = off; off = up(off + (size_t)nsym * 2);
     L.total = off;
     return L;
 }
@@ -92,10 +93,10 @@ __device__ void bitonic_sort(unsigned long long* key, uint32_t n) {
 }
 
 // Bytes of the codebook kernel's sort and tree arrays (25 per padded symbol),
-// rounded to 16; its one-symbol table follows.
+// rounded to 16.
 __host__ __device__ inline size_t book_smem_front(uint32_t np) { return ((size_t)np * 25 + 15) & ~(size_t)15; }
 
-__global__ void __launch_bounds__(1024) k_huff_book(const uint32_t* __restrict__ hist, uint32_t nsym, void* book) {
+__global__ void __launch_bounds__(1024, 1) k_huff_book(const uint32_t* __restrict__ hist, uint32_t nsym, void* book) {
     extern __shared__ __align__(16) unsigned char sm[];
     const HuffLayout L = huff_layout(nsym);
     char* B = (char*)book;
@@ -106,7 +107,6 @@ __global__ void __launch_bounds__(1024) k_huff_book(const uint32_t* __restrict__
     uint32_t* count = (uint32_t*)(B + L.count);
     uint32_t* base = (uint32_t*)(B + L.base);
     uint16_t* sorted = (uint16_t*)(B + L.sorted);
-    uint32_t* lut = (uint32_t*)(B + L.lut);
 
     uint32_t np = 2;
     while (np < nsym) np <<= 1;
@@ -115,7 +115,6 @@ __global__ void __launch_bounds__(1024) k_huff_book(const uint32_t* __restrict__
     int32_t* lpar = (int32_t*)(iw + np);                            // [np] parent of each leaf
     int32_t* ipar = lpar + np;                                      // [np] parent of each merged node
     uint8_t* depth = (uint8_t*)(ipar + np);                         // [np] depth of each merged node
-    uint32_t* slut = (uint32_t*)(sm + book_smem_front(np));         // [2^12] one-symbol table
     __shared__ uint32_t s_cnt[66];
     __shared__ unsigned long long s_first[66];
     __shared__ uint32_t s_base[66];
@@ -144,9 +143,11 @@ __global__ void __launch_bounds__(1024) k_huff_book(const uint32_t* __restrict__
         const uint32_t k = kk;
         s_ok = 1;
         // two-queue merge: leaves key[0..k), merged nodes iw[0..k-1); the
-        // heads of both queues stay in registers
+        // first two of both queues stay in registers, so that taking a head
+        // never waits for a shared-memory load
         uint32_t i = 0, j = 0, made = 0;
-        unsigned long long lw = k > 0 ? key[0] >> 16 : ~0ull, mw = ~0ull;
+        unsigned long long lw = k > 0 ? key[0] >> 16 : ~0ull, lwn = k > 1 ? key[1] >> 16 : ~0ull;
+        unsigned long long mw = ~0ull, mwn = ~0ull;
         for (uint32_t t = 0; k >= 2 && t + 1 < k; ++t) {
             unsigned long long w2 = 0;
 #pragma unroll
@@ -157,17 +158,20 @@ __global__ void __launch_bounds__(1024) k_huff_book(const uint32_t* __restrict__
                     w = lw;
                     lpar[i] = (int32_t)made;
                     ++i;
-                    lw = i < k ? key[i] >> 16 : ~0ull;
+                    lw = lwn;
+                    lwn = i + 1 < k ? key[i + 1] >> 16 : ~0ull;
                 } else {
                     w = mw;
                     ipar[j] = (int32_t)made;
                     ++j;
-                    mw = j < made ? iw[j] : ~0ull;
+                    mw = mwn;
+                    mwn = j + 1 < made ? iw[j + 1] : ~0ull;
                 }
                 w2 += w;
             }
             iw[made] = w2;
-            if (j == made) mw = w2;  // the merged queue was empty: its head is the new node
+            if (j == made) mw = w2;           // the merged queue was empty
+            else if (j + 1 == made) mwn = w2;  // it held one node
             ++made;
         }
         if (made > 0) ipar[made - 1] = -1;
@@ -238,20 +242,45 @@ __global__ void __launch_bounds__(1024) k_huff_book(const uint32_t* __restrict__
         count[i] = s_cnt[i];
         base[i] = s_base[i];
     }
-    for (uint32_t i = threadIdx.x; i < (1u << kLutBits); i += blockDim.x) slut[i] = 0;
-    __syncthreads();
-    for (uint32_t r = threadIdx.x; r < mm; r += blockDim.x) {
-        const uint32_t l = (uint32_t)(key[r] >> 16), s = (uint32_t)(key[r] & 0xffffu);
-        if (l <= (uint32_t)kLutBits) {
-            const uint32_t c0 = (uint32_t)(s_first[l] + (r - s_base[l])) << (kLutBits - l);
-            const uint32_t c1 = c0 + (1u << (kLutBits - l));
-            for (uint32_t e = c0; e < c1; ++e) slut[e] = (l << 16) | s;
-        }
+    if (threadIdx.x == 0) {
+        hdr->nsym = nsym;
+        hdr->max_len = s_maxlen;
+        hdr->nused = mm;
+        hdr->ok = s_ok;
+    }
+}
+
+// The decoder's table (many CTAs, after k_huff_book): entry p holds the
+// codeword that the kLutBits bits p start with (the canonical range of its
+// length holds p's prefix), and for small alphabets the codeword after it
+// when that one ends within the same bits (bits past them read as 0).
+__global__ void __launch_bounds__(256) k_huff_lut(uint32_t nsym, void* book) {
+    const HuffLayout L = huff_layout(nsym);
+    char* B = (char*)book;
+    const uint64_t* first = (const uint64_t*)(B + L.first);
+    const uint32_t* count = (const uint32_t*)(B + L.count);
+    const uint32_t* base = (const uint32_t*)(B + L.base);
+    const uint16_t* sorted = (const uint16_t*)(B + L.sorted);
+    uint32_t* lut = (uint32_t*)(B + L.lut);
+    __shared__ unsigned long long s_first[kLutBits + 1];
+    __shared__ uint32_t s_cnt[kLutBits + 1], s_base[kLutBits + 1];
+    if (threadIdx.x <= (unsigned)kLutBits) {
+        s_first[threadIdx.x] = first[threadIdx.x];
+        s_cnt[threadIdx.x] = count[threadIdx.x];
+        s_base[threadIdx.x] = base[threadIdx.x];
     }
     __syncthreads();
+    auto one = [&](uint32_t p) -> uint32_t {
+        for (uint32_t l = 1; l <= (uint32_t)kLutBits; ++l) {
+            const unsigned long long cw = p >> (kLutBits - l);
+            if (cw >= s_first[l] && cw - s_first[l] < s_cnt[l])
+                return (l << 16) | sorted[s_base[l] + (uint32_t)(cw - s_first[l])];
+        }
+        return 0u;
+    };
     const bool pair = nsym <= kPairMaxSym;
-    for (uint32_t p = threadIdx.x; p < (1u << kLutBits); p += blockDim.x) {
-        const uint32_t e1 = slut[p];
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < (1u << kLutBits); p += gridDim.x * blockDim.x) {
+        const uint32_t e1 = one(p);
         if (!pair) {
             lut[p] = e1;
             continue;
@@ -259,20 +288,13 @@ __global__ void __launch_bounds__(1024) k_huff_book(const uint32_t* __restrict__
         const uint32_t l1 = e1 >> 16, s1 = e1 & 0xffffu;
         uint32_t l2 = 0, s2 = 0;
         if (l1 > 0 && l1 < (uint32_t)kLutBits) {
-            // the codeword after s1 within the same 12 bits (bits past them read as 0)
-            const uint32_t e2 = slut[(p << l1) & ((1u << kLutBits) - 1)];
+            const uint32_t e2 = one((p << l1) & ((1u << kLutBits) - 1));
             if ((e2 >> 16) > 0 && (e2 >> 16) <= (uint32_t)kLutBits - l1) {
                 l2 = e2 >> 16;
                 s2 = e2 & 0xffffu;
             }
         }
         lut[p] = l1 ? (s1 | (s2 << 12) | (l1 << 24) | (l2 << 28)) : 0u;
-    }
-    if (threadIdx.x == 0) {
-        hdr->nsym = nsym;
-        hdr->max_len = s_maxlen;
-        hdr->nused = mm;
-        hdr->ok = s_ok;
     }
 }
 
@@ -497,24 +519,25 @@ __global__ void __launch_bounds__(kEncThreads) k_huff_encode(const uint16_t* __r
 }
 
 // ---------------------------------------------------------------- decoding
-constexpr int kDecThreads = 128;
+constexpr int kDecMaxThreads = 1024;  // one CTA per SM, one thread per chunk
 
-__global__ void __launch_bounds__(kDecThreads) k_huff_decode(const uint32_t* __restrict__ words, uint64_t word_cap,
+__global__ void __launch_bounds__(kDecMaxThreads) k_huff_decode(const uint32_t* __restrict__ words, uint64_t word_cap,
                                                               const uint64_t* __restrict__ off, uint64_t n,
                                                               const void* bookp, uint32_t nsym, uint16_t* out,
                                                               uint32_t* status) {
-    __shared__ uint32_t lut[1 << kLutBits];
     __shared__ unsigned long long first[66];
     __shared__ uint32_t cnt[66], base[66];
     extern __shared__ __align__(16) unsigned char smraw[];
-    uint16_t* sorted = (uint16_t*)smraw;
+    uint32_t* lut = (uint32_t*)smraw;                           // [2^kLutBits]
+    uint16_t* sorted = (uint16_t*)(lut + (1u << kLutBits));     // [nused]
     const HuffBook bk = huff_book(bookp, nsym);
     if (bk.hdr->nsym != nsym) {  // a book built for another alphabet
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, 8u);
         return;
     }
     const uint32_t nused = min(bk.hdr->nused, nsym), maxlen = min(bk.hdr->max_len, 64u);
-    for (uint32_t i = threadIdx.x; i < (1u << kLutBits); i += blockDim.x) lut[i] = bk.lut[i];
+    for (uint32_t i = threadIdx.x; i < (1u << kLutBits) / 4; i += blockDim.x)
+        reinterpret_cast<uint4*>(lut)[i] = __ldg(reinterpret_cast<const uint4*>(bk.lut) + i);
     for (uint32_t i = threadIdx.x; i < 66; i += blockDim.x) {
         first[i] = bk.first[i];
         cnt[i] = bk.count[i];
@@ -523,54 +546,77 @@ __global__ void __launch_bounds__(kDecThreads) k_huff_decode(const uint32_t* __r
     for (uint32_t i = threadIdx.x; i < nused; i += blockDim.x) sorted[i] = bk.sorted[i];
     __syncthreads();
     const uint64_t nc = (n + kHC - 1) / kHC;
-    const uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= nc) return;
+    for (uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t wb = off[c], we = umin64(off[c + 1], word_cap);
-    const uint64_t i0 = c * kHC, i1 = umin64(n, i0 + kHC);
-    auto wd = [&](uint64_t k) -> uint32_t { return wb + k < we ? __ldg(words + wb + k) : 0u; };
-    // a 12-word register queue: the window reads q[0..5]; words are loaded
-    // four at a time, eight words ahead of use, so their latency overlaps
-    // the decoding of the words before them
-    uint32_t q[12];
-#pragma unroll
-    for (int k = 0; k < 12; ++k) q[k] = wd(k);
-    uint64_t qbase = 0;  // word index of q[0]
-    uint32_t pos = 0;    // bit position inside q[0]
-    const bool vec = (reinterpret_cast<uintptr_t>(out) & 15) == 0;
-    uint32_t pk[4] = {0, 0, 0, 0};
-    bool bad = false;
-    uint64_t total_bits = 0;
-    const bool pair = nsym <= kPairMaxSym;
-    // place symbol i (16-byte stores of eight symbols when aligned)
-    auto put = [&](uint64_t i, uint32_t sv) {
-        if (vec) {
-            const int slot = (int)((i - i0) & 7);
-            pk[slot >> 1] |= sv << ((slot & 1) * 16);
-            if (slot == 7) {
-                *reinterpret_cast<uint4*>(out + i - 7) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                pk[0] = pk[1] = pk[2] = pk[3] = 0;
-            }
-        } else {
-            out[i] = (uint16_t)sv;
+    if (wb > we) {
+        atomicOr(status, 4u);
+        continue;
+    }
+    const uint64_t i0 = c * kHC;
+    const uint32_t m = (uint32_t)(umin64(n, i0 + kHC) - i0);  // symbols of this chunk
+    uint16_t* o = out + i0;
+    // Words arrive through a two-deep queue of aligned 16-byte loads (the
+    // words before wb in the first one are skipped), each used 4..8 words
+    // after it was issued.  Words past the chunk's end are read (within
+    // word_cap) but never consumed by a valid stream.
+    const bool vw = (reinterpret_cast<uintptr_t>(words) & 15) == 0;
+    auto ld4 = [&](uint64_t a) -> uint4 {  // a is a multiple of 4
+        if (vw && a + 4 <= word_cap) return __ldg(reinterpret_cast<const uint4*>(words + a));
+        uint4 r;
+        r.x = a < word_cap ? __ldg(words + a) : 0u;
+        r.y = a + 1 < word_cap ? __ldg(words + a + 1) : 0u;
+        r.z = a + 2 < word_cap ? __ldg(words + a + 2) : 0u;
+        r.w = a + 3 < word_cap ? __ldg(words + a + 3) : 0u;
+        return r;
+    };
+    uint64_t na = wb & ~3ull;
+    uint4 cur = ld4(na), nxt = ld4(na + 4);
+    na += 8;
+    uint32_t k = (uint32_t)(wb & 3);  // the next word of cur
+    auto sel = [&]() -> uint32_t { return k == 0 ? cur.x : k == 1 ? cur.y : k == 2 ? cur.z : cur.w; };
+    auto step_queue = [&]() {
+        if (k == 4) {
+            cur = nxt;
+            nxt = ld4(na);
+            na += 4;
+            k = 0;
         }
     };
-    for (uint64_t i = i0; i < i1;) {
-        if (pos >= 128) {  // consumed q[0..3]: shift the queue, fetch four more
-#pragma unroll
-            for (int k = 0; k < 8; ++k) q[k] = q[k + 4];
-            qbase += 4;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) q[k + 8] = wd(qbase + 8 + k);
-            pos -= 128;
+    // The window: the stream's next bit is bit ob (from the top) of w0; w1
+    // follows w0 and sel() follows w1.
+    uint32_t w0 = sel();
+    ++k;
+    step_queue();
+    uint32_t w1 = sel();
+    ++k;
+    step_queue();
+    uint32_t ob = 0;
+    // Output: symbols gather four at a time in a 64-bit register (slot 0 the
+    // oldest) and leave in 8-byte stores when out is 8-byte aligned; one
+    // store per symbol if not.
+    const bool vec = (reinterpret_cast<uintptr_t>(out) & 7) == 0;
+    unsigned long long acc = 0;
+    uint32_t pend = 0, g = 0;  // symbols in acc; symbols stored
+    auto emit = [&](uint32_t val, uint32_t cnt, uint32_t i) {  // cnt symbols, the first in the low half
+        if (vec) {
+            acc |= (unsigned long long)val << (16 * pend);
+            const uint32_t np = pend + cnt;
+            if (np >= 4) {
+                *reinterpret_cast<unsigned long long*>(o + g) = acc;
+                g += 4;
+                acc = np == 5 ? (unsigned long long)(val >> 16) : 0ull;
+            }
+            pend = np >= 4 ? np - 4 : np;
+        } else {
+            o[i] = (uint16_t)val;
+            if (cnt == 2) o[i + 1] = (uint16_t)(val >> 16);
         }
-        const uint32_t wsel = pos >> 5, o = pos & 31;
-        const uint32_t a = wsel == 0 ? q[0] : wsel == 1 ? q[1] : wsel == 2 ? q[2] : q[3];
-        const uint32_t b = wsel == 0 ? q[1] : wsel == 1 ? q[2] : wsel == 2 ? q[3] : q[4];
-        const uint32_t d = wsel == 0 ? q[2] : wsel == 1 ? q[3] : wsel == 2 ? q[4] : q[5];
-        // 64 bits starting at bit o of word a
-        const unsigned long long top = ((unsigned long long)a << 32) | b;
-        const unsigned long long win = o ? (top << o) | ((unsigned long long)d >> (32 - o)) : top;
-        const uint32_t e = lut[(uint32_t)(win >> (64 - kLutBits))];
+    };
+    const bool pair = nsym <= kPairMaxSym;
+    bool bad = false;
+    uint32_t used = 0;  // bits consumed
+    for (uint32_t i = 0; i < m;) {
+        const uint32_t e = lut[__funnelshift_l(w1, w0, ob) >> (32 - kLutBits)];
         uint32_t l, sv, l2 = 0, sv2 = 0;
         if (pair) {
             l = (e >> 24) & 15u;
@@ -581,7 +627,10 @@ __global__ void __launch_bounds__(kDecThreads) k_huff_decode(const uint32_t* __r
             l = e >> 16;
             sv = e & 0xffffu;
         }
-        if (l == 0) {
+        if (l == 0) {  // a codeword longer than the table: the canonical ranges on a 64-bit window
+            const uint32_t w2 = sel();
+            const unsigned long long win = ((unsigned long long)__funnelshift_l(w1, w0, ob) << 32) |
+                                           __funnelshift_l(w2, w1, ob);
             for (uint32_t L = kLutBits + 1; L <= maxlen; ++L) {
                 const unsigned long long cw = win >> (64 - L);
                 if (cw >= first[L] && cw - first[L] < cnt[L]) {
@@ -594,26 +643,41 @@ __global__ void __launch_bounds__(kDecThreads) k_huff_decode(const uint32_t* __r
                 bad = true;
                 break;
             }
+            emit(sv, 1, i);
+            used += l;
+            ob += l;
+            while (ob >= 32) {  // at most twice
+                w0 = w1;
+                w1 = sel();
+                ++k;
+                step_queue();
+                ob -= 32;
+            }
+            ++i;
+            continue;
         }
-        if (i + 1 >= i1) l2 = 0;  // the chunk's last symbol: what follows is padding
-        put(i, sv);
-        if (l2) put(i + 1, sv2);
-        pos += l + l2;
-        total_bits += l + l2;
+        if (i + 1 >= m) l2 = 0;  // the chunk's last symbol: what follows is padding
+        const uint32_t t = l + l2;  // <= 12
+        emit(l2 ? sv | (sv2 << 16) : sv, l2 ? 2u : 1u, i);
+        used += t;
         i += l2 ? 2 : 1;
+        ob += t;
+        const bool adv = ob >= 32;
+        const uint32_t wn = sel();
+        w0 = adv ? w1 : w0;
+        w1 = adv ? wn : w1;
+        ob -= adv ? 32u : 0u;
+        k += adv ? 1u : 0u;
+        step_queue();
     }
-    if (vec && !bad) {
-        // a last chunk that ends inside an 8-symbol group
-        const uint64_t done = (i1 - i0) & ~7ull;
-        for (uint64_t i = i0 + done; i < i1; ++i) {
-            const int slot = (int)((i - i0) & 7);
-            out[i] = (uint16_t)((pk[slot >> 1] >> ((slot & 1) * 16)) & 0xffffu);
-        }
+    if (vec && !bad) {  // the last 0..3 symbols
+        for (uint32_t j = 0; j < pend; ++j) o[g + j] = (uint16_t)(acc >> (16 * j));
     }
-    if (bad || wb > we || ((total_bits + 31) >> 5) > we - wb) atomicOr(status, 4u);
+    if (bad || ((uint64_t)(used + 31) >> 5) > we - wb) atomicOr(status, 4u);
+    }
 }
 
-static size_t dec_sorted_bytes(uint32_t nsym) { return ((size_t)nsym * 2 + 15) & ~(size_t)15; }
+static size_t dec_smem_bytes(uint32_t nsym) { return ((size_t)1 << kLutBits) * 4 + (((size_t)nsym * 2 + 15) & ~(size_t)15); }
 
 }  // namespace vsz
 
@@ -632,13 +696,15 @@ vsz_status vsz_huffman_book(const uint32_t* d_hist, uint32_t nsym, void* d_book,
     if (!d_hist || !d_book || !aligned(d_book, 16) || book_bytes < huff_layout(nsym).total) return VSZ_ERR_INVALID_ARG;
     uint32_t np = 2;
     while (np < nsym) np <<= 1;
-    const size_t smem = book_smem_front(np) + ((size_t)1 << kLutBits) * 4;
+    const size_t smem = book_smem_front(np);
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = raise_smem_attr((const void*)k_huff_book, smem);
     if (e != cudaSuccess) return cuda_fail(e);
     {
         TraceScope ts("huff_book", s);
         k_huff_book<<<1, 1024, smem, s>>>(d_hist, nsym, d_book);
+        if ((e = cudaGetLastError()) == cudaSuccess)
+            k_huff_lut<<<(1u << kLutBits) / 256, 256, 0, s>>>(nsym, d_book);
     }
     e = cudaGetLastError();
     return e == cudaSuccess ? VSZ_OK : cuda_fail(e);
@@ -677,7 +743,8 @@ size_t vsz_huffman_encode_workspace_size(uint64_t n) {
 vsz_status vsz_huffman_encode(const uint16_t* d_sym, uint64_t n, const void* d_book, uint32_t nsym,
                               uint32_t* d_words, uint64_t word_cap, uint64_t* d_chunk_off, uint32_t* d_status,
                               void* d_ws, size_t ws_bytes, void* stream) {
-    if (nsym == 0 || nsym > kMaxSym || !d_book || !d_chunk_off || !d_status) return VSZ_ERR_INVALID_ARG;
+    if (nsym == 0 || nsym > kMaxSym || !d_book || !aligned(d_book, 16) || !d_chunk_off || !d_status)
+        return VSZ_ERR_INVALID_ARG;
     if (n > 0 && (!d_sym || (word_cap > 0 && !d_words))) return VSZ_ERR_INVALID_ARG;
     if (!d_ws || !aligned(d_ws, 8) || ws_bytes < vsz_huffman_encode_workspace_size(n)) return VSZ_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
@@ -713,18 +780,24 @@ vsz_status vsz_huffman_encode(const uint16_t* d_sym, uint64_t n, const void* d_b
 
 vsz_status vsz_huffman_decode(const uint32_t* d_words, uint64_t word_cap, const uint64_t* d_chunk_off, uint64_t n,
                               const void* d_book, uint32_t nsym, uint16_t* d_sym, uint32_t* d_status, void* stream) {
-    if (nsym == 0 || nsym > kMaxSym || !d_book || !d_chunk_off || !d_status) return VSZ_ERR_INVALID_ARG;
+    if (nsym == 0 || nsym > kMaxSym || !d_book || !aligned(d_book, 16) || !d_chunk_off || !d_status)
+        return VSZ_ERR_INVALID_ARG;
     if (n > 0 && (!d_sym || !d_words)) return VSZ_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaMemsetAsync(d_status, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return cuda_fail(e);
     const uint64_t nc = (n + kHC - 1) / kHC;
     if (nc == 0) return VSZ_OK;
-    const size_t smem = dec_sorted_bytes(nsym);
+    const size_t smem = dec_smem_bytes(nsym);
     if ((e = raise_smem_attr((const void*)k_huff_decode, smem)) != cudaSuccess) return cuda_fail(e);
+    // one CTA per SM (the table fills most of its shared memory), a thread
+    // per chunk, threads looping when there are more chunks than that
+    const uint64_t sms = (uint64_t)num_sms();
+    const uint64_t G = umin64(sms, (nc + 31) / 32);
+    const uint64_t T = umin64((uint64_t)kDecMaxThreads, ((nc + G - 1) / G + 31) / 32 * 32);
     {
         TraceScope ts("huff_decode", s, 0, 0, n);
-        k_huff_decode<<<(unsigned)((nc + kDecThreads - 1) / kDecThreads), kDecThreads, smem, s>>>(
+        k_huff_decode<<<(unsigned)G, (unsigned)T, smem, s>>>(
             d_words, word_cap, d_chunk_off, n, d_book, nsym, d_sym, d_status);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
     }

@@ -118,3 +118,59 @@ def test_limits():
     book = vsz.HuffmanBook(hist, 2)
     words, off, st = vsz.huffman_encode(torch.zeros(0, dtype=torch.int16, device="cuda"), 0, book)
     assert int(st.item()) == 0 and int(off[0].item()) == 0
+
+
+def _round_trip(sym, nsym, weights, sym_shift=0, words_shift=0, out_shift=0):
+    """Encode sym with the book of `weights`, compare with the oracle, decode
+    (optionally from views that start 2 or 4 bytes past a 16-byte boundary)."""
+    n = sym.size
+    book = vsz.HuffmanBook(torch.from_numpy(weights.view(np.int32)).cuda(), nsym)
+    lo, co = oracle.huffman_book(weights)
+    ow, ooff = oracle.huffman_encode(sym, lo, co)
+    base = torch.zeros(n + 8, dtype=torch.int16, device="cuda")
+    base[sym_shift: sym_shift + n] = torch.from_numpy(sym.view(np.int16)).cuda()
+    cap = torch.zeros(ow.size + 16, dtype=torch.int32, device="cuda")
+    words, off, st = vsz.huffman_encode(base[sym_shift: sym_shift + n], n, book, words=cap)
+    assert int(st.item()) == 0
+    goff = off.cpu().numpy().view(np.uint64)
+    assert np.array_equal(goff, ooff)
+    assert np.array_equal(words[: int(goff[-1])].cpu().numpy().view(np.uint32), ow)
+    wbuf = torch.zeros(words.numel() + 4, dtype=torch.int32, device="cuda")
+    wbuf[words_shift: words_shift + words.numel()] = words
+    obuf = torch.zeros(n + 8, dtype=torch.int16, device="cuda")
+    dec, st2 = vsz.huffman_decode(wbuf[words_shift: words_shift + words.numel()], off, n, book,
+                                  out=obuf[out_shift: out_shift + n])
+    assert int(st2.item()) == 0
+    assert np.array_equal(dec[:n].cpu().numpy().view(np.uint16), sym)
+    return words, off, book
+
+
+@pytest.mark.parametrize("n", [1, 1000, 3 * 1024 + 517])
+def test_long_codewords(n):
+    # Fibonacci weights give codewords up to 39 bits; symbols drawn uniformly
+    # make most codewords longer than the decoder's 12-bit table and many
+    # longer than 32 bits (split in the encoder, spanning buffer refills in
+    # the decoder)
+    weights = np.array(_fib(40), np.uint32)
+    sym = np.random.default_rng(n).integers(0, 40, n).astype(np.uint16)
+    _round_trip(sym, 40, weights)
+
+
+@pytest.mark.parametrize("shifts", [(1, 0, 0), (0, 1, 0), (0, 0, 1), (3, 2, 5)])
+def test_unaligned_views(shifts):
+    rng = np.random.default_rng(17)
+    n, nsym = 5 * 1024 + 77, 1024
+    sym = np.minimum(rng.geometric(0.05, n) - 1, nsym - 1).astype(np.uint16)
+    weights = np.bincount(sym, minlength=nsym).astype(np.uint32)
+    _round_trip(sym, nsym, weights, *shifts)
+
+
+def test_truncated_stream_is_reported():
+    rng = np.random.default_rng(5)
+    n, nsym = 8 * 1024, 256
+    sym = rng.integers(0, nsym, n).astype(np.uint16)
+    weights = np.bincount(sym, minlength=nsym).astype(np.uint32)
+    words, off, book = _round_trip(sym, nsym, weights)
+    total = int(off[-1].item())
+    _, st = vsz.huffman_decode(words[: total - 40], off, n, book)
+    assert int(st.item()) & 4
