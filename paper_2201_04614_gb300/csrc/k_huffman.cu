@@ -362,10 +362,11 @@ __global__ void __launch_bounds__(kEncThreads) k_huff_chunk_words(const uint16_t
         uint32_t v[kLaneSyms];
         load32(sym, n, c, lane, vec, v);
         const uint64_t i0 = c * kHC + (uint64_t)lane * kLaneSyms;
+        const uint32_t lim = i0 + kLaneSyms <= n ? (uint32_t)kLaneSyms : (uint32_t)(n > i0 ? n - i0 : 0);
         unsigned int bits = 0;
 #pragma unroll
         for (int k = 0; k < kLaneSyms; ++k) {
-            if (i0 + k < n) {
+            if ((uint32_t)k < lim) {
                 const uint32_t l = v[k] < nsym ? slen[v[k]] : 0u;
                 bad |= l == 0;
                 bits += l;
