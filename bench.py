@@ -56,6 +56,9 @@ def parse_args():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched+tuned vs plain comparison")
     ap.add_argument("--batch-steps", type=int, default=20)
     ap.add_argument("--no-entropy", action="store_true", help="skip the Huffman stage and rate-distortion curve")
+    ap.add_argument("--batch-profile", action="store_true",
+                    help="only a reduced mixed batch (6 CESM-shaped 2D, 2 Hurricane-shaped 3D and one 10M 1D "
+                         "field, default classes, eb 1e-4): a small case for ncu captures of the batch kernels")
     return ap.parse_args()
 
 
@@ -858,8 +861,63 @@ def run_gpu(a):
         dist.destroy_process_group()
 
 
+def run_batch_profile(a):
+    """A reduced copy of the 96-field mixed batch (the first 6 of its 1800x3600
+    fields, the first 2 of its 100x500x500 fields and the first of its 10M 1D
+    fields: 98,880,000 values, 396 MB, larger than L2), default classes, rel eb
+    1e-4, one autotuned graph plan; `steps` compressions and reconstructions
+    after `warmup`.  Prints one JSON line with the per-class kernel times the
+    autotuner measured and the plan's GB/s.  Meant as the driver of ncu
+    captures of the batch kernels (the full batches hold >10 GB on the
+    device)."""
+    import numpy as np
+    import torch
+    import paper_2201_04614_gb300 as vsz
+    import synth
+    specs = synth.cfg3_fields()
+    pick = [s for s in specs if s[0].startswith("cesm2d_")][:6] + \
+        [s for s in specs if s[0].startswith("hurricane3d_")][:2] + [s for s in specs if s[0].startswith("hacc1d_")][:1]
+    blocks = {1: 256, 2: 16, 3: 8}
+    xs = [torch.from_numpy(np.ascontiguousarray(mk(), np.float32).reshape(-1)).cuda() for _, _, mk in pick]
+    fields = [vsz.Field(vsz.Params.make(sh, blocks[len(sh)], 1e-4, "rel", 512, "zero"), out_cap=x.numel(),
+                        fix_cap=max(1 << 16, x.numel() // 64)) for (_, sh, _), x in zip(pick, xs)]
+    outs = [torch.empty(x.numel(), dtype=torch.float32, device="cuda") for x in xs]
+    stream = torch.cuda.Stream()
+    n = sum(x.numel() for x in xs)
+    with torch.cuda.stream(stream):
+        bt = vsz.Batch(fields, xs, use_graph=True)
+        bt.set_outputs(outs)
+        cls = bt.autotune(stream, reps=3)
+        for _ in range(a.warmup):
+            bt.submit(stream)
+            bt.reconstruct(stream)
+        stream.synchronize()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        for _ in range(a.steps):
+            bt.submit(stream)
+        e1.record(stream)
+        for _ in range(a.steps):
+            bt.reconstruct(stream)
+        e2.record(stream)
+        stream.synchronize()
+    ms_c, ms_r = e0.elapsed_time(e1) / a.steps, e1.elapsed_time(e2) / a.steps
+    bad = sum(int(f.header()["status"] != 0) for f in fields)
+    line = {"batch_profile": "6 x 1800x3600 + 2 x 100x500x500 + 1 x 10M of the mixed batch, rel eb 1e-4, zero "
+                             "padding, default blocks, autotuned graph plan",
+            "values": n, "steps": a.steps, "compress_ms": ms_c, "reconstruct_ms": ms_r,
+            "compress_GBps": n * 4 / ms_c / 1e6, "reconstruct_GBps": n * 4 / ms_r / 1e6, "status_nonzero": bad,
+            "classes": [{k: c[k] for k in ("kind", "ndim", "block", "warps", "ctas_per_sm", "ms", "ms_default")}
+                        for c in cls if c["tiles"]]}
+    print(json.dumps(line), flush=True)
+    bt.close()
+
+
 def main():
     a = parse_args()
+    if a.batch_profile:
+        run_batch_profile(a)
+        return
     if a.impl == "reference":
         run_reference(a)
     else:

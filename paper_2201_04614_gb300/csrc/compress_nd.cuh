@@ -85,7 +85,10 @@ struct NdCfg {
     static constexpr int THREADS = WARPS * 32;
     static constexpr int MINB_C = ZSMEM && B >= 32 ? 2 : VSZ_ND_MINB_C;  // caps registers
     static constexpr int MINB_R = VSZ_ND_MINB_R;
-    static constexpr int STASH = VSZ_ND_STASH;             // stash entries per warp
+    // stash entries per warp: a 3D tile holds 8192 (b 8) or 32768 (b 16)
+    // values, so those take what shared memory has left at the same
+    // resident CTAs per SM (4 and 3); 2D tiles (at most 4096) keep the default
+    static constexpr int STASH = (ND == 3 && B == 8) ? 384 : (ND == 3 && B == 16) ? 512 : VSZ_ND_STASH;
     static constexpr size_t ZS_B = ZSMEM ? (size_t)B * 32 * 16 : 0;
     // ring stages: the z state of 3D blocks of 32 leaves room for two
     static constexpr int NS = ZS_B > 8192 ? 2 : VSZ_ND_STAGES;

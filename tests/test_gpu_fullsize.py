@@ -90,3 +90,22 @@ def test_every_element_round_trips(run):
     assert float(err.max()) <= h["eb_abs"] * (1 + 2.0 ** -20)
     # outlier count equals the number of code-0 elements
     assert int((f.codes[: N ** 3] == 0).sum()) == h["n_out"]
+
+
+@pytest.mark.parametrize("pad", ["zero", "block_avg", "global_avg", "edge_avg"])
+def test_small_2d_workload_matches_oracle(pad):
+    """The 512x512 climate-like field (32 Fourier modes, |k|^-2, noise 1e-3 x
+    range), block 16x16, R = 512, relative eb 1e-4: the whole output of the
+    one-field path against the oracle, for zero and non-zero padding."""
+    x = synth.cfg1_field()
+    p = vsz.Params.make((512, 512), 16, 1e-4, "rel", 512, pad)
+    f = vsz.Field(p, out_cap=512 * 512, fix_cap=512 * 512)
+    f.compress(torch.from_numpy(x.reshape(-1)).cuda())
+    got = f.to_host()
+    po = oracle.Params((512, 512), 16, 1e-4, oracle.EB_REL, 512, oracle.PAD_NAMES[pad])
+    c = oracle.compress(po, x)
+    assert got["header"]["eb_abs"] == c.eb.eb_abs
+    for k in ("codes", "blk_off", "out_idx", "out_delta", "fix_idx", "fix_bits"):
+        assert np.array_equal(got[k], getattr(c, k)), k
+    xo = oracle.decompress(po, c).view(np.uint32)
+    assert np.array_equal(f.reconstruct()[: 512 * 512].cpu().numpy().view(np.uint32), xo)
