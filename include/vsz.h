@@ -303,8 +303,10 @@ VSZ_API vsz_status vsz_batch_set_concurrent(vsz_batch b, int on);
  * reconstruction when outputs are set), run its whole sequence `reps` times
  * (1..50) per candidate shape (warps 2, 4, 8 x CTAs per SM 1, 2, 4 and the
  * most that fit) and keep the shape with the smallest median device time of
- * the class kernel (the default shape unless another is faster); then time
- * each sequence serial and concurrent and keep the faster.  Synchronous: it
+ * the class kernel (the default shape unless another is faster); keep those
+ * shapes only if the whole sequence runs faster with them than with the
+ * default ones; then time each sequence serial and concurrent and keep the
+ * faster.  Synchronous: it
  * waits for its own runs on `stream`, which must not be capturing
  * (VSZ_ERR_INVALID_ARG).  It compresses (and reconstructs) the batch many
  * times, with the same results each time, and drops the cached graphs.

@@ -773,8 +773,31 @@ vsz_status vsz_batch_autotune(vsz_batch b, void* stream, int reps) {
     // median device time of `reps` runs of a sequence (kind 0 compression,
     // 1 reconstruction), with events around class `cls` or, when cls < 0,
     // around the whole sequence
+    // A whole sequence (cls < 0) of a graph plan is timed as the plan runs
+    // it: its graph is captured again for the current shapes and replayed.
+    const bool graphs = b->use_graph && s != nullptr && s != cudaStreamLegacy && !Tracer::get().on();
     auto measure = [&](int kind, int cls, float* ms) -> vsz_status {
         std::vector<float> t;
+        if (cls < 0 && graphs) {
+            drop_graphs(b);
+            const vsz_status sw = kind ? vsz_batch_reconstruct(b, s) : vsz_batch_submit(b, s);  // builds the graph
+            if (sw != VSZ_OK) return sw;
+            for (int r = 0; r < reps; ++r) {
+                cudaError_t e2 = cudaEventRecord(tm.e0, s);
+                if (e2 != cudaSuccess) return cuda_fail(e2);
+                const vsz_status st2 = kind ? vsz_batch_reconstruct(b, s) : vsz_batch_submit(b, s);
+                if (st2 != VSZ_OK) return st2;
+                if ((e2 = cudaEventRecord(tm.e1, s)) != cudaSuccess) return cuda_fail(e2);
+                if ((e2 = cudaEventSynchronize(tm.e1)) != cudaSuccess) return cuda_fail(e2);
+                float v = 0.0f;
+                if ((e2 = cudaEventElapsedTime(&v, tm.e0, tm.e1)) != cudaSuccess) return cuda_fail(e2);
+                t.push_back(v);
+            }
+            drop_graphs(b);
+            std::sort(t.begin(), t.end());
+            *ms = t[t.size() / 2];
+            return VSZ_OK;
+        }
         for (int r = 0; r < reps; ++r) {
             tm.kind = kind;
             tm.cls = cls;
@@ -798,6 +821,7 @@ vsz_status vsz_batch_autotune(vsz_batch b, void* stream, int reps) {
     vsz_status st = launch_sequence(b, s);  // warm-up; the compressed data the inverse reads
     for (int kind = 0; kind < 2 && st == VSZ_OK; ++kind) {
         std::vector<BatchClass>& cls = kind ? b->rclasses : b->classes;
+        if (cls.empty() || (kind && !b->d_fix)) continue;  // no outputs set: nothing to reconstruct
         for (size_t c = 0; st == VSZ_OK && c < cls.size(); ++c) {
             BatchClass& k = cls[c];
             if (!k.total_tiles) continue;
@@ -828,6 +852,24 @@ vsz_status vsz_batch_autotune(vsz_batch b, void* stream, int reps) {
             k.ms_best = best;
         }
         if (st != VSZ_OK) break;
+        // Events around one class kernel break its overlap with its
+        // neighbours in the sequence, so keep the tuned shapes only if the
+        // whole sequence is faster with them than with the default ones.
+        bool changed = false;
+        for (const BatchClass& k : cls) changed |= k.shape.warps != 0 || k.shape.ctas != 0;
+        if (changed) {
+            std::vector<LaunchShape> tuned;
+            for (const BatchClass& k : cls) tuned.push_back(k.shape);
+            float t_tuned = 0.0f, t_def = 0.0f;
+            if ((st = measure(kind, -1, &t_tuned)) != VSZ_OK) break;
+            for (BatchClass& k : cls) k.shape = LaunchShape{};
+            if ((st = measure(kind, -1, &t_def)) != VSZ_OK) break;
+            if (t_tuned < t_def) {
+                for (size_t c = 0; c < cls.size(); ++c) cls[c].shape = tuned[c];
+            } else {
+                for (BatchClass& k : cls) k.ms_best = k.ms_default;
+            }
+        }
         int active = 0;
         for (const BatchClass& k : cls) active += k.total_tiles ? 1 : 0;
         if (active > 1) {
@@ -844,6 +886,7 @@ vsz_status vsz_batch_autotune(vsz_batch b, void* stream, int reps) {
         b->concurrent = conc0;
         b->rconcurrent = rconc0;
     }
+    drop_graphs(b);
     cudaEventDestroy(tm.e0);
     cudaEventDestroy(tm.e1);
     return st;
