@@ -152,55 +152,64 @@ __global__ void __launch_bounds__(256) k_fixups(const vsz_header* hdr, const uin
     }
 }
 
-// Code histogram: per-CTA shared-memory bins when they fit, else global.
-__global__ void __launch_bounds__(256) k_histogram(const uint16_t* __restrict__ codes, uint64_t n,
-                                                   uint32_t* hist, uint32_t nbins, int use_smem) {
-    extern __shared__ uint32_t sh[];
-    if (use_smem) {
-        for (uint32_t i = threadIdx.x; i < nbins; i += blockDim.x) sh[i] = 0;
-        __syncthreads();
-    }
-    // Codes cluster around R (small residuals): the 16 bins from R-8 count in
-    // packed 8-bit register counters, flushed every 248 codes; other codes
-    // add one at a time.  Eight codes per 16-byte load.
-    const uint32_t R = nbins / 2, base = R >= 8 ? R - 8 : 0;
-    unsigned long long lo = 0, hi = 0;
-    uint32_t pending = 0;
-    auto put = [&](uint32_t c, uint32_t k) { if (use_smem) atomicAdd(&sh[c], k); else atomicAdd(&hist[c], k); };
-    auto flush = [&]() {
+// Code histogram.  Codes cluster around R (small residuals): the kHistWin
+// bins from R - kHistWin/2 count in lane-private 32-bit counters in shared
+// memory (column `lane` of the warp's table, so a lane's increments need no
+// atomic and never share a bank with another lane's); every other code adds
+// with an atomic to the CTA's bins (shared memory when they fit, else
+// global).  At the end each warp sums its table's columns into the bins.
+constexpr int kHistWin = 64;
+constexpr int kHistThreads = 256;
+__global__ void __launch_bounds__(kHistThreads) k_histogram(const uint16_t* __restrict__ codes, uint64_t n,
+                                                            uint32_t* hist, uint32_t nbins, int use_smem) {
+    extern __shared__ uint32_t sm[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t* tab = sm + (size_t)warp * kHistWin * 32;   // [kHistWin][32] of this warp
+    uint32_t* sh = sm + (size_t)(kHistThreads / 32) * kHistWin * 32;  // [nbins] when use_smem
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const uint32_t a = (uint32_t)(lo >> (8 * k)) & 255u, b = (uint32_t)(hi >> (8 * k)) & 255u;
-            if (a) put(base + k, a);
-            if (b) put(base + 8 + k, b);
-        }
-        lo = hi = 0;
-        pending = 0;
-    };
+    for (int k = 0; k < kHistWin; ++k) tab[k * 32 + lane] = 0;
+    if (use_smem)
+        for (uint32_t i = threadIdx.x; i < nbins; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+    const uint32_t R = nbins / 2, base = R >= kHistWin / 2 ? R - kHistWin / 2 : 0;
+    auto put = [&](uint32_t c, uint32_t k) { if (use_smem) atomicAdd(&sh[c], k); else atomicAdd(&hist[c], k); };
     auto add = [&](uint32_t c) {
         const uint32_t k = c - base;
-        if (k < 8 && base + k < nbins) lo += 1ull << (8 * k);
-        else if (k < 16 && base + k < nbins) hi += 1ull << (8 * (k - 8));
+        if (k < (uint32_t)kHistWin && c < nbins) tab[k * 32 + lane] += 1u;
         else if (c < nbins) put(c, 1u);
     };
-    const uint64_t nth = (uint64_t)gridDim.x * blockDim.x, tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool vec = (reinterpret_cast<uintptr_t>(codes) & 15) == 0;
-    const uint64_t n8 = vec ? n / 8 : 0;
-    for (uint64_t j = tid; j < n8; j += nth) {
-        const uint4 v = *reinterpret_cast<const uint4*>(codes + 8 * j);
+    auto add8 = [&](const uint4 v) {
         const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             add(w[k] & 0xffffu);
             add(w[k] >> 16);
         }
-        if ((pending += 8) >= 248) flush();
+    };
+    const uint64_t nth = (uint64_t)gridDim.x * blockDim.x, tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool vec = (reinterpret_cast<uintptr_t>(codes) & 15) == 0;
+    const uint64_t n8 = vec ? n / 8 : 0;
+    uint64_t j = tid;
+    for (; j + 3 * nth < n8; j += 4 * nth) {  // four 16-byte loads in flight
+        uint4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = *reinterpret_cast<const uint4*>(codes + 8 * (j + u * nth));
+#pragma unroll
+        for (int u = 0; u < 4; ++u) add8(v[u]);
     }
-    for (uint64_t j = 8 * n8 + tid; j < n; j += nth) {
-        add(codes[j]);
-        if (++pending >= 248) flush();
+    for (; j < n8; j += nth) add8(*reinterpret_cast<const uint4*>(codes + 8 * j));
+    for (uint64_t i = 8 * n8 + tid; i < n; i += nth) add(codes[i]);
+    __syncwarp();
+    // bin base + k (k = lane, lane + 32): the sum of row k over the warp's
+    // 32 columns, read in a rotated order so that the lanes hit 32 banks
+#pragma unroll
+    for (int h = 0; h < kHistWin / 32; ++h) {
+        const uint32_t k = (uint32_t)(h * 32 + lane);
+        uint32_t sum = 0;
+#pragma unroll 8
+        for (int c = 0; c < 32; ++c) sum += tab[k * 32 + ((c + lane) & 31)];
+        if (sum && base + k < nbins) put(base + k, sum);
     }
-    flush();
     if (use_smem) {
         __syncthreads();
         for (uint32_t i = threadIdx.x; i < nbins; i += blockDim.x)
@@ -259,14 +268,14 @@ cudaError_t launch_fixups(const vsz_header* hdr, const uint32_t* fix_idx, const 
 cudaError_t launch_histogram(const uint16_t* codes, uint64_t n, uint32_t* hist, uint32_t nbins, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(hist, 0, (size_t)nbins * 4, s);
     if (e != cudaSuccess || n == 0) return e;
-    const size_t smem = (size_t)nbins * 4;
-    const int use_smem = smem <= 96 * 1024;
-    if (use_smem && smem > 48 * 1024) {
-        e = cudaFuncSetAttribute((const void*)k_histogram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    const int grid = grid_for((const void*)k_histogram, 256, use_smem ? smem : 0, 256 * 128, n);
-    k_histogram<<<grid, 256, use_smem ? smem : 0, s>>>(codes, n, hist, nbins, use_smem);
+    const size_t tab = (size_t)(kHistThreads / 32) * kHistWin * 32 * 4;  // the warps' window tables
+    const int use_smem = (size_t)nbins * 4 <= 96 * 1024;
+    const size_t smem = tab + (use_smem ? (size_t)nbins * 4 : 0);
+    if ((e = raise_smem_attr((const void*)k_histogram, smem)) != cudaSuccess) return e;
+    const int occ = occupancy((const void*)k_histogram, kHistThreads, smem);
+    const uint64_t want = (n + (uint64_t)kHistThreads * 128 - 1) / ((uint64_t)kHistThreads * 128);
+    const int grid = (int)umin64(want, (uint64_t)num_sms() * (uint64_t)(occ > 0 ? occ : 1));
+    k_histogram<<<grid, kHistThreads, smem, s>>>(codes, n, hist, nbins, use_smem);
     return cudaGetLastError();
 }
 

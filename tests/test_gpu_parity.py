@@ -302,7 +302,8 @@ def test_reconstruct_with_and_without_workspace_agree():
 @pytest.mark.parametrize("R,n,kind,offset", [(512, 1_000_003, "peaked", 0), (4, 10007, "uniform", 0),
                                              (2, 999, "const", 0), (512, 300_001, "const", 0),
                                              (32768, 200_000, "uniform", 0), (512, 77_777, "peaked", 1),
-                                             (7, 5000, "peaked", 3)])
+                                             (7, 5000, "peaked", 3), (512, 2_000_017, "wide", 0),
+                                             (40, 100_000, "wide", 2), (4096, 300_000, "wide", 0)])
 def test_code_histogram_synthetic(R, n, kind, offset):
     """Histogram of arbitrary code arrays: counts per bin equal numpy's, codes
     at or above 2R are not counted, any alignment of the codes."""
@@ -312,6 +313,8 @@ def test_code_histogram_synthetic(R, n, kind, offset):
         c = rng.integers(0, 2 * R + 3, n)
     elif kind == "const":
         c = np.full(n, R)
+    elif kind == "wide":  # partly outside the bins counted without atomics
+        c = np.clip(np.round(rng.normal(R, 40.0, n)), 0, 2 * R + 5)
     else:
         c = np.clip(np.round(rng.normal(R, 3.0, n)), 0, 2 * R + 5)
     c = c.astype(np.uint16)
