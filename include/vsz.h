@@ -590,6 +590,16 @@ VSZ_API vsz_status vsz_read_header(const vsz_compressed* c, vsz_header* h_out, v
  * Synchronizes the stream; a failing copy returns VSZ_ERR_CUDA. */
 VSZ_API vsz_status vsz_sync_status(const vsz_compressed* c, void* stream);
 
+/* Release what the library holds itself: tracing is switched off, pending
+ * trace records are dropped and the recorder's CUDA events destroyed, and
+ * the per-device and per-kernel caches of launch parameters (SM counts,
+ * occupancies, shared-memory limits already raised) are cleared, so that the
+ * library works again after the caller resets the device.  Buffers and batch
+ * plans are the caller's (vsz_batch_destroy releases a plan).  Call it with
+ * no library call in flight on any thread; later calls rebuild the caches.
+ * Always VSZ_OK. */
+VSZ_API vsz_status vsz_shutdown(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -83,7 +83,7 @@ EXPORTED = ["vsz_status_string", "vsz_last_cuda_error", "vsz_abi_version", "vsz_
             "vsz_batch_set_concurrent", "vsz_batch_autotune", "vsz_batch_set_outputs", "vsz_batch_reconstruct",
             "vsz_huffman_book_bytes", "vsz_huffman_book", "vsz_huffman_book_read", "vsz_huffman_encode",
             "vsz_huffman_encode_workspace_size", "vsz_sampling_autotune_workspace_size", "vsz_sampling_autotune",
-            "vsz_sync_status",
+            "vsz_sync_status", "vsz_shutdown",
             "vsz_huffman_decode",
             "vsz_tuner_features_workspace_size", "vsz_tuner_features",
             "vsz_tuner_sweep_workspace_size", "vsz_tuner_sweep", "vsz_tuner_guard_workspace_size",
@@ -534,6 +534,13 @@ class HuffmanBook:
         _check(lib().vsz_huffman_book_read(_ptr(self.buf), self.nsym, ln.ctypes.data, cw.ctypes.data,
                                            ctypes.byref(mx), _stream_handle(stream)), "vsz_huffman_book_read")
         return ln, cw, int(mx.value)
+
+
+def shutdown() -> None:
+    """vsz_shutdown: switch tracing off, destroy the library's own CUDA
+    events and clear its cached launch parameters (for use after a device
+    reset).  No library call may be in flight."""
+    _check(lib().vsz_shutdown(), "vsz_shutdown")
 
 
 def huffman_encode(sym, n: int, book: HuffmanBook, words=None, stream=None):

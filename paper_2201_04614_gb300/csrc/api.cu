@@ -13,33 +13,51 @@
 
 namespace vsz {
 
+// Per-device and per-kernel caches of launch parameters (vsz_shutdown
+// clears them, so that the library works again after a device reset).
+namespace {
+std::mutex g_cache_mu;
+int g_num_sms[64] = {0};
+std::unordered_map<const void*, int> g_grid_occ;                     // grid_for
+std::map<std::tuple<const void*, int, size_t>, int> g_occ;           // occupancy
+std::map<std::pair<int, const void*>, size_t> g_smem_attr;           // raise_smem_attr
+void* g_noalloc_addr[64] = {nullptr};                                 // noalloc_workspace
+}  // namespace
+
+void reset_launch_caches() {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    for (int& v : g_num_sms) v = 0;
+    g_grid_occ.clear();
+    g_occ.clear();
+    g_smem_attr.clear();
+    for (void*& p : g_noalloc_addr) p = nullptr;
+}
+
 int num_sms() {
-    static int cached[64] = {0};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
-    if (!cached[dev]) {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    if (!g_num_sms[dev]) {
         int v = 0;
         if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 148;
-        cached[dev] = v;
+        g_num_sms[dev] = v;
     }
-    return cached[dev];
+    return g_num_sms[dev];
 }
 
 // CTAs for a grid-stride kernel: enough to cover `work` at `per_cta` items
 // each, capped at the number of CTAs that are resident at once.
 int grid_for(const void* kernel, int threads, size_t smem, uint64_t per_cta, uint64_t work) {
-    static std::mutex mu;
-    static std::unordered_map<const void*, int> occ_cache;
     int occ = 0;
     {
-        std::lock_guard<std::mutex> lk(mu);
-        auto it = occ_cache.find(kernel);
-        if (it != occ_cache.end()) {
+        std::lock_guard<std::mutex> lk(g_cache_mu);
+        auto it = g_grid_occ.find(kernel);
+        if (it != g_grid_occ.end()) {
             occ = it->second;
         } else {
             if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, smem) != cudaSuccess || occ < 1)
                 occ = 1;
-            occ_cache[kernel] = occ;
+            g_grid_occ[kernel] = occ;
         }
     }
     const uint64_t want = (work + per_cta - 1) / (per_cta ? per_cta : 1);
@@ -50,18 +68,16 @@ int grid_for(const void* kernel, int threads, size_t smem, uint64_t per_cta, uin
 }
 
 int occupancy(const void* kernel, int threads, size_t smem) {
-    static std::mutex mu;
-    static std::map<std::tuple<const void*, int, size_t>, int> cache;
     const auto key = std::make_tuple(kernel, threads, smem);
-    std::lock_guard<std::mutex> lk(mu);
-    auto it = cache.find(key);
-    if (it != cache.end()) return it->second;
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    auto it = g_occ.find(key);
+    if (it != g_occ.end()) return it->second;
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, smem) != cudaSuccess) {
         (void)cudaGetLastError();
         occ = 0;
     }
-    cache[key] = occ;
+    g_occ[key] = occ;
     return occ;
 }
 
@@ -77,8 +93,6 @@ int grid_shape(const void* kernel, int threads, size_t smem, uint64_t per_cta, u
 }
 
 cudaError_t raise_smem_attr(const void* kernel, size_t bytes) {
-    static std::mutex mu;
-    static std::map<std::pair<int, const void*>, size_t> set;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -86,8 +100,8 @@ cudaError_t raise_smem_attr(const void* kernel, size_t bytes) {
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
     if (bytes > (size_t)optin) return cudaErrorInvalidValue;
-    std::lock_guard<std::mutex> lk(mu);
-    size_t& cur = set[std::make_pair(dev, kernel)];
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    size_t& cur = g_smem_attr[std::make_pair(dev, kernel)];
     if (bytes <= cur) return cudaSuccess;
     e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e == cudaSuccess) cur = bytes;
@@ -172,20 +186,18 @@ static __device__ __align__(256) unsigned char g_noalloc_ws[VSZ_NOALLOC_WS_BYTES
 // device.  In host code the array's name is only a host-side stand-in, so
 // kernels must get this address, never the name.
 static vsz_status noalloc_workspace(void** out) {
-    static std::mutex mu;
-    static void* addr[64] = {nullptr};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e);
     if (dev < 0 || dev >= 64) return VSZ_ERR_UNSUPPORTED;
-    std::lock_guard<std::mutex> lk(mu);
-    if (!addr[dev]) {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    if (!g_noalloc_addr[dev]) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_ws);
         if (e != cudaSuccess) return cuda_fail(e);
-        addr[dev] = p;
+        g_noalloc_addr[dev] = p;
     }
-    *out = addr[dev];
+    *out = g_noalloc_addr[dev];
     return VSZ_OK;
 }
 
@@ -429,6 +441,12 @@ vsz_status vsz_code_histogram(const vsz_params* p, const uint16_t* d_codes, uint
         e = launch_histogram(d_codes, g.n, d_hist, 2u * p->radius, (cudaStream_t)stream);
     }
     if (e != cudaSuccess) return cuda_fail(e);
+    return VSZ_OK;
+}
+
+vsz_status vsz_shutdown(void) {
+    Tracer::get().shutdown();
+    reset_launch_caches();
     return VSZ_OK;
 }
 

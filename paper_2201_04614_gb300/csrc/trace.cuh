@@ -82,6 +82,19 @@ public:
         return k;
     }
 
+    // Tracing off; drops the pending records and destroys every event.
+    void shutdown() {
+        std::lock_guard<std::mutex> lk(mu_);
+        on_ = false;
+        for (const TraceRec& r : pending_) {
+            if (r.a) cudaEventDestroy(r.a);
+            if (r.b) cudaEventDestroy(r.b);
+        }
+        pending_.clear();
+        for (cudaEvent_t e : pool_) cudaEventDestroy(e);
+        pool_.clear();
+    }
+
 private:
     std::mutex mu_;
     bool on_ = false;

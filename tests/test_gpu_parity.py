@@ -327,3 +327,30 @@ def test_code_histogram_synthetic(R, n, kind, offset):
     assert rc == 0
     want = np.bincount(c[c < 2 * R], minlength=2 * R)
     assert np.array_equal(hist.cpu().numpy().astype(np.int64), want)
+
+
+def test_trace_and_shutdown():
+    """Launch tracing records every kernel of a compression with its device
+    time; vsz_shutdown switches tracing off and clears the library's caches,
+    after which calls work again and give the same results."""
+    x = torch.from_numpy(np.exp(synth.grf3d((40, 64, 96), 5)).astype(np.float32).reshape(-1)).cuda()
+    p = vsz.Params.make((40, 64, 96), 8, 1e-4, "rel", 512, "zero")
+    f = vsz.Field(p)
+    vsz.trace_read()
+    vsz.trace_enable(True)
+    f.compress(x)
+    recs = vsz.trace_read()
+    names = [r["name"] for r in recs]
+    assert "lorenzo" in names and "range" in names, names
+    assert all(r["ms"] >= 0.0 for r in recs)
+    first = f.to_host()
+    vsz.shutdown()
+    f.compress(x)
+    assert vsz.trace_read() == []  # tracing is off after shutdown
+    again = f.to_host()
+    for key in ("codes", "blk_off", "out_idx", "out_delta"):
+        assert np.array_equal(first[key], again[key]), key
+    vsz.trace_enable(True)
+    f.reconstruct()
+    assert len(vsz.trace_read()) > 0
+    vsz.trace_enable(False)
