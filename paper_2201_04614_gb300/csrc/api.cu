@@ -24,7 +24,7 @@ std::map<std::pair<int, const void*>, size_t> g_smem_attr;           // raise_sm
 void* g_noalloc_addr[64] = {nullptr};                                 // noalloc_workspace
 }  // namespace
 
-void reset_launch_caches() {
+static void reset_launch_caches() {
     std::lock_guard<std::mutex> lk(g_cache_mu);
     for (int& v : g_num_sms) v = 0;
     g_grid_occ.clear();

@@ -310,7 +310,6 @@ cudaError_t launch_recon_batch_3d(uint32_t b, const ReconArgs* fields, const uin
                                   int* occ = nullptr);
 
 int num_sms();
-void reset_launch_caches();  // vsz_shutdown
 int grid_for(const void* kernel, int threads, size_t smem, uint64_t work_items_per_cta, uint64_t work);
 // Resident CTAs per SM of `kernel` at this block size and dynamic shared
 // memory (0 if it cannot launch), cached per (kernel, threads, smem).
