@@ -394,8 +394,9 @@ VSZ_API vsz_status vsz_code_histogram(const vsz_params* p, const uint16_t* d_cod
 VSZ_API size_t vsz_huffman_book_bytes(uint32_t nsym);
 
 /* Build the codebook of d_hist[nsym] (uint32 counts, device) into d_book
- * (device, 16-byte aligned, vsz_huffman_book_bytes(nsym) bytes; opaque) on
- * one CTA.  VSZ_ERR_UNSUPPORTED if nsym > VSZ_HUFF_MAX_SYMBOLS. */
+ * (device, 16-byte aligned, vsz_huffman_book_bytes(nsym) bytes; opaque):
+ * one CTA builds the tree, lengths and codewords, a second kernel the
+ * decoder's lookup table.  VSZ_ERR_UNSUPPORTED if nsym > VSZ_HUFF_MAX_SYMBOLS. */
 VSZ_API vsz_status vsz_huffman_book(const uint32_t* d_hist, uint32_t nsym, void* d_book, size_t book_bytes,
                                     void* stream);
 
