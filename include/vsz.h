@@ -591,6 +591,14 @@ VSZ_API vsz_status vsz_read_header(const vsz_compressed* c, vsz_header* h_out, v
  * Synchronizes the stream; a failing copy returns VSZ_ERR_CUDA. */
 VSZ_API vsz_status vsz_sync_status(const vsz_compressed* c, void* stream);
 
+/* Failure injection for tests (host side; no kernel is involved): the k-th
+ * device allocation the library makes for itself from now on (the tables
+ * of vsz_batch_create and vsz_batch_set_outputs) fails as if the device
+ * were out of memory, and the call that made it returns VSZ_ERR_CUDA after
+ * releasing what it had allocated.  k = 0 switches it off; negative k is
+ * VSZ_ERR_INVALID_ARG. */
+VSZ_API vsz_status vsz_debug_fail_alloc(int k);
+
 /* Release what the library holds itself: tracing is switched off, pending
  * trace records are dropped and the recorder's CUDA events destroyed, and
  * the per-device and per-kernel caches of launch parameters (SM counts,

@@ -83,7 +83,7 @@ EXPORTED = ["vsz_status_string", "vsz_last_cuda_error", "vsz_abi_version", "vsz_
             "vsz_batch_set_concurrent", "vsz_batch_autotune", "vsz_batch_set_outputs", "vsz_batch_reconstruct",
             "vsz_huffman_book_bytes", "vsz_huffman_book", "vsz_huffman_book_read", "vsz_huffman_encode",
             "vsz_huffman_encode_workspace_size", "vsz_sampling_autotune_workspace_size", "vsz_sampling_autotune",
-            "vsz_sync_status", "vsz_shutdown",
+            "vsz_sync_status", "vsz_shutdown", "vsz_debug_fail_alloc",
             "vsz_huffman_decode",
             "vsz_tuner_features_workspace_size", "vsz_tuner_features",
             "vsz_tuner_sweep_workspace_size", "vsz_tuner_sweep", "vsz_tuner_guard_workspace_size",

@@ -2,6 +2,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -23,6 +24,21 @@ std::map<std::tuple<const void*, int, size_t>, int> g_occ;           // occupanc
 std::map<std::pair<int, const void*>, size_t> g_smem_attr;           // raise_smem_attr
 void* g_noalloc_addr[64] = {nullptr};                                 // noalloc_workspace
 }  // namespace
+
+// Failure injection for tests: the k-th library device allocation from the
+// call of vsz_debug_fail_alloc(k) fails as if the device were out of memory.
+static std::atomic<int> g_fail_alloc{0};
+
+cudaError_t lib_malloc(void** p, size_t bytes) {
+    int k = g_fail_alloc.load();
+    while (k > 0 && !g_fail_alloc.compare_exchange_weak(k, k - 1)) {
+    }
+    if (k == 1) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
 
 static void reset_launch_caches() {
     std::lock_guard<std::mutex> lk(g_cache_mu);
@@ -441,6 +457,12 @@ vsz_status vsz_code_histogram(const vsz_params* p, const uint16_t* d_codes, uint
         e = launch_histogram(d_codes, g.n, d_hist, 2u * p->radius, (cudaStream_t)stream);
     }
     if (e != cudaSuccess) return cuda_fail(e);
+    return VSZ_OK;
+}
+
+vsz_status vsz_debug_fail_alloc(int k) {
+    if (k < 0) return VSZ_ERR_INVALID_ARG;
+    g_fail_alloc.store(k);
     return VSZ_OK;
 }
 

@@ -28,6 +28,7 @@
 
 #include "common.cuh"
 #include "compact.cuh"
+#include "misc.cuh"
 #include "memops.cuh"
 #include "stats.cuh"
 #include "trace.cuh"
@@ -308,7 +309,7 @@ static void free_batch(vsz_batch_st* b) {
 
 template <typename T>
 static cudaError_t upload(T** dst, const std::vector<T>& v) {
-    cudaError_t e = cudaMalloc((void**)dst, sizeof(T) * (v.empty() ? 1 : v.size()));
+    cudaError_t e = lib_malloc((void**)dst, sizeof(T) * (v.empty() ? 1 : v.size()));
     if (e != cudaSuccess) return e;
     if (!v.empty()) e = cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
     return e;

@@ -15,5 +15,8 @@ cudaError_t launch_origin_fix(const CompressArgs& a, cudaStream_t s);
 cudaError_t launch_fixups(const vsz_header* hdr, const uint32_t* fix_idx, const uint32_t* fix_bits,
                           uint64_t fix_cap, float* xhat, uint64_t n, cudaStream_t s);
 cudaError_t launch_histogram(const uint16_t* codes, uint64_t n, uint32_t* hist, uint32_t nbins, cudaStream_t s);
+// cudaMalloc of the library's own tables, with the failure injection of
+// vsz_debug_fail_alloc (api.cu)
+cudaError_t lib_malloc(void** p, size_t bytes);
 
 }  // namespace vsz

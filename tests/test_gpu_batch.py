@@ -251,3 +251,55 @@ def test_autotune_cache_round_trip(tmp_path):
     _assert_same(fields, want, "cached shapes")
     b1.close()
     b2.close()
+
+
+def test_allocation_failure_injection():
+    """Each device allocation that batch creation and vsz_batch_set_outputs
+    make for their tables can fail (injected on the host): the call raises
+    VSZ_ERR_CUDA after releasing what it had allocated, the library stays
+    usable, and a plan built afterwards gives the per-field results."""
+    L = vsz.lib()
+    fields, xs = _make()
+    ref_fields, _ = _make()
+    for f, x in zip(ref_fields, xs):
+        f.compress(x)
+    want = [_host(f) for f in ref_fields]
+    failed = 0
+    try:
+        for k in range(1, 200):
+            assert L.vsz_debug_fail_alloc(k) == 0
+            try:
+                b = vsz.Batch(fields, xs, use_graph=False)
+            except vsz.VszError as e:
+                assert e.status == 4
+                failed += 1
+                continue
+            break
+        else:
+            raise AssertionError("creation never succeeded")
+        assert failed >= 1
+        outs = _outs(fields)
+        failed_out = 0
+        for k in range(1, 200):
+            assert L.vsz_debug_fail_alloc(k) == 0
+            try:
+                b.set_outputs(outs)
+            except vsz.VszError as e:
+                assert e.status == 4
+                failed_out += 1
+                continue
+            break
+        assert failed_out >= 1
+    finally:
+        assert L.vsz_debug_fail_alloc(0) == 0
+    b.submit()
+    b.reconstruct()
+    torch.cuda.synchronize()
+    for i, (f, w) in enumerate(zip(fields, want)):
+        got = _host(f)
+        for key in ("codes", "blk_off", "out_idx", "out_delta"):
+            assert np.array_equal(got[key], w[key]), (MIX[i], key)
+        if f.n:
+            single = f.reconstruct().cpu().numpy().view(np.uint32)
+            assert np.array_equal(outs[i][: f.n].cpu().numpy().view(np.uint32), single), MIX[i]
+    b.close()
