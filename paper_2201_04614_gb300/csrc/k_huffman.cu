@@ -6,16 +6,17 @@
 // shared memory, then the two-queue Huffman merge (ties: the leaf first, so
 // equal weights resolve leaves before merged nodes, leaves in symbol order,
 // merged nodes in merge order), depths, canonical codewords (symbols sorted
-// by (length, symbol) get consecutive codes), and the decoder's tables.
+// by (length, symbol) get consecutive codes), and the canonical ranges; a
+// second, many-CTA kernel fills the decoder's lookup table.
 //
 // Stream: chunks of VSZ_HUFF_CHUNK symbols, each starting on a 32-bit word,
 // bits filling each word from its most significant bit; chunk_off[c] is the
 // first word of chunk c.  Encoding: per-chunk bit counts, a scan into word
 // offsets, then one warp per chunk (32 symbols per lane) packs its codewords
 // into shared memory and stores the words.
-// Decoding: one thread per chunk walks its bits with a 2^12-entry lookup
-// table (two codewords per entry when both fit, for alphabets up to 4096
-// symbols) and the canonical ranges for longer codewords, over a two-word
+// Decoding: one thread per chunk (one CTA per SM) walks its bits with a
+// 2^15-entry lookup table in shared memory (two codewords per entry when
+// both fit, for alphabets up to 4096 symbols) and the canonical ranges for longer codewords, over a two-word
 // window fed by aligned 16-byte loads issued ahead of use.
 #include <climits>
 
