@@ -297,24 +297,69 @@ __device__ __forceinline__ void edge_stats_unit(const CompressArgs& a, uint64_t 
         mn[f] = min(mn[f], v);
         mx[f] = max(mx[f], v);
     };
-    for (int lz = 0; lz < zlen; ++lz) {
-        for (int ly = 0; ly < ylen; ++ly) {
-            const bool face_row = ly == 0 || (nd == 3 && lz == 0);
-            const float* row = a.x + base + (uint64_t)lz * plane + (uint64_t)ly * nx;
-            int32_t q[4];
-            int cnt = 0;
-            if (face_row) {
-                for (int k = 0; k < valid; ++k) q[k] = prequant(row[k], inv2eb);
-                cnt = valid;
-            } else if (glane == 0 && valid > 0) {
-                q[0] = prequant(row[0], inv2eb);
-                cnt = 1;
+    // Face rows (every row of the first plane, the first row of the other
+    // planes) carry the y and z faces: the lane's 4 values, eight rows'
+    // loads issued before any is used.  The other rows carry only the x face:
+    // one value on the block's first lane, 32 rows' loads at a time.
+    const bool vec4 = valid == 4 && (reinterpret_cast<uintptr_t>(a.x) & 15) == 0 && (nx & 3) == 0;
+    auto row_ptr = [&](int lz, int ly) { return a.x + base + (uint64_t)lz * plane + (uint64_t)ly * nx; };
+    if (valid > 0) {
+        const int nface = nd == 3 ? ylen + zlen - 1 : 1;  // face row i: plane 0 row i, then plane i-ylen+1 row 0
+        constexpr int RF = 8;
+        for (int i0 = 0; i0 < nface; i0 += RF) {
+            float v[RF][4];
+#pragma unroll
+            for (int r = 0; r < RF; ++r) {
+                const int i = i0 + r;
+                const int lz = i < ylen ? 0 : i - ylen + 1, ly = i < ylen ? i : 0;
+                v[r][0] = v[r][1] = v[r][2] = v[r][3] = 0.0f;
+                if (i < nface) {
+                    const float* row = row_ptr(lz, ly);
+                    if (vec4) {
+                        const float4 f = __ldg(reinterpret_cast<const float4*>(row));
+                        v[r][0] = f.x;
+                        v[r][1] = f.y;
+                        v[r][2] = f.z;
+                        v[r][3] = f.w;
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            if (k < valid) v[r][k] = __ldg(row + k);
+                    }
+                }
             }
-            if (glane == 0 && cnt > 0) take(0, q[0]);
-            if (ly == 0)
-                for (int k = 0; k < cnt; ++k) take(1, q[k]);
-            if (nd == 3 && lz == 0)
-                for (int k = 0; k < cnt; ++k) take(2, q[k]);
+#pragma unroll
+            for (int r = 0; r < RF; ++r) {
+                const int i = i0 + r;
+                if (i >= nface) continue;
+                const int lz = i < ylen ? 0 : i - ylen + 1, ly = i < ylen ? i : 0;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    if (k >= valid) continue;
+                    const int32_t q = prequant(v[r][k], inv2eb);
+                    if (k == 0 && glane == 0) take(0, q);
+                    if (ly == 0) take(1, q);
+                    if (nd == 3 && lz == 0) take(2, q);
+                }
+            }
+        }
+        // the remaining rows: planes lz >= 1 (3D) or 0 (2D), rows ly >= 1
+        if (glane == 0) {
+            const int z1 = nd == 3 ? 1 : 0;
+            const int nrest = (zlen - z1) * (ylen - 1);
+            constexpr int RX = 32;
+            for (int i0 = 0; i0 < nrest; i0 += RX) {
+                float v[RX];
+#pragma unroll
+                for (int r = 0; r < RX; ++r) {
+                    const int i = i0 + r;
+                    const int lz = z1 + i / (ylen - 1), ly = 1 + i % (ylen - 1);
+                    v[r] = i < nrest ? __ldg(row_ptr(lz, ly)) : 0.0f;
+                }
+#pragma unroll
+                for (int r = 0; r < RX; ++r)
+                    if (i0 + r < nrest) take(0, prequant(v[r], inv2eb));
+            }
         }
     }
     for (int off = 1; off < G; off <<= 1) {  // the y and z faces span the block's lanes
