@@ -153,21 +153,24 @@ __global__ void __launch_bounds__(256) k_fixups(const vsz_header* hdr, const uin
 }
 
 // Code histogram.  Codes cluster around R (small residuals): the kHistWin
-// bins from R - kHistWin/2 count in lane-private 32-bit counters in shared
-// memory (column `lane` of the warp's table, so a lane's increments need no
-// atomic and never share a bank with another lane's); every other code adds
-// with an atomic to the CTA's bins (shared memory when they fit, else
-// global).  At the end each warp sums its table's columns into the bins.
+// bins from R - kHistWin/2 count in lane-private 16-bit counters in shared
+// memory, two bins to a 32-bit word (column `lane` of the warp's table, so
+// a lane's increments need no atomic and never share a bank with another
+// lane's); every other code adds with an atomic to the CTA's bins (shared
+// memory when they fit, else global).  At the end each warp sums its
+// table's columns into the bins.  The launch gives every thread at most
+// kHistMaxPerThread codes, so no 16-bit counter overflows.
 constexpr int kHistWin = 64;
 constexpr int kHistThreads = 256;
+constexpr uint64_t kHistMaxPerThread = 60000;
 __global__ void __launch_bounds__(kHistThreads) k_histogram(const uint16_t* __restrict__ codes, uint64_t n,
                                                             uint32_t* hist, uint32_t nbins, int use_smem) {
     extern __shared__ uint32_t sm[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t* tab = sm + (size_t)warp * kHistWin * 32;   // [kHistWin][32] of this warp
-    uint32_t* sh = sm + (size_t)(kHistThreads / 32) * kHistWin * 32;  // [nbins] when use_smem
+    uint32_t* tab = sm + (size_t)warp * (kHistWin / 2) * 32;   // [kHistWin/2][32] of this warp
+    uint32_t* sh = sm + (size_t)(kHistThreads / 32) * (kHistWin / 2) * 32;  // [nbins] when use_smem
 #pragma unroll
-    for (int k = 0; k < kHistWin; ++k) tab[k * 32 + lane] = 0;
+    for (int k = 0; k < kHistWin / 2; ++k) tab[k * 32 + lane] = 0;
     if (use_smem)
         for (uint32_t i = threadIdx.x; i < nbins; i += blockDim.x) sh[i] = 0;
     __syncthreads();
@@ -175,7 +178,7 @@ __global__ void __launch_bounds__(kHistThreads) k_histogram(const uint16_t* __re
     auto put = [&](uint32_t c, uint32_t k) { if (use_smem) atomicAdd(&sh[c], k); else atomicAdd(&hist[c], k); };
     auto add = [&](uint32_t c) {
         const uint32_t k = c - base;
-        if (k < (uint32_t)kHistWin && c < nbins) tab[k * 32 + lane] += 1u;
+        if (k < (uint32_t)kHistWin && c < nbins) tab[(k >> 1) * 32 + lane] += 1u << ((k & 1u) * 16);
         else if (c < nbins) put(c, 1u);
     };
     auto add8 = [&](const uint4 v) {
@@ -200,14 +203,14 @@ __global__ void __launch_bounds__(kHistThreads) k_histogram(const uint16_t* __re
     for (; j < n8; j += nth) add8(*reinterpret_cast<const uint4*>(codes + 8 * j));
     for (uint64_t i = 8 * n8 + tid; i < n; i += nth) add(codes[i]);
     __syncwarp();
-    // bin base + k (k = lane, lane + 32): the sum of row k over the warp's
-    // 32 columns, read in a rotated order so that the lanes hit 32 banks
+    // bin base + k (k = lane, lane + 32): the sum of its half-words over the
+    // warp's 32 columns, read in a rotated order so that the lanes hit 32 banks
 #pragma unroll
     for (int h = 0; h < kHistWin / 32; ++h) {
         const uint32_t k = (uint32_t)(h * 32 + lane);
         uint32_t sum = 0;
 #pragma unroll 8
-        for (int c = 0; c < 32; ++c) sum += tab[k * 32 + ((c + lane) & 31)];
+        for (int c = 0; c < 32; ++c) sum += (tab[(k >> 1) * 32 + ((c + lane) & 31)] >> ((k & 1u) * 16)) & 0xffffu;
         if (sum && base + k < nbins) put(base + k, sum);
     }
     if (use_smem) {
@@ -268,14 +271,17 @@ cudaError_t launch_fixups(const vsz_header* hdr, const uint32_t* fix_idx, const 
 cudaError_t launch_histogram(const uint16_t* codes, uint64_t n, uint32_t* hist, uint32_t nbins, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(hist, 0, (size_t)nbins * 4, s);
     if (e != cudaSuccess || n == 0) return e;
-    const size_t tab = (size_t)(kHistThreads / 32) * kHistWin * 32 * 4;  // the warps' window tables
+    const size_t tab = (size_t)(kHistThreads / 32) * (kHistWin / 2) * 32 * 4;  // the warps' window tables
     const int use_smem = (size_t)nbins * 4 <= 96 * 1024;
     const size_t smem = tab + (use_smem ? (size_t)nbins * 4 : 0);
     if ((e = raise_smem_attr((const void*)k_histogram, smem)) != cudaSuccess) return e;
     const int occ = occupancy((const void*)k_histogram, kHistThreads, smem);
     const uint64_t want = (n + (uint64_t)kHistThreads * 128 - 1) / ((uint64_t)kHistThreads * 128);
-    const int grid = (int)umin64(want, (uint64_t)num_sms() * (uint64_t)(occ > 0 ? occ : 1));
-    k_histogram<<<grid, kHistThreads, smem, s>>>(codes, n, hist, nbins, use_smem);
+    uint64_t grid = umin64(want, (uint64_t)num_sms() * (uint64_t)(occ > 0 ? occ : 1));
+    const uint64_t least = (n + kHistThreads * kHistMaxPerThread - 1) / (kHistThreads * kHistMaxPerThread);
+    if (grid < least) grid = least;  // at most kHistMaxPerThread codes per thread (16-bit counters)
+    if (grid > 0x7fffffffull) return cudaErrorInvalidValue;
+    k_histogram<<<(unsigned)grid, kHistThreads, smem, s>>>(codes, n, hist, nbins, use_smem);
     return cudaGetLastError();
 }
 
