@@ -361,9 +361,10 @@ VSZ_API vsz_status vsz_reconstruct_q(const vsz_params* p, const vsz_compressed* 
 
 /*
  * Code statistics (the learned tuner's labels): d_hist[0..2R-1] receives the
- * number of elements with each code (code 0 = outliers).  d_hist must hold
- * 2R uint32 and is overwritten.  Shannon entropy of the codes follows from
- * it on the host.
+ * number of elements with each code (code 0 = outliers); codes at or above
+ * 2R (not dual-quant codes) are not counted.  d_hist must hold 2R uint32
+ * and is overwritten.  d_codes may have any 2-byte alignment.  Shannon
+ * entropy of the codes follows from it on the host.
  */
 VSZ_API vsz_status vsz_code_histogram(const vsz_params* p, const uint16_t* d_codes, uint32_t* d_hist,
                               void* stream);
