@@ -31,6 +31,8 @@ RECON_WS_BYTES = 256         # VSZ_RECON_WS_BYTES
 
 
 class VszError(RuntimeError):
+    """A call of the library returned a non-zero vsz_status (`status`)."""
+
     def __init__(self, status: int, what: str, detail: str = ""):
         self.status = status
         super().__init__(f"{what}: {_STATUS.get(status, status)}{(' (' + detail + ')') if detail else ''}")
@@ -94,6 +96,7 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
+    """Compile libvsz.so in-tree for sm_103a (nvcc) if its sources changed; its path."""
     return _build.build(force=force)
 
 
@@ -194,29 +197,37 @@ class Params:
 
     @classmethod
     def make(cls, dims, block, eb, eb_mode="rel", radius=512, pad="zero") -> "Params":
+        """The paper's statement of the problem: C-order dims, block edge, error
+        bound (absolute or value-range relative, Sec. II-B), radius R of the
+        codes, padding mode by name (PAD_MODES, Sec. IV)."""
         em = {"abs": EB_ABS, "rel": EB_REL}[eb_mode] if isinstance(eb_mode, str) else int(eb_mode)
         pm = PAD_MODES[pad] if isinstance(pad, str) else int(pad)
         return cls(tuple(int(d) for d in dims), int(block), float(eb), em, int(radius), pm)
 
     def c(self) -> _CParams:
+        """The vsz_params struct of the C ABI."""
         d = list(self.dims) + [0] * (3 - len(self.dims))
         return _CParams(len(self.dims), (ctypes.c_uint64 * 3)(*d), self.block, self.eb,
                         self.eb_mode, self.radius, self.pad)
 
     @property
     def n(self) -> int:
+        """Values in the field."""
         return int(lib().vsz_num_elems(ctypes.byref(self.c())))
 
     @property
     def nblocks(self) -> int:
+        """Blocks of the field, partial blocks at the + edges included (Sec. III-A)."""
         return int(lib().vsz_num_blocks(ctypes.byref(self.c())))
 
     @property
     def is_block_pad(self) -> bool:
+        """A per-block padding value (Sec. IV-B-2)."""
         return self.pad in (4, 5, 6)
 
     @property
     def is_edge_pad(self) -> bool:
+        """Per-block and per-axis padding values (Sec. IV-B-3)."""
         return self.pad in (7, 8, 9)
 
     @property
@@ -225,14 +236,17 @@ class Params:
         return self.nblocks if self.is_block_pad else self.nblocks * len(self.dims) if self.is_edge_pad else 0
 
     def validate(self) -> int:
+        """vsz_validate: 0, or the status a call with these parameters would return."""
         return int(lib().vsz_validate(ctypes.byref(self.c())))
 
 
 def num_blocks(p: Params) -> int:
+    """Blocks of the field of `p`."""
     return p.nblocks
 
 
 def workspace_size(p: Params, out_cap: int, fix_cap: int) -> int:
+    """Bytes of the compression workspace for these list capacities (vsz_workspace_size)."""
     return int(lib().vsz_workspace_size(ctypes.byref(p.c()), out_cap, fix_cap))
 
 
@@ -296,15 +310,23 @@ class Field:
         return ctypes.c_void_p(x.data_ptr() if self.n else 0)
 
     def prequant_lorenzo(self, x, stream=None):
+        """Error-bound resolution and the fused prequantization, Lorenzo
+        prediction, post-quantization and guard (Sec. III-A, Alg. 2;
+        vsz_prequant_lorenzo).  The outliers stay staged until
+        outlier_compact."""
         _check(lib().vsz_prequant_lorenzo(ctypes.byref(self._cp), self._x(x), ctypes.byref(self._cc),
                                           _ptr(self.ws), self.ws_bytes, _stream_handle(stream)),
                "vsz_prequant_lorenzo")
 
     def outlier_compact(self, stream=None):
+        """The outlier and fixup lists in canonical block-major order, and the
+        block offsets (vsz_outlier_compact)."""
         _check(lib().vsz_outlier_compact(ctypes.byref(self._cp), ctypes.byref(self._cc), _ptr(self.ws),
                                          self.ws_bytes, _stream_handle(stream)), "vsz_outlier_compact")
 
     def compress(self, x, stream=None):
+        """prequant_lorenzo followed by outlier_compact (vsz_compress); x a
+        contiguous float32 CUDA tensor of n values."""
         _check(lib().vsz_compress(ctypes.byref(self._cp), self._x(x), ctypes.byref(self._cc), _ptr(self.ws),
                                   self.ws_bytes, _stream_handle(stream)), "vsz_compress")
 
@@ -315,6 +337,8 @@ class Field:
                                           _stream_handle(stream)), "vsz_compress_noalloc")
 
     def reconstruct(self, out=None, stream=None):
+        """The inverse (Sec. III-A): per-block prefix sums of the residuals,
+        x_hat = q * 2eb, fixups restored (vsz_reconstruct); returns x_hat."""
         import torch
         if out is None:
             out = torch.empty(max(self.n, 1), dtype=torch.float32, device=self.codes.device)
@@ -323,6 +347,7 @@ class Field:
         return out[: self.n]
 
     def reconstruct_q(self, out=None, stream=None):
+        """The inverse's prequantized integers q (vsz_reconstruct_q)."""
         import torch
         if out is None:
             out = torch.empty(max(self.n, 1), dtype=torch.int32, device=self.codes.device)
@@ -331,6 +356,8 @@ class Field:
         return out[: self.n]
 
     def code_histogram(self, out=None, stream=None):
+        """The 2R-bin histogram of the codes (vsz_code_histogram; the entropy
+        stage and the tuner's labels, Sec. II-B)."""
         import torch
         if out is None:
             out = torch.empty(2 * self.p.radius, dtype=torch.int32, device=self.codes.device)
@@ -343,6 +370,8 @@ class Field:
         return int(lib().vsz_sync_status(ctypes.byref(self._cc), _stream_handle(stream)))
 
     def header(self, stream=None) -> dict:
+        """The device header as a dict (resolved error bound, range, P,
+        counts, status); synchronizes the stream."""
         h = _CHeader()
         _check(lib().vsz_read_header(ctypes.byref(self._cc), ctypes.byref(h), _stream_handle(stream)),
                "vsz_read_header")
@@ -397,6 +426,7 @@ class Batch:
         self._h = h
 
     def submit(self, stream=None):
+        """Compress every field of the plan (vsz_batch_submit)."""
         _check(lib().vsz_batch_submit(self._h, _stream_handle(stream)), "vsz_batch_submit")
 
     def set_outputs(self, outs):
@@ -412,6 +442,7 @@ class Batch:
         self.outs = list(outs)
 
     def reconstruct(self, stream=None):
+        """Reconstruct every field into its output (vsz_batch_reconstruct)."""
         _check(lib().vsz_batch_reconstruct(self._h, _stream_handle(stream)), "vsz_batch_reconstruct")
 
     def classes(self) -> list:
@@ -426,9 +457,11 @@ class Batch:
         return out
 
     def set_shape(self, c: int, warps: int = 0, ctas_per_sm: int = 0):
+        """Launch shape of class c (0 = default); no shape changes a result."""
         _check(lib().vsz_batch_set_shape(self._h, c, warps, ctas_per_sm), "vsz_batch_set_shape")
 
     def set_concurrent(self, on: bool):
+        """Run the class kernels of each sequence as parallel branches."""
         _check(lib().vsz_batch_set_concurrent(self._h, 1 if on else 0), "vsz_batch_set_concurrent")
 
     def autotune(self, stream=None, reps: int = 3, cache: str | None = None) -> list:
@@ -496,6 +529,7 @@ class Batch:
         return True
 
     def close(self):
+        """Release the plan (vsz_batch_destroy)."""
         if getattr(self, "_h", None) is not None and self._h.value:
             lib().vsz_batch_destroy(self._h)
             self._h = None
@@ -561,6 +595,7 @@ def huffman_encode(sym, n: int, book: HuffmanBook, words=None, stream=None):
 
 
 def huffman_decode(words, chunk_off, n: int, book: HuffmanBook, out=None, stream=None):
+    """Decode n symbols (vsz_huffman_decode); returns (symbols, status)."""
     import torch
     if out is None:
         out = torch.empty(max(n, 1), dtype=torch.int16, device=words.device)

@@ -42,6 +42,7 @@ def _deps() -> list[str]:
 
 
 def is_stale() -> bool:
+    """The library is missing or older than one of its sources."""
     if not os.path.exists(LIB_PATH):
         return True
     t = os.path.getmtime(LIB_PATH)
@@ -62,6 +63,7 @@ def build(force: bool = False, verbose: bool = False, out: str | None = None,
     dflags = [f"-D{d}" for d in defines]
 
     def compile_one(src: str) -> str:
+        """nvcc of one translation unit; the object's path."""
         obj = os.path.join(bdir, src.replace(".cu", ".o"))
         cmd = [nvcc, *ARCH, *NVCC_FLAGS, *dflags, f"-I{INCLUDE}", "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)

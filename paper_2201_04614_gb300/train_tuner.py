@@ -115,6 +115,7 @@ def evaluate(net, X, masks, costs, nouts, dims, guard_fields=None):
 
 
 def main(argv=None):
+    """Generate the tuner's fields, label them by the GPU sweep, train, evaluate, save."""
     ap = argparse.ArgumentParser()
     ap.add_argument("--train", type=int, default=4000)
     ap.add_argument("--test", type=int, default=500)

@@ -42,14 +42,17 @@ def class_params(ndim: int, c: int):
 
 
 def class_mask(ndim: int) -> int:
+    """Bit c set for every class c allowed at this rank."""
     return sum(1 << c for c in range(NCLASS) if class_params(ndim, c) is not None)
 
 
 def default_class(ndim: int) -> int:
+    """The class of the default configuration: the rank's default block, zero padding."""
     return 3 * BLOCKS[ndim].index(DEFAULT_BLOCK[ndim])
 
 
 def params_for(p: Params, c: int) -> Params:
+    """`p` with the block size and padding mode of class c."""
     b, pad = class_params(len(p.dims), c)
     return Params(p.dims, b, p.eb, p.eb_mode, p.radius, PAD_MODES[pad])
 
@@ -157,6 +160,7 @@ def guard_counts(p: Params, x, class_a: int, class_b: int, stream=None):
 
 
 def guard_sample_dims(p: Params) -> tuple:
+    """Extents of the fixed block sample the guard compresses (vsz_tuner_guard_sample_dims)."""
     L = _bind()
     d = (ctypes.c_uint64 * 3)()
     _check(L.vsz_tuner_guard_sample_dims(ctypes.byref(p.c()), d), "vsz_tuner_guard_sample_dims")
@@ -291,6 +295,7 @@ class MLP:
 
     # ---- weights file: magic, nfeat, hidden, nclass, nparam (u32), mu, sigma, theta (f32)
     def save(self, path: str = WEIGHTS_PATH) -> None:
+        """Write the weights file (header with the shape, normalisation, parameters)."""
         norm = self.norm.cpu().numpy()
         with open(path, "wb") as f:
             f.write(_MAGIC + struct.pack("<4I", NFEAT, HIDDEN, NCLASS, NPARAM))
@@ -299,6 +304,7 @@ class MLP:
 
     @classmethod
     def load(cls, path: str = WEIGHTS_PATH, device=None) -> "MLP":
+        """Read a weights file written by save(); its shape must match this library's."""
         with open(path, "rb") as f:
             head = f.read(len(_MAGIC) + 16)
             if head[:len(_MAGIC)] != _MAGIC:
