@@ -876,7 +876,7 @@ def run_batch_profile(a):
     fields: 98,880,000 values, 396 MB, larger than L2), default classes, rel eb
     1e-4, one autotuned graph plan; `steps` compressions and reconstructions
     after `warmup`.  Prints one JSON line with the per-class kernel times the
-    autotuner measured and the plan's GB/s.  Meant as the driver of ncu
+    autotuner measured and the plan's GB/s.  A small case to run under ncu
     captures of the batch kernels (the full batches hold >10 GB on the
     device)."""
     import numpy as np
