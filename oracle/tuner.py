@@ -38,8 +38,12 @@ Definitions (the CUDA side computes the same quantities in its own kernels):
 
 Pins (tests/test_oracle_tuner.py): closed-form features of ramps, constants
 and two-valued fields; entropies of uniform and two-point histograms; costs
-recounted from the compression oracle on constant fields; the gradient
-against central finite differences; Adam's first steps in closed form.
+recounted from the compression oracle on constant fields; a hand-worked
+forward pass with non-zero weights in every layer, mu != 0, sigma != 1 and a
+negative pre-activation in each hidden layer (tests/golden/
+tuner_forward_handworked.json), which fixes the flat parameter layout too;
+the gradient against central finite differences; Adam's first steps in
+closed form, and a second step under a changed gradient.
 """
 from __future__ import annotations
 

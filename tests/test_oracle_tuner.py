@@ -8,10 +8,19 @@ and independent formulations, never against itself:
 * entropies of uniform and two-point histograms;
 * class costs of constant fields from the closed-form outlier counts of
   first-order Lorenzo (one nonzero residual per block, at its origin);
-* the gradient against central finite differences of the loss;
-* Adam's first steps in closed form (Kingma & Ba, 2015).
+* a hand-worked forward pass (tests/golden/tuner_forward_handworked.json):
+  non-zero weights in every layer at their documented flat offsets, mu != 0,
+  sigma != 1, a negative pre-activation in each hidden layer, an asymmetric
+  W2 and a class removed only by the mask; planted mistakes (transposed W2,
+  a dropped ReLU, swapped normalisation) each fail it;
+* the gradient against central finite differences of the loss, and its b3
+  part against the closed form mean(p - onehot(y));
+* Adam's first steps in closed form (Kingma & Ba, 2015), and a second step
+  under a changed gradient worked by hand.
 """
+import json
 import math
+import os
 
 import numpy as np
 import pytest
@@ -201,3 +210,99 @@ def test_adam_first_steps_closed_form():
     # a constant gradient keeps m_hat = g and v_hat = g^2 at every step
     t2, _, _ = T.adam_step(t1, g, m, v, 2, lr, eps=eps)
     assert np.allclose(t2, t1 - lr * g / (np.abs(g) + eps), rtol=0, atol=1e-14)
+
+
+# ---------------------------------------------------------------- hand-worked network
+GOLDEN_FWD = os.path.join(os.path.dirname(__file__), "golden", "tuner_forward_handworked.json")
+# documented flat layout: (offset, columns) of each parameter block
+LAYOUT = {"W1": (0, 12), "b1": (768, None), "W2": (832, 64), "b2": (4928, None), "W3": (4992, 64),
+          "b3": (5760, None)}
+
+
+def _golden():
+    with open(GOLDEN_FWD) as f:
+        gd = json.load(f)
+    theta = np.zeros(5772)
+    for name, (off, ncol) in LAYOUT.items():
+        for ent in gd[name]:
+            if ncol is None:
+                i, v = ent
+                theta[off + i] = v
+            else:
+                r, c, v = ent
+                theta[off + r * ncol + c] = v
+    X = np.array([s["x"] for s in gd["samples"]], np.float64)
+    masks = np.array([T.class_mask(s["ndim"]) for s in gd["samples"]])
+    return gd, theta, np.array(gd["mu"], np.float64), np.array(gd["sigma"], np.float64), X, masks
+
+
+def _expected_logits(s):
+    return np.array([-np.inf if v is None else v for v in s["logits"]], np.float64)
+
+
+def test_forward_handworked_network():
+    """Non-zero weights in every layer, mu != 0 and sigma != 1, a negative
+    pre-activation in each hidden layer, an asymmetric W2 and a class that
+    only the mask removes (tests/golden/tuner_forward_handworked.json)."""
+    gd, theta, mu, sigma, X, masks = _golden()
+    assert T.NPARAM == 5772
+    zm, p, (xt, a1, h1, a2, h2) = T.forward(theta, mu, sigma, X, masks)
+    for i, s in enumerate(gd["samples"]):
+        assert np.array_equal(xt[i], np.array(s["xt"], np.float64)), s["name"]
+        assert np.array_equal(a1[i, :4], s["a1_head"]) and np.all(a1[i, 4:] == 0), s["name"]
+        assert np.array_equal(h1[i, :4], s["h1_head"]) and np.all(h1[i, 4:] == 0), s["name"]
+        assert np.array_equal(a2[i, :4], s["a2_head"]) and np.all(a2[i, 4:] == 0), s["name"]
+        assert np.array_equal(h2[i, :4], s["h2_head"]) and np.all(h2[i, 4:] == 0), s["name"]
+        z = _expected_logits(s)
+        assert np.array_equal(zm[i], z), s["name"]
+        # softmax of the hand-worked logits over the allowed classes
+        e = [math.exp(v) if np.isfinite(v) else 0.0 for v in z]
+        assert np.allclose(p[i], np.array(e) / sum(e), rtol=1e-14, atol=0), s["name"]
+    assert list(T.predict(theta, mu, sigma, X, masks)) == [s["predicted"] for s in gd["samples"]]
+    # the gradient of the mean cross-entropy with respect to b3 is the mean
+    # of p - onehot(y) (softmax with cross-entropy, closed form)
+    y = np.array([4, 3])
+    _, g = T.loss_grad(theta, mu, sigma, X, y, masks)
+    onehot = np.zeros((2, T.NCLASS))
+    onehot[[0, 1], y] = 1.0
+    assert np.allclose(g[-T.NCLASS:], (p - onehot).mean(0), rtol=1e-13, atol=1e-15)
+
+
+def _forward_variant(theta, mu, sigma, X, masks, mistake):
+    """The network of the golden case with one planted mistake, to show that
+    the hand-worked case tells each of them apart."""
+    P = T.unflatten(theta)
+    xt = X * sigma + mu if mistake == "swapped_normalisation" else (X - mu) / sigma
+    a1 = xt @ P["W1"].T + P["b1"]
+    h1 = a1 if mistake == "no_relu1" else np.maximum(a1, 0.0)
+    W2 = P["W2"] if mistake == "w2_transposed" else P["W2"].T
+    a2 = h1 @ W2 + P["b2"]
+    h2 = a2 if mistake == "no_relu2" else np.maximum(a2, 0.0)
+    z = h2 @ P["W3"].T + P["b3"]
+    allowed = ((masks[:, None] >> np.arange(T.NCLASS)) & 1).astype(bool)
+    return np.where(allowed, z, -np.inf)
+
+
+@pytest.mark.parametrize("mistake", ["swapped_normalisation", "no_relu1", "w2_transposed", "no_relu2"])
+def test_handworked_network_catches_planted_mistakes(mistake):
+    gd, theta, mu, sigma, X, masks = _golden()
+    want = np.array([_expected_logits(s) for s in gd["samples"]])
+    assert np.array_equal(_forward_variant(theta, mu, sigma, X, masks, None), want)
+    assert not np.array_equal(_forward_variant(theta, mu, sigma, X, masks, mistake), want)
+
+
+def test_adam_second_step_with_a_changed_gradient():
+    """Two Adam steps with g1 = 2, g2 = -1, lr = 0.1, eps = 0, from theta = 0
+    (Kingma & Ba, 2015, Algorithm 1), worked by hand:
+      step 1: m = 0.2, v = 0.004, m_hat = 2, v_hat = 4, theta = -0.1 * 2 / 2 = -0.1;
+      step 2: m = 0.9 * 0.2 + 0.1 * (-1) = 0.08, v = 0.999 * 0.004 + 0.001 * 1 = 0.004996,
+              m_hat = 0.08 / 0.19 = 8/19, v_hat = 0.004996 / 0.001999 = 4996/1999,
+              theta = -0.1 - 0.1 * (8/19) / sqrt(4996/1999).
+    beta1 and beta2 enter differently under a changing gradient, so a swap
+    of the two, or a bias correction with the wrong power, fails."""
+    th1, m, v = T.adam_step(np.zeros(1), np.array([2.0]), np.zeros(1), np.zeros(1), 1, 0.1, eps=0.0)
+    assert th1[0] == pytest.approx(-0.1, rel=1e-15)
+    assert m[0] == pytest.approx(0.2, rel=1e-15) and v[0] == pytest.approx(0.004, rel=1e-14)
+    th2, m, v = T.adam_step(th1, np.array([-1.0]), m, v, 2, 0.1, eps=0.0)
+    assert m[0] == pytest.approx(0.08, rel=1e-14) and v[0] == pytest.approx(0.004996, rel=1e-14)
+    assert th2[0] == pytest.approx(-0.1 - 0.1 * (8 / 19) / math.sqrt(4996 / 1999), rel=1e-14)
