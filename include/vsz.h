@@ -333,6 +333,41 @@ VSZ_API vsz_status vsz_batch_autotune(vsz_batch b, void* stream, int reps);
 VSZ_API vsz_status vsz_batch_set_outputs(vsz_batch b, float* const* h_xhat);
 VSZ_API vsz_status vsz_batch_reconstruct(vsz_batch b, void* stream);
 
+/* Host copies of one field's compressed output, for
+ * vsz_batch_compress_host: the layout of vsz_compressed, in host memory
+ * (page-locked memory keeps the copies at the host link's full speed). */
+typedef struct {
+    uint16_t*   codes;     /* [n] */
+    int32_t*    pad;       /* [nb] (BLOCK_* modes), [nb * ndim] (EDGE_* modes); may be NULL otherwise */
+    uint32_t*   blk_off;   /* [nb+1] */
+    uint32_t*   out_idx;   /* [out_cap] */
+    int32_t*    out_delta; /* [out_cap] */
+    uint64_t    out_cap;
+    uint32_t*   fix_idx;   /* [fix_cap] */
+    uint32_t*   fix_bits;  /* [fix_cap] */
+    uint64_t    fix_cap;
+    vsz_header* hdr;       /* the field's header */
+} vsz_host_field;
+
+/*
+ * Compression of a whole batch from host memory to host memory (the
+ * dual-quant of Sec. III-A on every field of the plan, end to end): copies
+ * each field's input h_x[i] ([n_i] floats in host memory) into the job's
+ * device input d_x, runs the plan's compression exactly as
+ * vsz_batch_submit (graph replay when the plan uses one), then copies each
+ * field's header, codes, block offsets, padding table and its outlier and
+ * fixup lists back into h_out[i].  The lists are copied at their exact
+ * lengths, min(count, capacity) of both the device list and the host one;
+ * the header carries the counts and any device-recorded status.  Blocking:
+ * returns once the host buffers hold the result (it synchronizes `stream`
+ * twice: after the headers, to learn the list lengths, and at the end).
+ * h_x, h_out: host arrays of njobs entries.  Returns VSZ_ERR_INVALID_ARG on
+ * a NULL buffer where the field needs one, VSZ_ERR_CUDA if a copy or a
+ * launch fails; capacity overflow is reported in h_out[i].hdr->status.
+ */
+VSZ_API vsz_status vsz_batch_compress_host(vsz_batch b, const float* const* h_x, vsz_host_field* h_out,
+                                           void* stream);
+
 /* Bytes of the optional reconstruction workspace. */
 #define VSZ_RECON_WS_BYTES 256
 

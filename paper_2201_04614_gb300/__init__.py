@@ -70,6 +70,13 @@ class _CBatchClass(ctypes.Structure):
                 ("concurrent", ctypes.c_int32), ("kind", ctypes.c_int32)]
 
 
+class _CHostField(ctypes.Structure):
+    _fields_ = [("codes", ctypes.c_void_p), ("pad", ctypes.c_void_p), ("blk_off", ctypes.c_void_p),
+                ("out_idx", ctypes.c_void_p), ("out_delta", ctypes.c_void_p), ("out_cap", ctypes.c_uint64),
+                ("fix_idx", ctypes.c_void_p), ("fix_bits", ctypes.c_void_p), ("fix_cap", ctypes.c_uint64),
+                ("hdr", ctypes.c_void_p)]
+
+
 class _CTrace(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 24), ("ndim", ctypes.c_int32), ("block", ctypes.c_uint32),
                 ("n", ctypes.c_uint64), ("ms", ctypes.c_float), ("reserved", ctypes.c_uint32)]
@@ -83,6 +90,7 @@ EXPORTED = ["vsz_status_string", "vsz_last_cuda_error", "vsz_abi_version", "vsz_
             "vsz_compress_noalloc", "vsz_batch_workspace_size", "vsz_batch_create", "vsz_batch_submit",
             "vsz_batch_destroy", "vsz_batch_num_classes", "vsz_batch_get_class", "vsz_batch_set_shape",
             "vsz_batch_set_concurrent", "vsz_batch_autotune", "vsz_batch_set_outputs", "vsz_batch_reconstruct",
+            "vsz_batch_compress_host",
             "vsz_huffman_book_bytes", "vsz_huffman_book", "vsz_huffman_book_read", "vsz_huffman_encode",
             "vsz_huffman_encode_workspace_size", "vsz_sampling_autotune_workspace_size", "vsz_sampling_autotune",
             "vsz_sync_status", "vsz_shutdown", "vsz_debug_fail_alloc",
@@ -152,6 +160,7 @@ def lib():
     L.vsz_huffman_encode.argtypes = [vp, u64, vp, ctypes.c_uint32, vp, u64, vp, vp, vp, sz, vp]
     L.vsz_huffman_decode.argtypes = [vp, u64, vp, u64, vp, ctypes.c_uint32, vp, vp, vp]
     L.vsz_batch_reconstruct.argtypes = [vp, vp]
+    L.vsz_batch_compress_host.argtypes = [vp, P(ctypes.c_void_p), P(_CHostField), vp]
     L.vsz_trace_enable.argtypes = [ctypes.c_int]
     L.vsz_trace_read.argtypes = [P(_CTrace), ctypes.c_int]
     for name in EXPORTED:
@@ -444,6 +453,51 @@ class Batch:
     def reconstruct(self, stream=None):
         """Reconstruct every field into its output (vsz_batch_reconstruct)."""
         _check(lib().vsz_batch_reconstruct(self._h, _stream_handle(stream)), "vsz_batch_reconstruct")
+
+    def host_outputs(self, caps=None) -> list:
+        """Page-locked host buffers for compress_host: per field a dict of
+        CPU tensors shaped like the field's device outputs; caps[i] =
+        (outliers, fixups) sizes the host lists (default: the device lists'
+        capacities)."""
+        import torch
+        outs = []
+        for i, f in enumerate(self.fields):
+            oc, fc = caps[i] if caps is not None else (f.out_cap, f.fix_cap)
+
+            def pin(n, dt):
+                return torch.empty(max(int(n), 1), dtype=dt).pin_memory()
+            outs.append({"codes": pin(f.n, torch.int16), "blk_off": pin(f.nb + 1, torch.int32),
+                         "pad": pin(f.p.pad_len, torch.int32) if f.p.pad_len else None,
+                         "out_idx": pin(oc, torch.int32), "out_delta": pin(oc, torch.int32),
+                         "fix_idx": pin(fc, torch.int32), "fix_bits": pin(fc, torch.int32),
+                         "header": _CHeader()})
+        return outs
+
+    def compress_host(self, h_xs, h_outs, stream=None):
+        """Host memory to host memory (vsz_batch_compress_host): copies each
+        field's input from the CPU tensor h_xs[i] to its device input,
+        compresses the batch, and copies every field's header, codes, block
+        offsets, padding table and exact-length lists into h_outs[i] (from
+        host_outputs()).  Blocking."""
+        if len(h_xs) != len(self.fields) or len(h_outs) != len(self.fields):
+            raise ValueError("one host input and one host output per field")
+        xs = (ctypes.c_void_p * len(h_xs))()
+        hf = (_CHostField * len(h_xs))()
+        for i, (f, x, o) in enumerate(zip(self.fields, h_xs, h_outs)):
+            if f.n and (x.device.type != "cpu" or x.dtype.itemsize != 4 or not x.is_contiguous()
+                        or x.numel() < f.n):
+                raise ValueError("each host input must be a contiguous float32 CPU tensor of n values")
+            xs[i] = x.data_ptr() if f.n else None
+            hf[i].codes = o["codes"].data_ptr()
+            hf[i].pad = o["pad"].data_ptr() if o["pad"] is not None else None
+            hf[i].blk_off = o["blk_off"].data_ptr()
+            hf[i].out_idx, hf[i].out_delta = o["out_idx"].data_ptr(), o["out_delta"].data_ptr()
+            hf[i].out_cap = min(int(f.out_cap), o["out_idx"].numel(), o["out_delta"].numel())
+            hf[i].fix_idx, hf[i].fix_bits = o["fix_idx"].data_ptr(), o["fix_bits"].data_ptr()
+            hf[i].fix_cap = min(int(f.fix_cap), o["fix_idx"].numel(), o["fix_bits"].numel())
+            hf[i].hdr = ctypes.addressof(o["header"])
+        _check(lib().vsz_batch_compress_host(self._h, xs, hf, _stream_handle(stream)), "vsz_batch_compress_host")
+        return [{k: getattr(o["header"], k) for k, _ in _CHeader._fields_} for o in h_outs]
 
     def classes(self) -> list:
         """The plan's classes (rank, block, padding kind) with their launch

@@ -352,7 +352,7 @@ static cudaError_t launch_rclass(vsz_batch_st* b, size_t c, cudaStream_t s) {
 
 static cudaError_t launch_class(vsz_batch_st* b, size_t c, cudaStream_t s) {
     BatchClass& k = b->classes[c];
-    TraceScope ts("batch_lorenzo", s, k.nd, k.b);
+    TraceScope ts(k.pk == 1 ? "batch_lorenzo_bp" : k.pk == 2 ? "batch_lorenzo_gp" : "batch_lorenzo", s, k.nd, k.b);
     return k.nd == 1 ? launch_lorenzo_batch_1d(k.b, k.pk, k.d_args, k.d_prefix, (int)k.fields.size(), k.total_tiles,
                                                b->tickets + c, k.shape, s)
          : k.nd == 2 ? launch_lorenzo_batch_2d(k.b, k.pk, k.d_args, k.d_prefix, (int)k.fields.size(), k.total_tiles,
@@ -891,6 +891,59 @@ vsz_status vsz_batch_autotune(vsz_batch b, void* stream, int reps) {
     cudaEventDestroy(tm.e0);
     cudaEventDestroy(tm.e1);
     return st;
+}
+
+vsz_status vsz_batch_compress_host(vsz_batch b, const float* const* h_x, vsz_host_field* h_out, void* stream) {
+    if (!b || !h_x || !h_out) return VSZ_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int i = 0; i < b->n; ++i) {
+        const Geom& g = b->fields[i].a.g;
+        const vsz_host_field& o = h_out[i];
+        const int32_t pm = b->jobs[i].params.pad;
+        const bool table = (is_block_pad(pm) || is_edge_pad(pm)) && g.nb > 0;
+        if (!o.hdr || (g.n > 0 && (!h_x[i] || !o.codes)) || !o.blk_off || (table && !o.pad) ||
+            (o.out_cap && (!o.out_idx || !o.out_delta)) || (o.fix_cap && (!o.fix_idx || !o.fix_bits)))
+            return VSZ_ERR_INVALID_ARG;
+    }
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < b->n && e == cudaSuccess; ++i) {
+        const uint64_t n = b->fields[i].a.g.n;
+        if (n) e = cudaMemcpyAsync((void*)b->jobs[i].d_x, h_x[i], n * sizeof(float), cudaMemcpyHostToDevice, s);
+    }
+    if (e != cudaSuccess) return cuda_fail(e);
+    const vsz_status st = vsz_batch_submit(b, stream);
+    if (st != VSZ_OK) return st;
+    // headers first, then the dense outputs, which stay in flight while the
+    // host waits for the headers' list lengths
+    for (int i = 0; i < b->n && e == cudaSuccess; ++i)
+        e = cudaMemcpyAsync(h_out[i].hdr, b->jobs[i].out.hdr, sizeof(vsz_header), cudaMemcpyDeviceToHost, s);
+    for (int i = 0; i < b->n && e == cudaSuccess; ++i) {
+        const Geom& g = b->fields[i].a.g;
+        const vsz_compressed& c = b->jobs[i].out;
+        const int32_t pm = b->jobs[i].params.pad;
+        if (g.n) e = cudaMemcpyAsync(h_out[i].codes, c.codes, g.n * sizeof(uint16_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h_out[i].blk_off, c.blk_off, (g.nb + 1) * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+        const uint64_t plen = is_block_pad(pm) ? g.nb : is_edge_pad(pm) ? g.nb * (uint64_t)g.nd : 0;
+        if (e == cudaSuccess && plen)
+            e = cudaMemcpyAsync(h_out[i].pad, c.pad, plen * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    for (int i = 0; i < b->n && e == cudaSuccess; ++i) {
+        const vsz_compressed& c = b->jobs[i].out;
+        const vsz_host_field& o = h_out[i];
+        const uint64_t no = std::min(o.hdr->n_out, std::min(c.out_cap, o.out_cap));
+        const uint64_t nf = std::min(o.hdr->n_fix, std::min(c.fix_cap, o.fix_cap));
+        if (no) e = cudaMemcpyAsync(o.out_idx, c.out_idx, no * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+        if (no && e == cudaSuccess)
+            e = cudaMemcpyAsync(o.out_delta, c.out_delta, no * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+        if (nf && e == cudaSuccess)
+            e = cudaMemcpyAsync(o.fix_idx, c.fix_idx, nf * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+        if (nf && e == cudaSuccess)
+            e = cudaMemcpyAsync(o.fix_bits, c.fix_bits, nf * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e == cudaSuccess ? VSZ_OK : cuda_fail(e);
 }
 
 vsz_status vsz_batch_destroy(vsz_batch b) {

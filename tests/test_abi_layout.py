@@ -19,6 +19,7 @@ STRUCTS = {
     "vsz_field_job": vsz._CFieldJob,
     "vsz_batch_class": vsz._CBatchClass,
     "vsz_trace_record": vsz._CTrace,
+    "vsz_host_field": vsz._CHostField,
 }
 
 

@@ -303,3 +303,37 @@ def test_allocation_failure_injection():
             single = f.reconstruct().cpu().numpy().view(np.uint32)
             assert np.array_equal(outs[i][: f.n].cpu().numpy().view(np.uint32), single), MIX[i]
     b.close()
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_compress_host_equals_device_outputs(use_graph):
+    """vsz_batch_compress_host: host inputs in, host outputs out, identical to
+    what the plan leaves in device memory, with the lists at their exact
+    lengths; twice in a row, the second time from different host inputs."""
+    fields, xs = _make()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        b = vsz.Batch(fields, xs, use_graph=use_graph)
+    hout = b.host_outputs()
+    for shift in (0, 7):
+        hx = [torch.from_numpy(np.ascontiguousarray(
+            (field_for(dims, seed=50 + i + shift).reshape(-1) if int(np.prod(dims)) else np.zeros(0)), np.float32))
+            .pin_memory() for i, (dims, *_rest) in enumerate(MIX)]
+        heads = b.compress_host(hx, hout, stream)
+        ref, _ = _make(seed_shift=shift)
+        for f, x in zip(ref, hx):
+            f.compress(x.cuda())
+        for i, (f, o, h) in enumerate(zip(ref, hout, heads)):
+            w = f.to_host()
+            no, nf = int(w["header"]["n_out"]), int(w["header"]["n_fix"])
+            assert h["n_out"] == no and h["n_fix"] == nf and h["status"] == 0, MIX[i]
+            assert h["eb_abs"] == w["header"]["eb_abs"], MIX[i]
+            assert np.array_equal(o["codes"].numpy()[: f.n].view(np.uint16), w["codes"]), MIX[i]
+            assert np.array_equal(o["blk_off"].numpy()[: f.nb + 1].view(np.uint32), w["blk_off"]), MIX[i]
+            if w["pad"] is not None and f.p.pad_len:
+                assert np.array_equal(o["pad"].numpy()[: w["pad"].size], w["pad"]), MIX[i]
+            assert np.array_equal(o["out_idx"].numpy()[:no].view(np.uint32), w["out_idx"]), MIX[i]
+            assert np.array_equal(o["out_delta"].numpy()[:no], w["out_delta"]), MIX[i]
+            assert np.array_equal(o["fix_idx"].numpy()[:nf].view(np.uint32), w["fix_idx"]), MIX[i]
+            assert np.array_equal(o["fix_bits"].numpy()[:nf].view(np.uint32), w["fix_bits"]), MIX[i]
+    b.close()

@@ -11,7 +11,12 @@ The oracle cannot compress 134M values in a test's time, so:
   outlier slice blk_off[b]..blk_off[b+1]);
 * properties that hold at any size are checked on every element: the inverse
   reproduces the prequantized integers q = rint(x * inv2eb) exactly, and
-  |x - x_hat| <= eb_abs (1 + 2^-20).
+  |x - x_hat| <= eb_abs (1 + 2^-20);
+* the whole field against the oracle's whole-field compression and
+  decompression, bit for bit (codes, block offsets, outlier and fixup lists,
+  padding table, x_hat), at eb 1e-4 with zero padding and at eb 1e-5, where
+  the lists are long, with zero, block-average, global-average and
+  edge-average padding.
 """
 import numpy as np
 import pytest
@@ -109,3 +114,60 @@ def test_small_2d_workload_matches_oracle(pad):
         assert np.array_equal(got[k], getattr(c, k)), k
     xo = oracle.decompress(po, c).view(np.uint32)
     assert np.array_equal(f.reconstruct()[: 512 * 512].cpu().numpy().view(np.uint32), xo)
+
+
+# Whole-field parity on the 512^3 field, for the error bounds and paddings
+# the bench sweeps where the lists are long: at eb 1e-5 about 4.8 % of the
+# values are outliers, so outlier-dense tiles (the stash overflow and its
+# second walk, the compaction of long lists, the reconstruction's uncached
+# outlier path) run at scale.  The oracle compresses and decompresses the
+# whole field once per case (about 10 s each), the cases on the host's
+# threads at once; the GPU runs the launch configuration bench.py times.
+WHOLE_CASES = [(1e-4, "zero"), (1e-5, "zero"), (1e-5, "block_avg"), (1e-5, "global_avg"), (1e-5, "edge_avg")]
+
+
+@pytest.fixture(scope="module")
+def whole_oracle():
+    from concurrent.futures import ThreadPoolExecutor
+    x3 = synth.cfg2_field(N)
+    oracle.build()
+
+    def one(case):
+        eb, pad = case
+        po = oracle.Params((N, N, N), B, eb, oracle.EB_REL, 512, oracle.PAD_NAMES[pad])
+        c = oracle.compress(po, x3)
+        xo = oracle.decompress(po, c).view(np.uint32)
+        c.q = None  # the prequantized copy is not compared here
+        return c, xo
+
+    ex = ThreadPoolExecutor(len(WHOLE_CASES))
+    futs = {case: ex.submit(one, case) for case in WHOLE_CASES}
+    yield x3, futs
+    ex.shutdown(wait=True)
+
+
+@pytest.mark.parametrize("eb,pad", WHOLE_CASES)
+def test_whole_field_matches_oracle(whole_oracle, eb, pad):
+    x3, futs = whole_oracle
+    n = N ** 3
+    p = vsz.Params.make((N, N, N), B, eb, "rel", 512, pad)
+    f = vsz.Field(p, out_cap=n // 4, fix_cap=max(1 << 16, n // 64))
+    xd = torch.from_numpy(x3.reshape(-1)).cuda()
+    f.compress(xd)
+    xh = f.reconstruct()
+    torch.cuda.synchronize()
+    got = f.to_host()
+    h = got["header"]
+    assert h["status"] == 0 and h["recon_status"] == 0
+    c, xo = futs[(eb, pad)].result()
+    assert h["eb_abs"] == c.eb.eb_abs
+    assert h["n_out"] == len(c.out_idx) and h["n_fix"] == len(c.fix_idx)
+    if eb == 1e-5:
+        assert h["n_out"] > n // 50  # outlier-dense: several per row of every tile
+    for k in ("codes", "blk_off", "out_idx", "out_delta", "fix_idx", "fix_bits"):
+        assert np.array_equal(got[k], getattr(c, k)), k
+    if got["pad"] is not None and got["pad"].size == c.pad.size:
+        assert np.array_equal(got["pad"], c.pad)
+    assert np.array_equal(xh[:n].cpu().numpy().view(np.uint32), xo)
+    del f, xd, xh
+    torch.cuda.empty_cache()
