@@ -551,7 +551,11 @@ def measure_stream(a, vsz, T, torch, names, shapes, xs, eb, stream, keep_tuned=F
     nout_tuned = [int(h["n_out"]) for h in heads]
     status += [int(h["status"]) for h in heads]
 
-    # per-kernel device times of the tuned plan's compression and reconstruction
+    # per-kernel device times of the tuned plan's compression and reconstruction,
+    # with its class kernels one after another (parallel branches would time
+    # each kernel with its neighbours' work inside)
+    conc = bt.concurrency()
+    bt.set_concurrent_each(False, False)
     vsz.trace_enable(True)
     vsz.trace_read()
     reps = max(3, min(steps, 10))
@@ -565,6 +569,8 @@ def measure_stream(a, vsz, T, torch, names, shapes, xs, eb, stream, keep_tuned=F
         stream.synchronize()
     recs_r = vsz.trace_read(1 << 20)
     vsz.trace_enable(False)
+    bt.set_concurrent_each(*conc)
+    r["concurrent"] = {"compress": conc[0], "reconstruct": conc[1]}
     sb = sequence_bytes(tuned, heads)
     kern = {}
     for rec in recs_c:

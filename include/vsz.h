@@ -148,6 +148,18 @@ VSZ_API uint64_t vsz_num_blocks(const vsz_params* p);
  * be 256-byte aligned, and must not be shared by calls in flight at once. */
 VSZ_API size_t vsz_workspace_size(const vsz_params* p, uint64_t out_cap, uint64_t fix_cap);
 
+/* Bytes of a workspace whose outlier staging is laid out in block slots
+ * (2D/3D fields; the same as vsz_workspace_size for 1D fields): one slot of
+ * b^ndim + 1 entries per block, so the staging holds at least
+ * nb * (b^ndim + 1) entries whatever out_cap is.  With such a workspace the
+ * compression writes every outlier straight into its block's slot, in
+ * canonical order, and never walks a tile twice for its outliers however
+ * dense they are (at tight error bounds most residuals can be outliers;
+ * Sec. V-H counts them per padding mode).  Results are identical with either
+ * size; vsz_prequant_lorenzo and vsz_outlier_compact use the slot layout when
+ * ws_bytes is at least this large. */
+VSZ_API size_t vsz_workspace_size_dense(const vsz_params* p, uint64_t out_cap, uint64_t fix_cap);
+
 /*
  * Compression, step 1 (Sec. III-A, Alg. 2; Sec. IV; Sec. II-B): error-bound
  * resolution, prequantization q = rint(x * inv2eb), padding value, blockwise
@@ -210,6 +222,58 @@ VSZ_API vsz_status vsz_compress(const vsz_params* p, const float* d_x, vsz_compr
  */
 VSZ_API vsz_status vsz_compress_noalloc(const vsz_params* p, const float* d_x, vsz_compressed* c,
                                         void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* One field split across GPUs: the per-rank steps.                        */
+/* ------------------------------------------------------------------------ */
+/*
+ * Blocks are independent (Sec. III-A), so a field splits along dims[0] into
+ * slabs of whole blocks (every slab but the last a multiple of the block
+ * edge b along dims[0]), one per rank.  Three quantities cross slabs; the
+ * caller reduces each over the ranks with its own collective (the Python
+ * module paper_2201_04614_gb300.shard does it with torch.distributed):
+ *  1. relative eb (Sec. II-B): vsz_slab_range per slab, then the min of the
+ *     minima and the max of the maxima; the field's eb_abs is eb times their
+ *     difference in double (eb itself if it is 0 or no slab has a finite
+ *     value), exactly as the one-field call resolves it;
+ *  2. a global padding mode (Sec. IV-B-1): vsz_slab_qstats per slab under
+ *     the field's eb_abs, then the sums and counts added and the extremes
+ *     reduced; P = min, max, or floor((2S + m) / (2m)) of the totals;
+ *  3. vsz_compress_slab per slab with eb_abs and P, then the exclusive prefix
+ *     over the ranks of the slabs' n_out (from their headers), and
+ *     vsz_slab_rebase, which moves each slab's lists into the field's
+ *     canonical order: the concatenation over the ranks of the slabs' codes,
+ *     outlier lists, fixup lists, padding tables and blk_off[0..nb_slab) (then
+ *     the last slab's blk_off[nb_slab]) is the whole field's compression.
+ */
+typedef struct {
+    float    xmin, xmax;  /* finite range of the slab (valid if has_range) */
+    uint32_t has_range;   /* the slab holds a finite value */
+    uint32_t reserved;
+    int64_t  qsum;        /* sum of q = rint(x * inv2eb) over every value (NaN gives 0) */
+    int32_t  qmin, qmax;  /* extremes of q */
+} vsz_slab_stats;
+
+/* Finite min/max of the slab's n values into d_st->xmin/xmax/has_range
+ * (device struct, caller-owned). */
+VSZ_API vsz_status vsz_slab_range(const float* d_x, uint64_t n, vsz_slab_stats* d_st, void* stream);
+
+/* Sum and extremes of q over the slab (p: the slab, absolute mode with the
+ * field's eb_abs) into d_st->qsum/qmin/qmax. */
+VSZ_API vsz_status vsz_slab_qstats(const vsz_params* p, const float* d_x, vsz_slab_stats* d_st, void* stream);
+
+/* vsz_compress of one slab: p in absolute mode with the field's eb_abs (it
+ * resolves to the same inv2eb, ebx2 and eb_f32); pad_value is the field's P
+ * for a global padding mode and is ignored by the other modes.  Indices and
+ * block offsets are the slab's own until vsz_slab_rebase. */
+VSZ_API vsz_status vsz_compress_slab(const vsz_params* p, int32_t pad_value, const float* d_x, vsz_compressed* c,
+                                     void* d_ws, size_t ws_bytes, void* stream);
+
+/* Adds elem_base (the slab's first element in the field) to the slab's
+ * outlier and fixup indices and out_base (the outliers of the earlier slabs)
+ * to its blk_off[0..nb_slab]; the list lengths come from c->hdr. */
+VSZ_API vsz_status vsz_slab_rebase(const vsz_params* p, const vsz_compressed* c, uint64_t elem_base,
+                                   uint64_t out_base, void* stream);
 
 /* ------------------------------------------------------------------------ */
 /* Batches: many fields of uneven rank and size compressed together.        */
@@ -297,6 +361,9 @@ VSZ_API vsz_status vsz_batch_set_shape(vsz_batch b, int c, int warps, int ctas_p
  * origin pass, in reconstruction joined before the fixups.  Both sequences.
  * Drops the cached graphs. */
 VSZ_API vsz_status vsz_batch_set_concurrent(vsz_batch b, int on);
+/* As vsz_batch_set_concurrent, for the compression and the reconstruction
+ * sequence separately (the autotuner may choose differently for each). */
+VSZ_API vsz_status vsz_batch_set_concurrent_each(vsz_batch b, int compress_on, int reconstruct_on);
 
 /*
  * Autotune the plan on its own inputs: for each class (compression, and

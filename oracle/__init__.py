@@ -84,6 +84,8 @@ def _load():
         lib.vszo_lorenzo_delta.argtypes = [P(_Params), vp, vp, vp]
         lib.vszo_compress.argtypes = [P(_Params), vp, P(_Eb), vp, vp, vp, vp, vp, vp,
                                       P(ctypes.c_uint64), vp, vp, P(ctypes.c_uint64)]
+        lib.vszo_compress_given_pad.argtypes = [P(_Params), vp, ctypes.c_int32, P(_Eb), vp, vp, vp, vp, vp,
+                                                P(ctypes.c_uint64), vp, vp, P(ctypes.c_uint64)]
         lib.vszo_decompress.argtypes = [P(_Params), P(_Eb), vp, vp, vp, vp, vp,
                                         ctypes.c_uint64, vp, vp, ctypes.c_uint64, vp, vp]
         u32, u64 = ctypes.c_uint32, ctypes.c_uint64
@@ -239,6 +241,37 @@ def compress(p: Params, x) -> Compressed:
         raise ValueError(f"oracle compress failed rc={rc}")
     no, nf = n_out.value, n_fix.value
     return Compressed(EbInfo._from_c(e), codes, q, pad, blk_off,
+                      out_idx[:no].copy(), out_delta[:no].copy(),
+                      fix_idx[:nf].copy(), fix_bits[:nf].copy())
+
+
+def compress_given_pad(p: Params, x, P: int) -> Compressed:
+    """One whole-block slab of a field split along dims[0] (vszo_compress_given_pad):
+    p in absolute mode with the field's eb_abs, P the field's global padding
+    value (ignored by the other modes).  The returned q is not filled."""
+    x = _f32(x)
+    n = x.size
+    assert n == p.n, (n, p.n)
+    nb = p.nblocks
+    e = _Eb()
+    codes = np.zeros(n, np.uint16)
+    pad = np.zeros(p.pad_len, np.int32)
+    blk_off = np.zeros(nb + 1, np.uint32)
+    cap = max(n, 1)
+    out_idx = np.zeros(cap, np.uint32)
+    out_delta = np.zeros(cap, np.int32)
+    fix_idx = np.zeros(cap, np.uint32)
+    fix_bits = np.zeros(cap, np.uint32)
+    n_out = ctypes.c_uint64(0)
+    n_fix = ctypes.c_uint64(0)
+    rc = _load().vszo_compress_given_pad(ctypes.byref(p._c()), x.ctypes.data, int(P), ctypes.byref(e),
+                                         codes.ctypes.data, pad.ctypes.data, blk_off.ctypes.data,
+                                         out_idx.ctypes.data, out_delta.ctypes.data, ctypes.byref(n_out),
+                                         fix_idx.ctypes.data, fix_bits.ctypes.data, ctypes.byref(n_fix))
+    if rc:
+        raise ValueError(f"oracle compress_given_pad failed rc={rc}")
+    no, nf = n_out.value, n_fix.value
+    return Compressed(EbInfo._from_c(e), codes, None, pad, blk_off,
                       out_idx[:no].copy(), out_delta[:no].copy(),
                       fix_idx[:nf].copy(), fix_bits[:nf].copy())
 

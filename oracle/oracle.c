@@ -405,11 +405,43 @@ static float bits_float(uint32_t u)
     return v;
 }
 
+static int compress_impl(const vszo_params* p, const float* x, vszo_eb* eb,
+                         uint16_t* codes, int32_t* q_out, int32_t* pad,
+                         uint32_t* blk_off, uint32_t* out_idx, int32_t* out_delta,
+                         uint64_t* n_out, uint32_t* fix_idx, uint32_t* fix_bits,
+                         uint64_t* n_fix, const int32_t* global_pad);
+
 int vszo_compress(const vszo_params* p, const float* x, vszo_eb* eb,
                   uint16_t* codes, int32_t* q_out, int32_t* pad,
                   uint32_t* blk_off, uint32_t* out_idx, int32_t* out_delta,
                   uint64_t* n_out, uint32_t* fix_idx, uint32_t* fix_bits,
                   uint64_t* n_fix)
+{
+    return compress_impl(p, x, eb, codes, q_out, pad, blk_off, out_idx, out_delta, n_out,
+                         fix_idx, fix_bits, n_fix, NULL);
+}
+
+/* One slab of a field split across ranks along dims[0] in whole blocks:
+ * blocks are independent (Sec. III-A), so the slab's compression is the
+ * whole field's restricted to the slab, once the two field-wide quantities
+ * it depends on are given: the error bound (pass p in absolute mode with the
+ * field's eb_abs, which resolves to the same inv2eb, ebx2 and eb_f32) and,
+ * for a global padding mode (Sec. IV-B-1), the field's padding value P,
+ * which stands in for the slab's own.  Every other mode ignores P. */
+int vszo_compress_given_pad(const vszo_params* p, const float* x, int32_t P, vszo_eb* eb,
+                            uint16_t* codes, int32_t* pad, uint32_t* blk_off,
+                            uint32_t* out_idx, int32_t* out_delta, uint64_t* n_out,
+                            uint32_t* fix_idx, uint32_t* fix_bits, uint64_t* n_fix)
+{
+    return compress_impl(p, x, eb, codes, NULL, pad, blk_off, out_idx, out_delta, n_out,
+                         fix_idx, fix_bits, n_fix, &P);
+}
+
+static int compress_impl(const vszo_params* p, const float* x, vszo_eb* eb,
+                         uint16_t* codes, int32_t* q_out, int32_t* pad,
+                         uint32_t* blk_off, uint32_t* out_idx, int32_t* out_delta,
+                         uint64_t* n_out, uint32_t* fix_idx, uint32_t* fix_bits,
+                         uint64_t* n_fix, const int32_t* global_pad)
 {
     geom g;
     if (make_geom(p, &g)) return VSZO_ERR_ARG;
@@ -428,6 +460,9 @@ int vszo_compress(const vszo_params* p, const float* x, vszo_eb* eb,
     /* Sec. IV: the padding value(s). */
     rc = vszo_pad_values(p, q, pad);
     if (rc) { free(q); return rc; }
+    if (global_pad && (p->pad == VSZO_PAD_GLOBAL_MIN || p->pad == VSZO_PAD_GLOBAL_MAX ||
+                       p->pad == VSZO_PAD_GLOBAL_AVG))
+        pad[0] = *global_pad;
 
     const int32_t R = (int32_t)p->radius;
     uint64_t nb = vszo_num_blocks(p);

@@ -92,6 +92,13 @@ int vszo_compress(const vszo_params* p, const float* x, vszo_eb* eb,
                   uint64_t* n_out, uint32_t* fix_idx, uint32_t* fix_bits,
                   uint64_t* n_fix);
 
+/* One whole-block slab of a field split along dims[0]: p in absolute mode
+ * with the field's eb_abs; P the field's padding value for a global mode. */
+int vszo_compress_given_pad(const vszo_params* p, const float* x, int32_t P, vszo_eb* eb,
+                            uint16_t* codes, int32_t* pad, uint32_t* blk_off,
+                            uint32_t* out_idx, int32_t* out_delta, uint64_t* n_out,
+                            uint32_t* fix_idx, uint32_t* fix_bits, uint64_t* n_fix);
+
 /* Decompression (inverse dual-quant).  q_out (may be NULL) receives the
  * reconstructed prequantized integers, xhat[n] the values. */
 int vszo_decompress(const vszo_params* p, const vszo_eb* eb,

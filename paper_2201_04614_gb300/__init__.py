@@ -84,13 +84,14 @@ class _CTrace(ctypes.Structure):
 
 HEADER_BYTES = ctypes.sizeof(_CHeader)
 EXPORTED = ["vsz_status_string", "vsz_last_cuda_error", "vsz_abi_version", "vsz_validate",
-            "vsz_num_elems", "vsz_num_blocks", "vsz_workspace_size", "vsz_prequant_lorenzo",
+            "vsz_num_elems", "vsz_num_blocks", "vsz_workspace_size", "vsz_workspace_size_dense", "vsz_prequant_lorenzo",
             "vsz_outlier_compact", "vsz_compress", "vsz_reconstruct", "vsz_reconstruct_q",
             "vsz_code_histogram", "vsz_read_header", "vsz_trace_enable", "vsz_trace_read",
             "vsz_compress_noalloc", "vsz_batch_workspace_size", "vsz_batch_create", "vsz_batch_submit",
             "vsz_batch_destroy", "vsz_batch_num_classes", "vsz_batch_get_class", "vsz_batch_set_shape",
-            "vsz_batch_set_concurrent", "vsz_batch_autotune", "vsz_batch_set_outputs", "vsz_batch_reconstruct",
-            "vsz_batch_compress_host",
+            "vsz_batch_set_concurrent", "vsz_batch_set_concurrent_each", "vsz_batch_autotune", "vsz_batch_set_outputs",
+            "vsz_batch_reconstruct",
+            "vsz_batch_compress_host", "vsz_slab_range", "vsz_slab_qstats", "vsz_compress_slab", "vsz_slab_rebase",
             "vsz_huffman_book_bytes", "vsz_huffman_book", "vsz_huffman_book_read", "vsz_huffman_encode",
             "vsz_huffman_encode_workspace_size", "vsz_sampling_autotune_workspace_size", "vsz_sampling_autotune",
             "vsz_sync_status", "vsz_shutdown", "vsz_debug_fail_alloc",
@@ -131,6 +132,8 @@ def lib():
     L.vsz_num_blocks.argtypes = [P(_CParams)]
     L.vsz_workspace_size.restype = sz
     L.vsz_workspace_size.argtypes = [P(_CParams), u64, u64]
+    L.vsz_workspace_size_dense.restype = sz
+    L.vsz_workspace_size_dense.argtypes = [P(_CParams), u64, u64]
     for name in ("vsz_prequant_lorenzo", "vsz_compress"):
         getattr(L, name).argtypes = [P(_CParams), vp, P(_CCompressed), vp, sz, vp]
     L.vsz_outlier_compact.argtypes = [P(_CParams), P(_CCompressed), vp, sz, vp]
@@ -149,6 +152,7 @@ def lib():
     L.vsz_batch_get_class.argtypes = [vp, ctypes.c_int, P(_CBatchClass)]
     L.vsz_batch_set_shape.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     L.vsz_batch_set_concurrent.argtypes = [vp, ctypes.c_int]
+    L.vsz_batch_set_concurrent_each.argtypes = [vp, ctypes.c_int, ctypes.c_int]
     L.vsz_batch_autotune.argtypes = [vp, vp, ctypes.c_int]
     L.vsz_batch_set_outputs.argtypes = [vp, P(ctypes.c_void_p)]
     L.vsz_huffman_book_bytes.restype = sz
@@ -161,13 +165,18 @@ def lib():
     L.vsz_huffman_decode.argtypes = [vp, u64, vp, u64, vp, ctypes.c_uint32, vp, vp, vp]
     L.vsz_batch_reconstruct.argtypes = [vp, vp]
     L.vsz_batch_compress_host.argtypes = [vp, P(ctypes.c_void_p), P(_CHostField), vp]
+    L.vsz_slab_range.argtypes = [vp, u64, vp, vp]
+    L.vsz_slab_qstats.argtypes = [P(_CParams), vp, vp, vp]
+    L.vsz_compress_slab.argtypes = [P(_CParams), ctypes.c_int32, vp, P(_CCompressed), vp, sz, vp]
+    L.vsz_slab_rebase.argtypes = [P(_CParams), P(_CCompressed), u64, u64, vp]
     L.vsz_trace_enable.argtypes = [ctypes.c_int]
     L.vsz_trace_read.argtypes = [P(_CTrace), ctypes.c_int]
     for name in EXPORTED:
         if name.startswith(("vsz_tuner", "vsz_mlp", "vsz_sampling")):
             continue  # bound by tuner.py
         if name not in ("vsz_status_string", "vsz_last_cuda_error", "vsz_abi_version",
-                        "vsz_num_elems", "vsz_num_blocks", "vsz_workspace_size", "vsz_batch_workspace_size",
+                        "vsz_num_elems", "vsz_num_blocks", "vsz_workspace_size", "vsz_workspace_size_dense",
+                        "vsz_batch_workspace_size",
                         "vsz_huffman_book_bytes", "vsz_huffman_encode_workspace_size"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
@@ -259,6 +268,12 @@ def workspace_size(p: Params, out_cap: int, fix_cap: int) -> int:
     return int(lib().vsz_workspace_size(ctypes.byref(p.c()), out_cap, fix_cap))
 
 
+def workspace_size_dense(p: Params, out_cap: int, fix_cap: int) -> int:
+    """Bytes of a workspace with the dense-outlier buffers of a 2D/3D field
+    (vsz_workspace_size_dense): outlier-dense tiles are then read once."""
+    return int(lib().vsz_workspace_size_dense(ctypes.byref(p.c()), out_cap, fix_cap))
+
+
 def _stream_handle(stream) -> ctypes.c_void_p:
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
@@ -300,7 +315,7 @@ class Field:
         self.fix_idx = torch.empty(max(self.fix_cap, 1), dtype=i32, device=dev)
         self.fix_bits = torch.empty(max(self.fix_cap, 1), dtype=i32, device=dev)
         self.hdr = torch.zeros((HEADER_BYTES + 7) // 8, dtype=torch.int64, device=dev)
-        self.ws_bytes = workspace_size(params, self.out_cap, self.fix_cap)
+        self.ws_bytes = workspace_size_dense(params, self.out_cap, self.fix_cap)
         self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=dev)
         self.rws = torch.zeros(RECON_WS_BYTES // 4, dtype=torch.int32, device=dev)
         self._cp = params.c()
@@ -517,6 +532,18 @@ class Batch:
     def set_concurrent(self, on: bool):
         """Run the class kernels of each sequence as parallel branches."""
         _check(lib().vsz_batch_set_concurrent(self._h, 1 if on else 0), "vsz_batch_set_concurrent")
+
+    def set_concurrent_each(self, compress_on: bool, reconstruct_on: bool):
+        """set_concurrent for the compression and the reconstruction sequence separately."""
+        _check(lib().vsz_batch_set_concurrent_each(self._h, 1 if compress_on else 0, 1 if reconstruct_on else 0),
+               "vsz_batch_set_concurrent_each")
+
+    def concurrency(self) -> tuple:
+        """(compression, reconstruction) concurrent flags of the plan."""
+        cls = self.classes()
+        c = any(k["concurrent"] for k in cls if k["kind"] == 0)
+        r = any(k["concurrent"] for k in cls if k["kind"] == 1)
+        return c, r
 
     def autotune(self, stream=None, reps: int = 3, cache: str | None = None) -> list:
         """Tile autotuner (vsz_batch_autotune): synchronous; returns classes().

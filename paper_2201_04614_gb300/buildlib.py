@@ -20,7 +20,7 @@ BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(HERE, "libvsz.so")
 
 SOURCES = ["api.cu", "k_misc.cu", "k_batch.cu", "k_rank1.cu", "k_rank2.cu", "k_rank3.cu", "k_tuner.cu",
-           "k_huffman.cu"]
+           "k_huffman.cu", "k_shard.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC",
               "-Xcompiler", "-fvisibility=hidden"]

@@ -261,13 +261,33 @@ size_t vsz_workspace_size(const vsz_params* p, uint64_t out_cap, uint64_t fix_ca
     return ws_layout(g, out_cap, fix_cap).total;
 }
 
+size_t vsz_workspace_size_dense(const vsz_params* p, uint64_t out_cap, uint64_t fix_cap) {
+    Geom g;
+    if (make_geom(p, &g) != VSZ_OK) return 0;
+    return ws_layout(g, out_cap, fix_cap, true).total;
+}
+
 
 }  // extern "C"
 
 namespace vsz {
+// The workspace layout a call uses: block-slot staging for 2D/3D fields when
+// the workspace holds it (vsz_workspace_size_dense), else the plain one.
+static WsLayout layout_for(const Geom& g, const vsz_compressed* c, size_t ws_bytes, bool* slots) {
+    if (g.nd >= 2) {
+        const WsLayout Ls = ws_layout(g, c->out_cap, c->fix_cap, true);
+        if (ws_bytes >= Ls.total) {
+            *slots = true;
+            return Ls;
+        }
+    }
+    *slots = false;
+    return ws_layout(g, c->out_cap, c->fix_cap);
+}
+
 // Kernel arguments of one field's compression over its workspace.
 static CompressArgs compress_args(const Geom& g, const vsz_params* p, const float* d_x, const vsz_compressed* c,
-                                  char* ws, const WsLayout& L) {
+                                  char* ws, const WsLayout& L, bool slots) {
     CompressArgs a;
     std::memset(&a, 0, sizeof a);
     a.x = d_x;
@@ -281,7 +301,6 @@ static CompressArgs compress_args(const Geom& g, const vsz_params* p, const floa
     a.stage_out = (uint2*)(ws + L.stage_out);
     a.stage_fix = (uint2*)(ws + L.stage_fix);
     if (defers_origin(p->pad)) {
-        a.tstats = (TileStats*)(ws + L.tstats);
         a.origin = (int32_t*)(ws + L.origin);
         a.oflag = (uint8_t*)(ws + L.oflag);
     }
@@ -295,20 +314,22 @@ static CompressArgs compress_args(const Geom& g, const vsz_params* p, const floa
     a.R = (int32_t)p->radius;
     a.pad_mode = p->pad;
     a.vec = (aligned(d_x, 16) && aligned(c->codes, 16) && (g.nd == 1 || g.nx % 4 == 0)) ? 1 : 0;
+    if (slots) a.slots = a.stage_out;
     return a;
 }
 }  // namespace vsz
 
 extern "C" {
 
-vsz_status vsz_prequant_lorenzo(const vsz_params* p, const float* d_x, vsz_compressed* c, void* d_ws,
-                                size_t ws_bytes, void* stream) {
+static vsz_status prequant_lorenzo_impl(const vsz_params* p, const float* d_x, vsz_compressed* c, void* d_ws,
+                                        size_t ws_bytes, void* stream, const int32_t* given_pad) {
     Geom g;
     vsz_status st = make_geom(p, &g);
     if (st != VSZ_OK) return st;
     if ((st = check_compressed(g, p, c)) != VSZ_OK) return st;
     if (g.n > 0 && !d_x) return VSZ_ERR_INVALID_ARG;
-    const WsLayout L = ws_layout(g, c->out_cap, c->fix_cap);
+    bool slots = false;
+    const WsLayout L = layout_for(g, c, ws_bytes, &slots);
     if (!d_ws || ws_bytes < L.total || !aligned(d_ws, 256)) return VSZ_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     char* ws = (char*)d_ws;
@@ -330,7 +351,11 @@ vsz_status vsz_prequant_lorenzo(const vsz_params* p, const float* d_x, vsz_compr
     }
     if (g.ntiles == 0) return VSZ_OK;
 
-    const CompressArgs a = compress_args(g, p, d_x, c, ws, L);
+    CompressArgs a = compress_args(g, p, d_x, c, ws, L, slots);
+    if (given_pad) {
+        a.has_gpad = 1;
+        a.gpad = *given_pad;
+    }
     {
         TraceScope ts("lorenzo", s, g.nd, g.b, g.n);
         e = g.nd == 1 ? launch_lorenzo_1d(a, s) : g.nd == 2 ? launch_lorenzo_2d(a, s) : launch_lorenzo_3d(a, s);
@@ -346,13 +371,27 @@ vsz_status vsz_prequant_lorenzo(const vsz_params* p, const float* d_x, vsz_compr
     return VSZ_OK;
 }
 
+vsz_status vsz_prequant_lorenzo(const vsz_params* p, const float* d_x, vsz_compressed* c, void* d_ws,
+                                size_t ws_bytes, void* stream) {
+    return prequant_lorenzo_impl(p, d_x, c, d_ws, ws_bytes, stream, nullptr);
+}
+
+vsz_status vsz_compress_slab(const vsz_params* p, int32_t pad_value, const float* d_x, vsz_compressed* c,
+                             void* d_ws, size_t ws_bytes, void* stream) {
+    if (!p || p->eb_mode != VSZ_EB_ABS) return VSZ_ERR_INVALID_ARG;
+    vsz_status st = prequant_lorenzo_impl(p, d_x, c, d_ws, ws_bytes, stream, &pad_value);
+    if (st != VSZ_OK) return st;
+    return vsz_outlier_compact(p, c, d_ws, ws_bytes, stream);
+}
+
 vsz_status vsz_outlier_compact(const vsz_params* p, vsz_compressed* c, void* d_ws, size_t ws_bytes,
                                void* stream) {
     Geom g;
     vsz_status st = make_geom(p, &g);
     if (st != VSZ_OK) return st;
     if ((st = check_compressed(g, p, c)) != VSZ_OK) return st;
-    const WsLayout L = ws_layout(g, c->out_cap, c->fix_cap);
+    bool slots = false;
+    const WsLayout L = layout_for(g, c, ws_bytes, &slots);
     if (!d_ws || ws_bytes < L.total || !aligned(d_ws, 256)) return VSZ_ERR_INVALID_ARG;
     char* ws = (char*)d_ws;
     cudaStream_t s = (cudaStream_t)stream;
@@ -364,7 +403,7 @@ vsz_status vsz_outlier_compact(const vsz_params* p, vsz_compressed* c, void* d_w
     if (e != cudaSuccess) return cuda_fail(e);
     if (g.nchunks > 0) {
         TraceScope ts("compact_move", s, g.nd, g.b, g.n);
-        e = launch_compact_move(compress_args(g, p, nullptr, c, ws, L), s);
+        e = launch_compact_move(compress_args(g, p, nullptr, c, ws, L, slots), s);
     }
     if (e != cudaSuccess) return cuda_fail(e);
     return VSZ_OK;

@@ -23,6 +23,16 @@ constexpr int kSegCols = 128;
 constexpr int kChunk1D = 4096;
 constexpr int kTilesPerChunk = 32;   // tiles per compaction chunk (one CTA each)
 
+// Block-slot staging of the 2D/3D compression: when the workspace holds
+// it, the staging area has one slot of b^nd + 1 entries per block, and the
+// walk writes each outlier straight into its block's slot (position 1 + its
+// rank in the block; slot 0 holds the origin of a per-block padding mode).
+// No outlier needs a stash, a sort or a second walk, however dense they are;
+// the compaction moves each slot's entries to their final place.
+__host__ __device__ constexpr uint64_t block_slot(int nd, uint32_t b) {
+    return (nd == 3 ? (uint64_t)b * b * b : (uint64_t)b * b) + 1;
+}
+
 struct Geom {
     int32_t nd;
     uint32_t b;
@@ -40,9 +50,9 @@ struct Geom {
 struct WsHeader {
     unsigned long long stage_out;  // staging cursors
     unsigned long long stage_fix;
-    unsigned long long qsum;       // sum of q, two's complement
+    unsigned long long qsum;       // sum of q, two's complement (global padding)
     unsigned int xmin_ord, xmax_ord;  // order-preserving encodings of finite min/max
-    int qmin, qmax;
+    int qmin, qmax;                // extremes of q (global min / max padding)
     unsigned int done0, done1;     // last-block counters
     unsigned int nonfinite;        // a range pass met a NaN or Inf
     unsigned int fp32_ok;          // every |x * inv2eb| < 2^20 and no NaN/Inf (relative mode only)
@@ -50,16 +60,10 @@ struct WsHeader {
 };
 static_assert(sizeof(WsHeader) <= 256, "ws header");
 
-// q statistics of one tile (global padding modes).
-struct __align__(16) TileStats {
-    int32_t qmin, qmax;
-    long long qsum;
-};
 
 struct WsLayout {
     size_t tiles;      // uint4 per tile {stage_base_out, tot_out, stage_base_fix, tot_fix}
     size_t chunks;     // uint4 per chunk {sum_out, sum_fix, off_out, off_fix}
-    size_t tstats;     // TileStats per tile: q statistics (global padding)
     size_t origin;     // int32 per block: q at the block origin, then its residual (global padding)
     size_t oflag;      // uint8 per block: the origin is an outlier (global padding)
     size_t stage_out;  // uint2 per outlier {idx, delta}
@@ -69,15 +73,18 @@ struct WsLayout {
 
 inline size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
-inline WsLayout ws_layout(const Geom& g, uint64_t out_cap, uint64_t fix_cap) {
+// slots: the staging area of outliers laid out as block slots (2D/3D only).
+inline WsLayout ws_layout(const Geom& g, uint64_t out_cap, uint64_t fix_cap, bool slots = false) {
+    if (slots && g.nd >= 2) {
+        const uint64_t need = g.nb * block_slot(g.nd, g.b);
+        if (out_cap < need) out_cap = need;
+    }
     WsLayout L;
     size_t off = 256;
     L.tiles = off;
     off = align256(off + g.ntiles * 16);
     L.chunks = off;
     off = align256(off + g.nchunks * 16);
-    L.tstats = off;
-    off = align256(off + g.ntiles * 16);
     L.origin = off;
     off = align256(off + g.nb * 4);
     L.oflag = off;
@@ -181,7 +188,6 @@ struct CompressArgs {
     uint4* chunks;
     uint2* stage_out;
     uint2* stage_fix;
-    TileStats* tstats;     // [ntiles] q statistics per tile (global padding modes)
     int32_t* origin;       // [nb] block-origin q / residual (global padding modes)
     uint8_t* oflag;        // [nb] origin-outlier flags (global padding modes)
     uint32_t* out_idx;     // final lists (used by the batch compaction)
@@ -193,6 +199,9 @@ struct CompressArgs {
     int32_t R;
     int32_t pad_mode;
     int32_t vec;           // 16-byte vector path allowed
+    uint2* slots;          // block-slot staging (2D/3D: stage_out laid out as nb slots), or nullptr
+    int32_t has_gpad;      // a global padding value given by the caller (a slab of a split field)
+    int32_t gpad;
 };
 
 struct ReconArgs {
@@ -238,6 +247,26 @@ __host__ __device__ inline void block_origin(const Geom& g, uint64_t blk, uint64
     const uint64_t bz = r32 / nby, by = r32 - (uint32_t)bz * nby;
     *idx = (bz * g.b * g.ny + by * g.b) * g.nx + bx * g.b;
     *tile = r * g.nseg + (bx * g.b) / kSegCols;
+}
+
+// A tile's q statistics into its field's global-padding accumulators
+// (workspace header, zeroed by the first kernel of the call): the sum, and
+// the extremes for a min or max mode.  Integer sums and extremes do not
+// depend on the order of the tiles.
+__device__ __forceinline__ void global_stats_add(const CompressArgs& a, int32_t qmin, int32_t qmax, long long qsum) {
+    atomicAdd(&a.wsh->qsum, (unsigned long long)qsum);
+    if (a.pad_mode == VSZ_PAD_GLOBAL_MIN) atomicMin(&a.wsh->qmin, qmin);
+    if (a.pad_mode == VSZ_PAD_GLOBAL_MAX) atomicMax(&a.wsh->qmax, qmax);
+}
+
+// The global padding value (Sec. IV-B-1) once every tile is added: the
+// minimum, the maximum, or the rounded mean of q over the field.
+__device__ __forceinline__ int32_t global_pad_value(const CompressArgs& a) {
+    if (a.has_gpad) return a.gpad;  // the whole field's, for one slab of it
+    if (a.g.n == 0) return 0;
+    return a.pad_mode == VSZ_PAD_GLOBAL_MIN ? a.wsh->qmin
+         : a.pad_mode == VSZ_PAD_GLOBAL_MAX ? a.wsh->qmax
+         : rounded_mean((long long)a.wsh->qsum, (long long)a.g.n);
 }
 
 // Programmatic dependent launch.  Every kernel of the one-field sequence
@@ -310,6 +339,7 @@ cudaError_t launch_recon_batch_3d(uint32_t b, const ReconArgs* fields, const uin
                                   int* occ = nullptr);
 
 int num_sms();
+
 int grid_for(const void* kernel, int threads, size_t smem, uint64_t work_items_per_cta, uint64_t work);
 // Resident CTAs per SM of `kernel` at this block size and dynamic shared
 // memory (0 if it cannot launch), cached per (kernel, threads, smem).

@@ -4,7 +4,8 @@
 // per chunk of 32 tiles, turns the in-tile block offsets left by the
 // compression kernel into global ones and moves each tile's staged outliers
 // and fixups, which are contiguous both in staging and in the final lists, to
-// their canonical place.  Both bodies serve the single-field kernels
+// their canonical place.  With block-slot staging (2D/3D) part 2 gathers the
+// tile's outliers from its blocks' slots instead.  Both bodies serve the single-field kernels
 // (k_misc.cu) and the batch kernels (k_batch.cu).
 #pragma once
 
@@ -196,6 +197,116 @@ __device__ __forceinline__ void compact_chunk_body(uint64_t chunk, const Compres
     }
 }
 
+// Compaction, part 2, with block-slot staging (2D/3D): per chunk of tiles
+// (one CTA, one warp per tile), the tiles' offsets as above, each block's
+// final offset (lane k holds block k of the tile: at most 32 per tile), the
+// origin outlier a global or edge padding mode made (first in its block),
+// then each block's slot moved to its place: entries from slot 1 on, or from
+// slot 0 when a per-block padding mode put the block's origin there.
+__device__ __forceinline__ void compact_chunk_body_slots(uint64_t chunk, const CompressArgs& a) {
+    __shared__ uint4 rec[kTilesPerChunk];
+    __shared__ uint32_t toff_o[kTilesPerChunk], toff_f[kTilesPerChunk];
+    const Geom& g = a.g;
+    const uint64_t ntiles = g.ntiles, nseg = g.nseg, nbx = g.nbx;
+    const uint32_t bpt = g.bpt;
+    const uint64_t S = block_slot(g.nd, g.b);
+    const bool bp = is_block_pad(a.pad_mode);
+    const uint64_t t0 = chunk * kTilesPerChunk;
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (w == 0) {  // the chunk's tile offsets: chunk offset + exclusive scan of the tile totals
+        uint32_t bo = a.chunks[chunk].z, bf = a.chunks[chunk].w;
+        for (int i0 = 0; i0 < kTilesPerChunk; i0 += 32) {
+            const uint64_t t = t0 + i0 + l;
+            const uint4 r = t < ntiles ? a.tiles[t] : make_uint4(0, 0, 0, 0);
+            uint32_t io = r.y, iff = r.w;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const uint32_t yo = __shfl_up_sync(VSZ_FULL, io, off);
+                const uint32_t yf = __shfl_up_sync(VSZ_FULL, iff, off);
+                if (l >= off) { io += yo; iff += yf; }
+            }
+            rec[i0 + l] = r;
+            toff_o[i0 + l] = bo + io - r.y;
+            toff_f[i0 + l] = bf + iff - r.w;
+            bo += __shfl_sync(VSZ_FULL, io, 31);
+            bf += __shfl_sync(VSZ_FULL, iff, 31);
+        }
+    }
+    __syncthreads();
+
+    const int nt = (int)umin64(kTilesPerChunk, ntiles - t0);
+    for (int j = w; j < nt; j += 8) {
+        const uint64_t tt = t0 + j;
+        const uint4 rr = rec[j];
+        const uint32_t to = toff_o[j], tf = toff_f[j];
+        const uint64_t s = tt % nseg;
+        const uint64_t fb = (tt / nseg) * nbx + s * bpt;
+        const uint32_t nblk = (uint32_t)umin64(bpt, nbx - s * bpt);
+        const bool has = (uint32_t)l < nblk;
+        const uint64_t blk = fb + (uint64_t)l;
+        const uint32_t flag = (has && a.oflag && a.oflag[blk] != 0) ? 1u : 0u;
+        const uint32_t fl = __ballot_sync(VSZ_FULL, flag != 0u);
+        const uint32_t staged = rr.y - (uint32_t)__popc(fl);
+        const uint32_t eo = has ? a.blk_off[blk] : staged;  // in-tile offset, without origin outliers
+        uint32_t nx = __shfl_down_sync(VSZ_FULL, eo, 1);
+        if ((uint32_t)l + 1 >= nblk) nx = staged;
+        const uint32_t cnt = has ? nx - eo : 0u;
+        const uint32_t fin = to + eo + (uint32_t)__popc(fl & ((1u << l) - 1u));  // the block's final offset
+        const bool fits = (uint64_t)to + rr.y <= a.out_cap;
+        if (has) {
+            a.blk_off[blk] = fin;
+            if (flag && fits) {
+                uint64_t idx, tile;
+                block_origin(g, blk, &idx, &tile);
+                a.out_idx[fin] = (uint32_t)idx;
+                a.out_delta[fin] = a.origin[blk];
+            }
+        }
+        if (fits && staged) {
+            // a per-block padding mode's slot 0: the origin outlier, or the marker
+            uint32_t start = 1;
+            if (bp && has && cnt) start = a.slots[blk * S].x != 0xffffffffu ? 0u : 1u;
+            // each block's slot to its place, four blocks at a time so that
+            // every lane has up to four loads in flight
+            const uint64_t sbase = (uint64_t)blk * S + start;  // the slot's first entry
+            const uint32_t dbase = fin + flag;                  // the block's first non-origin place
+            for (uint32_t kk0 = 0; kk0 < nblk; kk0 += 4) {
+                uint32_t c[4], d0[4], cmax = 0;
+                uint64_t sb[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int kk = (int)((kk0 + q) & 31u);
+                    c[q] = __shfl_sync(VSZ_FULL, cnt, kk);
+                    d0[q] = __shfl_sync(VSZ_FULL, dbase, kk);
+                    sb[q] = __shfl_sync(VSZ_FULL, sbase, kk);
+                    if (kk0 + q >= nblk) c[q] = 0;
+                    cmax = c[q] > cmax ? c[q] : cmax;
+                }
+                for (uint32_t i = l; i < cmax; i += 32) {
+                    uint2 e[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (i < c[q]) e[q] = a.slots[sb[q] + i];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        if (i < c[q]) {
+                            a.out_idx[d0[q] + i] = e[q].x;
+                            a.out_delta[d0[q] + i] = (int32_t)e[q].y;
+                        }
+                    }
+                }
+            }
+        }
+        if (rr.w && (uint64_t)rr.z + rr.w <= a.fix_cap && (uint64_t)tf + rr.w <= a.fix_cap) {
+            for (uint32_t k = l; k < rr.w; k += 32) {
+                const uint2 e = a.stage_fix[rr.z + k];
+                a.fix_idx[tf + k] = e.x;
+                a.fix_bits[tf + k] = e.y;
+            }
+        }
+    }
+}
+
 // The origin pass of a global padding mode, for block `blk`: the residual
 // of the block origin q - P, its code, and whether it is an outlier (then
 // counted in its tile and chunk before the compaction).
@@ -211,51 +322,6 @@ __device__ __forceinline__ void origin_fix_block(const CompressArgs& a, uint64_t
         a.origin[blk] = d;
         atomicAdd(&a.tiles[tile].y, 1u);
         atomicAdd(&a.chunks[tile / kTilesPerChunk].x, 1u);
-    }
-}
-
-// The global padding value (Sec. IV-B-1) from the tiles' q statistics (one
-// CTA of 1024 threads per field, a fixed reduction order): the minimum, the
-// maximum, or the rounded mean of q; written to the field's header.
-__device__ __forceinline__ void pad_reduce_body(const CompressArgs& a) {
-    __shared__ int smn[32], smx[32];
-    __shared__ long long ssm[32];
-    int mn = INT_MAX, mx = INT_MIN;
-    long long sm = 0;
-    for (uint64_t t = threadIdx.x; t < a.g.ntiles; t += blockDim.x) {
-        const TileStats st = a.tstats[t];
-        mn = min(mn, st.qmin);
-        mx = max(mx, st.qmax);
-        sm += st.qsum;
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        mn = min(mn, __shfl_xor_sync(VSZ_FULL, mn, off));
-        mx = max(mx, __shfl_xor_sync(VSZ_FULL, mx, off));
-        sm += __shfl_xor_sync(VSZ_FULL, sm, off);
-    }
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) { smn[w] = mn; smx[w] = mx; ssm[w] = sm; }
-    __syncthreads();
-    if (w == 0) {
-        const int nw = (int)(blockDim.x >> 5);
-        mn = l < nw ? smn[l] : INT_MAX;
-        mx = l < nw ? smx[l] : INT_MIN;
-        sm = l < nw ? ssm[l] : 0;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            mn = min(mn, __shfl_xor_sync(VSZ_FULL, mn, off));
-            mx = max(mx, __shfl_xor_sync(VSZ_FULL, mx, off));
-            sm += __shfl_xor_sync(VSZ_FULL, sm, off);
-        }
-        if (l == 0) {
-            int32_t P = 0;
-            if (a.g.n > 0)
-                P = a.pad_mode == VSZ_PAD_GLOBAL_MIN ? mn
-                  : a.pad_mode == VSZ_PAD_GLOBAL_MAX ? mx
-                  : rounded_mean(sm, (long long)a.g.n);
-            const_cast<vsz_header*>(a.hdr)->pad_global = P;
-        }
     }
 }
 

@@ -29,17 +29,22 @@
 // Every input byte is read once from HBM and every code written once.
 //
 // The pass over a batch is branch-free: each row's residuals go to a
-// lane-private history and a flag bit marks rows that may hold an outlier or
-// a fixup.  After the batch, flagged rows (rare) are re-examined exactly and
-// their outliers and fixups appended to a per-warp stash in shared memory
-// (walk order).  At the end of the tile one atomic reserves
-// the tile's staging range and the stash is scattered into canonical order
-// (blocks in row-major order, row-major inside a block) with a counting
-// sort keyed by block: inside one block the walk order is already the
-// canonical order.  A tile whose stash overflows is walked a second time
-// (int32 arithmetic, no code stores), and each outlier or fixup is written
-// straight to its canonical place from per-block running ranks.  Tiles are
-// handed out by an atomic ticket, so warps that finish early take more.
+// lane-private history and two flag bits per row mark rows that may hold an
+// outlier or a fixup.  After the batch, flagged rows are re-examined exactly
+// (the guard only for rows flagged for it).  Inside one block the walk order
+// is the canonical order (blocks in row-major order, row-major inside a
+// block), so:
+//  - with block-slot staging (a workspace of vsz_workspace_size_dense), each
+//    outlier goes straight to its block's slot at 1 + its rank in the block
+//    (a scan over the block's b/4 lanes); fixups go to a per-warp stash;
+//  - otherwise outliers and fixups both go to the stash (walk order).
+// At the end of the tile one atomic reserves the tile's staging range of
+// what the stash holds, and the stash is scattered into canonical order with
+// a counting sort keyed by block.  A tile whose stash overflows counts only
+// from then on and is walked a second time (int32 arithmetic, no code
+// stores, no guard when the tile has no fixup), which writes each stashed
+// kind straight to its canonical place from per-block running ranks.  Tiles
+// are handed out by an atomic ticket, so warps that finish early take more.
 #pragma once
 
 #include <climits>
@@ -98,14 +103,22 @@ struct NdCfg {
     static constexpr size_t STASH_B = (size_t)STASH * 8;
     static constexpr size_t TAB_B = 128 * 4;
     static constexpr size_t HIST_B = (size_t)U * 32 * 16;  // residuals of the current batch
-    static constexpr size_t WARP_C = RING_C + STASH_B + TAB_B + ZS_B + HIST_B;
+    static constexpr size_t CNT_B = 3 * 32 * 4;            // per lane: outliers, fixups, segment fill
+    static constexpr size_t WARP_C = RING_C + STASH_B + TAB_B + ZS_B + HIST_B + CNT_B;
     static constexpr size_t SMEM_C = WARP_C * WARPS;
     // per-warp shared memory, reconstruction: ring of codes | z state | outliers of the tile
     static constexpr int OCAP = 256;
     static constexpr size_t RING_R = (size_t)NSR * U * 32 * 8;
     static constexpr size_t OC_B = (size_t)OCAP * 8;
-    static constexpr size_t WARP_R = RING_R + ZS_B + OC_B;
+    // the outliers' residuals of the current batch of an interior tile: 3D
+    // blocks up to 8 keep them in the z-state area (their z sums are in
+    // registers), every other shape in an area of its own
+    static constexpr size_t PS_RAW = (size_t)U * 32 * 16;
+    static constexpr size_t PS_B = (ND == 3 && B <= 8) ? 0 : PS_RAW;
+    static constexpr size_t WARP_R = RING_R + ZS_B + OC_B + PS_B;
     static constexpr size_t SMEM_R = WARP_R * WARPS;
+    // staging entries per block in the block-slot layout
+    static constexpr uint64_t SLOT = block_slot(ND, B);
 };
 
 __device__ __forceinline__ int32_t wsub(int32_t a, int32_t b) { return (int32_t)((uint32_t)a - (uint32_t)b); }
@@ -134,6 +147,12 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
     uint32_t* run = pre_out + 64;  // 64 counters: [fix][group]
     int4* zs = reinterpret_cast<int4*>(wsm + C::RING_C + C::STASH_B + C::TAB_B);
     int4* dh = reinterpret_cast<int4*>(wsm + C::RING_C + C::STASH_B + C::TAB_B + C::ZS_B) + lane;
+    // counters the rare path updates, kept in shared memory (lane-private) so
+    // that they hold no register through the walk
+    uint32_t* const cnt = reinterpret_cast<uint32_t*>(wsm + C::RING_C + C::STASH_B + C::TAB_B + C::ZS_B + C::HIST_B) + lane;
+    cnt[0] = 0;   // outliers of this lane's columns
+    cnt[32] = 0;  // fixups of this lane's columns
+    cnt[64] = 0;  // outliers of this lane's block in its buffer segment (first walk)
     const float4* ring_rd = reinterpret_cast<const float4*>(wsm) + lane;  // slot (h*U + u)*32
     const uint32_t ring_wr = smem_addr(wsm) + lane * 16;
 
@@ -202,7 +221,7 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
     };
 
     // results of the first pass that the second pass needs
-    uint32_t cnt_out = 0, cnt_fix = 0, nst = 0;
+    uint32_t nst = 0;
     int32_t Pb = BP || GP ? 0 : Pg;
     uint32_t eo_g = 0, ef_g = 0;
     unsigned long long base_out = 0, base_fix = 0;
@@ -210,6 +229,8 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
     uint32_t r0c01 = 0, r0c23 = 0;
     int32_t smin = INT_MAX, smax = INT_MIN;
     float sminf = __int_as_float(0x7f800000), smaxf = -__int_as_float(0x7f800000);
+    // an average padding needs only the sum of q
+    const bool need_mm = (BP || GP) && a.pad_mode != VSZ_PAD_GLOBAL_AVG && a.pad_mode != VSZ_PAD_BLOCK_AVG;
     long long ssum = 0;
 
     // Rare path of one batch: exact masks of the flagged rows; counts and
@@ -217,8 +238,16 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
     // Rows of a batch stored raw by the fp32 mode get their outliers' codes
     // zeroed here.
     uint32_t run_o = 0, run_f = 0;  // running ranks inside this lane's block (second walk)
-    auto rare_rows = [&](uint32_t rows, int h, uint64_t boff, int j, int lz, bool b0, bool imode, bool raw,
-                         bool emit) {
+    // block slots of the staging area (2D/3D, when the workspace holds
+    // them): block k's outliers at slots[k * S + 1 ...] in walk order, which
+    // inside a block is the canonical order; slot 0 holds the origin of a
+    // per-block padding mode
+    uint2* const slots = a.slots;
+    uint2* const myslot = slots ? slots + (bexists ? blk : 0) * (uint64_t)C::SLOT : nullptr;
+    bool ovf = false;               // the stash overflowed: count only, then walk again
+    bool nofix = false;             // second walk of a tile without fixups: no guard checks
+    auto rare_rows = [&](uint32_t rows, uint32_t rows_f, int h, uint64_t boff, int j, int lz, bool b0, bool imode,
+                         bool raw, bool emit) {
         while (rows) {
             const int u = __ffs(rows) - 1;
             rows &= rows - 1;
@@ -235,9 +264,11 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
             const float xv[4] = {v.x, v.y, v.z, v.w};
             uint32_t om = 0, fm = 0;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                om |= (code_of(d[k], R) == 0u ? 1u : 0u) << k;
-                fm |= (needs_fixup(xv[k], prequant(xv[k], inv2eb), ebx2, ebf) ? 1u : 0u) << k;
+            for (int k = 0; k < 4; ++k) om |= (code_of(d[k], R) == 0u ? 1u : 0u) << k;
+            if ((rows_f >> u) & 1u) {  // warp-uniform: some lane of this row may need a fixup
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    fm |= (needs_fixup(xv[k], prequant(xv[k], inv2eb), ebx2, ebf) ? 1u : 0u) << k;
             }
             om &= vmask;
             fm &= vmask;
@@ -256,28 +287,56 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
             if (((BP && !emit) || GP) && b0 && u == 0 && first) om &= ~1u;  // the origin waits for P
             const uint32_t co = __popc(om), cf = __popc(fm);
             if (!emit) {
-                cnt_out += co;
-                cnt_fix += cf;
-                const uint32_t cl = co + cf;
-                uint32_t incl = cl;
+                cnt[0] += co;
+                cnt[32] += cf;
+                if (slots && __any_sync(VSZ_FULL, om != 0u)) {
+                    // outliers to the block's slot: rank among the block's lanes
+                    uint32_t io = co;
 #pragma unroll
-                for (int off = 1; off < 32; off <<= 1) {
-                    const uint32_t y = __shfl_up_sync(VSZ_FULL, incl, off);
-                    if (lane >= off) incl += y;
-                }
-                uint32_t pos = nst + incl - cl;
-                const uint32_t total = __shfl_sync(VSZ_FULL, incl, 31);
-                if (nst + total <= (uint32_t)C::STASH) {
-                    const uint32_t row = (uint32_t)(lz * ylen + ly);
+                    for (int off = 1; off < G; off <<= 1) {
+                        const uint32_t y = __shfl_up_sync(VSZ_FULL, io, off);
+                        if (glane >= off) io += y;
+                    }
+                    const uint32_t seg_o = cnt[64];
+                    uint32_t pos = seg_o + io - co;
+                    const uint32_t idx0 = (uint32_t)(boff + (uint64_t)u * nx);
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
-                        if (om & (1u << k))
-                            stash[pos++] = make_uint2(stash_key(0, grp, row, lane * 4 + k), (uint32_t)d[k]);
-                        if (fm & (1u << k))
-                            stash[pos++] = make_uint2(stash_key(1, grp, row, lane * 4 + k), __float_as_uint(xv[k]));
+                        if (om & (1u << k)) {
+                            myslot[1 + pos] = make_uint2(idx0 + k, (uint32_t)d[k]);
+                            ++pos;
+                        }
                     }
+                    const uint32_t seg_n = seg_o + __shfl_sync(VSZ_FULL, io, src + G - 1);
+                    cnt[64] = seg_n;
                 }
-                nst += total;
+                // the stash overflowed: the tile is walked again for what the
+                // stash holds, and counts are all this walk still needs
+                if (ovf) continue;
+                const uint32_t oms = slots ? 0u : om;  // outliers that go to the stash
+                const uint32_t cl = __popc(oms) + cf;
+                if (__any_sync(VSZ_FULL, cl != 0u)) {
+                    uint32_t incl = cl;
+#pragma unroll
+                    for (int off = 1; off < 32; off <<= 1) {
+                        const uint32_t y = __shfl_up_sync(VSZ_FULL, incl, off);
+                        if (lane >= off) incl += y;
+                    }
+                    uint32_t pos = nst + incl - cl;
+                    const uint32_t total = __shfl_sync(VSZ_FULL, incl, 31);
+                    if (nst + total <= (uint32_t)C::STASH) {
+                        const uint32_t row = (uint32_t)(lz * ylen + ly);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            if (oms & (1u << k))
+                                stash[pos++] = make_uint2(stash_key(0, grp, row, lane * 4 + k), (uint32_t)d[k]);
+                            if (fm & (1u << k))
+                                stash[pos++] = make_uint2(stash_key(1, grp, row, lane * 4 + k), __float_as_uint(xv[k]));
+                        }
+                    }
+                    nst += total;
+                    ovf = ovf || nst > (uint32_t)C::STASH;
+                }
             } else {
                 // ranks inside the block: earlier rows, then earlier lanes of this row
                 uint32_t io = co, iff = cf;
@@ -292,8 +351,8 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
                 const uint32_t idx0 = (uint32_t)(boff + (uint64_t)u * nx);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    if (om & (1u << k)) {
-                        if (po < a.out_cap) a.stage_out[po] = make_uint2(idx0 + k, (uint32_t)d[k]);
+                    if (om & (1u << k)) {  // (with block slots the first walk placed them)
+                        if (!slots && po < a.out_cap) a.stage_out[po] = make_uint2(idx0 + k, (uint32_t)d[k]);
                         ++po;
                     }
                     if (fm & (1u << k)) {
@@ -392,22 +451,25 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
                     dh[u * 32] = make_int4(__float_as_int(d[0]), __float_as_int(d[1]), __float_as_int(d[2]),
                                            __float_as_int(d[3]));
                     uint32_t cb[4];
-                    bool flag = false;
+                    bool fo = false, ff = false;
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
                         cb[k] = __float_as_uint(__fadd_rn(d[k], RB));
                         const float xh = __fmul_rn(rp[k], ebx2);
-                        flag |= !(fabsf(d[k]) < Rf) | !(fabsf(__fsub_rn(xv[k], xh)) <= ebf);
+                        fo |= !(fabsf(d[k]) < Rf);
+                        ff |= !(fabsf(__fsub_rn(xv[k], xh)) <= ebf);
                     }
                     if (BP || GP) {
-                        sminf = fminf(sminf, fminf(fminf(rp[0], rp[1]), fminf(rp[2], rp[3])));
-                        smaxf = fmaxf(smaxf, fmaxf(fmaxf(rp[0], rp[1]), fmaxf(rp[2], rp[3])));
+                        if (need_mm) {
+                            sminf = fminf(sminf, fminf(fminf(rp[0], rp[1]), fminf(rp[2], rp[3])));
+                            smaxf = fmaxf(smaxf, fmaxf(fmaxf(rp[0], rp[1]), fmaxf(rp[2], rp[3])));
+                        }
                         // the row sum is an integer below 2^22: exact in fp32, converted by the
                         // 1.5 * 2^23 bias; a batch's sum stays below 2^24
                         const float rs = __fadd_rn(__fadd_rn(__fadd_rn(rp[0], rp[1]), rp[2]), rp[3]);
                         lsum += __float_as_int(__fadd_rn(rs, kMagic)) - 0x4B400000;
                     }
-                    fmask |= flag ? (1u << u) : 0u;
+                    fmask |= (fo ? (1u << u) : 0u) | (ff ? (0x100u << u) : 0u);
                     const uint32_t c01 = __byte_perm(cb[0], cb[1], 0x5410), c23 = __byte_perm(cb[2], cb[3], 0x5410);
                     if (BP && u == 0 && kb == 0) {
                         r0c01 = c01;
@@ -417,7 +479,9 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
                 }
                 if ((BP || GP) && kb == 0) qcorner = __float2int_rn(__int_as_float(dh[0].x));
                 const uint32_t rows = __reduce_or_sync(VSZ_FULL, fmask);
-                if (rows) rare_rows(rows, h, tile_base + off32(kb), jb, kb / BPP, kb == 0, false, true, false);
+                if (rows)
+                    rare_rows((rows | (rows >> 8)) & 0xffu, rows >> 8, h, tile_base + off32(kb), jb, kb / BPP, kb == 0,
+                              false, true, false);
                 h = h + 1 == C::NS ? 0 : h + 1;
                 if (BP || GP) {
                     ssum += lsum;
@@ -523,12 +587,13 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
                     // raw codes: the low 16 bits of fl(d + R + 2^23) are d + R
                     // whenever |d| < R; outlier rows are rewritten below
                     uint32_t cb[4];
-                    bool flag = false;
+                    bool fo = false, ff = false;
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
                         cb[k] = __float_as_uint(__fadd_rn(d[k], RB));
                         const float xh = __fmul_rn(rp[k], ebx2);
-                        flag |= !(fabsf(d[k]) < Rf) | !(fabsf(__fsub_rn(xr[u][k], xh)) <= ebf);
+                        fo |= !(fabsf(d[k]) < Rf);
+                        ff |= !(fabsf(__fsub_rn(xr[u][k], xh)) <= ebf);
                     }
                     if (BP || GP) {
                         float rs = 0.f;
@@ -542,7 +607,7 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
                         }
                         ssum += __float2int_rn(rs);
                     }
-                    fmask |= flag ? (1u << u) : 0u;
+                    fmask |= (fo ? (1u << u) : 0u) | (ff ? (0x100u << u) : 0u);
                     const uint32_t c01 = __byte_perm(cb[0], cb[1], 0x5410), c23 = __byte_perm(cb[2], cb[3], 0x5410);
                     if (BP && b0 && u == 0) {
                         r0c01 = c01;
@@ -585,18 +650,19 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
                     }
                     dh[u * 32] = make_int4(d[0], d[1], d[2], d[3]);
                     uint32_t c[4];
-                    bool flag = false;
+                    bool fo = false, ff = false;
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
                         c[k] = code_of(d[k], R);
-                        flag |= (c[k] == 0u) | needs_fixup(xr[u][k], q[k], ebx2, ebf);
+                        fo |= c[k] == 0u;
+                        if (!nofix) ff |= needs_fixup(xr[u][k], q[k], ebx2, ebf);
                         if ((BP || GP) && !emit && k < valid) {
                             smin = min(smin, q[k]);
                             smax = max(smax, q[k]);
                             ssum += q[k];
                         }
                     }
-                    fmask |= flag ? (1u << u) : 0u;
+                    fmask |= (fo ? (1u << u) : 0u) | (ff ? (0x100u << u) : 0u);
                     if (!emit) {
                         const uint32_t c01 = c[0] | (c[1] << 16), c23 = c[2] | (c[3] << 16);
                         if (BP && b0 && u == 0) {
@@ -610,7 +676,7 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
             }
             // Rare path: rows that may hold an outlier or a fixup.
             const uint32_t rows = __reduce_or_sync(VSZ_FULL, valid ? fmask : 0u);
-            if (rows) rare_rows(rows, h, boff, j, lz, b0, imode, raw, emit);
+            if (rows) rare_rows((rows | (rows >> 8)) & 0xffu, rows >> 8, h, boff, j, lz, b0, imode, raw, emit);
             h = h + 1 == C::NS ? 0 : h + 1;
             hi = hi + 1 == C::NS ? 0 : hi + 1;
             lz = nlz;
@@ -643,8 +709,12 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
                 dcorner = wsub(qcorner, Pb);
                 const uint32_t cc = code_of(dcorner, R);
                 corner_out = (cc == 0u) ? 1u : 0u;
-                cnt_out += corner_out;
+                cnt[0] += corner_out;
                 r0c01 = (r0c01 & 0xffff0000u) | cc;
+                // block slots: slot 0 holds the origin outlier, or a marker
+                // index that no element has
+                if (slots) myslot[0] = corner_out ? make_uint2((uint32_t)tile_base, (uint32_t)dcorner)
+                                                  : make_uint2(0xffffffffu, 0u);
             }
             store4c(a.codes + tile_base, valid, vst, r0c01, r0c23);
         }
@@ -660,12 +730,12 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
                 smax = max(smax, __shfl_xor_sync(VSZ_FULL, smax, off));
                 ssum += __shfl_xor_sync(VSZ_FULL, ssum, off);
             }
-            if (lane == 0) a.tstats[t] = TileStats{smin, smax, ssum};
+            if (lane == 0) global_stats_add(a, smin, smax, ssum);
             if (first && bexists) a.origin[blk] = qcorner;
         }
 
         // Per-block counts, in-tile exclusive offsets (blk_off), tile totals.
-        uint32_t bo = cnt_out, bf = cnt_fix;
+        uint32_t bo = cnt[0], bf = cnt[32];
 #pragma unroll
         for (int off = 1; off < G; off <<= 1) {
             bo += __shfl_xor_sync(VSZ_FULL, bo, off);
@@ -689,7 +759,7 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
 
         if (tot_out | tot_fix) {
             if (lane == 0) {
-                if (tot_out) base_out = atomicAdd(&a.wsh->stage_out, (unsigned long long)tot_out);
+                if (tot_out && !slots) base_out = atomicAdd(&a.wsh->stage_out, (unsigned long long)tot_out);
                 if (tot_fix) base_fix = atomicAdd(&a.wsh->stage_fix, (unsigned long long)tot_fix);
                 uint4* ch = a.chunks + t / kTilesPerChunk;
                 if (tot_out) atomicAdd(&ch->x, tot_out);
@@ -701,13 +771,14 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
         if (lane == 0)
             a.tiles[t] = make_uint4((uint32_t)base_out, tot_out, (uint32_t)base_fix, tot_fix);
         if (!(tot_out | tot_fix)) break;
-        if (nst > (uint32_t)C::STASH) continue;  // stash overflow: second walk
+        nofix = tot_fix == 0u;
+        if (ovf) continue;  // stash or segment overflow: second walk
 
         // Counting sort of the stash into canonical order.
         if (first) {
             pre_out[grp] = (uint32_t)base_out + eo + corner_out;
             pre_fix[grp] = (uint32_t)base_fix + ef;
-            if (BP && corner_out) {
+            if (BP && corner_out && !slots) {
                 const uint64_t pos = base_out + eo;
                 if (pos < a.out_cap) a.stage_out[pos] = make_uint2((uint32_t)tile_base, (uint32_t)dcorner);
             }

@@ -151,9 +151,6 @@ __global__ void __launch_bounds__(256) k_batch_range(const BatchField* __restric
 }
 
 // Global padding value of every global-padding field (one CTA per field).
-__global__ void __launch_bounds__(1024) k_batch_pad_reduce(const BatchField* __restrict__ F) {
-    if (F[blockIdx.x].gpad) pad_reduce_body(F[blockIdx.x].a);
-}
 
 // Face statistics of every edge-padding field: items are warp units (tiles,
 // or 32 blocks in 1D), one warp each.
@@ -168,15 +165,31 @@ __global__ void __launch_bounds__(256) k_batch_edge_stats(const BatchField* __re
 }
 
 // Origin pass of every global- or edge-padding field: items are blocks.
+// Each warp takes 32 consecutive blocks: one search for the field of the
+// first, then a step forward for lanes past that field's end.
 __global__ void __launch_bounds__(256) k_batch_origin_fix(const BatchField* __restrict__ F, int nf,
                                                           const uint64_t* __restrict__ prefix, uint64_t nitems) {
-    for (uint64_t item = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; item < nitems;
-         item += (uint64_t)gridDim.x * blockDim.x) {
-        const int f = find_field(prefix, nf, item);
+    const int lane = threadIdx.x & 31;
+    const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    for (uint64_t w0 = ((uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; w0 < nitems;
+         w0 += nwarps * 32) {
+        int f = 0;
+        if (lane == 0) f = find_field(prefix, nf, w0);
+        f = __shfl_sync(VSZ_FULL, f, 0);
+        const uint64_t item = w0 + (uint64_t)lane;
+        if (item >= nitems) continue;
+        while (item >= prefix[f + 1]) ++f;
         const CompressArgs& a = F[f].a;
         const uint64_t blk = item - prefix[f];
         const int nd = a.g.nd;
-        origin_fix_block(a, blk, F[f].epad ? edge_origin_pred(a.pad + blk * (uint64_t)nd, nd) : a.hdr->pad_global);
+        int32_t P;
+        if (F[f].epad) {
+            P = edge_origin_pred(a.pad + blk * (uint64_t)nd, nd);
+        } else {
+            P = global_pad_value(a);
+            if (blk == 0) const_cast<vsz_header*>(a.hdr)->pad_global = P;
+        }
+        origin_fix_block(a, blk, P);
     }
 }
 
@@ -192,7 +205,8 @@ __global__ void __launch_bounds__(256) k_batch_compact_move(const BatchField* __
     for (uint64_t item = blockIdx.x; item < nchunks; item += gridDim.x) {
         const int f = find_field(prefix, nf, item);
         const CompressArgs& a = F[f].a;
-        compact_chunk_body(item - prefix[f], a);
+        if (a.slots) compact_chunk_body_slots(item - prefix[f], a);
+        else compact_chunk_body(item - prefix[f], a);
         __syncthreads();
     }
 }
@@ -264,12 +278,21 @@ struct vsz_batch_st {
     cudaGraphExec_t rexec = nullptr;
 };
 
+// Class of a job: (rank, block edge, padding kind 0 zero / 1 per block / 2 global or edge).
+using ClassKey = std::tuple<int, uint32_t, int>;
+static ClassKey class_key(const vsz_field_job& j, const Geom& g) {
+    const int32_t m = j.params.pad;
+    return std::make_tuple(g.nd, g.b, is_block_pad(m) ? 1 : (is_global_pad(m) || is_edge_pad(m)) ? 2 : 0);
+}
+
+// Workspace of a batch: the header, then every field's workspace (2D/3D
+// fields with block-slot staging).
 static size_t batch_layout(const vsz_field_job* jobs, int n, std::vector<size_t>* offs, std::vector<Geom>* geoms) {
     size_t off = kBatchHeader;  // batch header: class tickets
     for (int i = 0; i < n; ++i) {
         Geom g;
         if (make_geom(&jobs[i].params, &g) != VSZ_OK) return 0;
-        const WsLayout L = ws_layout(g, jobs[i].out.out_cap, jobs[i].out.fix_cap);
+        const WsLayout L = ws_layout(g, jobs[i].out.out_cap, jobs[i].out.fix_cap, true);
         if (offs) offs->push_back(off);
         if (geoms) geoms->push_back(g);
         off = align256(off + L.total);
@@ -407,7 +430,12 @@ static vsz_status launch_recon_sequence(vsz_batch_st* b, cudaStream_t s, const C
     const vsz_status st = run_classes(b, 1, s, tm);
     if (st != VSZ_OK) return st;
     TraceScope ts("batch_fixups", s);
-    k_batch_fixups<<<dim3((unsigned)b->n, 4), 256, 0, s>>>(b->d_fix);
+    // enough CTAs per field for its list capacity (fields with few fixups
+    // leave most of them idle at once)
+    uint64_t fcap = 0;
+    for (const vsz_field_job& j : b->jobs) fcap = j.out.fix_cap > fcap ? j.out.fix_cap : fcap;
+    const unsigned fy = (unsigned)umin64(256, umin64(65535, (fcap + 2047) / 2048 + 1));
+    k_batch_fixups<<<dim3((unsigned)b->n, fy), 256, 0, s>>>(b->d_fix);
     return (e = cudaGetLastError()) == cudaSuccess ? VSZ_OK : cuda_fail(e);
 }
 
@@ -438,7 +466,6 @@ static vsz_status launch_sequence(vsz_batch_st* b, cudaStream_t s, const ClassTi
     }
     if (b->origin_items) {
         TraceScope ts("batch_origin_fix", s);
-        k_batch_pad_reduce<<<b->n, 1024, 0, s>>>(b->d_fields);
         const int grid = grid_for((const void*)k_batch_origin_fix, 256, 0, 256, b->origin_items);
         k_batch_origin_fix<<<grid, 256, 0, s>>>(b->d_fields, b->n, b->d_ob_prefix, b->origin_items);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
@@ -487,11 +514,11 @@ vsz_status vsz_batch_create(const vsz_field_job* jobs, int njobs, void* d_ws, si
     char* ws = (char*)d_ws;
     b->tickets = (unsigned long long*)ws;
     std::vector<uint64_t> rp(1, 0), qp(1, 0), cp(1, 0), ep(1, 0);
-    std::map<std::tuple<int, uint32_t, int>, int> cls;
+    std::map<ClassKey, int> cls;
     for (int i = 0; i < njobs; ++i) {
         const vsz_field_job& j = jobs[i];
         const Geom& g = geoms[i];
-        const WsLayout L = ws_layout(g, j.out.out_cap, j.out.fix_cap);
+        const WsLayout L = ws_layout(g, j.out.out_cap, j.out.fix_cap, true);
         char* fw = ws + offs[i];
         BatchField bf;
         std::memset(&bf, 0, sizeof bf);
@@ -507,7 +534,6 @@ vsz_status vsz_batch_create(const vsz_field_job* jobs, int njobs, void* d_ws, si
         a.stage_out = (uint2*)(fw + L.stage_out);
         a.stage_fix = (uint2*)(fw + L.stage_fix);
         if (defers_origin(j.params.pad)) {
-            a.tstats = (TileStats*)(fw + L.tstats);
             a.origin = (int32_t*)(fw + L.origin);
             a.oflag = (uint8_t*)(fw + L.oflag);
         }
@@ -525,14 +551,15 @@ vsz_status vsz_batch_create(const vsz_field_job* jobs, int njobs, void* d_ws, si
         bf.rel = j.params.eb_mode == VSZ_EB_REL;
         bf.gpad = is_global_pad(j.params.pad) ? 1 : 0;
         bf.epad = is_edge_pad(j.params.pad) ? 1 : 0;
+        if (g.nd >= 2) a.slots = a.stage_out;  // block-slot staging
         b->fields.push_back(bf);
         const uint64_t items = (g.n + kItemElems - 1) / kItemElems;
         rp.push_back(rp.back() + (bf.rel ? (items ? items : 1) : 0));
         qp.push_back(qp.back() + (bf.gpad || bf.epad ? g.nb : 0));
         ep.push_back(ep.back() + (bf.epad ? edge_units(g) : 0));
         cp.push_back(cp.back() + g.nchunks);
-        const int pk = is_block_pad(j.params.pad) ? 1 : (bf.gpad || bf.epad) ? 2 : 0;
-        const auto key = std::make_tuple(g.nd, g.b, pk);
+        const ClassKey key = class_key(j, g);
+        const int pk = std::get<2>(key);
         auto it = cls.find(key);
         if (it == cls.end()) {
             BatchClass c;
@@ -753,6 +780,14 @@ vsz_status vsz_batch_set_shape(vsz_batch b, int c, int warps, int ctas_per_sm) {
 vsz_status vsz_batch_set_concurrent(vsz_batch b, int on) {
     if (!b) return VSZ_ERR_INVALID_ARG;
     b->concurrent = b->rconcurrent = on != 0;
+    drop_graphs(b);
+    return VSZ_OK;
+}
+
+vsz_status vsz_batch_set_concurrent_each(vsz_batch b, int compress_on, int reconstruct_on) {
+    if (!b) return VSZ_ERR_INVALID_ARG;
+    b->concurrent = compress_on != 0;
+    b->rconcurrent = reconstruct_on != 0;
     drop_graphs(b);
     return VSZ_OK;
 }

@@ -104,20 +104,16 @@ __global__ void __launch_bounds__(1024) k_compact_scan(uint4* chunks, uint64_t n
 
 __global__ void __launch_bounds__(256) k_compact(const CompressArgs a) {
     pdl_prologue();
-    compact_chunk_body(blockIdx.x, a);
-}
-
-// Global padding value of one field from its tiles' q statistics.
-__global__ void __launch_bounds__(1024) k_pad_reduce(const CompressArgs a) {
-    pdl_prologue();
-    pad_reduce_body(a);
+    if (a.slots) compact_chunk_body_slots(blockIdx.x, a);
+    else compact_chunk_body(blockIdx.x, a);
 }
 
 // Origin pass of a global padding mode (one field): every block origin's
 // residual q - P and its code, P from the field's header.
 __global__ void __launch_bounds__(256) k_origin_fix(const CompressArgs a) {
     pdl_prologue();
-    const int32_t P = a.hdr->pad_global;
+    const int32_t P = global_pad_value(a);
+    if (blockIdx.x == 0 && threadIdx.x == 0) const_cast<vsz_header*>(a.hdr)->pad_global = P;
     for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < a.g.nb; b += (uint64_t)gridDim.x * blockDim.x)
         origin_fix_block(a, b, P);
 }
@@ -255,9 +251,7 @@ cudaError_t launch_origin_fix(const CompressArgs& a, cudaStream_t s) {
         const int go = grid_for((const void*)k_origin_fix_edge, 256, 0, 256, a.g.nb);
         return launch_pdl(k_origin_fix_edge, go, 256, 0, s, a);
     }
-    cudaError_t e = launch_pdl(k_pad_reduce, 1, 1024, 0, s, a);
-    if (e != cudaSuccess || a.g.nb == 0) return e;
-    const int grid = grid_for((const void*)k_origin_fix, 256, 0, 256, a.g.nb);
+    const int grid = grid_for((const void*)k_origin_fix, 256, 0, 256, a.g.nb ? a.g.nb : 1);
     return launch_pdl(k_origin_fix, grid, 256, 0, s, a);
 }
 

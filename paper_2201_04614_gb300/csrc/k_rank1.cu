@@ -86,9 +86,16 @@ struct Step1 {
     }
 };
 
+// Outliers a warp keeps in shared memory while it walks a tile, in linear
+// (= canonical) order; a tile with more, or with a step that needs the
+// integer path, writes its lists by walking its steps with entries again.
+constexpr int kStash1 = 512;
+constexpr int kStash1F = 128;  // fixups (rounding at the quantization boundaries)
+
 // All the work of one 4096-element tile t of a 1D field.
 template <int B, bool BP, bool GP>
-__device__ __forceinline__ void compress_1d_tile(const CompressArgs& a, uint64_t t, int lane) {
+__device__ __forceinline__ void compress_1d_tile(const CompressArgs& a, uint64_t t, int lane,
+                                                 uint2* __restrict__ stash, uint2* __restrict__ fstash) {
     using C = Cfg1<B>;
     constexpr int EPL = C::EPL, G = C::G, SPAN = C::SPAN;
     const float inv2eb = a.hdr->inv2eb;
@@ -100,16 +107,21 @@ __device__ __forceinline__ void compress_1d_tile(const CompressArgs& a, uint64_t
     const int glane = lane & (G - 1);
     const uint64_t start = t * kChunk1D;
     uint32_t run_out = 0, run_fix = 0, stepmask = 0;
+    uint32_t nst = 0;   // outliers met by fp32 steps (stashed while they fit)
+    uint32_t nfst = 0;  // fixups met by fp32 steps (stashed while they fit)
+    bool slow = false;  // a step took the integer path
     int32_t gmin = INT_MAX, gmax = INT_MIN;  // q statistics of the tile (global padding)
     long long gsum = 0;
     // The value-range pass proved every |x * inv2eb| < 2^20 and no NaN/Inf:
     // full steps then run in exact fp32 -- rounding by the 1.5 * 2^23 bias,
     // differences of integers below 2^21, the code as the low half of
-    // d + R + 2^23 -- and only steps whose warp holds an outlier or a fixup
-    // take the integer path below.
+    // d + R + 2^23 -- with the outliers' codes zeroed and the outliers kept
+    // in the warp's stash; only steps whose warp holds a fixup take the
+    // integer path below.
     constexpr float kMagic = 12582912.0f;
     const bool fast = a.wsh->fp32_ok != 0u && a.vec != 0 && (BP || GP || (Pg >= -(1 << 20) && Pg <= (1 << 20)));
     const float Rf = (float)R, RB = (float)(R + 8388608), Pgf = (float)Pg;
+    const bool need_mm = GP && a.pad_mode != VSZ_PAD_GLOBAL_AVG;
 #pragma unroll 2
     for (int st = 0; st < C::STEPS; ++st) {
         const uint64_t s0 = start + (uint64_t)st * SPAN;
@@ -149,15 +161,63 @@ __device__ __forceinline__ void compress_1d_tile(const CompressArgs& a, uint64_t
 #pragma unroll
             for (int k = 1; k < EPL; ++k) d[k] = __fsub_rn(rp[k], rp[k - 1]);
             uint32_t cb[EPL];
-            bool flag = false;
+            uint32_t om = 0, fm = 0;
 #pragma unroll
             for (int k = 0; k < EPL; ++k) {
                 cb[k] = __float_as_uint(__fadd_rn(d[k], RB)) & 0xffffu;
                 // an outlier (the origin of a global padding mode waits for the origin pass)
                 const bool out = !(fabsf(d[k]) < Rf) && !(GP && k == 0 && origin);
-                flag |= out | !(fabsf(__fsub_rn(xv[k], __fmul_rn(rp[k], ebx2))) <= ebf);
+                om |= out ? (1u << k) : 0u;
+                fm |= !(fabsf(__fsub_rn(xv[k], __fmul_rn(rp[k], ebx2))) <= ebf) ? (1u << k) : 0u;
             }
-            if (!__any_sync(VSZ_FULL, flag)) {
+            {
+                if (__any_sync(VSZ_FULL, fm != 0u)) {
+                    // fixups (no NaN or Inf here: rounding at a quantization
+                    // boundary), kept in order beside the outliers
+                    const uint32_t cf = __popc(fm);
+                    uint32_t iff = cf;
+#pragma unroll
+                    for (int off = 1; off < 32; off <<= 1) {
+                        const uint32_t y = __shfl_up_sync(VSZ_FULL, iff, off);
+                        if (lane >= off) iff += y;
+                    }
+                    uint32_t pos = nfst + iff - cf;
+#pragma unroll
+                    for (int k = 0; k < EPL; ++k) {
+                        if (fm & (1u << k)) {
+                            if (pos < (uint32_t)kStash1F) fstash[pos] = make_uint2((uint32_t)(base + k), __float_as_uint(xv[k]));
+                            ++pos;
+                        }
+                    }
+                    const uint32_t sf = __shfl_sync(VSZ_FULL, iff, 31);
+                    nfst += sf;
+                    run_fix += sf;
+                    stepmask |= 1u << st;  // walked again if the stashes cannot serve the tile
+                }
+                uint32_t ex = 0, so = 0;  // outliers of earlier lanes of the step, of the step
+                if (__any_sync(VSZ_FULL, om != 0u)) {
+                    const uint32_t co = __popc(om);
+                    uint32_t io = co;
+#pragma unroll
+                    for (int off = 1; off < 32; off <<= 1) {
+                        const uint32_t y = __shfl_up_sync(VSZ_FULL, io, off);
+                        if (lane >= off) io += y;
+                    }
+                    so = __shfl_sync(VSZ_FULL, io, 31);
+                    ex = io - co;
+                    uint32_t pos = nst + ex;
+#pragma unroll
+                    for (int k = 0; k < EPL; ++k) {
+                        if (om & (1u << k)) {
+                            cb[k] = 0u;
+                            if (pos < (uint32_t)kStash1)
+                                stash[pos] = make_uint2((uint32_t)(base + k), (uint32_t)__float2int_rn(d[k]));
+                            ++pos;
+                        }
+                    }
+                    nst += so;
+                    stepmask |= 1u << st;  // walked again if the stash cannot serve the tile
+                }
                 uint16_t* cp = a.codes + base;
                 if (EPL == 4) {
                     *reinterpret_cast<uint2*>(cp) = make_uint2(cb[0] | (cb[1] << 16), cb[2] | (cb[3 % EPL] << 16));
@@ -168,25 +228,31 @@ __device__ __forceinline__ void compress_1d_tile(const CompressArgs& a, uint64_t
                 }
                 if (origin) {
                     const uint64_t blk = base / B;
-                    a.blk_off[blk] = run_out;
+                    a.blk_off[blk] = run_out + ex;
                     if (BP) a.pad[blk] = Pb;
                     if (GP) a.origin[blk] = __float2int_rn(rp[0]);
                 }
+                run_out += so;
                 if (GP) {
-                    float mn = rp[0], mx = rp[0], ls = rp[0];
+                    float ls = rp[0];
 #pragma unroll
-                    for (int k = 1; k < EPL; ++k) {
-                        mn = fminf(mn, rp[k]);
-                        mx = fmaxf(mx, rp[k]);
-                        ls = __fadd_rn(ls, rp[k]);
-                    }
-                    gmin = min(gmin, __float2int_rn(mn));
-                    gmax = max(gmax, __float2int_rn(mx));
+                    for (int k = 1; k < EPL; ++k) ls = __fadd_rn(ls, rp[k]);
                     gsum += __float2int_rn(ls);
+                    if (need_mm) {  // a min or max mode
+                        float mn = rp[0], mx = rp[0];
+#pragma unroll
+                        for (int k = 1; k < EPL; ++k) {
+                            mn = fminf(mn, rp[k]);
+                            mx = fmaxf(mx, rp[k]);
+                        }
+                        gmin = min(gmin, __float2int_rn(mn));
+                        gmax = max(gmax, __float2int_rn(mx));
+                    }
                 }
                 continue;
             }
         }
+        slow = true;
         Step1<B, BP, GP> S;
         S.run(a, base, lane, inv2eb, Pg);
         uint32_t co = 0, cf = 0;
@@ -247,7 +313,7 @@ __device__ __forceinline__ void compress_1d_tile(const CompressArgs& a, uint64_t
             gmax = max(gmax, __shfl_xor_sync(VSZ_FULL, gmax, off));
             gsum += __shfl_xor_sync(VSZ_FULL, gsum, off);
         }
-        if (lane == 0) a.tstats[t] = TileStats{gmin, gmax, gsum};
+        if (lane == 0) global_stats_add(a, gmin, gmax, gsum);
     }
     unsigned long long base_out = 0, base_fix = 0;
     if (run_out | run_fix) {
@@ -263,6 +329,16 @@ __device__ __forceinline__ void compress_1d_tile(const CompressArgs& a, uint64_t
     }
     if (lane == 0) a.tiles[t] = make_uint4((uint32_t)base_out, run_out, (uint32_t)base_fix, run_fix);
 
+    if (!slow && nst <= (uint32_t)kStash1 && nfst <= (uint32_t)kStash1F) {
+        // every entry comes from an fp32 step, stashed in order
+        __syncwarp();
+        for (uint32_t j = lane; j < nst; j += 32)
+            if (base_out + j < a.out_cap) a.stage_out[base_out + j] = stash[j];
+        for (uint32_t j = lane; j < nfst; j += 32)
+            if (base_fix + j < a.fix_cap) a.stage_fix[base_fix + j] = fstash[j];
+        __syncwarp();
+        return;
+    }
     // Emission in linear (= canonical) order, only for steps with entries.
     uint64_t ko = base_out, kf = base_fix;
     while (stepmask) {
@@ -308,13 +384,15 @@ __device__ __forceinline__ void compress_1d_tile(const CompressArgs& a, uint64_t
 template <int B, bool BP, bool GP>
 __global__ void __launch_bounds__(256) k_lorenzo_1d(const CompressArgs a) {
     pdl_prologue();
+    __shared__ uint2 stash[8][kStash1];
+    __shared__ uint2 fstash[8][kStash1F];
     const int lane = threadIdx.x & 31;
     for (;;) {
         unsigned long long tk = 0;
         if (lane == 0) tk = atomicAdd(&a.wsh->ticket, 1ull);
         const uint64_t t = __shfl_sync(VSZ_FULL, tk, 0);
         if (t >= a.g.ntiles) break;
-        compress_1d_tile<B, BP, GP>(a, t, lane);
+        compress_1d_tile<B, BP, GP>(a, t, lane, stash[threadIdx.x >> 5], fstash[threadIdx.x >> 5]);
     }
 }
 
@@ -324,6 +402,8 @@ template <int B, bool BP, bool GP>
 __global__ void __launch_bounds__(256) k_lorenzo_1d_batch(const CompressArgs* __restrict__ fields,
                                                           const uint64_t* __restrict__ tile_prefix, int nfields,
                                                           unsigned long long* ticket) {
+    __shared__ uint2 stash[8][kStash1];
+    __shared__ uint2 fstash[8][kStash1F];
     const int lane = threadIdx.x & 31;
     const uint64_t total = tile_prefix[nfields];
     for (;;) {
@@ -336,7 +416,8 @@ __global__ void __launch_bounds__(256) k_lorenzo_1d_batch(const CompressArgs* __
             const int mid = (lo + hi + 1) >> 1;
             if (tile_prefix[mid] <= gt) lo = mid; else hi = mid - 1;
         }
-        compress_1d_tile<B, BP, GP>(fields[lo], gt - tile_prefix[lo], lane);
+        compress_1d_tile<B, BP, GP>(fields[lo], gt - tile_prefix[lo], lane, stash[threadIdx.x >> 5],
+                                    fstash[threadIdx.x >> 5]);
     }
 }
 

@@ -36,7 +36,7 @@ __device__ __forceinline__ void nd_recon_tile(const ReconArgs& a, const uint64_t
     // interior tiles of 3D blocks up to 8 keep their z sums in registers, so
     // their outlier cache may also take the z-state area in front of it
     constexpr bool ZREG_R = ND == 3 && B <= 8;
-    constexpr uint32_t OCAP_BIG = (uint32_t)((C::ZS_B + C::OC_B) / 8);
+    constexpr uint32_t OCAP_BIG = (uint32_t)((C::ZS_B + C::OC_B - C::PS_RAW) / 8);  // ps takes the end
     const uint2* ring_rd = reinterpret_cast<const uint2*>(wsm) + lane;  // slot (h*U + u)*32
     const uint32_t ring_wr = smem_addr(wsm) + lane * 8;
 
@@ -119,6 +119,124 @@ __device__ __forceinline__ void nd_recon_tile(const ReconArgs& a, const uint64_t
         }
     }
 
+    // Outliers of one batch of an interior tile (every code 0 of its U rows),
+    // fetched at once: the k-th code 0 met in a block (planes, rows, then x)
+    // is the block's k-th outlier, so each one's rank is the block's running
+    // rank plus the code-0 counts of the earlier rows of the batch, of the
+    // block's earlier lanes in its row, and of the lane's earlier columns.
+    // The residuals land in ps (per lane and row), from where the row walk
+    // takes them; a tile whose outliers are cached in shared memory reads
+    // them from there, four at a time.
+    int4* const ps = reinterpret_cast<int4*>(wsm + C::RING_R + C::ZS_B + C::OC_B - (ZREG_R ? C::PS_RAW : 0)) + lane;
+    auto patch_batch = [&](const uint2 (&cw)[U], uint32_t base, uint32_t nx32) {
+        uint32_t zm = 0;  // bit u*4 + k: code 0 at row u, column k
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            zm |= (((cw[u].x & 0xffffu) == 0u) ? 1u : 0u) << (4 * u);
+            zm |= (((cw[u].x >> 16) == 0u) ? 2u : 0u) << (4 * u);
+            zm |= (((cw[u].y & 0xffffu) == 0u) ? 4u : 0u) << (4 * u);
+            zm |= (((cw[u].y >> 16) == 0u) ? 8u : 0u) << (4 * u);
+        }
+        // code-0 counts per row, one byte each (at most 4 per lane, 4G per block)
+        uint32_t pk = 0;
+#pragma unroll
+        for (int u = 0; u < U; ++u) pk |= (uint32_t)__popc((zm >> (4 * u)) & 0xfu) << (8 * u);
+        uint32_t inc = pk;
+#pragma unroll
+        for (int off = 1; off < G; off <<= 1) {
+            const uint32_t y = __shfl_up_sync(VSZ_FULL, inc, off);
+            if (glane >= off) inc += y;
+        }
+        const uint32_t tot = __shfl_sync(VSZ_FULL, inc, src + G - 1);  // the block's count per row
+        const uint32_t excl = inc - pk;                                  // earlier lanes of the block, per row
+        uint32_t rowpre[U];                                              // earlier rows of the batch
+        rowpre[0] = rank;
+#pragma unroll
+        for (int u = 1; u < U; ++u) rowpre[u] = rowpre[u - 1] + ((tot >> (8 * (u - 1))) & 0xffu);
+        auto rank_of = [&](uint32_t jq) {
+            const uint32_t u = jq >> 2, k = jq & 3u;
+            uint32_t rb = rowpre[0];
+#pragma unroll
+            for (int w = 1; w < U; ++w) rb = u == (uint32_t)w ? rowpre[w] : rb;
+            return rb + ((excl >> (8 * u)) & 0xffu) + (uint32_t)__popc((zm >> (4 * u)) & ((1u << k) - 1u));
+        };
+        if (!cached) {
+            // Outliers from the global lists: every one of the batch copied
+            // into shared memory at once (index beside residual, in the cache
+            // area this tile leaves unused), then one wait: a batch costs one
+            // memory latency however many outliers it holds.  The wait also
+            // completes the ring's prefetched batches, which stay valid.
+            int32_t* const pi = reinterpret_cast<int32_t*>(reinterpret_cast<int4*>(oc_idx) + lane);
+            int32_t* const pd = reinterpret_cast<int32_t*>(ps);
+            const uint32_t spi = smem_addr(pi), spd = smem_addr(pd);
+            uint32_t m = zm;
+#pragma unroll 1
+            while (m) {
+                const uint32_t jq = (uint32_t)(__ffs(m) - 1);
+                m &= m - 1u;
+                const uint32_t r = rank_of(jq);
+                const uint32_t off = (jq >> 2) * 32 * 16 + (jq & 3u) * 4;  // row u of the lane's column, entry k
+                if (r < hi && r < a.out_cap) {
+                    cp_async4(spi + off, a.out_idx + r, 4u);
+                    cp_async4(spd + off, a.out_delta + r, 4u);
+                } else {
+                    pi[off / 4] = -1;  // no such outlier: reported below
+                }
+            }
+            cp_async_commit();
+            cp_async_wait<0>();
+            m = zm;
+#pragma unroll 1
+            while (m) {
+                const uint32_t jq = (uint32_t)(__ffs(m) - 1);
+                m &= m - 1u;
+                const uint32_t off = (jq >> 2) * 32 * 4 + (jq & 3u);  // in 4-byte words
+                if ((uint32_t)pi[off] != base + (jq >> 2) * nx32 + (jq & 3u)) {
+                    atomicMax(&a.hdr->recon_status, (unsigned)VSZ_ERR_CORRUPT);
+                    pd[off] = 0;
+                }
+            }
+            rank = rowpre[U - 1] + ((tot >> (8 * (U - 1))) & 0xffu);
+            return;
+        }
+        uint32_t m = zm;
+#pragma unroll 1
+        while (m) {
+            uint32_t jj[4], rr[4], oi[4];
+            int32_t od[4];
+            bool v[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                v[q] = m != 0u;
+                jj[q] = v[q] ? (uint32_t)(__ffs(m) - 1) : 0u;
+                m &= m - 1u;
+                rr[q] = rank_of(jj[q]);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const bool in = v[q] && rr[q] < hi && rr[q] < a.out_cap;
+                oi[q] = ~0u;
+                od[q] = 0;
+                if (in) {
+                    oi[q] = cached ? oc_idx[rr[q] - lo_t] : a.out_idx[rr[q]];
+                    od[q] = cached ? oc_del[rr[q] - lo_t] : a.out_delta[rr[q]];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (!v[q]) continue;
+                const uint32_t u = jj[q] >> 2, k = jj[q] & 3u;
+                int32_t val = od[q];
+                if (oi[q] != base + u * nx32 + k) {
+                    atomicMax(&a.hdr->recon_status, (unsigned)VSZ_ERR_CORRUPT);
+                    val = 0;
+                }
+                reinterpret_cast<int32_t*>(ps + u * 32)[k] = val;
+            }
+        }
+        rank = rowpre[U - 1] + ((tot >> (8 * (U - 1))) & 0xffu);
+    };
+
     // copy the codes of batch (lz, j) into ring half h (vector path only)
     auto issue_batch = [&](int lz, int j, int h) {
         if (vec) {
@@ -191,6 +309,7 @@ __device__ __forceinline__ void nd_recon_tile(const ReconArgs& a, const uint64_t
                           ((cw[u].y - 0x00010001u) & ~cw[u].y & 0x80008000u);
                 }
                 const bool patch = anyout && __any_sync(VSZ_FULL, hz != 0u);
+                if (patch) patch_batch(cw, (uint32_t)tile_base + boff, nx32);
                 // one copy of the row code (the patch test is a uniform
                 // branch), which keeps the unrolled plane loop small
                 auto lrow = [&](int u) {
@@ -198,37 +317,12 @@ __device__ __forceinline__ void nd_recon_tile(const ReconArgs& a, const uint64_t
                     int32_t d[4];
 #pragma unroll
                     for (int k = 0; k < 4; ++k) d[k] = (int32_t)c[k] - R;
-                    if (patch) {
-                        uint32_t zm = 0;
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) zm |= (c[k] == 0u ? 1u : 0u) << k;
-                        if (__any_sync(VSZ_FULL, zm != 0u)) {
-                            const uint32_t cz = __popc(zm);
-                            uint32_t iz = cz;
-#pragma unroll
-                            for (int off = 1; off < G; off <<= 1) {
-                                const uint32_t y = __shfl_up_sync(VSZ_FULL, iz, off);
-                                if (glane >= off) iz += y;
-                            }
-                            const uint32_t gtot = __shfl_sync(VSZ_FULL, iz, src + G - 1);
-                            uint32_t r = rank + (iz - cz);
-                            const uint32_t roff = (uint32_t)tile_base + boff + (uint32_t)u * nx32;
-#pragma unroll
-                            for (int k = 0; k < 4; ++k) {
-                                if (zm & (1u << k)) {
-                                    const bool in = r < hi && r < a.out_cap;
-                                    const uint32_t oi = !in ? ~0u : cached ? oc_idx[r - lo_t] : a.out_idx[r];
-                                    if (in && oi == roff + k) {
-                                        d[k] = cached ? oc_del[r - lo_t] : a.out_delta[r];
-                                    } else {
-                                        atomicMax(&a.hdr->recon_status, (unsigned)VSZ_ERR_CORRUPT);
-                                        d[k] = 0;
-                                    }
-                                    ++r;
-                                }
-                            }
-                            rank += gtot;
-                        }
+                    if (patch) {  // the outliers' residuals, fetched for the whole batch
+                        const int4 pv = ps[u * 32];
+                        d[0] = c[0] ? d[0] : pv.x;
+                        d[1] = c[1] ? d[1] : pv.y;
+                        d[2] = c[2] ? d[2] : pv.z;
+                        d[3] = c[3] ? d[3] : pv.w;
                     }
                     // Sx
                     d[1] = wadd(d[1], d[0]);

@@ -10,6 +10,7 @@ import subprocess
 import pytest
 
 import paper_2201_04614_gb300 as vsz
+from paper_2201_04614_gb300 import shard
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 STRUCTS = {
@@ -20,6 +21,7 @@ STRUCTS = {
     "vsz_batch_class": vsz._CBatchClass,
     "vsz_trace_record": vsz._CTrace,
     "vsz_host_field": vsz._CHostField,
+    "vsz_slab_stats": shard._SlabStats,
 }
 
 
