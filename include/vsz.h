@@ -702,6 +702,15 @@ VSZ_API vsz_status vsz_sync_status(const vsz_compressed* c, void* stream);
  * VSZ_ERR_INVALID_ARG. */
 VSZ_API vsz_status vsz_debug_fail_alloc(int k);
 
+/* Bounds-checking build (compiled with -DVSZ_DEBUG_BOUNDS; a checking aid,
+ * since no memory checker is available on every machine): the kernels check
+ * the index of each write to a field-sized buffer (codes, values, lists,
+ * block slots, tables) and of each read of the block slots and outlier
+ * caches; an access out of its buffer is skipped and the site recorded.
+ * Reads the first recorded site number (0 if none) into *out and clears it.
+ * The normal build checks nothing and returns VSZ_ERR_UNSUPPORTED with 0. */
+VSZ_API vsz_status vsz_debug_bounds_word(uint32_t* out);
+
 /* Release what the library holds itself: tracing is switched off, pending
  * trace records are dropped and the recorder's CUDA events destroyed, and
  * the per-device and per-kernel caches of launch parameters (SM counts,

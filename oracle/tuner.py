@@ -184,14 +184,28 @@ def sweep_costs(x, dims, eb, eb_mode, radius) -> np.ndarray:
     return out
 
 
+# Estimated sizes within this fraction of the least count as equal, and the
+# padding that costs least to compute wins among them: zero, then per block
+# (a table written during the walk), then global (a statistic of the whole
+# field and a second pass over the block origins).
+SIZE_TOL = 0.005
+PAD_RANK = (0, 2, 1)  # by padslot: zero, global average, block average
+
+
 def label(costs) -> int:
-    """Cheapest class, ties to the lowest index."""
+    """The label of a field from its classes' estimated sizes: among the
+    classes within SIZE_TOL of the least size, the one with the cheapest
+    padding (PAD_RANK), then the smaller size, then the lower index."""
     costs = np.asarray(costs, np.float64)
-    best = 0
-    for c in range(1, costs.size):
-        if costs[c] < costs[best]:
-            best = c
-    return best
+    lo = float(np.min(costs))
+    best = None
+    for c in range(costs.size):
+        if not (costs[c] <= lo * (1.0 + SIZE_TOL)):
+            continue
+        key = (PAD_RANK[c % 3], float(costs[c]), c)
+        if best is None or key < best[0]:
+            best = (key, c)
+    return best[1]
 
 
 # ---------------------------------------------------------------- network
@@ -272,4 +286,11 @@ def adam_step(theta, grad, m, v, t: int, lr: float, beta1: float = 0.9, beta2: f
 def predict(theta, mu, sigma, X, masks) -> np.ndarray:
     """Most probable allowed class per sample, ties to the lowest index."""
     zm, _, _ = forward(theta, mu, sigma, X, masks)
-    return np.array([label(-row) for row in zm], np.int64)
+    out = []
+    for row in zm:
+        best = 0
+        for c in range(1, row.size):
+            if row[c] > row[best]:
+                best = c
+        out.append(best)
+    return np.array(out, np.int64)

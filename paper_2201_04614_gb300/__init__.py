@@ -94,7 +94,7 @@ EXPORTED = ["vsz_status_string", "vsz_last_cuda_error", "vsz_abi_version", "vsz_
             "vsz_batch_compress_host", "vsz_slab_range", "vsz_slab_qstats", "vsz_compress_slab", "vsz_slab_rebase",
             "vsz_huffman_book_bytes", "vsz_huffman_book", "vsz_huffman_book_read", "vsz_huffman_encode",
             "vsz_huffman_encode_workspace_size", "vsz_sampling_autotune_workspace_size", "vsz_sampling_autotune",
-            "vsz_sync_status", "vsz_shutdown", "vsz_debug_fail_alloc",
+            "vsz_sync_status", "vsz_shutdown", "vsz_debug_fail_alloc", "vsz_debug_bounds_word",
             "vsz_huffman_decode",
             "vsz_tuner_features_workspace_size", "vsz_tuner_features",
             "vsz_tuner_sweep_workspace_size", "vsz_tuner_sweep", "vsz_tuner_guard_workspace_size",
@@ -170,6 +170,7 @@ def lib():
     L.vsz_compress_slab.argtypes = [P(_CParams), ctypes.c_int32, vp, P(_CCompressed), vp, sz, vp]
     L.vsz_slab_rebase.argtypes = [P(_CParams), P(_CCompressed), u64, u64, vp]
     L.vsz_trace_enable.argtypes = [ctypes.c_int]
+    L.vsz_debug_bounds_word.argtypes = [P(ctypes.c_uint32)]
     L.vsz_trace_read.argtypes = [P(_CTrace), ctypes.c_int]
     for name in EXPORTED:
         if name.startswith(("vsz_tuner", "vsz_mlp", "vsz_sampling")):
@@ -181,6 +182,14 @@ def lib():
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
+
+
+def debug_bounds_word():
+    """The first out-of-bounds site recorded by a bounds-checking build (and
+    clears it); None for the normal build."""
+    v = ctypes.c_uint32(0)
+    rc = lib().vsz_debug_bounds_word(ctypes.byref(v))
+    return None if rc == 2 else int(v.value)
 
 
 def trace_enable(on: bool = True) -> None:

@@ -7,6 +7,7 @@
 #include <mutex>
 #include <tuple>
 #include <unordered_map>
+#include <vector>
 
 #include "common.cuh"
 #include "misc.cuh"
@@ -48,6 +49,14 @@ static void reset_launch_caches() {
     g_smem_attr.clear();
     for (void*& p : g_noalloc_addr) p = nullptr;
 }
+
+#ifdef VSZ_DEBUG_BOUNDS
+std::vector<unsigned int (*)()>& bounds_readers() {
+    static std::vector<unsigned int (*)()> v;  // one reader per translation unit
+    return v;
+}
+void register_bounds_reader(unsigned int (*reader)()) { bounds_readers().push_back(reader); }
+#endif
 
 int num_sms() {
     int dev = 0;
@@ -237,6 +246,27 @@ const char* vsz_status_string(vsz_status s) {
 }
 
 const char* vsz_last_cuda_error(void) { return g_last_err; }
+
+vsz_status vsz_debug_bounds_word(uint32_t* out) {
+    if (!out) return VSZ_ERR_INVALID_ARG;
+#ifdef VSZ_DEBUG_BOUNDS
+    uint32_t v = 0;
+    std::vector<unsigned int (*)()> rs;
+    {
+        std::lock_guard<std::mutex> lk(g_cache_mu);
+        rs = bounds_readers();
+    }
+    for (auto r : rs) {
+        const uint32_t w = r();
+        if (!v) v = w;
+    }
+    *out = v;
+    return VSZ_OK;
+#else
+    *out = 0;
+    return VSZ_ERR_UNSUPPORTED;
+#endif
+}
 
 int vsz_abi_version(void) { return VSZ_ABI_VERSION; }
 

@@ -97,6 +97,38 @@ inline WsLayout ws_layout(const Geom& g, uint64_t out_cap, uint64_t fix_cap, boo
     return L;
 }
 
+// ---- bounds-checking build ----------------------------------------------------
+// Built with -DVSZ_DEBUG_BOUNDS, the kernels check the index of each of their
+// writes to the field-sized buffers (codes, values, lists, slots, tables)
+// and of their reads of the slots and outlier caches against the buffer's
+// length; an access that would fall outside is skipped and its site number
+// recorded in a device word (first site wins; nothing traps).  Every
+// translation unit has its own word and registers a reader at load time;
+// vsz_debug_bounds_word() reads and clears them all.  In the normal build the
+// checks compile away.
+#ifdef VSZ_DEBUG_BOUNDS
+static __device__ unsigned int g_bounds_err;
+__device__ __forceinline__ bool in_bounds(uint64_t i, uint64_t n, unsigned int site) {
+    if (i < n) return true;
+    atomicCAS(&g_bounds_err, 0u, site);
+    return false;
+}
+#define VSZ_IN(i, n, site) (::vsz::in_bounds((uint64_t)(i), (uint64_t)(n), (site)))
+void register_bounds_reader(unsigned int (*reader)());
+static unsigned int read_and_clear_bounds_word() {
+    unsigned int v = 0, z = 0;
+    if (cudaMemcpyFromSymbol(&v, g_bounds_err, sizeof v) != cudaSuccess) return 0xffffffffu;
+    cudaMemcpyToSymbol(g_bounds_err, &z, sizeof z);
+    return v;
+}
+struct BoundsReaderReg {
+    BoundsReaderReg() { register_bounds_reader(&read_and_clear_bounds_word); }
+};
+static BoundsReaderReg g_bounds_reader_reg;
+#else
+#define VSZ_IN(i, n, site) true
+#endif
+
 // ---- device arithmetic ------------------------------------------------------
 
 __host__ __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }

@@ -253,7 +253,7 @@ __device__ __forceinline__ void compact_chunk_body_slots(uint64_t chunk, const C
         const uint32_t cnt = has ? nx - eo : 0u;
         const uint32_t fin = to + eo + (uint32_t)__popc(fl & ((1u << l) - 1u));  // the block's final offset
         const bool fits = (uint64_t)to + rr.y <= a.out_cap;
-        if (has) {
+        if (has && VSZ_IN(blk, g.nb, 403)) {
             a.blk_off[blk] = fin;
             if (flag && fits) {
                 uint64_t idx, tile;
@@ -286,10 +286,10 @@ __device__ __forceinline__ void compact_chunk_body_slots(uint64_t chunk, const C
                     uint2 e[4];
 #pragma unroll
                     for (int q = 0; q < 4; ++q)
-                        if (i < c[q]) e[q] = a.slots[sb[q] + i];
+                        if (i < c[q] && VSZ_IN(sb[q] + i, g.nb * S, 401)) e[q] = a.slots[sb[q] + i];
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        if (i < c[q]) {
+                        if (i < c[q] && VSZ_IN((uint64_t)d0[q] + i, a.out_cap, 402)) {
                             a.out_idx[d0[q] + i] = e[q].x;
                             a.out_delta[d0[q] + i] = (int32_t)e[q].y;
                         }

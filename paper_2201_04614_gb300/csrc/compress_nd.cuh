@@ -103,7 +103,7 @@ struct NdCfg {
     static constexpr size_t STASH_B = (size_t)STASH * 8;
     static constexpr size_t TAB_B = 128 * 4;
     static constexpr size_t HIST_B = (size_t)U * 32 * 16;  // residuals of the current batch
-    static constexpr size_t CNT_B = 3 * 32 * 4;            // per lane: outliers, fixups, segment fill
+    static constexpr size_t CNT_B = 2 * 32 * 4;            // per lane: outliers, fixups
     static constexpr size_t WARP_C = RING_C + STASH_B + TAB_B + ZS_B + HIST_B + CNT_B;
     static constexpr size_t SMEM_C = WARP_C * WARPS;
     // per-warp shared memory, reconstruction: ring of codes | z state | outliers of the tile
@@ -152,7 +152,6 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
     uint32_t* const cnt = reinterpret_cast<uint32_t*>(wsm + C::RING_C + C::STASH_B + C::TAB_B + C::ZS_B + C::HIST_B) + lane;
     cnt[0] = 0;   // outliers of this lane's columns
     cnt[32] = 0;  // fixups of this lane's columns
-    cnt[64] = 0;  // outliers of this lane's block in its buffer segment (first walk)
     const float4* ring_rd = reinterpret_cast<const float4*>(wsm) + lane;  // slot (h*U + u)*32
     const uint32_t ring_wr = smem_addr(wsm) + lane * 16;
 
@@ -244,6 +243,7 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
     // per-block padding mode
     uint2* const slots = a.slots;
     uint2* const myslot = slots ? slots + (bexists ? blk : 0) * (uint64_t)C::SLOT : nullptr;
+    uint32_t seg_o = 0;             // outliers of this lane's block in its slot (first walk)
     bool ovf = false;               // the stash overflowed: count only, then walk again
     bool nofix = false;             // second walk of a tile without fixups: no guard checks
     auto rare_rows = [&](uint32_t rows, uint32_t rows_f, int h, uint64_t boff, int j, int lz, bool b0, bool imode,
@@ -281,7 +281,8 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
                     r0c01 = c01;
                     r0c23 = c23;
                 } else {
-                    store4c(a.codes + boff + (uint64_t)u * nx, valid, vst, c01, c23);
+                    if (valid == 0 || VSZ_IN(boff + (uint64_t)u * nx + valid - 1, g.n, 101))
+                        store4c(a.codes + boff + (uint64_t)u * nx, valid, vst, c01, c23);
                 }
             }
             if (((BP && !emit) || GP) && b0 && u == 0 && first) om &= ~1u;  // the origin waits for P
@@ -297,18 +298,17 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
                         const uint32_t y = __shfl_up_sync(VSZ_FULL, io, off);
                         if (glane >= off) io += y;
                     }
-                    const uint32_t seg_o = cnt[64];
                     uint32_t pos = seg_o + io - co;
                     const uint32_t idx0 = (uint32_t)(boff + (uint64_t)u * nx);
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
                         if (om & (1u << k)) {
-                            myslot[1 + pos] = make_uint2(idx0 + k, (uint32_t)d[k]);
+                            if (VSZ_IN((uint64_t)(myslot - slots) + 1 + pos, g.nb * C::SLOT, 102))
+                                myslot[1 + pos] = make_uint2(idx0 + k, (uint32_t)d[k]);
                             ++pos;
                         }
                     }
-                    const uint32_t seg_n = seg_o + __shfl_sync(VSZ_FULL, io, src + G - 1);
-                    cnt[64] = seg_n;
+                    seg_o += __shfl_sync(VSZ_FULL, io, src + G - 1);
                 }
                 // the stash overflowed: the tile is walked again for what the
                 // stash holds, and counts are all this walk still needs
@@ -475,7 +475,8 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
                         r0c01 = c01;
                         r0c23 = c23;
                     }
-                    *reinterpret_cast<uint2*>(crow + (uint32_t)u * nx32) = make_uint2(c01, c23);
+                    if (VSZ_IN(tile_base + off32(kb) + (uint64_t)u * nx + 3, g.n, 103))
+                        *reinterpret_cast<uint2*>(crow + (uint32_t)u * nx32) = make_uint2(c01, c23);
                 }
                 if ((BP || GP) && kb == 0) qcorner = __float2int_rn(__int_as_float(dh[0].x));
                 const uint32_t rows = __reduce_or_sync(VSZ_FULL, fmask);
@@ -612,7 +613,7 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
                     if (BP && b0 && u == 0) {
                         r0c01 = c01;
                         r0c23 = c23;
-                    } else {
+                    } else if (valid == 0 || VSZ_IN(boff + (uint64_t)u * nx + valid - 1, g.n, 109)) {
                         store4c(a.codes + boff + (uint64_t)u * nx, valid, vst, c01, c23);
                     }
                 }
@@ -668,7 +669,7 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
                         if (BP && b0 && u == 0) {
                             r0c01 = c01;
                             r0c23 = c23;
-                        } else {
+                        } else if (valid == 0 || VSZ_IN(boff + (uint64_t)u * nx + valid - 1, g.n, 110)) {
                             store4c(a.codes + boff + (uint64_t)u * nx, valid, vst, c01, c23);
                         }
                     }
@@ -705,7 +706,7 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
                : a.pad_mode == VSZ_PAD_BLOCK_MAX ? smax
                : rounded_mean(ssum, m);
             if (first && bexists) {
-                a.pad[blk] = Pb;
+                if (VSZ_IN(blk, g.nb, 104)) a.pad[blk] = Pb;
                 dcorner = wsub(qcorner, Pb);
                 const uint32_t cc = code_of(dcorner, R);
                 corner_out = (cc == 0u) ? 1u : 0u;
@@ -713,10 +714,10 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
                 r0c01 = (r0c01 & 0xffff0000u) | cc;
                 // block slots: slot 0 holds the origin outlier, or a marker
                 // index that no element has
-                if (slots) myslot[0] = corner_out ? make_uint2((uint32_t)tile_base, (uint32_t)dcorner)
+                if (slots && VSZ_IN(blk, g.nb, 105)) myslot[0] = corner_out ? make_uint2((uint32_t)tile_base, (uint32_t)dcorner)
                                                   : make_uint2(0xffffffffu, 0u);
             }
-            store4c(a.codes + tile_base, valid, vst, r0c01, r0c23);
+            if (valid == 0 || VSZ_IN(tile_base + valid - 1, g.n, 106)) store4c(a.codes + tile_base, valid, vst, r0c01, r0c23);
         }
 
         if (GP) {
@@ -731,7 +732,7 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
                 ssum += __shfl_xor_sync(VSZ_FULL, ssum, off);
             }
             if (lane == 0) global_stats_add(a, smin, smax, ssum);
-            if (first && bexists) a.origin[blk] = qcorner;
+            if (first && bexists && VSZ_IN(blk, g.nb, 107)) a.origin[blk] = qcorner;
         }
 
         // Per-block counts, in-tile exclusive offsets (blk_off), tile totals.
@@ -755,7 +756,7 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
         ef_g = __shfl_sync(VSZ_FULL, ef, src);
         const uint32_t tot_out = __shfl_sync(VSZ_FULL, io, 31);
         const uint32_t tot_fix = __shfl_sync(VSZ_FULL, iff, 31);
-        if (first && bexists) a.blk_off[blk] = eo;
+        if (first && bexists && VSZ_IN(blk, g.nb + 1, 108)) a.blk_off[blk] = eo;
 
         if (tot_out | tot_fix) {
             if (lane == 0) {

@@ -219,14 +219,16 @@ __device__ __forceinline__ void compress_1d_tile(const CompressArgs& a, uint64_t
                     stepmask |= 1u << st;  // walked again if the stash cannot serve the tile
                 }
                 uint16_t* cp = a.codes + base;
-                if (EPL == 4) {
+                if (!VSZ_IN(base + EPL - 1, n, 301)) {
+                    // (bounds-checking build only) a step past the field
+                } else if (EPL == 4) {
                     *reinterpret_cast<uint2*>(cp) = make_uint2(cb[0] | (cb[1] << 16), cb[2] | (cb[3 % EPL] << 16));
                 } else {
                     *reinterpret_cast<uint4*>(cp) =
                         make_uint4(cb[0] | (cb[1] << 16), cb[2] | (cb[3 % EPL] << 16), cb[4 % EPL] | (cb[5 % EPL] << 16),
                                    cb[6 % EPL] | (cb[7 % EPL] << 16));
                 }
-                if (origin) {
+                if (origin && VSZ_IN(base / B, a.g.nb, 302)) {
                     const uint64_t blk = base / B;
                     a.blk_off[blk] = run_out + ex;
                     if (BP) a.pad[blk] = Pb;

@@ -217,7 +217,7 @@ __device__ __forceinline__ void nd_recon_tile(const ReconArgs& a, const uint64_t
                 const bool in = v[q] && rr[q] < hi && rr[q] < a.out_cap;
                 oi[q] = ~0u;
                 od[q] = 0;
-                if (in) {
+                if (in && (!cached || VSZ_IN(rr[q] - lo_t, ocap, 203))) {
                     oi[q] = cached ? oc_idx[rr[q] - lo_t] : a.out_idx[rr[q]];
                     od[q] = cached ? oc_del[rr[q] - lo_t] : a.out_delta[rr[q]];
                 }
@@ -363,6 +363,7 @@ __device__ __forceinline__ void nd_recon_tile(const ReconArgs& a, const uint64_t
                     }
                     const uint32_t ro = boff + (uint32_t)u * nx32;
                     if (QOUT) {
+                        if (VSZ_IN(tile_base + ro + 3, g.n, 201))
                         st_out4(reinterpret_cast<int4*>(reinterpret_cast<int32_t*>(a.out) + tile_base + ro),
                                 make_int4(d[0], d[1], d[2], d[3]));
                     } else {
@@ -378,7 +379,8 @@ __device__ __forceinline__ void nd_recon_tile(const ReconArgs& a, const uint64_t
                             vv.z = __float_as_int(__fmul_rn(q2f(d[2]), ebx2));
                             vv.w = __float_as_int(__fmul_rn(q2f(d[3]), ebx2));
                         }
-                        st_out4(reinterpret_cast<int4*>(reinterpret_cast<float*>(a.out) + tile_base + ro), vv);
+                        if (VSZ_IN(tile_base + ro + 3, g.n, 202))
+                            st_out4(reinterpret_cast<int4*>(reinterpret_cast<float*>(a.out) + tile_base + ro), vv);
                     }
                 };
 #pragma unroll
@@ -519,7 +521,9 @@ __device__ __forceinline__ void nd_recon_tile(const ReconArgs& a, const uint64_t
                 d[2] = wadd(d[2], pv.z); d[3] = wadd(d[3], pv.w);
                 stz = make_int4(d[0], d[1], d[2], d[3]);
             }
-            if (QOUT) {
+            if (valid > 0 && !VSZ_IN(roff + valid - 1, g.n, 204)) {
+                // (bounds-checking build only) an output row past the field
+            } else if (QOUT) {
                 int32_t* o = reinterpret_cast<int32_t*>(a.out) + roff;
                 if (full) {
                     *reinterpret_cast<int4*>(o) = make_int4(d[0], d[1], d[2], d[3]);

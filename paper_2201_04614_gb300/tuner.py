@@ -188,14 +188,27 @@ def sampling_autotune(p: Params, x, sample_frac: float = 0.05, iters: int = 3, s
             "sample_elems": int(ne.value)}
 
 
+# Estimated sizes within SIZE_TOL of the least count as equal; among them the
+# padding that costs least to compute wins (zero, then per block, then
+# global: a field-wide statistic and a pass over the block origins).
+SIZE_TOL = 0.005
+PAD_RANK = (0, 2, 1)  # by padding slot: zero, global average, block average
+
+
 def label_of(costs) -> int:
-    """Cheapest class, ties to the lowest index."""
+    """The label from the classes' estimated sizes (the sweep's costs): among
+    the classes within SIZE_TOL of the least size, the cheapest padding, then
+    the smaller size, then the lower index."""
     c = np.asarray(costs, np.float64)
-    best = 0
-    for k in range(1, c.size):
-        if c[k] < c[best]:
-            best = k
-    return best
+    lo = float(np.min(c))
+    best = None
+    for k in range(c.size):
+        if not (c[k] <= lo * (1.0 + SIZE_TOL)):
+            continue
+        key = (PAD_RANK[k % 3], float(c[k]), k)
+        if best is None or key < best[0]:
+            best = (key, k)
+    return best[1]
 
 
 # ---------------------------------------------------------------- network

@@ -149,6 +149,21 @@ def test_costs_of_a_constant_field():
     assert T.label([3.0, 1.0, 1.0, 0.5, 0.5]) == 3
 
 
+def test_label_prefers_the_cheaper_padding_within_the_tolerance():
+    inf = float("inf")
+    # class 1 (global average) is least by 0.2 %: within 0.5 % of it, zero
+    # padding (class 0) wins, and block average (class 2) beats global
+    assert T.label([100.0, 99.8, 99.9] + [inf] * 9) == 0
+    assert T.label([inf, 99.8, 99.9] + [inf] * 9) == 2
+    # a gain beyond the tolerance is taken: 1 % less than zero padding
+    assert T.label([100.0, 99.0, 99.9] + [inf] * 9) == 1
+    # among equal paddings the smaller size, then the lower index
+    assert T.label([100.6, 100.0, 200.0, 100.2, 300.0, 300.0] + [inf] * 6) == 3
+    assert T.label([100.0, 300.0, 300.0, 100.0] + [inf] * 8) == 0
+    assert T.label([100.4, 100.0] + [inf] * 10) == 0  # 0.4 % above the least: equal
+    assert T.label([100.6, 100.0] + [inf] * 10) == 1  # 0.6 % above: not
+
+
 def _rand_problem(seed, B=9):
     rng = np.random.default_rng(seed)
     theta = rng.normal(0, 0.4, T.NPARAM)

@@ -37,9 +37,21 @@ CASES = [((300, 519), 16, "block_avg", 1e-5, 8), ((19, 37, 260), 8, "zero", 1e-4
          ((10007,), 32, "global_avg", 1e-5, 64)]
 
 
+def _dirty_the_workspace(dims, block, n):
+    """A no-alloc call on another field of the same dims with more outliers
+    and a global padding mode, so that the next call finds the shared
+    workspace full of another call's counters, staged entries and tables."""
+    x = np.ascontiguousarray(_field(dims, seed=block + 1000), np.float32).reshape(-1)
+    p = vsz.Params.make(dims, block, 1e-7, "rel", 2, "global_avg")
+    f = vsz.Field(p, out_cap=n, fix_cap=n // 4)
+    f.compress_noalloc(torch.from_numpy(x).cuda())
+    assert f.header()["n_out"] > n // 4
+
+
 def test_noalloc_matches_compress_on_two_calls_in_a_row():
     """Each field is compressed through vsz_compress (caller workspace) and
-    then, in a row, through vsz_compress_noalloc; every output must be
+    then, in a row, through vsz_compress_noalloc, after a no-alloc call on a
+    different field left the shared workspace dirty; every output must be
     identical, and so must the reconstructions."""
     for dims, block, pad, eb, radius in CASES:
         x = np.ascontiguousarray(_field(dims, seed=block), np.float32).reshape(-1)
@@ -51,6 +63,7 @@ def test_noalloc_matches_compress_on_two_calls_in_a_row():
         want = ref.to_host()
         want_x = ref.reconstruct().cpu().numpy()
         assert want["header"]["n_out"] > 0  # the staging part of the workspace is exercised
+        _dirty_the_workspace(dims, block, n)
         for call in range(2):
             f = vsz.Field(p, out_cap=n, fix_cap=n // 4)
             f.compress_noalloc(xd)
@@ -83,3 +96,23 @@ def test_noalloc_rejects_calls_beyond_its_workspace():
     x = _field(dims, seed=5).reshape(-1)
     f2.compress_noalloc(torch.from_numpy(np.ascontiguousarray(x, np.float32)).cuda())
     assert f2.header()["status"] == 0
+
+
+def test_noalloc_call_leaves_device_memory_unchanged():
+    """The call allocates nothing: around a warmed-up call the device's free
+    memory (cudaMemGetInfo) does not move."""
+    dims = (300, 519)
+    x = np.ascontiguousarray(_field(dims, seed=3), np.float32).reshape(-1)
+    n = x.size
+    p = vsz.Params.make(dims, 16, 1e-5, "rel", 8, "block_avg")
+    f = vsz.Field(p, out_cap=n, fix_cap=n // 4)
+    xd = torch.from_numpy(x).cuda()
+    f.compress_noalloc(xd)  # warm-up: the library's first call on the device
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        f.compress_noalloc(xd)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert f.header()["status"] == 0 and f.header()["n_out"] > 0
