@@ -1098,6 +1098,7 @@ def run_batch_profile(a):
             bt.reconstruct(stream)
         stream.synchronize()
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        torch.cuda.nvtx.range_push("vsz_steps")  # ncu --nvtx --nvtx-include "vsz_steps/" selects these launches
         e0.record(stream)
         for _ in range(a.steps):
             bt.submit(stream)
@@ -1105,6 +1106,7 @@ def run_batch_profile(a):
         for _ in range(a.steps):
             bt.reconstruct(stream)
         e2.record(stream)
+        torch.cuda.nvtx.range_pop()
         stream.synchronize()
     ms_c, ms_r = e0.elapsed_time(e1) / a.steps, e1.elapsed_time(e2) / a.steps
     heads = [f.header() for f in fields]

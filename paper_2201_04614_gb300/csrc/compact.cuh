@@ -77,6 +77,12 @@ __device__ __forceinline__ void compact_chunk_body(uint64_t chunk, const Compres
     const uint64_t ntiles = g.ntiles, nseg = g.nseg, nbx = g.nbx;
     const uint32_t bpt = g.bpt;
     const uint64_t t0 = chunk * kTilesPerChunk;
+    // a chunk with no entries at offset 0 is final as the walk left it
+    // (every block offset in-tile and zero): nothing to move or add
+    {
+        const uint4 ch = a.chunks[chunk];
+        if ((ch.x | ch.y | ch.z | ch.w) == 0u) return;
+    }
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     if (w == 0) {  // the chunk's tile offsets: chunk offset + exclusive scan of the tile totals
         uint32_t bo = a.chunks[chunk].z, bf = a.chunks[chunk].w;
@@ -212,6 +218,12 @@ __device__ __forceinline__ void compact_chunk_body_slots(uint64_t chunk, const C
     const uint64_t S = block_slot(g.nd, g.b);
     const bool bp = is_block_pad(a.pad_mode);
     const uint64_t t0 = chunk * kTilesPerChunk;
+    // a chunk with no entries at offset 0 is final as the walk left it
+    // (every block offset in-tile and zero): nothing to move or add
+    {
+        const uint4 ch = a.chunks[chunk];
+        if ((ch.x | ch.y | ch.z | ch.w) == 0u) return;
+    }
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     if (w == 0) {  // the chunk's tile offsets: chunk offset + exclusive scan of the tile totals
         uint32_t bo = a.chunks[chunk].z, bf = a.chunks[chunk].w;

@@ -23,9 +23,10 @@
 // pipe: the rounded values are integers below 2^20 and every difference an
 // integer below 2^24, so each fp32 operation is exact.  Otherwise the tile
 // continues in int32 (wrapping) arithmetic, its carried state converted.
-// The fp32 mode stores every code raw (the low half of fl(d + R + 2^23),
-// which is d + R when |d| < R) and rewrites the codes of flagged rows that
-// hold an outlier.
+// The fp32 mode's code is the low half of fl(d + R + 2^23), which is d + R
+// when |d| < R; the lean walk of interior tiles stores it with the
+// outliers' codes already zeroed (a select on |d| < R), the general walk
+// stores it raw and rewrites the codes of flagged rows that hold an outlier.
 // Every input byte is read once from HBM and every code written once.
 //
 // The pass over a batch is branch-free: each row's residuals go to a
@@ -74,6 +75,9 @@
 #ifndef VSZ_ND_STAGES
 #define VSZ_ND_STAGES 2
 #endif
+#ifndef VSZ_ND_STASH3_8
+#define VSZ_ND_STASH3_8 384
+#endif
 #ifndef VSZ_ND_STAGES_R
 #define VSZ_ND_STAGES_R 6
 #endif
@@ -93,7 +97,7 @@ struct NdCfg {
     // stash entries per warp: a 3D tile holds 8192 (b 8) or 32768 (b 16)
     // values, so those take what shared memory has left at the same
     // resident CTAs per SM (4 and 3); 2D tiles (at most 4096) keep the default
-    static constexpr int STASH = (ND == 3 && B == 8) ? 384 : (ND == 3 && B == 16) ? 512 : VSZ_ND_STASH;
+    static constexpr int STASH = (ND == 3 && B == 8) ? VSZ_ND_STASH3_8 : (ND == 3 && B == 16) ? 512 : VSZ_ND_STASH;
     static constexpr size_t ZS_B = ZSMEM ? (size_t)B * 32 * 16 : 0;
     // ring stages: the z state of 3D blocks of 32 leaves room for two
     static constexpr int NS = ZS_B > 8192 ? 2 : VSZ_ND_STAGES;
@@ -454,9 +458,11 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
                     bool fo = false, ff = false;
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
-                        cb[k] = __float_as_uint(__fadd_rn(d[k], RB));
+                        // an outlier's code is 0 from the first store on
+                        const bool in = fabsf(d[k]) < Rf;
+                        cb[k] = in ? __float_as_uint(__fadd_rn(d[k], RB)) : 0u;
                         const float xh = __fmul_rn(rp[k], ebx2);
-                        fo |= !(fabsf(d[k]) < Rf);
+                        fo |= !in;
                         ff |= !(fabsf(__fsub_rn(xv[k], xh)) <= ebf);
                     }
                     if (BP || GP) {
@@ -480,9 +486,9 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
                 }
                 if ((BP || GP) && kb == 0) qcorner = __float2int_rn(__int_as_float(dh[0].x));
                 const uint32_t rows = __reduce_or_sync(VSZ_FULL, fmask);
-                if (rows)
+                if (rows)  // codes already final: no rewrite
                     rare_rows((rows | (rows >> 8)) & 0xffu, rows >> 8, h, tile_base + off32(kb), jb, kb / BPP, kb == 0,
-                              false, true, false);
+                              false, false, false);
                 h = h + 1 == C::NS ? 0 : h + 1;
                 if (BP || GP) {
                     ssum += lsum;

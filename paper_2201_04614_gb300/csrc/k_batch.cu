@@ -249,6 +249,13 @@ struct BatchClass {
     ReconArgs* d_rargs = nullptr;
     uint64_t* d_prefix = nullptr;
     uint64_t total_tiles = 0;
+    // a global or edge padding class: its fields' descriptors and the
+    // prefixes of their blocks and face-statistics units (the origin pass
+    // and edge statistics run on the class's own branch, after its kernel)
+    BatchField* d_bfields = nullptr;
+    uint64_t* d_ob_prefix = nullptr;
+    uint64_t* d_edge_prefix = nullptr;
+    uint64_t origin_items = 0, edge_items = 0;
     LaunchShape shape;             // launch shape of the class kernel (autotuned or set)
     float ms_best = 0.0f, ms_default = 0.0f;  // autotuner measurements
 };
@@ -260,11 +267,8 @@ struct vsz_batch_st {
     std::vector<BatchClass> classes;
     BatchField* d_fields = nullptr;
     uint64_t* d_range_prefix = nullptr;
-    uint64_t* d_ob_prefix = nullptr;    // blocks of the global- and edge-padding fields
-    uint64_t* d_edge_prefix = nullptr;  // face-statistics units of the edge-padding fields
-    uint64_t edge_items = 0;
     uint64_t* d_chunk_prefix = nullptr;
-    uint64_t range_items = 0, origin_items = 0, chunks = 0;
+    uint64_t range_items = 0, chunks = 0;
     unsigned long long* tickets = nullptr;  // in the caller's workspace
     bool use_graph = false;
     cudaGraphExec_t exec = nullptr;
@@ -321,11 +325,12 @@ static void free_batch(vsz_batch_st* b) {
     for (BatchClass& c : b->classes) {
         if (c.d_args) cudaFree(c.d_args);
         if (c.d_prefix) cudaFree(c.d_prefix);
+        if (c.d_bfields) cudaFree(c.d_bfields);
+        if (c.d_ob_prefix) cudaFree(c.d_ob_prefix);
+        if (c.d_edge_prefix) cudaFree(c.d_edge_prefix);
     }
     if (b->d_fields) cudaFree(b->d_fields);
     if (b->d_range_prefix) cudaFree(b->d_range_prefix);
-    if (b->d_ob_prefix) cudaFree(b->d_ob_prefix);
-    if (b->d_edge_prefix) cudaFree(b->d_edge_prefix);
     if (b->d_chunk_prefix) cudaFree(b->d_chunk_prefix);
     delete b;
 }
@@ -373,6 +378,28 @@ static cudaError_t launch_rclass(vsz_batch_st* b, size_t c, cudaStream_t s) {
                                              k.shape, s);
 }
 
+// The deferred block origins of a global or edge padding class, once its
+// kernel is done: face statistics of its edge-padding fields, then the
+// origin pass over its fields' blocks (on the class's stream).
+static cudaError_t launch_class_origins(vsz_batch_st* b, size_t c, cudaStream_t s) {
+    const BatchClass& k = b->classes[c];
+    const int nf = (int)k.fields.size();
+    if (k.edge_items) {
+        TraceScope ts("batch_edge_stats", s, k.nd, k.b);
+        const int grid = grid_for((const void*)k_batch_edge_stats, 256, 0, 8, k.edge_items);
+        k_batch_edge_stats<<<grid, 256, 0, s>>>(k.d_bfields, nf, k.d_edge_prefix, k.edge_items);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (k.origin_items) {
+        TraceScope ts("batch_origin_fix", s, k.nd, k.b);
+        const int grid = grid_for((const void*)k_batch_origin_fix, 256, 0, 256, k.origin_items);
+        k_batch_origin_fix<<<grid, 256, 0, s>>>(k.d_bfields, nf, k.d_ob_prefix, k.origin_items);
+        return cudaGetLastError();
+    }
+    return cudaSuccess;
+}
+
 static cudaError_t launch_class(vsz_batch_st* b, size_t c, cudaStream_t s) {
     BatchClass& k = b->classes[c];
     TraceScope ts(k.pk == 1 ? "batch_lorenzo_bp" : k.pk == 2 ? "batch_lorenzo_gp" : "batch_lorenzo", s, k.nd, k.b);
@@ -397,6 +424,7 @@ static vsz_status run_classes(vsz_batch_st* b, int kind, cudaStream_t s, const C
     std::vector<BatchClass>& cls = kind ? b->rclasses : b->classes;
     const bool conc = kind ? b->rconcurrent : b->concurrent;
     auto launch = [&](size_t c, cudaStream_t t) { return kind ? launch_rclass(b, c, t) : launch_class(b, c, t); };
+    auto post = [&](size_t c, cudaStream_t t) { return kind ? cudaSuccess : launch_class_origins(b, c, t); };
     cudaError_t e;
     std::vector<size_t> run;
     for (size_t c = 0; c < cls.size(); ++c)
@@ -407,8 +435,10 @@ static vsz_status run_classes(vsz_batch_st* b, int kind, cudaStream_t s, const C
         if ((e = cudaEventRecord(b->ev[0], s)) != cudaSuccess) return cuda_fail(e);
         for (size_t i = 1; i < run.size(); ++i)
             if ((e = cudaStreamWaitEvent(b->side[i - 1], b->ev[0], 0)) != cudaSuccess) return cuda_fail(e);
-        for (size_t i = 0; i < run.size(); ++i)
+        for (size_t i = 0; i < run.size(); ++i) {
             if ((e = launch(run[i], i == 0 ? s : b->side[i - 1])) != cudaSuccess) return cuda_fail(e);
+            if ((e = post(run[i], i == 0 ? s : b->side[i - 1])) != cudaSuccess) return cuda_fail(e);
+        }
         for (size_t i = 1; i < run.size(); ++i) {
             if ((e = cudaEventRecord(b->ev[i], b->side[i - 1])) != cudaSuccess) return cuda_fail(e);
             if ((e = cudaStreamWaitEvent(s, b->ev[i], 0)) != cudaSuccess) return cuda_fail(e);
@@ -420,6 +450,7 @@ static vsz_status run_classes(vsz_batch_st* b, int kind, cudaStream_t s, const C
         if (timed && (e = cudaEventRecord(tm->e0, s)) != cudaSuccess) return cuda_fail(e);
         if ((e = launch(c, s)) != cudaSuccess) return cuda_fail(e);
         if (timed && (e = cudaEventRecord(tm->e1, s)) != cudaSuccess) return cuda_fail(e);
+        if ((e = post(c, s)) != cudaSuccess) return cuda_fail(e);
     }
     return VSZ_OK;
 }
@@ -454,21 +485,10 @@ static vsz_status launch_sequence(vsz_batch_st* b, cudaStream_t s, const ClassTi
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
     }
     {
-        // forked after the range pass, joined before the origin pass
+        // forked after the range pass, joined before the compaction (each
+        // global or edge padding class runs its origin pass on its branch)
         const vsz_status st = run_classes(b, 0, s, tm);
         if (st != VSZ_OK) return st;
-    }
-    if (b->edge_items) {
-        TraceScope ts("batch_edge_stats", s);
-        const int grid = grid_for((const void*)k_batch_edge_stats, 256, 0, 8, b->edge_items);
-        k_batch_edge_stats<<<grid, 256, 0, s>>>(b->d_fields, b->n, b->d_edge_prefix, b->edge_items);
-        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
-    }
-    if (b->origin_items) {
-        TraceScope ts("batch_origin_fix", s);
-        const int grid = grid_for((const void*)k_batch_origin_fix, 256, 0, 256, b->origin_items);
-        k_batch_origin_fix<<<grid, 256, 0, s>>>(b->d_fields, b->n, b->d_ob_prefix, b->origin_items);
-        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
     }
     {
         TraceScope ts("batch_compact_scan", s);
@@ -513,7 +533,7 @@ vsz_status vsz_batch_create(const vsz_field_job* jobs, int njobs, void* d_ws, si
     b->use_graph = use_graph != 0;
     char* ws = (char*)d_ws;
     b->tickets = (unsigned long long*)ws;
-    std::vector<uint64_t> rp(1, 0), qp(1, 0), cp(1, 0), ep(1, 0);
+    std::vector<uint64_t> rp(1, 0), cp(1, 0);
     std::map<ClassKey, int> cls;
     for (int i = 0; i < njobs; ++i) {
         const vsz_field_job& j = jobs[i];
@@ -555,8 +575,6 @@ vsz_status vsz_batch_create(const vsz_field_job* jobs, int njobs, void* d_ws, si
         b->fields.push_back(bf);
         const uint64_t items = (g.n + kItemElems - 1) / kItemElems;
         rp.push_back(rp.back() + (bf.rel ? (items ? items : 1) : 0));
-        qp.push_back(qp.back() + (bf.gpad || bf.epad ? g.nb : 0));
-        ep.push_back(ep.back() + (bf.epad ? edge_units(g) : 0));
         cp.push_back(cp.back() + g.nchunks);
         const ClassKey key = class_key(j, g);
         const int pk = std::get<2>(key);
@@ -573,25 +591,31 @@ vsz_status vsz_batch_create(const vsz_field_job* jobs, int njobs, void* d_ws, si
     }
     if ((int)b->classes.size() > kMaxClasses) { free_batch(b); return VSZ_ERR_UNSUPPORTED; }
     b->range_items = rp.back();
-    b->origin_items = qp.back();
-    b->edge_items = ep.back();
     b->chunks = cp.back();
     cudaError_t e = upload(&b->d_fields, b->fields);
     if (e == cudaSuccess) e = upload(&b->d_range_prefix, rp);
-    if (e == cudaSuccess) e = upload(&b->d_ob_prefix, qp);
-    if (e == cudaSuccess) e = upload(&b->d_edge_prefix, ep);
     if (e == cudaSuccess) e = upload(&b->d_chunk_prefix, cp);
     for (BatchClass& c : b->classes) {
         if (e != cudaSuccess) break;
         std::vector<CompressArgs> args;
-        std::vector<uint64_t> pre(1, 0);
+        std::vector<BatchField> bfs;
+        std::vector<uint64_t> pre(1, 0), qp(1, 0), ep(1, 0);
         for (int i : c.fields) {
-            args.push_back(b->fields[i].a);
-            pre.push_back(pre.back() + b->fields[i].a.g.ntiles);
+            const BatchField& bf = b->fields[i];
+            args.push_back(bf.a);
+            bfs.push_back(bf);
+            pre.push_back(pre.back() + bf.a.g.ntiles);
+            qp.push_back(qp.back() + (bf.gpad || bf.epad ? bf.a.g.nb : 0));
+            ep.push_back(ep.back() + (bf.epad ? edge_units(bf.a.g) : 0));
         }
         c.total_tiles = pre.back();
+        c.origin_items = qp.back();
+        c.edge_items = ep.back();
         e = upload(&c.d_args, args);
         if (e == cudaSuccess) e = upload(&c.d_prefix, pre);
+        if (e == cudaSuccess && c.origin_items) e = upload(&c.d_bfields, bfs);
+        if (e == cudaSuccess && c.origin_items) e = upload(&c.d_ob_prefix, qp);
+        if (e == cudaSuccess && c.edge_items) e = upload(&c.d_edge_prefix, ep);
     }
     if (e != cudaSuccess) {
         free_batch(b);

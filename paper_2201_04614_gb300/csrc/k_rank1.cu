@@ -95,7 +95,8 @@ constexpr int kStash1F = 128;  // fixups (rounding at the quantization boundarie
 // All the work of one 4096-element tile t of a 1D field.
 template <int B, bool BP, bool GP>
 __device__ __forceinline__ void compress_1d_tile(const CompressArgs& a, uint64_t t, int lane,
-                                                 uint2* __restrict__ stash, uint2* __restrict__ fstash) {
+                                                 uint2* __restrict__ stash, uint2* __restrict__ fstash,
+                                                 int2* __restrict__ mm) {
     using C = Cfg1<B>;
     constexpr int EPL = C::EPL, G = C::G, SPAN = C::SPAN;
     const float inv2eb = a.hdr->inv2eb;
@@ -110,8 +111,7 @@ __device__ __forceinline__ void compress_1d_tile(const CompressArgs& a, uint64_t
     uint32_t nst = 0;   // outliers met by fp32 steps (stashed while they fit)
     uint32_t nfst = 0;  // fixups met by fp32 steps (stashed while they fit)
     bool slow = false;  // a step took the integer path
-    int32_t gmin = INT_MAX, gmax = INT_MIN;  // q statistics of the tile (global padding)
-    long long gsum = 0;
+    int32_t gsum = 0;  // a lane's sum of q over the tile's fp32 steps: at most 128 values of |q| < 2^20
     // The value-range pass proved every |x * inv2eb| < 2^20 and no NaN/Inf:
     // full steps then run in exact fp32 -- rounding by the 1.5 * 2^23 bias,
     // differences of integers below 2^21, the code as the low half of
@@ -122,6 +122,7 @@ __device__ __forceinline__ void compress_1d_tile(const CompressArgs& a, uint64_t
     const bool fast = a.wsh->fp32_ok != 0u && a.vec != 0 && (BP || GP || (Pg >= -(1 << 20) && Pg <= (1 << 20)));
     const float Rf = (float)R, RB = (float)(R + 8388608), Pgf = (float)Pg;
     const bool need_mm = GP && a.pad_mode != VSZ_PAD_GLOBAL_AVG;
+    if (need_mm) mm[lane] = make_int2(INT_MAX, INT_MIN);  // q extremes of the tile (global min or max)
 #pragma unroll 2
     for (int st = 0; st < C::STEPS; ++st) {
         const uint64_t s0 = start + (uint64_t)st * SPAN;
@@ -144,7 +145,7 @@ __device__ __forceinline__ void compress_1d_tile(const CompressArgs& a, uint64_t
                     ls = __fadd_rn(ls, rp[k]);  // |sum| < 2^23: exact
                 }
                 int32_t smin = __float2int_rn(mn), smax = __float2int_rn(mx);
-                long long ssum = __float2int_rn(ls);
+                int32_t ssum = __float2int_rn(ls);  // at most 256 values of |q| < 2^20
 #pragma unroll
                 for (int off = 1; off < G; off <<= 1) {
                     smin = min(smin, __shfl_xor_sync(VSZ_FULL, smin, off));
@@ -152,7 +153,7 @@ __device__ __forceinline__ void compress_1d_tile(const CompressArgs& a, uint64_t
                     ssum += __shfl_xor_sync(VSZ_FULL, ssum, off);
                 }
                 Pb = a.pad_mode == VSZ_PAD_BLOCK_MIN ? smin : a.pad_mode == VSZ_PAD_BLOCK_MAX ? smax
-                                                                : rounded_mean(ssum, (long long)B);
+                                                                : rounded_mean((long long)ssum, (long long)B);
                 Pf = (float)Pb;  // |Pb| < 2^20: exact
             }
             const float left = __shfl_up_sync(VSZ_FULL, rp[EPL - 1], 1);
@@ -240,15 +241,15 @@ __device__ __forceinline__ void compress_1d_tile(const CompressArgs& a, uint64_t
 #pragma unroll
                     for (int k = 1; k < EPL; ++k) ls = __fadd_rn(ls, rp[k]);
                     gsum += __float2int_rn(ls);
-                    if (need_mm) {  // a min or max mode
+                    if (need_mm) {  // a min or max mode: the lane's extremes in shared memory
                         float mn = rp[0], mx = rp[0];
 #pragma unroll
                         for (int k = 1; k < EPL; ++k) {
                             mn = fminf(mn, rp[k]);
                             mx = fmaxf(mx, rp[k]);
                         }
-                        gmin = min(gmin, __float2int_rn(mn));
-                        gmax = max(gmax, __float2int_rn(mx));
+                        const int2 e = mm[lane];
+                        mm[lane] = make_int2(min(e.x, __float2int_rn(mn)), max(e.y, __float2int_rn(mx)));
                     }
                 }
                 continue;
@@ -265,12 +266,19 @@ __device__ __forceinline__ void compress_1d_tile(const CompressArgs& a, uint64_t
             if (k < S.valid) {
                 co += (c[k] == 0u && !(GP && k == 0 && glane == 0));
                 cf += needs_fixup(S.x[k], S.q[k], ebx2, ebf) ? 1u : 0u;
-                if (GP) {
-                    gmin = min(gmin, S.q[k]);
-                    gmax = max(gmax, S.q[k]);
-                    gsum += S.q[k];
+                if (GP && need_mm) {
+                    const int2 e = mm[lane];
+                    mm[lane] = make_int2(min(e.x, S.q[k]), max(e.y, S.q[k]));
                 }
             }
+        }
+        if (GP) {  // an integer step's q are unbounded: its sum goes to the field at once
+            long long ss = 0;
+#pragma unroll
+            for (int k = 0; k < EPL; ++k) ss += k < S.valid ? (long long)S.q[k] : 0ll;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) ss += __shfl_xor_sync(VSZ_FULL, ss, off);
+            if (lane == 0) global_stats_add(a, INT_MAX, INT_MIN, ss);
         }
         // in-step exclusive prefix of outliers -> per-block offsets
         uint32_t io = co, iff = cf;
@@ -309,13 +317,22 @@ __device__ __forceinline__ void compress_1d_tile(const CompressArgs& a, uint64_t
     }
 
     if (GP) {
+        long long gs = gsum;
+        int32_t gmin = INT_MAX, gmax = INT_MIN;
+        if (need_mm) {
+            const int2 e = mm[lane];
+            gmin = e.x;
+            gmax = e.y;
+        }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
-            gmin = min(gmin, __shfl_xor_sync(VSZ_FULL, gmin, off));
-            gmax = max(gmax, __shfl_xor_sync(VSZ_FULL, gmax, off));
-            gsum += __shfl_xor_sync(VSZ_FULL, gsum, off);
+            if (need_mm) {
+                gmin = min(gmin, __shfl_xor_sync(VSZ_FULL, gmin, off));
+                gmax = max(gmax, __shfl_xor_sync(VSZ_FULL, gmax, off));
+            }
+            gs += __shfl_xor_sync(VSZ_FULL, gs, off);
         }
-        if (lane == 0) global_stats_add(a, gmin, gmax, gsum);
+        if (lane == 0) global_stats_add(a, gmin, gmax, gs);
     }
     unsigned long long base_out = 0, base_fix = 0;
     if (run_out | run_fix) {
@@ -384,28 +401,31 @@ __device__ __forceinline__ void compress_1d_tile(const CompressArgs& a, uint64_t
 
 // One field: tiles handed out by the field's own ticket.
 template <int B, bool BP, bool GP>
-__global__ void __launch_bounds__(256) k_lorenzo_1d(const CompressArgs a) {
+__global__ void __launch_bounds__(256, 4) k_lorenzo_1d(const CompressArgs a) {
     pdl_prologue();
     __shared__ uint2 stash[8][kStash1];
     __shared__ uint2 fstash[8][kStash1F];
+    __shared__ int2 mm[8][32];
     const int lane = threadIdx.x & 31;
     for (;;) {
         unsigned long long tk = 0;
         if (lane == 0) tk = atomicAdd(&a.wsh->ticket, 1ull);
         const uint64_t t = __shfl_sync(VSZ_FULL, tk, 0);
         if (t >= a.g.ntiles) break;
-        compress_1d_tile<B, BP, GP>(a, t, lane, stash[threadIdx.x >> 5], fstash[threadIdx.x >> 5]);
+        compress_1d_tile<B, BP, GP>(a, t, lane, stash[threadIdx.x >> 5], fstash[threadIdx.x >> 5],
+                                    mm[threadIdx.x >> 5]);
     }
 }
 
 // Many 1D fields with the same block length and padding kind: one queue
 // over all their tiles (tile_prefix as for the 2D/3D batch kernel).
 template <int B, bool BP, bool GP>
-__global__ void __launch_bounds__(256) k_lorenzo_1d_batch(const CompressArgs* __restrict__ fields,
+__global__ void __launch_bounds__(256, 4) k_lorenzo_1d_batch(const CompressArgs* __restrict__ fields,
                                                           const uint64_t* __restrict__ tile_prefix, int nfields,
                                                           unsigned long long* ticket) {
     __shared__ uint2 stash[8][kStash1];
     __shared__ uint2 fstash[8][kStash1F];
+    __shared__ int2 mm[8][32];
     const int lane = threadIdx.x & 31;
     const uint64_t total = tile_prefix[nfields];
     for (;;) {
@@ -419,7 +439,7 @@ __global__ void __launch_bounds__(256) k_lorenzo_1d_batch(const CompressArgs* __
             if (tile_prefix[mid] <= gt) lo = mid; else hi = mid - 1;
         }
         compress_1d_tile<B, BP, GP>(fields[lo], gt - tile_prefix[lo], lane, stash[threadIdx.x >> 5],
-                                    fstash[threadIdx.x >> 5]);
+                                    fstash[threadIdx.x >> 5], mm[threadIdx.x >> 5]);
     }
 }
 

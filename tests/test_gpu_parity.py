@@ -354,3 +354,38 @@ def test_trace_and_shutdown():
     f.reconstruct()
     assert len(vsz.trace_read()) > 0
     vsz.trace_enable(False)
+
+
+@pytest.mark.parametrize("dims,block", [((16, 24, 256), 8), ((12, 16, 384), 4), ((64, 256), 16), ((40, 512), 8)])
+def test_dense_outliers_aligned_unaligned_and_corrupt_lists(dims, block):
+    """Interior tiles whose every batch holds outliers (radius 8 at a relative
+    eb of 1e-6), their outliers fetched from the global lists: as allocated
+    (16-byte words), at a 4-byte offset (single loads), and with one index
+    changed in the middle of the list (reported as corrupt)."""
+    import ctypes
+    x = field_for(dims, seed=21)
+    f, c, g, o, xx = run_both(x, dims, block, 1e-6, radius=8)
+    n_out = len(c.out_idx)
+    assert n_out > 0.5 * xx.size
+    assert_parity(f, c, g, o, xx, "zero")
+    xo = o[1].view(np.uint32)
+    bi = torch.zeros(f.out_cap + 1, dtype=torch.int32, device="cuda")
+    bd = torch.zeros(f.out_cap + 1, dtype=torch.int32, device="cuda")
+    bi[1:1 + n_out] = f.out_idx[:n_out]
+    bd[1:1 + n_out] = f.out_delta[:n_out]
+    cc = vsz._CCompressed(f.codes.data_ptr(), f.pad.data_ptr() if f.pad is not None else 0, f.blk_off.data_ptr(),
+                          bi[1:].data_ptr(), bd[1:].data_ptr(), f.out_cap, f.fix_idx.data_ptr(),
+                          f.fix_bits.data_ptr(), f.fix_cap, f.hdr.data_ptr())
+    out = torch.empty(xx.size, dtype=torch.float32, device="cuda")
+
+    def recon():
+        vsz._check(vsz.lib().vsz_reconstruct(ctypes.byref(f._cp), ctypes.byref(cc), vsz._ptr(out), vsz._ptr(f.rws),
+                                             vsz.RECON_WS_BYTES, None), "vsz_reconstruct")
+        torch.cuda.synchronize()
+        return out.cpu().numpy().view(np.uint32)
+
+    assert np.array_equal(recon(), xo)
+    assert f.header()["recon_status"] == 0
+    bi[1 + n_out // 2] += 1
+    recon()
+    assert f.header()["recon_status"] == 5
