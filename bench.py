@@ -1002,7 +1002,21 @@ def run_gpu(a):
                        "offsets, padding table and exact-length outlier and fixup lists back to page-locked "
                        "host memory",
                "status_nonzero": sum(1 for h in hh if h["status"])}
-        del hx, hout
+        # the host link on its own (context for e2e): one 1 GiB copy each way
+        # between page-locked memory and the device, on the same stream
+        hb = torch.empty(1 << 28, dtype=torch.float32).pin_memory()
+        db = torch.empty(1 << 28, dtype=torch.float32, device="cuda")
+        link = {}
+        for name, (dst, src) in (("h2d_GBps", (db, hb)), ("d2h_GBps", (hb, db))):
+            with torch.cuda.stream(stream):
+                dst.copy_(src, non_blocking=True)
+                e0.record(stream)
+                dst.copy_(src, non_blocking=True)
+                e1.record(stream)
+            e1.synchronize()
+            link[name] = (1 << 30) / (e0.elapsed_time(e1) * 1e-3) / 1e9
+        e2e["host_link"] = link
+        del hb, db, hx, hout
     bt.close()
     del bt, tuned, outs
     torch.cuda.empty_cache()

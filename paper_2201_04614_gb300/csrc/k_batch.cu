@@ -58,11 +58,18 @@ __device__ __forceinline__ int find_field(const uint64_t* __restrict__ prefix, i
     return lo;
 }
 
+// blockIdx.x: the field; blockIdx.y strides over its chunk sums and (a
+// chained field) its tile-chain status words; CTA (f, 0) sets the headers.
 __global__ void __launch_bounds__(256) k_batch_begin(const BatchField* __restrict__ F,
                                                      unsigned long long* tickets) {
     const BatchField& b = F[blockIdx.x];
     const CompressArgs& a = b.a;
-    for (uint64_t i = threadIdx.x; i < a.g.nchunks; i += blockDim.x) a.chunks[i] = make_uint4(0, 0, 0, 0);
+    const uint64_t i0 = (uint64_t)blockIdx.y * blockDim.x + threadIdx.x, stride = (uint64_t)gridDim.y * blockDim.x;
+    if (!a.chained)
+        for (uint64_t i = i0; i < a.g.nchunks; i += stride) a.chunks[i] = make_uint4(0, 0, 0, 0);
+    else
+        for (uint64_t i = i0; i < a.g.ntiles; i += stride) a.tiles[i] = make_uint4(0, 0, 0, 0);
+    if (blockIdx.y != 0) return;
     if (threadIdx.x == 0) {
         WsHeader* w = a.wsh;
         w->stage_out = 0;
@@ -195,6 +202,7 @@ __global__ void __launch_bounds__(256) k_batch_origin_fix(const BatchField* __re
 
 __global__ void __launch_bounds__(1024) k_batch_compact_scan(const BatchField* __restrict__ F) {
     const CompressArgs& a = F[blockIdx.x].a;
+    if (a.chained && a.g.ntiles > 0) return;  // placed and closed by the tile chain
     compact_scan_body(a.chunks, a.g.nchunks, const_cast<vsz_header*>(a.hdr), a.blk_off, a.g.nb, a.out_cap,
                       a.fix_cap);
 }
@@ -269,6 +277,8 @@ struct vsz_batch_st {
     uint64_t* d_range_prefix = nullptr;
     uint64_t* d_chunk_prefix = nullptr;
     uint64_t range_items = 0, chunks = 0;
+    unsigned begin_y = 1;                // CTAs per field of the begin kernel
+    bool scan = false;                   // some field is staged (or empty): the compaction scan runs
     unsigned long long* tickets = nullptr;  // in the caller's workspace
     bool use_graph = false;
     cudaGraphExec_t exec = nullptr;
@@ -474,7 +484,7 @@ static vsz_status launch_sequence(vsz_batch_st* b, cudaStream_t s, const ClassTi
     cudaError_t e;
     {
         TraceScope ts("batch_begin", s);
-        k_batch_begin<<<b->n, 256, 0, s>>>(b->d_fields, b->tickets);
+        k_batch_begin<<<dim3((unsigned)b->n, b->begin_y), 256, 0, s>>>(b->d_fields, b->tickets);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return cuda_fail(e);
@@ -490,7 +500,7 @@ static vsz_status launch_sequence(vsz_batch_st* b, cudaStream_t s, const ClassTi
         const vsz_status st = run_classes(b, 0, s, tm);
         if (st != VSZ_OK) return st;
     }
-    {
+    if (b->scan) {
         TraceScope ts("batch_compact_scan", s);
         k_batch_compact_scan<<<b->n, 1024, 0, s>>>(b->d_fields);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
@@ -572,10 +582,14 @@ vsz_status vsz_batch_create(const vsz_field_job* jobs, int njobs, void* d_ws, si
         bf.gpad = is_global_pad(j.params.pad) ? 1 : 0;
         bf.epad = is_edge_pad(j.params.pad) ? 1 : 0;
         if (g.nd >= 2) a.slots = a.stage_out;  // block-slot staging
+        a.chained = chained_field(j.params.pad) ? 1 : 0;
         b->fields.push_back(bf);
         const uint64_t items = (g.n + kItemElems - 1) / kItemElems;
         rp.push_back(rp.back() + (bf.rel ? (items ? items : 1) : 0));
-        cp.push_back(cp.back() + g.nchunks);
+        cp.push_back(cp.back() + (a.chained ? 0 : g.nchunks));  // chained fields need no compaction
+        const uint64_t zw = a.chained ? g.ntiles : g.nchunks;          // begin's zeroing
+        if (!a.chained || g.ntiles == 0) b->scan = true;
+        b->begin_y = (unsigned)umax64(b->begin_y, umin64(16, (zw + 4095) / 4096));
         const ClassKey key = class_key(j, g);
         const int pk = std::get<2>(key);
         auto it = cls.find(key);

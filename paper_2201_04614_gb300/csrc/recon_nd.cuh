@@ -161,64 +161,40 @@ __device__ __forceinline__ void nd_recon_tile(const ReconArgs& a, const uint64_t
             return rb + ((excl >> (8 * u)) & 0xffu) + (uint32_t)__popc((zm >> (4 * u)) & ((1u << k) - 1u));
         };
         if (!cached) {
-            // Outliers from the global lists.  A lane's outliers in one row
-            // of the batch are consecutive in the list (ranks r0 .. r0+c-1,
-            // c <= 4), so each row takes one or two aligned 16-byte words of
-            // each list that cover them; the q-th set bit of the row's mask
-            // takes entry q.  Lists not 16-byte aligned, or a run that ends
-            // past the block or the capacity, take single loads instead.
-            const bool al = ((reinterpret_cast<uintptr_t>(a.out_idx) | reinterpret_cast<uintptr_t>(a.out_delta)) &
-                             15u) == 0u;
-            const uint64_t lim = umin64(hi, a.out_cap);
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const uint32_t nib = (zm >> (4 * u)) & 0xfu;
-                if (!nib) continue;
-                const uint32_t c = (uint32_t)__popc(nib);
-                const uint32_t r0 = rowpre[u] + ((excl >> (8 * u)) & 0xffu);
-                const uint32_t a0 = r0 & ~3u, off = r0 & 3u;
-                const bool two = off + c > 4u;
-                int32_t dv[4];
-                uint32_t iv[4];
-                if (al && (uint64_t)r0 + c <= lim && (uint64_t)a0 + (two ? 8u : 4u) <= a.out_cap &&
-                    VSZ_IN((uint64_t)a0 + (two ? 7u : 3u), a.out_cap, 205)) {
-                    const uint4 i0 = ld_stream_u4(a.out_idx + a0), d0 = ld_stream_u4(a.out_delta + a0);
-                    uint4 i1 = i0, d1 = d0;
-                    if (two) {
-                        i1 = ld_stream_u4(a.out_idx + a0 + 4);
-                        d1 = ld_stream_u4(a.out_delta + a0 + 4);
-                    }
-                    const uint32_t wi[8] = {i0.x, i0.y, i0.z, i0.w, i1.x, i1.y, i1.z, i1.w};
-                    const uint32_t wd[8] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {  // entry off + q, by selects (no local memory)
-                        iv[q] = off == 0u ? wi[q] : off == 1u ? wi[q + 1] : off == 2u ? wi[q + 2] : wi[q + 3];
-                        dv[q] = (int32_t)(off == 0u ? wd[q] : off == 1u ? wd[q + 1] : off == 2u ? wd[q + 2] : wd[q + 3]);
-                    }
+            // Outliers from the global lists: every one of the batch copied
+            // into shared memory at once (index beside residual, in the cache
+            // area this tile leaves unused), then one wait: a batch costs one
+            // memory latency however many outliers it holds.  The wait also
+            // completes the ring's prefetched batches, which stay valid.
+            int32_t* const pi = reinterpret_cast<int32_t*>(reinterpret_cast<int4*>(oc_idx) + lane);
+            int32_t* const pd = reinterpret_cast<int32_t*>(ps);
+            const uint32_t spi = smem_addr(pi), spd = smem_addr(pd);
+            uint32_t m = zm;
+#pragma unroll 1
+            while (m) {
+                const uint32_t jq = (uint32_t)(__ffs(m) - 1);
+                m &= m - 1u;
+                const uint32_t r = rank_of(jq);
+                const uint32_t off = (jq >> 2) * 32 * 16 + (jq & 3u) * 4;  // row u of the lane's column, entry k
+                if (r < hi && r < a.out_cap) {
+                    cp_async4(spi + off, a.out_idx + r, 4u);
+                    cp_async4(spd + off, a.out_delta + r, 4u);
                 } else {
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const bool in = (uint32_t)q < c && (uint64_t)r0 + q < lim;
-                        iv[q] = in ? a.out_idx[r0 + q] : ~0u;  // no such outlier: reported below
-                        dv[q] = in ? a.out_delta[r0 + q] : 0;
-                    }
+                    pi[off / 4] = -1;  // no such outlier: reported below
                 }
-                int32_t pv[4] = {0, 0, 0, 0};
-                uint32_t qn = 0;
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    if ((nib >> k) & 1u) {
-                        const uint32_t ei = qn == 0u ? iv[0] : qn == 1u ? iv[1] : qn == 2u ? iv[2] : iv[3];
-                        const int32_t ed = qn == 0u ? dv[0] : qn == 1u ? dv[1] : qn == 2u ? dv[2] : dv[3];
-                        if (ei != base + (uint32_t)u * nx32 + (uint32_t)k) {
-                            atomicMax(&a.hdr->recon_status, (unsigned)VSZ_ERR_CORRUPT);
-                        } else {
-                            pv[k] = ed;
-                        }
-                        ++qn;
-                    }
+            }
+            cp_async_commit();
+            cp_async_wait<0>();
+            m = zm;
+#pragma unroll 1
+            while (m) {
+                const uint32_t jq = (uint32_t)(__ffs(m) - 1);
+                m &= m - 1u;
+                const uint32_t off = (jq >> 2) * 32 * 4 + (jq & 3u);  // in 4-byte words
+                if ((uint32_t)pi[off] != base + (jq >> 2) * nx32 + (jq & 3u)) {
+                    atomicMax(&a.hdr->recon_status, (unsigned)VSZ_ERR_CORRUPT);
+                    pd[off] = 0;
                 }
-                ps[u * 32] = make_int4(pv[0], pv[1], pv[2], pv[3]);
             }
             rank = rowpre[U - 1] + ((tot >> (8 * (U - 1))) & 0xffu);
             return;
