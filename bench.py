@@ -434,8 +434,8 @@ def kernel_key(rec) -> tuple:
 def class_key(p) -> tuple:
     """(compression kernel name, rank, block) of a field's batch class: its
     trace name carries the padding kind (none, per block, global or edge)."""
-    nm = "batch_lorenzo_bp" if p.is_block_pad else ("batch_lorenzo_gp" if p.pad in (1, 2, 3) or p.is_edge_pad
-                                                    else "batch_lorenzo")
+    nm = ("batch_lorenzo_bp" if p.is_block_pad else "batch_lorenzo_gp" if p.pad in (1, 2, 3)
+          else ("batch_lorenzo_ep" if len(p.dims) > 1 else "batch_lorenzo_gp") if p.is_edge_pad else "batch_lorenzo")
     return nm, len(p.dims), int(p.block)
 
 
@@ -881,8 +881,9 @@ def oracle_stream_rate_parallel(specs_host, eb: float, seconds: float, threads: 
 def batch_kernel_name(key) -> str:
     name, nd, b = key
     bp = "true" if name.endswith("_bp") else "false"
-    gp = "true" if name.endswith("_gp") else "false"
-    return f"k_lorenzo_1d_batch<{b},{bp},{gp}>" if nd == 1 else f"k_lorenzo_nd_batch<{nd},{b},{bp},{gp}>"
+    gp = "true" if name.endswith(("_gp", "_ep")) else "false"
+    ep = ",true" if name.endswith("_ep") else ""
+    return f"k_lorenzo_1d_batch<{b},{bp},{gp}>" if nd == 1 else f"k_lorenzo_nd_batch<{nd},{b},{bp},{gp}{ep}>"
 
 
 def strip_private(d: dict) -> dict:

@@ -342,7 +342,7 @@ VSZ_API vsz_status vsz_batch_destroy(vsz_batch b);
 typedef struct {
     int32_t  ndim;
     uint32_t block;
-    int32_t  pad_kind;     /* 0 zero padding, 1 per-block padding, 2 global or edge padding (origins deferred) */
+    int32_t  pad_kind;     /* 0 zero, 1 per-block, 2 global, 3 edge padding (2, 3: origins deferred) */
     int32_t  nfields;      /* fields in the class */
     uint64_t tiles;        /* tiles of all of them */
     int32_t  warps;        /* warps per CTA of the class kernel (0 = default: 4, or 8 in 1D) */

@@ -373,7 +373,9 @@ __device__ __forceinline__ bool chain_lookback(uint64_t* st, uint64_t t, uint32_
             const uint32_t mo = po ? (uint32_t)(((2ull << (__ffs(po) - 1)) - 1ull)) : VSZ_FULL;
             const uint32_t mf = pf ? (uint32_t)(((2ull << (__ffs(pf) - 1)) - 1ull)) : VSZ_FULL;
             if ((need_o && (zo & mo)) || (need_f && (zf & mf))) {
-                if (global_ns() - t0 > limit) {
+                // lanes read the clock at different instants: the warp gives
+                // up together, as soon as any lane sees the limit passed
+                if (__any_sync(VSZ_FULL, global_ns() - t0 > limit)) {
                     ok = false;
                     break;
                 }

@@ -353,6 +353,9 @@ __device__ __forceinline__ void edge_stats_unit(const CompressArgs& a, uint64_t 
         if (b < g.nb) a.pad[b] = prequant(a.x[b * g.b], inv2eb);
         return;
     }
+    // the compression walk gathered the faces itself (fp32 mode proved for
+    // the whole field by the range pass)
+    if (a.wsh->fp32_ok != 0u) return;
     const int nd = g.nd;
     const uint64_t B = g.b;
     const int G = (int)(B / 4);

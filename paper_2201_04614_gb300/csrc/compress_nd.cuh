@@ -138,7 +138,7 @@ __device__ __forceinline__ uint32_t stash_key(uint32_t fix, uint32_t g, uint32_t
 // per-block padding mode; GP: a global padding mode, whose value is known
 // only once every tile has been walked, so block origins are deferred to
 // the origin pass (their q and the tile's q statistics are recorded here).
-template <int ND, int B, bool BP, bool GP>
+template <int ND, int B, bool BP, bool GP, bool EP = false>
 __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t t, unsigned char* wsm, int lane) {
     using C = NdCfg<ND, B>;
     constexpr int G = C::G;
@@ -235,6 +235,26 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
     // an average padding needs only the sum of q
     const bool need_mm = (BP || GP) && a.pad_mode != VSZ_PAD_GLOBAL_AVG && a.pad_mode != VSZ_PAD_BLOCK_AVG;
     long long ssum = 0;
+    // Edge padding (Sec. IV-B-3): the min / max / sum of q over each block's
+    // faces (x: local x = 0, y: local y = 0, z: local z = 0), gathered by the
+    // walk when the range pass proved the fp32 mode for the whole field (then
+    // every |q| < 2^20 and a lane's face sums fit in 32 bits); otherwise the
+    // face-statistics pass computes them from x.
+    const bool efs = EP && fast;
+    const int ekind = EP ? a.pad_mode - VSZ_PAD_EDGE_MIN : 0;  // 0 min, 1 max, 2 mean
+    const int32_t eid = ekind == 0 ? INT_MAX : ekind == 1 ? INT_MIN : 0;
+    int32_t efx = eid, efy = eid, efz = eid;
+    auto etake = [&](int32_t& acc, int32_t v) {
+        acc = ekind == 0 ? min(acc, v) : ekind == 1 ? max(acc, v) : acc + v;
+    };
+    // nv of a row's 4 values (exact integers below 2^20 as floats)
+    auto etake_row = [&](int32_t& acc, const float (&r)[4], int nv) {
+        float m = ekind == 0 ? __int_as_float(0x7f800000) : ekind == 1 ? -__int_as_float(0x7f800000) : 0.0f;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (k < nv) m = ekind == 0 ? fminf(m, r[k]) : ekind == 1 ? fmaxf(m, r[k]) : __fadd_rn(m, r[k]);
+        if (nv > 0) etake(acc, __float2int_rn(m));
+    };
 
     // Rare path of one batch: exact masks of the flagged rows; counts and
     // stash entries (first walk) or direct canonical writes (second walk).
@@ -486,7 +506,12 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
                         fo |= !in;
                         ff |= !(fabsf(__fsub_rn(xv[k], xh)) <= ebf);
                     }
-                    if (BP || GP) {
+                    if (EP && efs) {
+                        if (first) etake(efx, __float2int_rn(rp[0]));    // local x = 0: every row
+                        if (jb == 0 && u == 0) etake_row(efy, rp, 4);    // local y = 0
+                        if (ND == 3 && kb < BPP) etake_row(efz, rp, 4);  // local z = 0: the first plane
+                    }
+                    if (BP || (GP && !EP)) {
                         if (need_mm) {
                             sminf = fminf(sminf, fminf(fminf(rp[0], rp[1]), fminf(rp[2], rp[3])));
                             smaxf = fmaxf(smaxf, fmaxf(fmaxf(rp[0], rp[1]), fmaxf(rp[2], rp[3])));
@@ -511,7 +536,7 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
                     rare_rows((rows | (rows >> 8)) & 0xffu, rows >> 8, h, tile_base + off32(kb), jb, kb / BPP, kb == 0,
                               false, false, false);
                 h = h + 1 == C::NS ? 0 : h + 1;
-                if (BP || GP) {
+                if (BP || (GP && !EP)) {
                     ssum += lsum;
                     lsum = 0;
                 }
@@ -623,7 +648,12 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
                         fo |= !(fabsf(d[k]) < Rf);
                         ff |= !(fabsf(__fsub_rn(xr[u][k], xh)) <= ebf);
                     }
-                    if (BP || GP) {
+                    if (EP && efs && valid > 0) {
+                        if (first) etake(efx, __float2int_rn(rp[0]));
+                        if (ly == 0) etake_row(efy, rp, valid);
+                        if (ND == 3 && lz == 0) etake_row(efz, rp, valid);
+                    }
+                    if (BP || (GP && !EP)) {
                         float rs = 0.f;
 #pragma unroll
                         for (int k = 0; k < 4; ++k) {
@@ -684,7 +714,7 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
                         c[k] = code_of(d[k], R);
                         fo |= c[k] == 0u;
                         if (!nofix) ff |= needs_fixup(xr[u][k], q[k], ebx2, ebf);
-                        if ((BP || GP) && !emit && k < valid) {
+                        if ((BP || (GP && !EP)) && !emit && k < valid) {
                             smin = min(smin, q[k]);
                             smax = max(smax, q[k]);
                             ssum += q[k];
@@ -747,9 +777,8 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
             if (valid == 0 || VSZ_IN(tile_base + valid - 1, g.n, 106)) store4c(a.codes + tile_base, valid, vst, r0c01, r0c23);
         }
 
-        if (GP) {
-            // the tile's q statistics for the global padding value; the
-            // block origins wait for it in the origin table
+        if (GP && !EP) {
+            // the tile's q statistics for the global padding value
             smin = min(smin, __float2int_rn(sminf));
             smax = max(smax, __float2int_rn(smaxf));
 #pragma unroll
@@ -759,7 +788,33 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
                 ssum += __shfl_xor_sync(VSZ_FULL, ssum, off);
             }
             if (lane == 0) global_stats_add(a, smin, smax, ssum);
-            if (first && bexists && VSZ_IN(blk, g.nb, 107)) a.origin[blk] = qcorner;
+        }
+        // the block origins wait for the padding value in the origin table
+        if (GP && first && bexists && VSZ_IN(blk, g.nb, 107)) a.origin[blk] = qcorner;
+        if (EP && efs) {
+            // each block's face scalars: its G lanes reduced, then the
+            // minimum, maximum or rounded mean (counts of in-field elements)
+#pragma unroll
+            for (int off = 1; off < G; off <<= 1) {
+                etake(efx, __shfl_xor_sync(VSZ_FULL, efx, off));
+                etake(efy, __shfl_xor_sync(VSZ_FULL, efy, off));
+                if (ND == 3) etake(efz, __shfl_xor_sync(VSZ_FULL, efz, off));
+            }
+            if (first && bexists && VSZ_IN(blk * ND + ND - 1, g.nb * ND, 112)) {
+                const long long xl = (long long)umin64(B, nx - bx * B), yl = ylen, zl = zlen;
+                auto fin = [&](int32_t acc, long long cnt) {
+                    return ekind == 2 ? rounded_mean((long long)acc, cnt) : acc;
+                };
+                int32_t* pd = a.pad + blk * ND;
+                if (ND == 3) {
+                    pd[0] = fin(efz, yl * xl);
+                    pd[1] = fin(efy, zl * xl);
+                    pd[2] = fin(efx, zl * yl);
+                } else {
+                    pd[0] = fin(efy, xl);
+                    pd[1] = fin(efx, yl);
+                }
+            }
         }
 
         // Per-block counts, in-tile exclusive offsets (blk_off), tile totals.
@@ -820,7 +875,7 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
                         uint2 e[4];
 #pragma unroll
                         for (int q = 0; q < 4; ++q)
-                            if (i < c[q] && VSZ_IN(s0[q] + i, g.nb * C::SLOT, 109)) e[q] = slots[s0[q] + i];
+                            if (i < c[q] && VSZ_IN(s0[q] + i, g.nb * C::SLOT, 111)) e[q] = slots[s0[q] + i];
 #pragma unroll
                         for (int q = 0; q < 4; ++q)
                             if (i < c[q]) put_out((uint64_t)d0[q] + i, e[q].x, e[q].y);
@@ -888,7 +943,7 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
 }
 
 // One field: tiles handed out by the field's own ticket.
-template <int ND, int B, bool BP, bool GP>
+template <int ND, int B, bool BP, bool GP, bool EP = false>
 __global__ void __launch_bounds__(NdCfg<ND, B>::THREADS, NdCfg<ND, B>::MINB_C)
 k_lorenzo_nd(const CompressArgs a) {
     pdl_prologue();
@@ -900,7 +955,7 @@ k_lorenzo_nd(const CompressArgs a) {
         if (lane == 0) tk = atomicAdd(&a.wsh->ticket, 1ull);
         const uint64_t t = __shfl_sync(VSZ_FULL, tk, 0);
         if (t >= a.g.ntiles) break;
-        nd_compress_tile<ND, B, BP, GP>(a, t, wsm, lane);
+        nd_compress_tile<ND, B, BP, GP, EP>(a, t, wsm, lane);
     }
 }
 
@@ -919,7 +974,7 @@ struct NdBatchBounds {
 // Many fields of one class (rank, block edge, padding kind): one queue over
 // the tiles of all of them.  tile_prefix[f] is the first global tile of field
 // f, tile_prefix[nfields] the total.  Any warps per CTA up to 8.
-template <int ND, int B, bool BP, bool GP>
+template <int ND, int B, bool BP, bool GP, bool EP = false>
 __global__ void __launch_bounds__(NdBatchBounds<ND, B>::MAXT, NdBatchBounds<ND, B>::MINB)
 k_lorenzo_nd_batch(const CompressArgs* __restrict__ fields, const uint64_t* __restrict__ tile_prefix, int nfields,
                    unsigned long long* ticket) {
@@ -937,7 +992,7 @@ k_lorenzo_nd_batch(const CompressArgs* __restrict__ fields, const uint64_t* __re
             const int mid = (lo + hi + 1) >> 1;
             if (tile_prefix[mid] <= gt) lo = mid; else hi = mid - 1;
         }
-        nd_compress_tile<ND, B, BP, GP>(fields[lo], gt - tile_prefix[lo], wsm, lane);
+        nd_compress_tile<ND, B, BP, GP, EP>(fields[lo], gt - tile_prefix[lo], wsm, lane);
     }
 }
 

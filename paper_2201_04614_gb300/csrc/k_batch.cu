@@ -250,7 +250,7 @@ using namespace vsz;
 struct BatchClass {
     int nd;
     uint32_t b;
-    int pk;                        // 0 zero padding, 1 per-block padding, 2 global padding (compression)
+    int pk;                        // 0 zero, 1 per-block, 2 global, 3 edge padding (compression)
     int kind = 0;                  // 0 compression, 1 reconstruction
     std::vector<int> fields;       // indices into the batch
     CompressArgs* d_args = nullptr;
@@ -292,11 +292,11 @@ struct vsz_batch_st {
     cudaGraphExec_t rexec = nullptr;
 };
 
-// Class of a job: (rank, block edge, padding kind 0 zero / 1 per block / 2 global or edge).
+// Class of a job: (rank, block edge, padding kind 0 zero / 1 per block / 2 global / 3 edge).
 using ClassKey = std::tuple<int, uint32_t, int>;
 static ClassKey class_key(const vsz_field_job& j, const Geom& g) {
     const int32_t m = j.params.pad;
-    return std::make_tuple(g.nd, g.b, is_block_pad(m) ? 1 : (is_global_pad(m) || is_edge_pad(m)) ? 2 : 0);
+    return std::make_tuple(g.nd, g.b, is_block_pad(m) ? 1 : is_global_pad(m) ? 2 : is_edge_pad(m) ? 3 : 0);
 }
 
 // Workspace of a batch: the header, then every field's workspace (2D/3D
@@ -412,7 +412,9 @@ static cudaError_t launch_class_origins(vsz_batch_st* b, size_t c, cudaStream_t 
 
 static cudaError_t launch_class(vsz_batch_st* b, size_t c, cudaStream_t s) {
     BatchClass& k = b->classes[c];
-    TraceScope ts(k.pk == 1 ? "batch_lorenzo_bp" : k.pk == 2 ? "batch_lorenzo_gp" : "batch_lorenzo", s, k.nd, k.b);
+    TraceScope ts(k.pk == 1 ? "batch_lorenzo_bp" : k.pk == 2 ? "batch_lorenzo_gp" : k.pk == 3 ? "batch_lorenzo_ep"
+                                                                                             : "batch_lorenzo",
+                  s, k.nd, k.b);
     return k.nd == 1 ? launch_lorenzo_batch_1d(k.b, k.pk, k.d_args, k.d_prefix, (int)k.fields.size(), k.total_tiles,
                                                b->tickets + c, k.shape, s)
          : k.nd == 2 ? launch_lorenzo_batch_2d(k.b, k.pk, k.d_args, k.d_prefix, (int)k.fields.size(), k.total_tiles,

@@ -664,13 +664,14 @@ static cudaError_t launch_c1_batch_k(const CompressArgs* fields, const uint64_t*
     return cudaGetLastError();
 }
 
-// pk: 0 zero padding, 1 per-block padding, 2 global padding
+// pk: 0 zero padding, 1 per-block padding, 2 global padding, 3 edge padding
 template <int B>
 static cudaError_t launch_c1_batch(int pk, const CompressArgs* fields, const uint64_t* tile_prefix, int nfields,
                                    uint64_t total_tiles, unsigned long long* ticket, LaunchShape sh, cudaStream_t s,
                                    int* occ) {
     if (pk == 1) return launch_c1_batch_k<B, true, false>(fields, tile_prefix, nfields, total_tiles, ticket, sh, s, occ);
-    if (pk == 2) return launch_c1_batch_k<B, false, true>(fields, tile_prefix, nfields, total_tiles, ticket, sh, s, occ);
+    if (pk == 2 || pk == 3)  // global or edge padding (a 1D block's face is its first value)
+        return launch_c1_batch_k<B, false, true>(fields, tile_prefix, nfields, total_tiles, ticket, sh, s, occ);
     return launch_c1_batch_k<B, false, false>(fields, tile_prefix, nfields, total_tiles, ticket, sh, s, occ);
 }
 

@@ -614,29 +614,30 @@ k_recon_nd_batch(const ReconArgs* __restrict__ fields, const uint64_t* __restric
 }
 
 // Host-side launch helpers for one rank, instantiated by k_rank2.cu / k_rank3.cu.
-template <int ND, int B, bool BP, bool GP>
+template <int ND, int B, bool BP, bool GP, bool EP = false>
 cudaError_t launch_nd_compress_k(const CompressArgs& a, cudaStream_t s) {
     using C = NdCfg<ND, B>;
-    const void* k = (const void*)k_lorenzo_nd<ND, B, BP, GP>;
+    const void* k = (const void*)k_lorenzo_nd<ND, B, BP, GP, EP>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM_C);
     if (e != cudaSuccess) return e;
     const int grid = grid_for(k, C::THREADS, C::SMEM_C, C::WARPS, a.g.ntiles);
-    return launch_pdl(k_lorenzo_nd<ND, B, BP, GP>, grid, C::THREADS, C::SMEM_C, s, a);
+    return launch_pdl(k_lorenzo_nd<ND, B, BP, GP, EP>, grid, C::THREADS, C::SMEM_C, s, a);
 }
 
 template <int ND, int B>
 cudaError_t launch_nd_compress(const CompressArgs& a, cudaStream_t s) {
     if (is_block_pad(a.pad_mode)) return launch_nd_compress_k<ND, B, true, false>(a, s);
+    if (is_edge_pad(a.pad_mode)) return launch_nd_compress_k<ND, B, false, true, true>(a, s);
     if (defers_origin(a.pad_mode)) return launch_nd_compress_k<ND, B, false, true>(a, s);
     return launch_nd_compress_k<ND, B, false, false>(a, s);
 }
 
-template <int ND, int B, bool BP, bool GP>
+template <int ND, int B, bool BP, bool GP, bool EP = false>
 cudaError_t launch_nd_compress_batch_k(const CompressArgs* fields, const uint64_t* tile_prefix, int nfields,
                                        uint64_t total_tiles, unsigned long long* ticket, LaunchShape sh,
                                        cudaStream_t s, int* occ) {
     using C = NdCfg<ND, B>;
-    const void* k = (const void*)k_lorenzo_nd_batch<ND, B, BP, GP>;
+    const void* k = (const void*)k_lorenzo_nd_batch<ND, B, BP, GP, EP>;
     const int warps = sh.warps > 0 ? sh.warps : C::WARPS;
     if (warps * 32 > NdBatchBounds<ND, B>::MAXT) {
         if (occ) *occ = 0;
@@ -650,17 +651,20 @@ cudaError_t launch_nd_compress_batch_k(const CompressArgs* fields, const uint64_
     }
     if (e != cudaSuccess) return e;
     const int grid = grid_shape(k, warps * 32, smem, (uint64_t)warps, total_tiles, sh.ctas);
-    k_lorenzo_nd_batch<ND, B, BP, GP><<<grid, warps * 32, smem, s>>>(fields, tile_prefix, nfields, ticket);
+    k_lorenzo_nd_batch<ND, B, BP, GP, EP><<<grid, warps * 32, smem, s>>>(fields, tile_prefix, nfields, ticket);
     return cudaGetLastError();
 }
 
-// pk: 0 zero padding, 1 per-block padding, 2 global padding
+// pk: 0 zero padding, 1 per-block padding, 2 global padding, 3 edge padding
 template <int ND, int B>
 cudaError_t launch_nd_compress_batch(int pk, const CompressArgs* fields, const uint64_t* tile_prefix, int nfields,
                                      uint64_t total_tiles, unsigned long long* ticket, LaunchShape sh,
                                      cudaStream_t s, int* occ) {
     if (pk == 1)
         return launch_nd_compress_batch_k<ND, B, true, false>(fields, tile_prefix, nfields, total_tiles, ticket, sh, s, occ);
+    if (pk == 3)
+        return launch_nd_compress_batch_k<ND, B, false, true, true>(fields, tile_prefix, nfields, total_tiles, ticket, sh,
+                                                                    s, occ);
     if (pk == 2)
         return launch_nd_compress_batch_k<ND, B, false, true>(fields, tile_prefix, nfields, total_tiles, ticket, sh, s, occ);
     return launch_nd_compress_batch_k<ND, B, false, false>(fields, tile_prefix, nfields, total_tiles, ticket, sh, s, occ);
