@@ -49,9 +49,7 @@ typedef enum {
     VSZ_ERR_CAPACITY = 3,     /* outlier or fixup lists longer than the caller's capacity */
     VSZ_ERR_CUDA = 4,         /* a CUDA launch or runtime call failed */
     VSZ_ERR_CORRUPT = 5,      /* reconstruction met a code 0 with no matching outlier */
-    VSZ_ERR_TOO_LARGE = 6,    /* the call needs more scratch than vsz_compress_noalloc's fixed workspace */
-    VSZ_ERR_TIMEOUT = 7       /* a device-side wait ran past its limit (compression's tile chain);
-                                 the call's outputs are not valid, the context stays usable */
+    VSZ_ERR_TOO_LARGE = 6     /* the call needs more scratch than vsz_compress_noalloc's fixed workspace */
 } vsz_status;
 
 /* Sec. II-B: absolute, or value-range relative (eb * (max - min)). */
@@ -167,15 +165,9 @@ VSZ_API size_t vsz_workspace_size_dense(const vsz_params* p, uint64_t out_cap, u
  * resolution, prequantization q = rint(x * inv2eb), padding value, blockwise
  * first-order Lorenzo prediction, post-quantization into uint16 codes, and
  * the fp32 error-bound guard.  Writes c->codes, c->pad (block modes),
- * c->hdr (scalars).  Zero and per-block padding: the outlier and fixup
- * lists are written in their canonical place as well (each tile learns the
- * number of entries before it from a chained scan over the tiles, a
- * decoupled look-back whose waits are bounded: a wait past its limit sets
- * c->hdr->status = VSZ_ERR_TIMEOUT), with c->blk_off and the counts, so the
- * compression is complete when the call's kernels are.  Global and edge
- * padding settle the block origins after the walk: their lists stay staged
- * in the workspace until vsz_outlier_compact.  For VSZ_EB_REL the value
- * range is reduced on the device; no host synchronization happens.
+ * c->hdr (scalars), and leaves per-tile outlier and fixup lists staged in
+ * the workspace.  For VSZ_EB_REL the value range is reduced on the device;
+ * no host synchronization happens.
  *   p         field and method parameters (host)
  *   d_x       [n] fp32 input (device), 16-byte aligned for the vector path
  *   c         output buffers (host struct of device pointers)
@@ -194,8 +186,6 @@ VSZ_API vsz_status vsz_prequant_lorenzo(const vsz_params* p, const float* d_x, v
  * is longer than its capacity, the counts and blk_off are still exact, the
  * lists are truncated and c->hdr->status = VSZ_ERR_CAPACITY; retry with
  * larger buffers.  Must follow vsz_prequant_lorenzo on the same workspace.
- * For zero and per-block padding step 1 has already done all of this (the
- * call launches nothing, except for an empty field's blk_off[0]).
  */
 VSZ_API vsz_status vsz_outlier_compact(const vsz_params* p, vsz_compressed* c,
                                void* d_ws, size_t ws_bytes, void* stream);
@@ -720,22 +710,6 @@ VSZ_API vsz_status vsz_debug_fail_alloc(int k);
  * Reads the first recorded site number (0 if none) into *out and clears it.
  * The normal build checks nothing and returns VSZ_ERR_UNSUPPORTED with 0. */
 VSZ_API vsz_status vsz_debug_bounds_word(uint32_t* out);
-
-/* The tile chain on its own, for tests of its waits (Sec. III-A lists in
- * canonical order; the compression kernels of zero and per-block padding
- * use the same device code).  One warp per tile takes tiles 0..ntiles-1 in
- * ticket order; tile t publishes (agg_o[t], agg_f[t]) and receives the sums
- * over tiles 0..t-1 in ex[2t], ex[2t+1].  Tile `withhold` (or none, if
- * negative) takes its ticket but never publishes, so the tiles after it wait
- * until their limit of wait_ns nanoseconds runs out, give up, and count
- * themselves in *d_timeouts.  Device arrays: agg_o, agg_f uint32[ntiles];
- * status uint64[2*ntiles] (zeroed by the call); ex uint64[2*ntiles];
- * d_timeouts uint32[2] (timeouts, then the ticket counter).  Asynchronous on
- * `stream`.  VSZ_ERR_INVALID_ARG on a NULL array, ntiles < 1 or > 65536,
- * or wait_ns = 0. */
-VSZ_API vsz_status vsz_debug_chain(const uint32_t* agg_o, const uint32_t* agg_f, int ntiles, int withhold,
-                                   uint32_t wait_ns, uint64_t* status, uint64_t* ex, uint32_t* d_timeouts,
-                                   void* stream);
 
 /* Release what the library holds itself: tracing is switched off, pending
  * trace records are dropped and the recorder's CUDA events destroyed, and

@@ -25,8 +25,7 @@ PAD_MODES = {
     "block_min": 4, "block_max": 5, "block_avg": 6, "edge_min": 7, "edge_max": 8, "edge_avg": 9,
 }
 _STATUS = {0: "VSZ_OK", 1: "VSZ_ERR_INVALID_ARG", 2: "VSZ_ERR_UNSUPPORTED",
-           3: "VSZ_ERR_CAPACITY", 4: "VSZ_ERR_CUDA", 5: "VSZ_ERR_CORRUPT", 6: "VSZ_ERR_TOO_LARGE",
-           7: "VSZ_ERR_TIMEOUT"}
+           3: "VSZ_ERR_CAPACITY", 4: "VSZ_ERR_CUDA", 5: "VSZ_ERR_CORRUPT", 6: "VSZ_ERR_TOO_LARGE"}
 NOALLOC_WS_BYTES = 16 << 20  # VSZ_NOALLOC_WS_BYTES
 RECON_WS_BYTES = 256         # VSZ_RECON_WS_BYTES
 
@@ -95,7 +94,7 @@ EXPORTED = ["vsz_status_string", "vsz_last_cuda_error", "vsz_abi_version", "vsz_
             "vsz_batch_compress_host", "vsz_slab_range", "vsz_slab_qstats", "vsz_compress_slab", "vsz_slab_rebase",
             "vsz_huffman_book_bytes", "vsz_huffman_book", "vsz_huffman_book_read", "vsz_huffman_encode",
             "vsz_huffman_encode_workspace_size", "vsz_sampling_autotune_workspace_size", "vsz_sampling_autotune",
-            "vsz_sync_status", "vsz_shutdown", "vsz_debug_fail_alloc", "vsz_debug_bounds_word", "vsz_debug_chain",
+            "vsz_sync_status", "vsz_shutdown", "vsz_debug_fail_alloc", "vsz_debug_bounds_word",
             "vsz_huffman_decode",
             "vsz_tuner_features_workspace_size", "vsz_tuner_features",
             "vsz_tuner_sweep_workspace_size", "vsz_tuner_sweep", "vsz_tuner_guard_workspace_size",
@@ -172,7 +171,6 @@ def lib():
     L.vsz_slab_rebase.argtypes = [P(_CParams), P(_CCompressed), u64, u64, vp]
     L.vsz_trace_enable.argtypes = [ctypes.c_int]
     L.vsz_debug_bounds_word.argtypes = [P(ctypes.c_uint32)]
-    L.vsz_debug_chain.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_uint32, vp, vp, vp, vp]
     L.vsz_trace_read.argtypes = [P(_CTrace), ctypes.c_int]
     for name in EXPORTED:
         if name.startswith(("vsz_tuner", "vsz_mlp", "vsz_sampling")):
@@ -192,22 +190,6 @@ def debug_bounds_word():
     v = ctypes.c_uint32(0)
     rc = lib().vsz_debug_bounds_word(ctypes.byref(v))
     return None if rc == 2 else int(v.value)
-
-
-def debug_chain(agg_o, agg_f, withhold: int = -1, wait_ns: int = 1_000_000_000, stream=None) -> dict:
-    """The tile chain alone (vsz_debug_chain): int32 CUDA tensors of per-tile
-    totals; tile `withhold` never publishes.  Returns {"ex_o", "ex_f": the
-    exclusive sums each tile received (int64 tensors), "timeouts": the
-    tiles that gave up waiting}."""
-    import torch
-    n = int(agg_o.numel())
-    st = torch.empty(2 * n, dtype=torch.int64, device=agg_o.device)
-    ex = torch.zeros(2 * n, dtype=torch.int64, device=agg_o.device)
-    ctl = torch.zeros(2, dtype=torch.int32, device=agg_o.device)
-    _check(lib().vsz_debug_chain(_ptr(agg_o), _ptr(agg_f), n, int(withhold), int(wait_ns), _ptr(st), _ptr(ex),
-                                 _ptr(ctl), _stream_handle(stream)), "vsz_debug_chain")
-    torch.cuda.synchronize(agg_o.device)
-    return {"ex_o": ex[0::2].cpu(), "ex_f": ex[1::2].cpu(), "timeouts": int(ctl[0].item())}
 
 
 def trace_enable(on: bool = True) -> None:

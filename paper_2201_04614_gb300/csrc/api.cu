@@ -241,21 +241,11 @@ const char* vsz_status_string(vsz_status s) {
     case VSZ_ERR_CUDA: return "VSZ_ERR_CUDA";
     case VSZ_ERR_CORRUPT: return "VSZ_ERR_CORRUPT";
     case VSZ_ERR_TOO_LARGE: return "VSZ_ERR_TOO_LARGE";
-    case VSZ_ERR_TIMEOUT: return "VSZ_ERR_TIMEOUT";
     default: return "VSZ_ERR_UNKNOWN";
     }
 }
 
 const char* vsz_last_cuda_error(void) { return g_last_err; }
-
-vsz_status vsz_debug_chain(const uint32_t* agg_o, const uint32_t* agg_f, int ntiles, int withhold, uint32_t wait_ns,
-                           uint64_t* status, uint64_t* ex, uint32_t* d_timeouts, void* stream) {
-    if (!agg_o || !agg_f || !status || !ex || !d_timeouts || ntiles < 1 || ntiles > 65536 || wait_ns == 0)
-        return VSZ_ERR_INVALID_ARG;
-    const cudaError_t e = launch_debug_chain(agg_o, agg_f, ntiles, withhold, wait_ns, status, ex, d_timeouts,
-                                             (cudaStream_t)stream);
-    return e == cudaSuccess ? VSZ_OK : cuda_fail(e);
-}
 
 vsz_status vsz_debug_bounds_word(uint32_t* out) {
     if (!out) return VSZ_ERR_INVALID_ARG;
@@ -354,8 +344,11 @@ static CompressArgs compress_args(const Geom& g, const vsz_params* p, const floa
     a.R = (int32_t)p->radius;
     a.pad_mode = p->pad;
     a.vec = (aligned(d_x, 16) && aligned(c->codes, 16) && (g.nd == 1 || g.nx % 4 == 0)) ? 1 : 0;
-    if (slots) a.slots = a.stage_out;
-    a.chained = chained_field(p->pad) ? 1 : 0;
+    a.blk_in = c->blk_off;
+    if (slots) {
+        a.slots = a.stage_out;
+        a.blk_in = (uint32_t*)(ws + L.blkin);
+    }
     return a;
 }
 }  // namespace vsz
@@ -382,8 +375,7 @@ static vsz_status prequant_lorenzo_impl(const vsz_params* p, const float* d_x, v
     cudaError_t e;
     {
         TraceScope ts("begin", s, g.nd, g.b, g.n);
-        e = launch_begin(wsh, chunks, g.nchunks, (uint4*)(ws + L.tiles), chained_field(p->pad) ? g.ntiles : 0,
-                         c->hdr, p->eb, rel, s);
+        e = launch_begin(wsh, chunks, g.nchunks, c->hdr, p->eb, rel, s);
     }
     if (e != cudaSuccess) return cuda_fail(e);
     if (rel) {
@@ -437,10 +429,6 @@ vsz_status vsz_outlier_compact(const vsz_params* p, vsz_compressed* c, void* d_w
     if (!d_ws || ws_bytes < L.total || !aligned(d_ws, 256)) return VSZ_ERR_INVALID_ARG;
     char* ws = (char*)d_ws;
     cudaStream_t s = (cudaStream_t)stream;
-    // zero or per-block padding: the compression's tile chain already wrote
-    // the lists in place and closed them (an empty field still gets its
-    // blk_off[0] and counts from the scan below)
-    if (chained_field(p->pad) && g.ntiles > 0) return VSZ_OK;
     cudaError_t e;
     {
         TraceScope ts("compact_scan", s, g.nd, g.b, g.n);

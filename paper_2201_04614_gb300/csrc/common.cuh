@@ -66,6 +66,7 @@ struct WsLayout {
     size_t chunks;     // uint4 per chunk {sum_out, sum_fix, off_out, off_fix}
     size_t origin;     // int32 per block: q at the block origin, then its residual (global padding)
     size_t oflag;      // uint8 per block: the origin is an outlier (global padding)
+    size_t blkin;      // uint32 per block: in-tile offsets from the walk (block slots only)
     size_t stage_out;  // uint2 per outlier {idx, delta}
     size_t stage_fix;  // uint2 per fixup {idx, bits}
     size_t total;
@@ -89,6 +90,8 @@ inline WsLayout ws_layout(const Geom& g, uint64_t out_cap, uint64_t fix_cap, boo
     off = align256(off + g.nb * 4);
     L.oflag = off;
     off = align256(off + g.nb);
+    L.blkin = off;
+    if (slots && g.nd >= 2) off = align256(off + g.nb * 4);
     L.stage_out = off;
     off = align256(off + out_cap * 8);
     L.stage_fix = off;
@@ -214,7 +217,9 @@ struct CompressArgs {
     const float* x;
     uint16_t* codes;
     int32_t* pad;          // [nb] block modes
-    uint32_t* blk_off;     // [nb+1]; receives in-tile exclusive prefixes here
+    uint32_t* blk_off;     // [nb+1]
+    uint32_t* blk_in;      // [nb] in-tile exclusive prefixes from the walk: blk_off itself, or (block
+                           // slots) a workspace table, which the compaction reads while it writes blk_off
     const vsz_header* hdr;
     WsHeader* wsh;
     uint4* tiles;
@@ -235,8 +240,6 @@ struct CompressArgs {
     uint2* slots;          // block-slot staging (2D/3D: stage_out laid out as nb slots), or nullptr
     int32_t has_gpad;      // a global padding value given by the caller (a slab of a split field)
     int32_t gpad;
-    int32_t chained;       // lists placed by the tile chain (tiles[] holds its status words)
-    uint32_t chain_ns;     // wait limit of the tile chain, in ns (0: the default)
 };
 
 struct ReconArgs {
@@ -264,10 +267,6 @@ __host__ __device__ inline bool is_global_pad(int m) {
 __host__ __device__ inline bool is_edge_pad(int m) {
     return m == VSZ_PAD_EDGE_MIN || m == VSZ_PAD_EDGE_MAX || m == VSZ_PAD_EDGE_AVG;
 }
-// Zero and per-block padding know every residual during the walk, so the
-// tile chain places their lists (no staging, no compaction); global and edge
-// padding settle block origins after the walk and keep the staged path.
-__host__ __device__ inline bool chained_field(int m) { return !is_global_pad(m) && !is_edge_pad(m); }
 // Modes whose padding is known only after the walk: the walk leaves the block
 // origins to an origin pass (global statistics, or per-block face statistics).
 __host__ __device__ inline bool defers_origin(int m) { return is_global_pad(m) || is_edge_pad(m); }
@@ -306,115 +305,6 @@ __device__ __forceinline__ int32_t global_pad_value(const CompressArgs& a) {
     return a.pad_mode == VSZ_PAD_GLOBAL_MIN ? a.wsh->qmin
          : a.pad_mode == VSZ_PAD_GLOBAL_MAX ? a.wsh->qmax
          : rounded_mean((long long)a.wsh->qsum, (long long)a.g.n);
-}
-
-// ---------------------------------------------------------------------------
-// The tile chain: a decoupled look-back over the tiles of one field (the
-// single-pass prefix scan of Merrill and Garland), which gives each tile the
-// number of outliers and fixups of the field's earlier tiles, so that a
-// tile writes its entries straight to their canonical place in the lists
-// (Sec. III-A) and no compaction pass runs.  Tiles are handed out in order
-// by an atomic ticket, so every tile a tile waits for was taken earlier by a
-// running warp, which publishes its own totals before it waits for anyone.
-// Status words (two per tile, outliers then fixups, zeroed by the first
-// kernel of the call): bits 63:62 the flag (0 not yet, 1 the tile's own
-// total, 2 the inclusive prefix), bits 61:0 the value.
-constexpr uint64_t kChainAgg = 1ull << 62;
-constexpr uint64_t kChainInc = 2ull << 62;
-constexpr uint64_t kChainVal = (1ull << 62) - 1;
-constexpr uint32_t kChainWaitNs = 1000000000u;  // default wait limit: 1 s
-
-__device__ __forceinline__ void st_relaxed_u64(uint64_t* p, uint64_t v) {
-    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t* p) {
-    uint64_t v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ uint64_t global_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Tile t of the field whose status words are st (2 per tile) publishes its
-// totals (agg_o outliers, agg_f fixups) and receives the sums over tiles
-// 0..t-1 in *ex_o / *ex_f (every lane of the warp).  A wait longer than
-// wait_ns gives up: the tile publishes what it summed, and false is
-// returned (the caller records VSZ_ERR_TIMEOUT).
-__device__ __forceinline__ bool chain_lookback(uint64_t* st, uint64_t t, uint32_t agg_o, uint32_t agg_f,
-                                               uint32_t wait_ns, int lane, uint64_t* ex_o, uint64_t* ex_f) {
-    if (lane == 0) {
-        const uint64_t flag = t == 0 ? kChainInc : kChainAgg;
-        st_relaxed_u64(st + 2 * t + 1, flag | agg_f);
-        st_relaxed_u64(st + 2 * t, flag | agg_o);
-    }
-    uint64_t so = 0, sf = 0;
-    bool ok = true;
-    if (t > 0) {
-        bool need_o = true, need_f = true;
-        long long w = (long long)t - 1;  // the window: tiles w, w-1, .., w-31 (lane order)
-        const uint64_t t0 = global_ns();
-        const uint32_t limit = wait_ns ? wait_ns : kChainWaitNs;
-        uint32_t sleep = 32;
-        while (need_o || need_f) {
-            const long long tt = w - lane;
-            uint64_t vo = kChainInc, vf = kChainInc;  // before the first tile: an inclusive 0
-            if (tt >= 0) {
-                vo = ld_relaxed_u64(st + 2 * tt);
-                vf = ld_relaxed_u64(st + 2 * tt + 1);
-            }
-            const uint32_t po = __ballot_sync(VSZ_FULL, (vo >> 62) == 2u);
-            const uint32_t pf = __ballot_sync(VSZ_FULL, (vf >> 62) == 2u);
-            const uint32_t zo = __ballot_sync(VSZ_FULL, (vo >> 62) == 0u);
-            const uint32_t zf = __ballot_sync(VSZ_FULL, (vf >> 62) == 0u);
-            // lanes up to the nearest inclusive prefix count
-            const uint32_t mo = po ? (uint32_t)(((2ull << (__ffs(po) - 1)) - 1ull)) : VSZ_FULL;
-            const uint32_t mf = pf ? (uint32_t)(((2ull << (__ffs(pf) - 1)) - 1ull)) : VSZ_FULL;
-            if ((need_o && (zo & mo)) || (need_f && (zf & mf))) {
-                // lanes read the clock at different instants: the warp gives
-                // up together, as soon as any lane sees the limit passed
-                if (__any_sync(VSZ_FULL, global_ns() - t0 > limit)) {
-                    ok = false;
-                    break;
-                }
-                __nanosleep(sleep);
-                sleep = sleep < 512 ? sleep * 2 : 512;
-                continue;
-            }
-            unsigned long long co = (need_o && ((mo >> lane) & 1u)) ? (vo & kChainVal) : 0ull;
-            unsigned long long cf = (need_f && ((mf >> lane) & 1u)) ? (vf & kChainVal) : 0ull;
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                co += __shfl_xor_sync(VSZ_FULL, co, off);
-                cf += __shfl_xor_sync(VSZ_FULL, cf, off);
-            }
-            so += co;
-            sf += cf;
-            if (po) need_o = false;
-            if (pf) need_f = false;
-            w -= 32;
-        }
-        if (lane == 0) {
-            st_relaxed_u64(st + 2 * t + 1, kChainInc | ((sf + agg_f) & kChainVal));
-            st_relaxed_u64(st + 2 * t, kChainInc | ((so + agg_o) & kChainVal));
-        }
-    }
-    *ex_o = so;
-    *ex_f = sf;
-    return ok;
-}
-
-// The last tile of a chained field closes the lists: counts in the header,
-// blk_off[nb], and the capacity status (what the compaction scan does for
-// a staged field).
-__device__ __forceinline__ void chain_close(const CompressArgs& a, uint64_t n_out, uint64_t n_fix) {
-    vsz_header* h = const_cast<vsz_header*>(a.hdr);
-    h->n_out = n_out;
-    h->n_fix = n_fix;
-    a.blk_off[a.g.nb] = (uint32_t)n_out;
-    if (n_out > a.out_cap || n_fix > a.fix_cap) atomicMax(&h->status, (unsigned)VSZ_ERR_CAPACITY);
 }
 
 // Programmatic dependent launch.  Every kernel of the one-field sequence

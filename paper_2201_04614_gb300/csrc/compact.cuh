@@ -203,117 +203,161 @@ __device__ __forceinline__ void compact_chunk_body(uint64_t chunk, const Compres
     }
 }
 
-// Compaction, part 2, with block-slot staging (2D/3D): per chunk of tiles
-// (one CTA, one warp per tile), the tiles' offsets as above, each block's
-// final offset (lane k holds block k of the tile: at most 32 per tile), the
-// origin outlier a global or edge padding mode made (first in its block),
-// then each block's slot moved to its place: entries from slot 1 on, or from
-// slot 0 when a per-block padding mode put the block's origin there.
-__device__ __forceinline__ void compact_chunk_body_slots(uint64_t chunk, const CompressArgs& a) {
-    __shared__ uint4 rec[kTilesPerChunk];
-    __shared__ uint32_t toff_o[kTilesPerChunk], toff_f[kTilesPerChunk];
+// Compaction, part 2, with block-slot staging (2D/3D).  Outliers cluster
+// where the field is rough, so one chunk can hold most of a field's
+// entries: a chunk is served by up to kSplit CTAs (split 0..kSplit-1), each
+// moving an equal share of the chunk's entries, and a CTA whose share is
+// empty returns at once.  Every CTA of a chunk builds the same table in
+// shared memory: each block's first place relative to the chunk (tile
+// offset + the block's in-tile offset from the walk + the origin outliers
+// of the tile's earlier blocks), non-decreasing over the chunk's blocks in
+// order (the places of a tile's missing blocks repeat its end).  Place q of
+// the chunk then lies in the block whose first place is the largest one
+// <= q (a binary search over the table); it is that block's entry q - first,
+// which is its origin outlier (global or edge padding: a block's first
+// entry, placed by split 0) or the slot entry after it, counting from slot 1,
+// or from slot 0 when a per-block padding mode put the block's origin there.
+// Split 0 also writes the blocks' final offsets (blk_off) and moves the
+// fixups (contiguous per tile in staging and in the list).
+constexpr int kSplit = 8;                 // CTAs per chunk at most
+constexpr uint32_t kSplitMinEntries = 2048;  // entries a CTA moves at least before the chunk is split further
+constexpr int kMoveUnroll = 8;            // entries in flight per thread
+
+// Splits a chunk of `entries` outliers needs (the per-field launch gives
+// every chunk kSplit CTAs; a batch lists the extra ones of its dense chunks).
+__host__ __device__ inline uint32_t chunk_splits(uint32_t entries) {
+    const uint32_t ns = (entries + kSplitMinEntries - 1) / kSplitMinEntries;
+    return ns < 1u ? 1u : ns > (uint32_t)kSplit ? (uint32_t)kSplit : ns;
+}
+
+__device__ __forceinline__ void compact_chunk_body_slots(uint64_t chunk, int split, const CompressArgs& a) {
+    constexpr int kTab = kTilesPerChunk * 32;          // table entries (32 blocks per tile at most)
+    constexpr uint64_t kOrig = 1ull << 63;             // source word flag: the block's origin outlier comes first
+    __shared__ uint32_t s_first[kTab];                 // [tile * bpt + block]: first place, chunk-relative
+    __shared__ uint64_t s_src[kTab];                   // slot index of the block's place 0 (place r: + r)
+    __shared__ uint32_t s_toff[kTilesPerChunk + 1], s_tfix[kTilesPerChunk];
+    __shared__ uint4 s_rec[kTilesPerChunk];
     const Geom& g = a.g;
-    const uint64_t ntiles = g.ntiles, nseg = g.nseg, nbx = g.nbx;
+    const uint32_t nseg = (uint32_t)g.nseg;  // (tile and block counts are below 2^32)
+    const uint64_t nbx = g.nbx;
     const uint32_t bpt = g.bpt;
     const uint64_t S = block_slot(g.nd, g.b);
     const bool bp = is_block_pad(a.pad_mode);
     const uint64_t t0 = chunk * kTilesPerChunk;
-    // a chunk with no entries at offset 0 is final as the walk left it
-    // (every block offset in-tile and zero): nothing to move or add
-    {
-        const uint4 ch = a.chunks[chunk];
-        if ((ch.x | ch.y | ch.z | ch.w) == 0u) return;
-    }
+    const int nt = (int)umin64(kTilesPerChunk, g.ntiles - t0);
+    const uint4 ch = a.chunks[chunk];  // {outliers, fixups, offset of outliers, offset of fixups}
+    const uint32_t E = ch.x;
+    const uint32_t ns = chunk_splits(E);
+    if (split > 0 && (uint32_t)split >= ns) return;
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (w == 0) {  // the chunk's tile offsets: chunk offset + exclusive scan of the tile totals
-        uint32_t bo = a.chunks[chunk].z, bf = a.chunks[chunk].w;
-        for (int i0 = 0; i0 < kTilesPerChunk; i0 += 32) {
-            const uint64_t t = t0 + i0 + l;
-            const uint4 r = t < ntiles ? a.tiles[t] : make_uint4(0, 0, 0, 0);
-            uint32_t io = r.y, iff = r.w;
+    // One round of loads: warp 0 the tile records, every thread four table
+    // entries' in-tile offsets, origin flags and (per-block padding) slot-0
+    // markers.  Entry i is block i % bpt of tile i / bpt, so a warp's lanes
+    // cover whole tiles (bpt divides 32); entries past the chunk's tiles are
+    // sentinels.
+    constexpr int kPer = kTab / 256;
+    const uint32_t nent = (uint32_t)nt * bpt;
+    uint4 r = make_uint4(0, 0, 0, 0);
+    if (w == 0 && l < nt) r = a.tiles[t0 + l];
+    uint32_t eo[kPer], fl[kPer], s0[kPer];
+    uint64_t bk[kPer];
+    bool has[kPer];
 #pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const uint32_t yo = __shfl_up_sync(VSZ_FULL, io, off);
-                const uint32_t yf = __shfl_up_sync(VSZ_FULL, iff, off);
-                if (l >= off) { io += yo; iff += yf; }
-            }
-            rec[i0 + l] = r;
-            toff_o[i0 + l] = bo + io - r.y;
-            toff_f[i0 + l] = bf + iff - r.w;
-            bo += __shfl_sync(VSZ_FULL, io, 31);
-            bf += __shfl_sync(VSZ_FULL, iff, 31);
+    for (int u = 0; u < kPer; ++u) {
+        const uint32_t i = (uint32_t)threadIdx.x + 256u * u;
+        const uint32_t j = i / bpt, k = i % bpt;
+        const uint32_t tt = (uint32_t)t0 + j, row = tt / nseg, sg = tt - row * nseg;
+        has[u] = i < nent && k < (uint32_t)umin64(bpt, nbx - (uint64_t)sg * bpt);
+        bk[u] = (uint64_t)row * nbx + (uint64_t)sg * bpt + k;
+        eo[u] = has[u] ? a.blk_in[bk[u]] : 0u;
+        fl[u] = (has[u] && a.oflag && a.oflag[bk[u]] != 0) ? 1u : 0u;
+        s0[u] = (bp && has[u] && a.slots[bk[u] * S].x != 0xffffffffu) ? 1u : 0u;
+    }
+    if (w == 0) {  // chunk-relative tile offsets: exclusive scan of the tile totals
+        uint32_t io = r.y, iff = r.w;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t yo = __shfl_up_sync(VSZ_FULL, io, off);
+            const uint32_t yf = __shfl_up_sync(VSZ_FULL, iff, off);
+            if (l >= off) { io += yo; iff += yf; }
         }
+        s_rec[l] = r;
+        s_toff[l] = io - r.y;
+        s_tfix[l] = iff - r.w;
+        if (l == 31) s_toff[32] = io;
+    }
+    __syncthreads();
+    // the table; split 0 writes the final offsets and places origin outliers
+    const uint32_t gmask = bpt >= 32 ? VSZ_FULL : (((1u << bpt) - 1u) << (l & ~(bpt - 1)));  // this lane's tile
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+        const uint32_t i = (uint32_t)threadIdx.x + 256u * u;
+        const uint32_t j = i / bpt;
+        const uint32_t fls = __ballot_sync(VSZ_FULL, fl[u] != 0u) & gmask & ((1u << l) - 1u);
+        uint32_t first = 0xffffffffu;
+        uint64_t src = 0;
+        if (i < nent) {
+            first = has[u] ? s_toff[j] + eo[u] + (uint32_t)__popc(fls) : s_toff[j + 1];
+            // place r of the block: its origin outlier (r = 0, flagged), else
+            // slot entry r - flag, counted from slot 1 or (slot-0 marker) 0
+            src = (bk[u] * S + (s0[u] ? 0u : 1u) - fl[u]) | (fl[u] ? kOrig : 0ull);
+            if (split == 0 && has[u] && VSZ_IN(bk[u], g.nb, 403)) {
+                const uint32_t fin = ch.z + first;
+                a.blk_off[bk[u]] = fin;
+                if (fl[u] && (uint64_t)fin < a.out_cap) {
+                    uint64_t idx, tile;
+                    block_origin(g, bk[u], &idx, &tile);
+                    a.out_idx[fin] = (uint32_t)idx;
+                    a.out_delta[fin] = a.origin[bk[u]];
+                }
+            }
+        }
+        s_first[i] = first;
+        s_src[i] = src;
     }
     __syncthreads();
 
-    const int nt = (int)umin64(kTilesPerChunk, ntiles - t0);
-    for (int j = w; j < nt; j += 8) {
-        const uint64_t tt = t0 + j;
-        const uint4 rr = rec[j];
-        const uint32_t to = toff_o[j], tf = toff_f[j];
-        const uint64_t s = tt % nseg;
-        const uint64_t fb = (tt / nseg) * nbx + s * bpt;
-        const uint32_t nblk = (uint32_t)umin64(bpt, nbx - s * bpt);
-        const bool has = (uint32_t)l < nblk;
-        const uint64_t blk = fb + (uint64_t)l;
-        const uint32_t flag = (has && a.oflag && a.oflag[blk] != 0) ? 1u : 0u;
-        const uint32_t fl = __ballot_sync(VSZ_FULL, flag != 0u);
-        const uint32_t staged = rr.y - (uint32_t)__popc(fl);
-        const uint32_t eo = has ? a.blk_off[blk] : staged;  // in-tile offset, without origin outliers
-        uint32_t nx = __shfl_down_sync(VSZ_FULL, eo, 1);
-        if ((uint32_t)l + 1 >= nblk) nx = staged;
-        const uint32_t cnt = has ? nx - eo : 0u;
-        const uint32_t fin = to + eo + (uint32_t)__popc(fl & ((1u << l) - 1u));  // the block's final offset
-        const bool fits = (uint64_t)to + rr.y <= a.out_cap;
-        if (has && VSZ_IN(blk, g.nb, 403)) {
-            a.blk_off[blk] = fin;
-            if (flag && fits) {
-                uint64_t idx, tile;
-                block_origin(g, blk, &idx, &tile);
-                a.out_idx[fin] = (uint32_t)idx;
-                a.out_delta[fin] = a.origin[blk];
+    // this CTA's share of the chunk's places; place q lies in the entry with
+    // the largest first place <= q (s_first[0] = 0, sentinels never count)
+    const uint32_t q0 = (uint32_t)((uint64_t)E * (uint32_t)split / ns);
+    const uint32_t q1 = (uint32_t)((uint64_t)E * ((uint32_t)split + 1) / ns);
+    for (uint32_t qb = q0; qb < q1; qb += blockDim.x * kMoveUnroll) {
+        uint2 e[kMoveUnroll];
+        uint32_t d[kMoveUnroll];
+        bool mv[kMoveUnroll];
+#pragma unroll
+        for (int u = 0; u < kMoveUnroll; ++u) {
+            const uint32_t q = qb + (uint32_t)u * blockDim.x + threadIdx.x;
+            uint32_t k = 0;
+#pragma unroll
+            for (uint32_t step = kTab / 2; step > 0; step >>= 1) k += s_first[k + step] <= q ? step : 0u;
+            const uint32_t rq = q - s_first[k];
+            const uint64_t sw = s_src[k];
+            const uint64_t src = (sw & ~kOrig) + rq;
+            d[u] = ch.z + q;
+            mv[u] = q < q1 && !((sw & kOrig) && rq == 0) && (uint64_t)d[u] < a.out_cap &&
+                    VSZ_IN(src, g.nb * S, 401);
+            if (mv[u]) e[u] = a.slots[src];
+        }
+#pragma unroll
+        for (int u = 0; u < kMoveUnroll; ++u) {
+            if (mv[u] && VSZ_IN((uint64_t)d[u], a.out_cap, 402)) {
+                a.out_idx[d[u]] = e[u].x;
+                a.out_delta[d[u]] = (int32_t)e[u].y;
             }
         }
-        if (fits && staged) {
-            // a per-block padding mode's slot 0: the origin outlier, or the marker
-            uint32_t start = 1;
-            if (bp && has && cnt) start = a.slots[blk * S].x != 0xffffffffu ? 0u : 1u;
-            // each block's slot to its place, four blocks at a time so that
-            // every lane has up to four loads in flight
-            const uint64_t sbase = (uint64_t)blk * S + start;  // the slot's first entry
-            const uint32_t dbase = fin + flag;                  // the block's first non-origin place
-            for (uint32_t kk0 = 0; kk0 < nblk; kk0 += 4) {
-                uint32_t c[4], d0[4], cmax = 0;
-                uint64_t sb[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int kk = (int)((kk0 + q) & 31u);
-                    c[q] = __shfl_sync(VSZ_FULL, cnt, kk);
-                    d0[q] = __shfl_sync(VSZ_FULL, dbase, kk);
-                    sb[q] = __shfl_sync(VSZ_FULL, sbase, kk);
-                    if (kk0 + q >= nblk) c[q] = 0;
-                    cmax = c[q] > cmax ? c[q] : cmax;
+    }
+
+    if (split == 0 && ch.y) {  // fixups: tile by tile, contiguous in staging and in the list
+        for (int j = w; j < nt; j += 8) {
+            const uint4 rr = s_rec[j];
+            const uint32_t tf = ch.w + s_tfix[j];
+            if (rr.w && (uint64_t)rr.z + rr.w <= a.fix_cap && (uint64_t)tf + rr.w <= a.fix_cap) {
+                for (uint32_t k = l; k < rr.w; k += 32) {
+                    const uint2 fe = a.stage_fix[rr.z + k];
+                    a.fix_idx[tf + k] = fe.x;
+                    a.fix_bits[tf + k] = fe.y;
                 }
-                for (uint32_t i = l; i < cmax; i += 32) {
-                    uint2 e[4];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        if (i < c[q] && VSZ_IN(sb[q] + i, g.nb * S, 401)) e[q] = a.slots[sb[q] + i];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        if (i < c[q] && VSZ_IN((uint64_t)d0[q] + i, a.out_cap, 402)) {
-                            a.out_idx[d0[q] + i] = e[q].x;
-                            a.out_delta[d0[q] + i] = (int32_t)e[q].y;
-                        }
-                    }
-                }
-            }
-        }
-        if (rr.w && (uint64_t)rr.z + rr.w <= a.fix_cap && (uint64_t)tf + rr.w <= a.fix_cap) {
-            for (uint32_t k = l; k < rr.w; k += 32) {
-                const uint2 e = a.stage_fix[rr.z + k];
-                a.fix_idx[tf + k] = e.x;
-                a.fix_bits[tf + k] = e.y;
             }
         }
     }

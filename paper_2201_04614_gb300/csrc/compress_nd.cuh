@@ -270,26 +270,12 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
     uint32_t seg_o = 0;             // outliers of this lane's block in its slot (first walk)
     bool ovf = false;               // the stash overflowed: count only, then walk again
     bool nofix = false;             // second walk of a tile without fixups: no guard checks
-    // where entries go: the final lists at their canonical place (tile
-    // chain), or the staging area that the compaction moves from
-    const bool chained = a.chained != 0;
+    // entries go to the staging area, which the compaction moves from
     auto put_out = [&](uint64_t pos, uint32_t idx, uint32_t d) {
-        if (pos >= a.out_cap) return;
-        if (chained) {
-            a.out_idx[pos] = idx;
-            a.out_delta[pos] = (int32_t)d;
-        } else {
-            a.stage_out[pos] = make_uint2(idx, d);
-        }
+        if (pos < a.out_cap) a.stage_out[pos] = make_uint2(idx, d);
     };
     auto put_fix = [&](uint64_t pos, uint32_t idx, uint32_t bits) {
-        if (pos >= a.fix_cap) return;
-        if (chained) {
-            a.fix_idx[pos] = idx;
-            a.fix_bits[pos] = bits;
-        } else {
-            a.stage_fix[pos] = make_uint2(idx, bits);
-        }
+        if (pos < a.fix_cap) a.stage_fix[pos] = make_uint2(idx, bits);
     };
     auto rare_rows = [&](uint32_t rows, uint32_t rows_f, int h, uint64_t boff, int j, int lz, bool b0, bool imode,
                          bool raw, bool emit) {
@@ -838,55 +824,9 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
         ef_g = __shfl_sync(VSZ_FULL, ef, src);
         const uint32_t tot_out = __shfl_sync(VSZ_FULL, io, 31);
         const uint32_t tot_fix = __shfl_sync(VSZ_FULL, iff, 31);
-        if (chained) {
-            // the field's entries before this tile, from the tile chain
-            uint64_t xo = 0, xf = 0;
-            if (!chain_lookback(reinterpret_cast<uint64_t*>(a.tiles), t, tot_out, tot_fix, a.chain_ns, lane, &xo,
-                                &xf) && lane == 0)
-                atomicMax(const_cast<uint32_t*>(&a.hdr->status), (unsigned)VSZ_ERR_TIMEOUT);
-            base_out = xo;
-            base_fix = xf;
-            if (lane == 0 && t + 1 == g.ntiles) chain_close(a, xo + tot_out, xf + tot_fix);
-            if (first && bexists && VSZ_IN(blk, g.nb + 1, 108)) a.blk_off[blk] = (uint32_t)(xo + eo);
-            if (slots && tot_out) {
-                // each block's slot to its place: entries from slot 1 on, or
-                // from slot 0 when a per-block padding put the block's
-                // origin outlier there; four blocks at a time, so that
-                // every lane has up to four loads in flight
-                constexpr int NBT = 32 / G;  // blocks of a tile
-                const uint32_t cb = (first && bexists) ? bo : 0u;
-                const uint32_t db = (uint32_t)(xo + eo);  // final offsets are 32-bit (blk_off)
-                const uint32_t kb = (uint32_t)blk * 2u + ((BP && corner_out) ? 0u : 1u);  // block, first slot
-#pragma unroll 1
-                for (int k0 = 0; k0 < NBT; k0 += 4) {
-                    uint32_t c[4], d0[4], cmax = 0;
-                    uint64_t s0[4];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int sl = ((k0 + q) % NBT) * G;
-                        c[q] = __shfl_sync(VSZ_FULL, cb, sl);
-                        d0[q] = __shfl_sync(VSZ_FULL, db, sl);
-                        const uint32_t kq = __shfl_sync(VSZ_FULL, kb, sl);
-                        s0[q] = (uint64_t)(kq >> 1) * C::SLOT + (kq & 1u);
-                        if (k0 + q >= NBT) c[q] = 0;
-                        cmax = c[q] > cmax ? c[q] : cmax;
-                    }
-                    for (uint32_t i = lane; i < cmax; i += 32) {
-                        uint2 e[4];
-#pragma unroll
-                        for (int q = 0; q < 4; ++q)
-                            if (i < c[q] && VSZ_IN(s0[q] + i, g.nb * C::SLOT, 111)) e[q] = slots[s0[q] + i];
-#pragma unroll
-                        for (int q = 0; q < 4; ++q)
-                            if (i < c[q]) put_out((uint64_t)d0[q] + i, e[q].x, e[q].y);
-                    }
-                }
-            }
-        } else if (first && bexists && VSZ_IN(blk, g.nb + 1, 108)) {
-            a.blk_off[blk] = eo;
-        }
+        if (first && bexists && VSZ_IN(blk, g.nb + 1, 108)) a.blk_in[blk] = eo;
 
-        if (!chained && (tot_out | tot_fix)) {
+        if (tot_out | tot_fix) {
             if (lane == 0) {
                 if (tot_out && !slots) base_out = atomicAdd(&a.wsh->stage_out, (unsigned long long)tot_out);
                 if (tot_fix) base_fix = atomicAdd(&a.wsh->stage_fix, (unsigned long long)tot_fix);
@@ -897,7 +837,7 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
             base_out = __shfl_sync(VSZ_FULL, base_out, 0);
             base_fix = __shfl_sync(VSZ_FULL, base_fix, 0);
         }
-        if (lane == 0 && !chained)
+        if (lane == 0)
             a.tiles[t] = make_uint4((uint32_t)base_out, tot_out, (uint32_t)base_fix, tot_fix);
         if (!(tot_out | tot_fix)) break;
         nofix = tot_fix == 0u;

@@ -39,6 +39,9 @@ constexpr uint64_t kItemElems = 1ull << 18;  // elements per statistics work ite
 constexpr int kMaxClasses = 28;               // tickets in the batch header, per sequence
 constexpr size_t kBatchHeader = 512;          // compression tickets, then reconstruction tickets
 constexpr size_t kReconTickets = 256;         // byte offset of the reconstruction tickets
+constexpr int kSplitCount = 60;               // header word: extra compaction items listed by the scan
+static_assert(kReconTickets / 8 + kMaxClasses <= kSplitCount && (kSplitCount + 1) * 8 <= kBatchHeader,
+              "batch header words");
 
 struct BatchField {
     CompressArgs a;     // the field's pointers, geometry and workspace
@@ -58,17 +61,14 @@ __device__ __forceinline__ int find_field(const uint64_t* __restrict__ prefix, i
     return lo;
 }
 
-// blockIdx.x: the field; blockIdx.y strides over its chunk sums and (a
-// chained field) its tile-chain status words; CTA (f, 0) sets the headers.
+// blockIdx.x: the field; blockIdx.y strides over its chunk sums; CTA (f, 0)
+// sets the headers.
 __global__ void __launch_bounds__(256) k_batch_begin(const BatchField* __restrict__ F,
                                                      unsigned long long* tickets) {
     const BatchField& b = F[blockIdx.x];
     const CompressArgs& a = b.a;
     const uint64_t i0 = (uint64_t)blockIdx.y * blockDim.x + threadIdx.x, stride = (uint64_t)gridDim.y * blockDim.x;
-    if (!a.chained)
-        for (uint64_t i = i0; i < a.g.nchunks; i += stride) a.chunks[i] = make_uint4(0, 0, 0, 0);
-    else
-        for (uint64_t i = i0; i < a.g.ntiles; i += stride) a.tiles[i] = make_uint4(0, 0, 0, 0);
+    for (uint64_t i = i0; i < a.g.nchunks; i += stride) a.chunks[i] = make_uint4(0, 0, 0, 0);
     if (blockIdx.y != 0) return;
     if (threadIdx.x == 0) {
         WsHeader* w = a.wsh;
@@ -94,6 +94,7 @@ __global__ void __launch_bounds__(256) k_batch_begin(const BatchField* __restric
         if (!b.rel) resolve_eb(h, b.eb, false, false, 0.0f, 0.0f);
     }
     if (blockIdx.x == 0 && threadIdx.x < kMaxClasses) tickets[threadIdx.x] = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) tickets[kSplitCount] = 0;
 }
 
 // Finite min/max of every relative-eb field; items of kItemElems elements.
@@ -200,21 +201,43 @@ __global__ void __launch_bounds__(256) k_batch_origin_fix(const BatchField* __re
     }
 }
 
-__global__ void __launch_bounds__(1024) k_batch_compact_scan(const BatchField* __restrict__ F) {
+// One CTA per field: the chunk offsets and totals, then (a block-slot
+// field) the extra compaction items of its dense chunks, {field, chunk *
+// kSplit + split} for splits 1.., appended to `list`.
+__global__ void __launch_bounds__(1024) k_batch_compact_scan(const BatchField* __restrict__ F, uint2* list,
+                                                             unsigned long long* count) {
     const CompressArgs& a = F[blockIdx.x].a;
-    if (a.chained && a.g.ntiles > 0) return;  // placed and closed by the tile chain
     compact_scan_body(a.chunks, a.g.nchunks, const_cast<vsz_header*>(a.hdr), a.blk_off, a.g.nb, a.out_cap,
                       a.fix_cap);
+    if (!a.slots || !list) return;
+    for (uint64_t c = threadIdx.x; c < a.g.nchunks; c += blockDim.x) {
+        const uint32_t ns = chunk_splits(a.chunks[c].x);
+        if (ns > 1) {
+            const unsigned long long base = atomicAdd(count, (unsigned long long)(ns - 1));
+            for (uint32_t sp = 1; sp < ns; ++sp)
+                list[base + sp - 1] = make_uint2(blockIdx.x, (uint32_t)(c * kSplit + sp));
+        }
+    }
 }
 
-__global__ void __launch_bounds__(256) k_batch_compact_move(const BatchField* __restrict__ F, int nf,
+// Items: first the extra splits the scan listed (the heavy ones), then
+// split 0 of every chunk of every field.
+__global__ void __launch_bounds__(256, 3) k_batch_compact_move(const BatchField* __restrict__ F, int nf,
                                                             const uint64_t* __restrict__ prefix,
-                                                            uint64_t nchunks) {
-    for (uint64_t item = blockIdx.x; item < nchunks; item += gridDim.x) {
-        const int f = find_field(prefix, nf, item);
-        const CompressArgs& a = F[f].a;
-        if (a.slots) compact_chunk_body_slots(item - prefix[f], a);
-        else compact_chunk_body(item - prefix[f], a);
+                                                            uint64_t nchunks, const uint2* __restrict__ list,
+                                                            const unsigned long long* __restrict__ count) {
+    const uint64_t nx = list ? *count : 0;
+    for (uint64_t item = blockIdx.x; item < nx + nchunks; item += gridDim.x) {
+        if (item < nx) {
+            const uint2 it = list[item];
+            compact_chunk_body_slots(it.y / kSplit, (int)(it.y % kSplit), F[it.x].a);
+        } else {
+            const uint64_t c = item - nx;
+            const int f = find_field(prefix, nf, c);
+            const CompressArgs& a = F[f].a;
+            if (a.slots) compact_chunk_body_slots(c - prefix[f], 0, a);
+            else compact_chunk_body(c - prefix[f], a);
+        }
         __syncthreads();
     }
 }
@@ -276,9 +299,10 @@ struct vsz_batch_st {
     BatchField* d_fields = nullptr;
     uint64_t* d_range_prefix = nullptr;
     uint64_t* d_chunk_prefix = nullptr;
+    uint2* d_split = nullptr;            // extra compaction items of dense chunks (filled by the scan)
+    uint64_t split_cap = 0;
     uint64_t range_items = 0, chunks = 0;
     unsigned begin_y = 1;                // CTAs per field of the begin kernel
-    bool scan = false;                   // some field is staged (or empty): the compaction scan runs
     unsigned long long* tickets = nullptr;  // in the caller's workspace
     bool use_graph = false;
     cudaGraphExec_t exec = nullptr;
@@ -342,6 +366,7 @@ static void free_batch(vsz_batch_st* b) {
     if (b->d_fields) cudaFree(b->d_fields);
     if (b->d_range_prefix) cudaFree(b->d_range_prefix);
     if (b->d_chunk_prefix) cudaFree(b->d_chunk_prefix);
+    if (b->d_split) cudaFree(b->d_split);
     delete b;
 }
 
@@ -502,15 +527,16 @@ static vsz_status launch_sequence(vsz_batch_st* b, cudaStream_t s, const ClassTi
         const vsz_status st = run_classes(b, 0, s, tm);
         if (st != VSZ_OK) return st;
     }
-    if (b->scan) {
+    {
         TraceScope ts("batch_compact_scan", s);
-        k_batch_compact_scan<<<b->n, 1024, 0, s>>>(b->d_fields);
+        k_batch_compact_scan<<<b->n, 1024, 0, s>>>(b->d_fields, b->d_split, b->tickets + kSplitCount);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
     }
     if (b->chunks) {
         TraceScope ts("batch_compact_move", s);
-        const int grid = grid_for((const void*)k_batch_compact_move, 256, 0, 1, b->chunks);
-        k_batch_compact_move<<<grid, 256, 0, s>>>(b->d_fields, b->n, b->d_chunk_prefix, b->chunks);
+        const int grid = grid_for((const void*)k_batch_compact_move, 256, 0, 1, b->chunks + b->split_cap);
+        k_batch_compact_move<<<grid, 256, 0, s>>>(b->d_fields, b->n, b->d_chunk_prefix, b->chunks, b->d_split,
+                                                  b->tickets + kSplitCount);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
     }
     return VSZ_OK;
@@ -583,15 +609,16 @@ vsz_status vsz_batch_create(const vsz_field_job* jobs, int njobs, void* d_ws, si
         bf.rel = j.params.eb_mode == VSZ_EB_REL;
         bf.gpad = is_global_pad(j.params.pad) ? 1 : 0;
         bf.epad = is_edge_pad(j.params.pad) ? 1 : 0;
-        if (g.nd >= 2) a.slots = a.stage_out;  // block-slot staging
-        a.chained = chained_field(j.params.pad) ? 1 : 0;
+        a.blk_in = a.blk_off;
+        if (g.nd >= 2) {  // block-slot staging
+            a.slots = a.stage_out;
+            a.blk_in = (uint32_t*)(fw + L.blkin);
+        }
         b->fields.push_back(bf);
         const uint64_t items = (g.n + kItemElems - 1) / kItemElems;
         rp.push_back(rp.back() + (bf.rel ? (items ? items : 1) : 0));
-        cp.push_back(cp.back() + (a.chained ? 0 : g.nchunks));  // chained fields need no compaction
-        const uint64_t zw = a.chained ? g.ntiles : g.nchunks;          // begin's zeroing
-        if (!a.chained || g.ntiles == 0) b->scan = true;
-        b->begin_y = (unsigned)umax64(b->begin_y, umin64(16, (zw + 4095) / 4096));
+        cp.push_back(cp.back() + g.nchunks);
+        b->begin_y = (unsigned)umax64(b->begin_y, umin64(16, (g.nchunks + 4095) / 4096));
         const ClassKey key = class_key(j, g);
         const int pk = std::get<2>(key);
         auto it = cls.find(key);
@@ -611,6 +638,9 @@ vsz_status vsz_batch_create(const vsz_field_job* jobs, int njobs, void* d_ws, si
     cudaError_t e = upload(&b->d_fields, b->fields);
     if (e == cudaSuccess) e = upload(&b->d_range_prefix, rp);
     if (e == cudaSuccess) e = upload(&b->d_chunk_prefix, cp);
+    for (const BatchField& bf : b->fields)
+        if (bf.a.slots) b->split_cap += bf.a.g.nchunks * (kSplit - 1);
+    if (e == cudaSuccess && b->split_cap) e = lib_malloc((void**)&b->d_split, sizeof(uint2) * b->split_cap);
     for (BatchClass& c : b->classes) {
         if (e != cudaSuccess) break;
         std::vector<CompressArgs> args;

@@ -10,14 +10,10 @@
 
 namespace vsz {
 
-// tiles / nzt: the tile chain's status words of a chained field (nzt
-// tiles, two words each), zeroed for this call; nzt = 0 otherwise.
-__global__ void k_begin(WsHeader* wsh, uint4* chunks, uint64_t nchunks, uint4* tiles, uint64_t nzt, vsz_header* hdr,
-                        double eb, int rel) {
+__global__ void k_begin(WsHeader* wsh, uint4* chunks, uint64_t nchunks, vsz_header* hdr, double eb, int rel) {
     pdl_prologue();
     const uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     for (uint64_t i = i0; i < nchunks; i += (uint64_t)gridDim.x * blockDim.x) chunks[i] = make_uint4(0, 0, 0, 0);
-    for (uint64_t i = i0; i < nzt; i += (uint64_t)gridDim.x * blockDim.x) tiles[i] = make_uint4(0, 0, 0, 0);
     if (i0 == 0) {
         wsh->stage_out = 0;
         wsh->stage_fix = 0;
@@ -108,7 +104,7 @@ __global__ void __launch_bounds__(1024) k_compact_scan(uint4* chunks, uint64_t n
 
 __global__ void __launch_bounds__(256) k_compact(const CompressArgs a) {
     pdl_prologue();
-    if (a.slots) compact_chunk_body_slots(blockIdx.x, a);
+    if (a.slots) compact_chunk_body_slots(blockIdx.x, (int)blockIdx.y, a);
     else compact_chunk_body(blockIdx.x, a);
 }
 
@@ -220,49 +216,13 @@ __global__ void __launch_bounds__(kHistThreads) k_histogram(const uint16_t* __re
     }
 }
 
-// The tile chain alone (vsz_debug_chain): warps take tiles by ticket, the
-// withheld tile publishes nothing, the others run the look-back with a
-// short limit.  ctl[0] counts timeouts, ctl[1] is the ticket.
-__global__ void __launch_bounds__(256) k_debug_chain(const uint32_t* __restrict__ agg_o,
-                                                     const uint32_t* __restrict__ agg_f, int ntiles, int withhold,
-                                                     uint32_t wait_ns, uint64_t* status, uint64_t* ex,
-                                                     unsigned int* ctl) {
-    const int lane = threadIdx.x & 31;
-    for (;;) {
-        unsigned int tk = 0;
-        if (lane == 0) tk = atomicAdd(&ctl[1], 1u);
-        const int t = (int)__shfl_sync(VSZ_FULL, tk, 0);
-        if (t >= ntiles) break;
-        if (t == withhold) continue;
-        uint64_t xo = 0, xf = 0;
-        const bool ok = chain_lookback(status, (uint64_t)t, agg_o[t], agg_f[t], wait_ns, lane, &xo, &xf);
-        if (lane == 0) {
-            ex[2 * t] = xo;
-            ex[2 * t + 1] = xf;
-            if (!ok) atomicAdd(&ctl[0], 1u);
-        }
-    }
-}
-
 // ---------------------------------------------------------------------------
 // Launch helpers used by api.cu.
 
-cudaError_t launch_debug_chain(const uint32_t* agg_o, const uint32_t* agg_f, int ntiles, int withhold,
-                               uint32_t wait_ns, uint64_t* status, uint64_t* ex, unsigned int* ctl, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(status, 0, sizeof(uint64_t) * 2 * (size_t)ntiles, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ctl, 0, 2 * sizeof(unsigned int), s);
-    if (e != cudaSuccess) return e;
-    // every warp resident at once: at most 8 CTAs of 8 warps
-    const int warps = ntiles < 64 ? ntiles : 64;
-    const int ctas = (warps + 7) / 8;
-    k_debug_chain<<<ctas, 256, 0, s>>>(agg_o, agg_f, ntiles, withhold, wait_ns, status, ex, ctl);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_begin(WsHeader* wsh, uint4* chunks, uint64_t nchunks, uint4* tiles, uint64_t nzt, vsz_header* hdr,
-                         double eb, bool rel, cudaStream_t s) {
-    const int grid = (int)umin64(64, (umax64(nchunks, nzt) + 255) / 256 + 1);
-    return launch_pdl(k_begin, grid, 256, 0, s, wsh, chunks, nchunks, tiles, nzt, hdr, eb, rel ? 1 : 0);
+cudaError_t launch_begin(WsHeader* wsh, uint4* chunks, uint64_t nchunks, vsz_header* hdr, double eb, bool rel,
+                         cudaStream_t s) {
+    const int grid = (int)umin64(64, (nchunks + 255) / 256 + 1);
+    return launch_pdl(k_begin, grid, 256, 0, s, wsh, chunks, nchunks, hdr, eb, rel ? 1 : 0);
 }
 
 cudaError_t launch_range(const float* x, uint64_t n, WsHeader* wsh, vsz_header* hdr, double eb, bool vec,
@@ -278,7 +238,9 @@ cudaError_t launch_compact_scan(const Geom& g, uint4* chunks, vsz_header* hdr, u
 
 cudaError_t launch_compact_move(const CompressArgs& a, cudaStream_t s) {
     if (a.g.nchunks == 0) return cudaSuccess;
-    return launch_pdl(k_compact, (unsigned)a.g.nchunks, 256, 0, s, a);
+    // block slots: kSplit CTAs per chunk (blockIdx.y), those past the
+    // chunk's share return at once
+    return launch_pdl(k_compact, dim3((unsigned)a.g.nchunks, a.slots ? kSplit : 1), 256, 0, s, a);
 }
 
 cudaError_t launch_origin_fix(const CompressArgs& a, cudaStream_t s) {

@@ -335,24 +335,7 @@ __device__ __forceinline__ void compress_1d_tile(const CompressArgs& a, uint64_t
         if (lane == 0) global_stats_add(a, gmin, gmax, gs);
     }
     unsigned long long base_out = 0, base_fix = 0;
-    const bool chained = a.chained != 0;
-    if (chained) {
-        // the field's entries before this tile, from the tile chain; the
-        // walk wrote in-tile block offsets, which now move by base_out
-        uint64_t xo = 0, xf = 0;
-        if (!chain_lookback(reinterpret_cast<uint64_t*>(a.tiles), t, run_out, run_fix, a.chain_ns, lane, &xo, &xf) &&
-            lane == 0)
-            atomicMax(const_cast<uint32_t*>(&a.hdr->status), (unsigned)VSZ_ERR_TIMEOUT);
-        base_out = xo;
-        base_fix = xf;
-        if (lane == 0 && t + 1 == a.g.ntiles) chain_close(a, xo + run_out, xf + run_fix);
-        if (xo) {
-            __syncwarp();
-            const uint64_t b0 = start / B, b1 = umin64(a.g.nb, (start + kChunk1D + B - 1) / B);
-            for (uint64_t b = b0 + lane; b < b1; b += 32)
-                if (VSZ_IN(b, a.g.nb, 303)) a.blk_off[b] += (uint32_t)xo;
-        }
-    } else if (run_out | run_fix) {
+    if (run_out | run_fix) {
         if (lane == 0) {
             if (run_out) base_out = atomicAdd(&a.wsh->stage_out, (unsigned long long)run_out);
             if (run_fix) base_fix = atomicAdd(&a.wsh->stage_fix, (unsigned long long)run_fix);
@@ -363,25 +346,13 @@ __device__ __forceinline__ void compress_1d_tile(const CompressArgs& a, uint64_t
         base_out = __shfl_sync(VSZ_FULL, base_out, 0);
         base_fix = __shfl_sync(VSZ_FULL, base_fix, 0);
     }
-    if (lane == 0 && !chained) a.tiles[t] = make_uint4((uint32_t)base_out, run_out, (uint32_t)base_fix, run_fix);
-    // where entries go: the final lists (tile chain) or the staging area
+    if (lane == 0) a.tiles[t] = make_uint4((uint32_t)base_out, run_out, (uint32_t)base_fix, run_fix);
+    // entries go to the staging area, which the compaction moves from
     auto put_out = [&](uint64_t pos, uint2 e) {
-        if (pos >= a.out_cap) return;
-        if (chained) {
-            a.out_idx[pos] = e.x;
-            a.out_delta[pos] = (int32_t)e.y;
-        } else {
-            a.stage_out[pos] = e;
-        }
+        if (pos < a.out_cap) a.stage_out[pos] = e;
     };
     auto put_fix = [&](uint64_t pos, uint2 e) {
-        if (pos >= a.fix_cap) return;
-        if (chained) {
-            a.fix_idx[pos] = e.x;
-            a.fix_bits[pos] = e.y;
-        } else {
-            a.stage_fix[pos] = e;
-        }
+        if (pos < a.fix_cap) a.stage_fix[pos] = e;
     };
 
     if (!slow && nst <= (uint32_t)kStash1 && nfst <= (uint32_t)kStash1F) {

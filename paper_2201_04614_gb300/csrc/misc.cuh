@@ -4,8 +4,8 @@
 
 namespace vsz {
 
-cudaError_t launch_begin(WsHeader* wsh, uint4* chunks, uint64_t nchunks, uint4* tiles, uint64_t nzt, vsz_header* hdr,
-                         double eb, bool rel, cudaStream_t s);
+cudaError_t launch_begin(WsHeader* wsh, uint4* chunks, uint64_t nchunks, vsz_header* hdr, double eb, bool rel,
+                         cudaStream_t s);
 cudaError_t launch_range(const float* x, uint64_t n, WsHeader* wsh, vsz_header* hdr, double eb, bool vec,
                          cudaStream_t s);
 cudaError_t launch_compact_scan(const Geom& g, uint4* chunks, vsz_header* hdr, uint32_t* blk_off,
@@ -18,7 +18,5 @@ cudaError_t launch_histogram(const uint16_t* codes, uint64_t n, uint32_t* hist, 
 // cudaMalloc of the library's own tables, with the failure injection of
 // vsz_debug_fail_alloc (api.cu)
 cudaError_t lib_malloc(void** p, size_t bytes);
-cudaError_t launch_debug_chain(const uint32_t* agg_o, const uint32_t* agg_f, int ntiles, int withhold,
-                               uint32_t wait_ns, uint64_t* status, uint64_t* ex, unsigned int* ctl, cudaStream_t s);
 
 }  // namespace vsz
