@@ -71,6 +71,9 @@ def parse_args(argv=None):
                     help="only a reduced mixed stream (4 of its 1800x3600 fields, 2 of its 100x500x500 fields and "
                          "the first 20M values of its 1D field), the tuner's classes, eb --eb: a small case for "
                          "ncu captures of the batch kernels")
+    ap.add_argument("--field-profile", action="store_true",
+                    help="only the one-field step (--size, --block, --field-eb, --pad): a case for ncu captures of "
+                         "the one-field kernels")
     return ap.parse_args(argv)
 
 
@@ -956,7 +959,10 @@ def run_gpu(a):
     stream.synchronize()
     t0 = time.time()
     with torch.cuda.stream(stream):
+        # ncu --nvtx --nvtx-include "vsz_headline/" selects the timed launches
+        torch.cuda.nvtx.range_push("vsz_headline")
         ms_step = timed_loop(lambda: bt.submit(stream), stream)
+        torch.cuda.nvtx.range_pop()
     t1 = time.time()
     clocks = sampler.summary(t0, t1) if sampler else None
     value = job_gbps(world, n_total, ms_step)
@@ -1139,6 +1145,44 @@ def run_batch_profile(a):
     bt.close()
 
 
+def run_field_profile(a):
+    """The one-field step alone on the NYX-like field of edge --size (block
+    --block, rel eb --field-eb, padding --pad): `warmup` steps, then `steps`
+    compressions and `steps` reconstructions inside the NVTX range
+    "vsz_steps".  Prints one JSON line with the compression and
+    reconstruction GB/s and the outlier counts."""
+    import torch
+    import paper_2201_04614_gb300 as vsz
+    import synth
+    x3 = synth.lognormal3d(a.size, seed=rank_field_seed(0))
+    n = x3.size
+    xd = torch.from_numpy(x3.reshape(-1)).cuda()
+    p = vsz.Params.make(x3.shape, a.block, a.field_eb, "rel", R, a.pad)
+    f = vsz.Field(p, out_cap=max(1 << 20, n // 4), fix_cap=max(1 << 16, n // 64))
+    xh = torch.empty(n, dtype=torch.float32, device="cuda")
+    for _ in range(a.warmup):
+        f.compress(xd)
+        f.reconstruct(out=xh)
+    torch.cuda.synchronize()
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    torch.cuda.nvtx.range_push("vsz_steps")
+    e0.record()
+    for _ in range(a.steps):
+        f.compress(xd)
+    e1.record()
+    for _ in range(a.steps):
+        f.reconstruct(out=xh)
+    e2.record()
+    torch.cuda.nvtx.range_pop()
+    e2.synchronize()
+    h = f.header()
+    ms_c, ms_r = e0.elapsed_time(e1) / a.steps, e1.elapsed_time(e2) / a.steps
+    print(json.dumps({"field_profile": f"{a.size}^3 NYX-like, block {a.block}, rel eb {a.field_eb:g}, {a.pad}",
+                      "values": n, "steps": a.steps, "compress_ms": ms_c, "reconstruct_ms": ms_r,
+                      "compress_GBps": n * 4 / ms_c / 1e6, "reconstruct_GBps": n * 4 / ms_r / 1e6,
+                      "n_out": int(h["n_out"]), "n_fix": int(h["n_fix"]), "status": int(h["status"])}), flush=True)
+
+
 def _class_values(fields) -> dict:
     out = {}
     for f in fields:
@@ -1151,6 +1195,9 @@ def main():
     a = parse_args()
     if a.batch_profile:
         run_batch_profile(a)
+        return
+    if a.field_profile:
+        run_field_profile(a)
         return
     if a.impl == "reference":
         run_reference(a)

@@ -195,6 +195,24 @@ __device__ __forceinline__ int32_t edge_origin_pred(const int32_t* __restrict__ 
     }
     return (int32_t)acc;
 }
+// The same prediction from the scalars in registers (p2 unused below 3D,
+// p1 in 1D): the subsets S of {0, .., nd-1} unrolled, no indexed array.
+__device__ __forceinline__ int32_t edge_origin_pred_r(int32_t p0, int32_t p1, int32_t p2, int nd) {
+    uint32_t acc = 0;
+#pragma unroll
+    for (unsigned S = 1; S < 8u; ++S) {
+        if (S < (1u << nd)) {
+            long long sum = 0;
+            int m = 0;
+            if (S & 1u) { sum += p0; ++m; }
+            if (S & 2u) { sum += p1; ++m; }
+            if (S & 4u) { sum += p2; ++m; }
+            const uint32_t v = (uint32_t)rounded_mean(sum, m);
+            acc = (__popc(S) & 1) ? acc + v : acc - v;
+        }
+    }
+    return (int32_t)acc;
+}
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;

@@ -206,22 +206,27 @@ __device__ __forceinline__ void compact_chunk_body(uint64_t chunk, const Compres
 // Compaction, part 2, with block-slot staging (2D/3D).  Outliers cluster
 // where the field is rough, so one chunk can hold most of a field's
 // entries: a chunk is served by up to kSplit CTAs (split 0..kSplit-1), each
-// moving an equal share of the chunk's entries, and a CTA whose share is
-// empty returns at once.  Every CTA of a chunk builds the same table in
-// shared memory: each block's first place relative to the chunk (tile
-// offset + the block's in-tile offset from the walk + the origin outliers
-// of the tile's earlier blocks), non-decreasing over the chunk's blocks in
-// order (the places of a tile's missing blocks repeat its end).  Place q of
-// the chunk then lies in the block whose first place is the largest one
-// <= q (a binary search over the table); it is that block's entry q - first,
-// which is its origin outlier (global or edge padding: a block's first
-// entry, placed by split 0) or the slot entry after it, counting from slot 1,
-// or from slot 0 when a per-block padding mode put the block's origin there.
-// Split 0 also writes the blocks' final offsets (blk_off) and moves the
-// fixups (contiguous per tile in staging and in the list).
-constexpr int kSplit = 8;                 // CTAs per chunk at most
-constexpr uint32_t kSplitMinEntries = 2048;  // entries a CTA moves at least before the chunk is split further
-constexpr int kMoveUnroll = 8;            // entries in flight per thread
+// moving an equal share of the chunk's places, and a CTA whose share is
+// empty returns at once.  A CTA owns the chunk's tiles whose first place
+// falls in its share (the last split also those starting at the chunk's
+// end): it writes their blocks' final offsets (blk_off) and places their
+// origin outliers (global or edge padding: a block's first entry).  It
+// builds in shared memory a table of the blocks that hold entries, for the
+// tiles it owns or whose places meet its share, in order: each one's first
+// place relative to the chunk (tile offset + the block's in-tile offset
+// from the walk + the origin outliers of the tile's earlier blocks) and the
+// slot index of that place.  A block's places are its origin outlier, if
+// any, then its slot entries, from slot 1 on, or from slot 0 when a
+// per-block padding mode put the block's origin there.  A warp moves a
+// contiguous run of the share, 32 places at a time: with k0 the block
+// holding the window's first place qs, lane j reads the first place of
+// block k0+1+j, and since first places strictly increase, the OR over the
+// lanes of 1 << (first - qs) (for those inside the window) marks where
+// blocks start; place qs+i is in block k0 + the marks at 1..i.  Split 0
+// moves the fixups (contiguous per tile in staging and in the list).
+constexpr int kSplit = 8;                    // CTAs per chunk at most
+constexpr uint32_t kSplitMinEntries = 4096;  // entries a CTA moves at least before the chunk is split further
+constexpr int kMoveWindows = 8;              // 32-place windows a warp maps before it moves them
 
 // Splits a chunk of `entries` outliers needs (the per-field launch gives
 // every chunk kSplit CTAs; a batch lists the extra ones of its dense chunks).
@@ -231,16 +236,16 @@ __host__ __device__ inline uint32_t chunk_splits(uint32_t entries) {
 }
 
 __device__ __forceinline__ void compact_chunk_body_slots(uint64_t chunk, int split, const CompressArgs& a) {
-    constexpr int kTab = kTilesPerChunk * 32;          // table entries (32 blocks per tile at most)
+    constexpr int kTab = kTilesPerChunk * 32;          // blocks of a chunk at most (32 per tile)
     constexpr uint64_t kOrig = 1ull << 63;             // source word flag: the block's origin outlier comes first
-    __shared__ uint32_t s_first[kTab];                 // [tile * bpt + block]: first place, chunk-relative
-    __shared__ uint64_t s_src[kTab];                   // slot index of the block's place 0 (place r: + r)
-    __shared__ uint32_t s_toff[kTilesPerChunk + 1], s_tfix[kTilesPerChunk];
+    __shared__ uint32_t s_first[kTab + 32];            // blocks with entries: first place (then sentinels)
+    __shared__ uint64_t s_src[kTab];                   // ... slot index of place 0 (place r: + r)
+    __shared__ uint32_t s_toff[kTilesPerChunk + 1], s_tfix[kTilesPerChunk], s_nblk[kTilesPerChunk];
+    __shared__ uint64_t s_fb[kTilesPerChunk];          // first block of each tile
     __shared__ uint4 s_rec[kTilesPerChunk];
+    __shared__ uint32_t s_wtot[kTab / 32];             // blocks with entries per warp and round
     const Geom& g = a.g;
-    const uint32_t nseg = (uint32_t)g.nseg;  // (tile and block counts are below 2^32)
-    const uint64_t nbx = g.nbx;
-    const uint32_t bpt = g.bpt;
+    const uint32_t bpt = g.bpt, lb = (uint32_t)(__ffs(bpt) - 1);  // blocks per tile: a power of two
     const uint64_t S = block_slot(g.nd, g.b);
     const bool bp = is_block_pad(a.pad_mode);
     const uint64_t t0 = chunk * kTilesPerChunk;
@@ -250,30 +255,8 @@ __device__ __forceinline__ void compact_chunk_body_slots(uint64_t chunk, int spl
     const uint32_t ns = chunk_splits(E);
     if (split > 0 && (uint32_t)split >= ns) return;
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    // One round of loads: warp 0 the tile records, every thread four table
-    // entries' in-tile offsets, origin flags and (per-block padding) slot-0
-    // markers.  Entry i is block i % bpt of tile i / bpt, so a warp's lanes
-    // cover whole tiles (bpt divides 32); entries past the chunk's tiles are
-    // sentinels.
-    constexpr int kPer = kTab / 256;
-    const uint32_t nent = (uint32_t)nt * bpt;
-    uint4 r = make_uint4(0, 0, 0, 0);
-    if (w == 0 && l < nt) r = a.tiles[t0 + l];
-    uint32_t eo[kPer], fl[kPer], s0[kPer];
-    uint64_t bk[kPer];
-    bool has[kPer];
-#pragma unroll
-    for (int u = 0; u < kPer; ++u) {
-        const uint32_t i = (uint32_t)threadIdx.x + 256u * u;
-        const uint32_t j = i / bpt, k = i % bpt;
-        const uint32_t tt = (uint32_t)t0 + j, row = tt / nseg, sg = tt - row * nseg;
-        has[u] = i < nent && k < (uint32_t)umin64(bpt, nbx - (uint64_t)sg * bpt);
-        bk[u] = (uint64_t)row * nbx + (uint64_t)sg * bpt + k;
-        eo[u] = has[u] ? a.blk_in[bk[u]] : 0u;
-        fl[u] = (has[u] && a.oflag && a.oflag[bk[u]] != 0) ? 1u : 0u;
-        s0[u] = (bp && has[u] && a.slots[bk[u] * S].x != 0xffffffffu) ? 1u : 0u;
-    }
-    if (w == 0) {  // chunk-relative tile offsets: exclusive scan of the tile totals
+    if (w == 0) {  // tile records, chunk-relative tile offsets, tile geometry
+        const uint4 r = l < nt ? a.tiles[t0 + l] : make_uint4(0, 0, 0, 0);
         uint32_t io = r.y, iff = r.w;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
@@ -285,65 +268,128 @@ __device__ __forceinline__ void compact_chunk_body_slots(uint64_t chunk, int spl
         s_toff[l] = io - r.y;
         s_tfix[l] = iff - r.w;
         if (l == 31) s_toff[32] = io;
+        const uint64_t tt = t0 + (uint64_t)l;
+        const uint64_t row = tt / g.nseg, sg = tt - row * g.nseg;
+        s_fb[l] = row * g.nbx + sg * bpt;
+        s_nblk[l] = l < nt ? (uint32_t)umin64(bpt, g.nbx - sg * bpt) : 0u;
     }
     __syncthreads();
-    // the table; split 0 writes the final offsets and places origin outliers
-    const uint32_t gmask = bpt >= 32 ? VSZ_FULL : (((1u << bpt) - 1u) << (l & ~(bpt - 1)));  // this lane's tile
+    // this CTA's share of places, the tiles it owns and the tiles it needs
+    const uint32_t q0 = (uint32_t)((uint64_t)E * (uint32_t)split / ns);
+    const uint32_t q1 = (uint32_t)((uint64_t)E * ((uint32_t)split + 1) / ns);
+    const bool lastsplit = (uint32_t)split + 1 == ns;
+    uint32_t owned, needed;
+    {
+        const uint32_t tj = s_toff[l], tj1 = s_toff[l + 1];
+        const bool valid = l < nt;
+        const bool own = valid && tj >= q0 && (tj < q1 || lastsplit);
+        const bool meets = valid && tj < q1 && tj1 > q0;
+        owned = __ballot_sync(VSZ_FULL, own);
+        needed = owned | __ballot_sync(VSZ_FULL, meets);
+    }
+    const uint32_t ja = needed ? (uint32_t)(__ffs(needed) - 1) : 0u;
+    const uint32_t jb = needed ? (uint32_t)(31 - __clz(needed)) : 0u;
+    const uint32_t ibase = ja << lb, ntab = needed ? (jb - ja + 1u) << lb : 0u;
+    // the table: four entries per thread at most, one round of loads; a
+    // warp's lanes cover whole tiles (bpt divides 32)
+    constexpr int kPer = kTab / 256;
+    const uint32_t tmask = bpt >= 32 ? VSZ_FULL : (((1u << bpt) - 1u) << (l & ~(bpt - 1)));  // this lane's tile
+    const uint32_t lt = (1u << l) - 1u;
+    uint32_t eo[kPer], fl[kPer], s0[kPer];
+    uint64_t bk[kPer];
+    bool has[kPer];
 #pragma unroll
     for (int u = 0; u < kPer; ++u) {
         const uint32_t i = (uint32_t)threadIdx.x + 256u * u;
-        const uint32_t j = i / bpt;
-        const uint32_t fls = __ballot_sync(VSZ_FULL, fl[u] != 0u) & gmask & ((1u << l) - 1u);
-        uint32_t first = 0xffffffffu;
-        uint64_t src = 0;
-        if (i < nent) {
-            first = has[u] ? s_toff[j] + eo[u] + (uint32_t)__popc(fls) : s_toff[j + 1];
-            // place r of the block: its origin outlier (r = 0, flagged), else
-            // slot entry r - flag, counted from slot 1 or (slot-0 marker) 0
-            src = (bk[u] * S + (s0[u] ? 0u : 1u) - fl[u]) | (fl[u] ? kOrig : 0ull);
-            if (split == 0 && has[u] && VSZ_IN(bk[u], g.nb, 403)) {
-                const uint32_t fin = ch.z + first;
-                a.blk_off[bk[u]] = fin;
-                if (fl[u] && (uint64_t)fin < a.out_cap) {
-                    uint64_t idx, tile;
-                    block_origin(g, bk[u], &idx, &tile);
-                    a.out_idx[fin] = (uint32_t)idx;
-                    a.out_delta[fin] = a.origin[bk[u]];
-                }
+        const uint32_t j = (ibase + i) >> lb, k = (ibase + i) & (bpt - 1u);
+        has[u] = i < ntab && k < s_nblk[j < 32u ? j : 0u];
+        bk[u] = s_fb[j < 32u ? j : 0u] + k;
+        eo[u] = has[u] ? a.blk_in[bk[u]] : 0u;
+        fl[u] = (has[u] && a.oflag && a.oflag[bk[u]] != 0) ? 1u : 0u;
+        s0[u] = (bp && has[u] && a.slots[bk[u] * S].x != 0xffffffffu) ? 1u : 0u;
+    }
+    uint32_t first[kPer], keep[kPer];
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+        const uint32_t i = (uint32_t)threadIdx.x + 256u * u;
+        const uint32_t j = i < ntab ? (ibase + i) >> lb : 0u;
+        const uint32_t fls = __ballot_sync(VSZ_FULL, fl[u] != 0u) & tmask & lt;
+        first[u] = has[u] ? s_toff[j] + eo[u] + (uint32_t)__popc(fls) : s_toff[j + 1];
+        uint32_t nxt = __shfl_down_sync(VSZ_FULL, first[u], 1);
+        if ((i & (bpt - 1u)) == bpt - 1u) nxt = s_toff[j + 1];  // the tile's last block: up to the tile's end
+        keep[u] = (has[u] && nxt > first[u]) ? 1u : 0u;
+        if (has[u] && ((owned >> j) & 1u) && VSZ_IN(bk[u], g.nb, 403)) {
+            const uint32_t fin = ch.z + first[u];
+            a.blk_off[bk[u]] = fin;
+            if (fl[u] && (uint64_t)fin < a.out_cap) {
+                uint64_t idx, tile;
+                block_origin(g, bk[u], &idx, &tile);
+                a.out_idx[fin] = (uint32_t)idx;
+                a.out_delta[fin] = a.origin[bk[u]];
             }
         }
-        s_first[i] = first;
-        s_src[i] = src;
+        const uint32_t kb = __ballot_sync(VSZ_FULL, keep[u] != 0u);
+        if (l == 0) s_wtot[u * 8 + w] = (uint32_t)__popc(kb);
+        keep[u] = keep[u] ? (uint32_t)__popc(kb & lt) + 1u : 0u;  // rank among the warp's kept, plus one
     }
     __syncthreads();
-
-    // this CTA's share of the chunk's places; place q lies in the entry with
-    // the largest first place <= q (s_first[0] = 0, sentinels never count)
-    const uint32_t q0 = (uint32_t)((uint64_t)E * (uint32_t)split / ns);
-    const uint32_t q1 = (uint32_t)((uint64_t)E * ((uint32_t)split + 1) / ns);
-    for (uint32_t qb = q0; qb < q1; qb += blockDim.x * kMoveUnroll) {
-        uint2 e[kMoveUnroll];
-        uint32_t d[kMoveUnroll];
-        bool mv[kMoveUnroll];
+    uint32_t nkeep = 0, before[kPer];  // kept blocks in all, before each round of this warp
 #pragma unroll
-        for (int u = 0; u < kMoveUnroll; ++u) {
-            const uint32_t q = qb + (uint32_t)u * blockDim.x + threadIdx.x;
-            uint32_t k = 0;
+    for (int q = 0; q < kTab / 32; ++q) {
+        const uint32_t v = s_wtot[q];
 #pragma unroll
-            for (uint32_t step = kTab / 2; step > 0; step >>= 1) k += s_first[k + step] <= q ? step : 0u;
-            const uint32_t rq = q - s_first[k];
-            const uint64_t sw = s_src[k];
-            const uint64_t src = (sw & ~kOrig) + rq;
-            d[u] = ch.z + q;
-            mv[u] = q < q1 && !((sw & kOrig) && rq == 0) && (uint64_t)d[u] < a.out_cap &&
-                    VSZ_IN(src, g.nb * S, 401);
-            if (mv[u]) e[u] = a.slots[src];
+        for (int u = 0; u < kPer; ++u)
+            if (q == u * 8) before[u] = nkeep;
+        nkeep += v;
+    }
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+        uint32_t c = before[u];
+        for (int q = u * 8; q < u * 8 + w; ++q) c += s_wtot[q];
+        if (keep[u]) {
+            c += keep[u] - 1u;
+            s_first[c] = first[u];
+            s_src[c] = (bk[u] * S + (s0[u] ? 0u : 1u) - fl[u]) | (fl[u] ? kOrig : 0ull);
         }
+    }
+    if (threadIdx.x < 32) s_first[nkeep + threadIdx.x] = 0xffffffffu;  // sentinels past the last block
+    __syncthreads();
+
+    // the moves: a contiguous run of the share per warp, whole windows
+    const uint32_t per = ((q1 - q0 + 8 * 32 - 1) / (8 * 32)) * 32;
+    const uint32_t wq0 = q0 + (uint32_t)w * per, wq1 = min(q1, wq0 + per);
+    if (wq0 < wq1 && nkeep > 0) {
+        uint32_t k0 = 0;  // the kept block holding place wq0: the last first place <= wq0
 #pragma unroll
-        for (int u = 0; u < kMoveUnroll; ++u) {
-            if (mv[u] && VSZ_IN((uint64_t)d[u], a.out_cap, 402)) {
-                a.out_idx[d[u]] = e[u].x;
-                a.out_delta[d[u]] = (int32_t)e[u].y;
+        for (uint32_t step = kTab / 2; step > 0; step >>= 1)
+            if (k0 + step < nkeep && s_first[k0 + step] <= wq0) k0 += step;
+        const uint32_t upto = (l == 31) ? VSZ_FULL : ((2u << l) - 1u);  // marks at 1..l
+        for (uint32_t qs = wq0; qs < wq1; qs += 32u * kMoveWindows) {
+            uint2 e[kMoveWindows];
+            uint32_t d[kMoveWindows];
+            bool mv[kMoveWindows];
+#pragma unroll
+            for (int m = 0; m < kMoveWindows; ++m) {
+                const uint32_t ws = qs + 32u * m;                 // this window's first place
+                const uint32_t dj = s_first[k0 + 1 + l] - ws;     // where block k0+1+l starts, from ws
+                const uint32_t marks = __reduce_or_sync(VSZ_FULL, dj < 32u ? (1u << dj) : 0u);
+                const uint32_t kq = k0 + (uint32_t)__popc(marks & upto);
+                k0 += (uint32_t)__popc(__ballot_sync(VSZ_FULL, dj <= 32u));  // the next window's first block
+                const uint32_t q = ws + (uint32_t)l;
+                const uint32_t rq = q - s_first[kq];
+                const uint64_t sw = s_src[kq];
+                const uint64_t src = (sw & ~kOrig) + rq;
+                d[m] = ch.z + q;
+                mv[m] = q < wq1 && !((sw & kOrig) && rq == 0) && (uint64_t)d[m] < a.out_cap &&
+                        VSZ_IN(src, g.nb * S, 401);
+                if (mv[m]) e[m] = a.slots[src];
+            }
+#pragma unroll
+            for (int m = 0; m < kMoveWindows; ++m) {
+                if (mv[m] && VSZ_IN((uint64_t)d[m], a.out_cap, 402)) {
+                    a.out_idx[d[m]] = e[m].x;
+                    a.out_delta[d[m]] = (int32_t)e[m].y;
+                }
             }
         }
     }
@@ -366,10 +412,12 @@ __device__ __forceinline__ void compact_chunk_body_slots(uint64_t chunk, int spl
 // The origin pass of a global padding mode, for block `blk`: the residual
 // of the block origin q - P, its code, and whether it is an outlier (then
 // counted in its tile and chunk before the compaction).
-__device__ __forceinline__ void origin_fix_block(const CompressArgs& a, uint64_t blk, int32_t P) {
+// q0: the block origin's q, a.origin[blk] (loaded ahead by the caller, so
+// that a thread can have several blocks' loads in flight).
+__device__ __forceinline__ void origin_fix_block(const CompressArgs& a, uint64_t blk, int32_t q0, int32_t P) {
     uint64_t idx, tile;
     block_origin(a.g, blk, &idx, &tile);
-    const int32_t d = (int32_t)((uint32_t)a.origin[blk] - (uint32_t)P);
+    const int32_t d = (int32_t)((uint32_t)q0 - (uint32_t)P);
     const uint32_t c = code_of(d, a.R);
     a.codes[idx] = (uint16_t)c;
     const bool out = c == 0u;

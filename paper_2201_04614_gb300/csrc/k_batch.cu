@@ -175,29 +175,62 @@ __global__ void __launch_bounds__(256) k_batch_edge_stats(const BatchField* __re
 // Origin pass of every global- or edge-padding field: items are blocks.
 // Each warp takes 32 consecutive blocks: one search for the field of the
 // first, then a step forward for lanes past that field's end.
+// A warp takes kObWarp consecutive items (blocks of the class's global- or
+// edge-padding fields, in field order), eight per lane: the field, its
+// padding value and geometry once, then every lane's origin loads (and an
+// edge field's face scalars) in flight together.  A range that runs into
+// the next field goes item by item.
+constexpr int kObLane = 8;
+constexpr uint64_t kObWarp = 32 * kObLane;
+
 __global__ void __launch_bounds__(256) k_batch_origin_fix(const BatchField* __restrict__ F, int nf,
                                                           const uint64_t* __restrict__ prefix, uint64_t nitems) {
     const int lane = threadIdx.x & 31;
     const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
-    for (uint64_t w0 = ((uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; w0 < nitems;
-         w0 += nwarps * 32) {
+    for (uint64_t w0 = ((uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kObWarp; w0 < nitems;
+         w0 += nwarps * kObWarp) {
         int f = 0;
         if (lane == 0) f = find_field(prefix, nf, w0);
         f = __shfl_sync(VSZ_FULL, f, 0);
-        const uint64_t item = w0 + (uint64_t)lane;
-        if (item >= nitems) continue;
-        while (item >= prefix[f + 1]) ++f;
-        const CompressArgs& a = F[f].a;
-        const uint64_t blk = item - prefix[f];
-        const int nd = a.g.nd;
-        int32_t P;
-        if (F[f].epad) {
-            P = edge_origin_pred(a.pad + blk * (uint64_t)nd, nd);
-        } else {
-            P = global_pad_value(a);
-            if (blk == 0) const_cast<vsz_header*>(a.hdr)->pad_global = P;
+        const uint64_t fb = prefix[f], fe = prefix[f + 1];
+        if (w0 + kObWarp <= fe) {
+            const CompressArgs& a = F[f].a;
+            const bool ep = F[f].epad != 0;
+            const int nd = a.g.nd;
+            const int32_t Pg = ep ? 0 : global_pad_value(a);
+            int32_t q0[kObLane], sc[kObLane][3];
+#pragma unroll
+            for (int u = 0; u < kObLane; ++u) {
+                const uint64_t blk = w0 + (uint64_t)(u * 32 + lane) - fb;
+                q0[u] = a.origin[blk];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) sc[u][k] = (ep && k < nd) ? a.pad[blk * (uint64_t)nd + k] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < kObLane; ++u) {
+                const uint64_t blk = w0 + (uint64_t)(u * 32 + lane) - fb;
+                if (!ep && blk == 0) const_cast<vsz_header*>(a.hdr)->pad_global = Pg;
+                origin_fix_block(a, blk, q0[u], ep ? edge_origin_pred_r(sc[u][0], sc[u][1], sc[u][2], nd) : Pg);
+            }
+            continue;
         }
-        origin_fix_block(a, blk, P);
+        for (int u = 0; u < kObLane; ++u) {
+            const uint64_t item = w0 + (uint64_t)(u * 32 + lane);
+            if (item >= nitems) break;
+            int g = f;
+            while (item >= prefix[g + 1]) ++g;
+            const CompressArgs& a = F[g].a;
+            const uint64_t blk = item - prefix[g];
+            const int nd = a.g.nd;
+            int32_t P;
+            if (F[g].epad) {
+                P = edge_origin_pred(a.pad + blk * (uint64_t)nd, nd);
+            } else {
+                P = global_pad_value(a);
+                if (blk == 0) const_cast<vsz_header*>(a.hdr)->pad_global = P;
+            }
+            origin_fix_block(a, blk, a.origin[blk], P);
+        }
     }
 }
 
@@ -428,7 +461,7 @@ static cudaError_t launch_class_origins(vsz_batch_st* b, size_t c, cudaStream_t 
     }
     if (k.origin_items) {
         TraceScope ts("batch_origin_fix", s, k.nd, k.b);
-        const int grid = grid_for((const void*)k_batch_origin_fix, 256, 0, 256, k.origin_items);
+        const int grid = grid_for((const void*)k_batch_origin_fix, 256, 0, 8 * kObWarp, k.origin_items);
         k_batch_origin_fix<<<grid, 256, 0, s>>>(k.d_bfields, nf, k.d_ob_prefix, k.origin_items);
         return cudaGetLastError();
     }

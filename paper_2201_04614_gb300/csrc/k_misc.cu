@@ -110,12 +110,27 @@ __global__ void __launch_bounds__(256) k_compact(const CompressArgs a) {
 
 // Origin pass of a global padding mode (one field): every block origin's
 // residual q - P and its code, P from the field's header.
+// Four blocks per thread per round, their origin loads issued first.
+constexpr int kOriginUnroll = 4;
+
 __global__ void __launch_bounds__(256) k_origin_fix(const CompressArgs a) {
     pdl_prologue();
     const int32_t P = global_pad_value(a);
     if (blockIdx.x == 0 && threadIdx.x == 0) const_cast<vsz_header*>(a.hdr)->pad_global = P;
-    for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < a.g.nb; b += (uint64_t)gridDim.x * blockDim.x)
-        origin_fix_block(a, b, P);
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t b0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b0 < a.g.nb; b0 += kOriginUnroll * stride) {
+        int32_t q0[kOriginUnroll];
+#pragma unroll
+        for (int u = 0; u < kOriginUnroll; ++u) {
+            const uint64_t b = b0 + u * stride;
+            q0[u] = b < a.g.nb ? a.origin[b] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < kOriginUnroll; ++u) {
+            const uint64_t b = b0 + u * stride;
+            if (b < a.g.nb) origin_fix_block(a, b, q0[u], P);
+        }
+    }
 }
 
 __global__ void __launch_bounds__(256) k_edge_stats(const CompressArgs a) {
@@ -131,8 +146,23 @@ __global__ void __launch_bounds__(256) k_edge_stats(const CompressArgs a) {
 __global__ void __launch_bounds__(256) k_origin_fix_edge(const CompressArgs a) {
     pdl_prologue();
     const int nd = a.g.nd;
-    for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < a.g.nb; b += (uint64_t)gridDim.x * blockDim.x)
-        origin_fix_block(a, b, edge_origin_pred(a.pad + b * (uint64_t)nd, nd));
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t b0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b0 < a.g.nb; b0 += kOriginUnroll * stride) {
+        int32_t q0[kOriginUnroll], sc[kOriginUnroll][3];
+#pragma unroll
+        for (int u = 0; u < kOriginUnroll; ++u) {
+            const uint64_t b = b0 + u * stride;
+            const bool in = b < a.g.nb;
+            q0[u] = in ? a.origin[b] : 0;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) sc[u][k] = (in && k < nd) ? a.pad[b * (uint64_t)nd + k] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < kOriginUnroll; ++u) {
+            const uint64_t b = b0 + u * stride;
+            if (b < a.g.nb) origin_fix_block(a, b, q0[u], edge_origin_pred_r(sc[u][0], sc[u][1], sc[u][2], nd));
+        }
+    }
 }
 
 // Fixups restore their values verbatim after the inverse.
@@ -250,10 +280,10 @@ cudaError_t launch_origin_fix(const CompressArgs& a, cudaStream_t s) {
         const int gs = grid_for((const void*)k_edge_stats, 256, 0, 1, items);
         cudaError_t e = launch_pdl(k_edge_stats, gs, 256, 0, s, a);
         if (e != cudaSuccess) return e;
-        const int go = grid_for((const void*)k_origin_fix_edge, 256, 0, 256, a.g.nb);
+        const int go = grid_for((const void*)k_origin_fix_edge, 256, 0, 256 * kOriginUnroll, a.g.nb);
         return launch_pdl(k_origin_fix_edge, go, 256, 0, s, a);
     }
-    const int grid = grid_for((const void*)k_origin_fix, 256, 0, 256, a.g.nb ? a.g.nb : 1);
+    const int grid = grid_for((const void*)k_origin_fix, 256, 0, 256 * kOriginUnroll, a.g.nb ? a.g.nb : 1);
     return launch_pdl(k_origin_fix, grid, 256, 0, s, a);
 }
 
