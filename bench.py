@@ -71,6 +71,9 @@ def parse_args(argv=None):
                     help="only a reduced mixed stream (4 of its 1800x3600 fields, 2 of its 100x500x500 fields and "
                          "the first 20M values of its 1D field), the tuner's classes, eb --eb: a small case for "
                          "ncu captures of the batch kernels")
+    ap.add_argument("--entropy-profile", action="store_true",
+                    help="only the entropy stage on the codes of the one-field workload (--size, --block, --pad; "
+                         "timed at --field-eb): a case for ncu captures of the Huffman kernels")
     ap.add_argument("--field-profile", action="store_true",
                     help="only the one-field step (--size, --block, --field-eb, --pad): a case for ncu captures of "
                          "the one-field kernels")
@@ -1198,6 +1201,14 @@ def main():
         return
     if a.field_profile:
         run_field_profile(a)
+        return
+    if a.entropy_profile:
+        import torch
+        import synth
+        x3 = synth.lognormal3d(a.size, seed=rank_field_seed(0))
+        xd = torch.from_numpy(x3.reshape(-1)).cuda()
+        print(json.dumps({"entropy_profile": f"{a.size}^3 NYX-like, block {a.block}, {a.pad}",
+                          **run_entropy(a, x3, xd)}), flush=True)
         return
     if a.impl == "reference":
         run_reference(a)

@@ -602,10 +602,12 @@ VSZ_API vsz_status vsz_tuner_sweep(const vsz_params* p, const float* d_x, double
  * (3D); r is a region's element count.  Regions are aligned to every
  * class's blocks, so each sampled block is a block of the field.  In
  * relative mode the error bound is relative to the sample's own range.
+ * d_cost (device double[2], or NULL): the two classes' estimated sizes on
+ * the sample, computed as vsz_tuner_sweep computes a class's cost.
  */
 VSZ_API size_t vsz_tuner_guard_workspace_size(const vsz_params* p, int class_a, int class_b);
 VSZ_API vsz_status vsz_tuner_guard(const vsz_params* p, const float* d_x, int class_a, int class_b,
-                                   uint64_t* d_nout, void* d_ws, size_t ws_bytes, void* stream);
+                                   uint64_t* d_nout, double* d_cost, void* d_ws, size_t ws_bytes, void* stream);
 
 /* Dims of the guard's stacked sample (host, no GPU work): sub_dims[0..2]. */
 VSZ_API vsz_status vsz_tuner_guard_sample_dims(const vsz_params* p, uint64_t* sub_dims);

@@ -705,7 +705,7 @@ size_t vsz_tuner_guard_workspace_size(const vsz_params* p, int class_a, int clas
 }
 
 vsz_status vsz_tuner_guard(const vsz_params* p, const float* d_x, int class_a, int class_b, uint64_t* d_nout,
-                           void* d_ws, size_t ws_bytes, void* stream) {
+                           double* d_cost, void* d_ws, size_t ws_bytes, void* stream) {
     GuardGeom G;
     vsz_params pa, pb;
     CountBufs B;
@@ -727,6 +727,17 @@ vsz_status vsz_tuner_guard(const vsz_params* p, const float* d_x, int class_a, i
     for (int k = 0; k < 2; ++k) {
         if ((st = count_class(pc[k], src, ws, B, s)) != VSZ_OK) return st;
         k_copy_nout<<<1, 32, 0, s>>>((const vsz_header*)(ws + B.off_hdr), d_nout + k);
+        if (d_cost) {  // the class's estimated size on the sample, as the sweep computes it
+            if ((st = vsz_code_histogram(pc[k], (const uint16_t*)(ws + B.off_codes), (uint32_t*)(ws + B.off_hist),
+                                         s)) != VSZ_OK)
+                return st;
+            Geom gc;
+            make_geom(pc[k], &gc);
+            const double npad =
+                pc[k]->pad == VSZ_PAD_BLOCK_AVG ? (double)gc.nb : pc[k]->pad == VSZ_PAD_GLOBAL_AVG ? 1.0 : 0.0;
+            k_class_cost<<<1, 1024, 0, s>>>((const uint32_t*)(ws + B.off_hist), 2u * p->radius, gc.n,
+                                            (const vsz_header*)(ws + B.off_hdr), npad, d_cost + k);
+        }
     }
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? VSZ_OK : cuda_fail(e);

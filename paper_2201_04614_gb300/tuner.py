@@ -79,7 +79,7 @@ def _bind():
     L.vsz_tuner_sweep.argtypes = [P(_CParams), vp, vp, vp, vp, sz, vp]
     L.vsz_tuner_guard_workspace_size.restype = sz
     L.vsz_tuner_guard_workspace_size.argtypes = [P(_CParams), i32, i32]
-    L.vsz_tuner_guard.argtypes = [P(_CParams), vp, i32, i32, vp, vp, sz, vp]
+    L.vsz_tuner_guard.argtypes = [P(_CParams), vp, i32, i32, vp, vp, vp, sz, vp]
     L.vsz_tuner_guard_sample_dims.argtypes = [P(_CParams), P(ctypes.c_uint64)]
     L.vsz_mlp_forward.argtypes = [vp, vp, vp, vp, i32, vp, vp, vp]
     L.vsz_mlp_grad_workspace_size.restype = sz
@@ -143,9 +143,10 @@ def sweep(p: Params, x, stream=None, with_nout: bool = False):
     return (cost, nout) if with_nout else cost
 
 
-def guard_counts(p: Params, x, class_a: int, class_b: int, stream=None):
+def guard_counts(p: Params, x, class_a: int, class_b: int, stream=None, with_cost: bool = False):
     """Exact outlier counts of two classes on the guard's fixed sample
-    (device uint64[2] viewed as int64)."""
+    (device uint64[2] viewed as int64); with_cost also returns the two
+    classes' estimated sizes on the sample (float64[2], as the sweep's)."""
     torch = _torch()
     L = _bind()
     _xcheck(x, p)
@@ -154,9 +155,11 @@ def guard_counts(p: Params, x, class_a: int, class_b: int, stream=None):
         raise ValueError("invalid parameters or classes for the guard")
     ws = _ws(need, x.device)
     out = torch.zeros(2, dtype=torch.int64, device=x.device)
-    _check(L.vsz_tuner_guard(ctypes.byref(p.c()), _ptr(x), int(class_a), int(class_b), _ptr(out), _ptr(ws),
-                             ws.numel(), _stream_handle(stream)), "vsz_tuner_guard")
-    return out
+    cost = torch.zeros(2, dtype=torch.float64, device=x.device) if with_cost else None
+    _check(L.vsz_tuner_guard(ctypes.byref(p.c()), _ptr(x), int(class_a), int(class_b), _ptr(out),
+                             _ptr(cost) if with_cost else None, _ptr(ws), ws.numel(), _stream_handle(stream)),
+           "vsz_tuner_guard")
+    return (out, cost) if with_cost else out
 
 
 def guard_sample_dims(p: Params) -> tuple:
@@ -331,11 +334,31 @@ class MLP:
 
 
 # ---------------------------------------------------------------- choosing
+def guard_pick(tuned: int, default: int, nout, cost) -> int:
+    """The guard's decision between the network's class and the default
+    from their outlier counts and estimated sizes on the guard's sample: the
+    default wins when the tuned class has more outliers, and, when the tuned
+    class's padding costs more to compute, when the two sizes tie by the
+    labels' rule (within SIZE_TOL of the smaller one; among tied classes the
+    cheaper padding wins, as in label_of)."""
+    if tuned == default:
+        return default
+    if int(nout[0]) > int(nout[1]):
+        return default
+    if cost is not None and PAD_RANK[tuned % 3] > PAD_RANK[default % 3]:
+        lo = min(float(cost[0]), float(cost[1]))
+        if float(cost[1]) <= lo * (1.0 + SIZE_TOL):
+            return default
+    return tuned
+
+
 def choose(fields, mlp: MLP | None = None, guard: bool = True, stream=None) -> list:
     """Tuned class for each (Params, x) of `fields`: features of every field,
-    one batched MLP inference, then the guard (the default class wins when
-    the tuned one has more outliers on the fixed sample).  Returns a list of
-    dicts {class, predicted, default, guard_nout}."""
+    one batched MLP inference, then the guard on a fixed sample of the field
+    (guard_pick: the default class wins when the tuned one has more outliers,
+    or when its dearer padding buys no size outside the labels' tie
+    tolerance).  Returns a list of dicts {class, predicted, default,
+    guard_nout, guard_cost}."""
     torch = _torch()
     if mlp is None:
         mlp = MLP.load()
@@ -354,11 +377,12 @@ def choose(fields, mlp: MLP | None = None, guard: bool = True, stream=None) -> l
         nd = len(p.dims)
         d = default_class(nd)
         c = int(pred[i])
-        rec = {"predicted": c, "default": d, "class": c, "guard_nout": None}
+        rec = {"predicted": c, "default": d, "class": c, "guard_nout": None, "guard_cost": None}
         if guard and c != d and p.n > 0:
-            cnt = guard_counts(p, x, c, d, stream=stream).cpu().numpy()
+            cnt, cost = guard_counts(p, x, c, d, stream=stream, with_cost=True)
+            cnt, cost = cnt.cpu().numpy(), cost.cpu().numpy()
             rec["guard_nout"] = (int(cnt[0]), int(cnt[1]))
-            if cnt[0] > cnt[1]:
-                rec["class"] = d
+            rec["guard_cost"] = (float(cost[0]), float(cost[1]))
+            rec["class"] = guard_pick(c, d, cnt, cost)
         out.append(rec)
     return out

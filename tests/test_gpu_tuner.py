@@ -113,11 +113,18 @@ def test_guard_counts_match_oracle(dims, ca, cb):
     p = vsz.Params.make(dims, 8, 1e-4, "rel", 64, "zero")
     sub = stacked_sample(x, dims)
     assert T.guard_sample_dims(p) == sub.shape
-    got = T.guard_counts(p, torch.from_numpy(x).cuda(), ca, cb).cpu().numpy()
+    got, cost = T.guard_counts(p, torch.from_numpy(x).cuda(), ca, cb, with_cost=True)
+    got, cost = got.cpu().numpy(), cost.cpu().numpy()
     for k, c in enumerate((ca, cb)):
         b, pad = OT.class_params(len(dims), c)
         r = oracle.compress(oracle.Params(sub.shape, b, 1e-4, oracle.EB_REL, 64, pad), sub)
         assert int(got[k]) == len(r.out_idx)
+        # the estimated size on the sample, as the sweep's cost of the class
+        want = OT.class_cost(sub.reshape(-1), sub.shape, 1e-4, oracle.EB_REL, 64, c)[0]
+        assert np.isclose(cost[k], want, rtol=1e-10, atol=0)
+    # without sizes the counts are the same
+    plain = T.guard_counts(p, torch.from_numpy(x).cuda(), ca, cb).cpu().numpy()
+    assert np.array_equal(plain, got)
 
 
 def _problem(seed, B):
