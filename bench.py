@@ -985,6 +985,14 @@ def run_gpu(a):
                 "values_per_launch": dom_vals,
                 "traffic": profiled_traffic(kname, f"stream eb{a.eb:g} tuned", units=dom_vals)}
     step_frac = sb["total"] / (ms_step * 1e-3) / 1e9 / peak
+    # the largest single launch of the step by device time (the range pass
+    # over every value, for the relative error bound), beside the class kernel
+    big = max(kern, key=lambda k: kern[k]["ms"])
+    big_s = kern[big]["ms"] / kern[big]["launches"] * 1e-3
+    big_bytes = sb["per_kernel"].get(big)
+    largest = {"kernel": big[0], "share": kern[big]["ms"] / sum(v["ms"] for v in kern.values()),
+               "us": big_s * 1e6, "achieved": big_bytes / big_s / 1e9 if big_bytes else None,
+               "frac": big_bytes / big_s / 1e9 / peak if big_bytes else None}
 
     # e2e through the C ABI from host memory to host memory
     e2e = None
@@ -1071,7 +1079,8 @@ def run_gpu(a):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32/i32", "data": "synthetic", "config": workload_config(a),
-            "roofline": roofline, "step_hbm_frac": step_frac, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roofline, "step_hbm_frac": step_frac, "largest_launch": largest, "cpu_baseline": cpu,
+            "e2e": e2e,
             "clocks": clocks, "gpu_launches": launches,
             "plain_GBps": head["plain_GBps"], "tuned_vs_plain": head["tuned_vs_plain"],
             "stream": strip_private(head), f"stream_eb_{a.eb_beside:g}": strip_private(beside),
