@@ -199,8 +199,12 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
     const uint64_t blk = (bz * g.nby + by) * g.nbx + bx;
     const uint64_t tile_base = (ND == 3 ? bz * B * plane : 0) + by * B * nx + x0;
     const float* xsrc = a.x;
-    // interior tile: every lane holds 4 columns, b rows and (3D) b planes
-    const bool interior = vec && s * kSegCols + kSegCols <= nx && ylen == B && (ND == 2 || zlen == B);
+    // interior tile: b rows and (3D) b planes, every lane 4 columns or (the
+    // field's last segment, nx a multiple of 4) none; a short segment takes
+    // the lean walk only with zero padding, whose walk keeps no statistic
+    // that lanes past the field would enter
+    const bool interior = vec && ylen == B && (ND == 2 || zlen == B) &&
+                          (s * kSegCols + kSegCols <= nx || (!BP && !GP && !EP));
 
     // copy the rows of batch (lz, j) into ring half h
     auto issue_batch = [&](int lz, int j, int h) {
@@ -414,7 +418,10 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
             constexpr int BPP = B / U;                       // batches per plane
             constexpr int NB = (ND == 3 ? B : 1) * BPP;      // batches per tile
             const uint32_t nx32 = (uint32_t)nx, pl32 = (uint32_t)plane;
-            const float* xl = a.x + tile_base;
+            // a lane past the field's last column copies nothing (zeros)
+            // from the field's start: its source and size, once per tile
+            const float* xl = valid ? a.x + tile_base : a.x;
+            const uint32_t xsz = valid ? 16u : 0u;
             uint16_t* cl = a.codes + tile_base;
             auto off32 = [&](int kb) -> uint32_t {
                 return (uint32_t)(kb / BPP) * pl32 + (uint32_t)((kb % BPP) * U) * nx32;
@@ -423,7 +430,7 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
                 const float* src0 = xl + off32(kb);
                 const uint32_t dst0 = ring_wr + (uint32_t)(st * U * 32 * 16);
 #pragma unroll
-                for (int u = 0; u < U; ++u) cp_async16(dst0 + u * 32 * 16, src0 + (uint32_t)u * nx32, 16u);
+                for (int u = 0; u < U; ++u) cp_async16(dst0 + u * 32 * 16, src0 + (uint32_t)u * nx32, xsz);
                 cp_async_commit();
             };
 #pragma unroll
@@ -513,11 +520,11 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs& a, uint64_t
                         r0c01 = c01;
                         r0c23 = c23;
                     }
-                    if (VSZ_IN(tile_base + off32(kb) + (uint64_t)u * nx + 3, g.n, 103))
+                    if (valid && VSZ_IN(tile_base + off32(kb) + (uint64_t)u * nx + 3, g.n, 103))
                         *reinterpret_cast<uint2*>(crow + (uint32_t)u * nx32) = make_uint2(c01, c23);
                 }
                 if ((BP || GP) && kb == 0) qcorner = __float2int_rn(__int_as_float(dh[0].x));
-                const uint32_t rows = __reduce_or_sync(VSZ_FULL, fmask);
+                const uint32_t rows = __reduce_or_sync(VSZ_FULL, valid ? fmask : 0u);
                 if (rows)  // codes already final: no rewrite
                     rare_rows((rows | (rows >> 8)) & 0xffu, rows >> 8, h, tile_base + off32(kb), jb, kb / BPP, kb == 0,
                               false, false, false);

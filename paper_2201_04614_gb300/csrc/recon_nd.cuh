@@ -95,7 +95,9 @@ __device__ __forceinline__ void nd_recon_tile(const ReconArgs& a, const uint64_t
     // batch when it is short enough.
     uint32_t lo_t = 0;
     bool cached = false;
-    const bool interior = vec && s * kSegCols + kSegCols <= nx && ylen == B && (ND == 2 || zlen == B);
+    // interior tile: b rows and (3D) b planes, every lane 4 columns or (the
+    // field's last segment, nx a multiple of 4) none
+    const bool interior = vec && ylen == B && (ND == 2 || zlen == B);
     const uint32_t ocap = ZREG_R && interior ? OCAP_BIG : (uint32_t)C::OCAP;
     uint32_t* const oc_idx = ZREG_R && interior ? reinterpret_cast<uint32_t*>(zs) : oc_idx0;
     int32_t* const oc_del = reinterpret_cast<int32_t*>(oc_idx + ocap);
@@ -137,6 +139,7 @@ __device__ __forceinline__ void nd_recon_tile(const ReconArgs& a, const uint64_t
             zm |= (((cw[u].y & 0xffffu) == 0u) ? 4u : 0u) << (4 * u);
             zm |= (((cw[u].y >> 16) == 0u) ? 8u : 0u) << (4 * u);
         }
+        if (!valid) zm = 0;  // a lane past the field's last column (its codes read as 0)
         // code-0 counts per row, one byte each (at most 4 per lane, 4G per block)
         uint32_t pk = 0;
 #pragma unroll
@@ -265,12 +268,15 @@ __device__ __forceinline__ void nd_recon_tile(const ReconArgs& a, const uint64_t
         constexpr bool ZREG = ND == 3 && B <= 8;
         constexpr int NB = NPL * BPP;
         const uint32_t nx32 = (uint32_t)nx, pl32 = (uint32_t)plane;
-        const uint16_t* cl = a.codes + tile_base;
+        // a lane past the field's last column copies nothing (zeros) from
+        // the field's start: its source and size, once per tile
+        const uint16_t* cl = valid ? a.codes + tile_base : a.codes;
+        const uint32_t csz = valid ? 8u : 0u;
         auto issue_fast = [&](int kb, int st) {
             const uint16_t* src0 = cl + (uint32_t)(kb / BPP) * pl32 + (uint32_t)((kb % BPP) * U) * nx32;
             const uint32_t dst0 = ring_wr + (uint32_t)(st * U * 32 * 8);
 #pragma unroll
-            for (int u = 0; u < U; ++u) cp_async8(dst0 + u * 32 * 8, src0 + (uint32_t)u * nx32, 8u);
+            for (int u = 0; u < U; ++u) cp_async8(dst0 + u * 32 * 8, src0 + (uint32_t)u * nx32, csz);
             cp_async_commit();
         };
 #pragma unroll
@@ -308,7 +314,7 @@ __device__ __forceinline__ void nd_recon_tile(const ReconArgs& a, const uint64_t
                     hz |= ((cw[u].x - 0x00010001u) & ~cw[u].x & 0x80008000u) |
                           ((cw[u].y - 0x00010001u) & ~cw[u].y & 0x80008000u);
                 }
-                const bool patch = anyout && __any_sync(VSZ_FULL, hz != 0u);
+                const bool patch = anyout && __any_sync(VSZ_FULL, valid && hz != 0u);
                 if (patch) patch_batch(cw, (uint32_t)tile_base + boff, nx32);
                 // one copy of the row code (the patch test is a uniform
                 // branch), which keeps the unrolled plane loop small
@@ -363,7 +369,7 @@ __device__ __forceinline__ void nd_recon_tile(const ReconArgs& a, const uint64_t
                     }
                     const uint32_t ro = boff + (uint32_t)u * nx32;
                     if (QOUT) {
-                        if (VSZ_IN(tile_base + ro + 3, g.n, 201))
+                        if (valid && VSZ_IN(tile_base + ro + 3, g.n, 201))
                         st_out4(reinterpret_cast<int4*>(reinterpret_cast<int32_t*>(a.out) + tile_base + ro),
                                 make_int4(d[0], d[1], d[2], d[3]));
                     } else {
@@ -379,7 +385,7 @@ __device__ __forceinline__ void nd_recon_tile(const ReconArgs& a, const uint64_t
                             vv.z = __float_as_int(__fmul_rn(q2f(d[2]), ebx2));
                             vv.w = __float_as_int(__fmul_rn(q2f(d[3]), ebx2));
                         }
-                        if (VSZ_IN(tile_base + ro + 3, g.n, 202))
+                        if (valid && VSZ_IN(tile_base + ro + 3, g.n, 202))
                             st_out4(reinterpret_cast<int4*>(reinterpret_cast<float*>(a.out) + tile_base + ro), vv);
                     }
                 };
