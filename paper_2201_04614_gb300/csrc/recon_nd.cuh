@@ -23,6 +23,11 @@
 
 namespace vsz {
 
+// Codes 1 (residual 1 - R, never an outlier), which a lane past a field's
+// last column copies instead of codes in the lean reconstruction walk, so
+// that the walk's outlier tests need no mask (global memory, never written).
+__device__ __align__(16) uint16_t kOneCodes[8] = {1, 1, 1, 1, 1, 1, 1, 1};
+
 // The inverse of one tile t of one field, by one warp whose shared memory
 // slice is wsm.
 template <int ND, int B, bool QOUT>
@@ -139,7 +144,6 @@ __device__ __forceinline__ void nd_recon_tile(const ReconArgs& a, const uint64_t
             zm |= (((cw[u].y & 0xffffu) == 0u) ? 4u : 0u) << (4 * u);
             zm |= (((cw[u].y >> 16) == 0u) ? 8u : 0u) << (4 * u);
         }
-        if (!valid) zm = 0;  // a lane past the field's last column (its codes read as 0)
         // code-0 counts per row, one byte each (at most 4 per lane, 4G per block)
         uint32_t pk = 0;
 #pragma unroll
@@ -268,15 +272,13 @@ __device__ __forceinline__ void nd_recon_tile(const ReconArgs& a, const uint64_t
         constexpr bool ZREG = ND == 3 && B <= 8;
         constexpr int NB = NPL * BPP;
         const uint32_t nx32 = (uint32_t)nx, pl32 = (uint32_t)plane;
-        // a lane past the field's last column copies nothing (zeros) from
-        // the field's start: its source and size, once per tile
-        const uint16_t* cl = valid ? a.codes + tile_base : a.codes;
-        const uint32_t csz = valid ? 8u : 0u;
+        const uint16_t* cl = a.codes + tile_base;
         auto issue_fast = [&](int kb, int st) {
             const uint16_t* src0 = cl + (uint32_t)(kb / BPP) * pl32 + (uint32_t)((kb % BPP) * U) * nx32;
             const uint32_t dst0 = ring_wr + (uint32_t)(st * U * 32 * 8);
 #pragma unroll
-            for (int u = 0; u < U; ++u) cp_async8(dst0 + u * 32 * 8, src0 + (uint32_t)u * nx32, csz);
+            for (int u = 0; u < U; ++u)  // a lane past the field's last column copies codes 1 (no outlier)
+                cp_async8(dst0 + u * 32 * 8, valid ? src0 + (uint32_t)u * nx32 : kOneCodes, 8u);
             cp_async_commit();
         };
 #pragma unroll
@@ -314,7 +316,7 @@ __device__ __forceinline__ void nd_recon_tile(const ReconArgs& a, const uint64_t
                     hz |= ((cw[u].x - 0x00010001u) & ~cw[u].x & 0x80008000u) |
                           ((cw[u].y - 0x00010001u) & ~cw[u].y & 0x80008000u);
                 }
-                const bool patch = anyout && __any_sync(VSZ_FULL, valid && hz != 0u);
+                const bool patch = anyout && __any_sync(VSZ_FULL, hz != 0u);
                 if (patch) patch_batch(cw, (uint32_t)tile_base + boff, nx32);
                 // one copy of the row code (the patch test is a uniform
                 // branch), which keeps the unrolled plane loop small
