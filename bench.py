@@ -833,18 +833,26 @@ def run_entropy(a, x3, xd, log_fn=log) -> dict:
         nwords = int(off[-1].item())
         dec, st2 = vsz.huffman_decode(words, off, n, book)
         ok = int(st.item()) == 0 and int(st2.item()) == 0 and bool(torch.equal(dec[:n], f.codes[:n]))
+        # the same stream with its decode index, decoded a warp per chunk
+        words_ix, off_ix, st_ix, index = vsz.huffman_encode(f.codes, n, book, index=True)
+        dec_ix, st_dix = vsz.huffman_decode_indexed(words_ix, off_ix, index, n, book)
+        ok = ok and int(st_ix.item()) == 0 and int(st_dix.item()) == 0 and bool(torch.equal(dec_ix[:n], f.codes[:n])) \
+            and bool(torch.equal(off_ix, off)) and bool(torch.equal(words_ix[:nwords], words[:nwords]))
         nc = off.numel() - 1
         table_bits = 32 * (p.nblocks + 1) + 64 * (nc + 1) + 32 * p.pad_len
         bits = 32 * nwords + 64 * int(h["n_out"]) + 64 * int(h["n_fix"]) + table_bits
         mse = float(((xh.double() - xd.double()) ** 2).mean().item())
         psnr = 20 * math.log10(vrange) - 10 * math.log10(mse) if mse > 0 else float("inf")
         row = {"eb": eb, "bits_per_value": bits / n, "ratio": 32.0 * n / bits, "huffman_bits_per_value": 32 * nwords / n,
+               "decode_index_bits_per_value": 512.0 * nc / n,
                "psnr_db": psnr, "n_out": int(h["n_out"]), "n_fix": int(h["n_fix"]), "round_trip_ok": ok}
         if eb == a.field_eb:
             ms_hist = ev_ms(lambda: f.code_histogram(out=hist))
             ms_book = ev_ms(lambda: vsz.HuffmanBook(hist, nsym))
             ms_enc = ev_ms(lambda: vsz.huffman_encode(f.codes, n, book, words=words))
             ms_dec = ev_ms(lambda: vsz.huffman_decode(words, off, n, book, out=dec))
+            ms_enc_ix = ev_ms(lambda: vsz.huffman_encode(f.codes, n, book, words=words_ix, index=index))
+            ms_dec_ix = ev_ms(lambda: vsz.huffman_decode_indexed(words_ix, off_ix, index, n, book, out=dec_ix))
             # bytes each pass must move: encode reads the codes twice (bit
             # counts, then packing) and writes the stream; decode reads the
             # stream and writes the codes
@@ -853,6 +861,7 @@ def run_entropy(a, x3, xd, log_fn=log) -> dict:
             vsz.trace_read()
             vsz.huffman_encode(f.codes, n, book, words=words)
             vsz.huffman_decode(words, off, n, book, out=dec)
+            vsz.huffman_decode_indexed(words_ix, off_ix, index, n, book, out=dec_ix)
             vsz.trace_enable(False)
             kern = {r["name"]: round(r["ms"] * 1e3, 1) for r in vsz.trace_read(64)}
             row["timing"] = {
@@ -860,10 +869,12 @@ def run_entropy(a, x3, xd, log_fn=log) -> dict:
                 "encode_us": ms_enc * 1e3, "decode_us": ms_dec * 1e3,
                 "encode_GBps_fp32_in": 4 * n / (ms_enc * 1e-3) / 1e9, "decode_GBps_fp32_out": 4 * n / (ms_dec * 1e-3) / 1e9,
                 "encode_hbm_GBps": enc_bytes / (ms_enc * 1e-3) / 1e9, "decode_hbm_GBps": dec_bytes / (ms_dec * 1e-3) / 1e9,
+                "encode_indexed_us": ms_enc_ix * 1e3, "decode_indexed_us": ms_dec_ix * 1e3,
+                "decode_indexed_hbm_GBps": (dec_bytes + 64 * nc) / (ms_dec_ix * 1e-3) / 1e9,
                 "kernels_us_one_call": kern}
         out["curve"].append(row)
         log_fn(f"[bench] entropy eb={eb:g}: {row}")
-        del f, book, words, off, dec
+        del f, book, words, off, dec, words_ix, off_ix, index, dec_ix
         torch.cuda.empty_cache()
     return out
 

@@ -532,6 +532,30 @@ VSZ_API vsz_status vsz_huffman_decode(const uint32_t* d_words, uint64_t word_cap
                                       uint64_t n, const void* d_book, uint32_t nsym, uint16_t* d_sym,
                                       uint32_t* d_status, void* stream);
 
+/* Decode index (Sec. II-B's Huffman stage, decoded in parallel): the same
+ * stream as vsz_huffman_encode (bit for bit), plus d_index[32 * nchunks]
+ * (uint16, device): entry 32 c + j is the bit, relative to the start of
+ * chunk c, where its codes 32 j .. 32 j + 31 begin (the chunk's total bits
+ * for lanes past the end of the data).  The index is 64 bytes per chunk of
+ * 1024 codes and is not part of the stream: it lets vsz_huffman_decode_indexed
+ * give each chunk to a warp.  *d_status as vsz_huffman_encode, plus bit 16 if
+ * a chunk holds 2^16 bits or more (its index entries are then truncated and
+ * the stream must be decoded with vsz_huffman_decode).  VSZ_ERR_INVALID_ARG
+ * as vsz_huffman_encode, or if d_index is NULL with n > 0. */
+VSZ_API vsz_status vsz_huffman_encode_indexed(const uint16_t* d_sym, uint64_t n, const void* d_book, uint32_t nsym,
+                                              uint32_t* d_words, uint64_t word_cap, uint64_t* d_chunk_off,
+                                              uint16_t* d_index, uint32_t* d_status, void* d_ws, size_t ws_bytes,
+                                              void* stream);
+
+/* Decode n codes as vsz_huffman_decode, with the decode index of
+ * vsz_huffman_encode_indexed: one warp per chunk, each lane decoding its 32
+ * codes from its own starting bit.  Same outputs and status bits; bit 4 also
+ * if a lane's codes do not end where the next lane's begin (a stream or an
+ * index that do not belong together). */
+VSZ_API vsz_status vsz_huffman_decode_indexed(const uint32_t* d_words, uint64_t word_cap, const uint64_t* d_chunk_off,
+                                              const uint16_t* d_index, uint64_t n, const void* d_book, uint32_t nsym,
+                                              uint16_t* d_sym, uint32_t* d_status, void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* Learned tuner of block size and padding mode.                            */
 /* ------------------------------------------------------------------------ */

@@ -95,7 +95,7 @@ EXPORTED = ["vsz_status_string", "vsz_last_cuda_error", "vsz_abi_version", "vsz_
             "vsz_huffman_book_bytes", "vsz_huffman_book", "vsz_huffman_book_read", "vsz_huffman_encode",
             "vsz_huffman_encode_workspace_size", "vsz_sampling_autotune_workspace_size", "vsz_sampling_autotune",
             "vsz_sync_status", "vsz_shutdown", "vsz_debug_fail_alloc", "vsz_debug_bounds_word",
-            "vsz_huffman_decode",
+            "vsz_huffman_decode", "vsz_huffman_encode_indexed", "vsz_huffman_decode_indexed",
             "vsz_tuner_features_workspace_size", "vsz_tuner_features",
             "vsz_tuner_sweep_workspace_size", "vsz_tuner_sweep", "vsz_tuner_guard_workspace_size",
             "vsz_tuner_guard", "vsz_tuner_guard_sample_dims", "vsz_mlp_forward", "vsz_mlp_grad_workspace_size",
@@ -163,6 +163,8 @@ def lib():
     L.vsz_huffman_encode_workspace_size.argtypes = [u64]
     L.vsz_huffman_encode.argtypes = [vp, u64, vp, ctypes.c_uint32, vp, u64, vp, vp, vp, sz, vp]
     L.vsz_huffman_decode.argtypes = [vp, u64, vp, u64, vp, ctypes.c_uint32, vp, vp, vp]
+    L.vsz_huffman_encode_indexed.argtypes = [vp, u64, vp, ctypes.c_uint32, vp, u64, vp, vp, vp, vp, sz, vp]
+    L.vsz_huffman_decode_indexed.argtypes = [vp, u64, vp, vp, u64, vp, ctypes.c_uint32, vp, vp, vp]
     L.vsz_batch_reconstruct.argtypes = [vp, vp]
     L.vsz_batch_compress_host.argtypes = [vp, P(ctypes.c_void_p), P(_CHostField), vp]
     L.vsz_slab_range.argtypes = [vp, u64, vp, vp]
@@ -667,10 +669,14 @@ def shutdown() -> None:
     _check(lib().vsz_shutdown(), "vsz_shutdown")
 
 
-def huffman_encode(sym, n: int, book: HuffmanBook, words=None, stream=None):
+def huffman_encode(sym, n: int, book: HuffmanBook, words=None, stream=None, index=None):
     """Encode n uint16 symbols (a CUDA tensor viewed as int16/uint16).
     Returns (words, chunk_off, status) as CUDA tensors; status is read by
-    the caller (bit 1: a symbol without a codeword, bit 2: words too short)."""
+    the caller (bit 1: a symbol without a codeword, bit 2: words too short).
+    With index (an int16 CUDA tensor of 32 entries per chunk, or True to
+    allocate one) the decode index is written too (vsz_huffman_encode_indexed;
+    bit 16: a chunk too long to index) and (words, chunk_off, status, index)
+    is returned."""
     import torch
     nc = (n + HUFF_CHUNK - 1) // HUFF_CHUNK
     off = torch.empty(nc + 1, dtype=torch.int64, device=sym.device)
@@ -679,9 +685,17 @@ def huffman_encode(sym, n: int, book: HuffmanBook, words=None, stream=None):
     st = torch.empty(1, dtype=torch.int32, device=sym.device)
     wsb = int(lib().vsz_huffman_encode_workspace_size(n))
     ws = torch.empty(wsb, dtype=torch.uint8, device=sym.device)
-    _check(lib().vsz_huffman_encode(_ptr(sym), n, _ptr(book.buf), book.nsym, _ptr(words), words.numel(),
-                                    _ptr(off), _ptr(st), _ptr(ws), wsb, _stream_handle(stream)), "vsz_huffman_encode")
-    return words, off, st
+    if index is None:
+        _check(lib().vsz_huffman_encode(_ptr(sym), n, _ptr(book.buf), book.nsym, _ptr(words), words.numel(),
+                                        _ptr(off), _ptr(st), _ptr(ws), wsb, _stream_handle(stream)),
+               "vsz_huffman_encode")
+        return words, off, st
+    if index is True:
+        index = torch.empty(max(1, 32 * nc), dtype=torch.int16, device=sym.device)
+    _check(lib().vsz_huffman_encode_indexed(_ptr(sym), n, _ptr(book.buf), book.nsym, _ptr(words), words.numel(),
+                                            _ptr(off), _ptr(index), _ptr(st), _ptr(ws), wsb, _stream_handle(stream)),
+           "vsz_huffman_encode_indexed")
+    return words, off, st, index
 
 
 def huffman_decode(words, chunk_off, n: int, book: HuffmanBook, out=None, stream=None):
@@ -692,4 +706,17 @@ def huffman_decode(words, chunk_off, n: int, book: HuffmanBook, out=None, stream
     st = torch.empty(1, dtype=torch.int32, device=words.device)
     _check(lib().vsz_huffman_decode(_ptr(words), words.numel(), _ptr(chunk_off), n, _ptr(book.buf), book.nsym,
                                     _ptr(out), _ptr(st), _stream_handle(stream)), "vsz_huffman_decode")
+    return out, st
+
+
+def huffman_decode_indexed(words, chunk_off, index, n: int, book: HuffmanBook, out=None, stream=None):
+    """Decode n symbols with the decode index (vsz_huffman_decode_indexed):
+    a warp per chunk; returns (symbols, status)."""
+    import torch
+    if out is None:
+        out = torch.empty(max(n, 1), dtype=torch.int16, device=words.device)
+    st = torch.empty(1, dtype=torch.int32, device=words.device)
+    _check(lib().vsz_huffman_decode_indexed(_ptr(words), words.numel(), _ptr(chunk_off), _ptr(index), n,
+                                            _ptr(book.buf), book.nsym, _ptr(out), _ptr(st), _stream_handle(stream)),
+           "vsz_huffman_decode_indexed")
     return out, st

@@ -443,11 +443,14 @@ __global__ void __launch_bounds__(1024) k_huff_scan(unsigned long long* rt, uint
 // chunk: each lane writes its 32 codewords through a 64-bit bit-writer into
 // the warp's words in shared memory (the words it shares with its neighbour
 // lanes by OR), then the warp stores them and the chunk's final offset
-// replaces its local one.
+// replaces its local one.  With a decode index, lane j also records the
+// chunk-relative bit where its 32 codewords start (index[32 c + j]; a chunk
+// of 2^16 bits or more cannot be indexed: status bit 16).
 __global__ void __launch_bounds__(kEncThreads) k_huff_encode(const uint16_t* __restrict__ sym, uint64_t n,
                                                               const void* bookp, uint32_t nsym, uint64_t* off,
                                                               const unsigned long long* __restrict__ rt,
-                                                              uint32_t* words, uint64_t word_cap) {
+                                                              uint32_t* words, uint64_t word_cap, uint16_t* index,
+                                                              uint32_t* status) {
     __shared__ uint32_t sw[kEncThreads / 32][kChunkWordsMax];
     extern __shared__ __align__(16) unsigned char smraw[];
     unsigned long long* scode = (unsigned long long*)smraw;  // [nsym]
@@ -481,6 +484,10 @@ __global__ void __launch_bounds__(kEncThreads) k_huff_encode(const uint16_t* __r
         const uint32_t total = __shfl_sync(VSZ_FULL, x, 31);
         const uint32_t nw = min((total + 31u) / 32u, (uint32_t)kChunkWordsMax);
         const uint32_t pos = x - mybits;  // this lane's first bit in the chunk
+        if (index) {
+            index[c * 32 + lane] = (uint16_t)pos;
+            if (lane == 31 && total > 0xffffu) atomicOr(status, 16u);
+        }
         for (uint32_t i = lane; i < nw; i += 32) ws[i] = 0;
         __syncwarp();
         // bit-writer: acc holds nacc pending bits (nacc < 32 between codes);
@@ -679,6 +686,135 @@ __global__ void __launch_bounds__(kDecMaxThreads) k_huff_decode(const uint32_t* 
     }
 }
 
+// Indexed decoding: one warp per chunk; lane j decodes the chunk's codes
+// 32j..32j+31 starting at the bit index[32 c + j] that the encoder recorded,
+// over a two-word window whose words it reads through L1 (the chunk's words
+// are shared by its lanes).  Same table and canonical ranges as above.  A
+// lane whose codes do not end exactly where the next lane's start (or past
+// the chunk's words, for the last lane) reports status bit 4.
+__global__ void __launch_bounds__(kDecMaxThreads) k_huff_decode_ix(const uint32_t* __restrict__ words,
+                                                                 uint64_t word_cap, const uint64_t* __restrict__ off,
+                                                                 const uint16_t* __restrict__ index, uint64_t n,
+                                                                 const void* bookp, uint32_t nsym, uint16_t* out,
+                                                                 uint32_t* status) {
+    __shared__ unsigned long long first[66];
+    __shared__ uint32_t cnt[66], base[66];
+    extern __shared__ __align__(16) unsigned char smraw[];
+    uint32_t* lut = (uint32_t*)smraw;                           // [2^kLutBits]
+    uint16_t* sorted = (uint16_t*)(lut + (1u << kLutBits));     // [nused]
+    const HuffBook bk = huff_book(bookp, nsym);
+    if (bk.hdr->nsym != nsym) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, 8u);
+        return;
+    }
+    const uint32_t nused = min(bk.hdr->nused, nsym), maxlen = min(bk.hdr->max_len, 64u);
+    for (uint32_t i = threadIdx.x; i < (1u << kLutBits) / 4; i += blockDim.x)
+        reinterpret_cast<uint4*>(lut)[i] = __ldg(reinterpret_cast<const uint4*>(bk.lut) + i);
+    for (uint32_t i = threadIdx.x; i < 66; i += blockDim.x) {
+        first[i] = bk.first[i];
+        cnt[i] = bk.count[i];
+        base[i] = bk.base[i];
+    }
+    for (uint32_t i = threadIdx.x; i < nused; i += blockDim.x) sorted[i] = bk.sorted[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const uint64_t nc = (n + kHC - 1) / kHC;
+    const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    const bool vec = (reinterpret_cast<uintptr_t>(out) & 7) == 0;
+    const bool pair = nsym <= kPairMaxSym;
+    auto rd = [&](uint64_t a) -> uint32_t { return a < word_cap ? __ldg(words + a) : 0u; };
+    for (uint64_t c = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < nc; c += nwarps) {
+        const uint64_t wb = off[c], we = umin64(off[c + 1], word_cap);
+        if (wb > we) {
+            if (lane == 0) atomicOr(status, 4u);
+            continue;
+        }
+        const uint32_t start = index[c * 32 + lane];
+        const uint64_t i0 = c * kHC + (uint64_t)lane * kLaneSyms;
+        const uint32_t m = i0 < n ? (uint32_t)umin64(kLaneSyms, n - i0) : 0u;  // this lane's codes
+        uint16_t* o = out + i0;
+        uint64_t nxt = wb + (start >> 5);
+        uint32_t w0 = rd(nxt), w1 = rd(nxt + 1);
+        nxt += 2;
+        uint32_t ob = start & 31u;
+        unsigned long long acc = 0;
+        uint32_t pend = 0, g = 0;
+        auto emit = [&](uint32_t val, uint32_t k, uint32_t i) {  // k symbols, the first in the low half
+            if (vec) {
+                acc |= (unsigned long long)val << (16 * pend);
+                const uint32_t np = pend + k;
+                if (np >= 4) {
+                    *reinterpret_cast<unsigned long long*>(o + g) = acc;
+                    g += 4;
+                    acc = np == 5 ? (unsigned long long)(val >> 16) : 0ull;
+                }
+                pend = np >= 4 ? np - 4 : np;
+            } else {
+                o[i] = (uint16_t)val;
+                if (k == 2) o[i + 1] = (uint16_t)(val >> 16);
+            }
+        };
+        bool bad = false;
+        uint32_t used = 0;
+        for (uint32_t i = 0; i < m;) {
+            const uint32_t e = lut[__funnelshift_l(w1, w0, ob) >> (32 - kLutBits)];
+            uint32_t l, sv, l2 = 0, sv2 = 0;
+            if (pair) {
+                l = (e >> 24) & 15u;
+                sv = e & 0xfffu;
+                l2 = e >> 28;
+                sv2 = (e >> 12) & 0xfffu;
+            } else {
+                l = e >> 16;
+                sv = e & 0xffffu;
+            }
+            if (l == 0) {  // a codeword longer than the table: the canonical ranges on a 64-bit window
+                const uint32_t w2 = rd(nxt);
+                const unsigned long long win = ((unsigned long long)__funnelshift_l(w1, w0, ob) << 32) |
+                                               __funnelshift_l(w2, w1, ob);
+                for (uint32_t L = kLutBits + 1; L <= maxlen; ++L) {
+                    const unsigned long long cw = win >> (64 - L);
+                    if (cw >= first[L] && cw - first[L] < cnt[L]) {
+                        sv = sorted[base[L] + (uint32_t)(cw - first[L])];
+                        l = L;
+                        break;
+                    }
+                }
+                if (l == 0) {
+                    bad = true;
+                    break;
+                }
+                emit(sv, 1, i);
+                used += l;
+                ob += l;
+                while (ob >= 32) {  // at most twice
+                    w0 = w1;
+                    w1 = rd(nxt++);
+                    ob -= 32;
+                }
+                ++i;
+                continue;
+            }
+            if (i + 1 >= m) l2 = 0;  // the lane's last code: what follows is the next lane's
+            const uint32_t t = l + l2;  // <= 15
+            emit(l2 ? sv | (sv2 << 16) : sv, l2 ? 2u : 1u, i);
+            used += t;
+            i += l2 ? 2 : 1;
+            ob += t;
+            if (ob >= 32) {
+                w0 = w1;
+                w1 = rd(nxt++);
+                ob -= 32;
+            }
+        }
+        if (vec && !bad)
+            for (uint32_t j = 0; j < pend; ++j) o[g + j] = (uint16_t)(acc >> (16 * j));
+        const bool ends = lane < 31 ? start + used == (uint32_t)index[c * 32 + lane + 1]
+                                    : ((uint64_t)start + used + 31) / 32 <= we - wb;
+        if (bad || !ends) atomicOr(status, 4u);
+    }
+}
+
 static size_t dec_smem_bytes(uint32_t nsym) { return ((size_t)1 << kLutBits) * 4 + (((size_t)nsym * 2 + 15) & ~(size_t)15); }
 
 }  // namespace vsz
@@ -742,9 +878,9 @@ size_t vsz_huffman_encode_workspace_size(uint64_t n) {
     return (kEncMaxCtas + 1) * sizeof(unsigned long long);
 }
 
-vsz_status vsz_huffman_encode(const uint16_t* d_sym, uint64_t n, const void* d_book, uint32_t nsym,
-                              uint32_t* d_words, uint64_t word_cap, uint64_t* d_chunk_off, uint32_t* d_status,
-                              void* d_ws, size_t ws_bytes, void* stream) {
+static vsz_status huffman_encode_impl(const uint16_t* d_sym, uint64_t n, const void* d_book, uint32_t nsym,
+                                      uint32_t* d_words, uint64_t word_cap, uint64_t* d_chunk_off, uint16_t* d_index,
+                                      uint32_t* d_status, void* d_ws, size_t ws_bytes, void* stream) {
     if (nsym == 0 || nsym > kMaxSym || !d_book || !aligned(d_book, 16) || !d_chunk_off || !d_status)
         return VSZ_ERR_INVALID_ARG;
     if (n > 0 && (!d_sym || (word_cap > 0 && !d_words))) return VSZ_ERR_INVALID_ARG;
@@ -774,10 +910,26 @@ vsz_status vsz_huffman_encode(const uint16_t* d_sym, uint64_t n, const void* d_b
     }
     {
         TraceScope ts("huff_encode", s, 0, 0, n);
-        k_huff_encode<<<G, kEncThreads, smem, s>>>(d_sym, n, d_book, nsym, d_chunk_off, rt, d_words, word_cap);
+        k_huff_encode<<<G, kEncThreads, smem, s>>>(d_sym, n, d_book, nsym, d_chunk_off, rt, d_words, word_cap,
+                                                   d_index, d_status);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
     }
     return VSZ_OK;
+}
+
+vsz_status vsz_huffman_encode(const uint16_t* d_sym, uint64_t n, const void* d_book, uint32_t nsym,
+                              uint32_t* d_words, uint64_t word_cap, uint64_t* d_chunk_off, uint32_t* d_status,
+                              void* d_ws, size_t ws_bytes, void* stream) {
+    return huffman_encode_impl(d_sym, n, d_book, nsym, d_words, word_cap, d_chunk_off, nullptr, d_status, d_ws,
+                               ws_bytes, stream);
+}
+
+vsz_status vsz_huffman_encode_indexed(const uint16_t* d_sym, uint64_t n, const void* d_book, uint32_t nsym,
+                                      uint32_t* d_words, uint64_t word_cap, uint64_t* d_chunk_off, uint16_t* d_index,
+                                      uint32_t* d_status, void* d_ws, size_t ws_bytes, void* stream) {
+    if (n > 0 && !d_index) return VSZ_ERR_INVALID_ARG;
+    return huffman_encode_impl(d_sym, n, d_book, nsym, d_words, word_cap, d_chunk_off, d_index, d_status, d_ws,
+                               ws_bytes, stream);
 }
 
 vsz_status vsz_huffman_decode(const uint32_t* d_words, uint64_t word_cap, const uint64_t* d_chunk_off, uint64_t n,
@@ -801,6 +953,31 @@ vsz_status vsz_huffman_decode(const uint32_t* d_words, uint64_t word_cap, const 
         TraceScope ts("huff_decode", s, 0, 0, n);
         k_huff_decode<<<(unsigned)G, (unsigned)T, smem, s>>>(
             d_words, word_cap, d_chunk_off, n, d_book, nsym, d_sym, d_status);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
+    }
+    return VSZ_OK;
+}
+
+vsz_status vsz_huffman_decode_indexed(const uint32_t* d_words, uint64_t word_cap, const uint64_t* d_chunk_off,
+                                      const uint16_t* d_index, uint64_t n, const void* d_book, uint32_t nsym,
+                                      uint16_t* d_sym, uint32_t* d_status, void* stream) {
+    if (nsym == 0 || nsym > kMaxSym || !d_book || !aligned(d_book, 16) || !d_chunk_off || !d_status)
+        return VSZ_ERR_INVALID_ARG;
+    if (n > 0 && (!d_sym || !d_words || !d_index)) return VSZ_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(d_status, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    const uint64_t nc = (n + kHC - 1) / kHC;
+    if (nc == 0) return VSZ_OK;
+    const size_t smem = dec_smem_bytes(nsym);
+    if ((e = raise_smem_attr((const void*)k_huff_decode_ix, smem)) != cudaSuccess) return cuda_fail(e);
+    // one CTA of 32 warps per SM (the table fills most of its shared memory),
+    // a warp per chunk, warps looping when there are more chunks than that
+    const uint64_t G = umin64((uint64_t)num_sms(), (nc + 31) / 32);
+    {
+        TraceScope ts("huff_decode_ix", s, 0, 0, n);
+        k_huff_decode_ix<<<(unsigned)G, kDecMaxThreads, smem, s>>>(d_words, word_cap, d_chunk_off, d_index, n,
+                                                                   d_book, nsym, d_sym, d_status);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
     }
     return VSZ_OK;

@@ -174,3 +174,86 @@ def test_truncated_stream_is_reported():
     total = int(off[-1].item())
     _, st = vsz.huffman_decode(words[: total - 40], off, n, book)
     assert int(st.item()) & 4
+
+
+# ---------------------------------------------------------------- decode index
+def _oracle_index(sym, lens):
+    """The decode index from the oracle's code lengths: for chunk c and lane
+    j, the bits of the chunk's codes before code 32 j (the chunk's total for
+    lanes past the data)."""
+    n = sym.size
+    nc = (n + 1023) // 1024
+    bits = np.zeros(nc * 1024, np.int64)
+    bits[:n] = lens[sym].astype(np.int64)
+    per = bits.reshape(nc, 32, 32).sum(axis=2)
+    return (np.cumsum(per, axis=1) - per).astype(np.uint16).reshape(-1)
+
+
+def _indexed_round_trip(sym, nsym, weights, words_shift=0, out_shift=0):
+    n = sym.size
+    book = vsz.HuffmanBook(torch.from_numpy(weights.view(np.int32)).cuda(), nsym)
+    lo, co = oracle.huffman_book(weights)
+    ow, ooff = oracle.huffman_encode(sym, lo, co)
+    sym_t = torch.from_numpy(sym.view(np.int16)).cuda()
+    cap = torch.zeros(ow.size + 16, dtype=torch.int32, device="cuda")
+    words, off, st, index = vsz.huffman_encode(sym_t, n, book, words=cap, index=True)
+    assert int(st.item()) == 0
+    goff = off.cpu().numpy().view(np.uint64)
+    assert np.array_equal(goff, ooff)  # the same stream as without the index
+    assert np.array_equal(words[: int(goff[-1])].cpu().numpy().view(np.uint32), ow)
+    nc = (n + 1023) // 1024
+    assert np.array_equal(index[: 32 * nc].cpu().numpy().view(np.uint16), _oracle_index(sym, lo))
+    wbuf = torch.zeros(words.numel() + 4, dtype=torch.int32, device="cuda")
+    wbuf[words_shift: words_shift + words.numel()] = words
+    obuf = torch.zeros(n + 8, dtype=torch.int16, device="cuda")
+    dec, st2 = vsz.huffman_decode_indexed(wbuf[words_shift: words_shift + words.numel()], off, index, n, book,
+                                          out=obuf[out_shift: out_shift + n])
+    assert int(st2.item()) == 0
+    assert np.array_equal(dec[:n].cpu().numpy().view(np.uint16), sym)
+    return words, off, index, book
+
+
+@pytest.mark.parametrize("case", _streams(), ids=lambda c: f"{c[0]}-{c[1]}")
+def test_indexed_stream_matches_oracle_and_decodes(case):
+    if case[0] == "dq":
+        _, dims, block, eb, R = case
+        sym_t, n, nsym = _dq_codes(dims, block, eb, R, seed=3)
+        sym = sym_t.cpu().numpy().view(np.uint16).copy()
+    else:
+        _, n, nsym, seed, _ = case
+        rng = np.random.default_rng(seed)
+        sym = np.minimum(rng.geometric(0.3, n) - 1, nsym - 1).astype(np.uint16)
+    hist = np.bincount(sym, minlength=nsym).astype(np.uint32)
+    _indexed_round_trip(sym, nsym, hist)
+
+
+@pytest.mark.parametrize("n", [1, 1000, 3 * 1024 + 517])
+def test_indexed_long_codewords(n):
+    # codewords up to 39 bits, many longer than the 15-bit table and than 32
+    weights = np.array(_fib(40), np.uint32)
+    sym = np.random.default_rng(n).integers(0, 40, n).astype(np.uint16)
+    _indexed_round_trip(sym, 40, weights)
+
+
+@pytest.mark.parametrize("shifts", [(1, 0), (0, 1), (2, 5)])
+def test_indexed_unaligned_views(shifts):
+    rng = np.random.default_rng(17)
+    n, nsym = 5 * 1024 + 77, 1024
+    sym = np.minimum(rng.geometric(0.05, n) - 1, nsym - 1).astype(np.uint16)
+    weights = np.bincount(sym, minlength=nsym).astype(np.uint32)
+    _indexed_round_trip(sym, nsym, weights, *shifts)
+
+
+def test_index_that_does_not_fit_the_stream_is_reported():
+    rng = np.random.default_rng(8)
+    n, nsym = 6 * 1024, 512
+    sym = np.minimum(rng.geometric(0.02, n) - 1, nsym - 1).astype(np.uint16)
+    weights = np.bincount(sym, minlength=nsym).astype(np.uint32)
+    words, off, index, book = _indexed_round_trip(sym, nsym, weights)
+    bad = index.clone()
+    bad[2 * 32 + 7] += 5  # lane 6 of chunk 2 then ends short of where lane 7 is said to start
+    _, st = vsz.huffman_decode_indexed(words, off, bad, n, book)
+    assert int(st.item()) & 4
+    total = int(off[-1].item())
+    _, st = vsz.huffman_decode_indexed(words[: total - 40], off, index, n, book)
+    assert int(st.item()) & 4
