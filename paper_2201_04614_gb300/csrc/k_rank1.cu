@@ -123,14 +123,23 @@ __device__ __forceinline__ void compress_1d_tile(const CompressArgs& a, uint64_t
     const float Rf = (float)R, RB = (float)(R + 8388608), Pgf = (float)Pg;
     const bool need_mm = GP && a.pad_mode != VSZ_PAD_GLOBAL_AVG;
     if (need_mm) mm[lane] = make_int2(INT_MAX, INT_MIN);  // q extremes of the tile (global min or max)
-#pragma unroll 2
+    // The next full step's values are loaded before this step's work, so a
+    // warp keeps two steps of loads in flight (the code stores in between
+    // would otherwise hold the next loads back: the compiler cannot prove
+    // that they do not alias the input).  Whenever a step takes the fp32
+    // path, xn holds its values: the step before it was full too, and loaded it.
+    float xn[EPL];
+    if (fast && start + SPAN <= n) load_epl<EPL>(a.x + start + (uint64_t)lane * EPL, EPL, true, xn);
+#pragma unroll 1
     for (int st = 0; st < C::STEPS; ++st) {
         const uint64_t s0 = start + (uint64_t)st * SPAN;
         if (s0 >= n) break;
         const uint64_t base = s0 + (uint64_t)lane * EPL;
         if (fast && s0 + SPAN <= n) {
             float xv[EPL], rp[EPL];
-            load_epl<EPL>(a.x + base, EPL, true, xv);
+#pragma unroll
+            for (int k = 0; k < EPL; ++k) xv[k] = xn[k];
+            if (st + 1 < C::STEPS && s0 + 2 * SPAN <= n) load_epl<EPL>(a.x + base + SPAN, EPL, true, xn);
 #pragma unroll
             for (int k = 0; k < EPL; ++k) rp[k] = __fsub_rn(__fadd_rn(__fmul_rn(xv[k], inv2eb), kMagic), kMagic);
             const bool origin = glane == 0;  // this lane's first value opens a block
