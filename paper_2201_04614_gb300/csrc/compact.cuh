@@ -77,15 +77,15 @@ __device__ __forceinline__ void compact_chunk_body(uint64_t chunk, const Compres
     const uint64_t ntiles = g.ntiles, nseg = g.nseg, nbx = g.nbx;
     const uint32_t bpt = g.bpt;
     const uint64_t t0 = chunk * kTilesPerChunk;
-    // a chunk with no entries at offset 0 is final as the walk left it
-    // (every block offset in-tile and zero): nothing to move or add
-    {
-        const uint4 ch = a.chunks[chunk];
-        if ((ch.x | ch.y | ch.z | ch.w) == 0u) return;
-    }
+    // A chunk with no outliers in it or before it has its block offsets
+    // final as the walk left them (in-tile, and zero): only its fixups, if
+    // it has any, move.
+    const uint4 ch = a.chunks[chunk];  // {outliers, fixups, offset of outliers, offset of fixups}
+    const bool outl = (ch.x | ch.z) != 0u;
+    if (!outl && ch.y == 0u) return;
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     if (w == 0) {  // the chunk's tile offsets: chunk offset + exclusive scan of the tile totals
-        uint32_t bo = a.chunks[chunk].z, bf = a.chunks[chunk].w;
+        uint32_t bo = ch.z, bf = ch.w;
         for (int i0 = 0; i0 < kTilesPerChunk; i0 += 32) {
             const uint64_t t = t0 + i0 + l;
             const uint4 r = t < ntiles ? a.tiles[t] : make_uint4(0, 0, 0, 0);
@@ -113,84 +113,86 @@ __device__ __forceinline__ void compact_chunk_body(uint64_t chunk, const Compres
         const uint64_t s = tt % nseg;
         const uint64_t fb = (tt / nseg) * nbx + s * bpt;
         const uint32_t nblk = (uint32_t)umin64(bpt, nbx - s * bpt);
-        // origin outliers of this tile's blocks (global padding only)
-        uint32_t nflag = 0;
-        const uint32_t nwords = (nblk + 31) / 32;
-        if (a.oflag) {
-            for (uint32_t wd = 0; wd < nwords; ++wd) {
-                const uint32_t k = wd * 32 + l;
-                const uint32_t bits = __ballot_sync(VSZ_FULL, k < nblk && a.oflag[fb + k] != 0);
-                if (l == 0) fw[w][wd] = bits;
-                nflag += __popc(bits);
+        if (outl) {
+            // origin outliers of this tile's blocks (global padding only)
+            uint32_t nflag = 0;
+            const uint32_t nwords = (nblk + 31) / 32;
+            if (a.oflag) {
+                for (uint32_t wd = 0; wd < nwords; ++wd) {
+                    const uint32_t k = wd * 32 + l;
+                    const uint32_t bits = __ballot_sync(VSZ_FULL, k < nblk && a.oflag[fb + k] != 0);
+                    if (l == 0) fw[w][wd] = bits;
+                    nflag += __popc(bits);
+                }
             }
-        }
-        const uint32_t staged = rr.y - nflag;
-        if (nflag == 0) {
-            for (uint32_t k = l; k < nblk; k += 32) a.blk_off[fb + k] += to;
-            if (rr.y && (uint64_t)rr.x + rr.y <= a.out_cap && (uint64_t)to + rr.y <= a.out_cap) {
-                uint32_t k = l;
-                for (; k + 96 < rr.y; k += 128) {  // four loads in flight per lane
-                    uint2 e[4];
+            const uint32_t staged = rr.y - nflag;
+            if (nflag == 0) {
+                for (uint32_t k = l; k < nblk; k += 32) a.blk_off[fb + k] += to;
+                if (rr.y && (uint64_t)rr.x + rr.y <= a.out_cap && (uint64_t)to + rr.y <= a.out_cap) {
+                    uint32_t k = l;
+                    for (; k + 96 < rr.y; k += 128) {  // four loads in flight per lane
+                        uint2 e[4];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) e[u] = a.stage_out[rr.x + k + 32 * u];
+                        for (int u = 0; u < 4; ++u) e[u] = a.stage_out[rr.x + k + 32 * u];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        a.out_idx[to + k + 32 * u] = e[u].x;
-                        a.out_delta[to + k + 32 * u] = (int32_t)e[u].y;
+                        for (int u = 0; u < 4; ++u) {
+                            a.out_idx[to + k + 32 * u] = e[u].x;
+                            a.out_delta[to + k + 32 * u] = (int32_t)e[u].y;
+                        }
+                    }
+                    for (; k < rr.y; k += 32) {
+                        const uint2 e = a.stage_out[rr.x + k];
+                        a.out_idx[to + k] = e.x;
+                        a.out_delta[to + k] = (int32_t)e.y;
                     }
                 }
-                for (; k < rr.y; k += 32) {
-                    const uint2 e = a.stage_out[rr.x + k];
-                    a.out_idx[to + k] = e.x;
-                    a.out_delta[to + k] = (int32_t)e.y;
-                }
-            }
-        } else {
-            __syncwarp();
-            {  // exclusive prefix of the words' popcounts (nwords <= 32)
-                const uint32_t c = l < (int)nwords ? __popc(fw[w][l]) : 0u;
-                uint32_t inc = c;
+            } else {
+                __syncwarp();
+                {  // exclusive prefix of the words' popcounts (nwords <= 32)
+                    const uint32_t c = l < (int)nwords ? __popc(fw[w][l]) : 0u;
+                    uint32_t inc = c;
 #pragma unroll
-                for (int off = 1; off < 32; off <<= 1) {
-                    const uint32_t y = __shfl_up_sync(VSZ_FULL, inc, off);
-                    if (l >= off) inc += y;
+                    for (int off = 1; off < 32; off <<= 1) {
+                        const uint32_t y = __shfl_up_sync(VSZ_FULL, inc, off);
+                        if (l >= off) inc += y;
+                    }
+                    if (l < (int)nwords) fpre[w][l] = inc - c;
                 }
-                if (l < (int)nwords) fpre[w][l] = inc - c;
-            }
-            __syncwarp();
-            // flagged origins before block k, and k's own flag
-            auto before = [&](uint32_t k) {
-                return fpre[w][k >> 5] + __popc(fw[w][k >> 5] & ((1u << (k & 31)) - 1u));
-            };
-            const bool fits = (uint64_t)to + rr.y <= a.out_cap;
-            for (uint32_t k = l; k < nblk; k += 32) {
-                const uint32_t np = a.blk_off[fb + k] + before(k);
-                a.blk_off[fb + k] = to + np;
-                if (fits && ((fw[w][k >> 5] >> (k & 31)) & 1u)) {
-                    uint64_t idx, tile;
-                    block_origin(g, fb + k, &idx, &tile);
-                    a.out_idx[to + np] = (uint32_t)idx;
-                    a.out_delta[to + np] = a.origin[fb + k];
-                }
-            }
-            if (staged && (uint64_t)rr.x + staged <= a.out_cap && fits) {
-                // block of an entry inside the tile, from its element index
-                const uint32_t nx32 = (uint32_t)g.nx, c0 = (uint32_t)(s * kSegCols), e0 = (uint32_t)(tt * kChunk1D);
-                auto place = [&](uint32_t i, uint2 e) {
-                    const uint32_t k = (g.nd == 1 ? e.x - e0 : e.x % nx32 - c0) / g.b;
-                    const uint32_t pos = to + i + before(k) + ((fw[w][k >> 5] >> (k & 31)) & 1u);
-                    a.out_idx[pos] = e.x;
-                    a.out_delta[pos] = (int32_t)e.y;
+                __syncwarp();
+                // flagged origins before block k, and k's own flag
+                auto before = [&](uint32_t k) {
+                    return fpre[w][k >> 5] + __popc(fw[w][k >> 5] & ((1u << (k & 31)) - 1u));
                 };
-                uint32_t i = l;
-                for (; i + 96 < staged; i += 128) {  // four loads in flight per lane
-                    uint2 e[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) e[u] = a.stage_out[rr.x + i + 32 * u];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) place(i + 32 * u, e[u]);
+                const bool fits = (uint64_t)to + rr.y <= a.out_cap;
+                for (uint32_t k = l; k < nblk; k += 32) {
+                    const uint32_t np = a.blk_off[fb + k] + before(k);
+                    a.blk_off[fb + k] = to + np;
+                    if (fits && ((fw[w][k >> 5] >> (k & 31)) & 1u)) {
+                        uint64_t idx, tile;
+                        block_origin(g, fb + k, &idx, &tile);
+                        a.out_idx[to + np] = (uint32_t)idx;
+                        a.out_delta[to + np] = a.origin[fb + k];
+                    }
                 }
-                for (; i < staged; i += 32) place(i, a.stage_out[rr.x + i]);
+                if (staged && (uint64_t)rr.x + staged <= a.out_cap && fits) {
+                    // block of an entry inside the tile, from its element index
+                    const uint32_t nx32 = (uint32_t)g.nx, c0 = (uint32_t)(s * kSegCols), e0 = (uint32_t)(tt * kChunk1D);
+                    auto place = [&](uint32_t i, uint2 e) {
+                        const uint32_t k = (g.nd == 1 ? e.x - e0 : e.x % nx32 - c0) / g.b;
+                        const uint32_t pos = to + i + before(k) + ((fw[w][k >> 5] >> (k & 31)) & 1u);
+                        a.out_idx[pos] = e.x;
+                        a.out_delta[pos] = (int32_t)e.y;
+                    };
+                    uint32_t i = l;
+                    for (; i + 96 < staged; i += 128) {  // four loads in flight per lane
+                        uint2 e[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) e[u] = a.stage_out[rr.x + i + 32 * u];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) place(i + 32 * u, e[u]);
+                    }
+                    for (; i < staged; i += 32) place(i, a.stage_out[rr.x + i]);
+                }
             }
         }
         if (rr.w && (uint64_t)rr.z + rr.w <= a.fix_cap && (uint64_t)tf + rr.w <= a.fix_cap) {
@@ -256,7 +258,8 @@ __device__ __forceinline__ void compact_chunk_body_slots(uint64_t chunk, int spl
     if (split > 0 && (uint32_t)split >= ns) return;
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     if (w == 0) {  // tile records, chunk-relative tile offsets, tile geometry
-        const uint4 r = l < nt ? a.tiles[t0 + l] : make_uint4(0, 0, 0, 0);
+        // (a chunk without entries has tile records of zeros: not read)
+        const uint4 r = (l < nt && (E | ch.y) != 0u) ? a.tiles[t0 + l] : make_uint4(0, 0, 0, 0);
         uint32_t io = r.y, iff = r.w;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
@@ -304,9 +307,12 @@ __device__ __forceinline__ void compact_chunk_body_slots(uint64_t chunk, int spl
         const uint32_t j = (ibase + i) >> lb, k = (ibase + i) & (bpt - 1u);
         has[u] = i < ntab && k < s_nblk[j < 32u ? j : 0u];
         bk[u] = s_fb[j < 32u ? j : 0u] + k;
-        eo[u] = has[u] ? a.blk_in[bk[u]] : 0u;
-        fl[u] = (has[u] && a.oflag && a.oflag[bk[u]] != 0) ? 1u : 0u;
-        s0[u] = (bp && has[u] && a.slots[bk[u] * S].x != 0xffffffffu) ? 1u : 0u;
+        // a chunk without outliers (E = 0: none staged, no origin outlier)
+        // has every in-tile offset zero and no slot to move from
+        const bool rd = has[u] && E != 0u;
+        eo[u] = rd ? a.blk_in[bk[u]] : 0u;
+        fl[u] = (rd && a.oflag && a.oflag[bk[u]] != 0) ? 1u : 0u;
+        s0[u] = (bp && rd && a.slots[bk[u] * S].x != 0xffffffffu) ? 1u : 0u;
     }
     uint32_t first[kPer], keep[kPer];
 #pragma unroll
