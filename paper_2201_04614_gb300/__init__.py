@@ -295,6 +295,18 @@ def _ptr(t) -> ctypes.c_void_p:
     return ctypes.c_void_p(t.data_ptr() if t is not None and t.numel() > 0 else 0)
 
 
+def _need(t, name: str, itemsize: int, count: int) -> None:
+    """Raise unless t is a contiguous CUDA tensor of itemsize-byte elements
+    holding at least count of them: the C ABI trusts the sizes it is given,
+    so a short buffer must be refused here, before any call."""
+    if t is None or not getattr(t, "is_cuda", False):
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.element_size() != itemsize or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous tensor of {itemsize}-byte elements")
+    if t.numel() < count:
+        raise ValueError(f"{name} holds {t.numel()} elements, the call needs {count}")
+
+
 class Field:
     """Device buffers of one compressed field, and the calls on them.
 
@@ -396,6 +408,7 @@ class Field:
         import torch
         if out is None:
             out = torch.empty(2 * self.p.radius, dtype=torch.int32, device=self.codes.device)
+        _need(out, "out", 4, 2 * self.p.radius)
         _check(lib().vsz_code_histogram(ctypes.byref(self._cp), _ptr(self.codes), _ptr(out),
                                         _stream_handle(stream)), "vsz_code_histogram")
         return out
@@ -644,6 +657,7 @@ class HuffmanBook:
     def __init__(self, hist, nsym: int | None = None, stream=None):
         import torch
         self.nsym = int(nsym if nsym is not None else hist.numel())
+        _need(hist, "hist", 4, self.nsym)
         nb = int(lib().vsz_huffman_book_bytes(self.nsym))
         if nb == 0:
             raise VszError(2 if self.nsym > HUFF_MAX_SYMBOLS else 1, "vsz_huffman_book_bytes")
@@ -679,6 +693,11 @@ def huffman_encode(sym, n: int, book: HuffmanBook, words=None, stream=None, inde
     is returned."""
     import torch
     nc = (n + HUFF_CHUNK - 1) // HUFF_CHUNK
+    _need(sym, "sym", 2, n)
+    if words is not None:
+        _need(words, "words", 4, 0)
+    if index is not None and index is not True:
+        _need(index, "index", 2, 32 * nc)
     off = torch.empty(nc + 1, dtype=torch.int64, device=sym.device)
     if words is None:
         words = torch.empty(max(1, n // 2 + nc + 16), dtype=torch.int32, device=sym.device)  # 16 bits/symbol
@@ -701,6 +720,11 @@ def huffman_encode(sym, n: int, book: HuffmanBook, words=None, stream=None, inde
 def huffman_decode(words, chunk_off, n: int, book: HuffmanBook, out=None, stream=None):
     """Decode n symbols (vsz_huffman_decode); returns (symbols, status)."""
     import torch
+    nc = (n + HUFF_CHUNK - 1) // HUFF_CHUNK
+    _need(words, "words", 4, 0)
+    _need(chunk_off, "chunk_off", 8, nc + 1)
+    if out is not None:
+        _need(out, "out", 2, n)
     if out is None:
         out = torch.empty(max(n, 1), dtype=torch.int16, device=words.device)
     st = torch.empty(1, dtype=torch.int32, device=words.device)
@@ -713,6 +737,12 @@ def huffman_decode_indexed(words, chunk_off, index, n: int, book: HuffmanBook, o
     """Decode n symbols with the decode index (vsz_huffman_decode_indexed):
     a warp per chunk; returns (symbols, status)."""
     import torch
+    nc = (n + HUFF_CHUNK - 1) // HUFF_CHUNK
+    _need(words, "words", 4, 0)
+    _need(chunk_off, "chunk_off", 8, nc + 1)
+    _need(index, "index", 2, 32 * nc)
+    if out is not None:
+        _need(out, "out", 2, n)
     if out is None:
         out = torch.empty(max(n, 1), dtype=torch.int16, device=words.device)
     st = torch.empty(1, dtype=torch.int32, device=words.device)
