@@ -389,6 +389,7 @@ class Field:
         import torch
         if out is None:
             out = torch.empty(max(self.n, 1), dtype=torch.float32, device=self.codes.device)
+        _need(out, "out", 4, self.n)
         _check(lib().vsz_reconstruct(ctypes.byref(self._cp), ctypes.byref(self._cc), _ptr(out), _ptr(self.rws),
                                      RECON_WS_BYTES, _stream_handle(stream)), "vsz_reconstruct")
         return out[: self.n]
@@ -398,6 +399,7 @@ class Field:
         import torch
         if out is None:
             out = torch.empty(max(self.n, 1), dtype=torch.int32, device=self.codes.device)
+        _need(out, "out", 4, self.n)
         _check(lib().vsz_reconstruct_q(ctypes.byref(self._cp), ctypes.byref(self._cc), _ptr(out), _ptr(self.rws),
                                        RECON_WS_BYTES, _stream_handle(stream)), "vsz_reconstruct_q")
         return out[: self.n]

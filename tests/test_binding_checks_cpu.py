@@ -1,4 +1,5 @@
-"""The binding's buffer checks on the entropy-stage calls (host logic, no GPU).
+"""The binding's buffer checks on the entropy-stage and reconstruction calls
+(host logic, no GPU).
 
 The C ABI takes plain pointers and trusts the sizes it is given, so the
 Python binding refuses a buffer that is not a contiguous CUDA tensor of the
@@ -97,3 +98,19 @@ def test_decode_checks_offsets_output_and_index(indexed):
             dec(FakeCuda(50, 4), FakeCuda(4, 8), index=FakeCuda(95, 2))
         with pytest.raises(TypeError):
             dec(FakeCuda(50, 4), FakeCuda(4, 8), index=FakeCuda(96, 4))
+
+
+class FieldShape:
+    """What Field's reconstruction reads before its buffer check: the size."""
+
+    n = 5000
+
+
+@pytest.mark.parametrize("method", [vsz.Field.reconstruct, vsz.Field.reconstruct_q])
+def test_reconstruction_checks_its_output(method):
+    with pytest.raises(ValueError):
+        method(FieldShape(), out=FakeCuda(4999, 4))
+    with pytest.raises(TypeError):
+        method(FieldShape(), out=FakeCuda(5000, 2))
+    with pytest.raises(TypeError):
+        method(FieldShape(), out=FakeHost(5000, 4))
