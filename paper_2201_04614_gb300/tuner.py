@@ -22,7 +22,7 @@ import struct
 
 import numpy as np
 
-from . import Params, VszError, _check, _ptr, _stream_handle, lib, PAD_MODES
+from . import Params, VszError, _check, _need, _ptr, _stream_handle, lib, PAD_MODES
 
 NFEAT, NCLASS, HIDDEN = 12, 12, 64
 NPARAM = HIDDEN * NFEAT + HIDDEN + HIDDEN * HIDDEN + HIDDEN + NCLASS * HIDDEN + NCLASS
@@ -110,6 +110,16 @@ def _xcheck(x, p: Params):
         raise ValueError(f"x has {x.numel()} elements, params describe {p.n}")
 
 
+def _rows_check(X, *per_row):
+    """X must be a matrix of NFEAT features per sample, and every per-sample
+    array must cover its rows: the kernels read them by sample index."""
+    if X.dim() != 2 or X.shape[1] != NFEAT:
+        raise ValueError(f"X must have shape [n, {NFEAT}], not {tuple(X.shape)}")
+    for a in per_row:
+        if a.numel() < X.shape[0]:
+            raise ValueError(f"a per-sample array holds {a.numel()} entries for {X.shape[0]} samples")
+
+
 # ---------------------------------------------------------------- field-level calls
 def features(p: Params, x, out64=None, out32=None, stream=None):
     """The 12 features of a field on the device: (float64[12], float32[12])."""
@@ -119,6 +129,8 @@ def features(p: Params, x, out64=None, out32=None, stream=None):
     dev = x.device
     f64 = out64 if out64 is not None else torch.empty(NFEAT, dtype=torch.float64, device=dev)
     f32 = out32 if out32 is not None else torch.empty(NFEAT, dtype=torch.float32, device=dev)
+    _need(f64, "out64", 8, NFEAT)
+    _need(f32, "out32", 4, NFEAT)
     ws = _ws(L.vsz_tuner_features_workspace_size(), dev)
     _check(L.vsz_tuner_features(ctypes.byref(p.c()), _ptr(x), _ptr(f64), _ptr(f32), _ptr(ws), ws.numel(),
                                 _stream_handle(stream)), "vsz_tuner_features")
@@ -176,6 +188,7 @@ def sampling_autotune(p: Params, x, sample_frac: float = 0.05, iters: int = 3, s
     returns {"block", "ms" (per block size), "sample_elems"}.  Synchronous."""
     torch = _torch()
     L = _bind()
+    _xcheck(x, p)
     wsb = int(L.vsz_sampling_autotune_workspace_size(ctypes.byref(p.c()), float(sample_frac)))
     if wsb == 0:
         raise VszError(1, "vsz_sampling_autotune_workspace_size")
@@ -248,6 +261,7 @@ class MLP:
         X = torch.as_tensor(X, dtype=torch.float32, device=self.device).contiguous()
         M = torch.as_tensor(np.asarray(masks, np.uint32).view(np.int32) if not isinstance(masks, torch.Tensor)
                             else masks, device=self.device).to(torch.int32).contiguous()
+        _rows_check(X, M)
         n = X.shape[0]
         logits = torch.empty((max(n, 1), NCLASS), dtype=torch.float32, device=self.device)
         cls = torch.empty(max(n, 1), dtype=torch.int32, device=self.device)
@@ -264,6 +278,9 @@ class MLP:
         M = torch.as_tensor(np.asarray(masks, np.uint32).view(np.int32) if not isinstance(masks, torch.Tensor)
                             else masks, device=self.device).to(torch.int32).contiguous()
         I = None if idx is None else torch.as_tensor(idx, dtype=torch.int32, device=self.device).contiguous()
+        _rows_check(X, M, Y)
+        if I is not None and I.numel() and bool(((I < 0) | (I >= X.shape[0])).any()):
+            raise ValueError(f"idx holds a sample index outside 0..{X.shape[0] - 1}")
         batch = X.shape[0] if I is None else I.numel()
         g = torch.empty(NPARAM, dtype=torch.float32, device=self.device)
         loss = torch.empty(1, dtype=torch.float32, device=self.device)

@@ -1,5 +1,5 @@
-"""The binding's buffer checks on the entropy-stage and reconstruction calls
-(host logic, no GPU).
+"""The binding's buffer checks on the entropy-stage, reconstruction and
+tuner calls (host logic, no GPU).
 
 The C ABI takes plain pointers and trusts the sizes it is given, so the
 Python binding refuses a buffer that is not a contiguous CUDA tensor of the
@@ -114,3 +114,17 @@ def test_reconstruction_checks_its_output(method):
         method(FieldShape(), out=FakeCuda(5000, 2))
     with pytest.raises(TypeError):
         method(FieldShape(), out=FakeHost(5000, 4))
+
+
+def test_tuner_sample_arrays_must_cover_the_feature_rows():
+    import torch
+    from paper_2201_04614_gb300 import tuner as T
+    X = torch.zeros(5, T.NFEAT)
+    T._rows_check(X, torch.zeros(5), torch.zeros(7))
+    with pytest.raises(ValueError):
+        T._rows_check(X, torch.zeros(4))
+    with pytest.raises(ValueError):
+        T._rows_check(torch.zeros(5, T.NFEAT - 1))
+    with pytest.raises(ValueError):
+        T._rows_check(torch.zeros(5 * T.NFEAT))
+
