@@ -205,6 +205,13 @@ class GpuSlabBackend:
     def __init__(self, job: SlabJob, x, out_cap: int | None = None, fix_cap: int | None = None):
         import torch
         from . import lib
+        if not (getattr(x, "is_cuda", False) and x.dtype == torch.float32 and x.is_contiguous()):
+            raise TypeError("x must be a contiguous float32 CUDA tensor")
+        need = 1
+        for d in job.slab_dims:
+            need *= int(d)
+        if x.numel() != need:
+            raise ValueError(f"x has {x.numel()} values, the slab {tuple(job.slab_dims)} holds {need}")
         self.job, self.x = job, x
         self.L = lib()
         self.st = torch.zeros(4, dtype=torch.int64, device=x.device)  # vsz_slab_stats (32 bytes)

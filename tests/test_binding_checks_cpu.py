@@ -128,3 +128,17 @@ def test_tuner_sample_arrays_must_cover_the_feature_rows():
     with pytest.raises(ValueError):
         T._rows_check(torch.zeros(5 * T.NFEAT))
 
+
+
+def test_slab_backend_needs_the_slab_values():
+    import torch
+    from paper_2201_04614_gb300 import shard
+
+    class FakeF32(FakeCuda):
+        dtype = torch.float32
+
+    job = shard.SlabJob((40, 30, 20), 8, 1e-3, shard.EB_REL, 64, 0, 8, 24)  # 16 planes of 30 x 20
+    with pytest.raises(ValueError):
+        shard.GpuSlabBackend(job, FakeF32(16 * 30 * 20 - 1, 4))
+    with pytest.raises(TypeError):
+        shard.GpuSlabBackend(job, torch.zeros(16 * 30 * 20))  # a host tensor
