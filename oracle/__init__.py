@@ -8,6 +8,7 @@ ctypes and numpy.  It shares no code with the CUDA library.
 
 Parity status per function (what pins it is in tests/test_oracle_*.py):
   resolve_eb, prequant, pad_values, lorenzo_delta, compress, decompress:
+  pinned.  huffman_book / huffman_encode / huffman_decode / huffman_index:
   pinned.  The padding *benefit* (fewer outliers, Sec. V-H) is data
   dependent: parity unpinned, only its trend is checked.
 """
@@ -331,6 +332,26 @@ def huffman_encode(sym, lengths, codes, chunk: int = HUFF_CHUNK):
     if rc:
         raise ValueError(f"oracle huffman_encode failed rc={rc}")
     return words[: int(off[-1])].copy(), off
+
+
+# The decode index (the Huffman stage of Sec. II-B decoded in parallel; the
+# paper decodes serially): the stream is unchanged, and beside it, for chunk
+# c and sub-chunk j of HUFF_LANES per chunk, the bit of chunk c's stream where
+# the sub-chunk's first code begins -- the sum of the lengths of the chunk's
+# codes before it.  Sub-chunks past the end of the data get the chunk's total.
+HUFF_LANES = 32
+
+
+def huffman_index(sym, lengths, chunk: int = HUFF_CHUNK, lanes: int = HUFF_LANES):
+    """Decode index: int64[nchunks * lanes], bit offsets inside each chunk."""
+    sym = np.ascontiguousarray(sym, dtype=np.uint16).reshape(-1)
+    lengths = np.asarray(lengths, np.int64)
+    n = sym.size
+    nchunks = (n + chunk - 1) // chunk
+    bits = np.zeros(nchunks * chunk, np.int64)
+    bits[:n] = lengths[sym]
+    per = bits.reshape(nchunks, lanes, chunk // lanes).sum(axis=2)
+    return (np.cumsum(per, axis=1) - per).reshape(-1)
 
 
 def huffman_decode(words, chunk_off, n, lengths, codes, chunk: int = HUFF_CHUNK):

@@ -178,15 +178,10 @@ def test_truncated_stream_is_reported():
 
 # ---------------------------------------------------------------- decode index
 def _oracle_index(sym, lens):
-    """The decode index from the oracle's code lengths: for chunk c and lane
-    j, the bits of the chunk's codes before code 32 j (the chunk's total for
-    lanes past the data)."""
-    n = sym.size
-    nc = (n + 1023) // 1024
-    bits = np.zeros(nc * 1024, np.int64)
-    bits[:n] = lens[sym].astype(np.int64)
-    per = bits.reshape(nc, 32, 32).sum(axis=2)
-    return (np.cumsum(per, axis=1) - per).astype(np.uint16).reshape(-1)
+    """The oracle's decode index (for chunk c and lane j, the bits of the
+    chunk's codes before code 32 j; the chunk's total for lanes past the
+    data), as the device stores it: uint16."""
+    return oracle.huffman_index(sym, lens).astype(np.uint16)
 
 
 def _indexed_round_trip(sym, nsym, weights, words_shift=0, out_shift=0):

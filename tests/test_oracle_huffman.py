@@ -134,3 +134,67 @@ def test_lone_symbol():
     words, off = oracle.huffman_encode(sym, ln, cw, 64)
     assert off.tolist() == [0, 2, 4] and (words == 0).all()  # 64 bits, then 36 bits: two words each
     assert np.array_equal(oracle.huffman_decode(words, off, 100, ln, cw, 64), sym)
+
+
+def walk_index(words, off, n, ln, cw, chunk, lanes):
+    """The decode index found by reading the packed stream one bit at a time:
+    at every (chunk / lanes)-th code of a chunk, the bit reached so far;
+    each codeword is recognised by its (length, value) in the codebook, and
+    must be the symbol that was encoded (checked by the caller)."""
+    table = {(int(ln[s]), int(cw[s])): s for s in range(len(ln)) if ln[s]}
+    per = chunk // lanes
+    nchunks = (n + chunk - 1) // chunk
+    index, decoded = [], []
+    for c in range(nchunks):
+        base = int(off[c]) * 32
+
+        def bit(k):
+            w = int(words[(base + k) // 32])
+            return (w >> (31 - (base + k) % 32)) & 1
+
+        pos = 0
+        cnt = min(chunk, n - c * chunk)
+        for i in range(chunk):
+            if i % per == 0:
+                index.append(pos)
+            if i >= cnt:
+                continue
+            v, L = 0, 0
+            while (L, v) not in table:
+                v = (v << 1) | bit(pos + L)
+                L += 1
+                assert L <= 64
+            decoded.append(table[(L, v)])
+            pos += L
+    return np.array(index, np.int64), np.array(decoded, np.uint16)
+
+
+@pytest.mark.parametrize("n,chunk,lanes,kind", [(1, 1024, 32, "geo"), (1000, 1024, 32, "geo"),
+                                                (3 * 1024 + 517, 1024, 32, "fib"), (2500, 256, 8, "geo"),
+                                                (4096, 1024, 32, "lone")])
+def test_decode_index_against_a_bit_walk(n, chunk, lanes, kind):
+    rng = np.random.default_rng(n)
+    if kind == "fib":  # codewords up to 39 bits
+        f = [1, 1]
+        while len(f) < 40:
+            f.append(f[-1] + f[-2])
+        hist = np.array(f, np.uint32)
+        sym = rng.integers(0, 40, n).astype(np.uint16)
+    elif kind == "lone":
+        sym = np.full(n, 3, np.uint16)
+        hist = np.bincount(sym, minlength=8).astype(np.uint32)
+    else:
+        sym = np.minimum(rng.geometric(0.1, n) - 1, 299).astype(np.uint16)
+        hist = np.bincount(sym, minlength=300).astype(np.uint32)
+    ln, cw = oracle.huffman_book(hist)
+    words, off = oracle.huffman_encode(sym, ln, cw, chunk)
+    want, decoded = walk_index(words, off, n, ln, cw, chunk, lanes)
+    assert np.array_equal(decoded, sym)
+    got = oracle.huffman_index(sym, ln, chunk, lanes)
+    assert got.tolist() == want.tolist()
+    # a sub-chunk past the data starts at the chunk's end; the chunk fits its words
+    nc = (n + chunk - 1) // chunk
+    last = got.reshape(nc, lanes)[-1]
+    full = (n - (nc - 1) * chunk + chunk // lanes - 1) // (chunk // lanes)
+    assert (last[full:] == int(ln.astype(np.int64)[sym[(nc - 1) * chunk:]].sum())).all()
+    assert all(got.reshape(nc, lanes)[c, -1] <= 32 * int(off[c + 1] - off[c]) for c in range(nc))
