@@ -103,3 +103,16 @@ def test_calls_without_gpu_fail_cleanly(vsz):
     assert rc == 1
     rc = L.vsz_reconstruct(ctypes.byref(p), ctypes.byref(cc), None, None, 0, None)
     assert rc == 1
+
+
+def test_entropy_calls_reject_missing_buffers_on_the_host(vsz):
+    """The Huffman calls refuse a missing codebook, status word or offsets
+    before any GPU work; the codebook size follows the symbol limit."""
+    L = vsz.lib()
+    assert L.vsz_huffman_book_bytes(0) == 0
+    assert L.vsz_huffman_book_bytes(vsz.HUFF_MAX_SYMBOLS + 1) == 0
+    assert L.vsz_huffman_book_bytes(1024) > L.vsz_huffman_book_bytes(16) > 0
+    assert L.vsz_huffman_encode_indexed(None, 10, None, 1024, None, 0, None, None, None, None, 0, None) == 1
+    assert L.vsz_huffman_decode_indexed(None, 0, None, None, 10, None, 1024, None, None, None) == 1
+    assert L.vsz_huffman_decode(None, 0, None, 10, None, 1024, None, None, None) == 1
+    assert L.vsz_huffman_decode_indexed(None, 0, None, None, 10, None, 0, None, None, None) == 1  # nsym 0
